@@ -1,0 +1,338 @@
+"""Benchmark of the forward-model hot path (model cube -> PSF x LSF convolution
+-> moments -> masked chi-squared) on the Fabry-Perot-like workload: one
+192 x 192 x 48 galaxy (10 km/s channels, PSF FWHM 3 px, LSF FWHM 30 km/s,
+S/N < 3 masked) and 400 parameter sets per step -- the live points of one
+nested-sampling iteration, evaluated in one batched launch.
+
+A step is one pass of the whole hot path over one batch of 400 models.  The
+parameter sets are drawn from the uniform prior of the workload (a fresh batch
+per step, resident in HBM before timing starts); L2 is flushed (a 256 MiB
+write) between timed steps.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbk|reference]
+
+Under torchrun each rank evaluates its own batches (independent models, no
+data-path collective); value is the total over ranks divided by the slowest
+rank's time.  `--impl reference` times the FP64 CPU oracle on the host cores
+instead (a bounded sample of the same workload per step).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1510_01815_gb300 import synth  # noqa: E402
+
+METRIC = "model-cube evals/s and galaxy fits/s at matched chi2 (learned+batched vs plain)"
+OPS_PER_EXT_VOXEL = 7  # minimal FP32 + MUFU lane ops of the line-sampling loop
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gbk", choices=["gbk", "reference"])
+    ap.add_argument("--models", type=int, default=synth.FP_LIVE_POINTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def ext_dims(g):
+    """(ex, ey, ez) of the extended grid: data grid plus the kernel radii
+    R = ceil(4 sigma) on each side (PSF in pixels, LSF in channels)."""
+    import math
+    s_xy = g.psf_fwhm / 2.3548200450309493
+    s_z = g.lsf_fwhm / 2.3548200450309493 / g.dv
+    R = math.ceil(g.halo_sigmas * s_xy) if s_xy > 0 else 0
+    Rz = math.ceil(g.halo_sigmas * s_z) if (s_z > 0 and g.lsf_mode == 0) else 0
+    return g.nx + 2 * R, g.ny + 2 * R, g.nz + 2 * Rz
+
+
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "0x1"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+def make_galaxy(gbk, torch, g, seed, device):
+    """One synthetic Fabry-Perot galaxy: true parameters from the prior, maps
+    from the library at those parameters, seeded noise (5 km/s on v,
+    5 sqrt(2) on sigma), S/N < 3 and 2% dead-fibre masks."""
+    rng = np.random.default_rng(seed)
+    p_true = synth.draw_fp_params(rng, 1)
+    maps = gbk.eval_maps(g, torch.from_numpy(p_true), device=device).cpu().numpy()[0]
+    shape = (g.ny, g.nx)
+    v = (maps[1] + synth.gaussian_noise(rng, shape, 5.0)).astype(np.float32)
+    s = (maps[2] + synth.gaussian_noise(rng, shape, 5.0 * np.sqrt(2.0))).astype(np.float32)
+    wv, ws = synth.weights(shape, 5.0)
+    mask = (synth.sn_mask(maps[0]) * synth.dead_fibre_mask(rng, shape)).astype(np.uint8)
+    return p_true[0], (v, s, wv, ws, mask)
+
+
+def cpu_baseline(g, obs_np, n_models, seed):
+    """The FP64 oracle, as it stands, on all host cores: one batch of models
+    evaluated with OpenMP (one model per core at a time)."""
+    import oracle
+    cores = oracle.max_threads()
+    n = max(4, cores)
+    rng = np.random.default_rng(seed + 99)
+    ps = synth.draw_fp_params(rng, n)
+    o = oracle.Obs(*obs_np)
+    t = time.perf_counter()
+    oracle.chi2_batch(oracle.Geom(**g.asdict()), ps, o, nthreads=cores)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the %d models of one step (192x192x48, direct 3-D convolution, FP64), "
+                      "OpenMP over models, %.1f s" % (n, n_models, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    g = synth.FP_GEOM
+    cores = oracle.max_threads()
+    per_step = max(4, cores)
+    rng = np.random.default_rng(2015)
+    p_true = synth.draw_fp_params(rng, 1)[0]
+    og = oracle.Geom(**g.asdict())
+    m = oracle.evaluate(og, p_true)
+    shape = (g.ny, g.nx)
+    wv, wsig = synth.weights(shape, 5.0)
+    obs = oracle.Obs((m[1] + rng.normal(0, 5, shape)).astype(np.float32),
+                     (m[2] + rng.normal(0, 7.07, shape)).astype(np.float32), wv, wsig,
+                     (synth.sn_mask(m[0]) * synth.dead_fibre_mask(rng, shape)).astype(np.uint8))
+    pool = synth.draw_fp_params(rng, per_step * (args.warmup + args.steps))
+    for s in range(args.warmup):
+        oracle.chi2_batch(og, pool[s * per_step:(s + 1) * per_step], obs, nthreads=cores)
+    t = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        oracle.chi2_batch(og, pool[s * per_step:(s + 1) * per_step], obs, nthreads=cores)
+    dt = time.perf_counter() - t
+    value = per_step * args.steps / dt
+    sample = "%d of the %d models per step (192x192x48), FP64 oracle, OpenMP over models" % (
+        per_step, args.models)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fabry-perot 192x192x48, 400 live points per step", "models_per_step": per_step,
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_gbk(args):
+    import torch
+    from paper_1510_01815_gb300 import build as gbuild
+    gbuild.build()
+    from paper_1510_01815_gb300 import gbk
+
+    ws, rank, local = dist_info()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+
+    g = synth.FP_GEOM
+    n = args.models
+    K, W = args.steps, args.warmup
+    p_true, obs_np = make_galaxy(gbk, torch, g, 2015, dev)
+    obs = gbk.Obs.from_numpy(*obs_np, device=dev)
+    rng = np.random.default_rng(7000 + rank)
+    pool_np = synth.draw_fp_params(rng, n * (K + W)).reshape(K + W, n, synth.NPAR)
+    pool = torch.from_numpy(pool_np).to(dev)
+    chi2 = torch.empty((K + W, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s):
+        gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_FUSED, None, stream)
+
+    for s in range(W):
+        step(s)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if not args.quick:
+        clocks.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        step(W + k)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if not args.quick else None
+    times = [starts[k].elapsed_time(ends[k]) for k in range(K)]
+    total_ms = float(sum(times))
+    assert torch.isfinite(chi2[W:]).all(), "non-finite chi2 in the timed steps"
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / K
+    value = ws * n * K / (total_ms * 1e-3)
+
+    out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "fabry-perot 192x192x48 at 10 km/s, PSF 3 px, LSF 30 km/s, "
+                                  "400 live points per step (one batched launch)",
+                      "models_per_step": n, "path": "fused", "l2": "flushed between steps (256 MiB write)",
+                      "parallelism": "replicas" if ws > 1 else "single"},
+           "gpu_launches": K}
+    if args.quick:
+        if rank == 0:
+            print(json.dumps(out))
+        return
+
+    # ---- roofline of the fused kernel: ALU (FP32 issue + MUFU ex2) ----
+    ex, ey, ez = ext_dims(g)
+    ext_vox = n * ex * ey * ez
+    r32, rmu = gbk.gbk_measure_alu_peak(stream)
+    t_min_per_vox = max(OPS_PER_EXT_VOXEL / r32, 1.0 / rmu)
+    peak_ops = OPS_PER_EXT_VOXEL / t_min_per_vox
+    achieved_ops = OPS_PER_EXT_VOXEL * ext_vox / (ms_step * 1e-3)
+    out["roofline"] = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                       "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                       "kernel": "fused_eval_kernel",
+                       "basis": "%d FP32+MUFU lane ops per extended voxel (%d x %d x %d per model); peak = "
+                                "measured FFMA issue rate %.1f Tops/s and ex2 rate %.1f Tops/s"
+                                % (OPS_PER_EXT_VOXEL, ex, ey, ez, r32 / 1e12, rmu / 1e12),
+                       "peak_source": "measured on this device by gbk_measure_alu_peak"}
+    out["clocks"] = clk
+
+    # ---- end to end through the public API with host buffers ----
+    pin_params = torch.from_numpy(pool_np).pin_memory()
+    pin_chi2 = torch.empty((K + W, n), dtype=torch.float64).pin_memory()
+    pin_obs = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in obs_np]
+    d_params = torch.empty((n, synth.NPAR), dtype=torch.float64, device=dev)
+    d_obs = [torch.empty(a.shape, dtype=a.dtype, device=dev) for a in pin_obs]
+    e_obs = gbk.Obs(*d_obs)
+    d_chi2 = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def e2e_step(s):
+        d_params.copy_(pin_params[s], non_blocking=True)
+        for d, h in zip(d_obs, pin_obs):
+            d.copy_(h, non_blocking=True)
+        gbk.gbk_chi2(g, d_params, e_obs, d_chi2, None, gbk.PATH_AUTO, None, stream)
+        pin_chi2[s].copy_(d_chi2, non_blocking=True)
+
+    for s in range(W):
+        e2e_step(s)
+    torch.cuda.synchronize()
+    e_ms = 0.0
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step(W + k)
+        b.record(stream)
+        b.synchronize()
+        e_ms += a.elapsed_time(b)
+    h2d = n * synth.NPAR * 8 + sum(int(h.numel() * h.element_size()) for h in pin_obs)
+    if dist:
+        t = torch.tensor([e_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+    out["e2e"] = {"value": ws * n * K / (e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": n * 8}
+    ok = np.allclose(pin_chi2[W:].numpy(), chi2[W:].cpu().numpy(), rtol=0, atol=0)
+    out["e2e"]["matches_device_run"] = bool(ok)
+    out["gpu_launches_e2e"] = K
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, obs_np, n, 2015)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gbk(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * gbk.h -- C ABI of the GB300 disc-galaxy kinematic-model library (libgbk.so).
+ *
+ * The library evaluates the intensity-cube forward model of Bekiaris et al.
+ * 2015 (arXiv:1510.01815), Sec. 2: for each parameter set it builds the
+ * (x, y, v) cube of a thin exponential disc with an arctan rotation curve and
+ * a constant intrinsic dispersion (Sec. 2.1, Eqs. 1-8), convolves it with a
+ * Gaussian PSF x LSF kernel (Eq. 9, Sec. 2.2.3), down-samples it (Sec. 2.2.4),
+ * takes the moment-0/1/2 maps (Sec. 2.2.5) and reduces the masked chi-squared
+ * of Eq. 11 against observed velocity and dispersion maps (Sec. 2.2.6).
+ *
+ * Conventions shared by every entry point
+ *  - All arithmetic runs in the library's CUDA kernels on the device of the
+ *    calling thread.  Cubes, maps and residuals are FP32; parameters and
+ *    chi-squared values are FP64.
+ *  - Every buffer is owned by the caller.  Pointers documented as "device"
+ *    must be device (or managed) memory of the current device; "host" means
+ *    ordinary host memory.  The library never allocates device memory: entry
+ *    points that need scratch take a caller-provided workspace whose size is
+ *    given by the matching *_workspace_bytes() query.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Entry
+ *    points marked "asynchronous" only enqueue work on it.
+ *  - Every function returns a gbk_status.  Arguments are validated on the
+ *    host before anything is launched; on error nothing is launched and
+ *    gbk_last_error() returns a message for the calling thread.  No function
+ *    aborts, traps or prints.
+ *  - Layouts are row-major with x fastest: a cube is [model][z][y][x], a map
+ *    set is [model][3][y][x] = (m0, m1, m2), residuals are
+ *    [model][2][y][x] = (velocity, dispersion).
+ *  - Parameter vectors are GBK_NPAR doubles in the order of the enum below:
+ *    centre (pixels), position angle and inclination (degrees), systemic and
+ *    asymptotic velocities (km/s), turn-over radius (pixels), intrinsic
+ *    dispersion (km/s), central surface brightness and exponential scale
+ *    length (pixels).  Pixel centres sit at integer coordinates 0..N-1;
+ *    channel k has velocity vc + (k - (nz-1)/2) dv.
+ */
+#ifndef GBK_API_H_INCLUDED
+#define GBK_API_H_INCLUDED
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GBK_API __attribute__((visibility("default")))
+#else
+#define GBK_API
+#endif
+
+typedef int32_t gbk_status;
+
+#define GBK_OK          0
+#define GBK_EINVAL      1  /* an argument failed validation                    */
+#define GBK_ECUDA       2  /* a CUDA runtime call failed (message has details) */
+#define GBK_EWORKSPACE  3  /* the workspace is missing or too small            */
+#define GBK_EUNSUPPORTED 4 /* a valid request this build cannot serve          */
+
+/* Parameter order (Sec. 2.1; Vmax is the paper's V_t, h its r_0). */
+enum {
+    GBK_X0 = 0, GBK_Y0, GBK_PA, GBK_INCL, GBK_VSYS, GBK_VMAX, GBK_RT, GBK_SIG0,
+    GBK_I0, GBK_H, GBK_NPAR
+};
+
+/* Observation geometry (host struct, passed by pointer).
+ *  nx, ny, nz    data cube size: spaxels along x, y and velocity channels (>= 1)
+ *  upsample      model upsampling factor u >= 1 (Sec. 2.2.2, Sec. 2.2.4)
+ *  dv            channel width in km/s (> 0)
+ *  vc            velocity of the band centre in km/s
+ *  psf_fwhm      PSF FWHM in pixels (>= 0; 0 = no spatial convolution)
+ *  lsf_fwhm      LSF FWHM in km/s (>= 0)
+ *  lsf_mode      0: the LSF is a convolution along velocity (Eq. 9 as
+ *                written); 1: the LSF is folded into the line width in
+ *                quadrature and only the PSF is convolved
+ *  halo_sigmas   kernel truncation radius in standard deviations (> 0,
+ *                usually 4): R = ceil(halo_sigmas * sigma) on each axis.
+ * The Gaussian kernels are sampled at integer offsets |j| <= R and
+ * normalised to unit sum per axis; the model is evaluated on the data grid
+ * extended by R on every side and the "valid" linear convolution is kept. */
+typedef struct gbk_geom {
+    int32_t nx, ny, nz;
+    int32_t upsample;
+    double dv;
+    double vc;
+    double psf_fwhm;
+    double lsf_fwhm;
+    int32_t lsf_mode;
+    int32_t reserved;   /* must be 0 */
+    double halo_sigmas;
+} gbk_geom;
+
+/* Observed maps of one galaxy, each ny*nx, device memory.
+ *  v_obs, s_obs  observed velocity and dispersion maps (km/s)
+ *  w_v, w_s      weights 1/E_v and sqrt(W)/E_s (Eq. 11 with W folded in)
+ *  mask          1 = use the spaxel, 0 = leave it out */
+typedef struct gbk_obs {
+    const float *v_obs;
+    const float *s_obs;
+    const float *w_v;
+    const float *w_s;
+    const uint8_t *mask;
+} gbk_obs;
+
+/* Evaluation paths (the `flags` argument of gbk_chi2). */
+#define GBK_PATH_AUTO    0u  /* fused unless the request needs the staged path    */
+#define GBK_PATH_FUSED   1u  /* one kernel; the cube never leaves the SM           */
+#define GBK_PATH_STAGED  2u  /* model cube -> separable conv -> moments, via HBM   */
+
+/* Bytes of workspace gbk_eval_cubes / gbk_chi2 need for n_models models on
+ * the given path (0 when the path needs none).  Host function; returns 0 and
+ * sets the last error on invalid arguments. */
+GBK_API size_t gbk_workspace_bytes(const gbk_geom *g, int32_t n_models, uint32_t flags);
+
+/* Forward model, Sec. 2.2.2-2.2.5.  Asynchronous.
+ *  g         geometry (host)
+ *  n_models  number of parameter sets (>= 0; 0 is a no-op)
+ *  params    device, [n_models][GBK_NPAR] FP64
+ *  cubes     device, [n_models][nz][ny][nx] FP32, or NULL.  When non-NULL the
+ *            staged path runs and the convolved, down-sampled cube is written.
+ *  maps      device, [n_models][3][ny][nx] FP32 (m0, m1, m2), or NULL.
+ *            m0 = sum over channels, m1 = intensity-weighted mean velocity,
+ *            m2 = intensity-weighted standard deviation.  A spectrum with
+ *            m0 <= 1e-20 * I0 is invalid and gets (0, Vsys, 0).
+ *  workspace device scratch of gbk_workspace_bytes(g, n_models,
+ *            cubes ? GBK_PATH_STAGED : GBK_PATH_FUSED) bytes (may be NULL
+ *            when that is 0).
+ * Validation: sizes >= 1, dv > 0, psf/lsf >= 0, halo_sigmas > 0, and for
+ * every model 0 <= i < 90 deg, r_t > 0, sigma0 > 0, I0 > 0, h > 0 -- the
+ * parameter checks run on the device and invalid models get NaN maps and
+ * chi-squared (the host cannot read device parameters without a sync). */
+GBK_API gbk_status gbk_eval_cubes(const gbk_geom *g, int32_t n_models, const double *params,
+                          float *cubes, float *maps, void *workspace, size_t ws_bytes,
+                          void *stream);
+
+/* Masked chi-squared of Eq. 11 for n_models parameter sets against one
+ * galaxy's observed maps.  Asynchronous.
+ *  obs     host struct of device pointers (see gbk_obs)
+ *  chi2    device, [n_models] FP64 (required)
+ *  resid   device, [n_models][2][ny][nx] FP32 weighted residuals
+ *          w_v (m1 - v_obs) and w_s (m2 - s_obs), 0 where masked or
+ *          invalid; or NULL
+ *  flags   GBK_PATH_AUTO, GBK_PATH_FUSED or GBK_PATH_STAGED.
+ * The reduction order is fixed, so results are bitwise reproducible. */
+GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *params,
+                    const gbk_obs *obs, double *chi2, float *resid, uint32_t flags,
+                    void *workspace, size_t ws_bytes, void *stream);
+
+/* Eq. 11 alone, from caller-supplied FP32 maps [n_models][3][ny][nx]
+ * (device).  Spaxels with m0 <= 0 count as invalid.  Asynchronous; needs
+ * no workspace. */
+GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, const float *maps,
+                              const gbk_obs *obs, double *chi2, float *resid, void *stream);
+
+/* Diagnostics (no counterpart in the paper): measured lane-operation rates
+ * of the two ALU pipes the fused evaluator is bound by, FP32 FMA and the
+ * MUFU base-2 exponential, on the current device (each a 2-pass timed run
+ * of independent dependency chains on every SM).  Synchronises `stream`.
+ *  ffma_lane_ops_per_s, ex2_lane_ops_per_s   host outputs. */
+GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ex2_lane_ops_per_s,
+                                        void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+GBK_API const char *gbk_last_error(void);
+
+/* Library version string. */
+GBK_API const char *gbk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBK_API_H_INCLUDED */

@@ -1,0 +1,298 @@
+// gbk_api.cu -- C ABI entry points of libgbk.so: argument validation, path
+// selection, workspace layout and kernel launches.  All model arithmetic is in
+// the kernels (k_fused.cu, k_staged.cu).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "gbk_api_internal.h"
+#include "k_fused.h"
+#include "k_staged.h"
+
+namespace gbk {
+
+static thread_local std::string t_last_error;
+
+gbk_status fail(gbk_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return code;
+}
+
+gbk_status ok()
+{
+    t_last_error.clear();
+    return GBK_OK;
+}
+
+gbk_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(GBK_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+gbk_status derive_geom(const gbk_geom *in, Geom *g)
+{
+    if (!in) return fail(GBK_EINVAL, "geometry pointer is NULL");
+    if (in->nx < 1 || in->ny < 1 || in->nz < 1)
+        return fail(GBK_EINVAL, "cube size must be >= 1 (got %d x %d x %d)", in->nx, in->ny, in->nz);
+    if (in->upsample < 1 || in->upsample > 16) return fail(GBK_EINVAL, "upsample must be in 1..16");
+    if (!(std::isfinite(in->dv) && in->dv > 0.0)) return fail(GBK_EINVAL, "dv must be finite and > 0");
+    if (!std::isfinite(in->vc)) return fail(GBK_EINVAL, "vc must be finite");
+    if (!finite_nonneg(in->psf_fwhm)) return fail(GBK_EINVAL, "psf_fwhm must be finite and >= 0");
+    if (!finite_nonneg(in->lsf_fwhm)) return fail(GBK_EINVAL, "lsf_fwhm must be finite and >= 0");
+    if (in->lsf_mode != 0 && in->lsf_mode != 1) return fail(GBK_EINVAL, "lsf_mode must be 0 or 1");
+    if (in->reserved != 0) return fail(GBK_EINVAL, "reserved must be 0");
+    if (!(std::isfinite(in->halo_sigmas) && in->halo_sigmas > 0.0 && in->halo_sigmas <= 16.0))
+        return fail(GBK_EINVAL, "halo_sigmas must be in (0, 16]");
+    const int u = in->upsample;
+    double sxy = (double)u * in->psf_fwhm / kFwhmPerSigma;
+    int R = sxy > 0.0 ? (int)std::ceil(in->halo_sigmas * sxy) : 0;
+    double sz = 0.0;
+    int Rz = 0;
+    if (in->lsf_mode == 0) {
+        sz = (double)u * (in->lsf_fwhm / kFwhmPerSigma) / in->dv;
+        Rz = sz > 0.0 ? (int)std::ceil(in->halo_sigmas * sz) : 0;
+    }
+    if (R > kMaxRadius || Rz > kMaxRadius)
+        return fail(GBK_EUNSUPPORTED, "kernel radius %d/%d exceeds the supported %d", R, Rz, kMaxRadius);
+    g->nx = in->nx; g->ny = in->ny; g->nz = in->nz; g->u = u;
+    g->R = R; g->Rz = Rz;
+    g->nxf = u * in->nx; g->nyf = u * in->ny; g->nzf = u * in->nz;
+    g->ex = g->nxf + 2 * R; g->ey = g->nyf + 2 * R; g->ez = g->nzf + 2 * Rz;
+    long long ext_elems = (long long)g->ex * g->ey * g->ez;
+    if (ext_elems > (1LL << 31) - 1 || (long long)g->nxf * g->nyf > (1LL << 28))
+        return fail(GBK_EUNSUPPORTED, "cube too large for one model (%lld extended voxels)", ext_elems);
+    g->dv = (float)in->dv;
+    g->vc = (float)in->vc;
+    g->sig_xy = (float)sxy;
+    g->sig_z = (float)sz;
+    g->sig_lsf_kms = (float)(in->lsf_fwhm / kFwhmPerSigma);
+    g->lsf_mode = in->lsf_mode;
+    return GBK_OK;
+}
+
+// Checks that p is usable by a kernel on the current device.
+gbk_status check_device_ptr(const void *p, const char *name, size_t align)
+{
+    if (!p) return fail(GBK_EINVAL, "%s is NULL", name);
+    if (((uintptr_t)p) % align != 0) return fail(GBK_EINVAL, "%s is not %zu-byte aligned", name, align);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GBK_EINVAL, "%s is not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(GBK_EINVAL, "%s must be device or managed memory", name);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(GBK_EINVAL, "%s lives on device %d, current device is %d", name, at.device, dev);
+    return GBK_OK;
+}
+
+gbk_status check_obs(const gbk_obs *obs)
+{
+    if (!obs) return fail(GBK_EINVAL, "obs is NULL");
+    gbk_status s;
+    if ((s = check_device_ptr(obs->v_obs, "obs.v_obs", 4))) return s;
+    if ((s = check_device_ptr(obs->s_obs, "obs.s_obs", 4))) return s;
+    if ((s = check_device_ptr(obs->w_v, "obs.w_v", 4))) return s;
+    if ((s = check_device_ptr(obs->w_s, "obs.w_s", 4))) return s;
+    if ((s = check_device_ptr(obs->mask, "obs.mask", 1))) return s;
+    return GBK_OK;
+}
+
+bool fused_config(const Geom &g, int *cs, int *band)
+{
+    if (g.u != 1) return false;
+    const size_t target = 110 * 1024;
+    for (int pass = 0; pass < 2; ++pass) {
+        size_t limit = pass == 0 ? target : (size_t)kFusedMaxSmem;
+        for (int c = 1; c <= kFusedMaxCluster; c *= 2) {
+            int b = (g.ey + c - 1) / c;
+            if (fused_smem_bytes_host(g, b) <= limit) {
+                *cs = c;
+                *band = b;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Staged workspace: [ext][fine (u > 1)][data (if not caller's)][partials].
+struct StagedLayout {
+    int e_pitch;
+    size_t e_stride, f_stride, d_stride;
+    size_t off_ext, off_fine, off_data, off_part, total;
+    int bpm;
+};
+
+StagedLayout staged_layout(const Geom &g, int n, bool own_data, bool want_partials)
+{
+    StagedLayout L;
+    L.e_pitch = (g.ex + 3) & ~3;
+    L.e_stride = (size_t)g.ez * g.ey * L.e_pitch;
+    L.f_stride = (size_t)g.nzf * g.nyf * g.nxf;
+    L.d_stride = (size_t)g.nz * g.ny * g.nx;
+    L.bpm = (g.nx * g.ny + 255) / 256;
+    size_t off = 0;
+    L.off_ext = off; off += align256(sizeof(float) * L.e_stride * n);
+    L.off_fine = off; if (g.u > 1) off += align256(sizeof(float) * L.f_stride * n);
+    L.off_data = off; if (own_data) off += align256(sizeof(float) * L.d_stride * n);
+    L.off_part = off; if (want_partials) off += align256(sizeof(double) * L.bpm * n);
+    L.total = off;
+    return L;
+}
+
+}  // namespace gbk
+
+using namespace gbk;
+
+extern "C" {
+
+const char *gbk_last_error(void) { return t_last_error.c_str(); }
+
+const char *gbk_version(void) { return "gbk 0.1 (sm_103a)"; }
+
+size_t gbk_workspace_bytes(const gbk_geom *gin, int32_t n_models, uint32_t flags)
+{
+    ok();
+    Geom g;
+    if (derive_geom(gin, &g) != GBK_OK) return 0;
+    if (n_models < 0) { fail(GBK_EINVAL, "n_models must be >= 0"); return 0; }
+    int cs, band;
+    bool fused_ok = fused_config(g, &cs, &band);
+    if (flags == GBK_PATH_FUSED || (flags == GBK_PATH_AUTO && fused_ok)) return 0;
+    return staged_layout(g, n_models, true, true).total;
+}
+
+static gbk_status run_staged(const Geom &g, int32_t n, const double *params, float *cubes, float *maps,
+                             const gbk_obs *obs, double *chi2, float *resid, void *ws, size_t ws_bytes,
+                             cudaStream_t st)
+{
+    bool own_data = (cubes == nullptr);
+    StagedLayout L = staged_layout(g, n, own_data, chi2 != nullptr);
+    if (L.total > 0) {
+        if (!ws) return fail(GBK_EWORKSPACE, "the staged path needs %zu bytes of workspace", L.total);
+        if (ws_bytes < L.total)
+            return fail(GBK_EWORKSPACE, "workspace of %zu bytes is smaller than the %zu needed", ws_bytes, L.total);
+        gbk_status s = check_device_ptr(ws, "workspace", 256);
+        if (s) return s;
+    }
+    char *base = (char *)ws;
+    StagedArgs a = {};
+    a.g = g;
+    a.n_models = n;
+    a.params = params;
+    a.ext = (float *)(base + L.off_ext);
+    a.e_pitch = L.e_pitch;
+    a.e_model_stride = L.e_stride;
+    a.data = own_data ? (float *)(base + L.off_data) : cubes;
+    a.d_model_stride = L.d_stride;
+    if (g.u > 1) {
+        a.fine = (float *)(base + L.off_fine);
+        a.f_model_stride = L.f_stride;
+    } else {
+        a.fine = a.data;
+        a.f_model_stride = L.d_stride;
+    }
+    a.maps = maps;
+    a.chi2 = chi2;
+    a.resid = resid;
+    a.partials = chi2 ? (double *)(base + L.off_part) : nullptr;
+    if (obs) a.obs = *obs;
+    bool want_moments = (maps || chi2 || resid);
+    cudaError_t e = launch_staged(a, want_moments, st);
+    if (e != cudaSuccess) return cuda_fail(e, "staged launch");
+    return ok();
+}
+
+static gbk_status run_fused(const Geom &g, int32_t n, const double *params, float *maps, const gbk_obs *obs,
+                            double *chi2, float *resid, cudaStream_t st)
+{
+    FusedArgs a = {};
+    if (!fused_config(g, &a.cs, &a.band))
+        return fail(GBK_EUNSUPPORTED, "the fused path cannot serve this geometry (upsample %d, %d x %d)", g.u,
+                    g.nx, g.ny);
+    a.g = g;
+    a.n_models = n;
+    a.params = params;
+    if (obs) a.obs = *obs;
+    a.maps = maps;
+    a.chi2 = chi2;
+    a.resid = resid;
+    if (n == 0) return ok();
+    cudaError_t e = launch_fused(a, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+    return ok();
+}
+
+gbk_status gbk_eval_cubes(const gbk_geom *gin, int32_t n_models, const double *params, float *cubes,
+                          float *maps, void *workspace, size_t ws_bytes, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    if (n_models < 0) return fail(GBK_EINVAL, "n_models must be >= 0");
+    if (n_models == 0) return ok();
+    if ((s = check_device_ptr(params, "params", 8))) return s;
+    if (cubes && (s = check_device_ptr(cubes, "cubes", 16))) return s;
+    if (maps && (s = check_device_ptr(maps, "maps", 4))) return s;
+    if (!cubes && !maps) return ok();
+    cudaStream_t st = (cudaStream_t)stream;
+    int cs, band;
+    if (cubes || !fused_config(g, &cs, &band))
+        return run_staged(g, n_models, params, cubes, maps, nullptr, nullptr, nullptr, workspace, ws_bytes, st);
+    return run_fused(g, n_models, params, maps, nullptr, nullptr, nullptr, st);
+}
+
+gbk_status gbk_chi2(const gbk_geom *gin, int32_t n_models, const double *params, const gbk_obs *obs,
+                    double *chi2, float *resid, uint32_t flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    if (n_models < 0) return fail(GBK_EINVAL, "n_models must be >= 0");
+    if (flags > GBK_PATH_STAGED) return fail(GBK_EINVAL, "unknown flags 0x%x", flags);
+    if (n_models == 0) return ok();
+    if ((s = check_device_ptr(params, "params", 8))) return s;
+    if ((s = check_device_ptr(chi2, "chi2", 8))) return s;
+    if (resid && (s = check_device_ptr(resid, "resid", 4))) return s;
+    if ((s = check_obs(obs))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int cs, band;
+    bool fused_ok = fused_config(g, &cs, &band);
+    if (flags == GBK_PATH_STAGED || (flags == GBK_PATH_AUTO && !fused_ok))
+        return run_staged(g, n_models, params, nullptr, nullptr, obs, chi2, resid, workspace, ws_bytes, st);
+    return run_fused(g, n_models, params, nullptr, obs, chi2, resid, st);
+}
+
+gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, const float *maps, const gbk_obs *obs,
+                              double *chi2, float *resid, void *stream)
+{
+    if (nx < 1 || ny < 1) return fail(GBK_EINVAL, "map size must be >= 1");
+    if (n_models < 0) return fail(GBK_EINVAL, "n_models must be >= 0");
+    if (n_models == 0) return ok();
+    gbk_status s;
+    if ((s = check_device_ptr(maps, "maps", 4))) return s;
+    if ((s = check_device_ptr(chi2, "chi2", 8))) return s;
+    if (resid && (s = check_device_ptr(resid, "resid", 4))) return s;
+    if ((s = check_obs(obs))) return s;
+    cudaError_t e = launch_chi2_maps(nx, ny, n_models, maps, *obs, chi2, resid, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "chi2_from_maps launch");
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// gbk_internal.cuh -- device-side pieces shared by the library's kernels.
+//
+// Model: Bekiaris et al. 2015, Sec. 2.1 (Eqs. 1-8).  Everything here runs on
+// the GPU; the host side only validates arguments and launches.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gbk.h"
+
+namespace gbk {
+
+constexpr double kFwhmPerSigma = 2.3548200450309493;  // 2 sqrt(2 ln 2)
+constexpr float kInvalidFraction = 1e-20f;            // m0 <= this * I0: invalid spectrum
+constexpr int kMaxRadius = 64;                        // largest kernel radius served
+
+// Geometry after host-side derivation of kernel radii and sizes.
+struct Geom {
+    int nx, ny, nz;        // data cube
+    int u;                 // upsampling factor
+    int R, Rz;             // kernel radii on the (fine) model grid
+    int nxf, nyf, nzf;     // fine data grid = u * (nx, ny, nz)
+    int ex, ey, ez;        // fine extended grid
+    float dv, vc;
+    float sig_xy;          // PSF sigma, fine pixels
+    float sig_z;           // LSF sigma, fine channels (mode 0)
+    float sig_lsf_kms;     // LSF sigma, km/s (mode 1 folds it into the line)
+    int lsf_mode;
+};
+
+// Per-model constants, derived once per block.
+struct ModelConst {
+    float x0, y0, sin_pa, cos_pa, sin_i, inv_cos_i;
+    float vsys, vrot_k;    // vrot_k = (2/pi) Vmax
+    float inv_rt, i0, inv_h;
+    float sigma;           // line sigma, km/s
+    float amp;             // dv / (sigma sqrt(2 pi))
+    float alpha;           // sqrt(log2 e) / (sigma sqrt 2): exp(-d^2/2s^2) = 2^-(alpha d)^2
+    int valid;             // 0 if a parameter is outside its domain
+};
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ inline ModelConst model_const(const double *p, const Geom &g)
+{
+    ModelConst c;
+    bool ok = (p[GBK_INCL] >= 0.0) && (p[GBK_INCL] < 90.0) && (p[GBK_RT] > 0.0) &&
+              (p[GBK_SIG0] > 0.0) && (p[GBK_I0] > 0.0) && (p[GBK_H] > 0.0);
+    for (int k = 0; k < GBK_NPAR; ++k) ok = ok && isfinite(p[k]);
+    c.valid = ok ? 1 : 0;
+    float s0 = (float)p[GBK_SIG0];
+    float sig = s0;
+    if (g.lsf_mode == 1) sig = sqrtf(s0 * s0 + g.sig_lsf_kms * g.sig_lsf_kms);
+    float sp, cp, si, ci;
+    // sin/cos of (degrees / 180) * pi with exact argument reduction.
+    sincospif((float)(p[GBK_PA] / 180.0), &sp, &cp);
+    sincospif((float)(p[GBK_INCL] / 180.0), &si, &ci);
+    c.x0 = (float)p[GBK_X0];
+    c.y0 = (float)p[GBK_Y0];
+    c.sin_pa = sp;
+    c.cos_pa = cp;
+    c.sin_i = si;
+    c.inv_cos_i = 1.0f / ci;
+    c.vsys = (float)p[GBK_VSYS];
+    c.vrot_k = (float)(0.63661977236758134 * p[GBK_VMAX]);
+    c.inv_rt = (float)(1.0 / p[GBK_RT]);
+    c.i0 = (float)p[GBK_I0];
+    c.inv_h = (float)(1.0 / p[GBK_H]);
+    c.sigma = sig;
+    c.amp = g.dv / (sig * 2.5066282746310002f);
+    c.alpha = 0.84932180028801904f / sig;  // sqrt(log2(e) / 2) / sigma
+    return c;
+}
+
+// Line-of-sight velocity (Eq. 8) and surface brightness (Eq. 5) at sky
+// position (x, y) in data pixels.  Vrot(r) cos(theta) is computed as
+// [Vrot(r)/r] x_e (Eqs. 4, 6), whose r -> 0 limit is (2/pi) Vmax / r_t.
+__device__ __forceinline__ void los(const ModelConst &c, float x, float y, float &v, float &bright)
+{
+    float dx = x - c.x0, dy = y - c.y0;
+    float xe = -dx * c.sin_pa + dy * c.cos_pa;  // Eq. 1
+    float ye = -dx * c.cos_pa - dy * c.sin_pa;  // Eq. 2
+    float yd = ye * c.inv_cos_i;
+    float r = sqrtf(xe * xe + yd * yd);         // Eq. 3
+    float f = (r > 0.f) ? c.vrot_k * atanf(r * c.inv_rt) / r : c.vrot_k * c.inv_rt;
+    v = c.vsys + f * xe * c.sin_i;              // Eq. 8
+    bright = c.i0 * expf(-r * c.inv_h);         // Eq. 5
+}
+
+// Unnormalised Gaussian tap exp(-j^2 / (2 sigma^2)) (sigma > 0).
+__device__ __forceinline__ float gauss_tap(int j, float sigma)
+{
+    float t = (float)j / sigma;
+    return expf(-0.5f * t * t);
+}
+
+// Block-wide: taps w[0..2R] = normalised Gaussian of width sigma.  `scratch`
+// holds at least 2R+1 floats.  Must be called by every thread of the block;
+// ends with __syncthreads().
+__device__ inline void block_taps(float sigma, int R, float *w)
+{
+    for (int j = threadIdx.x; j <= 2 * R; j += blockDim.x)
+        w[j] = (R == 0) ? 1.f : gauss_tap(j - R, sigma);
+    __syncthreads();
+    __shared__ float s_norm;
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int j = 0; j <= 2 * R; ++j) s += w[j];
+        s_norm = 1.f / s;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j <= 2 * R; j += blockDim.x) w[j] *= s_norm;
+    __syncthreads();
+}
+
+}  // namespace gbk

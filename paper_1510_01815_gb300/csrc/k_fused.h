@@ -1,0 +1,27 @@
+// k_fused.h -- launcher of the fused forward-model kernel (host side).
+#pragma once
+
+#include "gbk_internal.cuh"
+
+namespace gbk {
+
+constexpr int kFusedThreads = 256;
+constexpr int kFusedMaxSmem = 227 * 1024;
+constexpr int kFusedMaxCluster = 16;
+
+struct FusedArgs {
+    Geom g;                 // u must be 1
+    int n_models;
+    const double *params;   // [n_models][GBK_NPAR]
+    gbk_obs obs;            // device pointers; used when chi2 or resid is set
+    float *maps;            // [n_models][3][ny][nx] or null
+    double *chi2;           // [n_models] or null
+    float *resid;           // [n_models][2][ny][nx] or null
+    int cs;                 // CTAs (cluster size) per model
+    int band;               // extended rows per CTA = ceil(ey / cs)
+};
+
+size_t fused_smem_bytes_host(const Geom &g, int band);
+cudaError_t launch_fused(const FusedArgs &args, cudaStream_t stream);
+
+}  // namespace gbk

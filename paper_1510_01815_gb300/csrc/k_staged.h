@@ -1,0 +1,34 @@
+// k_staged.h -- launchers of the staged (cube-materialising) kernels.
+#pragma once
+
+#include "gbk_internal.cuh"
+
+namespace gbk {
+
+constexpr int kConvTX = 32;
+constexpr int kConvTY = 8;
+
+struct StagedArgs {
+    Geom g;
+    int n_models;
+    const double *params;    // [n][GBK_NPAR]
+    float *ext;              // fine extended model cube, [n][ez][ey][e_pitch]
+    int e_pitch;             // row pitch of ext in floats (multiple of 4, >= ex)
+    size_t e_model_stride;   // floats per model in ext
+    float *fine;             // convolved fine cube [n][nzf][nyf][nxf]
+    size_t f_model_stride;
+    float *data;             // data-resolution cube [n][nz][ny][nx] (== fine when u == 1)
+    size_t d_model_stride;
+    float *maps;             // [n][3][ny][nx] or null
+    double *chi2;            // [n] or null
+    float *resid;            // [n][2][ny][nx] or null
+    double *partials;        // [n][ceil(nx*ny/256)] when chi2 is set
+    gbk_obs obs;
+};
+
+size_t conv_smem_bytes(const Geom &g);
+cudaError_t launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream);
+cudaError_t launch_chi2_maps(int nx, int ny, int n_models, const float *maps, const gbk_obs &obs,
+                             double *chi2, float *resid, cudaStream_t stream);
+
+}  // namespace gbk

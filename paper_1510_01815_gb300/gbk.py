@@ -1,0 +1,208 @@
+"""Python binding of libgbk.so (the C ABI in include/gbk.h).
+
+Argument marshalling only: every step of the forward model runs in the
+library's CUDA kernels.  Device buffers are torch tensors; the stream is
+torch's current stream unless one is given.  If the shared library has not
+been built this module raises -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbk.so")
+
+NPAR = 10
+GBK_OK, GBK_EINVAL, GBK_ECUDA, GBK_EWORKSPACE, GBK_EUNSUPPORTED = 0, 1, 2, 3, 4
+PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
+
+
+class GbkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("gbk status %d: %s" % (status, msg))
+        self.status = status
+
+
+class CGeom(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("upsample", ctypes.c_int32), ("dv", ctypes.c_double), ("vc", ctypes.c_double),
+                ("psf_fwhm", ctypes.c_double), ("lsf_fwhm", ctypes.c_double),
+                ("lsf_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("halo_sigmas", ctypes.c_double)]
+
+
+class CObs(ctypes.Structure):
+    _fields_ = [("v_obs", ctypes.c_void_p), ("s_obs", ctypes.c_void_p), ("w_v", ctypes.c_void_p),
+                ("w_s", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libgbk.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgbk.so is not built (run paper_1510_01815_gb300/build.py or "
+                               "__graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_size_t
+        gp, op = ctypes.POINTER(CGeom), ctypes.POINTER(CObs)
+        sig = {
+            "gbk_workspace_bytes": (sz, [gp, i32, u32]),
+            "gbk_eval_cubes": (i32, [gp, i32, vp, vp, vp, vp, sz, vp]),
+            "gbk_chi2": (i32, [gp, i32, vp, op, vp, vp, u32, vp, sz, vp]),
+            "gbk_chi2_from_maps": (i32, [i32, i32, i32, vp, op, vp, vp, vp]),
+            "gbk_measure_alu_peak": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]),
+            "gbk_last_error": (ctypes.c_char_p, []),
+            "gbk_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps",
+            "gbk_measure_alu_peak", "gbk_last_error", "gbk_version"]
+
+
+def cgeom(g):
+    """A gbk_geom from any object with the Geometry attributes."""
+    return CGeom(int(g.nx), int(g.ny), int(g.nz), int(getattr(g, "upsample", 1)), float(g.dv),
+                 float(getattr(g, "vc", 0.0)), float(getattr(g, "psf_fwhm", 0.0)),
+                 float(getattr(g, "lsf_fwhm", 0.0)), int(getattr(g, "lsf_mode", 0)), 0,
+                 float(getattr(g, "halo_sigmas", 4.0)))
+
+
+def _check(status):
+    if status != GBK_OK:
+        raise GbkError(status, lib().gbk_last_error().decode())
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Obs:
+    """Observed maps of one galaxy as device tensors ([ny][nx]; mask uint8)."""
+
+    def __init__(self, v_obs, s_obs, w_v, w_s, mask):
+        self.v_obs, self.s_obs, self.w_v, self.w_s, self.mask = v_obs, s_obs, w_v, w_s, mask
+        self._c = CObs(_ptr(v_obs, torch.float32, "v_obs"), _ptr(s_obs, torch.float32, "s_obs"),
+                       _ptr(w_v, torch.float32, "w_v"), _ptr(w_s, torch.float32, "w_s"),
+                       _ptr(mask, torch.uint8, "mask"))
+
+    @classmethod
+    def from_numpy(cls, v, s, w_v, w_s, mask, device="cuda"):
+        f = lambda a: torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        return cls(f(v), f(s), f(w_v), f(w_s),
+                   torch.as_tensor(mask, dtype=torch.uint8).contiguous().to(device))
+
+    def c(self):
+        return self._c
+
+
+def gbk_workspace_bytes(geom, n_models, flags=PATH_AUTO):
+    g = cgeom(geom)
+    n = lib().gbk_workspace_bytes(ctypes.byref(g), int(n_models), int(flags))
+    err = lib().gbk_last_error().decode()
+    if n == 0 and err:
+        raise GbkError(GBK_EINVAL, err)
+    return int(n)
+
+
+def gbk_eval_cubes(geom, params, cubes=None, maps=None, workspace=None, stream=None):
+    g = cgeom(geom)
+    n = params.shape[0] if params.dim() == 2 else params.numel() // NPAR
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_eval_cubes(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"),
+                                _ptr(cubes, torch.float32, "cubes"), _ptr(maps, torch.float32, "maps"),
+                                _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def gbk_chi2(geom, params, obs, chi2, resid=None, flags=PATH_AUTO, workspace=None, stream=None):
+    g = cgeom(geom)
+    n = params.shape[0] if params.dim() == 2 else params.numel() // NPAR
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_chi2(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"),
+                          ctypes.byref(obs.c()), _ptr(chi2, torch.float64, "chi2"),
+                          _ptr(resid, torch.float32, "resid"), int(flags),
+                          _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def gbk_chi2_from_maps(maps, obs, chi2, resid=None, stream=None):
+    n, three, ny, nx = maps.shape
+    _check(lib().gbk_chi2_from_maps(int(nx), int(ny), int(n), _ptr(maps, torch.float32, "maps"),
+                                    ctypes.byref(obs.c()), _ptr(chi2, torch.float64, "chi2"),
+                                    _ptr(resid, torch.float32, "resid"), _stream(stream)))
+
+
+def gbk_measure_alu_peak(stream=None):
+    """(FP32 FMA, MUFU ex2) lane-operations per second on the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().gbk_measure_alu_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return a.value, b.value
+
+
+def gbk_version():
+    return lib().gbk_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# Convenience wrappers that allocate outputs with torch (device memory is the
+# caller's; these only size and allocate the tensors the C calls fill).
+
+def workspace_for(geom, n_models, flags=PATH_AUTO, device="cuda"):
+    nb = gbk_workspace_bytes(geom, n_models, flags)
+    return torch.empty(max(nb, 1), dtype=torch.uint8, device=device) if nb else None
+
+
+def eval_maps(geom, params, device="cuda", stream=None):
+    params = params.to(device=device, dtype=torch.float64).contiguous()
+    n = params.shape[0]
+    maps = torch.empty((n, 3, geom.ny, geom.nx), dtype=torch.float32, device=device)
+    ws = workspace_for(geom, n, PATH_AUTO, device) if getattr(geom, "upsample", 1) > 1 else None
+    gbk_eval_cubes(geom, params, maps=maps, workspace=ws, stream=stream)
+    return maps
+
+
+def eval_cubes(geom, params, device="cuda", stream=None):
+    params = params.to(device=device, dtype=torch.float64).contiguous()
+    n = params.shape[0]
+    cubes = torch.empty((n, geom.nz, geom.ny, geom.nx), dtype=torch.float32, device=device)
+    maps = torch.empty((n, 3, geom.ny, geom.nx), dtype=torch.float32, device=device)
+    ws = workspace_for(geom, n, PATH_STAGED, device)
+    gbk_eval_cubes(geom, params, cubes=cubes, maps=maps, workspace=ws, stream=stream)
+    return cubes, maps
+
+
+def chi2(geom, params, obs, flags=PATH_AUTO, want_resid=False, device="cuda", stream=None):
+    params = params.to(device=device, dtype=torch.float64).contiguous()
+    n = params.shape[0]
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    resid = torch.empty((n, 2, geom.ny, geom.nx), dtype=torch.float32, device=device) if want_resid else None
+    ws = workspace_for(geom, n, flags, device)
+    gbk_chi2(geom, params, obs, out, resid, flags, ws, stream)
+    return (out, resid) if want_resid else out

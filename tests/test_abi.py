@@ -1,0 +1,106 @@
+"""The C ABI: the library builds, loads and exports every symbol include/gbk.h
+declares; host-side validation rejects bad arguments before any launch.
+These tests make no compute calls and need no GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1510_01815_gb300 import build as gbuild
+from paper_1510_01815_gb300.synth import SINGLE_GEOM, FP_GEOM, GRID_GEOM
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbk.h")
+
+
+@pytest.fixture(scope="module")
+def gbk():
+    gbuild.build()
+    from paper_1510_01815_gb300 import gbk as G
+    G.lib()
+    return G
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"GBK_API\s+[\w\s\*]*?\b(gbk_\w+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for s in ("gbk_eval_cubes", "gbk_chi2", "gbk_workspace_bytes", "gbk_last_error"):
+        assert s in syms
+
+
+def test_every_declared_symbol_is_exported(gbk):
+    out = subprocess.run(["nm", "-D", "--defined-only", gbk.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(gbk_\w+)", out))
+    for s in declared_symbols():
+        assert s in exported, s
+        assert hasattr(gbk.lib(), s)
+    assert set(gbk.exported_symbols()) <= exported
+
+
+def test_no_stray_exports(gbk):
+    out = subprocess.run(["nm", "-D", "--defined-only", gbk.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(\w+)", out))
+    extra = {s for s in exported if s.startswith("gbk_")} - set(declared_symbols())
+    assert not extra, extra
+
+
+def test_version(gbk):
+    assert "sm_103a" in gbk.gbk_version()
+
+
+def test_workspace_sizes(gbk):
+    # fused path needs none; the staged path holds the extended cube, the data
+    # cube and the chi2 partials
+    assert gbk.gbk_workspace_bytes(SINGLE_GEOM, 10, gbk.PATH_FUSED) == 0
+    assert gbk.gbk_workspace_bytes(SINGLE_GEOM, 10, gbk.PATH_AUTO) == 0
+    n = 7
+    ws = gbk.gbk_workspace_bytes(SINGLE_GEOM, n, gbk.PATH_STAGED)
+    # 32x32x64, R = 5 (PSF FWHM 2.5), Rz = 3 (LSF 30 km/s at 20 km/s)
+    ext = 70 * 42 * 44 * 4 * n      # row pitch 42 -> 44
+    data = 64 * 32 * 32 * 4 * n
+    part = 4 * 8 * n
+    al = lambda b: (b + 255) // 256 * 256
+    assert ws == al(ext) + al(data) + al(part)
+    assert gbk.gbk_workspace_bytes(GRID_GEOM.with_(upsample=2), 1, gbk.PATH_AUTO) > 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=0), dict(nz=-1), dict(dv=0.0), dict(dv=float("nan")), dict(psf_fwhm=-1.0),
+    dict(lsf_mode=2), dict(upsample=0), dict(halo_sigmas=0.0), dict(psf_fwhm=1e4)])
+def test_invalid_geometry_rejected(gbk, bad):
+    g = SINGLE_GEOM.with_(**bad)
+    with pytest.raises(gbk.GbkError) as ei:
+        gbk.gbk_workspace_bytes(g, 1, gbk.PATH_STAGED)
+    assert ei.value.status in (gbk.GBK_EINVAL, gbk.GBK_EUNSUPPORTED)
+    cg = gbk.cgeom(g)
+    st = gbk.lib().gbk_eval_cubes(ctypes.byref(cg), 1, None, None, None, None, 0, None)
+    assert st in (gbk.GBK_EINVAL, gbk.GBK_EUNSUPPORTED)
+    assert gbk.lib().gbk_last_error().decode()
+
+
+def test_zero_models_is_a_noop(gbk):
+    cg = gbk.cgeom(SINGLE_GEOM)
+    assert gbk.lib().gbk_eval_cubes(ctypes.byref(cg), 0, None, None, None, None, 0, None) == 0
+    assert gbk.lib().gbk_chi2(ctypes.byref(cg), 0, None, None, None, None, 0, None, 0, None) == 0
+
+
+def test_null_and_host_pointers_rejected(gbk):
+    cg = gbk.cgeom(SINGLE_GEOM)
+    assert gbk.lib().gbk_eval_cubes(ctypes.byref(cg), 1, None, None, None, None, 0, None) == gbk.GBK_EINVAL
+    host = (ctypes.c_double * 10)()
+    st = gbk.lib().gbk_eval_cubes(ctypes.byref(cg), 1, ctypes.cast(host, ctypes.c_void_p), None, None,
+                                  None, 0, None)
+    assert st == gbk.GBK_EINVAL
+    assert "params" in gbk.lib().gbk_last_error().decode()
+
+
+def test_bad_flags_rejected(gbk):
+    cg = gbk.cgeom(FP_GEOM)
+    st = gbk.lib().gbk_chi2(ctypes.byref(cg), 1, None, None, None, None, 99, None, 0, None)
+    assert st == gbk.GBK_EINVAL

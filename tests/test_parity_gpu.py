@@ -1,0 +1,193 @@
+"""GPU parity: the CUDA forward model against the FP64 oracle, element by
+element, through the C ABI.  Tolerances are stated in tests/cases.py."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from cases import ogeom, make_obs, model_params, check_maps, chi2_bound
+from paper_1510_01815_gb300 import synth
+from paper_1510_01815_gb300.synth import Geometry, params as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1510_01815_gb300 import build, gbk
+    build.build()
+    assert torch.cuda.is_available(), "the -m gpu tests need a CUDA device"
+    return gbk
+
+
+CASES = {
+    "single": (synth.SINGLE_GEOM, synth.SINGLE_TRUTH),
+    "single_mode1": (synth.SINGLE_GEOM.with_(lsf_mode=1), synth.SINGLE_TRUTH),
+    "no_conv": (synth.SINGLE_GEOM.with_(psf_fwhm=0.0, lsf_fwhm=0.0), synth.SINGLE_TRUTH),
+    "tiny_1x1x1": (Geometry(1, 1, 1, 20.0, 0.0, 2.5, 30.0), P(0.3, 0.2, 40, 50, 0, 150, 2, 40, 1, 3)),
+    "odd_3x5x7": (Geometry(3, 5, 7, 40.0, 0.0, 1.5, 50.0), P(1.2, 2.3, 200, 35, 10, 120, 1.5, 30, 2, 2)),
+    "prime_13x11x17": (Geometry(13, 11, 17, 25.0, 0.0, 3.3, 45.0), P(6.4, 4.9, 75, 62, -5, 180, 2.5, 25, 1, 3)),
+    "narrow_band": (Geometry(9, 7, 4, 10.0, 0.0, 2.0, 60.0), P(4.1, 3.2, 10, 40, 0, 30, 2, 20, 1, 3)),
+    "wide_kernels": (Geometry(24, 20, 40, 10.0, 5.0, 9.0, 150.0), P(11.6, 9.3, 300, 45, 5, 90, 4, 30, 1, 6)),
+    "grid64": (synth.GRID_GEOM, P(33.1, 30.7, 222, 48, 0, 240, 5.5, 55, 1, 12)),
+    "nonsquare": (Geometry(40, 24, 32, 15.0, 0.0, 2.0, 35.0), P(19.7, 12.2, 145, 58, 0, 210, 3, 35, 1, 5)),
+    "edge_on": (synth.SINGLE_GEOM, P(15.5, 15.5, 120, 88.5, 0, 200, 3, 40, 1, 1.0)),
+    "vc_offset": (synth.SINGLE_GEOM.with_(vc=100.0), P(15.2, 16.1, 30, 50, 100, 200, 3, 40, 1, 4)),
+}
+
+
+def _params(case, n=4, seed=7):
+    g, p = CASES[case]
+    ps = model_params(g, p, n, seed)
+    ps[:, synth.INCL] = np.minimum(ps[:, synth.INCL], 89.0)
+    return g, p, ps
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_maps_fused_vs_oracle(G, case):
+    g, p, ps = _params(case)
+    ref = oracle.evaluate_batch(ogeom(g), ps)
+    maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    check_maps(maps, ref, ps, case)
+
+
+@pytest.mark.parametrize("case", ["single", "single_mode1", "tiny_1x1x1", "odd_3x5x7", "narrow_band",
+                                  "wide_kernels", "nonsquare", "edge_on"])
+def test_cube_and_maps_staged_vs_oracle(G, case):
+    g, p, ps = _params(case, n=3)
+    cubes, maps = G.eval_cubes(g, torch.from_numpy(ps))
+    cubes, maps = cubes.cpu().numpy(), maps.cpu().numpy()
+    for i in range(ps.shape[0]):
+        cref, mref = oracle.evaluate(ogeom(g), ps[i], want_cube=True)
+        scale = np.abs(cref).max()
+        err = np.abs(cubes[i] - cref).max() / scale
+        assert err <= 1e-4, "%s model %d cube rel err %.3g" % (case, i, err)
+        check_maps(maps[i:i + 1], mref[None], ps[i:i + 1], case)
+
+
+@pytest.mark.parametrize("u,case", [(2, "single"), (2, "odd_3x5x7"), (3, "tiny_1x1x1"), (2, "nonsquare")])
+def test_upsampled_staged_vs_oracle(G, u, case):
+    g, p, ps = _params(case, n=2)
+    g = g.with_(upsample=u)
+    ref = oracle.evaluate_batch(ogeom(g), ps)
+    maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    check_maps(maps, ref, ps, "%s u=%d" % (case, u))
+    cubes, maps2 = G.eval_cubes(g, torch.from_numpy(ps))
+    cref, _ = oracle.evaluate(ogeom(g), ps[0], want_cube=True)
+    assert np.abs(cubes[0].cpu().numpy() - cref).max() <= 1e-4 * np.abs(cref).max()
+
+
+@pytest.mark.parametrize("case", ["single", "single_mode1", "grid64", "nonsquare", "edge_on", "prime_13x11x17"])
+@pytest.mark.parametrize("path", ["fused", "staged"])
+def test_chi2_vs_oracle(G, case, path):
+    g, p, ps = _params(case, n=5, seed=11)
+    obs = make_obs(g, p, seed=3)
+    flags = G.PATH_FUSED if path == "fused" else G.PATH_STAGED
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    c, resid = G.chi2(g, torch.from_numpy(ps), dobs, flags=flags, want_resid=True)
+    c, resid = c.cpu().numpy(), resid.cpu().numpy()
+    ref_c, ref_r = oracle.chi2_batch(ogeom(g), ps, obs, want_resid=True)
+    gmaps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    rmaps = oracle.evaluate_batch(ogeom(g), ps)
+    for i in range(ps.shape[0]):
+        bound = chi2_bound(rmaps[i], gmaps[i], obs, ref_c[i])
+        assert abs(c[i] - ref_c[i]) <= bound, (case, path, i, c[i], ref_c[i], bound)
+        # residual maps: same bound per spaxel from the map deviation
+        dv = np.abs(obs.w_v * (gmaps[i][1] - rmaps[i][1]))
+        ds = np.abs(obs.w_s * (gmaps[i][2] - rmaps[i][2]))
+        use = (obs.mask != 0) & (rmaps[i][0] > 0)
+        assert np.all(np.abs(resid[i][0] - ref_r[i][0])[use] <= dv[use] + 1e-5 * np.abs(ref_r[i][0][use]) + 1e-6)
+        assert np.all(np.abs(resid[i][1] - ref_r[i][1])[use] <= ds[use] + 1e-5 * np.abs(ref_r[i][1][use]) + 1e-6)
+        assert np.all(resid[i][:, obs.mask == 0] == 0)
+
+
+def test_chi2_reduction_on_identical_maps(G):
+    """The reduction alone, on the same FP32 maps: 1e-5 relative."""
+    g = synth.SINGLE_GEOM
+    ps = model_params(g, synth.SINGLE_TRUTH, 6, seed=5)
+    maps = oracle.evaluate_batch(ogeom(g), ps).astype(np.float32)
+    obs = make_obs(g, synth.SINGLE_TRUTH, seed=4)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    resid = torch.empty((6, 2, g.ny, g.nx), dtype=torch.float32, device="cuda")
+    G.gbk_chi2_from_maps(torch.from_numpy(maps).cuda(), dobs, out, resid)
+    torch.cuda.synchronize()
+    for i in range(6):
+        ref, rr = oracle.chi2_maps(maps[i].astype(np.float64), obs, want_resid=True)
+        assert abs(out[i].item() - ref) <= 1e-5 * ref + 1e-12, (i, out[i].item(), ref)
+        np.testing.assert_allclose(resid[i].cpu().numpy(), rr, rtol=1e-5, atol=1e-6)
+
+
+def test_noiseless_truth_gives_zero_chi2(G):
+    """Observed maps made by the same GPU path at the same parameters: chi2 = 0
+    exactly (bitwise-identical maps)."""
+    g, p = synth.SINGLE_GEOM, synth.SINGLE_TRUTH
+    maps = G.eval_maps(g, torch.from_numpy(p[None]))
+    wv, ws = synth.weights((g.ny, g.nx), 5.0)
+    dobs = G.Obs(maps[0, 1].contiguous(), maps[0, 2].contiguous(), torch.from_numpy(wv).cuda(),
+                 torch.from_numpy(ws).cuda(), torch.ones((g.ny, g.nx), dtype=torch.uint8, device="cuda"))
+    c = G.chi2(g, torch.from_numpy(p[None]), dobs, flags=G.PATH_FUSED)
+    assert c.item() == 0.0
+
+
+def test_bitwise_deterministic(G):
+    g, p, ps = _params("grid64", n=8)
+    obs = make_obs(g, p, seed=9)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    a = G.chi2(g, torch.from_numpy(ps), dobs).cpu().numpy()
+    b = G.chi2(g, torch.from_numpy(ps), dobs).cpu().numpy()
+    assert np.array_equal(a, b)
+    m1 = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    m2 = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    assert np.array_equal(m1, m2)
+
+
+def test_invalid_parameters_give_nan(G):
+    g = synth.SINGLE_GEOM
+    ps = np.array([synth.SINGLE_TRUTH] * 4)
+    ps[1, synth.INCL] = 90.0
+    ps[2, synth.SIG0] = -1.0
+    ps[3, synth.RT] = np.nan
+    obs = make_obs(g, synth.SINGLE_TRUTH, seed=1)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    for flags in (G.PATH_FUSED, G.PATH_STAGED):
+        c = G.chi2(g, torch.from_numpy(ps), dobs, flags=flags).cpu().numpy()
+        assert np.isfinite(c[0]) and np.all(np.isnan(c[1:])), (flags, c)
+    maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    assert np.isfinite(maps[0]).all() and np.isnan(maps[1:]).all()
+
+
+def test_fused_and_staged_agree(G):
+    g, p, ps = _params("nonsquare", n=6)
+    obs = make_obs(g, p, seed=2)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    a = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED).cpu().numpy()
+    b = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_STAGED).cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=2e-4)
+
+
+@pytest.mark.slow
+def test_fabry_perot_full_size(G):
+    """192 x 192 x 48 at the launch configuration the benchmark times (a
+    cluster of CTAs per model), full maps of two models against the oracle and
+    chi2 of a 400-model batch against sampled oracle models."""
+    g = synth.FP_GEOM
+    rng = np.random.default_rng(21)
+    ps = synth.draw_fp_params(rng, 400)
+    ref = oracle.evaluate_batch(ogeom(g), ps[:2])
+    maps = G.eval_maps(g, torch.from_numpy(ps[:2])).cpu().numpy()
+    check_maps(maps, ref, ps[:2], "fp")
+    p_true = ps[0]
+    m_true = ref[0]
+    shape = (g.ny, g.nx)
+    obs = oracle.Obs((m_true[1] + rng.normal(0, 5, shape)).astype(np.float32),
+                     (m_true[2] + rng.normal(0, 7.07, shape)).astype(np.float32),
+                     *synth.weights(shape, 5.0),
+                     (synth.sn_mask(m_true[0]) * synth.dead_fibre_mask(rng, shape)).astype(np.uint8))
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    c = G.chi2(g, torch.from_numpy(ps), dobs).cpu().numpy()
+    allmaps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    for i in (0, 1, 137, 399):
+        rm = ref[i] if i < 2 else oracle.evaluate(ogeom(g), ps[i])
+        rc = oracle.chi2_maps(rm, obs)
+        assert abs(c[i] - rc) <= chi2_bound(rm, allmaps[i], obs, rc), (i, c[i], rc)
