@@ -214,8 +214,8 @@ static gbk_status run_staged(const Geom &g, int32_t n, const double *params, flo
     a.partials = chi2 ? (double *)(base + L.off_part) : nullptr;
     if (obs) a.obs = *obs;
     bool want_moments = (maps || chi2 || resid);
-    cudaError_t e = launch_staged(a, want_moments, st);
-    if (e != cudaSuccess) return cuda_fail(e, "staged launch");
+    gbk_status s = launch_staged(a, want_moments, st);
+    if (s) return s;
     return ok();
 }
 
@@ -234,8 +234,8 @@ static gbk_status run_fused(const Geom &g, int32_t n, const double *params, floa
     a.chi2 = chi2;
     a.resid = resid;
     if (n == 0) return ok();
-    cudaError_t e = launch_fused(a, st);
-    if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+    gbk_status s = launch_fused(a, st);
+    if (s) return s;
     return ok();
 }
 

@@ -32,6 +32,7 @@
 // CTA, then cluster rank 0 over the ranks.
 #include <cooperative_groups.h>
 
+#include "gbk_api_internal.h"
 #include "gbk_internal.cuh"
 #include "k_fused.h"
 
@@ -122,31 +123,52 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
     const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;  // v of e = 0
     const float al = c.alpha, adv = c.alpha * g.dv, inv_al = 1.f / c.alpha;
     const int nsp = nrows * g.ex;
+    const float v_lo = g.vc - 0.5f * (float)(g.nz - 1) * g.dv;  // first and last data channel
+    const float v_hi = g.vc + 0.5f * (float)(g.nz - 1) * g.dv;
     for (int idx = threadIdx.x; idx < nsp; idx += blockDim.x) {
         int r = idx / g.ex, xe = idx - r * g.ex;
         float x = (float)(xe - g.R), y = (float)(row0 + r - g.R);
         float vl, br;
         los(c, x, y, vl, br);
-        float base = vz0 - vl;      // d at e = 0
+        // Sums are taken about a = v_los clamped into the band: for a line
+        // inside the band a = v_los; for a line outside it the band edge keeps
+        // the FP32 second moment of the truncated spectrum free of
+        // cancellation.  (The moments do not depend on this choice.)
+        float a_c = fminf(fmaxf(vl, v_lo), v_hi);
+        float base = vz0 - vl;      // d = v_e - v_los at e = 0 (Gaussian argument)
+        float sh = vl - a_c;        // d' = d + sh = v_e - a (moment weight)
         float ub = al * base;
-        float s0a = 0.f, s1a = 0.f, s2a = 0.f, s0b = 0.f, s1b = 0.f, s2b = 0.f;
-        int e = elo;
-        for (; e + 1 < ehi; e += 2) {
-            float u0 = fmaf((float)e, adv, ub);
-            float u1 = u0 + adv;
-            float g0 = ex2_approx(-u0 * u0);
-            float g1 = ex2_approx(-u1 * u1);
-            float t0 = g0 * u0, t1 = g1 * u1;
-            s0a += g0; s1a += t0; s2a = fmaf(t0, u0, s2a);
-            s0b += g1; s1b += t1; s2b = fmaf(t1, u1, s2b);
+        float s0, s1, s2;
+        if (sh == 0.f) {
+            float s0a = 0.f, s1a = 0.f, s2a = 0.f, s0b = 0.f, s1b = 0.f, s2b = 0.f;
+            int e = elo;
+            for (; e + 1 < ehi; e += 2) {
+                float u0 = fmaf((float)e, adv, ub);
+                float u1 = u0 + adv;
+                float g0 = ex2_approx(-u0 * u0);
+                float g1 = ex2_approx(-u1 * u1);
+                float t0 = g0 * u0, t1 = g1 * u1;
+                s0a += g0; s1a += t0; s2a = fmaf(t0, u0, s2a);
+                s0b += g1; s1b += t1; s2b = fmaf(t1, u1, s2b);
+            }
+            if (e < ehi) {
+                float u0 = fmaf((float)e, adv, ub);
+                float g0 = ex2_approx(-u0 * u0);
+                float t0 = g0 * u0;
+                s0a += g0; s1a += t0; s2a = fmaf(t0, u0, s2a);
+            }
+            s0 = s0a + s0b; s1 = s1a + s1b; s2 = s2a + s2b;
+        } else {
+            float ubs = al * (base + sh);
+            s0 = s1 = s2 = 0.f;
+            for (int e = elo; e < ehi; ++e) {
+                float u0 = fmaf((float)e, adv, ub);
+                float w0 = fmaf((float)e, adv, ubs);
+                float g0 = ex2_approx(-u0 * u0);
+                float t0 = g0 * w0;
+                s0 += g0; s1 += t0; s2 = fmaf(t0, w0, s2);
+            }
         }
-        if (e < ehi) {
-            float u0 = fmaf((float)e, adv, ub);
-            float g0 = ex2_approx(-u0 * u0);
-            float t0 = g0 * u0;
-            s0a += g0; s1a += t0; s2a = fmaf(t0, u0, s2a);
-        }
-        float s0 = s0a + s0b, s1 = s1a + s1b, s2 = s2a + s2b;
         float E0 = 0.f, E1 = 0.f, E2 = 0.f;
         for (int pass = 0; pass < 2; ++pass) {
             int eb = pass ? ehi : 0, ee = pass ? g.ez : elo;
@@ -154,12 +176,13 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
                 float d = fmaf((float)k, g.dv, base);
                 float u = al * d;
                 float gg = ex2_approx(-u * u);
+                float dp = d + sh;
                 float4 T = ztab[k];
                 float t0 = gg * T.x;
                 float h = gg * T.y;
                 E0 += t0;
-                E1 = fmaf(t0, d, E1 + h);
-                E2 = fmaf(t0 * d, d, fmaf(h, 2.f * d, fmaf(gg, T.z, E2)));
+                E1 = fmaf(t0, dp, E1 + h);
+                E2 = fmaf(t0 * dp, dp, fmaf(h, 2.f * dp, fmaf(gg, T.z, E2)));
             }
         }
         float A = c.amp * br;
@@ -167,7 +190,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
         q.x = A * (s0 + E0);
         q.y = A * fmaf(s1, inv_al, E1);
         q.z = A * (fmaf(s2, inv_al * inv_al, var_z * s0) + E2);
-        q.w = vl;
+        q.w = a_c;
         Q[idx] = q;
     }
     __syncthreads();
@@ -267,17 +290,23 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
     cluster.sync();  // keep every CTA's shared memory alive until rank 0 is done
 }
 
-cudaError_t launch_fused(const FusedArgs &args, cudaStream_t stream)
+gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
 {
     size_t smem = fused_smem_bytes(args.g, args.band);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused_eval_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedMaxSmem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(fused_eval_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        configured = true;
+    // Shared-memory opt-in is set to what this launch needs (static shared
+    // memory of the kernel counts against the same per-block limit).
+    static size_t configured = 0;
+    static bool cluster_configured = false;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(fused_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "fused kernel: setting dynamic shared memory");
+        configured = smem;
+    }
+    if (!cluster_configured) {
+        cudaError_t e = cudaFuncSetAttribute(fused_eval_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return cuda_fail(e, "fused kernel: allowing 16-CTA clusters");
+        cluster_configured = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(args.n_models * args.cs), 1, 1);
@@ -291,7 +320,9 @@ cudaError_t launch_fused(const FusedArgs &args, cudaStream_t stream)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fused_eval_kernel, args);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fused_eval_kernel, args);
+    if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+    return GBK_OK;
 }
 
 }  // namespace gbk

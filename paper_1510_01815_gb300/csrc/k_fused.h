@@ -6,7 +6,9 @@
 namespace gbk {
 
 constexpr int kFusedThreads = 256;
-constexpr int kFusedMaxSmem = 227 * 1024;
+// Opt-in shared memory per block is 227 KB; 2 KB are left for the static
+// shared memory of the kernel.
+constexpr int kFusedMaxSmem = 225 * 1024;
 constexpr int kFusedMaxCluster = 16;
 
 struct FusedArgs {
@@ -22,6 +24,6 @@ struct FusedArgs {
 };
 
 size_t fused_smem_bytes_host(const Geom &g, int band);
-cudaError_t launch_fused(const FusedArgs &args, cudaStream_t stream);
+gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream);
 
 }  // namespace gbk

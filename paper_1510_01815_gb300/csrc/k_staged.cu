@@ -12,6 +12,7 @@
 //                       partials (Sec. 2.2.5-2.2.6)
 //   chi2_final_kernel   fixed-order FP64 sum of the partials
 //   chi2_maps_kernel    Eq. 11 from caller-supplied maps, one block per model
+#include "gbk_api_internal.h"
 #include "gbk_internal.cuh"
 #include "k_staged.h"
 
@@ -162,8 +163,8 @@ __global__ void __launch_bounds__(256) downsample_kernel(StagedArgs a)
 
 // ----------------------------------------------------------------------------
 // Moments of the data cube, one thread per spaxel.  Sums are taken about the
-// spaxel's own line-of-sight velocity (exact re-centring; keeps the FP32
-// second moment free of cancellation).
+// spaxel's own line-of-sight velocity clamped into the band, which keeps the
+// FP32 second moment free of cancellation.
 __device__ __forceinline__ void finish_moments(float s0, float s1, float s2, float cen,
                                                const ModelConst &c, float &m0, float &m1, float &m2,
                                                bool &valid)
@@ -208,8 +209,10 @@ __global__ void __launch_bounds__(256) moments_kernel(StagedArgs a)
     double acc = 0.0;
     if (pix < np) {
         int y = pix / g.nx, x = pix - y * g.nx;
-        float cen, br;
-        los(c, (float)x, (float)y, cen, br);
+        float vl, br;
+        los(c, (float)x, (float)y, vl, br);
+        // centre: v_los clamped into the band (see the fused kernel)
+        float cen = fminf(fmaxf(vl, g.vc - 0.5f * (float)(g.nz - 1) * g.dv), g.vc + 0.5f * (float)(g.nz - 1) * g.dv);
         const float *D = a.data + (size_t)model * a.d_model_stride + pix;
         float base = g.vc - 0.5f * (float)(g.nz - 1) * g.dv - cen;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
@@ -286,41 +289,47 @@ size_t conv_smem_bytes(const Geom &g)
     return sizeof(float) * (size_t)((2 * g.R + 1) + W + SY * SX + SY * kConvTX + W * kConvTX * kConvTY);
 }
 
-cudaError_t launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream)
+gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream)
 {
     const Geom &g = a.g;
-    if (a.n_models == 0) return cudaSuccess;
+    if (a.n_models == 0) return GBK_OK;
+    cudaError_t e;
     {
         long per_model = (long)g.ey * (a.e_pitch / 4);
         long bpm = (per_model + 255) / 256;
         model_cube_kernel<<<(unsigned)(bpm * a.n_models), 256, 0, stream>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "model cube kernel launch");
     }
     {
         size_t smem = conv_smem_bytes(g);
         static size_t configured = 0;
         if (smem > 48 * 1024 && smem > configured) {
-            cudaError_t e = cudaFuncSetAttribute(conv3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(conv3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e, "conv kernel: setting dynamic shared memory");
             configured = smem;
         }
         int tiles = ((g.nxf + kConvTX - 1) / kConvTX) * ((g.nyf + kConvTY - 1) / kConvTY);
         conv3d_kernel<<<(unsigned)(tiles * a.n_models), kConvTX * kConvTY, smem, stream>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "conv kernel launch");
     }
     if (g.u > 1) {
         long total = (long)g.nx * g.ny * g.nz * a.n_models;
         long blocks = (total + 255) / 256;
         if (blocks > 152L * 64) blocks = 152L * 64;
         downsample_kernel<<<(unsigned)blocks, 256, 0, stream>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "down-sampling kernel launch");
     }
     if (want_moments) {
         int np = g.nx * g.ny;
         int bpm = (np + 255) / 256;
         moments_kernel<<<(unsigned)(bpm * a.n_models), 256, 0, stream>>>(a);
-        if (a.chi2)
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "moments kernel launch");
+        if (a.chi2) {
             chi2_final_kernel<<<(a.n_models + 127) / 128, 128, 0, stream>>>(a.partials, bpm, a.n_models, a.chi2);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "chi2 final kernel launch");
+        }
     }
-    return cudaGetLastError();
+    return GBK_OK;
 }
 
 cudaError_t launch_chi2_maps(int nx, int ny, int n_models, const float *maps, const gbk_obs &obs,

@@ -27,7 +27,7 @@ struct StagedArgs {
 };
 
 size_t conv_smem_bytes(const Geom &g);
-cudaError_t launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream);
+gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream);
 cudaError_t launch_chi2_maps(int nx, int ny, int n_models, const float *maps, const gbk_obs &obs,
                              double *chi2, float *resid, cudaStream_t stream);
 

@@ -87,7 +87,10 @@ def test_chi2_vs_oracle(G, case, path):
     c, resid = G.chi2(g, torch.from_numpy(ps), dobs, flags=flags, want_resid=True)
     c, resid = c.cpu().numpy(), resid.cpu().numpy()
     ref_c, ref_r = oracle.chi2_batch(ogeom(g), ps, obs, want_resid=True)
-    gmaps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    if path == "fused":
+        gmaps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    else:
+        gmaps = G.eval_cubes(g, torch.from_numpy(ps))[1].cpu().numpy()
     rmaps = oracle.evaluate_batch(ogeom(g), ps)
     for i in range(ps.shape[0]):
         bound = chi2_bound(rmaps[i], gmaps[i], obs, ref_c[i])
