@@ -154,12 +154,15 @@ GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, 
                               const gbk_obs *obs, double *chi2, float *resid, void *stream);
 
 /* Diagnostics (no counterpart in the paper): measured lane-operation rates
- * of the two ALU pipes the fused evaluator is bound by, FP32 FMA and the
- * MUFU base-2 exponential, on the current device (each a 2-pass timed run
- * of independent dependency chains on every SM).  Synchronises `stream`.
- *  ffma_lane_ops_per_s, ex2_lane_ops_per_s   host outputs. */
-GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ex2_lane_ops_per_s,
-                                        void *stream);
+ * of the ALU pipes the fused evaluator is bound by -- FP32 FMA issued as
+ * scalar and as packed f32x2 instructions, and the MUFU base-2 exponential
+ * -- on the current device (each a 2-pass timed run of independent
+ * dependency chains on every SM).  Synchronises `stream`.
+ *  ffma_lane_ops_per_s    host output: scalar FFMA lane operations / s
+ *  ffma2_lane_ops_per_s   host output: FMA lane operations / s via f32x2
+ *  ex2_lane_ops_per_s     host output: ex2.approx lane operations / s */
+GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ffma2_lane_ops_per_s,
+                                        double *ex2_lane_ops_per_s, void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 GBK_API const char *gbk_last_error(void);

@@ -59,8 +59,8 @@ __device__ inline ModelConst model_const(const double *p, const Geom &g)
     if (g.lsf_mode == 1) sig = sqrtf(s0 * s0 + g.sig_lsf_kms * g.sig_lsf_kms);
     float sp, cp, si, ci;
     // sin/cos of (degrees / 180) * pi with exact argument reduction.
-    sincospif((float)(p[GBK_PA] / 180.0), &sp, &cp);
-    sincospif((float)(p[GBK_INCL] / 180.0), &si, &ci);
+    sincospif((float)(p[GBK_PA] * (1.0 / 180.0)), &sp, &cp);
+    sincospif((float)(p[GBK_INCL] * (1.0 / 180.0)), &si, &ci);
     c.x0 = (float)p[GBK_X0];
     c.y0 = (float)p[GBK_Y0];
     c.sin_pa = sp;
@@ -69,9 +69,9 @@ __device__ inline ModelConst model_const(const double *p, const Geom &g)
     c.inv_cos_i = 1.0f / ci;
     c.vsys = (float)p[GBK_VSYS];
     c.vrot_k = (float)(0.63661977236758134 * p[GBK_VMAX]);
-    c.inv_rt = (float)(1.0 / p[GBK_RT]);
+    c.inv_rt = 1.0f / (float)p[GBK_RT];
     c.i0 = (float)p[GBK_I0];
-    c.inv_h = (float)(1.0 / p[GBK_H]);
+    c.inv_h = 1.0f / (float)p[GBK_H];
     c.sigma = sig;
     c.amp = g.dv / (sig * 2.5066282746310002f);
     c.alpha = 0.84932180028801904f / sig;  // sqrt(log2(e) / 2) / sigma

@@ -5,7 +5,7 @@
 
 namespace gbk {
 
-constexpr int kFusedThreads = 256;
+constexpr int kFusedThreads = 512;
 // Opt-in shared memory per block is 227 KB; 2 KB are left for the static
 // shared memory of the kernel.
 constexpr int kFusedMaxSmem = 225 * 1024;

@@ -27,6 +27,30 @@ __global__ void __launch_bounds__(256) probe_ffma_kernel(float a, float b)
     if (s == 12345.678f) g_probe_sink = s;
 }
 
+// Packed FP32: one fma.rn.f32x2 performs two lane FMAs.
+__global__ void __launch_bounds__(256) probe_ffma2_kernel(float a, float b)
+{
+    unsigned long long x[kProbeChains], av, bv;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a), "f"(a));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(bv) : "f"(b), "f"(b));
+    for (int c = 0; c < kProbeChains; ++c) {
+        float lo = (float)(threadIdx.x + c) * 1e-3f, hi = lo + 0.5f;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x[c]) : "f"(lo), "f"(hi));
+    }
+    for (int i = 0; i < kProbeIters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c)
+            asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(av), "l"(bv));
+    }
+    float s = 0.f;
+    for (int c = 0; c < kProbeChains; ++c) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[c]));
+        s += lo + hi;
+    }
+    if (s == 12345.678f) g_probe_sink = s;
+}
+
 __global__ void __launch_bounds__(256) probe_ex2_kernel(float a)
 {
     float x[kProbeChains];
@@ -44,10 +68,11 @@ __global__ void __launch_bounds__(256) probe_ex2_kernel(float a)
 
 using namespace gbk;
 
-extern "C" gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ex2_lane_ops_per_s,
-                                           void *stream)
+extern "C" gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ffma2_lane_ops_per_s,
+                                           double *ex2_lane_ops_per_s, void *stream)
 {
-    if (!ffma_lane_ops_per_s || !ex2_lane_ops_per_s) return fail(GBK_EINVAL, "output pointer is NULL");
+    if (!ffma_lane_ops_per_s || !ffma2_lane_ops_per_s || !ex2_lane_ops_per_s)
+        return fail(GBK_EINVAL, "output pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -67,6 +92,14 @@ extern "C" gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *
     }
     cudaEventElapsedTime(&ms, t0, t1);
     *ffma_lane_ops_per_s = lanes / (ms * 1e-3);
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(t0, st);
+        probe_ffma2_kernel<<<blocks, threads, 0, st>>>(0.9999f, 1e-4f);
+        cudaEventRecord(t1, st);
+        cudaEventSynchronize(t1);
+    }
+    cudaEventElapsedTime(&ms, t0, t1);
+    *ffma2_lane_ops_per_s = 2.0 * lanes / (ms * 1e-3);
     for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(t0, st);
         probe_ex2_kernel<<<blocks, threads, 0, st>>>(0.5f);

@@ -55,7 +55,7 @@ def lib():
             "gbk_eval_cubes": (i32, [gp, i32, vp, vp, vp, vp, sz, vp]),
             "gbk_chi2": (i32, [gp, i32, vp, op, vp, vp, u32, vp, sz, vp]),
             "gbk_chi2_from_maps": (i32, [i32, i32, i32, vp, op, vp, vp, vp]),
-            "gbk_measure_alu_peak": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]),
+            "gbk_measure_alu_peak": (i32, [ctypes.POINTER(ctypes.c_double)] * 3 + [vp]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
         }
@@ -160,10 +160,11 @@ def gbk_chi2_from_maps(maps, obs, chi2, resid=None, stream=None):
 
 
 def gbk_measure_alu_peak(stream=None):
-    """(FP32 FMA, MUFU ex2) lane-operations per second on the current device."""
-    a, b = ctypes.c_double(), ctypes.c_double()
-    _check(lib().gbk_measure_alu_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream)))
-    return a.value, b.value
+    """(scalar FFMA, packed f32x2 FMA, MUFU ex2) lane operations per second
+    on the current device."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().gbk_measure_alu_peak(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream(stream)))
+    return a.value, b.value, c.value
 
 
 def gbk_version():
