@@ -224,6 +224,7 @@ def run_gbk(args):
     def step(s):
         gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_FUSED, None, stream)
 
+    tuning = gbk.gbk_autotune(g, pool[0], obs, chi2[0], stream)
     for s in range(W):
         step(s)
     torch.cuda.synchronize()
@@ -261,6 +262,8 @@ def run_gbk(args):
            "config": {"workload": "fabry-perot 192x192x48 at 10 km/s, PSF 3 px, LSF 30 km/s, "
                                   "400 live points per step (one batched launch)",
                       "models_per_step": n, "path": "fused", "l2": "flushed between steps (256 MiB write)",
+                      "tuning": {"cluster_ctas": tuning["cluster_ctas"], "threads": tuning["threads"],
+                                 "candidates": tuning["candidates"]},
                       "parallelism": "replicas" if ws > 1 else "single"},
            "gpu_launches": K}
     if args.quick:

@@ -153,6 +153,35 @@ GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *p
 GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, const float *maps,
                               const gbk_obs *obs, double *chi2, float *resid, void *stream);
 
+/* Launch tuning of the fused path (no counterpart in the paper).  A tuning
+ * is the number of CTAs that cooperate on one model (a thread-block cluster
+ * of 1..16 CTAs sharing the model's extended rows through distributed shared
+ * memory) and the block size (512, 384 or 256 threads).  The library keeps
+ * one tuning per geometry (size, kernel radii, LSF mode) for the life of the
+ * process; without one it uses a heuristic. */
+typedef struct gbk_tuning {
+    int32_t cluster_ctas;  /* CTAs per model                              */
+    int32_t threads;       /* threads per CTA                             */
+    float ms;              /* autotune: median time of the best candidate */
+    int32_t candidates;    /* autotune: configurations timed              */
+} gbk_tuning;
+
+/* Times every valid tuning of the fused path on this batch (params, obs and
+ * chi2_scratch as for gbk_chi2; chi2_scratch is overwritten) and keeps the
+ * fastest for this geometry.  Synchronises `stream`; several launches per
+ * candidate.  best (host) receives the choice.  Call it outside any stream
+ * capture. */
+GBK_API gbk_status gbk_autotune(const gbk_geom *g, int32_t n_models, const double *params,
+                                const gbk_obs *obs, double *chi2_scratch, gbk_tuning *best,
+                                void *stream);
+
+/* The tuning the next fused call with this geometry will use (host out). */
+GBK_API gbk_status gbk_get_tuning(const gbk_geom *g, gbk_tuning *out);
+
+/* Sets the tuning for this geometry (e.g. one saved from an earlier
+ * gbk_autotune); t == NULL forgets it.  EINVAL if it cannot run here. */
+GBK_API gbk_status gbk_set_tuning(const gbk_geom *g, const gbk_tuning *t);
+
 /* Diagnostics (no counterpart in the paper): measured lane-operation rates
  * of the ALU pipes the fused evaluator is bound by -- FP32 FMA issued as
  * scalar and as packed f32x2 instructions, and the MUFU base-2 exponential

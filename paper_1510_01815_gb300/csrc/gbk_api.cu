@@ -111,24 +111,6 @@ gbk_status check_obs(const gbk_obs *obs)
     return GBK_OK;
 }
 
-bool fused_config(const Geom &g, int *cs, int *band)
-{
-    if (g.u != 1) return false;
-    const size_t target = 110 * 1024;
-    for (int pass = 0; pass < 2; ++pass) {
-        size_t limit = pass == 0 ? target : (size_t)kFusedMaxSmem;
-        for (int c = 1; c <= kFusedMaxCluster; c *= 2) {
-            int b = (g.ey + c - 1) / c;
-            if (fused_smem_bytes_host(g, b) <= limit) {
-                *cs = c;
-                *band = b;
-                return true;
-            }
-        }
-    }
-    return false;
-}
-
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Staged workspace: [ext][fine (u > 1)][data (if not caller's)][partials].
@@ -172,8 +154,8 @@ size_t gbk_workspace_bytes(const gbk_geom *gin, int32_t n_models, uint32_t flags
     Geom g;
     if (derive_geom(gin, &g) != GBK_OK) return 0;
     if (n_models < 0) { fail(GBK_EINVAL, "n_models must be >= 0"); return 0; }
-    int cs, band;
-    bool fused_ok = fused_config(g, &cs, &band);
+    FusedConfig fc;
+    bool fused_ok = fused_config(g, &fc);
     if (flags == GBK_PATH_FUSED || (flags == GBK_PATH_AUTO && fused_ok)) return 0;
     return staged_layout(g, n_models, true, true).total;
 }
@@ -223,9 +205,13 @@ static gbk_status run_fused(const Geom &g, int32_t n, const double *params, floa
                             double *chi2, float *resid, cudaStream_t st)
 {
     FusedArgs a = {};
-    if (!fused_config(g, &a.cs, &a.band))
+    FusedConfig fc;
+    if (!fused_config(g, &fc))
         return fail(GBK_EUNSUPPORTED, "the fused path cannot serve this geometry (upsample %d, %d x %d)", g.u,
                     g.nx, g.ny);
+    a.cs = fc.cs;
+    a.band = fc.band;
+    a.threads = fc.threads;
     a.g = g;
     a.n_models = n;
     a.params = params;
@@ -252,8 +238,8 @@ gbk_status gbk_eval_cubes(const gbk_geom *gin, int32_t n_models, const double *p
     if (maps && (s = check_device_ptr(maps, "maps", 4))) return s;
     if (!cubes && !maps) return ok();
     cudaStream_t st = (cudaStream_t)stream;
-    int cs, band;
-    if (cubes || !fused_config(g, &cs, &band))
+    FusedConfig fc;
+    if (cubes || !fused_config(g, &fc))
         return run_staged(g, n_models, params, cubes, maps, nullptr, nullptr, nullptr, workspace, ws_bytes, st);
     return run_fused(g, n_models, params, maps, nullptr, nullptr, nullptr, st);
 }
@@ -272,8 +258,8 @@ gbk_status gbk_chi2(const gbk_geom *gin, int32_t n_models, const double *params,
     if (resid && (s = check_device_ptr(resid, "resid", 4))) return s;
     if ((s = check_obs(obs))) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    int cs, band;
-    bool fused_ok = fused_config(g, &cs, &band);
+    FusedConfig fc;
+    bool fused_ok = fused_config(g, &fc);
     if (flags == GBK_PATH_STAGED || (flags == GBK_PATH_AUTO && !fused_ok))
         return run_staged(g, n_models, params, nullptr, nullptr, obs, chi2, resid, workspace, ws_bytes, st);
     return run_fused(g, n_models, params, nullptr, obs, chi2, resid, st);

@@ -11,6 +11,5 @@ gbk_status cuda_fail(cudaError_t e, const char *what);
 gbk_status derive_geom(const gbk_geom *in, Geom *g);
 gbk_status check_device_ptr(const void *p, const char *name, size_t align);
 gbk_status check_obs(const gbk_obs *obs);
-bool fused_config(const Geom &g, int *cs, int *band);
 
 }  // namespace gbk

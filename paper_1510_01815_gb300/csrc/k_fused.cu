@@ -26,8 +26,11 @@
 // Work decomposition: one thread-block cluster per model; the CTAs of the
 // cluster split the extended rows into balanced bands.  Each CTA
 //   phase 1  samples the Gaussian line of every extended spaxel of its band
-//            (the hot loop: one ex2 and five FP32 operations per extended
-//            voxel) into per-spaxel sums Q = (q0, q1, q2, a);
+//            (the hot loop: one ex2 and five FP32 lane operations per
+//            extended voxel, issued as packed f32x2 pairs) into per-spaxel
+//            sums Q = (q0, q1, q2, a); the 2 Rz channels at each band edge
+//            use three table-weighted sums referenced to their block's
+//            middle channel;
 //   phase 2  applies the PSF along x in shared memory (Q -> P);
 //   phase 3  copies the R rows above and below its band from its neighbours'
 //            shared memory (DSMEM, once, coalesced) so that no halo row is
@@ -61,12 +64,27 @@ __host__ __device__ inline size_t fused_q_floats4(const Geom &g, int band)
     return q > h ? q : h;
 }
 
+// Edge channels of the extended band: the lower block [0, elo) and the upper
+// block [ehi, ez) have part of their LSF window outside the data band.
+__host__ __device__ inline int edge_lo_end(const Geom &g) { return g.ez < 2 * g.Rz ? g.ez : 2 * g.Rz; }
+__host__ __device__ inline int edge_hi_begin(const Geom &g)
+{
+    int elo = edge_lo_end(g);
+    return g.nz > elo ? g.nz : elo;
+}
+// Floats per edge table: both blocks, each padded to an even length.
+__host__ __device__ inline int edge_table_len(const Geom &g)
+{
+    int lo = edge_lo_end(g), hi = g.ez - edge_hi_begin(g);
+    return pad4(((lo + 1) & ~1) + ((hi + 1) & ~1));
+}
+
 __host__ __device__ inline size_t fused_smem_bytes(const Geom &g, int band)
 {
     size_t b = 0;
     b += fused_q_floats4(g, band) * sizeof(float4);  // Q / halo rows
     b += (size_t)band * g.nx * sizeof(float4);        // P: band rows after the x pass
-    b += (size_t)g.ez * sizeof(float4);               // z edge table (G0, dv H1, dv^2 H2, -)
+    b += (size_t)3 * edge_table_len(g) * sizeof(float);  // edge tables G0, A1, A2
     b += (size_t)pad4(2 * g.R + 1) * sizeof(float);   // PSF taps
     b += (size_t)pad4(band + 2 * g.R) * sizeof(int);  // row offsets of the y pass
     b += 64 * sizeof(double);                         // reduction scratch
@@ -114,7 +132,8 @@ struct KahanF {
     }
 };
 
-__global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs a)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const Geom &g = a.g;
@@ -131,8 +150,11 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *Q = reinterpret_cast<float4 *>(smem);
     float4 *P = Q + fused_q_floats4(g, band);
-    float4 *ztab = P + (size_t)band * g.nx;
-    float *wxy = reinterpret_cast<float *>(ztab + g.ez);
+    const int etl = edge_table_len(g);
+    float *eG0 = reinterpret_cast<float *>(P + (size_t)band * g.nx);
+    float *eA1 = eG0 + etl;
+    float *eA2 = eA1 + etl;
+    float *wxy = eA2 + etl;
     int *rowoff = reinterpret_cast<int *>(wxy + pad4(2 * R + 1));
     double *red = reinterpret_cast<double *>(rowoff + pad4(band + 2 * R));
 
@@ -150,8 +172,16 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
         for (int j = -g.Rz; j <= g.Rz; ++j) V = fmaf(tap_raw(j, g.sig_z, g.Rz), (float)(j * j), V);
         s_var_z = g.dv * g.dv * (V / S);
     }
-    for (int ee = tid - 32; ee < g.ez; ee += nthr) {  // warps 1.. : z edge table
-        if (ee < 0) continue;
+    // Edge tables.  For an edge channel e with in-band LSF tap sums
+    // G0 = sum L_j, H1 = dv sum L_j j, H2 = dv^2 sum L_j j^2 (j = k - e over
+    // data channels k) and delta = (e - e_ref) dv from its block's middle
+    // channel e_ref:  A1 = delta G0 + H1,  A2 = delta^2 G0 + 2 delta H1 + H2,
+    // so that the moment weights are T0 = G0, T1 = d_ref G0 + A1 and
+    // T2 = d_ref^2 G0 + 2 d_ref A1 + A2 with d_ref = v(e_ref) - a.
+    const int elo = edge_lo_end(g), ehi = edge_hi_begin(g);
+    const int hi_off = (elo + 1) & ~1;  // table slot of channel ehi
+    for (int ee = tid - 32; ee < g.ez; ee += nthr) {  // warps 1.. (warp 0 holds thread 0)
+        if (ee < 0 || (ee >= elo && ee < ehi)) continue;
         int kd = ee - g.Rz;  // data channel of extended channel ee
         int jlo = max(0, kd - g.Rz) - kd, jhi = min(g.nz - 1, kd + g.Rz) - kd;
         float S = tap_sum(g.sig_z, g.Rz);
@@ -162,7 +192,16 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
             H1 = fmaf(w, (float)j, H1);
             H2 = fmaf(w, (float)(j * j), H2);
         }
-        ztab[ee] = make_float4(G0 / S, g.dv * (H1 / S), g.dv * g.dv * (H2 / S), 0.f);
+        G0 /= S;
+        H1 = g.dv * (H1 / S);
+        H2 = g.dv * g.dv * (H2 / S);
+        bool lower = ee < elo;
+        float eref = lower ? 0.5f * (float)(elo - 1) : 0.5f * (float)(ehi + g.ez - 1);
+        float delta = ((float)ee - eref) * g.dv;
+        int slot = lower ? ee : hi_off + (ee - ehi);
+        eG0[slot] = G0;
+        eA1[slot] = fmaf(delta, G0, H1);
+        eA2[slot] = fmaf(delta, fmaf(delta, G0, 2.f * H1), H2);
     }
     // y-pass row offsets (in float4 units from Q) of extended rows [row0 - R, row1 + R)
     for (int k = tid; k < nrows + 2 * R; k += nthr) {
@@ -175,18 +214,17 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
     }
     __syncthreads();
 
-    const ModelConst c = mc;
+    const ModelConst &c = mc;  // read from shared memory (broadcast) to save registers
     const float var_z = s_var_z;
 
     // ---- phase 1: Gaussian line of every extended spaxel of the band ----
     // Interior channels [elo, ehi) have their whole LSF window inside the band.
-    const int elo = min(2 * g.Rz, g.ez);
-    const int ehi = max(g.nz, elo);
     const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;  // v of e = 0
     const float al = c.alpha, adv = c.alpha * g.dv, inv_al = 1.f / c.alpha;
-    const float adv2 = 2.f * adv, adv3 = 3.f * adv;
     const float v_lo = g.vc - 0.5f * (float)(g.nz - 1) * g.dv;  // first and last data channel
     const float v_hi = g.vc + 0.5f * (float)(g.nz - 1) * g.dv;
+    const float eref_lo = 0.5f * (float)(elo - 1), eref_hi = 0.5f * (float)(ehi + g.ez - 1);
+    const f32x2 ADV = pk2(adv, adv), TWO = pk2(2.f, 2.f), Z2 = pk2(0.f, 0.f);
     const int nsp = nrows * g.ex;
     int r = tid / g.ex, xe = tid - r * g.ex;
     const int dr_e = nthr / g.ex, dx_e = nthr - dr_e * g.ex;  // (row, col) step of idx += nthr
@@ -199,68 +237,87 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
         // the FP32 second moment of the truncated spectrum free of
         // cancellation.  (The moments do not depend on this choice.)
         float a_c = fminf(fmaxf(vl, v_lo), v_hi);
-        float base = vz0 - vl;      // d = v_e - v_los at e = 0 (Gaussian argument)
-        float sh = vl - a_c;        // d' = d + sh = v_e - a (moment weight)
-        float ub = al * base;
-        float s0, s1, s2;           // in units of u = alpha d: sum g, sum g u, sum g u^2
-        if (sh == 0.f) {
-            float s0a = 0.f, s1a = 0.f, s2a = 0.f, s0b = 0.f, s1b = 0.f, s2b = 0.f;
+        float sh = vl - a_c;
+        float ub = al * (vz0 - vl);  // u = alpha (v_e - v_los) at e = 0
+        const f32x2 UB = pk2(ub, ub);
+
+        // interior: sums of g, g m, g m^2 with m = alpha (v_e - a)
+        float s0, s1, s2;
+        if (!__any_sync(__activemask(), sh != 0.f)) {
+            // m = u: the Gaussian argument is also the moment variable
+            f32x2 S0 = Z2, S1 = Z2, S2 = Z2;
+            f32x2 FE = pk2((float)elo, (float)(elo + 1));
             int e = elo;
-            float fe = (float)elo;
-            for (; e + 4 <= ehi; e += 4, fe += 4.f) {
-                float u0 = fmaf(fe, adv, ub);
-                float u1 = u0 + adv, u2 = u0 + adv2, u3 = u0 + adv3;
-                float w0 = u0 * u0, w1 = u1 * u1, w2 = u2 * u2, w3 = u3 * u3;
-                float g0 = ex2_approx(-w0), g1 = ex2_approx(-w1);
-                float g2 = ex2_approx(-w2), g3 = ex2_approx(-w3);
-                s0a += g0; s1a = fmaf(g0, u0, s1a); s2a = fmaf(g0, w0, s2a);
-                s0b += g1; s1b = fmaf(g1, u1, s1b); s2b = fmaf(g1, w1, s2b);
-                s0a += g2; s1a = fmaf(g2, u2, s1a); s2a = fmaf(g2, w2, s2a);
-                s0b += g3; s1b = fmaf(g3, u3, s1b); s2b = fmaf(g3, w3, s2b);
+#pragma unroll 2
+            for (; e + 2 <= ehi; e += 2) {
+                f32x2 U = fma2(FE, ADV, UB);
+                f32x2 W = mul2(U, U);
+                float w0, w1;
+                upk2(W, w0, w1);
+                f32x2 G = pk2(ex2_approx(-w0), ex2_approx(-w1));
+                S0 = add2(S0, G); S1 = fma2(G, U, S1); S2 = fma2(G, W, S2);
+                FE = add2(FE, TWO);
             }
+            s0 = hsum2(S0);
+            s1 = hsum2(S1);
+            s2 = hsum2(S2);
+            float fe = (float)e;
             for (; e < ehi; ++e, fe += 1.f) {
                 float u0 = fmaf(fe, adv, ub);
                 float w0 = u0 * u0;
                 float g0 = ex2_approx(-w0);
-                s0a += g0; s1a = fmaf(g0, u0, s1a); s2a = fmaf(g0, w0, s2a);
+                s0 += g0; s1 = fmaf(g0, u0, s1); s2 = fmaf(g0, w0, s2);
             }
-            s0 = s0a + s0b; s1 = s1a + s1b; s2 = s2a + s2b;
         } else {
-            float ubs = al * (base + sh);
+            // some lane of the warp has its line outside the band: m = u + alpha sh
+            float su = al * sh;
             s0 = s1 = s2 = 0.f;
             float fe = (float)elo;
             for (int e = elo; e < ehi; ++e, fe += 1.f) {
                 float u0 = fmaf(fe, adv, ub);
-                float w0 = fmaf(fe, adv, ubs);
+                float m0 = u0 + su;
                 float g0 = ex2_approx(-u0 * u0);
-                float t0 = g0 * w0;
-                s0 += g0; s1 += t0; s2 = fmaf(t0, w0, s2);
+                float t0 = g0 * m0;
+                s0 += g0; s1 += t0; s2 = fmaf(t0, m0, s2);
             }
         }
-        float E0 = 0.f, E1 = 0.f, E2 = 0.f;
-        for (int pass = 0; pass < 2; ++pass) {
-            int eb = pass ? ehi : 0, ee = pass ? g.ez : elo;
-            float fk = (float)eb;
-            for (int k = eb; k < ee; ++k, fk += 1.f) {
-                float d = fmaf(fk, g.dv, base);
-                float u = al * d;
-                float gg = ex2_approx(-u * u);
-                float dp = d + sh;
-                float4 T = ztab[k];
-                float t0 = gg * T.x;
-                float h = gg * T.y;
-                E0 += t0;
-                E1 = fmaf(t0, dp, E1 + h);
-                E2 = fmaf(t0 * dp, dp, fmaf(h, 2.f * dp, fmaf(gg, T.z, E2)));
+        float q0 = s0, q1 = s1 * inv_al, q2 = fmaf(s2, inv_al * inv_al, var_z * s0);
+
+        // edge blocks: E0 = sum g G0, B1 = sum g A1, B2 = sum g A2
+        for (int blk = 0; blk < 2; ++blk) {
+            int eb = blk ? ehi : 0, ee = blk ? g.ez : elo;
+            if (eb >= ee) continue;
+            const int toff = blk ? hi_off - ehi : 0;  // table slot = e + toff
+            f32x2 E0 = Z2, B1 = Z2, B2 = Z2;
+            f32x2 FK = pk2((float)eb, (float)(eb + 1));
+            int k = eb;
+            for (; k + 2 <= ee; k += 2) {
+                f32x2 U = fma2(FK, ADV, UB);
+                f32x2 W = mul2(U, U);
+                float w0, w1;
+                upk2(W, w0, w1);
+                f32x2 G = pk2(ex2_approx(-w0), ex2_approx(-w1));
+                const int t = k + toff;
+                E0 = fma2(G, *reinterpret_cast<const f32x2 *>(eG0 + t), E0);
+                B1 = fma2(G, *reinterpret_cast<const f32x2 *>(eA1 + t), B1);
+                B2 = fma2(G, *reinterpret_cast<const f32x2 *>(eA2 + t), B2);
+                FK = add2(FK, TWO);
             }
+            float e0 = hsum2(E0), b1 = hsum2(B1), b2 = hsum2(B2);
+            if (k < ee) {
+                float u0 = fmaf((float)k, adv, ub);
+                float g0 = ex2_approx(-u0 * u0);
+                e0 = fmaf(g0, eG0[k + toff], e0);
+                b1 = fmaf(g0, eA1[k + toff], b1);
+                b2 = fmaf(g0, eA2[k + toff], b2);
+            }
+            float dref = fmaf(blk ? eref_hi : eref_lo, g.dv, vz0) - a_c;
+            q0 += e0;
+            q1 += fmaf(dref, e0, b1);
+            q2 += fmaf(dref, fmaf(dref, e0, 2.f * b1), b2);
         }
         float A = c.amp * br;
-        float4 q;
-        q.x = A * (s0 + E0);
-        q.y = A * fmaf(s1, inv_al, E1);
-        q.z = A * (fmaf(s2, inv_al * inv_al, var_z * s0) + E2);
-        q.w = a_c;
-        Q[idx] = q;
+        Q[idx] = make_float4(A * q0, A * q1, A * q2, a_c);
         xe += dx_e; r += dr_e;
         if (xe >= g.ex) { xe -= g.ex; ++r; }
     }
@@ -371,27 +428,27 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_eval_kernel(FusedArgs 
     cluster.sync();  // keep every CTA's shared memory alive until rank 0 is done
 }
 
-gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
+template <int NT, int MINB>
+static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_t stream)
 {
-    size_t smem = fused_smem_bytes(args.g, args.band);
     // Shared-memory opt-in is set to what this launch needs (static shared
     // memory of the kernel counts against the same per-block limit).
     static size_t configured = 0;
     static bool cluster_configured = false;
+    auto kern = fused_eval_kernel<NT, MINB>;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel: setting dynamic shared memory");
         configured = smem;
     }
     if (!cluster_configured) {
-        cudaError_t e = cudaFuncSetAttribute(fused_eval_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel: allowing 16-CTA clusters");
         cluster_configured = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(args.n_models * args.cs), 1, 1);
-    cfg.blockDim = dim3(kFusedThreads, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
@@ -401,9 +458,20 @@ gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, fused_eval_kernel, args);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
     return GBK_OK;
+}
+
+gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
+{
+    size_t smem = fused_smem_bytes(args.g, args.band);
+    switch (args.threads) {
+    case 512: return launch_variant<512, 2>(args, smem, stream);
+    case 384: return launch_variant<384, 2>(args, smem, stream);
+    case 256: return launch_variant<256, 3>(args, smem, stream);
+    default: return fail(GBK_EINVAL, "unsupported fused block size %d", args.threads);
+    }
 }
 
 }  // namespace gbk

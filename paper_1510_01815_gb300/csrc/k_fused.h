@@ -5,7 +5,7 @@
 
 namespace gbk {
 
-constexpr int kFusedThreads = 512;
+constexpr int kFusedThreads = 512;  // default block size (variants: 512, 384, 256)
 // Opt-in shared memory per block is 227 KB; 2 KB are left for the static
 // shared memory of the kernel.
 constexpr int kFusedMaxSmem = 225 * 1024;
@@ -19,11 +19,21 @@ struct FusedArgs {
     float *maps;            // [n_models][3][ny][nx] or null
     double *chi2;           // [n_models] or null
     float *resid;           // [n_models][2][ny][nx] or null
-    int cs;                 // CTAs (cluster size) per model
-    int band;               // extended rows per CTA = ceil(ey / cs)
+    int cs;                 // CTAs (cluster size) per model, 1..16
+    int band;               // most extended rows of any CTA = ceil(ey / cs)
+    int threads;            // block size: 512, 384 or 256
+};
+
+// Launch configuration of the fused kernel (see tune.cu).
+struct FusedConfig {
+    int cs;       // CTAs (cluster size) per model
+    int band;     // ceil(ey / cs)
+    int threads;  // block size
 };
 
 size_t fused_smem_bytes_host(const Geom &g, int band);
+bool fused_config(const Geom &g, FusedConfig *cfg);
+bool fused_config_valid(const Geom &g, int cs, int threads, FusedConfig *cfg);
 gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream);
 
 }  // namespace gbk

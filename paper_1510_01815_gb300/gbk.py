@@ -32,6 +32,11 @@ class CGeom(ctypes.Structure):
                 ("halo_sigmas", ctypes.c_double)]
 
 
+class CTuning(ctypes.Structure):
+    _fields_ = [("cluster_ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("candidates", ctypes.c_int32)]
+
+
 class CObs(ctypes.Structure):
     _fields_ = [("v_obs", ctypes.c_void_p), ("s_obs", ctypes.c_void_p), ("w_v", ctypes.c_void_p),
                 ("w_s", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
@@ -56,6 +61,9 @@ def lib():
             "gbk_chi2": (i32, [gp, i32, vp, op, vp, vp, u32, vp, sz, vp]),
             "gbk_chi2_from_maps": (i32, [i32, i32, i32, vp, op, vp, vp, vp]),
             "gbk_measure_alu_peak": (i32, [ctypes.POINTER(ctypes.c_double)] * 3 + [vp]),
+            "gbk_autotune": (i32, [gp, i32, vp, op, vp, ctypes.POINTER(CTuning), vp]),
+            "gbk_get_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
+            "gbk_set_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
         }
@@ -69,7 +77,8 @@ def lib():
 
 def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps",
-            "gbk_measure_alu_peak", "gbk_last_error", "gbk_version"]
+            "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
+            "gbk_last_error", "gbk_version"]
 
 
 def cgeom(g):
@@ -165,6 +174,35 @@ def gbk_measure_alu_peak(stream=None):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib().gbk_measure_alu_peak(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream(stream)))
     return a.value, b.value, c.value
+
+
+def gbk_autotune(geom, params, obs, chi2_scratch, stream=None):
+    """Times the fused-path tunings on this batch and keeps the fastest for
+    the geometry; returns a dict of the choice."""
+    g = cgeom(geom)
+    n = params.shape[0] if params.dim() == 2 else params.numel() // NPAR
+    t = CTuning()
+    _check(lib().gbk_autotune(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"),
+                              ctypes.byref(obs.c()), _ptr(chi2_scratch, torch.float64, "chi2_scratch"),
+                              ctypes.byref(t), _stream(stream)))
+    return {"cluster_ctas": t.cluster_ctas, "threads": t.threads, "ms": t.ms, "candidates": t.candidates}
+
+
+def gbk_get_tuning(geom):
+    g = cgeom(geom)
+    t = CTuning()
+    _check(lib().gbk_get_tuning(ctypes.byref(g), ctypes.byref(t)))
+    return {"cluster_ctas": t.cluster_ctas, "threads": t.threads}
+
+
+def gbk_set_tuning(geom, cluster_ctas=None, threads=None):
+    """Forces a tuning for the geometry (None forgets it)."""
+    g = cgeom(geom)
+    if cluster_ctas is None:
+        _check(lib().gbk_set_tuning(ctypes.byref(g), None))
+        return
+    t = CTuning(int(cluster_ctas), int(threads), 0.0, 0)
+    _check(lib().gbk_set_tuning(ctypes.byref(g), ctypes.byref(t)))
 
 
 def gbk_version():

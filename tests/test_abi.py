@@ -104,3 +104,25 @@ def test_bad_flags_rejected(gbk):
     cg = gbk.cgeom(FP_GEOM)
     st = gbk.lib().gbk_chi2(ctypes.byref(cg), 1, None, None, None, None, 99, None, 0, None)
     assert st == gbk.GBK_EINVAL
+
+
+def test_tuning_host_logic(gbk):
+    """Heuristic default, forced tunings and their validation (no GPU)."""
+    from paper_1510_01815_gb300.synth import Geometry
+    g = FP_GEOM
+    t = gbk.gbk_get_tuning(g)
+    assert 1 <= t["cluster_ctas"] <= 16 and t["threads"] in (256, 384, 512)
+    gbk.gbk_set_tuning(g, 8, 512)
+    assert gbk.gbk_get_tuning(g) == {"cluster_ctas": 8, "threads": 512}
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_set_tuning(g, 17, 512)
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_set_tuning(g, 8, 300)
+    with pytest.raises(gbk.GbkError):      # one CTA cannot hold a 204-row band
+        gbk.gbk_set_tuning(g, 1, 512)
+    gbk.gbk_set_tuning(g, None)
+    assert gbk.gbk_get_tuning(g) == t
+    small = Geometry(3, 5, 7, 40.0, 0.0, 1.5, 50.0)
+    assert gbk.gbk_get_tuning(small)["cluster_ctas"] >= 1
+    with pytest.raises(gbk.GbkError):      # upsampled geometries use the staged path
+        gbk.gbk_get_tuning(SINGLE_GEOM.with_(upsample=2))

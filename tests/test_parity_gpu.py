@@ -194,3 +194,40 @@ def test_fabry_perot_full_size(G):
         rm = ref[i] if i < 2 else oracle.evaluate(ogeom(g), ps[i])
         rc = oracle.chi2_maps(rm, obs)
         assert abs(c[i] - rc) <= chi2_bound(rm, allmaps[i], obs, rc), (i, c[i], rc)
+
+
+@pytest.mark.parametrize("case,cs,threads", [
+    ("grid64", 1, 512), ("grid64", 2, 384), ("grid64", 3, 256), ("grid64", 5, 512), ("grid64", 16, 384),
+    ("single", 1, 256), ("single", 7, 512), ("nonsquare", 4, 384), ("wide_kernels", 6, 512),
+    ("prime_13x11x17", 16, 256)])
+def test_every_tuning_matches_oracle(G, case, cs, threads):
+    """Forced launch configurations (CTAs per model, block size) all give the
+    oracle's maps; chi2 agrees across configurations."""
+    g, p, ps = _params(case, n=3)
+    ref = oracle.evaluate_batch(ogeom(g), ps)
+    obs = make_obs(g, p, seed=5)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    base = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED).cpu().numpy()
+    try:
+        G.gbk_set_tuning(g, cs, threads)
+        maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+        c = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED).cpu().numpy()
+    finally:
+        G.gbk_set_tuning(g, None)
+    check_maps(maps, ref, ps, "%s cs=%d nt=%d" % (case, cs, threads))
+    np.testing.assert_allclose(c, base, rtol=1e-5)
+
+
+def test_autotune_picks_a_valid_tuning(G):
+    g, p, ps = _params("grid64", n=16)
+    obs = make_obs(g, p, seed=6)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    scratch = torch.empty(16, dtype=torch.float64, device="cuda")
+    try:
+        t = G.gbk_autotune(g, torch.from_numpy(ps).cuda(), dobs, scratch)
+        assert t["candidates"] >= 3 and t["ms"] > 0
+        assert G.gbk_get_tuning(g) == {"cluster_ctas": t["cluster_ctas"], "threads": t["threads"]}
+        maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    finally:
+        G.gbk_set_tuning(g, None)
+    check_maps(maps, oracle.evaluate_batch(ogeom(g), ps), ps, "autotuned")
