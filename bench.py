@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--models", type=int, default=synth.FP_LIVE_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
+    ap.add_argument("--tuning", default=None,
+                    help="CTAS,THREADS,PERSISTENT: use this fused-kernel tuning instead of autotuning")
     return ap.parse_args()
 
 
@@ -224,7 +226,12 @@ def run_gbk(args):
     def step(s):
         gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_FUSED, None, stream)
 
-    tuning = gbk.gbk_autotune(g, pool[0], obs, chi2[0], stream)
+    if args.tuning:
+        cs_, nt_, pe_ = (int(v) for v in args.tuning.split(","))
+        gbk.gbk_set_tuning(g, cs_, nt_, pe_)
+        tuning = {"cluster_ctas": cs_, "threads": nt_, "persistent": pe_, "candidates": 0}
+    else:
+        tuning = gbk.gbk_autotune(g, pool[0], obs, chi2[0], stream)
     for s in range(W):
         step(s)
     torch.cuda.synchronize()
@@ -263,7 +270,7 @@ def run_gbk(args):
                                   "400 live points per step (one batched launch)",
                       "models_per_step": n, "path": "fused", "l2": "flushed between steps (256 MiB write)",
                       "tuning": {"cluster_ctas": tuning["cluster_ctas"], "threads": tuning["threads"],
-                                 "candidates": tuning["candidates"]},
+                                 "persistent": tuning["persistent"], "candidates": tuning["candidates"]},
                       "parallelism": "replicas" if ws > 1 else "single"},
            "gpu_launches": K}
     if args.quick:

@@ -156,14 +156,16 @@ GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, 
 /* Launch tuning of the fused path (no counterpart in the paper).  A tuning
  * is the number of CTAs that cooperate on one model (a thread-block cluster
  * of 1..16 CTAs sharing the model's extended rows through distributed shared
- * memory) and the block size (512, 384 or 256 threads).  The library keeps
+ * memory), the block size (512, 384 or 256 threads) and the grid shape.  The library keeps
  * one tuning per geometry (size, kernel radii, LSF mode) for the life of the
  * process; without one it uses a heuristic. */
 typedef struct gbk_tuning {
-    int32_t cluster_ctas;  /* CTAs per model                              */
-    int32_t threads;       /* threads per CTA                             */
-    float ms;              /* autotune: median time of the best candidate */
-    int32_t candidates;    /* autotune: configurations timed              */
+    int32_t cluster_ctas;  /* CTAs per model                                  */
+    int32_t threads;       /* threads per CTA                                 */
+    int32_t persistent;    /* 1: one resident wave of clusters loops over the */
+                           /* models; 0: one cluster per model                */
+    float ms;              /* autotune: median time of the best candidate     */
+    int32_t candidates;    /* autotune: configurations timed                  */
 } gbk_tuning;
 
 /* Times every valid tuning of the fused path on this batch (params, obs and

@@ -212,6 +212,7 @@ static gbk_status run_fused(const Geom &g, int32_t n, const double *params, floa
     a.cs = fc.cs;
     a.band = fc.band;
     a.threads = fc.threads;
+    a.persistent = fc.persistent;
     a.g = g;
     a.n_models = n;
     a.params = params;

@@ -7,7 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/gbk.h"
+#include "gbk.h"
 
 namespace gbk {
 

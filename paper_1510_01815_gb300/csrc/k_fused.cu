@@ -23,8 +23,12 @@
 //     (clamped into the band) keeps the FP32 second moment free of
 //     cancellation.
 //
-// Work decomposition: one thread-block cluster per model; the CTAs of the
-// cluster split the extended rows into balanced bands.  Each CTA
+// Work decomposition: thread-block clusters loop over the models (either one
+// resident wave of clusters, as many as fit on the device, or one cluster per
+// model -- a tuning choice); the CTAs of a cluster split a model's
+// extended rows into balanced bands.  The PSF taps, LSF edge tables and row
+// offsets depend only on the geometry and are set up once per CTA.  For each
+// model each CTA
 //   phase 1  samples the Gaussian line of every extended spaxel of its band
 //            (the hot loop: one ex2 and five FP32 lane operations per
 //            extended voxel, issued as packed f32x2 pairs) into per-spaxel
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     const Geom &g = a.g;
     const int cs = a.cs;
     const int rank = (int)cluster.block_rank();
-    const int model = blockIdx.x / cs;
+    const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;  // this cluster, clusters in the grid
     const int band = a.band;                          // max rows of any CTA
     const int row0 = band_begin(rank, g.ey, cs);
     const int row1 = band_begin(rank + 1, g.ey, cs);
@@ -161,8 +165,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     __shared__ ModelConst mc;
     __shared__ float s_var_z;  // dv^2 * sum_j j^2 L_j
 
-    // ---- set-up, all in parallel, one barrier ----
-    if (tid == 0) mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
+    // ---- set-up of the geometry-only tables, all in parallel, one barrier ----
     if (tid >= nthr - 32) {  // last warp: PSF taps
         for (int j = tid - (nthr - 32); j <= 2 * R; j += 32)
             wxy[j] = tap_raw(j - R, g.sig_xy, R) / tap_sum(g.sig_xy, R);
@@ -213,9 +216,13 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         rowoff[k] = off;
     }
     __syncthreads();
-
-    const ModelConst &c = mc;  // read from shared memory (broadcast) to save registers
     const float var_z = s_var_z;
+    const ModelConst &c = mc;  // read from shared memory (broadcast) to save registers
+
+    // Persistent: the clusters of the grid take the models in turn.
+    for (int model = cid; model < a.n_models; model += ncl) {
+    if (tid == 0) mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
+    __syncthreads();
 
     // ---- phase 1: Gaussian line of every extended spaxel of the band ----
     // Interior channels [elo, ehi) have their whole LSF window inside the band.
@@ -341,13 +348,33 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     cluster.sync();  // every CTA's P is complete and visible cluster-wide; Q is free
 
     // ---- phase 3a: copy the halo rows of the y pass from the neighbours ----
-    for (int k = 0; k < 2 * R; ++k) {
-        int er = (k < R) ? row0 - R + k : row1 + (k - R);
-        if (er < 0 || er >= g.ey) continue;
-        int owner = band_owner(er, g.ey, cs);
-        const float4 *src = cluster.map_shared_rank(P, owner) + (size_t)(er - band_begin(owner, g.ey, cs)) * g.nx;
-        float4 *dst = Q + (size_t)k * g.nx;
-        for (int xx = tid; xx < g.nx; xx += nthr) dst[xx] = src[xx];
+    // All of a thread's remote loads are issued before its shared stores so
+    // the DSMEM latencies overlap.
+    {
+        const int nh = 2 * R * g.nx;
+        constexpr int kU = 4;
+        for (int base = tid; base < nh; base += kU * nthr) {
+            float4 v[kU];
+            int dst[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                int i = base + u * nthr;
+                dst[u] = -1;
+                if (i < nh) {
+                    int k = i / g.nx, xx = i - k * g.nx;
+                    int er = (k < R) ? row0 - R + k : row1 + (k - R);
+                    if (er >= 0 && er < g.ey) {
+                        int owner = band_owner(er, g.ey, cs);
+                        const float4 *src = cluster.map_shared_rank(P, owner);
+                        v[u] = src[(size_t)(er - band_begin(owner, g.ey, cs)) * g.nx + xx];
+                        dst[u] = i;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (dst[u] >= 0) Q[dst[u]] = v[u];
+        }
     }
     __syncthreads();
 
@@ -363,8 +390,20 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     const float nanf_ = __int_as_float(0x7fc00000);
     r = tid / g.nx;
     x = tid - r * g.nx;
+    const bool want_obs = want_chi2 || a.resid;
     for (int idx = tid; idx < nyout * g.nx; idx += nthr) {
         int y = ylo + r;
+        size_t pix = (size_t)y * g.nx + x;
+        // observed values first, so their latency overlaps the y pass
+        uint8_t mk = 0;
+        float vo = 0.f, so = 0.f, wv = 0.f, ws = 0.f;
+        if (want_obs) {
+            mk = a.obs.mask[pix];
+            vo = a.obs.v_obs[pix];
+            so = a.obs.s_obs[pix];
+            wv = a.obs.w_v[pix];
+            ws = a.obs.w_s[pix];
+        }
         int k0 = y - (row0 - R);  // row-offset index of extended row y (tap j = 0)
         float cen = Q[rowoff[k0 + R] + x].w;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
@@ -374,24 +413,24 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         if (!c.valid) {
             m0 = m1 = m2 = nanf_;
         } else if (valid) {
-            float mu = s1 / s0;
-            float var = fmaf(-mu, mu, s2 / s0);
+            float inv = __frcp_rn(s0);
+            float mu = s1 * inv;
+            float var = fmaf(-mu, mu, s2 * inv);
             m0 = s0;
             m1 = cen + mu;
             m2 = sqrtf(fmaxf(var, 0.f));
         } else {
             m0 = 0.f; m1 = c.vsys; m2 = 0.f;
         }
-        size_t pix = (size_t)y * g.nx + x;
         if (a.maps) {
             float *mp = a.maps + (size_t)model * 3 * np;
             mp[pix] = m0; mp[np + pix] = m1; mp[2 * np + pix] = m2;
         }
-        if (want_chi2 || a.resid) {
+        if (want_obs) {
             float rv = 0.f, rs = 0.f;
-            if (a.obs.mask[pix] != 0 && (valid || !c.valid)) {
-                rv = a.obs.w_v[pix] * (m1 - a.obs.v_obs[pix]);
-                rs = a.obs.w_s[pix] * (m2 - a.obs.s_obs[pix]);
+            if (mk != 0 && (valid || !c.valid)) {
+                rv = wv * (m1 - vo);
+                rs = ws * (m2 - so);
             }
             acc.add(rv * rv);
             acc.add(rs * rs);
@@ -416,7 +455,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             red[32] = s;
         }
     }
-    cluster.sync();  // halo copies done everywhere; CTA parts visible
+    // Halo reads of every CTA's P are done and the CTA parts of chi2 are
+    // visible.  No second barrier is needed before the next model: P and
+    // red are next written after that model's first cluster barrier, which
+    // rank 0 reaches only once it has read the parts below.
+    cluster.sync();
     if (want_chi2 && rank == 0 && tid == 0) {
         double s = 0.0;
         for (int rr = 0; rr < cs; ++rr) {
@@ -425,6 +468,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         }
         a.chi2[model] = c.valid ? s : (double)nanf_;
     }
+    }  // models
     cluster.sync();  // keep every CTA's shared memory alive until rank 0 is done
 }
 
@@ -447,7 +491,6 @@ static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_
         cluster_configured = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(args.n_models * args.cs), 1, 1);
     cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
@@ -458,6 +501,23 @@ static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // One wave of clusters: as many as can be resident at once (cached per
+    // cluster size and shared-memory size), each looping over models.
+    static int cached_cs = -1, cached_clusters = 0;
+    static size_t cached_smem = 0;
+    if (cached_cs != args.cs || cached_smem != smem) {
+        cfg.gridDim = dim3((unsigned)args.cs, 1, 1);
+        int ncl = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+        if (e != cudaSuccess) return cuda_fail(e, "fused kernel: cluster occupancy query");
+        if (ncl < 1) return fail(GBK_EUNSUPPORTED, "no %d-CTA cluster of the fused kernel fits on this device", args.cs);
+        cached_cs = args.cs;
+        cached_smem = smem;
+        cached_clusters = ncl;
+    }
+    int ncl = args.n_models;
+    if (args.persistent && cached_clusters < ncl) ncl = cached_clusters;
+    cfg.gridDim = dim3((unsigned)(ncl * args.cs), 1, 1);
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
     return GBK_OK;

@@ -22,18 +22,21 @@ struct FusedArgs {
     int cs;                 // CTAs (cluster size) per model, 1..16
     int band;               // most extended rows of any CTA = ceil(ey / cs)
     int threads;            // block size: 512, 384 or 256
+    int persistent;         // 1: one resident wave of clusters loops over the models;
+                            // 0: one cluster per model
 };
 
 // Launch configuration of the fused kernel (see tune.cu).
 struct FusedConfig {
-    int cs;       // CTAs (cluster size) per model
-    int band;     // ceil(ey / cs)
-    int threads;  // block size
+    int cs;          // CTAs (cluster size) per model
+    int band;        // ceil(ey / cs)
+    int threads;     // block size
+    int persistent;  // grid shape (see FusedArgs)
 };
 
 size_t fused_smem_bytes_host(const Geom &g, int band);
 bool fused_config(const Geom &g, FusedConfig *cfg);
-bool fused_config_valid(const Geom &g, int cs, int threads, FusedConfig *cfg);
+bool fused_config_valid(const Geom &g, int cs, int threads, int persistent, FusedConfig *cfg);
 gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream);
 
 }  // namespace gbk

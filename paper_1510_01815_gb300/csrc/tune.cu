@@ -1,7 +1,7 @@
 // tune.cu -- launch configuration of the fused kernel: a heuristic default
 // and a measuring autotuner with a per-geometry cache.
 //
-// A configuration is (cluster size = CTAs per model, block size).  The
+// A configuration is (cluster size = CTAs per model, block size, grid shape).  The
 // cluster size sets how many extended rows each CTA owns (its shared memory
 // and the balance of the line-sampling work); the block size sets the
 // register budget and the warps per SM.  The autotuner times every valid
@@ -36,8 +36,9 @@ static size_t occupancy_smem(int threads)
     return (size_t)(228 * 1024 / b) - 3 * 1024;
 }
 
-bool fused_config_valid(const Geom &g, int cs, int threads, FusedConfig *cfg)
+bool fused_config_valid(const Geom &g, int cs, int threads, int persistent, FusedConfig *cfg)
 {
+    if (persistent != 0 && persistent != 1) return false;
     if (g.u != 1 || cs < 1 || cs > kFusedMaxCluster || cs > g.ey) return false;
     if (threads != 512 && threads != 384 && threads != 256) return false;
     int band = (g.ey + cs - 1) / cs;
@@ -45,6 +46,7 @@ bool fused_config_valid(const Geom &g, int cs, int threads, FusedConfig *cfg)
     cfg->cs = cs;
     cfg->band = band;
     cfg->threads = threads;
+    cfg->persistent = persistent;
     return true;
 }
 
@@ -61,13 +63,13 @@ static double balance(const Geom &g, int cs, int threads)
 
 static bool heuristic(const Geom &g, FusedConfig *cfg)
 {
-    const int threads = 384;
+    const int threads = 512;
     double best = -1.0;
     for (int pass = 0; pass < 2 && best < 0.0; ++pass) {
         size_t cap = pass == 0 ? occupancy_smem(threads) : (size_t)kFusedMaxSmem;
         for (int cs = 1; cs <= kFusedMaxCluster; ++cs) {
             FusedConfig c;
-            if (!fused_config_valid(g, cs, threads, &c)) continue;
+            if (!fused_config_valid(g, cs, threads, 0, &c)) continue;
             if (fused_smem_bytes_host(g, c.band) > cap) continue;
             double b = balance(g, cs, threads);
             if (b > best + 1e-3) {
@@ -115,13 +117,14 @@ gbk_status gbk_autotune(const gbk_geom *gin, int32_t n_models, const double *par
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    FusedConfig bestc = {0, 0, 0};
+    FusedConfig bestc = {0, 0, 0, 0};
     float best_ms = 0.f;
     int tried = 0;
+    for (int pers = 0; pers < 2; ++pers) {
     for (int ti = 0; ti < 3; ++ti) {
         for (int cs = 1; cs <= kFusedMaxCluster; ++cs) {
             FusedConfig c;
-            if (!fused_config_valid(g, cs, kBlockSizes[ti], &c)) continue;
+            if (!fused_config_valid(g, cs, kBlockSizes[ti], pers, &c)) continue;
             FusedArgs a = {};
             a.g = g;
             a.n_models = n_models;
@@ -131,6 +134,7 @@ gbk_status gbk_autotune(const gbk_geom *gin, int32_t n_models, const double *par
             a.cs = c.cs;
             a.band = c.band;
             a.threads = c.threads;
+            a.persistent = c.persistent;
             if (launch_fused(a, st) != GBK_OK) {  // e.g. a cluster shape the device cannot place
                 cudaGetLastError();
                 continue;
@@ -156,6 +160,7 @@ gbk_status gbk_autotune(const gbk_geom *gin, int32_t n_models, const double *par
             }
         }
     }
+    }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     cudaError_t e = cudaGetLastError();
@@ -167,6 +172,7 @@ gbk_status gbk_autotune(const gbk_geom *gin, int32_t n_models, const double *par
     }
     best->cluster_ctas = bestc.cs;
     best->threads = bestc.threads;
+    best->persistent = bestc.persistent;
     best->ms = best_ms;
     best->candidates = tried;
     return ok();
@@ -182,6 +188,7 @@ gbk_status gbk_get_tuning(const gbk_geom *gin, gbk_tuning *out)
     if (!fused_config(g, &c)) return fail(GBK_EUNSUPPORTED, "the fused path cannot serve this geometry");
     out->cluster_ctas = c.cs;
     out->threads = c.threads;
+    out->persistent = c.persistent;
     out->ms = 0.f;
     out->candidates = 0;
     return ok();
@@ -198,9 +205,9 @@ gbk_status gbk_set_tuning(const gbk_geom *gin, const gbk_tuning *t)
         return ok();
     }
     FusedConfig c;
-    if (!fused_config_valid(g, t->cluster_ctas, t->threads, &c))
-        return fail(GBK_EINVAL, "cluster_ctas %d / threads %d is not a valid fused configuration here",
-                    t->cluster_ctas, t->threads);
+    if (!fused_config_valid(g, t->cluster_ctas, t->threads, t->persistent, &c))
+        return fail(GBK_EINVAL, "cluster_ctas %d / threads %d / persistent %d is not a valid fused configuration here",
+                    t->cluster_ctas, t->threads, t->persistent);
     g_tune_cache[key_of(g)] = c;
     return ok();
 }

@@ -33,8 +33,8 @@ class CGeom(ctypes.Structure):
 
 
 class CTuning(ctypes.Structure):
-    _fields_ = [("cluster_ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("candidates", ctypes.c_int32)]
+    _fields_ = [("cluster_ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("candidates", ctypes.c_int32)]
 
 
 class CObs(ctypes.Structure):
@@ -185,23 +185,24 @@ def gbk_autotune(geom, params, obs, chi2_scratch, stream=None):
     _check(lib().gbk_autotune(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"),
                               ctypes.byref(obs.c()), _ptr(chi2_scratch, torch.float64, "chi2_scratch"),
                               ctypes.byref(t), _stream(stream)))
-    return {"cluster_ctas": t.cluster_ctas, "threads": t.threads, "ms": t.ms, "candidates": t.candidates}
+    return {"cluster_ctas": t.cluster_ctas, "threads": t.threads, "persistent": t.persistent, "ms": t.ms,
+            "candidates": t.candidates}
 
 
 def gbk_get_tuning(geom):
     g = cgeom(geom)
     t = CTuning()
     _check(lib().gbk_get_tuning(ctypes.byref(g), ctypes.byref(t)))
-    return {"cluster_ctas": t.cluster_ctas, "threads": t.threads}
+    return {"cluster_ctas": t.cluster_ctas, "threads": t.threads, "persistent": t.persistent}
 
 
-def gbk_set_tuning(geom, cluster_ctas=None, threads=None):
+def gbk_set_tuning(geom, cluster_ctas=None, threads=None, persistent=0):
     """Forces a tuning for the geometry (None forgets it)."""
     g = cgeom(geom)
     if cluster_ctas is None:
         _check(lib().gbk_set_tuning(ctypes.byref(g), None))
         return
-    t = CTuning(int(cluster_ctas), int(threads), 0.0, 0)
+    t = CTuning(int(cluster_ctas), int(threads), int(persistent), 0.0, 0)
     _check(lib().gbk_set_tuning(ctypes.byref(g), ctypes.byref(t)))
 
 

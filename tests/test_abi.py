@@ -112,8 +112,10 @@ def test_tuning_host_logic(gbk):
     g = FP_GEOM
     t = gbk.gbk_get_tuning(g)
     assert 1 <= t["cluster_ctas"] <= 16 and t["threads"] in (256, 384, 512)
-    gbk.gbk_set_tuning(g, 8, 512)
-    assert gbk.gbk_get_tuning(g) == {"cluster_ctas": 8, "threads": 512}
+    gbk.gbk_set_tuning(g, 8, 512, 1)
+    assert gbk.gbk_get_tuning(g) == {"cluster_ctas": 8, "threads": 512, "persistent": 1}
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_set_tuning(g, 8, 512, 2)
     with pytest.raises(gbk.GbkError):
         gbk.gbk_set_tuning(g, 17, 512)
     with pytest.raises(gbk.GbkError):

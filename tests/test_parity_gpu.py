@@ -196,25 +196,28 @@ def test_fabry_perot_full_size(G):
         assert abs(c[i] - rc) <= chi2_bound(rm, allmaps[i], obs, rc), (i, c[i], rc)
 
 
-@pytest.mark.parametrize("case,cs,threads", [
-    ("grid64", 1, 512), ("grid64", 2, 384), ("grid64", 3, 256), ("grid64", 5, 512), ("grid64", 16, 384),
-    ("single", 1, 256), ("single", 7, 512), ("nonsquare", 4, 384), ("wide_kernels", 6, 512),
-    ("prime_13x11x17", 16, 256)])
-def test_every_tuning_matches_oracle(G, case, cs, threads):
-    """Forced launch configurations (CTAs per model, block size) all give the
-    oracle's maps; chi2 agrees across configurations."""
-    g, p, ps = _params(case, n=3)
-    ref = oracle.evaluate_batch(ogeom(g), ps)
+@pytest.mark.parametrize("case,cs,threads,pers", [
+    ("grid64", 1, 512, 0), ("grid64", 2, 384, 1), ("grid64", 3, 256, 0), ("grid64", 5, 512, 1),
+    ("grid64", 16, 384, 0), ("single", 1, 256, 1), ("single", 7, 512, 0), ("nonsquare", 4, 384, 1),
+    ("wide_kernels", 6, 512, 0), ("prime_13x11x17", 16, 256, 1)])
+def test_every_tuning_matches_oracle(G, case, cs, threads, pers):
+    """Forced launch configurations (CTAs per model, block size, grid shape)
+    all give the oracle's maps; chi2 of all 600 models agrees with the
+    default configuration (a persistent grid loops several models per
+    cluster at this batch size)."""
+    g, p, ps = _params(case, n=600)
+    sample = [0, 1, 299, 598, 599]
+    ref = oracle.evaluate_batch(ogeom(g), ps[sample])
     obs = make_obs(g, p, seed=5)
     dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
     base = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED).cpu().numpy()
     try:
-        G.gbk_set_tuning(g, cs, threads)
+        G.gbk_set_tuning(g, cs, threads, pers)
         maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
         c = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED).cpu().numpy()
     finally:
         G.gbk_set_tuning(g, None)
-    check_maps(maps, ref, ps, "%s cs=%d nt=%d" % (case, cs, threads))
+    check_maps(maps[sample], ref, ps[sample], "%s cs=%d nt=%d pers=%d" % (case, cs, threads, pers))
     np.testing.assert_allclose(c, base, rtol=1e-5)
 
 
@@ -226,7 +229,8 @@ def test_autotune_picks_a_valid_tuning(G):
     try:
         t = G.gbk_autotune(g, torch.from_numpy(ps).cuda(), dobs, scratch)
         assert t["candidates"] >= 3 and t["ms"] > 0
-        assert G.gbk_get_tuning(g) == {"cluster_ctas": t["cluster_ctas"], "threads": t["threads"]}
+        assert G.gbk_get_tuning(g) == {"cluster_ctas": t["cluster_ctas"], "threads": t["threads"],
+                                       "persistent": t["persistent"]}
         maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
     finally:
         G.gbk_set_tuning(g, None)
