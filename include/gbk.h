@@ -147,6 +147,27 @@ GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *p
                     const gbk_obs *obs, double *chi2, float *resid, uint32_t flags,
                     void *workspace, size_t ws_bytes, void *stream);
 
+/* gbk_chi2 on the staged path for callers that cannot allocate device
+ * memory (no counterpart in the paper).  A host application whose device
+ * memory is owned and pre-planned by another framework, or a real-time
+ * caller that forbids allocation after start-up, cannot hand the staged
+ * path a workspace.  This entry point needs none: its scratch is a 32 MiB
+ * array built into the library (every GPU that loads the library holds it
+ * until the process exits).  Arguments, outputs and results are those of
+ * gbk_chi2 with flags = GBK_PATH_STAGED.  Asynchronous.
+ *  - Batches needing more than 32 MiB of scratch (see gbk_workspace_bytes
+ *    with GBK_PATH_STAGED) are rejected with GBK_EWORKSPACE before anything
+ *    is launched.
+ *  - The first call on a device looks up the array's device address; make
+ *    it before any stream capture.
+ *  - All calls share the array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the
+ *    caller.  Nothing in the array has to start at zero.
+ *  - Allocates nothing (no cudaMalloc, cudaFree or allocating library
+ *    call). */
+GBK_API gbk_status gbk_chi2_noalloc(const gbk_geom *g, int32_t n_models, const double *params,
+                                    const gbk_obs *obs, double *chi2, float *resid, void *stream);
+
 /* Eq. 11 alone, from caller-supplied FP32 maps [n_models][3][ny][nx]
  * (device).  Spaxels with m0 <= 0 count as invalid.  Asynchronous; needs
  * no workspace. */

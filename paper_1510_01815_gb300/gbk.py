@@ -60,6 +60,7 @@ def lib():
             "gbk_eval_cubes": (i32, [gp, i32, vp, vp, vp, vp, sz, vp]),
             "gbk_chi2": (i32, [gp, i32, vp, op, vp, vp, u32, vp, sz, vp]),
             "gbk_chi2_from_maps": (i32, [i32, i32, i32, vp, op, vp, vp, vp]),
+            "gbk_chi2_noalloc": (i32, [gp, i32, vp, op, vp, vp, vp]),
             "gbk_measure_alu_peak": (i32, [ctypes.POINTER(ctypes.c_double)] * 3 + [vp]),
             "gbk_autotune": (i32, [gp, i32, vp, op, vp, ctypes.POINTER(CTuning), vp]),
             "gbk_get_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
@@ -76,7 +77,7 @@ def lib():
 
 
 def exported_symbols():
-    return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps",
+    return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_last_error", "gbk_version"]
 
@@ -159,6 +160,16 @@ def gbk_chi2(geom, params, obs, chi2, resid=None, flags=PATH_AUTO, workspace=Non
                           ctypes.byref(obs.c()), _ptr(chi2, torch.float64, "chi2"),
                           _ptr(resid, torch.float32, "resid"), int(flags),
                           _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def gbk_chi2_noalloc(geom, params, obs, chi2, resid=None, stream=None):
+    """gbk_chi2 on the staged path using the library's built-in scratch
+    instead of a caller workspace (for callers that cannot allocate)."""
+    g = cgeom(geom)
+    n = params.shape[0] if params.dim() == 2 else params.numel() // NPAR
+    _check(lib().gbk_chi2_noalloc(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"),
+                                  ctypes.byref(obs.c()), _ptr(chi2, torch.float64, "chi2"),
+                                  _ptr(resid, torch.float32, "resid"), _stream(stream)))
 
 
 def gbk_chi2_from_maps(maps, obs, chi2, resid=None, stream=None):
