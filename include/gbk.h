@@ -174,6 +174,63 @@ GBK_API gbk_status gbk_chi2_noalloc(const gbk_geom *g, int32_t n_models, const d
 GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, const float *maps,
                               const gbk_obs *obs, double *chi2, float *resid, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Levenberg-Marquardt fitting (Sec. 2.3.1).  The paper drives the C mpfit
+ * library on the CPU with a forward-difference Jacobian of step ~0.1 in every
+ * parameter, box constraints, one galaxy at a time; the model evaluations run
+ * on the GPU.  Here the damped normal equations
+ *     (J^T J + lambda diag(J^T J)) delta = -J^T r
+ * are formed and solved in FP64; a step is accepted when it lowers chi2
+ * (lambda /= 10, floor 1e-12), otherwise lambda *= 10; parameters are
+ * clipped to [lo, hi].  A galaxy stops when an accepted step lowers chi2 by
+ * less than ftol (relative), when |delta| <= xtol (|p| + xtol), when lambda
+ * exceeds 1e12, or after max_iter iterations.
+ * ------------------------------------------------------------------------ */
+#define GBK_JAC_FD_FORWARD  0  /* (r(p + h e_j) - r(p)) / h, h = fd_step[j]        */
+#define GBK_JAC_FD_CENTRAL  1  /* (r(p + h e_j) - r(p - h e_j)) / 2h               */
+#define GBK_JAC_TANGENT     2  /* analytic tangent of the whole forward model      */
+
+#define GBK_LM_BATCHED  0  /* all galaxies advance together; everything on the device */
+#define GBK_LM_PLAIN    1  /* one galaxy at a time; normal equations and the solve on  */
+                           /* the host in FP64 (the paper's CPU-optimiser arrangement) */
+
+/* Per-galaxy fit status (status_out). */
+#define GBK_FIT_RUNNING    0
+#define GBK_FIT_FTOL       1  /* relative chi2 decrease below ftol              */
+#define GBK_FIT_XTOL       2  /* step below xtol                                */
+#define GBK_FIT_MAXITER    3  /* max_iter reached                               */
+#define GBK_FIT_LAMBDA     4  /* lambda above 1e12: no downhill step found      */
+#define GBK_FIT_NONFINITE  5  /* chi2 at the current parameters is not finite   */
+
+typedef struct gbk_lm_opts {
+    int32_t max_iter;          /* iterations (each: Jacobian, solve, trial)       */
+    int32_t jacobian;          /* GBK_JAC_*                                      */
+    int32_t mode;              /* GBK_LM_*                                       */
+    uint32_t free_mask;        /* bit k set: parameter k is fitted (1..10 bits)  */
+    double ftol, xtol;         /* stopping tolerances (e.g. 1e-10)               */
+    double lambda0;            /* initial damping (e.g. 1e-3)                    */
+    double fd_step[GBK_NPAR];  /* absolute finite-difference steps (e.g. 0.1)    */
+} gbk_lm_opts;
+
+/* Workspace bytes gbk_fit_lm needs (0 and last error set on bad input). */
+GBK_API size_t gbk_fit_lm_workspace_bytes(const gbk_geom *g, int32_t n_gal, const gbk_lm_opts *opts);
+
+/* Fits n_gal galaxies that share one geometry.  Synchronises `stream`.
+ *  obs        device array [n_gal] of gbk_obs (each a galaxy's maps)
+ *  lo, hi     device [n_gal][GBK_NPAR] box constraints
+ *  params     device [n_gal][GBK_NPAR]: start on entry, fit on return
+ *             (fixed parameters are left as given)
+ *  chi2_out   device [n_gal] chi2 at the returned parameters
+ *  iters_out  device [n_gal] iterations used
+ *  status_out device [n_gal] GBK_FIT_* codes
+ * The batched mode captures one iteration in a CUDA graph and replays it,
+ * reading the number of running galaxies back every 8 iterations; finished
+ * galaxies are skipped by the kernels. */
+GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *obs, const double *lo,
+                              const double *hi, double *params, const gbk_lm_opts *opts, double *chi2_out,
+                              int32_t *iters_out, int32_t *status_out, void *workspace, size_t ws_bytes,
+                              void *stream);
+
 /* Launch tuning of the fused path (no counterpart in the paper).  A tuning
  * is the number of CTAs that cooperate on one model (a thread-block cluster
  * of 1..16 CTAs sharing the model's extended rows through distributed shared

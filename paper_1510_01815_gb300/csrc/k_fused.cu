@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     double *red = reinterpret_cast<double *>(rowoff + pad4(band + 2 * R));
 
     __shared__ ModelConst mc;
+    __shared__ gbk_obs s_ob;   // observed maps of the current model's galaxy
     __shared__ float s_var_z;  // dv^2 * sum_j j^2 L_j
 
     // ---- set-up of the geometry-only tables, all in parallel, one barrier ----
@@ -221,7 +222,12 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
 
     // Persistent: the clusters of the grid take the models in turn.
     for (int model = cid; model < a.n_models; model += ncl) {
-    if (tid == 0) mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
+    const int gal = a.models_per_gal > 0 ? model / a.models_per_gal : 0;
+    if (a.skip && a.skip[gal] != 0) continue;  // same decision in every CTA of the cluster
+    if (tid == 0) {
+        mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
+        s_ob = a.obs_list ? a.obs_list[gal] : a.obs;
+    }
     __syncthreads();
 
     // ---- phase 1: Gaussian line of every extended spaxel of the band ----
@@ -398,11 +404,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         uint8_t mk = 0;
         float vo = 0.f, so = 0.f, wv = 0.f, ws = 0.f;
         if (want_obs) {
-            mk = a.obs.mask[pix];
-            vo = a.obs.v_obs[pix];
-            so = a.obs.s_obs[pix];
-            wv = a.obs.w_v[pix];
-            ws = a.obs.w_s[pix];
+            mk = s_ob.mask[pix];
+            vo = s_ob.v_obs[pix];
+            so = s_ob.s_obs[pix];
+            wv = s_ob.w_v[pix];
+            ws = s_ob.w_s[pix];
         }
         int k0 = y - (row0 - R);  // row-offset index of extended row y (tap j = 0)
         float cen = Q[rowoff[k0 + R] + x].w;
@@ -529,7 +535,7 @@ gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
     switch (args.threads) {
     case 512: return launch_variant<512, 2>(args, smem, stream);
     case 384: return launch_variant<384, 2>(args, smem, stream);
-    case 256: return launch_variant<256, 3>(args, smem, stream);
+    case 256: return launch_variant<256, 2>(args, smem, stream);
     default: return fail(GBK_EINVAL, "unsupported fused block size %d", args.threads);
     }
 }

@@ -16,6 +16,9 @@ struct FusedArgs {
     int n_models;
     const double *params;   // [n_models][GBK_NPAR]
     gbk_obs obs;            // device pointers; used when chi2 or resid is set
+    const gbk_obs *obs_list;  // optional device array, one entry per galaxy (overrides obs)
+    int models_per_gal;       // with obs_list / skip: model m belongs to galaxy m / models_per_gal
+    const int32_t *skip;      // optional device flags per galaxy: non-zero = leave its models alone
     float *maps;            // [n_models][3][ny][nx] or null
     double *chi2;           // [n_models] or null
     float *resid;           // [n_models][2][ny][nx] or null

@@ -1,0 +1,254 @@
+// k_lm.cu -- device side of batched Levenberg-Marquardt (Sec. 2.3.1):
+// finite-difference batch construction, FP64 normal equations, the damped
+// Cholesky solve and the accept/reject update, one galaxy per thread or CTA.
+#include "gbk_internal.cuh"
+#include "k_lm.h"
+
+namespace gbk {
+
+// ----------------------------------------------------------------------------
+// Finite-difference batch: slot 0 holds p; slot 1 + j holds p + h_j e_j (and
+// for central differences slot 1 + P + j holds p - h_j e_j).  A forward step
+// that would leave the box is taken backwards instead.
+__global__ void lm_build_fd_kernel(LmArgs a)
+{
+    int gal = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gal >= a.n_gal || a.done[gal]) return;
+    const double *p = a.params + (size_t)gal * GBK_NPAR;
+    const double *hi = a.hi + (size_t)gal * GBK_NPAR;
+    const double *lo = a.lo + (size_t)gal * GBK_NPAR;
+    double *pb = a.pbatch + (size_t)gal * a.m * GBK_NPAR;
+    for (int s = 0; s < a.m; ++s)
+        for (int k = 0; k < GBK_NPAR; ++k) pb[s * GBK_NPAR + k] = p[k];
+    for (int j = 0; j < a.np; ++j) {
+        int k = a.free_idx[j];
+        double h = a.fd_step[k];
+        if (a.central) {
+            pb[(1 + j) * GBK_NPAR + k] = p[k] + h;
+            pb[(1 + a.np + j) * GBK_NPAR + k] = p[k] - h;
+            a.hstep[(size_t)gal * a.np + j] = 2.0 * h;
+        } else {
+            if (p[k] + h > hi[k] && p[k] - h >= lo[k]) h = -h;
+            pb[(1 + j) * GBK_NPAR + k] = p[k] + h;
+            a.hstep[(size_t)gal * a.np + j] = h;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// J^T J and J^T r from the batch residuals; one CTA per galaxy.  Products are
+// accumulated in FP32 per thread (a few residuals each) and reduced in FP64
+// in a fixed order.
+template <int NP>
+__global__ void __launch_bounds__(256) lm_normal_fd_kernel(LmArgs a)
+{
+    const int gal = blockIdx.x;
+    if (a.done[gal]) return;
+    constexpr int NT = NP * (NP + 1) / 2;
+    const size_t n2 = (size_t)2 * a.np_pix;
+    const float *R = a.resid + (size_t)gal * a.m * n2;
+    float inv_h[NP];
+    for (int j = 0; j < NP; ++j) inv_h[j] = (float)(1.0 / a.hstep[(size_t)gal * NP + j]);
+    float jtj[NT], jtr[NP];
+    for (int t = 0; t < NT; ++t) jtj[t] = 0.f;
+    for (int j = 0; j < NP; ++j) jtr[j] = 0.f;
+    for (size_t i = threadIdx.x; i < n2; i += blockDim.x) {
+        float r0 = R[i];
+        float J[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            float rp = R[(size_t)(1 + j) * n2 + i];
+            float rm = a.central ? R[(size_t)(1 + NP + j) * n2 + i] : r0;
+            J[j] = (rp - rm) * inv_h[j];
+        }
+        int t = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            jtr[j] = fmaf(J[j], r0, jtr[j]);
+#pragma unroll
+            for (int k = j; k < NP; ++k) {
+                jtj[t] = fmaf(J[j], J[k], jtj[t]);
+                ++t;
+            }
+        }
+    }
+    __shared__ double red[8][NT + NP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < NT + NP; ++t) {
+        double v = (t < NT) ? (double)jtj[t] : (double)jtr[t - NT];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][t] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NT + NP; t += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][t];
+        if (t < NT) {
+            // upper-triangle index t -> (j, k)
+            int j = 0, rem = t;
+            while (rem >= NP - j) { rem -= NP - j; ++j; }
+            int k = j + rem;
+            a.jtj[(size_t)gal * NP * NP + j * NP + k] = s;
+            a.jtj[(size_t)gal * NP * NP + k * NP + j] = s;
+        } else {
+            a.jtr[(size_t)gal * NP + (t - NT)] = s;
+        }
+    }
+    if (threadIdx.x == 0) a.chi2_cur[gal] = a.chi2_batch[(size_t)gal * a.m];
+}
+
+// ----------------------------------------------------------------------------
+// Damped solve and trial point; one thread per galaxy.  A Cholesky failure
+// raises lambda tenfold and retries.
+template <int NP>
+__global__ void lm_solve_kernel(LmArgs a)
+{
+    int gal = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gal >= a.n_gal || a.done[gal]) return;
+    const double *JTJ = a.jtj + (size_t)gal * NP * NP;
+    const double *JTr = a.jtr + (size_t)gal * NP;
+    double lam = a.lambda[gal];
+    double L[NP][NP], d[NP];
+    bool ok = false;
+    for (int attempt = 0; attempt < 12 && !ok; ++attempt) {
+        ok = true;
+        for (int j = 0; j < NP && ok; ++j)
+            for (int k = 0; k <= j; ++k) {
+                double v = JTJ[j * NP + k];
+                if (j == k) v += lam * (JTJ[j * NP + j] > 0.0 ? JTJ[j * NP + j] : 1.0);
+                for (int q = 0; q < k; ++q) v -= L[j][q] * L[k][q];
+                if (j == k) {
+                    if (!(v > 0.0)) { ok = false; break; }
+                    L[j][j] = sqrt(v);
+                } else {
+                    L[j][k] = v / L[k][k];
+                }
+            }
+        if (!ok) lam *= 10.0;
+    }
+    a.lambda[gal] = lam;
+    double *pt = a.ptrial + (size_t)gal * GBK_NPAR;
+    const double *p = a.params + (size_t)gal * GBK_NPAR;
+    for (int k = 0; k < GBK_NPAR; ++k) pt[k] = p[k];
+    if (!ok) {  // no usable damping: the trial equals p and will be rejected
+        a.dnorm[gal] = 0.0;
+        a.pnorm[gal] = 1.0;
+        return;
+    }
+    // forward then back substitution: L L^T d = -JTr
+    double y[NP];
+    for (int j = 0; j < NP; ++j) {
+        double v = -JTr[j];
+        for (int q = 0; q < j; ++q) v -= L[j][q] * y[q];
+        y[j] = v / L[j][j];
+    }
+    for (int j = NP - 1; j >= 0; --j) {
+        double v = y[j];
+        for (int q = j + 1; q < NP; ++q) v -= L[q][j] * d[q];
+        d[j] = v / L[j][j];
+    }
+    double dn = 0.0, pn = 0.0;
+    for (int j = 0; j < NP; ++j) {
+        int k = a.free_idx[j];
+        double lo = a.lo[(size_t)gal * GBK_NPAR + k], hi = a.hi[(size_t)gal * GBK_NPAR + k];
+        double v = p[k] + d[j];
+        v = v < lo ? lo : (v > hi ? hi : v);
+        double step = v - p[k];
+        pt[k] = v;
+        dn += step * step;
+        pn += p[k] * p[k];
+    }
+    a.dnorm[gal] = sqrt(dn);
+    a.pnorm[gal] = sqrt(pn);
+}
+
+// ----------------------------------------------------------------------------
+__global__ void lm_accept_kernel(LmArgs a)
+{
+    int gal = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gal >= a.n_gal || a.done[gal]) return;
+    double cc = a.chi2_cur[gal], ct = a.chi2_trial[gal];
+    int st = GBK_FIT_RUNNING;
+    int it = a.iters[gal] + 1;
+    a.iters[gal] = it;
+    if (!isfinite(cc)) {
+        st = GBK_FIT_NONFINITE;
+    } else if (isfinite(ct) && ct <= cc && a.dnorm[gal] > 0.0) {
+        double *p = a.params + (size_t)gal * GBK_NPAR;
+        const double *pt = a.ptrial + (size_t)gal * GBK_NPAR;
+        for (int k = 0; k < GBK_NPAR; ++k) p[k] = pt[k];
+        a.chi2_best[gal] = ct;
+        a.chi2_cur[gal] = ct;
+        double lam = a.lambda[gal] * 0.1;
+        a.lambda[gal] = lam < 1e-12 ? 1e-12 : lam;
+        double rel = (cc - ct) / (cc > 1e-300 ? cc : 1e-300);
+        if (rel < a.ftol) st = GBK_FIT_FTOL;
+        else if (a.dnorm[gal] <= a.xtol * (a.pnorm[gal] + a.xtol)) st = GBK_FIT_XTOL;
+    } else {
+        a.chi2_best[gal] = cc;
+        double lam = a.lambda[gal] * 10.0;
+        a.lambda[gal] = lam;
+        if (lam > 1e12) st = GBK_FIT_LAMBDA;
+    }
+    if (st == GBK_FIT_RUNNING && it >= a.max_iter) st = GBK_FIT_MAXITER;
+    a.status[gal] = st;
+    if (st != GBK_FIT_RUNNING) a.done[gal] = 1;
+    else atomicAdd(a.n_active, 1);
+}
+
+__global__ void lm_init_kernel(LmArgs a, double lambda0)
+{
+    int gal = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gal >= a.n_gal) return;
+    a.lambda[gal] = lambda0;
+    a.iters[gal] = 0;
+    a.status[gal] = GBK_FIT_RUNNING;
+    a.done[gal] = 0;
+    a.chi2_best[gal] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// ----------------------------------------------------------------------------
+template <int NP>
+static void launch_np(const LmArgs &a, int which, cudaStream_t st)
+{
+    if (which == 0) lm_normal_fd_kernel<NP><<<a.n_gal, 256, 0, st>>>(a);
+    else lm_solve_kernel<NP><<<(a.n_gal + 63) / 64, 64, 0, st>>>(a);
+}
+
+static void dispatch_np(const LmArgs &a, int which, cudaStream_t st)
+{
+    switch (a.np) {
+    case 1: launch_np<1>(a, which, st); break;
+    case 2: launch_np<2>(a, which, st); break;
+    case 3: launch_np<3>(a, which, st); break;
+    case 4: launch_np<4>(a, which, st); break;
+    case 5: launch_np<5>(a, which, st); break;
+    case 6: launch_np<6>(a, which, st); break;
+    case 7: launch_np<7>(a, which, st); break;
+    case 8: launch_np<8>(a, which, st); break;
+    case 9: launch_np<9>(a, which, st); break;
+    default: launch_np<10>(a, which, st); break;
+    }
+}
+
+void lm_launch_init(const LmArgs &a, double lambda0, cudaStream_t st)
+{
+    lm_init_kernel<<<(a.n_gal + 127) / 128, 128, 0, st>>>(a, lambda0);
+}
+
+void lm_launch_build_fd(const LmArgs &a, cudaStream_t st)
+{
+    lm_build_fd_kernel<<<(a.n_gal + 127) / 128, 128, 0, st>>>(a);
+}
+
+void lm_launch_normal_fd(const LmArgs &a, cudaStream_t st) { dispatch_np(a, 0, st); }
+
+void lm_launch_solve(const LmArgs &a, cudaStream_t st) { dispatch_np(a, 1, st); }
+
+void lm_launch_accept(const LmArgs &a, cudaStream_t st)
+{
+    lm_accept_kernel<<<(a.n_gal + 127) / 128, 128, 0, st>>>(a);
+}
+
+}  // namespace gbk

@@ -1,0 +1,431 @@
+// lm.cu -- gbk_fit_lm: Levenberg-Marquardt over the fused forward model
+// (Sec. 2.3.1 of Bekiaris et al. 2015).
+//
+// Batched mode: every galaxy advances together.  One iteration is
+//   finite-difference batch -> fused evaluation (chi2 and residual maps of
+//   1 + P models per galaxy) -> FP64 normal equations -> damped Cholesky
+//   solve -> fused evaluation of the trial points -> accept/reject,
+// all on the device; it is captured once in a CUDA graph and replayed, and
+// the host reads the number of running galaxies every kPoll iterations.
+//
+// Plain mode: the paper's arrangement -- one galaxy at a time, the model
+// evaluations on the GPU, the residual maps copied to the host every
+// iteration, the normal equations and the solve on the CPU in FP64.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gbk_api_internal.h"
+#include "k_fused.h"
+#include "k_lm.h"
+
+namespace gbk {
+
+constexpr int kPoll = 8;
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct LmPlan {
+    int np, m, central, idx[GBK_NPAR];
+};
+
+static gbk_status lm_plan(const gbk_lm_opts *o, LmPlan *pl)
+{
+    if (!o) return fail(GBK_EINVAL, "opts is NULL");
+    if (o->max_iter < 1 || o->max_iter > 100000) return fail(GBK_EINVAL, "max_iter must be in 1..100000");
+    if (o->mode != GBK_LM_BATCHED && o->mode != GBK_LM_PLAIN) return fail(GBK_EINVAL, "unknown LM mode %d", o->mode);
+    if (o->jacobian != GBK_JAC_FD_FORWARD && o->jacobian != GBK_JAC_FD_CENTRAL && o->jacobian != GBK_JAC_TANGENT)
+        return fail(GBK_EINVAL, "unknown Jacobian kind %d", o->jacobian);
+    if (o->jacobian == GBK_JAC_TANGENT) return fail(GBK_EUNSUPPORTED, "the tangent Jacobian is not built in this library");
+    if (!(o->ftol >= 0.0) || !(o->xtol >= 0.0) || !(o->lambda0 > 0.0))
+        return fail(GBK_EINVAL, "ftol, xtol must be >= 0 and lambda0 > 0");
+    int np = 0;
+    for (int k = 0; k < GBK_NPAR; ++k)
+        if (o->free_mask & (1u << k)) {
+            if (!(o->fd_step[k] > 0.0) || !std::isfinite(o->fd_step[k]))
+                return fail(GBK_EINVAL, "fd_step[%d] must be finite and > 0", k);
+            pl->idx[np++] = k;
+        }
+    if (np == 0) return fail(GBK_EINVAL, "free_mask selects no parameter");
+    if (o->free_mask >> GBK_NPAR) return fail(GBK_EINVAL, "free_mask has bits beyond the %d parameters", GBK_NPAR);
+    pl->np = np;
+    pl->central = o->jacobian == GBK_JAC_FD_CENTRAL;
+    pl->m = 1 + (pl->central ? 2 : 1) * np;
+    return GBK_OK;
+}
+
+// Workspace layout; `ng` galaxies share one batch at a time (n_gal in the
+// batched mode, 1 in the plain mode).
+struct LmLayout {
+    size_t pbatch, resid, chi2b, hstep, jtj, jtr, ptrial, chi2t, chi2cur, chi2best, lambda, dnorm, pnorm;
+    size_t iters, status, done, nact, total;
+};
+
+static LmLayout lm_layout(const Geom &g, int ng, const LmPlan &pl)
+{
+    LmLayout L;
+    size_t o = 0, npix = (size_t)g.nx * g.ny;
+    auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
+    L.pbatch = take(sizeof(double) * ng * pl.m * GBK_NPAR);
+    L.resid = take(sizeof(float) * ng * pl.m * 2 * npix);
+    L.chi2b = take(sizeof(double) * ng * pl.m);
+    L.hstep = take(sizeof(double) * ng * pl.np);
+    L.jtj = take(sizeof(double) * ng * pl.np * pl.np);
+    L.jtr = take(sizeof(double) * ng * pl.np);
+    L.ptrial = take(sizeof(double) * ng * GBK_NPAR);
+    L.chi2t = take(sizeof(double) * ng);
+    L.chi2cur = take(sizeof(double) * ng);
+    L.chi2best = take(sizeof(double) * ng);
+    L.lambda = take(sizeof(double) * ng);
+    L.dnorm = take(sizeof(double) * ng);
+    L.pnorm = take(sizeof(double) * ng);
+    L.iters = take(sizeof(int32_t) * ng);
+    L.status = take(sizeof(int32_t) * ng);
+    L.done = take(sizeof(int32_t) * ng);
+    L.nact = take(sizeof(int32_t));
+    L.total = o;
+    return L;
+}
+
+static gbk_status fused_for(const Geom &g, int n_models, const double *params, const gbk_obs *obs_list,
+                            const gbk_obs *obs_one, int mpg, const int32_t *skip, double *chi2, float *resid,
+                            cudaStream_t st)
+{
+    FusedConfig fc;
+    if (!fused_config(g, &fc)) return fail(GBK_EUNSUPPORTED, "the fused path cannot serve this geometry");
+    FusedArgs a = {};
+    a.g = g;
+    a.n_models = n_models;
+    a.params = params;
+    if (obs_one) a.obs = *obs_one;
+    a.obs_list = obs_list;
+    a.models_per_gal = mpg;
+    a.skip = skip;
+    a.chi2 = chi2;
+    a.resid = resid;
+    a.cs = fc.cs;
+    a.band = fc.band;
+    a.threads = fc.threads;
+    a.persistent = fc.persistent;
+    return launch_fused(a, st);
+}
+
+// ----------------------------------------------------------------------------
+// Host FP64 linear algebra of the plain mode (same damping rule as the device).
+static bool host_solve(const std::vector<double> &JTJ, const std::vector<double> &JTr, int np, double &lam,
+                       std::vector<double> &d)
+{
+    std::vector<double> L((size_t)np * np);
+    bool ok = false;
+    for (int attempt = 0; attempt < 12 && !ok; ++attempt) {
+        ok = true;
+        for (int j = 0; j < np && ok; ++j)
+            for (int k = 0; k <= j; ++k) {
+                double v = JTJ[j * np + k];
+                if (j == k) v += lam * (JTJ[j * np + j] > 0.0 ? JTJ[j * np + j] : 1.0);
+                for (int q = 0; q < k; ++q) v -= L[j * np + q] * L[k * np + q];
+                if (j == k) {
+                    if (!(v > 0.0)) { ok = false; break; }
+                    L[j * np + j] = std::sqrt(v);
+                } else {
+                    L[j * np + k] = v / L[k * np + k];
+                }
+            }
+        if (!ok) lam *= 10.0;
+    }
+    if (!ok) return false;
+    std::vector<double> y(np);
+    d.assign(np, 0.0);
+    for (int j = 0; j < np; ++j) {
+        double v = -JTr[j];
+        for (int q = 0; q < j; ++q) v -= L[j * np + q] * y[q];
+        y[j] = v / L[j * np + j];
+    }
+    for (int j = np - 1; j >= 0; --j) {
+        double v = y[j];
+        for (int q = j + 1; q < np; ++q) v -= L[q * np + j] * d[q];
+        d[j] = v / L[j * np + j];
+    }
+    return true;
+}
+
+struct CudaGuard {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~CudaGuard()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+static gbk_status lm_plain(const Geom &g, int n_gal, const gbk_obs *obs, const double *lo, const double *hi,
+                           double *params, const gbk_lm_opts *o, const LmPlan &pl, double *chi2_out,
+                           int32_t *iters_out, int32_t *status_out, char *ws, cudaStream_t st)
+{
+    LmLayout L = lm_layout(g, 1, pl);
+    const size_t npix = (size_t)g.nx * g.ny, n2 = 2 * npix;
+    const int np = pl.np, m = pl.m;
+    std::vector<gbk_obs> h_obs(n_gal);
+    std::vector<double> h_lo((size_t)n_gal * GBK_NPAR), h_hi(h_lo.size()), h_p(h_lo.size());
+    std::vector<double> h_chi2(n_gal);
+    std::vector<int32_t> h_it(n_gal), h_st(n_gal);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h_obs.data(), obs, sizeof(gbk_obs) * n_gal, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(h_lo.data(), lo, sizeof(double) * h_lo.size(), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(h_hi.data(), hi, sizeof(double) * h_hi.size(), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(h_p.data(), params, sizeof(double) * h_p.size(), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return cuda_fail(e, "plain LM: reading inputs");
+    double *d_pb = (double *)(ws + L.pbatch), *d_chi2b = (double *)(ws + L.chi2b);
+    float *d_res = (float *)(ws + L.resid);
+    double *d_pt = (double *)(ws + L.ptrial), *d_ct = (double *)(ws + L.chi2t);
+    std::vector<double> pb((size_t)m * GBK_NPAR), chi2b(m), hs(np), JTJ((size_t)np * np), JTr(np), dlt;
+    std::vector<float> res((size_t)m * n2);
+    for (int gal = 0; gal < n_gal; ++gal) {
+        double *p = &h_p[(size_t)gal * GBK_NPAR];
+        const double *plo = &h_lo[(size_t)gal * GBK_NPAR], *phi = &h_hi[(size_t)gal * GBK_NPAR];
+        double lam = o->lambda0, best = NAN;
+        int it = 0, status = GBK_FIT_RUNNING;
+        while (status == GBK_FIT_RUNNING) {
+            // Jacobian batch
+            for (int s = 0; s < m; ++s) std::memcpy(&pb[(size_t)s * GBK_NPAR], p, sizeof(double) * GBK_NPAR);
+            for (int j = 0; j < np; ++j) {
+                int k = pl.idx[j];
+                double h = o->fd_step[k];
+                if (pl.central) {
+                    pb[(size_t)(1 + j) * GBK_NPAR + k] = p[k] + h;
+                    pb[(size_t)(1 + np + j) * GBK_NPAR + k] = p[k] - h;
+                    hs[j] = 2.0 * h;
+                } else {
+                    if (p[k] + h > phi[k] && p[k] - h >= plo[k]) h = -h;
+                    pb[(size_t)(1 + j) * GBK_NPAR + k] = p[k] + h;
+                    hs[j] = h;
+                }
+            }
+            if ((e = cudaMemcpyAsync(d_pb, pb.data(), sizeof(double) * pb.size(), cudaMemcpyHostToDevice, st)))
+                return cuda_fail(e, "plain LM: batch upload");
+            gbk_status s = fused_for(g, m, d_pb, nullptr, &h_obs[gal], m, nullptr, d_chi2b, d_res, st);
+            if (s) return s;
+            if ((e = cudaMemcpyAsync(res.data(), d_res, sizeof(float) * res.size(), cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaMemcpyAsync(chi2b.data(), d_chi2b, sizeof(double) * m, cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaStreamSynchronize(st)))
+                return cuda_fail(e, "plain LM: residual download");
+            double cc = chi2b[0];
+            ++it;
+            if (!std::isfinite(cc)) { status = GBK_FIT_NONFINITE; break; }
+            std::fill(JTJ.begin(), JTJ.end(), 0.0);
+            std::fill(JTr.begin(), JTr.end(), 0.0);
+            std::vector<double> J(np);
+            for (size_t i = 0; i < n2; ++i) {
+                double r0 = res[i];
+                for (int j = 0; j < np; ++j) {
+                    double rm = pl.central ? res[(size_t)(1 + np + j) * n2 + i] : r0;
+                    J[j] = ((double)res[(size_t)(1 + j) * n2 + i] - rm) / hs[j];
+                }
+                for (int j = 0; j < np; ++j) {
+                    JTr[j] += J[j] * r0;
+                    for (int k = 0; k <= j; ++k) JTJ[j * np + k] += J[j] * J[k];
+                }
+            }
+            for (int j = 0; j < np; ++j)
+                for (int k = 0; k < j; ++k) JTJ[k * np + j] = JTJ[j * np + k];
+            // damped solve and trial point
+            std::vector<double> pt(p, p + GBK_NPAR);
+            double dn = 0.0, pn = 0.0;
+            bool solved = host_solve(JTJ, JTr, np, lam, dlt);
+            if (solved)
+                for (int j = 0; j < np; ++j) {
+                    int k = pl.idx[j];
+                    double v = std::fmin(std::fmax(p[k] + dlt[j], plo[k]), phi[k]);
+                    dn += (v - p[k]) * (v - p[k]);
+                    pn += p[k] * p[k];
+                    pt[k] = v;
+                }
+            double ct = NAN;
+            if (solved && dn > 0.0) {
+                if ((e = cudaMemcpyAsync(d_pt, pt.data(), sizeof(double) * GBK_NPAR, cudaMemcpyHostToDevice, st)))
+                    return cuda_fail(e, "plain LM: trial upload");
+                s = fused_for(g, 1, d_pt, nullptr, &h_obs[gal], 1, nullptr, d_ct, nullptr, st);
+                if (s) return s;
+                if ((e = cudaMemcpyAsync(&ct, d_ct, sizeof(double), cudaMemcpyDeviceToHost, st)) ||
+                    (e = cudaStreamSynchronize(st)))
+                    return cuda_fail(e, "plain LM: trial download");
+            }
+            if (std::isfinite(ct) && ct <= cc && dn > 0.0) {
+                std::memcpy(p, pt.data(), sizeof(double) * GBK_NPAR);
+                best = ct;
+                lam = std::fmax(lam * 0.1, 1e-12);
+                double rel = (cc - ct) / std::fmax(cc, 1e-300);
+                if (rel < o->ftol) status = GBK_FIT_FTOL;
+                else if (std::sqrt(dn) <= o->xtol * (std::sqrt(pn) + o->xtol)) status = GBK_FIT_XTOL;
+            } else {
+                best = cc;
+                lam *= 10.0;
+                if (lam > 1e12) status = GBK_FIT_LAMBDA;
+            }
+            if (status == GBK_FIT_RUNNING && it >= o->max_iter) status = GBK_FIT_MAXITER;
+        }
+        h_chi2[gal] = best;
+        h_it[gal] = it;
+        h_st[gal] = status;
+    }
+    if ((e = cudaMemcpyAsync(params, h_p.data(), sizeof(double) * h_p.size(), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(chi2_out, h_chi2.data(), sizeof(double) * n_gal, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(iters_out, h_it.data(), sizeof(int32_t) * n_gal, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(status_out, h_st.data(), sizeof(int32_t) * n_gal, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return cuda_fail(e, "plain LM: writing results");
+    return ok();
+}
+
+static gbk_status lm_iteration(const Geom &g, const LmArgs &a, const gbk_obs *obs, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(a.n_active, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "LM: clearing the running count");
+    lm_launch_build_fd(a, st);
+    gbk_status s = fused_for(g, a.n_gal * a.m, a.pbatch, obs, nullptr, a.m, a.done, a.chi2_batch, a.resid, st);
+    if (s) return s;
+    lm_launch_normal_fd(a, st);
+    lm_launch_solve(a, st);
+    s = fused_for(g, a.n_gal, a.ptrial, obs, nullptr, 1, a.done, a.chi2_trial, nullptr, st);
+    if (s) return s;
+    lm_launch_accept(a, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "LM iteration launch");
+    return GBK_OK;
+}
+
+static gbk_status lm_batched(const Geom &g, int n_gal, const gbk_obs *obs, const double *lo, const double *hi,
+                             double *params, const gbk_lm_opts *o, const LmPlan &pl, double *chi2_out,
+                             int32_t *iters_out, int32_t *status_out, char *ws, cudaStream_t user)
+{
+    LmLayout L = lm_layout(g, n_gal, pl);
+    LmArgs a = {};
+    a.n_gal = n_gal;
+    a.np = pl.np;
+    for (int j = 0; j < pl.np; ++j) a.free_idx[j] = pl.idx[j];
+    for (int k = 0; k < GBK_NPAR; ++k) a.fd_step[k] = o->fd_step[k];
+    a.m = pl.m;
+    a.central = pl.central;
+    a.np_pix = g.nx * g.ny;
+    a.max_iter = o->max_iter;
+    a.ftol = o->ftol;
+    a.xtol = o->xtol;
+    a.lo = lo;
+    a.hi = hi;
+    a.params = params;
+    a.pbatch = (double *)(ws + L.pbatch);
+    a.resid = (float *)(ws + L.resid);
+    a.chi2_batch = (double *)(ws + L.chi2b);
+    a.hstep = (double *)(ws + L.hstep);
+    a.jtj = (double *)(ws + L.jtj);
+    a.jtr = (double *)(ws + L.jtr);
+    a.ptrial = (double *)(ws + L.ptrial);
+    a.chi2_trial = (double *)(ws + L.chi2t);
+    a.chi2_cur = (double *)(ws + L.chi2cur);
+    a.chi2_best = (double *)(ws + L.chi2best);
+    a.lambda = (double *)(ws + L.lambda);
+    a.dnorm = (double *)(ws + L.dnorm);
+    a.pnorm = (double *)(ws + L.pnorm);
+    a.iters = (int32_t *)(ws + L.iters);
+    a.status = (int32_t *)(ws + L.status);
+    a.done = (int32_t *)(ws + L.done);
+    a.n_active = (int32_t *)(ws + L.nact);
+
+    CudaGuard cg;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&cg.s, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&cg.e0, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&cg.e1, cudaEventDisableTiming)) || (e = cudaEventRecord(cg.e0, user)) ||
+        (e = cudaStreamWaitEvent(cg.s, cg.e0, 0)))
+        return cuda_fail(e, "LM: stream set-up");
+    cudaStream_t st = cg.s;
+    lm_launch_init(a, o->lambda0, st);
+    // The first iteration runs eagerly (it also settles the fused kernel's
+    // launch configuration); the rest replay a captured graph.
+    gbk_status s = lm_iteration(g, a, obs, st);
+    if (s) return s;
+    int32_t h_active = n_gal;
+    int done_iters = 1;
+    if (o->max_iter > 1) {
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
+            return cuda_fail(e, "LM: begin graph capture");
+        s = lm_iteration(g, a, obs, st);
+        e = cudaStreamEndCapture(st, &cg.graph);
+        if (s) return s;
+        if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");
+        if ((e = cudaGraphInstantiate(&cg.exec, cg.graph, 0))) return cuda_fail(e, "LM: graph instantiation");
+        while (done_iters < o->max_iter) {
+            int burst = kPoll;
+            if (done_iters + burst > o->max_iter) burst = o->max_iter - done_iters;
+            for (int b = 0; b < burst; ++b)
+                if ((e = cudaGraphLaunch(cg.exec, st))) return cuda_fail(e, "LM: graph launch");
+            done_iters += burst;
+            if ((e = cudaMemcpyAsync(&h_active, a.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaStreamSynchronize(st)))
+                return cuda_fail(e, "LM: polling");
+            if (h_active == 0) break;
+        }
+    }
+    if ((e = cudaMemcpyAsync(chi2_out, a.chi2_best, sizeof(double) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(iters_out, a.iters, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(status_out, a.status, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaEventRecord(cg.e1, st)) || (e = cudaStreamWaitEvent(user, cg.e1, 0)) ||
+        (e = cudaStreamSynchronize(st)))
+        return cuda_fail(e, "LM: results");
+    return ok();
+}
+
+}  // namespace gbk
+
+using namespace gbk;
+
+extern "C" {
+
+size_t gbk_fit_lm_workspace_bytes(const gbk_geom *gin, int32_t n_gal, const gbk_lm_opts *opts)
+{
+    ok();
+    Geom g;
+    if (derive_geom(gin, &g)) return 0;
+    LmPlan pl;
+    if (lm_plan(opts, &pl)) return 0;
+    if (n_gal < 0) { fail(GBK_EINVAL, "n_gal must be >= 0"); return 0; }
+    return lm_layout(g, opts->mode == GBK_LM_PLAIN ? 1 : n_gal, pl).total;
+}
+
+gbk_status gbk_fit_lm(const gbk_geom *gin, int32_t n_gal, const gbk_obs *obs, const double *lo, const double *hi,
+                      double *params, const gbk_lm_opts *opts, double *chi2_out, int32_t *iters_out,
+                      int32_t *status_out, void *workspace, size_t ws_bytes, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    LmPlan pl;
+    if ((s = lm_plan(opts, &pl))) return s;
+    if (n_gal < 0) return fail(GBK_EINVAL, "n_gal must be >= 0");
+    if (n_gal == 0) return ok();
+    if (g.u != 1) return fail(GBK_EUNSUPPORTED, "LM fitting uses the fused path, which needs upsample == 1");
+    FusedConfig fc;
+    if (!fused_config(g, &fc)) return fail(GBK_EUNSUPPORTED, "the fused path cannot serve this geometry");
+    if ((s = check_device_ptr(obs, "obs", 8)) || (s = check_device_ptr(lo, "lo", 8)) ||
+        (s = check_device_ptr(hi, "hi", 8)) || (s = check_device_ptr(params, "params", 8)) ||
+        (s = check_device_ptr(chi2_out, "chi2_out", 8)) || (s = check_device_ptr(iters_out, "iters_out", 4)) ||
+        (s = check_device_ptr(status_out, "status_out", 4)))
+        return s;
+    LmLayout L = lm_layout(g, opts->mode == GBK_LM_PLAIN ? 1 : n_gal, pl);
+    if (!workspace || ws_bytes < L.total)
+        return fail(GBK_EWORKSPACE, "gbk_fit_lm needs %zu bytes of workspace (got %zu)", L.total, ws_bytes);
+    if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (opts->mode == GBK_LM_PLAIN)
+        return lm_plain(g, n_gal, obs, lo, hi, params, opts, pl, chi2_out, iters_out, status_out, (char *)workspace, st);
+    return lm_batched(g, n_gal, obs, lo, hi, params, opts, pl, chi2_out, iters_out, status_out, (char *)workspace, st);
+}
+
+}  // extern "C"

@@ -26,7 +26,7 @@ static TuneKey key_of(const Geom &g) { return TuneKey(g.nx, g.ny, g.nz, g.R, g.R
 
 static const int kBlockSizes[3] = {512, 384, 256};
 
-static int min_blocks_per_sm(int threads) { return threads == 256 ? 3 : 2; }
+static int min_blocks_per_sm(int threads) { (void)threads; return 2; }
 
 // Shared memory per CTA that still lets min_blocks_per_sm CTAs share an SM
 // (228 KB per SM, 1 KB reserved per CTA, 2 KB kept for static shared memory).

@@ -16,6 +16,9 @@ LIB_PATH = os.path.join(HERE, "libgbk.so")
 NPAR = 10
 GBK_OK, GBK_EINVAL, GBK_ECUDA, GBK_EWORKSPACE, GBK_EUNSUPPORTED = 0, 1, 2, 3, 4
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
+JAC_FD_FORWARD, JAC_FD_CENTRAL, JAC_TANGENT = 0, 1, 2
+LM_BATCHED, LM_PLAIN = 0, 1
+FIT_STATUS = {0: "running", 1: "ftol", 2: "xtol", 3: "maxiter", 4: "lambda", 5: "nonfinite"}
 
 
 class GbkError(RuntimeError):
@@ -35,6 +38,12 @@ class CGeom(ctypes.Structure):
 class CTuning(ctypes.Structure):
     _fields_ = [("cluster_ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("ms", ctypes.c_float), ("candidates", ctypes.c_int32)]
+
+
+class CLmOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("jacobian", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("free_mask", ctypes.c_uint32), ("ftol", ctypes.c_double), ("xtol", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("fd_step", ctypes.c_double * 10)]
 
 
 class CObs(ctypes.Structure):
@@ -65,6 +74,8 @@ def lib():
             "gbk_autotune": (i32, [gp, i32, vp, op, vp, ctypes.POINTER(CTuning), vp]),
             "gbk_get_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
             "gbk_set_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
+            "gbk_fit_lm_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
+            "gbk_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz, vp]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
         }
@@ -79,6 +90,7 @@ def lib():
 def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
+            "gbk_fit_lm_workspace_bytes", "gbk_fit_lm",
             "gbk_last_error", "gbk_version"]
 
 
@@ -215,6 +227,67 @@ def gbk_set_tuning(geom, cluster_ctas=None, threads=None, persistent=0):
         return
     t = CTuning(int(cluster_ctas), int(threads), int(persistent), 0.0, 0)
     _check(lib().gbk_set_tuning(ctypes.byref(g), ctypes.byref(t)))
+
+
+def lm_opts(max_iter=200, jacobian=JAC_FD_FORWARD, mode=LM_BATCHED, free=(0, 1, 2, 3, 4, 5, 6, 7),
+            ftol=1e-10, xtol=1e-10, lambda0=1e-3, fd_step=0.1):
+    """Options of gbk_fit_lm; fd_step is a scalar or ten values."""
+    steps = [float(fd_step)] * NPAR if the_scalar(fd_step) else [float(v) for v in fd_step]
+    mask = 0
+    for k in free:
+        mask |= 1 << int(k)
+    return CLmOpts(int(max_iter), int(jacobian), int(mode), mask, float(ftol), float(xtol), float(lambda0),
+                   (ctypes.c_double * 10)(*steps))
+
+
+def the_scalar(v):
+    return not hasattr(v, "__len__")
+
+
+def obs_array(obs_list, device="cuda"):
+    """Device array of gbk_obs structs for gbk_fit_lm (keeps the tensors alive
+    through the returned tuple)."""
+    arr = (CObs * len(obs_list))(*[o.c() for o in obs_list])
+    raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(device)
+    return raw, obs_list
+
+
+def gbk_fit_lm_workspace_bytes(geom, n_gal, opts):
+    g = cgeom(geom)
+    n = lib().gbk_fit_lm_workspace_bytes(ctypes.byref(g), int(n_gal), ctypes.byref(opts))
+    err = lib().gbk_last_error().decode()
+    if n == 0 and err:
+        raise GbkError(GBK_EINVAL, err)
+    return int(n)
+
+
+def gbk_fit_lm(geom, obs_dev, lo, hi, params, opts, chi2_out, iters_out, status_out, workspace, stream=None):
+    g = cgeom(geom)
+    n = params.shape[0]
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_fit_lm(ctypes.byref(g), int(n), _ptr(obs_dev, torch.uint8, "obs"),
+                            _ptr(lo, torch.float64, "lo"), _ptr(hi, torch.float64, "hi"),
+                            _ptr(params, torch.float64, "params"), ctypes.byref(opts),
+                            _ptr(chi2_out, torch.float64, "chi2_out"), _ptr(iters_out, torch.int32, "iters_out"),
+                            _ptr(status_out, torch.int32, "status_out"), _ptr(workspace, None, "workspace"),
+                            ws_bytes, _stream(stream)))
+
+
+def fit_lm(geom, obs_list, p0, lo, hi, opts, device="cuda", stream=None):
+    """Convenience: fits len(obs_list) galaxies sharing `geom`; returns
+    (params, chi2, iters, status) as numpy arrays."""
+    import numpy as np
+    n = len(obs_list)
+    obs_dev, _keep = obs_array(obs_list, device)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(n, NPAR)).to(device)
+    p, dlo, dhi = t(p0), t(lo), t(hi)
+    chi2 = torch.empty(n, dtype=torch.float64, device=device)
+    iters = torch.empty(n, dtype=torch.int32, device=device)
+    status = torch.empty(n, dtype=torch.int32, device=device)
+    nb = gbk_fit_lm_workspace_bytes(geom, n, opts)
+    ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
+    gbk_fit_lm(geom, obs_dev, dlo, dhi, p, opts, chi2, iters, status, ws, stream)
+    return p.cpu().numpy(), chi2.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
 
 
 def gbk_version():
