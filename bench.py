@@ -4,7 +4,10 @@
 S/N < 3 masked) and 400 parameter sets per step -- the live points of one
 nested-sampling iteration, evaluated in one batched launch.
 
-A step is one pass of the whole hot path over one batch of 400 models.  The
+A step is one pass of the whole hot path over one batch of 400 models.
+The line also carries `fits`: galaxy fits/s of the plain per-galaxy
+finite-difference LM (the paper's arrangement) and of the batched forms on
+one batch of noiseless mock galaxies, with the recovery they reach.  The
 parameter sets are drawn from the uniform prior of the workload (a fresh batch
 per step, resident in HBM before timing starts); L2 is flushed (a 256 MiB
 write) between timed steps.  Prints one JSON line.
@@ -51,6 +54,8 @@ def parse():
     ap.add_argument("--impl", default="gbk", choices=["gbk", "reference"])
     ap.add_argument("--models", type=int, default=synth.FP_LIVE_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fits", action="store_true", help="skip the galaxy-fit (LM) measurement")
+    ap.add_argument("--fit-galaxies", type=int, default=256)
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
     ap.add_argument("--tuning", default=None,
                     help="CTAS,THREADS,PERSISTENT: use this fused-kernel tuning instead of autotuning")
@@ -125,6 +130,72 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
+FIT_FREE = synth.FREE_DEFAULT
+
+
+def fit_batch(gbk, torch, n, seed, device):
+    """n noiseless single-galaxy mocks (32 x 32 x 64) with truths spread over a
+    32-pixel frame, their maps from the library, and 20 %-perturbed starts
+    clipped to the fit bounds (i in 1-89 deg, Sec. 3.1)."""
+    g = synth.SINGLE_GEOM
+    rng = np.random.default_rng(seed)
+    truth = np.tile(synth.SINGLE_TRUTH, (n, 1))
+    truth[:, synth.X0] = rng.uniform(13.0, 18.0, n)
+    truth[:, synth.Y0] = rng.uniform(13.0, 18.0, n)
+    truth[:, synth.PA] = rng.uniform(0.0, 180.0, n)
+    truth[:, synth.INCL] = rng.uniform(30.0, 70.0, n)
+    truth[:, synth.VMAX] = rng.uniform(100.0, 300.0, n)
+    truth[:, synth.RT] = rng.uniform(2.0, 5.0, n)
+    truth[:, synth.SIG0] = rng.uniform(20.0, 60.0, n)
+    maps = gbk.eval_maps(g, torch.from_numpy(truth), device=device).cpu().numpy()
+    shape = (g.ny, g.nx)
+    wv, ws = synth.weights(shape, 5.0)
+    ones = np.ones(shape, np.uint8)
+    obs = [gbk.Obs.from_numpy(maps[i, 1], maps[i, 2], wv, ws, ones, device=device) for i in range(n)]
+    lo = np.tile(truth[0], (n, 1))
+    hi = lo.copy()
+    lo[:, synth.X0], hi[:, synth.X0] = 0.0, 31.0
+    lo[:, synth.Y0], hi[:, synth.Y0] = 0.0, 31.0
+    lo[:, synth.PA], hi[:, synth.PA] = -360.0, 720.0
+    lo[:, synth.INCL], hi[:, synth.INCL] = 1.0, 89.0
+    lo[:, synth.VSYS], hi[:, synth.VSYS] = -200.0, 200.0
+    lo[:, synth.VMAX], hi[:, synth.VMAX] = 1.0, 600.0
+    lo[:, synth.RT], hi[:, synth.RT] = 0.05, 30.0
+    lo[:, synth.SIG0], hi[:, synth.SIG0] = 1.0, 300.0
+    lo[:, synth.I0] = hi[:, synth.I0] = truth[:, synth.I0]
+    lo[:, synth.H] = hi[:, synth.H] = truth[:, synth.H]
+    p0 = np.array([synth.perturb(rng, truth[i], FIT_FREE, 0.2, lo[i], hi[i]) for i in range(n)])
+    return g, truth, obs, p0, lo, hi
+
+
+def run_fits(gbk, torch, n, device, forms):
+    """Galaxy fits/s of the LM forms on the same noiseless batch, with the
+    recovery the paper's thresholds ask for (|dV_t| < 2 km/s, |dPA| < 1 deg)."""
+    g, truth, obs, p0, lo, hi = fit_batch(gbk, torch, n, 4242, device)
+    out = {"workload": "%d noiseless 32x32x64 mock galaxies, 20%% perturbed starts, %d free parameters"
+                       % (n, len(FIT_FREE))}
+    for name, mode, jac in forms:
+        opts = gbk.lm_opts(max_iter=200, jacobian=jac, mode=mode, free=FIT_FREE)
+        gbk.fit_lm(g, obs[:4], p0[:4], lo[:4], hi[:4], opts, device=device)  # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        q, c, it, st = gbk.fit_lm(g, obs, p0, lo, hi, opts, device=device)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        dv = np.abs(q[:, synth.VMAX] - truth[:, synth.VMAX])
+        dpa = np.abs((q[:, synth.PA] - truth[:, synth.PA] + 180.0) % 360.0 - 180.0)
+        out[name] = {"fits_per_s": n / dt, "seconds": dt, "p50_iters": float(np.percentile(it, 50)),
+                     "p99_iters": float(np.percentile(it, 99)),
+                     "recovered_frac": float(np.mean((dv < 2.0) & (dpa < 1.0))),
+                     "median_dvmax": float(np.median(dv)), "median_dpa": float(np.median(dpa)),
+                     "median_chi2": float(np.median(c))}
+    if "plain_fd" in out:
+        for name in out:
+            if isinstance(out[name], dict) and name != "plain_fd":
+                out[name]["speedup_vs_plain"] = out[name]["fits_per_s"] / out["plain_fd"]["fits_per_s"]
+    return out
+
+
 def make_galaxy(gbk, torch, g, seed, device):
     """One synthetic Fabry-Perot galaxy: true parameters from the prior, maps
     from the library at those parameters, seeded noise (5 km/s on v,
@@ -335,6 +406,10 @@ def run_gbk(args):
     out["e2e"]["matches_device_run"] = bool(ok)
     out["gpu_launches_e2e"] = K
 
+    if not args.no_fits:
+        out["fits"] = run_fits(gbk, torch, args.fit_galaxies, dev,
+                               [("plain_fd", gbk.LM_PLAIN, gbk.JAC_FD_FORWARD),
+                                ("batched_fd", gbk.LM_BATCHED, gbk.JAC_FD_FORWARD)])
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, obs_np, n, 2015)
     if rank == 0:

@@ -174,6 +174,25 @@ GBK_API gbk_status gbk_chi2_noalloc(const gbk_geom *g, int32_t n_models, const d
 GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, const float *maps,
                               const gbk_obs *obs, double *chi2, float *resid, void *stream);
 
+/* Analytic Jacobian of the weighted residual maps of gbk_chi2 (forward-mode
+ * derivatives through Eqs. 1-11; no counterpart code in the paper, which
+ * used finite differences).  Asynchronous.  For each model:
+ *   J[k] = d(resid)/d(param k) for all GBK_NPAR parameters, written to jac
+ *          (device, [n_models][GBK_NPAR][2][ny][nx] FP32) when jac != NULL;
+ *   jtj  = J_f^T J_f, device [n_models][nf][nf] FP64, and
+ *   jtv  = J_f^T v, device [n_models][nf] FP64, where J_f keeps the nf
+ *          parameters selected by free_mask (in parameter order) and v is
+ *          `cot` (device [n_models][2][ny][nx]) or, when cot == NULL, the
+ *          residuals themselves (then jtv is the gradient of chi2 / 2);
+ *   chi2 = sum of squared residuals, device [n_models] (may be NULL).
+ * Masked and invalid spaxels have zero rows.  At the disc centre (r = 0)
+ * the brightness derivative with respect to the centre and the angles uses
+ * the one-sided value 0.  Serves geometries whose per-CTA tables fit in
+ * shared memory (EUNSUPPORTED otherwise, e.g. above about 64 x 64 spaxels). */
+GBK_API gbk_status gbk_jacobian(const gbk_geom *g, int32_t n_models, const double *params,
+                                const gbk_obs *obs, uint32_t free_mask, const float *cot, double *jtj,
+                                double *jtv, double *chi2, float *jac, void *stream);
+
 /* ------------------------------------------------------------------------
  * Levenberg-Marquardt fitting (Sec. 2.3.1).  The paper drives the C mpfit
  * library on the CPU with a forward-difference Jacobian of step ~0.1 in every
@@ -189,6 +208,7 @@ GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, 
 #define GBK_JAC_FD_FORWARD  0  /* (r(p + h e_j) - r(p)) / h, h = fd_step[j]        */
 #define GBK_JAC_FD_CENTRAL  1  /* (r(p + h e_j) - r(p - h e_j)) / 2h               */
 #define GBK_JAC_TANGENT     2  /* analytic tangent of the whole forward model      */
+                               /* (gbk_jacobian's kernel; 1 evaluation-like pass) */
 
 #define GBK_LM_BATCHED  0  /* all galaxies advance together; everything on the device */
 #define GBK_LM_PLAIN    1  /* one galaxy at a time; normal equations and the solve on  */

@@ -1,0 +1,42 @@
+// jacobian.cu -- gbk_jacobian: host side of the analytic Jacobian kernel.
+#include "gbk_api_internal.h"
+#include "k_tangent.h"
+
+using namespace gbk;
+
+extern "C" gbk_status gbk_jacobian(const gbk_geom *gin, int32_t n_models, const double *params,
+                                   const gbk_obs *obs, uint32_t free_mask, const float *cot, double *jtj,
+                                   double *jtv, double *chi2, float *jac, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    if (n_models < 0) return fail(GBK_EINVAL, "n_models must be >= 0");
+    if (free_mask == 0 || (free_mask >> GBK_NPAR)) return fail(GBK_EINVAL, "free_mask must select 1..10 parameters");
+    if (g.u != 1) return fail(GBK_EUNSUPPORTED, "the Jacobian kernel needs upsample == 1");
+    TangentArgs a = {};
+    if (!tangent_config(g, &a.cs, &a.band))
+        return fail(GBK_EUNSUPPORTED, "geometry %d x %d too large for the Jacobian kernel", g.nx, g.ny);
+    if (n_models == 0) return ok();
+    if ((s = check_device_ptr(params, "params", 8))) return s;
+    if ((s = check_obs(obs))) return s;
+    if (cot && (s = check_device_ptr(cot, "cot", 4))) return s;
+    if (jtj && (s = check_device_ptr(jtj, "jtj", 8))) return s;
+    if (jtv && (s = check_device_ptr(jtv, "jtv", 8))) return s;
+    if (chi2 && (s = check_device_ptr(chi2, "chi2", 8))) return s;
+    if (jac && (s = check_device_ptr(jac, "jac", 4))) return s;
+    a.g = g;
+    a.n_models = n_models;
+    a.params = params;
+    a.obs = *obs;
+    a.np = 0;
+    for (int k = 0; k < GBK_NPAR; ++k)
+        if (free_mask & (1u << k)) a.free_idx[a.np++] = k;
+    a.cot = cot;
+    a.jtj = jtj;
+    a.jtv = jtv;
+    a.chi2 = chi2;
+    a.jac = jac;
+    if ((s = launch_tangent(a, (cudaStream_t)stream))) return s;
+    return ok();
+}

@@ -1,0 +1,433 @@
+// k_tangent.cu -- analytic Jacobian of the residual maps (forward-mode
+// derivatives through the whole forward model of Sec. 2.1-2.2.6).
+//
+// For a spaxel with line centre v, brightness I and line width sigma the
+// model cube is c_e = A g_e, A = I dv / (sigma sqrt(2 pi)),
+// g_e = exp(-d_e^2 / 2 sigma^2), d_e = v_e - v.  For any parameter theta
+//   dc_e/dtheta = c_e [ dlnA/dtheta + d_e/sigma^2 dv/dtheta + d_e^2/sigma^3 dsigma/dtheta ],
+// so the derivatives of the spaxel's moment sums q_m = sum_e c_e T_m(e) (the
+// z-folded weights of the fused kernel, taken about a fixed centre a) are
+//   dq_m = A [ dlnA B_0m + dv/sigma^2 B_1m + dsigma/sigma^3 B_2m ],
+//   B_km = sum_e g_e d_e^k T_m(e),  k, m = 0..2.
+// The channel loop accumulates the twelve sums needed for the nine B_km
+// (powers 0..4 of d against the LSF tap moments G0, H1, H2 of each channel);
+// the geometry supplies dv, dlnI and dsigma per spaxel by the chain rule
+// through Eqs. 1-8.  The PSF passes are linear, so the derivative triplets go
+// through the same re-centred x and y passes as the values; the moments'
+// quotient rule then gives dm1, dm2 and the Jacobian rows
+// J_v = w_v dm1, J_s = w_s dm2 of the residual maps.  Per model the kernel
+// reduces J^T J and J^T v (v = the residuals, or a caller's cotangent maps)
+// in a fixed order and can also write J itself.
+//
+// Where a parameter's derivative is not defined -- the brightness cusp at
+// r = 0 -- the one-sided value 0 is used for dr.  The centre a is held fixed
+// (the moments do not depend on it).  Sums are taken about the line centre
+// and shifted to a afterwards; that is exact algebra, and the small FP32
+// cancellation it allows for lines far outside the band only affects the
+// Jacobian (chi2 values for LM decisions come from the fused kernel).
+#include <cooperative_groups.h>
+
+#include "gbk_api_internal.h"
+#include "gbk_internal.cuh"
+#include "k_tangent.h"
+
+namespace cg = cooperative_groups;
+
+namespace gbk {
+
+constexpr int NPT = GBK_NPAR;        // derivatives carried for every parameter
+constexpr int kRec = 4 + 3 * NPT;    // floats per spaxel record: a, q0..q2, dq (3 per parameter)
+constexpr int kRec4 = (kRec + 3) / 4;
+constexpr int kJRow = NPT + 2;       // Jacobian row in shared memory: J[10], r, v
+
+__host__ __device__ inline int tg_band_begin(int rank, int ey, int cs) { return (int)(((long)rank * ey) / cs); }
+__device__ inline int tg_band_owner(int er, int ey, int cs) { return (int)((((long)er + 1) * cs - 1) / ey); }
+
+__host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads)
+{
+    size_t q = (size_t)band * g.ex, h = (size_t)2 * g.R * g.nx;
+    size_t b = (q > h ? q : h) * kRec4 * 16;              // Q records / halo rows
+    b += (size_t)band * g.nx * kRec4 * 16;                // P records
+    b += (size_t)g.ez * 16;                               // per-channel (G0, H1, H2, -)
+    b += (size_t)((2 * g.R + 1 + 3) & ~3) * 4;            // PSF taps
+    b += (size_t)((band + 2 * g.R + 3) & ~3) * 4;         // row offsets
+    b += (size_t)2 * threads * kJRow * 4;                 // Jacobian rows of one chunk
+    b += 128 * 8;                                          // reductions
+    return b;
+}
+
+size_t tangent_smem_bytes_host(const Geom &g, int band, int threads) { return tangent_smem_bytes(g, band, threads); }
+
+// Re-centres the record at rec (centre rec.w... stored as r[0] = a) to centre c
+// and accumulates it with weight w into acc[0..kRec).
+__device__ __forceinline__ void accum_rec(const float *rec, float c, float w, float *acc)
+{
+    float D = rec[0] - c;
+#pragma unroll
+    for (int t = 0; t <= NPT; ++t) {  // triplet 0: values; 1..NPT: derivatives
+        const float x0 = rec[1 + 3 * t], x1 = rec[2 + 3 * t], x2 = rec[3 + 3 * t];
+        float t0 = w * x0, t1 = w * x1;
+        acc[1 + 3 * t] += t0;
+        acc[2 + 3 * t] += fmaf(D, t0, t1);
+        acc[3 + 3 * t] += fmaf(w, x2, D * fmaf(D, t0, 2.f * t1));
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const Geom &g = a.g;
+    const int cs = a.cs;
+    const int rank = (int)cluster.block_rank();
+    const int model = blockIdx.x / cs;
+    const int band = a.band;
+    const int row0 = tg_band_begin(rank, g.ey, cs), row1 = tg_band_begin(rank + 1, g.ey, cs);
+    const int nrows = row1 - row0;
+    const int R = g.R;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int gal = a.models_per_gal > 0 ? model / a.models_per_gal : 0;
+    if (a.skip && a.skip[gal] != 0) return;  // the whole cluster returns together
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    size_t qn = (size_t)band * g.ex, hn = (size_t)2 * R * g.nx;
+    float *Q = reinterpret_cast<float *>(smem);                        // records, stride kRec4*4
+    float *P = Q + (qn > hn ? qn : hn) * kRec4 * 4;
+    float4 *ztab = reinterpret_cast<float4 *>(P + (size_t)band * g.nx * kRec4 * 4);
+    float *wxy = reinterpret_cast<float *>(ztab + g.ez);
+    int *rowoff = reinterpret_cast<int *>(wxy + ((2 * R + 1 + 3) & ~3));
+    float *jrows = reinterpret_cast<float *>(rowoff + ((band + 2 * R + 3) & ~3));
+    double *red = reinterpret_cast<double *>(jrows + (size_t)2 * nthr * kJRow);
+    constexpr int RS = kRec4 * 4;  // record stride in floats
+
+    __shared__ ModelConst mc;
+    __shared__ gbk_obs s_ob;
+    __shared__ float s_norm_xy, s_norm_z;
+    __shared__ double s_free_part[80];
+
+    if (tid == 0) {
+        mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
+        s_ob = a.obs_list ? a.obs_list[gal] : a.obs;
+        float sx = 0.f, sz = 0.f;
+        for (int j = -R; j <= R; ++j) sx += (R == 0) ? 1.f : gauss_tap(j, g.sig_xy);
+        for (int j = -g.Rz; j <= g.Rz; ++j) sz += (g.Rz == 0) ? 1.f : gauss_tap(j, g.sig_z);
+        s_norm_xy = 1.f / sx;
+        s_norm_z = 1.f / sz;
+    }
+    __syncthreads();
+    for (int j = tid; j <= 2 * R; j += nthr) wxy[j] = ((R == 0) ? 1.f : gauss_tap(j - R, g.sig_xy)) * s_norm_xy;
+    for (int e = tid; e < g.ez; e += nthr) {
+        int kd = e - g.Rz;
+        int jlo = max(0, kd - g.Rz) - kd, jhi = min(g.nz - 1, kd + g.Rz) - kd;
+        float G0 = 0.f, H1 = 0.f, H2 = 0.f;
+        for (int j = jlo; j <= jhi; ++j) {
+            float w = ((g.Rz == 0) ? 1.f : gauss_tap(j, g.sig_z)) * s_norm_z;
+            G0 += w;
+            H1 = fmaf(w, (float)j, H1);
+            H2 = fmaf(w, (float)(j * j), H2);
+        }
+        ztab[e] = make_float4(G0, g.dv * H1, g.dv * g.dv * H2, 0.f);
+    }
+    for (int k = tid; k < nrows + 2 * R; k += nthr) {
+        int er = row0 - R + k;
+        int off;
+        if (er < row0) off = k * g.nx;
+        else if (er < row1) off = (int)((P - Q) / RS) + (er - row0) * g.nx;
+        else off = (R + (er - row1)) * g.nx;
+        rowoff[k] = off;  // in records
+    }
+    __syncthreads();
+    const ModelConst &c = mc;
+
+    // ---- phase 1: records (a, q, dq) of the band's extended spaxels ----
+    const float kdeg = 0.017453292519943295f;  // radians per degree
+    const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;
+    const float v_lo = g.vc - 0.5f * (float)(g.nz - 1) * g.dv, v_hi = g.vc + 0.5f * (float)(g.nz - 1) * g.dv;
+    const float sig = c.sigma, isig2 = 1.f / (sig * sig), isig3 = isig2 / sig;
+    const float s0p = (float)a.params[(size_t)model * GBK_NPAR + GBK_SIG0];
+    const float dsig_ds0 = (g.lsf_mode == 1) ? s0p / sig : 1.f;
+    const float vmax = (float)a.params[(size_t)model * GBK_NPAR + GBK_VMAX];
+    const float rtv = (float)a.params[(size_t)model * GBK_NPAR + GBK_RT];
+    const float hv = (float)a.params[(size_t)model * GBK_NPAR + GBK_H];
+    const float ci = 1.f / c.inv_cos_i;
+    for (int idx = tid; idx < nrows * g.ex; idx += nthr) {
+        int rr = idx / g.ex, xe_i = idx - rr * g.ex;
+        float x = (float)(xe_i - R), y = (float)(row0 + rr - R);
+        // geometry and its derivatives (Eqs. 1-8)
+        float dx = x - c.x0, dy = y - c.y0;
+        float xe = -dx * c.sin_pa + dy * c.cos_pa;
+        float ye = -dx * c.cos_pa - dy * c.sin_pa;
+        float yd = ye * c.inv_cos_i;
+        float r = sqrtf(xe * xe + yd * yd);
+        float u = r * c.inv_rt;
+        float at = atanf(u);
+        float fv = (r > 0.f) ? 0.63661977f * at / r : 0.63661977f * c.inv_rt;  // f / Vmax
+        float f = vmax * fv;
+        float w = xe * c.sin_i;
+        float vl = c.vsys + f * w;
+        float br = c.i0 * expf(-r * c.inv_h);
+        float fp;  // df/dr
+        if (u < 0.1f) fp = vmax * 0.63661977f * c.inv_rt * c.inv_rt * u * (-2.f / 3.f + 0.8f * u * u);
+        else fp = vmax * 0.63661977f * (u / (1.f + u * u) - at) / (r * r);
+        float rx = 0.f, ry = 0.f, ri = 0.f;
+        if (r > 0.f) {
+            rx = xe / r;
+            ry = ye * c.inv_cos_i * c.inv_cos_i / r;
+            ri = yd * yd * (c.sin_i * c.inv_cos_i) / r * kdeg;
+        }
+        float dxe[3] = {c.sin_pa, -c.cos_pa, ye * kdeg};   // d x_e / d(x0, y0, PA)
+        float dye[3] = {c.cos_pa, c.sin_pa, -xe * kdeg};   // d y_e / d(x0, y0, PA)
+        float dv[NPT], dlnA[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) { dv[k] = 0.f; dlnA[k] = 0.f; }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float drk = rx * dxe[k] + ry * dye[k];
+            dv[k] = f * c.sin_i * dxe[k] + fp * drk * w;
+            dlnA[k] = -drk * c.inv_h;
+        }
+        dv[GBK_INCL] = kdeg * f * xe * ci + fp * ri * w;
+        dlnA[GBK_INCL] = -ri * c.inv_h;
+        dv[GBK_VSYS] = 1.f;
+        dv[GBK_VMAX] = fv * w;
+        dv[GBK_RT] = -0.63661977f * vmax / (rtv * rtv + r * r) * w;
+        dlnA[GBK_SIG0] = -dsig_ds0 / sig;
+        dlnA[GBK_I0] = 1.f / c.i0;
+        dlnA[GBK_H] = r / (hv * hv);
+        // channel sums: S_k^G = sum g d^k G0 (k <= 4), S_k^1 = sum g d^k H1 (k <= 3), S_k^2 = sum g d^k H2 (k <= 2)
+        float a_c = fminf(fmaxf(vl, v_lo), v_hi);
+        float sh = vl - a_c;
+        float base = vz0 - vl;
+        float SG[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, S1[4] = {0.f, 0.f, 0.f, 0.f}, S2[3] = {0.f, 0.f, 0.f};
+        float fe = 0.f;
+        for (int e = 0; e < g.ez; ++e, fe += 1.f) {
+            float d = fmaf(fe, g.dv, base);
+            float t = c.alpha * d;
+            float gg = ex2_approx(-t * t);
+            float4 T = ztab[e];
+            float g1 = gg * d, g2 = g1 * d, g3 = g2 * d, g4 = g3 * d;
+            SG[0] = fmaf(gg, T.x, SG[0]); SG[1] = fmaf(g1, T.x, SG[1]); SG[2] = fmaf(g2, T.x, SG[2]);
+            SG[3] = fmaf(g3, T.x, SG[3]); SG[4] = fmaf(g4, T.x, SG[4]);
+            S1[0] = fmaf(gg, T.y, S1[0]); S1[1] = fmaf(g1, T.y, S1[1]); S1[2] = fmaf(g2, T.y, S1[2]);
+            S1[3] = fmaf(g3, T.y, S1[3]);
+            S2[0] = fmaf(gg, T.z, S2[0]); S2[1] = fmaf(g1, T.z, S2[1]); S2[2] = fmaf(g2, T.z, S2[2]);
+        }
+        // B_km (k: power of d from the derivative; m: moment weight about a)
+        float B[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            B[k][0] = SG[k];
+            B[k][1] = SG[k + 1] + sh * SG[k] + S1[k];
+            B[k][2] = SG[k + 2] + 2.f * sh * SG[k + 1] + 2.f * S1[k + 1] + sh * sh * SG[k] + 2.f * sh * S1[k] + S2[k];
+        }
+        float A = c.amp * br;
+        float *rec = Q + (size_t)idx * RS;
+        rec[0] = a_c;
+        rec[1] = A * B[0][0];
+        rec[2] = A * B[0][1];
+        rec[3] = A * B[0][2];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            float ds = (k == GBK_SIG0) ? dsig_ds0 : 0.f;
+            float cA = dlnA[k], cv = dv[k] * isig2, cs3 = ds * isig3;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) rec[4 + 3 * k + m] = A * (cA * B[0][m] + cv * B[1][m] + cs3 * B[2][m]);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: x pass on every triplet ----
+    for (int idx = tid; idx < nrows * g.nx; idx += nthr) {
+        int rr = idx / g.nx, xx = idx - rr * g.nx;
+        const float *row = Q + ((size_t)rr * g.ex + xx) * RS;
+        float cen = row[(size_t)R * RS];
+        float acc[RS];
+#pragma unroll
+        for (int t = 0; t < RS; ++t) acc[t] = 0.f;
+        for (int j = 0; j <= 2 * R; ++j) accum_rec(row + (size_t)j * RS, cen, wxy[j], acc);
+        float *out = P + (size_t)idx * RS;
+        out[0] = cen;
+#pragma unroll
+        for (int t = 1; t < kRec; ++t) out[t] = acc[t];
+    }
+    cluster.sync();
+
+    // ---- phase 3a: halo records from the neighbours ----
+    for (int k = 0; k < 2 * R; ++k) {
+        int er = (k < R) ? row0 - R + k : row1 + (k - R);
+        if (er < 0 || er >= g.ey) continue;
+        int owner = tg_band_owner(er, g.ey, cs);
+        const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(P, owner)) +
+                            (size_t)(er - tg_band_begin(owner, g.ey, cs)) * g.nx * kRec4;
+        float4 *dst = reinterpret_cast<float4 *>(Q) + (size_t)k * g.nx * kRec4;
+        for (int i = tid; i < g.nx * kRec4; i += nthr) dst[i] = src[i];
+    }
+    __syncthreads();
+
+    // ---- phase 3b: y pass, moments, Jacobian rows, chunked J^T J ----
+    const int ylo = max(row0 - R, 0), yhi = min(row1 - R, g.ny);
+    const int nout = max(0, yhi - ylo) * g.nx;
+    const size_t np = (size_t)g.nx * g.ny;
+    const float thr = kInvalidFraction * c.i0;
+    const int nf = a.np;
+    const int nent = nf * (nf + 1) / 2 + nf + 1;  // J^T J upper triangle, J^T v, sum r^2
+    double part = 0.0;                             // this thread's entry (tid < nent)
+    for (int base = 0; base < nout; base += nthr) {
+        int idx = base + tid;
+        float jv[NPT], js[NPT], rv = 0.f, rs = 0.f, cv_ = 0.f, cs_ = 0.f;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) { jv[k] = 0.f; js[k] = 0.f; }
+        if (idx < nout) {
+            int yy = idx / g.nx, xx = idx - yy * g.nx;
+            int y = ylo + yy;
+            size_t pix = (size_t)y * g.nx + xx;
+            int k0 = y - (row0 - R);
+            float cen = Q[((size_t)rowoff[k0 + R] + xx) * RS];
+            float acc[RS];
+#pragma unroll
+            for (int t = 0; t < RS; ++t) acc[t] = 0.f;
+            for (int j = 0; j <= 2 * R; ++j) accum_rec(Q + ((size_t)rowoff[k0 + j] + xx) * RS, cen, wxy[j], acc);
+            float S0 = acc[1], S1v = acc[2], S2v = acc[3];
+            bool use = c.valid && S0 > thr && s_ob.mask[pix] != 0;
+            if (use) {
+                float inv = 1.f / S0;
+                float mu = S1v * inv;
+                float var = fmaxf(fmaf(-mu, mu, S2v * inv), 0.f);
+                float m2 = sqrtf(var);
+                float wv = s_ob.w_v[pix], ws = s_ob.w_s[pix];
+                rv = wv * (cen + mu - s_ob.v_obs[pix]);
+                rs = ws * (m2 - s_ob.s_obs[pix]);
+                float inv2m2 = m2 > 0.f ? 0.5f / m2 : 0.f;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    float d0 = acc[4 + 3 * k], d1 = acc[5 + 3 * k], d2 = acc[6 + 3 * k];
+                    float dmu = (d1 - mu * d0) * inv;
+                    float dvar = (d2 - S2v * inv * d0) * inv - 2.f * mu * dmu;
+                    jv[k] = wv * dmu;
+                    js[k] = ws * dvar * inv2m2;
+                }
+                if (a.cot) {
+                    cv_ = a.cot[(size_t)model * 2 * np + pix];
+                    cs_ = a.cot[(size_t)model * 2 * np + np + pix];
+                } else {
+                    cv_ = rv;
+                    cs_ = rs;
+                }
+            }
+            if (a.jac) {
+                float *J = a.jac + (size_t)model * NPT * 2 * np;
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    J[((size_t)k * 2) * np + pix] = jv[k];
+                    J[((size_t)k * 2 + 1) * np + pix] = js[k];
+                }
+            }
+        }
+        // rows of this chunk to shared memory
+        float *r0p = jrows + (size_t)(2 * tid) * kJRow, *r1p = r0p + kJRow;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) { r0p[k] = jv[k]; r1p[k] = js[k]; }
+        r0p[NPT] = rv; r0p[NPT + 1] = cv_;
+        r1p[NPT] = rs; r1p[NPT + 1] = cs_;
+        __syncthreads();
+        if (tid < nent) {
+            // entry tid: (j, k) of the upper triangle, then J^T v, then sum r^2
+            int j = -1, k = -1, t = tid, kind = 0;
+            int ntri = nf * (nf + 1) / 2;
+            if (t < ntri) {
+                j = 0;
+                while (t >= nf - j) { t -= nf - j; ++j; }
+                k = j + t;
+                j = a.free_idx[j];
+                k = a.free_idx[k];
+            } else if (t < ntri + nf) {
+                kind = 1;
+                j = a.free_idx[t - ntri];
+            } else {
+                kind = 2;
+            }
+            float s = 0.f;
+            int rows = 2 * min(nthr, nout - base);
+            for (int q = 0; q < rows; ++q) {
+                const float *row = jrows + (size_t)q * kJRow;
+                s = (kind == 0) ? fmaf(row[j], row[k], s)
+                                : (kind == 1 ? fmaf(row[j], row[NPT + 1], s) : fmaf(row[NPT], row[NPT], s));
+            }
+            part += (double)s;
+        }
+        __syncthreads();
+    }
+    if (tid < nent) s_free_part[tid] = part;
+    cluster.sync();
+    if (rank == 0 && tid < nent) {
+        double s = 0.0;
+        for (int q = 0; q < cs; ++q) {
+            const double *p = (q == 0) ? s_free_part : cluster.map_shared_rank(s_free_part, q);
+            s += p[tid];
+        }
+        if (!c.valid) s = (double)__int_as_float(0x7fc00000);
+        int ntri = nf * (nf + 1) / 2;
+        if (tid < ntri) {
+            int j = 0, t = tid;
+            while (t >= nf - j) { t -= nf - j; ++j; }
+            int k = j + t;
+            if (a.jtj) {
+                a.jtj[(size_t)model * nf * nf + j * nf + k] = s;
+                a.jtj[(size_t)model * nf * nf + k * nf + j] = s;
+            }
+        } else if (tid < ntri + nf) {
+            if (a.jtv) a.jtv[(size_t)model * nf + (tid - ntri)] = s;
+        } else {
+            if (a.chi2) a.chi2[model] = s;
+        }
+    }
+    cluster.sync();
+}
+
+gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
+{
+    size_t smem = tangent_smem_bytes(args.g, args.band, kTangentThreads);
+    static size_t configured = 0;
+    static bool cl = false;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(tangent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "tangent kernel: setting dynamic shared memory");
+        configured = smem;
+    }
+    if (!cl) {
+        cudaError_t e = cudaFuncSetAttribute(tangent_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return cuda_fail(e, "tangent kernel: allowing 16-CTA clusters");
+        cl = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(args.n_models * args.cs), 1, 1);
+    cfg.blockDim = dim3(kTangentThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)args.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, tangent_kernel, args);
+    if (e != cudaSuccess) return cuda_fail(e, "tangent kernel launch");
+    return GBK_OK;
+}
+
+bool tangent_config(const Geom &g, int *cs, int *band)
+{
+    if (g.u != 1) return false;
+    for (int c = 1; c <= 16; ++c) {
+        int b = (g.ey + c - 1) / c;
+        if (c > g.ey) break;
+        if (tangent_smem_bytes(g, b, kTangentThreads) <= (size_t)200 * 1024) {
+            *cs = c;
+            *band = b;
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace gbk

@@ -1,0 +1,32 @@
+// k_tangent.h -- launcher of the analytic Jacobian kernel.
+#pragma once
+
+#include "gbk_internal.cuh"
+
+namespace gbk {
+
+constexpr int kTangentThreads = 256;
+
+struct TangentArgs {
+    Geom g;                  // u must be 1
+    int n_models;
+    const double *params;    // [n_models][GBK_NPAR]
+    gbk_obs obs;             // single galaxy (used when obs_list is null)
+    const gbk_obs *obs_list; // optional, one per galaxy
+    int models_per_gal;      // model m belongs to galaxy m / models_per_gal (0: galaxy 0)
+    const int32_t *skip;     // optional per-galaxy skip flags
+    int np;                  // free parameters
+    int free_idx[GBK_NPAR];  // their indices
+    const float *cot;        // optional cotangent maps [n_models][2][ny][nx] (default: the residuals)
+    double *jtj;             // [n_models][np][np] or null
+    double *jtv;             // [n_models][np] or null: J^T (cot or residuals)
+    double *chi2;            // [n_models] or null: sum of squared residuals
+    float *jac;              // [n_models][GBK_NPAR][2][ny][nx] or null
+    int cs, band;            // cluster size, most extended rows per CTA
+};
+
+size_t tangent_smem_bytes_host(const Geom &g, int band, int threads);
+bool tangent_config(const Geom &g, int *cs, int *band);
+gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream);
+
+}  // namespace gbk

@@ -2,9 +2,12 @@
 // (Sec. 2.3.1 of Bekiaris et al. 2015).
 //
 // Batched mode: every galaxy advances together.  One iteration is
-//   finite-difference batch -> fused evaluation (chi2 and residual maps of
-//   1 + P models per galaxy) -> FP64 normal equations -> damped Cholesky
-//   solve -> fused evaluation of the trial points -> accept/reject,
+//   Jacobian -> FP64 normal equations -> damped Cholesky solve -> fused
+//   evaluation of the trial points -> accept/reject,
+// where the Jacobian is either a finite-difference batch (fused evaluation
+// of chi2 and residual maps of 1 + P or 1 + 2P models per galaxy, then a
+// reduction kernel) or the analytic tangent kernel, which reduces J^T J and
+// J^T r directly;
 // all on the device; it is captured once in a CUDA graph and replayed, and
 // the host reads the number of running galaxies every kPoll iterations.
 //
@@ -18,6 +21,7 @@
 #include "gbk_api_internal.h"
 #include "k_fused.h"
 #include "k_lm.h"
+#include "k_tangent.h"
 
 namespace gbk {
 
@@ -26,7 +30,7 @@ constexpr int kPoll = 8;
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct LmPlan {
-    int np, m, central, idx[GBK_NPAR];
+    int np, m, central, tangent, idx[GBK_NPAR];
 };
 
 static gbk_status lm_plan(const gbk_lm_opts *o, LmPlan *pl)
@@ -36,7 +40,6 @@ static gbk_status lm_plan(const gbk_lm_opts *o, LmPlan *pl)
     if (o->mode != GBK_LM_BATCHED && o->mode != GBK_LM_PLAIN) return fail(GBK_EINVAL, "unknown LM mode %d", o->mode);
     if (o->jacobian != GBK_JAC_FD_FORWARD && o->jacobian != GBK_JAC_FD_CENTRAL && o->jacobian != GBK_JAC_TANGENT)
         return fail(GBK_EINVAL, "unknown Jacobian kind %d", o->jacobian);
-    if (o->jacobian == GBK_JAC_TANGENT) return fail(GBK_EUNSUPPORTED, "the tangent Jacobian is not built in this library");
     if (!(o->ftol >= 0.0) || !(o->xtol >= 0.0) || !(o->lambda0 > 0.0))
         return fail(GBK_EINVAL, "ftol, xtol must be >= 0 and lambda0 > 0");
     int np = 0;
@@ -50,7 +53,10 @@ static gbk_status lm_plan(const gbk_lm_opts *o, LmPlan *pl)
     if (o->free_mask >> GBK_NPAR) return fail(GBK_EINVAL, "free_mask has bits beyond the %d parameters", GBK_NPAR);
     pl->np = np;
     pl->central = o->jacobian == GBK_JAC_FD_CENTRAL;
-    pl->m = 1 + (pl->central ? 2 : 1) * np;
+    pl->tangent = o->jacobian == GBK_JAC_TANGENT;
+    pl->m = pl->tangent ? 1 : 1 + (pl->central ? 2 : 1) * np;
+    if (pl->tangent && o->mode == GBK_LM_PLAIN)
+        return fail(GBK_EINVAL, "the plain mode uses finite differences (the paper's arrangement)");
     return GBK_OK;
 }
 
@@ -284,14 +290,21 @@ static gbk_status lm_plain(const Geom &g, int n_gal, const gbk_obs *obs, const d
     return ok();
 }
 
-static gbk_status lm_iteration(const Geom &g, const LmArgs &a, const gbk_obs *obs, cudaStream_t st)
+static gbk_status lm_iteration(const Geom &g, const LmArgs &a, const gbk_obs *obs, bool tangent,
+                               const TangentArgs &ta, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(a.n_active, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "LM: clearing the running count");
-    lm_launch_build_fd(a, st);
-    gbk_status s = fused_for(g, a.n_gal * a.m, a.pbatch, obs, nullptr, a.m, a.done, a.chi2_batch, a.resid, st);
-    if (s) return s;
-    lm_launch_normal_fd(a, st);
+    gbk_status s;
+    if (tangent) {
+        // analytic J^T J and J^T r at the current point
+        if ((s = launch_tangent(ta, st))) return s;
+    } else {
+        lm_launch_build_fd(a, st);
+        s = fused_for(g, a.n_gal * a.m, a.pbatch, obs, nullptr, a.m, a.done, a.chi2_batch, a.resid, st);
+        if (s) return s;
+        lm_launch_normal_fd(a, st);
+    }
     lm_launch_solve(a, st);
     s = fused_for(g, a.n_gal, a.ptrial, obs, nullptr, 1, a.done, a.chi2_trial, nullptr, st);
     if (s) return s;
@@ -347,16 +360,35 @@ static gbk_status lm_batched(const Geom &g, int n_gal, const gbk_obs *obs, const
         return cuda_fail(e, "LM: stream set-up");
     cudaStream_t st = cg.s;
     lm_launch_init(a, o->lambda0, st);
-    // The first iteration runs eagerly (it also settles the fused kernel's
-    // launch configuration); the rest replay a captured graph.
-    gbk_status s = lm_iteration(g, a, obs, st);
+    TangentArgs ta = {};
+    if (pl.tangent) {
+        if (!tangent_config(g, &ta.cs, &ta.band))
+            return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
+        ta.g = g;
+        ta.n_models = n_gal;
+        ta.params = params;
+        ta.obs_list = obs;
+        ta.models_per_gal = 1;
+        ta.skip = a.done;
+        ta.np = pl.np;
+        for (int j = 0; j < pl.np; ++j) ta.free_idx[j] = pl.idx[j];
+        ta.jtj = a.jtj;
+        ta.jtv = a.jtr;
+        // chi2 at the start point from the fused kernel: accept/reject
+        // decisions always compare fused-kernel chi2 values
+        gbk_status s0 = fused_for(g, n_gal, params, obs, nullptr, 1, nullptr, a.chi2_cur, nullptr, st);
+        if (s0) return s0;
+    }
+    // The first iteration runs eagerly (it also settles the kernels' launch
+    // configurations); the rest replay a captured graph.
+    gbk_status s = lm_iteration(g, a, obs, pl.tangent, ta, st);
     if (s) return s;
     int32_t h_active = n_gal;
     int done_iters = 1;
     if (o->max_iter > 1) {
         if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
             return cuda_fail(e, "LM: begin graph capture");
-        s = lm_iteration(g, a, obs, st);
+        s = lm_iteration(g, a, obs, pl.tangent, ta, st);
         e = cudaStreamEndCapture(st, &cg.graph);
         if (s) return s;
         if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");

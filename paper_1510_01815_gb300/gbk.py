@@ -76,6 +76,7 @@ def lib():
             "gbk_set_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
             "gbk_fit_lm_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
             "gbk_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz, vp]),
+            "gbk_jacobian": (i32, [gp, i32, vp, op, u32, vp, vp, vp, vp, vp, vp]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
         }
@@ -90,7 +91,7 @@ def lib():
 def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
-            "gbk_fit_lm_workspace_bytes", "gbk_fit_lm",
+            "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian",
             "gbk_last_error", "gbk_version"]
 
 
@@ -288,6 +289,65 @@ def fit_lm(geom, obs_list, p0, lo, hi, opts, device="cuda", stream=None):
     ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
     gbk_fit_lm(geom, obs_dev, dlo, dhi, p, opts, chi2, iters, status, ws, stream)
     return p.cpu().numpy(), chi2.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
+
+
+def gbk_jacobian(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), cot=None, jtj=None, jtv=None, chi2=None,
+                 jac=None, stream=None):
+    g = cgeom(geom)
+    n = params.shape[0]
+    mask = 0
+    for k in free:
+        mask |= 1 << int(k)
+    _check(lib().gbk_jacobian(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"), ctypes.byref(obs.c()),
+                              mask, _ptr(cot, torch.float32, "cot"), _ptr(jtj, torch.float64, "jtj"),
+                              _ptr(jtv, torch.float64, "jtv"), _ptr(chi2, torch.float64, "chi2"),
+                              _ptr(jac, torch.float32, "jac"), _stream(stream)))
+
+
+def jacobian(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), device="cuda"):
+    """Convenience: (J [n][10][2][ny][nx], J^T J, J^T r, chi2) as torch tensors."""
+    params = params.to(device=device, dtype=torch.float64).contiguous()
+    n, nf = params.shape[0], len(free)
+    jac = torch.empty((n, NPAR, 2, geom.ny, geom.nx), dtype=torch.float32, device=device)
+    jtj = torch.empty((n, nf, nf), dtype=torch.float64, device=device)
+    jtv = torch.empty((n, nf), dtype=torch.float64, device=device)
+    c2 = torch.empty(n, dtype=torch.float64, device=device)
+    gbk_jacobian(geom, params, obs, free, None, jtj, jtv, c2, jac)
+    return jac, jtj, jtv, c2
+
+
+class ResidualMaps(torch.autograd.Function):
+    """Weighted residual maps [n][2][ny][nx] of a batch of parameter sets
+    against one galaxy, differentiable with respect to the parameters: the
+    forward pass is the fused kernel (gbk_chi2 with residuals), the backward
+    pass the analytic Jacobian kernel (gbk_jacobian with the incoming
+    gradient as cotangent), so grad_params = J^T grad_resid for all ten
+    parameters."""
+
+    @staticmethod
+    def forward(ctx, params, geom, obs):
+        params = params.contiguous()
+        n = params.shape[0]
+        out = torch.empty(n, dtype=torch.float64, device=params.device)
+        resid = torch.empty((n, 2, geom.ny, geom.nx), dtype=torch.float32, device=params.device)
+        gbk_chi2(geom, params.detach(), obs, out, resid, PATH_FUSED)
+        ctx.save_for_backward(params.detach())
+        ctx.geom, ctx.obs = geom, obs
+        return resid
+
+    @staticmethod
+    def backward(ctx, grad_resid):
+        (params,) = ctx.saved_tensors
+        n = params.shape[0]
+        g = torch.empty((n, NPAR), dtype=torch.float64, device=params.device)
+        cot = grad_resid.to(torch.float32).contiguous()
+        gbk_jacobian(ctx.geom, params, ctx.obs, tuple(range(NPAR)), cot, None, g, None, None)
+        return g.to(params.dtype), None, None
+
+
+def residual_maps(params, geom, obs):
+    """Differentiable residual maps (see ResidualMaps)."""
+    return ResidualMaps.apply(params, geom, obs)
 
 
 def gbk_version():

@@ -128,3 +128,21 @@ def test_tuning_host_logic(gbk):
     assert gbk.gbk_get_tuning(small)["cluster_ctas"] >= 1
     with pytest.raises(gbk.GbkError):      # upsampled geometries use the staged path
         gbk.gbk_get_tuning(SINGLE_GEOM.with_(upsample=2))
+
+
+def test_jacobian_and_lm_validation(gbk):
+    import torch
+    g = SINGLE_GEOM
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_fit_lm_workspace_bytes(g, 4, gbk.lm_opts(free=()))
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_fit_lm_workspace_bytes(g, 4, gbk.lm_opts(max_iter=0))
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_fit_lm_workspace_bytes(g, 4, gbk.lm_opts(jacobian=gbk.JAC_TANGENT, mode=gbk.LM_PLAIN))
+    assert gbk.gbk_fit_lm_workspace_bytes(g, 4, gbk.lm_opts()) > 0
+    # tangent mode needs no finite-difference batch
+    assert (gbk.gbk_fit_lm_workspace_bytes(g, 64, gbk.lm_opts(jacobian=gbk.JAC_TANGENT))
+            < gbk.gbk_fit_lm_workspace_bytes(g, 64, gbk.lm_opts()))
+    cg = gbk.cgeom(g)
+    st = gbk.lib().gbk_jacobian(ctypes.byref(cg), 1, None, None, 0, None, None, None, None, None, None)
+    assert st == gbk.GBK_EINVAL
