@@ -409,7 +409,8 @@ def run_gbk(args):
     if not args.no_fits:
         out["fits"] = run_fits(gbk, torch, args.fit_galaxies, dev,
                                [("plain_fd", gbk.LM_PLAIN, gbk.JAC_FD_FORWARD),
-                                ("batched_fd", gbk.LM_BATCHED, gbk.JAC_FD_FORWARD)])
+                                ("batched_fd", gbk.LM_BATCHED, gbk.JAC_FD_FORWARD),
+                                ("batched_tangent", gbk.LM_BATCHED, gbk.JAC_TANGENT)])
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, obs_np, n, 2015)
     if rank == 0:
