@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fits", action="store_true", help="skip the galaxy-fit (LM) measurement")
     ap.add_argument("--fit-galaxies", type=int, default=256)
+    ap.add_argument("--path", default="fused", choices=["fused", "staged"],
+                    help="fused (default) or staged (cube materialised in HBM) evaluation")
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
     ap.add_argument("--tuning", default=None,
                     help="CTAS,THREADS,PERSISTENT: use this fused-kernel tuning instead of autotuning")
@@ -294,10 +296,18 @@ def run_gbk(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(s):
-        gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_FUSED, None, stream)
+    staged = args.path == "staged"
+    ws_staged = gbk.workspace_for(g, n, gbk.PATH_STAGED, dev) if staged else None
 
-    if args.tuning:
+    def step(s):
+        if staged:
+            gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_STAGED, ws_staged, stream)
+        else:
+            gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_FUSED, None, stream)
+
+    if staged:
+        tuning = {"cluster_ctas": 0, "threads": 0, "persistent": 0, "candidates": 0}
+    elif args.tuning:
         cs_, nt_, pe_ = (int(v) for v in args.tuning.split(","))
         gbk.gbk_set_tuning(g, cs_, nt_, pe_)
         tuning = {"cluster_ctas": cs_, "threads": nt_, "persistent": pe_, "candidates": 0}
@@ -343,14 +353,36 @@ def run_gbk(args):
                       "tuning": {"cluster_ctas": tuning["cluster_ctas"], "threads": tuning["threads"],
                                  "persistent": tuning["persistent"], "candidates": tuning["candidates"]},
                       "parallelism": "replicas" if ws > 1 else "single"},
-           "gpu_launches": K}
+           "gpu_launches": K * (4 if staged else 1)}
+    if staged:
+        out["config"]["path"] = "staged"
     if args.quick:
         if rank == 0:
             print(json.dumps(out))
         return
 
-    # ---- roofline of the fused kernel: ALU (FP32 issue + MUFU ex2) ----
     ex, ey, ez = ext_dims(g)
+    if staged:
+        # HBM roofline of the staged chain: extended cube written and read
+        # once, data cube written and read once (algorithmic bytes)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        per_model = 4.0 * (2 * ex * ey * ez + 2 * g.nx * g.ny * g.nz)
+        ach = n * per_model / (ms_step * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "traffic": None, "kernel": "staged chain (model cube, conv, moments)",
+                           "basis": "%.1f MB algorithmic traffic per model" % (per_model / 1e6),
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+        out["clocks"] = clk
+        if rank == 0:
+            print(json.dumps(out))
+        return
+
+    # ---- roofline of the fused kernel: ALU (FP32 issue + MUFU ex2) ----
     ext_vox = n * ex * ey * ez
     r32, r32x2, rmu = gbk.gbk_measure_alu_peak(stream)
     rfma = max(r32, r32x2)
