@@ -251,6 +251,59 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
                               int32_t *iters_out, int32_t *status_out, void *workspace, size_t ws_bytes,
                               void *stream);
 
+/* ------------------------------------------------------------------------
+ * Nested grids (Sec. 2.3.3): chi2 at every node of a regular grid, then a
+ * new grid with the same number of nodes around the best node over a
+ * smaller volume, for `levels` levels.  Level 0 spans [lo, hi] with nodes[k]
+ * points per parameter (both ends included; nodes[k] == 1 keeps parameter k
+ * at fixed[k]); level l+1 spans best +- one level-l step, clipped to
+ * [lo, hi].  The linear node index is row-major in parameter order (the
+ * first gridded parameter varies slowest); equal chi2 values go to the
+ * lowest index, NaN counts as worse than any number.  Node values are
+ * lo + i * ((hi - lo) / (n - 1)) in FP64.  Nodes are evaluated `chunk` at a
+ * time with the fused path.  Synchronises `stream` once per level.
+ *  obs, lo, hi, nodes, fixed   host (obs holds device pointers)
+ *  best_params  host [GBK_NPAR]: the best node of the last level
+ *  best_index   host [levels]:   best linear index per level
+ *  best_chi2    host [levels]:   its chi2
+ * ------------------------------------------------------------------------ */
+GBK_API size_t gbk_grid_workspace_bytes(const gbk_geom *g, const int32_t *nodes, int32_t chunk);
+GBK_API gbk_status gbk_grid(const gbk_geom *g, const gbk_obs *obs, const double *lo, const double *hi,
+                            const int32_t *nodes, const double *fixed, int32_t levels, int32_t chunk,
+                            double *best_params, int64_t *best_index, double *best_chi2, void *workspace,
+                            size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Nested sampling (Sec. 2.3.2; the paper used MultiNest).  Vanilla nested
+ * sampling with an ellipsoidal bound: n_live points from the uniform prior
+ * over [lo, hi] (lo == hi fixes a parameter); each iteration draws `batch`
+ * proposals uniformly inside the live points' bounding ellipsoid (volume
+ * enlarged by 1.1 / efr) and inside the box, evaluates all their
+ * likelihoods L = exp(-chi2/2) in one fused launch, and lets each proposal
+ * in draw order replace the worst live point if it beats it (ln X -= 1 /
+ * n_live per replacement).  Stops when ln(Z + L_max X) - ln Z < tol or after
+ * max_iter iterations.  Random numbers: SplitMix64 seeded with `seed`,
+ * Box-Muller normals.  Synchronises `stream` every iteration.
+ *  obs, lo, hi (host; obs holds device pointers)
+ *  post_mean, post_std  host [GBK_NPAR] posterior moments
+ *  log_z, n_eval, n_iter host scalars
+ * ------------------------------------------------------------------------ */
+typedef struct gbk_ns_opts {
+    int32_t n_live;    /* live points (e.g. 50 in the paper, 400 for the FP workload) */
+    int32_t batch;     /* proposals per iteration                                     */
+    double tol;        /* evidence tolerance (0.5)                                   */
+    double efr;        /* target efficiency: bound volume x 1.1 / efr (1.0)          */
+    uint64_t seed;
+    int32_t max_iter;
+    int32_t reserved;  /* must be 0 */
+} gbk_ns_opts;
+
+GBK_API size_t gbk_nested_sample_workspace_bytes(const gbk_geom *g, const gbk_ns_opts *opts);
+GBK_API gbk_status gbk_nested_sample(const gbk_geom *g, const gbk_obs *obs, const double *lo, const double *hi,
+                                     const gbk_ns_opts *opts, double *post_mean, double *post_std, double *log_z,
+                                     int64_t *n_eval, int32_t *n_iter, void *workspace, size_t ws_bytes,
+                                     void *stream);
+
 /* Launch tuning of the fused path (no counterpart in the paper).  A tuning
  * is the number of CTAs that cooperate on one model (a thread-block cluster
  * of 1..16 CTAs sharing the model's extended rows through distributed shared

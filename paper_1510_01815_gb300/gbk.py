@@ -46,6 +46,12 @@ class CLmOpts(ctypes.Structure):
                 ("lambda0", ctypes.c_double), ("fd_step", ctypes.c_double * 10)]
 
 
+class CNsOpts(ctypes.Structure):
+    _fields_ = [("n_live", ctypes.c_int32), ("batch", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("efr", ctypes.c_double), ("seed", ctypes.c_uint64), ("max_iter", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class CObs(ctypes.Structure):
     _fields_ = [("v_obs", ctypes.c_void_p), ("s_obs", ctypes.c_void_p), ("w_v", ctypes.c_void_p),
                 ("w_s", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
@@ -77,6 +83,16 @@ def lib():
             "gbk_fit_lm_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
             "gbk_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz, vp]),
             "gbk_jacobian": (i32, [gp, i32, vp, op, u32, vp, vp, vp, vp, vp, vp]),
+            "gbk_grid_workspace_bytes": (sz, [gp, ctypes.POINTER(ctypes.c_int32), i32]),
+            "gbk_grid": (i32, [gp, op, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), i32, i32,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_double), vp, sz, vp]),
+            "gbk_nested_sample_workspace_bytes": (sz, [gp, ctypes.POINTER(CNsOpts)]),
+            "gbk_nested_sample": (i32, [gp, op, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(CNsOpts), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), vp, sz, vp]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
         }
@@ -91,7 +107,8 @@ def lib():
 def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
-            "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian",
+            "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
+            "gbk_nested_sample_workspace_bytes", "gbk_nested_sample",
             "gbk_last_error", "gbk_version"]
 
 
@@ -348,6 +365,49 @@ class ResidualMaps(torch.autograd.Function):
 def residual_maps(params, geom, obs):
     """Differentiable residual maps (see ResidualMaps)."""
     return ResidualMaps.apply(params, geom, obs)
+
+
+def gbk_grid(geom, obs, lo, hi, nodes, fixed, levels=3, chunk=16384, device="cuda", stream=None):
+    """Nested-grid search; returns (best_params, best_index per level,
+    best_chi2 per level) as numpy arrays."""
+    import numpy as np
+    g = cgeom(geom)
+    D = ctypes.c_double * NPAR
+    I = ctypes.c_int32 * NPAR
+    nd = I(*[int(v) for v in nodes])
+    nb = lib().gbk_grid_workspace_bytes(ctypes.byref(g), nd, int(chunk))
+    if nb == 0:
+        raise GbkError(GBK_EINVAL, lib().gbk_last_error().decode())
+    ws = torch.empty(nb, dtype=torch.uint8, device=device)
+    bp = D()
+    bi = (ctypes.c_int64 * levels)()
+    bc = (ctypes.c_double * levels)()
+    _check(lib().gbk_grid(ctypes.byref(g), ctypes.byref(obs.c()), D(*[float(v) for v in lo]),
+                          D(*[float(v) for v in hi]), nd, D(*[float(v) for v in fixed]), int(levels), int(chunk),
+                          bp, bi, bc, _ptr(ws, None, "workspace"), nb, _stream(stream)))
+    return np.array(bp[:]), np.array(bi[:]), np.array(bc[:])
+
+
+def gbk_nested_sample(geom, obs, lo, hi, n_live=400, batch=None, tol=0.5, efr=1.0, seed=1, max_iter=100000,
+                      device="cuda", stream=None):
+    """Nested sampling; returns dict(mean, std, log_z, n_eval, n_iter)."""
+    import numpy as np
+    g = cgeom(geom)
+    o = CNsOpts(int(n_live), int(batch if batch else max(1, n_live // 4)), float(tol), float(efr), int(seed),
+                int(max_iter), 0)
+    nb = lib().gbk_nested_sample_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
+    if nb == 0:
+        raise GbkError(GBK_EINVAL, lib().gbk_last_error().decode())
+    ws = torch.empty(nb, dtype=torch.uint8, device=device)
+    D = ctypes.c_double * NPAR
+    mean, std, lz = D(), D(), ctypes.c_double()
+    ne, ni = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().gbk_nested_sample(ctypes.byref(g), ctypes.byref(obs.c()), D(*[float(v) for v in lo]),
+                                   D(*[float(v) for v in hi]), ctypes.byref(o), mean, std, ctypes.byref(lz),
+                                   ctypes.byref(ne), ctypes.byref(ni), _ptr(ws, None, "workspace"), nb,
+                                   _stream(stream)))
+    return {"mean": np.array(mean[:]), "std": np.array(std[:]), "log_z": lz.value, "n_eval": ne.value,
+            "n_iter": ni.value}
 
 
 def gbk_version():
