@@ -346,6 +346,12 @@ GBK_API gbk_status gbk_set_tuning(const gbk_geom *g, const gbk_tuning *t);
 GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ffma2_lane_ops_per_s,
                                         double *ex2_lane_ops_per_s, void *stream);
 
+/* Reads and clears the library's device status word (host output): 0 when
+ * every bounded device-side wait since the last call completed; 1 when a
+ * TMA load of the staged convolution did not complete in time (the affected
+ * blocks stopped early and their output is incomplete).  Synchronising. */
+GBK_API gbk_status gbk_device_status(int32_t *status);
+
 /* Message of the last failed call on this thread ("" if none). */
 GBK_API const char *gbk_last_error(void);
 

@@ -93,6 +93,7 @@ def lib():
                                         ctypes.POINTER(CNsOpts), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), vp, sz, vp]),
+            "gbk_device_status": (i32, [ctypes.POINTER(ctypes.c_int32)]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
         }
@@ -108,7 +109,7 @@ def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
-            "gbk_nested_sample_workspace_bytes", "gbk_nested_sample",
+            "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_device_status",
             "gbk_last_error", "gbk_version"]
 
 
@@ -408,6 +409,13 @@ def gbk_nested_sample(geom, obs, lo, hi, n_live=400, batch=None, tol=0.5, efr=1.
                                    _stream(stream)))
     return {"mean": np.array(mean[:]), "std": np.array(std[:]), "log_z": lz.value, "n_eval": ne.value,
             "n_iter": ni.value}
+
+
+def gbk_device_status():
+    """Reads and clears the device status word (0 = all bounded waits completed)."""
+    v = ctypes.c_int32()
+    _check(lib().gbk_device_status(ctypes.byref(v)))
+    return v.value
 
 
 def gbk_version():

@@ -56,6 +56,7 @@ def test_maps_fused_vs_oracle(G, case):
 def test_cube_and_maps_staged_vs_oracle(G, case):
     g, p, ps = _params(case, n=3)
     cubes, maps = G.eval_cubes(g, torch.from_numpy(ps))
+    assert G.gbk_device_status() == 0
     cubes, maps = cubes.cpu().numpy(), maps.cpu().numpy()
     for i in range(ps.shape[0]):
         cref, mref = oracle.evaluate(ogeom(g), ps[i], want_cube=True)
