@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fits", action="store_true", help="skip the galaxy-fit (LM) measurement")
     ap.add_argument("--fit-galaxies", type=int, default=256)
+    ap.add_argument("--no-survey", action="store_true", help="skip the ragged survey-fit measurement")
+    ap.add_argument("--survey-galaxies", type=int, default=2048)
+    ap.add_argument("--survey-plain", type=int, default=64, help="galaxies the plain survey LM is timed on")
     ap.add_argument("--path", default="fused", choices=["fused", "staged"],
                     help="fused (default) or staged (cube materialised in HBM) evaluation")
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
@@ -195,6 +198,90 @@ def run_fits(gbk, torch, n, device, forms):
         for name in out:
             if isinstance(out[name], dict) and name != "plain_fd":
                 out[name]["speedup_vs_plain"] = out[name]["fits_per_s"] / out["plain_fd"]["fits_per_s"]
+    return out
+
+
+def survey_batch(gbk, torch, n, seed, device):
+    """n survey galaxies of different geometry (24-96 spaxels square, 32-128
+    channels, PSF 4 px, LSF 20-60 km/s, channel width keeping the line in
+    the band), maps from the library at the true parameters, seeded noise
+    (5 km/s on v, 5 sqrt(2) on sigma), 2 % dead fibres, 20 %-perturbed
+    starts inside the fit bounds."""
+    rng = np.random.default_rng(seed)
+    gal = synth.draw_survey(rng, n)
+    geoms = [g for g, _ in gal]
+    truth = np.array([p for _, p in gal])
+    maps, _, _ = gbk.survey_eval(geoms, truth, device=device)
+    obs, lo, hi, p0 = [], [], [], []
+    for i, g in enumerate(geoms):
+        m = maps[i].cpu().numpy()
+        shape = (g.ny, g.nx)
+        v = (m[1] + synth.gaussian_noise(rng, shape, 5.0)).astype(np.float32)
+        s = (m[2] + synth.gaussian_noise(rng, shape, 5.0 * np.sqrt(2.0))).astype(np.float32)
+        wv, ws = synth.weights(shape, 5.0)
+        mask = synth.dead_fibre_mask(rng, shape).astype(np.uint8)
+        obs.append(gbk.Obs.from_numpy(v, s, wv, ws, mask, device=device))
+        l, h = truth[i].copy(), truth[i].copy()
+        l[synth.X0], h[synth.X0] = 0.0, g.nx - 1.0
+        l[synth.Y0], h[synth.Y0] = 0.0, g.ny - 1.0
+        l[synth.PA], h[synth.PA] = -360.0, 720.0
+        l[synth.INCL], h[synth.INCL] = 1.0, 89.0
+        l[synth.VSYS], h[synth.VSYS] = -200.0, 200.0
+        l[synth.VMAX], h[synth.VMAX] = 1.0, 600.0
+        l[synth.RT], h[synth.RT] = 0.05, 60.0
+        l[synth.SIG0], h[synth.SIG0] = 1.0, 300.0
+        lo.append(l)
+        hi.append(h)
+        p0.append(synth.perturb(rng, truth[i], FIT_FREE, 0.2, l, h))
+    return geoms, truth, obs, np.array(p0), np.array(lo), np.array(hi)
+
+
+def run_survey(gbk, torch, n, n_plain, device):
+    """Survey-scale fitting: galaxy fits/s of the batched LM over a ragged
+    batch against the plain one-galaxy-at-a-time LM, iterations p50/p99,
+    recovery, and the ragged evaluator's throughput."""
+    geoms, truth, obs, p0, lo, hi = survey_batch(gbk, torch, n, 4, device)
+    pix = sum(g.nx * g.ny for g in geoms)
+    vox = sum(g.nx * g.ny * g.nz for g in geoms)
+    out = {"workload": "%d survey galaxies, 24-96 spaxels square x 32-128 channels (log-uniform), PSF 4 px, "
+                       "LSF 20-60 km/s, noise 5 / 5 sqrt(2) km/s, 2%% dead fibres, 20%% perturbed starts, "
+                       "%d free parameters" % (n, len(FIT_FREE)),
+           "data_voxels": vox, "spaxels": pix}
+    # ragged evaluator: one chi2 per galaxy
+    obs_dev, _keep = gbk.obs_array(obs, device)
+    d_p = torch.from_numpy(truth).to(device)
+    d_c = torch.empty(n, dtype=torch.float64, device=device)
+    ws = torch.empty(max(gbk.gbk_survey_workspace_bytes(geoms), 1), dtype=torch.uint8, device=device)
+    for _ in range(3):
+        gbk.gbk_survey_eval(geoms, d_p, obs_dev, None, d_c, None, ws)
+    torch.cuda.synchronize()
+    reps = 20
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        gbk.gbk_survey_eval(geoms, d_p, obs_dev, None, d_c, None, ws)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    out["eval"] = {"ms_per_survey": ms, "evals_per_s": n / (ms * 1e-3), "data_voxels_per_s": vox / (ms * 1e-3),
+                   "note": "time includes the per-call geometry-table upload and plan"}
+    for name, mode, sub in (("batched_fd", gbk.LM_BATCHED, n), ("plain_fd", gbk.LM_PLAIN, n_plain)):
+        opts = gbk.lm_opts(max_iter=200, jacobian=gbk.JAC_FD_FORWARD, mode=mode, free=FIT_FREE)
+        gbk.survey_fit_lm(geoms[:4], obs[:4], p0[:4], lo[:4], hi[:4], opts, device=device)  # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        q, c, it, st = gbk.survey_fit_lm(geoms[:sub], obs[:sub], p0[:sub], lo[:sub], hi[:sub], opts, device=device)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        tr = truth[:sub]
+        dv = np.abs(q[:, synth.VMAX] - tr[:, synth.VMAX])
+        dpa = np.abs((q[:, synth.PA] - tr[:, synth.PA] + 180.0) % 360.0 - 180.0)
+        out[name] = {"galaxies": sub, "fits_per_s": sub / dt, "seconds": dt,
+                     "p50_iters": float(np.percentile(it, 50)), "p99_iters": float(np.percentile(it, 99)),
+                     "converged_frac": float(np.mean(np.isin(st, [1, 2]))),
+                     "recovered_frac": float(np.mean((dv < 2.0) & (dpa < 1.0))),
+                     "median_dvmax": float(np.median(dv)), "median_dpa": float(np.median(dpa))}
+    out["batched_fd"]["speedup_vs_plain"] = out["batched_fd"]["fits_per_s"] / out["plain_fd"]["fits_per_s"]
     return out
 
 
@@ -443,6 +530,8 @@ def run_gbk(args):
                                [("plain_fd", gbk.LM_PLAIN, gbk.JAC_FD_FORWARD),
                                 ("batched_fd", gbk.LM_BATCHED, gbk.JAC_FD_FORWARD),
                                 ("batched_tangent", gbk.LM_BATCHED, gbk.JAC_TANGENT)])
+    if not args.no_survey:
+        out["survey"] = run_survey(gbk, torch, args.survey_galaxies, args.survey_plain, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, obs_np, n, 2015)
     if rank == 0:

@@ -252,6 +252,39 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
                               void *stream);
 
 /* ------------------------------------------------------------------------
+ * Survey batches: galaxies of different geometry (cube size, channel width,
+ * LSF, PSF) evaluated or fitted together -- the survey-scale setting of
+ * Sec. 1 and Sec. 5, with the model of Sec. 2.1-2.2 and the optimiser of
+ * Sec. 2.3.1 unchanged per galaxy.
+ *  geoms      host [n_gal]: geometry of each galaxy (upsample must be 1)
+ *  params     device [n_gal][GBK_NPAR]
+ *  obs        device [n_gal] gbk_obs, galaxy i's maps of geoms[i]'s size
+ *  maps       device, packed: galaxy i's [3][ny_i][nx_i] (m0, m1, m2) at
+ *             float offset 3 * P_i, P_i = sum_{j<i} nx_j * ny_j; or NULL
+ *  chi2       device [n_gal] or NULL
+ *  resid      device, packed: galaxy i's [2][ny_i][nx_i] at 2 * P_i; or NULL
+ * Every galaxy gets exactly the values gbk_chi2 / gbk_eval_cubes give it
+ * on its own (maps and residuals bit for bit; chi2 up to the order of its
+ * FP64 reduction).  The workspace holds the geometry tables, uploaded from
+ * the host on every call, and, for the fit, the batched LM state
+ * (gbk_survey_workspace_bytes with opts NULL for evaluation, with the LM
+ * options for fitting).  Galaxies are grouped by the thread-block cluster
+ * size they need, one launch per group, costliest galaxies first.
+ * gbk_survey_fit_lm is gbk_fit_lm per galaxy; the batched mode advances all
+ * galaxies together in one CUDA graph, the plain mode fits one galaxy after
+ * the other with the host solve; the tangent Jacobian is not served here
+ * (GBK_EUNSUPPORTED).
+ * ------------------------------------------------------------------------ */
+GBK_API size_t gbk_survey_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, const gbk_lm_opts *opts);
+GBK_API gbk_status gbk_survey_eval(const gbk_geom *geoms, int32_t n_gal, const double *params, const gbk_obs *obs,
+                                   float *maps, double *chi2, float *resid, void *workspace, size_t ws_bytes,
+                                   void *stream);
+GBK_API gbk_status gbk_survey_fit_lm(const gbk_geom *geoms, int32_t n_gal, const gbk_obs *obs, const double *lo,
+                                     const double *hi, double *params, const gbk_lm_opts *opts, double *chi2_out,
+                                     int32_t *iters_out, int32_t *status_out, void *workspace, size_t ws_bytes,
+                                     void *stream);
+
+/* ------------------------------------------------------------------------
  * Nested grids (Sec. 2.3.3): chi2 at every node of a regular grid, then a
  * new grid with the same number of nodes around the best node over a
  * smaller volume, for `levels` levels.  Level 0 spans [lo, hi] with nodes[k]

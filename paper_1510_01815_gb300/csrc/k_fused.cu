@@ -91,7 +91,6 @@ __host__ __device__ inline size_t fused_smem_bytes(const Geom &g, int band)
     b += (size_t)3 * edge_table_len(g) * sizeof(float);  // edge tables G0, A1, A2
     b += (size_t)pad4(2 * g.R + 1) * sizeof(float);   // PSF taps
     b += (size_t)pad4(band + 2 * g.R) * sizeof(int);  // row offsets of the y pass
-    b += 64 * sizeof(double);                         // reduction scratch
     return b;
 }
 
@@ -136,45 +135,41 @@ struct KahanF {
     }
 };
 
-template <int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
+// Dynamic shared memory of one model's geometry.
+struct FusedSmem {
+    float4 *Q, *P;
+    float *eG0, *eA1, *eA2, *wxy;
+    int *rowoff;
+};
+
+__device__ __forceinline__ FusedSmem fused_layout(unsigned char *smem, const Geom &g, int band)
 {
-    cg::cluster_group cluster = cg::this_cluster();
-    const Geom &g = a.g;
-    const int cs = a.cs;
-    const int rank = (int)cluster.block_rank();
-    const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;  // this cluster, clusters in the grid
-    const int band = a.band;                          // max rows of any CTA
-    const int row0 = band_begin(rank, g.ey, cs);
-    const int row1 = band_begin(rank + 1, g.ey, cs);
-    const int nrows = row1 - row0;
-    const int R = g.R;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-
-    extern __shared__ __align__(16) unsigned char smem[];
-    float4 *Q = reinterpret_cast<float4 *>(smem);
-    float4 *P = Q + fused_q_floats4(g, band);
+    FusedSmem L;
+    L.Q = reinterpret_cast<float4 *>(smem);
+    L.P = L.Q + fused_q_floats4(g, band);
     const int etl = edge_table_len(g);
-    float *eG0 = reinterpret_cast<float *>(P + (size_t)band * g.nx);
-    float *eA1 = eG0 + etl;
-    float *eA2 = eA1 + etl;
-    float *wxy = eA2 + etl;
-    int *rowoff = reinterpret_cast<int *>(wxy + pad4(2 * R + 1));
-    double *red = reinterpret_cast<double *>(rowoff + pad4(band + 2 * R));
+    L.eG0 = reinterpret_cast<float *>(L.P + (size_t)band * g.nx);
+    L.eA1 = L.eG0 + etl;
+    L.eA2 = L.eA1 + etl;
+    L.wxy = L.eA2 + etl;
+    L.rowoff = reinterpret_cast<int *>(L.wxy + pad4(2 * g.R + 1));
+    return L;
+}
 
-    __shared__ ModelConst mc;
-    __shared__ gbk_obs s_ob;   // observed maps of the current model's galaxy
-    __shared__ float s_var_z;  // dv^2 * sum_j j^2 L_j
-
-    // ---- set-up of the geometry-only tables, all in parallel, one barrier ----
+// Geometry-only tables of one CTA: PSF taps, LSF edge tables, the y-pass row
+// offsets and the LSF variance, written by disjoint threads (the caller
+// places a barrier before they are read).
+__device__ void fused_setup(const Geom &g, const FusedSmem &L, int row0, int row1, float *var_z)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x, R = g.R;
     if (tid >= nthr - 32) {  // last warp: PSF taps
         for (int j = tid - (nthr - 32); j <= 2 * R; j += 32)
-            wxy[j] = tap_raw(j - R, g.sig_xy, R) / tap_sum(g.sig_xy, R);
+            L.wxy[j] = tap_raw(j - R, g.sig_xy, R) / tap_sum(g.sig_xy, R);
     }
     if (tid == nthr - 64) {
         float S = tap_sum(g.sig_z, g.Rz), V = 0.f;
         for (int j = -g.Rz; j <= g.Rz; ++j) V = fmaf(tap_raw(j, g.sig_z, g.Rz), (float)(j * j), V);
-        s_var_z = g.dv * g.dv * (V / S);
+        *var_z = g.dv * g.dv * (V / S);
     }
     // Edge tables.  For an edge channel e with in-band LSF tap sums
     // G0 = sum L_j, H1 = dv sum L_j j, H2 = dv^2 sum L_j j^2 (j = k - e over
@@ -203,32 +198,95 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         float eref = lower ? 0.5f * (float)(elo - 1) : 0.5f * (float)(ehi + g.ez - 1);
         float delta = ((float)ee - eref) * g.dv;
         int slot = lower ? ee : hi_off + (ee - ehi);
-        eG0[slot] = G0;
-        eA1[slot] = fmaf(delta, G0, H1);
-        eA2[slot] = fmaf(delta, fmaf(delta, G0, 2.f * H1), H2);
+        L.eG0[slot] = G0;
+        L.eA1[slot] = fmaf(delta, G0, H1);
+        L.eA2[slot] = fmaf(delta, fmaf(delta, G0, 2.f * H1), H2);
     }
     // y-pass row offsets (in float4 units from Q) of extended rows [row0 - R, row1 + R)
+    const int nrows = row1 - row0;
     for (int k = tid; k < nrows + 2 * R; k += nthr) {
         int er = row0 - R + k;
         int off;
         if (er < row0) off = k * g.nx;                                        // top halo
-        else if (er < row1) off = (int)(P - Q) + (er - row0) * g.nx;          // own rows
+        else if (er < row1) off = (int)(L.P - L.Q) + (er - row0) * g.nx;      // own rows
         else off = (R + (er - row1)) * g.nx;                                  // bottom halo
-        rowoff[k] = off;
+        L.rowoff[k] = off;
     }
-    __syncthreads();
-    const float var_z = s_var_z;
-    const ModelConst &c = mc;  // read from shared memory (broadcast) to save registers
+}
 
-    // Persistent: the clusters of the grid take the models in turn.
-    for (int model = cid; model < a.n_models; model += ncl) {
-    const int gal = a.models_per_gal > 0 ? model / a.models_per_gal : 0;
+// RAGGED = false: one geometry (a.g) for every model; the tables are set up
+// once per CTA.  RAGGED = true: galaxy gal has geometry a.geoms[gal], its
+// maps and residuals are packed at pixel offset a.pix_off[gal] * models per
+// galaxy, and the tables are rebuilt for every model.
+template <int NT, int MINB, bool RAGGED>
+__global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = a.cs;
+    const int rank = (int)cluster.block_rank();
+    const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;  // this cluster, clusters in the grid
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int mpg = a.models_per_gal;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ModelConst mc;
+    __shared__ gbk_obs s_ob;   // observed maps of the current model's galaxy
+    __shared__ float s_var_z;  // dv^2 * sum_j j^2 L_j
+    __shared__ double red[40]; // chi2 reduction: one slot per warp, the CTA total in [32]
+    __shared__ Geom s_g;       // RAGGED: geometry of the current model
+
+    // Uniform geometry: the tables are built once, before the model loop.
+    int band = a.band, row0 = 0, row1 = 0;
+    FusedSmem L;
+    if (!RAGGED) {
+        row0 = band_begin(rank, a.g.ey, cs);
+        row1 = band_begin(rank + 1, a.g.ey, cs);
+        L = fused_layout(smem, a.g, band);
+        fused_setup(a.g, L, row0, row1, &s_var_z);
+        __syncthreads();
+    }
+
+    // The clusters of the grid take the models in turn.
+    for (int w = cid; w < a.n_models; w += ncl) {
+    int gal, model;
+    if (RAGGED) {
+        const int gi = w / mpg;
+        gal = a.order ? a.order[gi] : gi;
+        model = gal * mpg + (w - gi * mpg);
+    } else {
+        model = w;
+        gal = mpg > 0 ? model / mpg : 0;
+    }
     if (a.skip && a.skip[gal] != 0) continue;  // same decision in every CTA of the cluster
+    if (RAGGED) {
+        // The previous model ended with a cluster barrier, so nobody still
+        // reads s_g or the tables.
+        if (tid == 0) s_g = a.geoms[gal];
+        __syncthreads();
+        band = (s_g.ey + cs - 1) / cs;
+        row0 = band_begin(rank, s_g.ey, cs);
+        row1 = band_begin(rank + 1, s_g.ey, cs);
+        L = fused_layout(smem, s_g, band);
+        fused_setup(s_g, L, row0, row1, &s_var_z);
+    }
+    const Geom &g = RAGGED ? s_g : a.g;
+    const int nrows = row1 - row0;
+    const int R = g.R;
+    float4 *const Q = L.Q, *const P = L.P;
+    const float *const eG0 = L.eG0, *const eA1 = L.eA1, *const eA2 = L.eA2, *const wxy = L.wxy;
+    const int *const rowoff = L.rowoff;
+    const int elo = edge_lo_end(g), ehi = edge_hi_begin(g);
+    const int hi_off = (elo + 1) & ~1;  // table slot of channel ehi
+    // pixel offset of this model's maps and residuals
+    const size_t mo = RAGGED ? (size_t)a.pix_off[gal] * mpg + (size_t)(model - gal * mpg) * g.nx * g.ny
+                             : (size_t)model * g.nx * g.ny;
     if (tid == 0) {
         mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
         s_ob = a.obs_list ? a.obs_list[gal] : a.obs;
     }
     __syncthreads();
+    const float var_z = s_var_z;
+    const ModelConst &c = mc;  // read from shared memory (broadcast) to save registers
 
     // ---- phase 1: Gaussian line of every extended spaxel of the band ----
     // Interior channels [elo, ehi) have their whole LSF window inside the band.
@@ -429,7 +487,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             m0 = 0.f; m1 = c.vsys; m2 = 0.f;
         }
         if (a.maps) {
-            float *mp = a.maps + (size_t)model * 3 * np;
+            float *mp = a.maps + 3 * mo;
             mp[pix] = m0; mp[np + pix] = m1; mp[2 * np + pix] = m2;
         }
         if (want_obs) {
@@ -441,7 +499,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             acc.add(rv * rv);
             acc.add(rs * rs);
             if (a.resid) {
-                float *rp = a.resid + (size_t)model * 2 * np;
+                float *rp = a.resid + 2 * mo;
                 rp[pix] = rv; rp[np + pix] = rs;
             }
         }
@@ -478,14 +536,14 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     cluster.sync();  // keep every CTA's shared memory alive until rank 0 is done
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool RAGGED>
 static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_t stream)
 {
     // Shared-memory opt-in is set to what this launch needs (static shared
     // memory of the kernel counts against the same per-block limit).
     static size_t configured = 0;
     static bool cluster_configured = false;
-    auto kern = fused_eval_kernel<NT, MINB>;
+    auto kern = fused_eval_kernel<NT, MINB, RAGGED>;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel: setting dynamic shared memory");
@@ -511,7 +569,7 @@ static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_
     // cluster size and shared-memory size), each looping over models.
     static int cached_cs = -1, cached_clusters = 0;
     static size_t cached_smem = 0;
-    if (cached_cs != args.cs || cached_smem != smem) {
+    if (args.persistent && (cached_cs != args.cs || cached_smem != smem)) {
         cfg.gridDim = dim3((unsigned)args.cs, 1, 1);
         int ncl = 0;
         cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
@@ -531,13 +589,39 @@ static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_
 
 gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
 {
+    if (args.geoms) {
+        if (args.models_per_gal < 1 || args.n_models % args.models_per_gal != 0 || !args.pix_off)
+            return fail(GBK_EINVAL, "ragged fused launch: inconsistent batch description");
+        switch (args.threads) {
+        case 512: return launch_variant<512, 2, true>(args, args.smem, stream);
+        case 384: return launch_variant<384, 2, true>(args, args.smem, stream);
+        case 256: return launch_variant<256, 2, true>(args, args.smem, stream);
+        default: return fail(GBK_EINVAL, "unsupported fused block size %d", args.threads);
+        }
+    }
     size_t smem = fused_smem_bytes(args.g, args.band);
     switch (args.threads) {
-    case 512: return launch_variant<512, 2>(args, smem, stream);
-    case 384: return launch_variant<384, 2>(args, smem, stream);
-    case 256: return launch_variant<256, 2>(args, smem, stream);
+    case 512: return launch_variant<512, 2, false>(args, smem, stream);
+    case 384: return launch_variant<384, 2, false>(args, smem, stream);
+    case 256: return launch_variant<256, 2, false>(args, smem, stream);
     default: return fail(GBK_EINVAL, "unsupported fused block size %d", args.threads);
     }
+}
+
+// Shared memory a ragged launch with cluster size cs needs: the largest of
+// its geometries' needs; false if one of them does not fit.
+bool fused_config_ragged(const Geom *geoms, int n, int cs, int threads, size_t *smem)
+{
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) {
+        const Geom &g = geoms[i];
+        if (g.u != 1 || cs > g.ey) return false;
+        size_t b = fused_smem_bytes(g, (g.ey + cs - 1) / cs);
+        if (b > need) need = b;
+    }
+    if (need > (size_t)kFusedMaxSmem || (threads != 512 && threads != 384 && threads != 256)) return false;
+    *smem = need;
+    return true;
 }
 
 }  // namespace gbk

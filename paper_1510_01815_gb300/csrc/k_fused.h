@@ -27,6 +27,15 @@ struct FusedArgs {
     int threads;            // block size: 512, 384 or 256
     int persistent;         // 1: one resident wave of clusters loops over the models;
                             // 0: one cluster per model
+    // Ragged batches (geoms != null): galaxy gal has geometry geoms[gal] and
+    // models gal * models_per_gal + s, s < models_per_gal; its maps and
+    // residuals start at pixel offset pix_off[gal] * models_per_gal (times 3
+    // and 2) and model s of it follows at s * nx * ny.  n_models counts the
+    // models of the galaxies order[0 .. n_models / models_per_gal).
+    const Geom *geoms;      // device [n_gal]
+    const int64_t *pix_off; // device [n_gal]
+    const int32_t *order;   // device list of the galaxies this launch serves (null: 0, 1, ...)
+    size_t smem;            // dynamic shared memory (ragged: the largest geometry's need)
 };
 
 // Launch configuration of the fused kernel (see tune.cu).
@@ -38,6 +47,7 @@ struct FusedConfig {
 };
 
 size_t fused_smem_bytes_host(const Geom &g, int band);
+bool fused_config_ragged(const Geom *geoms, int n, int cs, int threads, size_t *smem);
 bool fused_config(const Geom &g, FusedConfig *cfg);
 bool fused_config_valid(const Geom &g, int cs, int threads, int persistent, FusedConfig *cfg);
 gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream);

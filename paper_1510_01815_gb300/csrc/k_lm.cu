@@ -45,8 +45,15 @@ __global__ void __launch_bounds__(256) lm_normal_fd_kernel(LmArgs a)
     const int gal = blockIdx.x;
     if (a.done[gal]) return;
     constexpr int NT = NP * (NP + 1) / 2;
-    const size_t n2 = (size_t)2 * a.np_pix;
-    const float *R = a.resid + (size_t)gal * a.m * n2;
+    size_t n2, base;
+    if (a.pix_off) {
+        n2 = (size_t)2 * (a.pix_off[gal + 1] - a.pix_off[gal]);
+        base = (size_t)2 * a.m * a.pix_off[gal];
+    } else {
+        n2 = (size_t)2 * a.np_pix;
+        base = (size_t)gal * a.m * n2;
+    }
+    const float *R = a.resid + base;
     float inv_h[NP];
     for (int j = 0; j < NP; ++j) inv_h[j] = (float)(1.0 / a.hstep[(size_t)gal * NP + j]);
     float jtj[NT], jtr[NP];

@@ -30,6 +30,8 @@ struct LmArgs {
     double *lambda, *dnorm, *pnorm;  // [n_gal]
     int32_t *iters, *status, *done;  // [n_gal]
     int32_t *n_active;       // [1] galaxies still running after the last accept
+    const int64_t *pix_off;  // ragged batches: [n_gal + 1] pixel offsets (galaxy gal's
+                             // residuals start at 2 m pix_off[gal]); null: np_pix each
 };
 
 void lm_launch_init(const LmArgs &a, double lambda0, cudaStream_t st);

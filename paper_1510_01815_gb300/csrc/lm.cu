@@ -15,6 +15,7 @@
 // evaluations on the GPU, the residual maps copied to the host every
 // iteration, the normal equations and the solve on the CPU in FP64.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -22,6 +23,7 @@
 #include "k_fused.h"
 #include "k_lm.h"
 #include "k_tangent.h"
+#include "survey.h"
 
 namespace gbk {
 
@@ -67,13 +69,14 @@ struct LmLayout {
     size_t iters, status, done, nact, total;
 };
 
-static LmLayout lm_layout(const Geom &g, int ng, const LmPlan &pl)
+// pix_total: pixels of all ng galaxies together.
+static LmLayout lm_layout_pix(size_t pix_total, int ng, const LmPlan &pl)
 {
     LmLayout L;
-    size_t o = 0, npix = (size_t)g.nx * g.ny;
+    size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
     L.pbatch = take(sizeof(double) * ng * pl.m * GBK_NPAR);
-    L.resid = take(sizeof(float) * ng * pl.m * 2 * npix);
+    L.resid = take(sizeof(float) * pl.m * 2 * pix_total);
     L.chi2b = take(sizeof(double) * ng * pl.m);
     L.hstep = take(sizeof(double) * ng * pl.np);
     L.jtj = take(sizeof(double) * ng * pl.np * pl.np);
@@ -91,6 +94,11 @@ static LmLayout lm_layout(const Geom &g, int ng, const LmPlan &pl)
     L.nact = take(sizeof(int32_t));
     L.total = o;
     return L;
+}
+
+static LmLayout lm_layout(const Geom &g, int ng, const LmPlan &pl)
+{
+    return lm_layout_pix((size_t)ng * g.nx * g.ny, ng, pl);
 }
 
 static gbk_status fused_for(const Geom &g, int n_models, const double *params, const gbk_obs *obs_list,
@@ -114,6 +122,20 @@ static gbk_status fused_for(const Geom &g, int n_models, const double *params, c
     a.threads = fc.threads;
     a.persistent = fc.persistent;
     return launch_fused(a, st);
+}
+
+// What the batched LM evaluates: one geometry for every galaxy, or a ragged
+// survey plan.
+struct EvalTarget {
+    const Geom *g;
+    const SurveyPlan *sp;
+};
+
+static gbk_status eval_for(const EvalTarget &t, int n_gal, int mpg, const double *params, const gbk_obs *obs_list,
+                           const int32_t *skip, double *chi2, float *resid, cudaStream_t st)
+{
+    if (t.sp) return survey_eval(*t.sp, mpg, params, obs_list, skip, nullptr, chi2, resid, st);
+    return fused_for(*t.g, n_gal * mpg, params, obs_list, nullptr, mpg, skip, chi2, resid, st);
 }
 
 // ----------------------------------------------------------------------------
@@ -290,7 +312,7 @@ static gbk_status lm_plain(const Geom &g, int n_gal, const gbk_obs *obs, const d
     return ok();
 }
 
-static gbk_status lm_iteration(const Geom &g, const LmArgs &a, const gbk_obs *obs, bool tangent,
+static gbk_status lm_iteration(const EvalTarget &t, const LmArgs &a, const gbk_obs *obs, bool tangent,
                                const TangentArgs &ta, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(a.n_active, 0, sizeof(int32_t), st);
@@ -301,12 +323,12 @@ static gbk_status lm_iteration(const Geom &g, const LmArgs &a, const gbk_obs *ob
         if ((s = launch_tangent(ta, st))) return s;
     } else {
         lm_launch_build_fd(a, st);
-        s = fused_for(g, a.n_gal * a.m, a.pbatch, obs, nullptr, a.m, a.done, a.chi2_batch, a.resid, st);
+        s = eval_for(t, a.n_gal, a.m, a.pbatch, obs, a.done, a.chi2_batch, a.resid, st);
         if (s) return s;
         lm_launch_normal_fd(a, st);
     }
     lm_launch_solve(a, st);
-    s = fused_for(g, a.n_gal, a.ptrial, obs, nullptr, 1, a.done, a.chi2_trial, nullptr, st);
+    s = eval_for(t, a.n_gal, 1, a.ptrial, obs, a.done, a.chi2_trial, nullptr, st);
     if (s) return s;
     lm_launch_accept(a, st);
     e = cudaGetLastError();
@@ -314,11 +336,11 @@ static gbk_status lm_iteration(const Geom &g, const LmArgs &a, const gbk_obs *ob
     return GBK_OK;
 }
 
-static gbk_status lm_batched(const Geom &g, int n_gal, const gbk_obs *obs, const double *lo, const double *hi,
+static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs, const double *lo, const double *hi,
                              double *params, const gbk_lm_opts *o, const LmPlan &pl, double *chi2_out,
                              int32_t *iters_out, int32_t *status_out, char *ws, cudaStream_t user)
 {
-    LmLayout L = lm_layout(g, n_gal, pl);
+    LmLayout L = t.sp ? lm_layout_pix((size_t)t.sp->total_pix(), n_gal, pl) : lm_layout(*t.g, n_gal, pl);
     LmArgs a = {};
     a.n_gal = n_gal;
     a.np = pl.np;
@@ -326,7 +348,8 @@ static gbk_status lm_batched(const Geom &g, int n_gal, const gbk_obs *obs, const
     for (int k = 0; k < GBK_NPAR; ++k) a.fd_step[k] = o->fd_step[k];
     a.m = pl.m;
     a.central = pl.central;
-    a.np_pix = g.nx * g.ny;
+    a.np_pix = t.sp ? 0 : t.g->nx * t.g->ny;
+    a.pix_off = t.sp ? t.sp->d_pix_off : nullptr;
     a.max_iter = o->max_iter;
     a.ftol = o->ftol;
     a.xtol = o->xtol;
@@ -362,6 +385,8 @@ static gbk_status lm_batched(const Geom &g, int n_gal, const gbk_obs *obs, const
     lm_launch_init(a, o->lambda0, st);
     TangentArgs ta = {};
     if (pl.tangent) {
+        if (t.sp) return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves one geometry per batch");
+        const Geom &g = *t.g;
         if (!tangent_config(g, &ta.cs, &ta.band))
             return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
         ta.g = g;
@@ -381,14 +406,14 @@ static gbk_status lm_batched(const Geom &g, int n_gal, const gbk_obs *obs, const
     }
     // The first iteration runs eagerly (it also settles the kernels' launch
     // configurations); the rest replay a captured graph.
-    gbk_status s = lm_iteration(g, a, obs, pl.tangent, ta, st);
+    gbk_status s = lm_iteration(t, a, obs, pl.tangent, ta, st);
     if (s) return s;
     int32_t h_active = n_gal;
     int done_iters = 1;
     if (o->max_iter > 1) {
         if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
             return cuda_fail(e, "LM: begin graph capture");
-        s = lm_iteration(g, a, obs, pl.tangent, ta, st);
+        s = lm_iteration(t, a, obs, pl.tangent, ta, st);
         e = cudaStreamEndCapture(st, &cg.graph);
         if (s) return s;
         if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");
@@ -412,6 +437,45 @@ static gbk_status lm_batched(const Geom &g, int n_gal, const gbk_obs *obs, const
         (e = cudaStreamSynchronize(st)))
         return cuda_fail(e, "LM: results");
     return ok();
+}
+
+// Survey batches: the batched mode over a ragged plan, or the plain mode one
+// galaxy (and geometry) at a time.
+size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_lm_opts *o)
+{
+    LmPlan pl;
+    if (lm_plan(o, &pl)) return 0;
+    if (pl.tangent) {
+        fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves one geometry per batch; use finite differences");
+        return 0;
+    }
+    if (o->mode == GBK_LM_PLAIN) {
+        size_t m = 256;
+        for (const Geom &g : sp.geo) m = std::max(m, lm_layout(g, 1, pl).total);
+        return m;
+    }
+    return lm_layout_pix((size_t)sp.total_pix(), sp.n_gal, pl).total;
+}
+
+gbk_status lm_survey(SurveyPlan &sp, const gbk_obs *obs, const double *lo, const double *hi, double *params,
+                     const gbk_lm_opts *o, double *chi2_out, int32_t *iters_out, int32_t *status_out, char *ws,
+                     size_t ws_bytes, cudaStream_t st)
+{
+    LmPlan pl;
+    gbk_status s = lm_plan(o, &pl);
+    if (s) return s;
+    if (ws_bytes < lm_survey_workspace(sp, o)) return fail(GBK_EWORKSPACE, "survey LM workspace too small");
+    if (o->mode == GBK_LM_PLAIN) {
+        for (int i = 0; i < sp.n_gal; ++i) {
+            const size_t q = (size_t)i * GBK_NPAR;
+            s = lm_plain(sp.geo[i], 1, obs + i, lo + q, hi + q, params + q, o, pl, chi2_out + i, iters_out + i,
+                         status_out + i, ws, st);
+            if (s) return s;
+        }
+        return ok();
+    }
+    EvalTarget t = {nullptr, &sp};
+    return lm_batched(t, sp.n_gal, obs, lo, hi, params, o, pl, chi2_out, iters_out, status_out, ws, st);
 }
 
 }  // namespace gbk
@@ -457,7 +521,8 @@ gbk_status gbk_fit_lm(const gbk_geom *gin, int32_t n_gal, const gbk_obs *obs, co
     cudaStream_t st = (cudaStream_t)stream;
     if (opts->mode == GBK_LM_PLAIN)
         return lm_plain(g, n_gal, obs, lo, hi, params, opts, pl, chi2_out, iters_out, status_out, (char *)workspace, st);
-    return lm_batched(g, n_gal, obs, lo, hi, params, opts, pl, chi2_out, iters_out, status_out, (char *)workspace, st);
+    EvalTarget t = {&g, nullptr};
+    return lm_batched(t, n_gal, obs, lo, hi, params, opts, pl, chi2_out, iters_out, status_out, (char *)workspace, st);
 }
 
 }  // extern "C"

@@ -1,0 +1,39 @@
+// survey.h -- ragged batches: galaxies of different geometry in one batch
+// (host-side plan and launcher of the fused kernel's ragged mode).
+#pragma once
+
+#include <vector>
+
+#include "gbk_internal.cuh"
+
+namespace gbk {
+
+// Galaxies served by one launch: the same cluster size and block size.
+struct SurveyClass {
+    int cs, threads;
+    int beg, end;  // range of SurveyPlan::order
+    size_t smem;   // dynamic shared memory of the launch
+};
+
+struct SurveyPlan {
+    int n_gal = 0;
+    std::vector<Geom> geo;          // derived geometry per galaxy
+    std::vector<int64_t> pix_off;   // n_gal + 1 prefix sums of nx * ny
+    std::vector<int32_t> order;     // galaxies grouped by class, costliest first
+    std::vector<SurveyClass> classes;
+    size_t table_bytes = 0;         // device tables at the start of the workspace
+    // device copies (inside the workspace) after survey_upload
+    Geom *d_geo = nullptr;
+    int64_t *d_pix_off = nullptr;
+    int32_t *d_order = nullptr;
+    int64_t total_pix() const { return pix_off.empty() ? 0 : pix_off.back(); }
+};
+
+gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp);
+gbk_status survey_upload(SurveyPlan *sp, char *ws, cudaStream_t st);
+// Models gal * mpg + s (s < mpg) of every galaxy: chi2 [n_gal * mpg] and the
+// packed maps / residuals (galaxy gal at pixel offset pix_off[gal] * mpg).
+gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, const gbk_obs *obs_list,
+                       const int32_t *skip, float *maps, double *chi2, float *resid, cudaStream_t st);
+
+}  // namespace gbk

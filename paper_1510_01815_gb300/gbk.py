@@ -93,6 +93,10 @@ def lib():
                                         ctypes.POINTER(CNsOpts), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), vp, sz, vp]),
+            "gbk_survey_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
+            "gbk_survey_eval": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "gbk_survey_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz,
+                                        vp]),
             "gbk_device_status": (i32, [ctypes.POINTER(ctypes.c_int32)]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
@@ -109,7 +113,8 @@ def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
-            "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_device_status",
+            "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
+            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_device_status",
             "gbk_last_error", "gbk_version"]
 
 
@@ -306,6 +311,82 @@ def fit_lm(geom, obs_list, p0, lo, hi, opts, device="cuda", stream=None):
     nb = gbk_fit_lm_workspace_bytes(geom, n, opts)
     ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
     gbk_fit_lm(geom, obs_dev, dlo, dhi, p, opts, chi2, iters, status, ws, stream)
+    return p.cpu().numpy(), chi2.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
+
+
+def cgeoms(geoms):
+    """A host array of gbk_geom structs, one per galaxy."""
+    return (CGeom * len(geoms))(*[cgeom(g) for g in geoms])
+
+
+def survey_pix_offsets(geoms):
+    """Packed pixel offsets P_i = sum_{j<i} nx_j ny_j (length n + 1)."""
+    off = [0]
+    for g in geoms:
+        off.append(off[-1] + int(g.nx) * int(g.ny))
+    return off
+
+
+def gbk_survey_workspace_bytes(geoms, opts=None):
+    arr = cgeoms(geoms)
+    nb = lib().gbk_survey_workspace_bytes(arr, len(geoms), ctypes.byref(opts) if opts is not None else None)
+    if nb == 0 and len(geoms) > 0:
+        err = lib().gbk_last_error().decode()
+        if err:
+            raise GbkError(GBK_EINVAL, err)
+    return nb
+
+
+def gbk_survey_eval(geoms, params, obs_dev=None, maps=None, chi2=None, resid=None, workspace=None, stream=None):
+    arr = cgeoms(geoms)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_survey_eval(arr, len(geoms), _ptr(params, torch.float64, "params"),
+                                 _ptr(obs_dev, torch.uint8, "obs"), _ptr(maps, torch.float32, "maps"),
+                                 _ptr(chi2, torch.float64, "chi2"), _ptr(resid, torch.float32, "resid"),
+                                 _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def gbk_survey_fit_lm(geoms, obs_dev, lo, hi, params, opts, chi2_out, iters_out, status_out, workspace,
+                      stream=None):
+    arr = cgeoms(geoms)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_survey_fit_lm(arr, len(geoms), _ptr(obs_dev, torch.uint8, "obs"),
+                                   _ptr(lo, torch.float64, "lo"), _ptr(hi, torch.float64, "hi"),
+                                   _ptr(params, torch.float64, "params"), ctypes.byref(opts),
+                                   _ptr(chi2_out, torch.float64, "chi2_out"),
+                                   _ptr(iters_out, torch.int32, "iters_out"),
+                                   _ptr(status_out, torch.int32, "status_out"), _ptr(workspace, None, "workspace"),
+                                   ws_bytes, _stream(stream)))
+
+
+def survey_eval(geoms, params, obs_list=None, want_maps=True, want_resid=False, device="cuda", stream=None):
+    """Convenience: (maps per galaxy [3][ny][nx] or None, chi2 [n] or None,
+    resid per galaxy [2][ny][nx] or None) for a ragged batch."""
+    params = torch.as_tensor(params, dtype=torch.float64).reshape(len(geoms), NPAR).to(device).contiguous()
+    off = survey_pix_offsets(geoms)
+    maps = torch.empty(3 * off[-1], dtype=torch.float32, device=device) if want_maps else None
+    obs_dev, _keep = obs_array(obs_list, device) if obs_list is not None else (None, None)
+    c2 = torch.empty(len(geoms), dtype=torch.float64, device=device) if obs_list is not None else None
+    res = torch.empty(2 * off[-1], dtype=torch.float32, device=device) if want_resid else None
+    ws = torch.empty(max(gbk_survey_workspace_bytes(geoms), 1), dtype=torch.uint8, device=device)
+    gbk_survey_eval(geoms, params, obs_dev, maps, c2, res, ws, stream)
+    split = lambda t, k: [t[k * off[i]:k * off[i + 1]].view(k, g.ny, g.nx) for i, g in enumerate(geoms)]
+    return (split(maps, 3) if maps is not None else None, c2, split(res, 2) if res is not None else None)
+
+
+def survey_fit_lm(geoms, obs_list, p0, lo, hi, opts, device="cuda", stream=None):
+    """Convenience: fits a ragged batch; returns (params, chi2, iters,
+    status) as numpy arrays."""
+    import numpy as np
+    n = len(geoms)
+    obs_dev, _keep = obs_array(obs_list, device)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(n, NPAR)).to(device)
+    p, dlo, dhi = t(p0), t(lo), t(hi)
+    chi2 = torch.empty(n, dtype=torch.float64, device=device)
+    iters = torch.empty(n, dtype=torch.int32, device=device)
+    status = torch.empty(n, dtype=torch.int32, device=device)
+    ws = torch.empty(max(gbk_survey_workspace_bytes(geoms, opts), 1), dtype=torch.uint8, device=device)
+    gbk_survey_fit_lm(geoms, obs_dev, dlo, dhi, p, opts, chi2, iters, status, ws, stream)
     return p.cpu().numpy(), chi2.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
 
 

@@ -146,3 +146,31 @@ def test_jacobian_and_lm_validation(gbk):
     cg = gbk.cgeom(g)
     st = gbk.lib().gbk_jacobian(ctypes.byref(cg), 1, None, None, 0, None, None, None, None, None, None)
     assert st == gbk.GBK_EINVAL
+
+
+def test_survey_host_logic(gbk):
+    """Survey planning is host-only: sizes, validation and the rule that the
+    workspace holds the geometry tables plus the LM state."""
+    from paper_1510_01815_gb300 import synth
+    import numpy as np
+    gal = synth.draw_survey(np.random.default_rng(4), 16)
+    geoms = [g for g, _ in gal]
+    tables = gbk.gbk_survey_workspace_bytes(geoms)
+    assert tables >= 16 * 64 and tables % 256 == 0
+    lm = gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts())
+    pix = sum(g.nx * g.ny for g in geoms)
+    # FD batch of 1 + 8 models per galaxy, two residual maps each
+    assert lm >= tables + 9 * 2 * pix * 4
+    # the plain mode needs room for one galaxy at a time
+    assert gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(mode=gbk.LM_PLAIN)) < lm
+    assert gbk.gbk_survey_workspace_bytes([], None) == 0
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT))
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_workspace_bytes(geoms + [SINGLE_GEOM.with_(upsample=2)])
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_workspace_bytes(geoms + [SINGLE_GEOM.with_(nx=0)])
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_workspace_bytes([SINGLE_GEOM.with_(nx=2048, ny=2048)])
+    cg = gbk.cgeoms(geoms)
+    assert gbk.lib().gbk_survey_eval(cg, len(geoms), None, None, None, None, None, None, 0, None) == gbk.GBK_EINVAL

@@ -1,0 +1,184 @@
+"""Ragged survey batches (gbk_survey_eval, gbk_survey_fit_lm): galaxies of
+different cube size, channel width, PSF and LSF in one batch.  Each galaxy
+is checked against the FP64 oracle evaluated with its own geometry, and
+against the single-geometry entry points."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from cases import check_maps, chi2_bound, make_obs, ogeom
+from paper_1510_01815_gb300 import synth
+from paper_1510_01815_gb300.synth import Geometry
+
+pytestmark = pytest.mark.gpu
+
+# Small but varied: odd and non-square sizes, PSF radius 0..7, LSF window
+# 1..19 channels, both LSF modes, a non-zero band centre, and one cube large
+# enough to need a two-CTA cluster.
+GEOMS = [
+    Geometry(24, 24, 32, 20.0, 0.0, 4.0, 30.0),
+    Geometry(31, 27, 40, 15.0, 0.0, 2.5, 45.0),
+    Geometry(40, 40, 48, 12.0, 0.0, 4.0, 60.0),
+    Geometry(17, 17, 33, 25.0, 10.0, 3.0, 20.0, lsf_mode=1),
+    Geometry(20, 36, 24, 30.0, 0.0, 0.0, 0.0),
+    Geometry(64, 64, 32, 30.0, 0.0, 4.0, 40.0),
+    Geometry(48, 48, 64, 10.0, 0.0, 4.0, 25.0),
+    Geometry(9, 5, 7, 40.0, 0.0, 2.0, 50.0),
+]
+
+
+def truth_for(g, rng):
+    return synth.params(rng.uniform(0.4, 0.6) * (g.nx - 1), rng.uniform(0.4, 0.6) * (g.ny - 1),
+                        rng.uniform(0.0, 45.0), rng.uniform(25.0, 70.0), g.vc + rng.uniform(-5.0, 5.0),
+                        rng.uniform(80.0, 200.0), rng.uniform(1.5, 5.0), rng.uniform(20.0, 60.0), 1.0,
+                        rng.uniform(4.0, 10.0))
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1510_01815_gb300 import build, gbk
+    build.build()
+    assert torch.cuda.is_available()
+    return gbk
+
+
+@pytest.fixture(scope="module")
+def survey():
+    rng = np.random.default_rng(41)
+    ps = np.array([truth_for(g, rng) for g in GEOMS])
+    obs = [make_obs(g, synth.perturb(rng, p, frac=0.05), seed=100 + i) for i, (g, p) in enumerate(zip(GEOMS, ps))]
+    return ps, obs
+
+
+def _dobs(G, o):
+    return G.Obs.from_numpy(o.v, o.s, o.w_v, o.w_s, o.mask)
+
+
+def test_survey_maps_vs_oracle(G, survey):
+    ps, _ = survey
+    maps, _, _ = G.survey_eval(GEOMS, ps)
+    for i, g in enumerate(GEOMS):
+        ref = oracle.evaluate(ogeom(g), ps[i])
+        check_maps(maps[i].cpu().numpy()[None], ref[None], ps[i:i + 1], label="survey galaxy %d" % i)
+
+
+def test_survey_chi2_vs_oracle(G, survey):
+    ps, obs = survey
+    dobs = [_dobs(G, o) for o in obs]
+    maps, c2, res = G.survey_eval(GEOMS, ps, dobs, want_resid=True)
+    c2 = c2.cpu().numpy()
+    for i, g in enumerate(GEOMS):
+        ref_maps = oracle.evaluate(ogeom(g), ps[i])
+        ref_c, ref_r = oracle.chi2_maps(ref_maps, obs[i], want_resid=True)
+        b = chi2_bound(ref_maps, maps[i].cpu().numpy(), obs[i], ref_c)
+        assert abs(c2[i] - ref_c) <= b, (i, c2[i], ref_c, b)
+        # residuals of the GPU maps, from the oracle's residual definition
+        _, own_r = oracle.chi2_maps(maps[i].cpu().numpy().astype(np.float64), obs[i], want_resid=True)
+        np.testing.assert_allclose(res[i].cpu().numpy(), own_r, rtol=1e-5, atol=1e-5)
+
+
+def test_survey_equals_single_geometry_calls(G, survey):
+    """Every galaxy of the ragged batch gets what gbk_chi2 gives it alone."""
+    ps, obs = survey
+    dobs = [_dobs(G, o) for o in obs]
+    maps, c2, res = G.survey_eval(GEOMS, ps, dobs, want_resid=True)
+    for i, g in enumerate(GEOMS):
+        one = G.eval_maps(g, torch.as_tensor(ps[i:i + 1]))[0]
+        np.testing.assert_allclose(maps[i].cpu().numpy(), one.cpu().numpy(), rtol=2e-6, atol=1e-6 * float(one[0].max()))
+        c_one, r_one = G.chi2(g, torch.as_tensor(ps[i:i + 1]), dobs[i], flags=G.PATH_FUSED, want_resid=True)
+        assert abs(float(c2[i]) - float(c_one[0])) <= 1e-5 * abs(float(c_one[0])) + 1e-9
+        np.testing.assert_allclose(res[i].cpu().numpy(), r_one[0].cpu().numpy(), rtol=1e-4, atol=1e-4)
+
+
+def test_survey_order_independent(G, survey):
+    """Reversing the galaxy list permutes the outputs and changes nothing else."""
+    ps, obs = survey
+    dobs = [_dobs(G, o) for o in obs]
+    _, c_fwd, _ = G.survey_eval(GEOMS, ps, dobs, want_maps=False)
+    _, c_rev, _ = G.survey_eval(GEOMS[::-1], ps[::-1].copy(), dobs[::-1], want_maps=False)
+    np.testing.assert_array_equal(c_fwd.cpu().numpy(), c_rev.cpu().numpy()[::-1])
+
+
+def test_survey_drawn_sizes(G):
+    """Galaxies drawn like the survey workload (24-96 spaxels, 32-128
+    channels, PSF 4 px): chi2 of each equals its single-geometry chi2."""
+    rng = np.random.default_rng(4)
+    gal = synth.draw_survey(rng, 24)
+    geoms = [g for g, _ in gal]
+    ps = np.array([p for _, p in gal])
+    obs = []
+    for g, p in gal:
+        v = np.full((g.ny, g.nx), 0.0, np.float32)
+        wv, ws = synth.weights((g.ny, g.nx), 5.0)
+        obs.append(G.Obs.from_numpy(v, v + 30.0, wv, ws, np.ones((g.ny, g.nx), np.uint8)))
+    _, c2, _ = G.survey_eval(geoms, ps, obs, want_maps=False)
+    for i, g in enumerate(geoms):
+        c_one = G.chi2(g, torch.as_tensor(ps[i:i + 1]), obs[i], flags=G.PATH_FUSED)
+        assert abs(float(c2[i]) - float(c_one[0])) <= 1e-5 * abs(float(c_one[0])), i
+
+
+def _bounds(g, p):
+    lo, hi = np.array(p, dtype=np.float64), np.array(p, dtype=np.float64)
+    lo[synth.X0], hi[synth.X0] = 0.0, g.nx - 1.0
+    lo[synth.Y0], hi[synth.Y0] = 0.0, g.ny - 1.0
+    lo[synth.PA], hi[synth.PA] = -360.0, 720.0
+    lo[synth.INCL], hi[synth.INCL] = 1.0, 89.0
+    lo[synth.VSYS], hi[synth.VSYS] = -200.0, 200.0
+    lo[synth.VMAX], hi[synth.VMAX] = 1.0, 600.0
+    lo[synth.RT], hi[synth.RT] = 0.05, 30.0
+    lo[synth.SIG0], hi[synth.SIG0] = 1.0, 300.0
+    return lo, hi
+
+
+def _noiseless(G, g, p):
+    m = oracle.evaluate(ogeom(g), p)
+    wv, ws = synth.weights((g.ny, g.nx), 5.0)
+    return G.Obs.from_numpy(m[1].astype(np.float32), m[2].astype(np.float32), wv, ws,
+                            np.ones((g.ny, g.nx), np.uint8))
+
+
+FIT_GEOMS = GEOMS[:4] + [GEOMS[6]]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_survey_fit_recovers(G, mode):
+    """Noiseless galaxies of different geometry from 20 %-perturbed starts:
+    V_t within 2 km/s and PA within 1 degree (Sec. 4.1 thresholds)."""
+    rng = np.random.default_rng(7)
+    ps = [truth_for(g, rng) for g in FIT_GEOMS]
+    for p in ps:
+        p[synth.INCL] = rng.uniform(40.0, 65.0)
+        p[synth.VMAX] = rng.uniform(120.0, 200.0)
+    obs = [_noiseless(G, g, p) for g, p in zip(FIT_GEOMS, ps)]
+    lo, hi = zip(*[_bounds(g, p) for g, p in zip(FIT_GEOMS, ps)])
+    p0 = [synth.perturb(rng, p, synth.FREE_DEFAULT, 0.2, l, h) for p, l, h in zip(ps, lo, hi)]
+    opts = G.lm_opts(max_iter=100, jacobian=G.JAC_FD_FORWARD, mode=mode)
+    q, c, it, st = G.survey_fit_lm(FIT_GEOMS, obs, p0, lo, hi, opts)
+    ps = np.array(ps)
+    assert np.all(np.isin(st, [1, 2])), (st, it)
+    assert np.all(np.abs(q[:, synth.VMAX] - ps[:, synth.VMAX]) < 2.0), (q[:, synth.VMAX], ps[:, synth.VMAX])
+    assert np.all(np.abs(q[:, synth.PA] - ps[:, synth.PA]) < 1.0), (q[:, synth.PA], ps[:, synth.PA])
+
+
+def test_survey_fit_matches_single_geometry_fits(G):
+    """Batched survey LM of each galaxy = gbk_fit_lm of that galaxy alone."""
+    rng = np.random.default_rng(9)
+    ps = [truth_for(g, rng) for g in FIT_GEOMS]
+    obs = [_noiseless(G, g, p) for g, p in zip(FIT_GEOMS, ps)]
+    lo, hi = zip(*[_bounds(g, p) for g, p in zip(FIT_GEOMS, ps)])
+    p0 = [synth.perturb(rng, p, synth.FREE_DEFAULT, 0.1, l, h) for p, l, h in zip(ps, lo, hi)]
+    opts = G.lm_opts(max_iter=60)
+    q, c, it, st = G.survey_fit_lm(FIT_GEOMS, obs, p0, lo, hi, opts)
+    for i, g in enumerate(FIT_GEOMS):
+        q1, c1, it1, st1 = G.fit_lm(g, [obs[i]], p0[i][None], lo[i][None], hi[i][None], opts)
+        scale = np.maximum(np.abs(q1[0]), 1.0)
+        assert np.all(np.abs(q[i] - q1[0]) <= 1e-3 * scale), (i, q[i], q1[0])
+
+
+def test_survey_rejects_tangent_and_large(G):
+    g = GEOMS[0]
+    with pytest.raises(G.GbkError):
+        G.gbk_survey_workspace_bytes([g], G.lm_opts(jacobian=G.JAC_TANGENT))
+    with pytest.raises(G.GbkError):
+        G.gbk_survey_workspace_bytes([g, Geometry(1024, 1024, 8, 20.0, 0.0, 4.0, 30.0)])
