@@ -67,6 +67,26 @@ def parse():
     return ap.parse_args()
 
 
+def job_throughput(local_ms, units_per_rank, dist=None):
+    """Whole-job throughput of a weak-scaling run: the units every rank
+    processed, over the slowest rank's time.  Returns (units/s, max ms)."""
+    import torch
+    world, t = 1, float(local_ms)
+    if dist is not None:
+        world = dist.get_world_size()
+        tt = torch.tensor([t], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * units_per_rank / (t * 1e-3), t
+
+
+def rank_pool(rank, n, steps):
+    """Each rank's own parameter sets (Fabry-Perot prior): disjoint seeds,
+    so no two ranks evaluate the same models."""
+    rng = np.random.default_rng(7000 + rank)
+    return synth.draw_fp_params(rng, n * steps).reshape(steps, n, synth.NPAR)
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -376,8 +396,7 @@ def run_gbk(args):
     K, W = args.steps, args.warmup
     p_true, obs_np = make_galaxy(gbk, torch, g, 2015, dev)
     obs = gbk.Obs.from_numpy(*obs_np, device=dev)
-    rng = np.random.default_rng(7000 + rank)
-    pool_np = synth.draw_fp_params(rng, n * (K + W)).reshape(K + W, n, synth.NPAR)
+    pool_np = rank_pool(rank, n, K + W)
     pool = torch.from_numpy(pool_np).to(dev)
     chi2 = torch.empty((K + W, n), dtype=torch.float64, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -424,12 +443,8 @@ def run_gbk(args):
     times = [starts[k].elapsed_time(ends[k]) for k in range(K)]
     total_ms = float(sum(times))
     assert torch.isfinite(chi2[W:]).all(), "non-finite chi2 in the timed steps"
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = job_throughput(total_ms, n * K, dist)
     ms_step = total_ms / K
-    value = ws * n * K / (total_ms * 1e-3)
 
     out = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": K, "warmup": W,
            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -515,11 +530,8 @@ def run_gbk(args):
         b.synchronize()
         e_ms += a.elapsed_time(b)
     h2d = n * synth.NPAR * 8 + sum(int(h.numel() * h.element_size()) for h in pin_obs)
-    if dist:
-        t = torch.tensor([e_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-    out["e2e"] = {"value": ws * n * K / (e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+    e_value, e_ms = job_throughput(e_ms, n * K, dist)
+    out["e2e"] = {"value": e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                   "d2h_bytes_per_step": n * 8}
     ok = np.allclose(pin_chi2[W:].numpy(), chi2[W:].cpu().numpy(), rtol=0, atol=0)
     out["e2e"]["matches_device_run"] = bool(ok)
