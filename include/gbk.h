@@ -380,10 +380,29 @@ GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ffm
                                         double *ex2_lane_ops_per_s, void *stream);
 
 /* Reads and clears the library's device status word (host output): 0 when
- * every bounded device-side wait since the last call completed; 1 when a
- * TMA load of the staged convolution did not complete in time (the affected
- * blocks stopped early and their output is incomplete).  Synchronising. */
+ * every bounded device-side wait since the last call completed; bit 0 set
+ * when a TMA load of the staged convolution did not complete in time, bit 1
+ * when a pipeline wait of the tensor-core GEMM did not (the affected blocks
+ * stopped early and their output is incomplete).  Synchronising. */
 GBK_API gbk_status gbk_device_status(int32_t *status);
+
+/* ------------------------------------------------------------------------
+ * BF16 tensor-core GEMM (tcgen05, TMA-fed, FP32 accumulation in tensor
+ * memory), the dense layer of the CNN that seeds the fits.  The paper has
+ * no counterpart: it is the building block of the learned initial guess
+ * that replaces the heuristic starting point of Sec. 2.1.9.
+ *   D[m][n] = alpha * sum_k A[m][k] B[n][k] (+ bias[n]) (ReLU if relu != 0)
+ *             (set to 0 where mask[m][n] <= 0, if mask != NULL)
+ *  A        device BF16 [M][lda], lda >= K, lda % 8 == 0, 16-byte aligned
+ *  B        device BF16 [N][ldb], ldb >= K, ldb % 8 == 0, 16-byte aligned
+ *  bias     device FP32 [N] or NULL
+ *  mask     device BF16 [M][ldm] or NULL
+ *  out_bf16 device BF16 [M][ldo] or NULL; out_f32 device FP32 [M][ldo] or
+ *           NULL (at least one)
+ * Asynchronous on `stream`; GBK_EINVAL on bad sizes or pointers. */
+GBK_API gbk_status gbk_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, int32_t lda, const void *B,
+                                 int32_t ldb, const float *bias, int32_t relu, const void *mask, int32_t ldm,
+                                 float alpha, void *out_bf16, float *out_f32, int32_t ldo, void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 GBK_API const char *gbk_last_error(void);

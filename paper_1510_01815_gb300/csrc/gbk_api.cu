@@ -8,6 +8,7 @@
 
 #include "gbk_api_internal.h"
 #include "k_fused.h"
+#include "k_gemm.h"
 #include "k_staged.h"
 
 namespace gbk {
@@ -147,6 +148,16 @@ extern "C" {
 const char *gbk_last_error(void) { return t_last_error.c_str(); }
 
 const char *gbk_version(void) { return "gbk 0.1 (sm_103a)"; }
+
+gbk_status gbk_device_status(int32_t *status)
+{
+    if (!status) return fail(GBK_EINVAL, "status is NULL");
+    int c = 0, g = 0;
+    gbk_status s;
+    if ((s = conv_status_read(&c)) || (s = gemm_status_read(&g))) return s;
+    *status = (c ? 1 : 0) | (g ? 2 : 0);
+    return ok();
+}
 
 size_t gbk_workspace_bytes(const gbk_geom *gin, int32_t n_models, uint32_t flags)
 {

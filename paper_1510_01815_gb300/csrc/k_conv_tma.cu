@@ -309,17 +309,13 @@ gbk_status launch_conv_tma(const StagedArgs &sa, cudaStream_t st)
     }
 }
 
-}  // namespace gbk
-
-using namespace gbk;
-
-extern "C" gbk_status gbk_device_status(int32_t *status)
+gbk_status conv_status_read(int *v)
 {
-    if (!status) return fail(GBK_EINVAL, "status is NULL");
-    int v = 0, zero = 0;
-    cudaError_t e = cudaMemcpyFromSymbol(&v, g_conv_status, sizeof(int));
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_conv_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_conv_status, &zero, sizeof(int));
-    if (e != cudaSuccess) return cuda_fail(e, "reading the device status");
-    *status = v;
-    return ok();
+    if (e != cudaSuccess) return cuda_fail(e, "reading the convolution status");
+    return GBK_OK;
 }
+
+}  // namespace gbk

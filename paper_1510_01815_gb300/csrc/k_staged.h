@@ -33,4 +33,6 @@ gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t st
 cudaError_t launch_chi2_maps(int nx, int ny, int n_models, const float *maps, const gbk_obs &obs,
                              double *chi2, float *resid, cudaStream_t stream);
 
+gbk_status conv_status_read(int *v);
+
 }  // namespace gbk

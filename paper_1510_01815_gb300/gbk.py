@@ -98,6 +98,8 @@ def lib():
             "gbk_survey_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz,
                                         vp]),
             "gbk_device_status": (i32, [ctypes.POINTER(ctypes.c_int32)]),
+            "gbk_gemm_bf16": (i32, [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, i32, ctypes.c_float, vp, vp, i32,
+                                    vp]),
             "gbk_last_error": (ctypes.c_char_p, []),
             "gbk_version": (ctypes.c_char_p, []),
         }
@@ -114,7 +116,7 @@ def exported_symbols():
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
-            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_device_status",
+            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_device_status", "gbk_gemm_bf16",
             "gbk_last_error", "gbk_version"]
 
 
@@ -388,6 +390,32 @@ def survey_fit_lm(geoms, obs_list, p0, lo, hi, opts, device="cuda", stream=None)
     ws = torch.empty(max(gbk_survey_workspace_bytes(geoms, opts), 1), dtype=torch.uint8, device=device)
     gbk_survey_fit_lm(geoms, obs_dev, dlo, dhi, p, opts, chi2, iters, status, ws, stream)
     return p.cpu().numpy(), chi2.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
+
+
+def gbk_gemm_bf16(A, B, out_bf16=None, out_f32=None, bias=None, relu=False, mask=None, alpha=1.0, stream=None):
+    """D = alpha A B^T (+ bias) (ReLU) (masked) on the tensor cores; A [M][K],
+    B [N][K] BF16 (row strides may exceed K); outputs [M][ldo]."""
+    M, K = A.shape
+    N = B.shape[0]
+    out = out_bf16 if out_bf16 is not None else out_f32
+    ldo = out.stride(0)
+    _check(lib().gbk_gemm_bf16(int(M), int(N), int(K), _strided(A, torch.bfloat16, "A"), int(A.stride(0)),
+                               _strided(B, torch.bfloat16, "B"), int(B.stride(0)), _ptr(bias, torch.float32, "bias"),
+                               int(bool(relu)), _strided(mask, torch.bfloat16, "mask"),
+                               int(mask.stride(0)) if mask is not None else 0, float(alpha),
+                               _strided(out_bf16, torch.bfloat16, "out_bf16"), _strided(out_f32, torch.float32, "out_f32"),
+                               int(ldo), _stream(stream)))
+
+
+def _strided(t, dtype, name):
+    """Pointer of a row-major 2-D tensor whose rows may be padded."""
+    if t is None:
+        return None
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("%s must be 2-D with unit column stride" % name)
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def gbk_jacobian(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), cot=None, jtj=None, jtv=None, chi2=None,

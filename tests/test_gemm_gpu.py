@@ -1,0 +1,81 @@
+"""The tcgen05 BF16 GEMM (gbk_gemm_bf16) against FP64 products of the same
+BF16 inputs.  The products of two BF16 numbers are exact in FP32, so the
+only error is the FP32 accumulation (relative ~K * 2^-24) and, for BF16
+outputs, the final rounding (2^-8)."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1510_01815_gb300 import build, gbk
+    build.build()
+    assert torch.cuda.is_available()
+    return gbk
+
+
+def _rand(shape, seed, scale=1.0):
+    g = torch.Generator().manual_seed(seed)
+    return (torch.randn(shape, generator=g, dtype=torch.float32) * scale).to(torch.bfloat16)
+
+
+def _ref(A, B):
+    return A.double() @ B.double().T
+
+
+SHAPES = [(128, 128, 64), (128, 16, 64), (300, 80, 200), (1000, 256, 512), (4096, 64, 32), (77, 11, 8),
+          (513, 144, 4096), (256, 128, 1000)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_gemm_f32_out(G, M, N, K):
+    A, B = _rand((M, K), 1), _rand((N, K), 2)
+    out = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    G.gbk_gemm_bf16(A.cuda(), B.cuda(), out_f32=out)
+    ref = _ref(A, B)
+    err = (out.cpu().double() - ref).abs().max().item()
+    scale = (A.double().abs() @ B.double().abs().T).max().item()
+    assert err <= 2e-6 * scale + 1e-6, (err, scale)
+    st = G.gbk_device_status()
+    assert st == 0
+
+
+def test_gemm_epilogue(G):
+    M, N, K = 700, 96, 192
+    A, B = _rand((M, K), 3), _rand((N, K), 4)
+    bias = torch.randn(N, generator=torch.Generator().manual_seed(5))
+    mask = _rand((M, N), 6)
+    out_b = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+    out_f = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    G.gbk_gemm_bf16(A.cuda(), B.cuda(), out_bf16=out_b, out_f32=out_f, bias=bias.cuda(), relu=True,
+                    mask=mask.cuda(), alpha=0.5)
+    ref = 0.5 * _ref(A, B) + bias.double()
+    ref = torch.clamp(ref, min=0.0) * (mask.double() > 0)
+    scale = 0.5 * (A.double().abs() @ B.double().abs().T).max().item()
+    assert (out_f.cpu().double() - ref).abs().max().item() <= 2e-6 * scale + 1e-6
+    # BF16 output = FP32 result rounded to nearest even
+    np.testing.assert_array_equal(out_b.cpu().float().numpy(), out_f.cpu().to(torch.bfloat16).float().numpy())
+
+
+def test_gemm_strided_operands(G):
+    """Row strides larger than K (views into wider buffers) and ldo > N."""
+    M, N, K = 256, 48, 72
+    Aw, Bw = _rand((M, 136), 7), _rand((N, 80), 8)
+    A, B = Aw[:, :K], Bw[:, :K]
+    outw = torch.zeros((M, 64), dtype=torch.float32, device="cuda")
+    G.gbk_gemm_bf16(Aw.cuda()[:, :K], Bw.cuda()[:, :K], out_f32=outw[:, :N])
+    ref = _ref(A, B)
+    scale = (A.double().abs() @ B.double().abs().T).max().item()
+    assert (outw[:, :N].cpu().double() - ref).abs().max().item() <= 2e-6 * scale + 1e-6
+    assert torch.all(outw[:, N:] == 0)
+
+
+def test_gemm_rejects_bad_strides(G):
+    A = torch.zeros((16, 12), dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros((16, 12), dtype=torch.bfloat16, device="cuda")
+    out = torch.zeros((16, 16), dtype=torch.float32, device="cuda")
+    with pytest.raises(G.GbkError):
+        G.gbk_gemm_bf16(A, B, out_f32=out)  # lda = 12 is not a multiple of 8
