@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--no-survey", action="store_true", help="skip the ragged survey-fit measurement")
     ap.add_argument("--survey-galaxies", type=int, default=2048)
     ap.add_argument("--survey-plain", type=int, default=64, help="galaxies the plain survey LM is timed on")
+    ap.add_argument("--no-cnn", action="store_true", help="skip the learned-seed (CNN) measurement")
+    ap.add_argument("--cnn-train", type=int, default=262144, help="training galaxies of the CNN seed")
+    ap.add_argument("--cnn-epochs", type=int, default=4)
+    ap.add_argument("--cnn-batch", type=int, default=1024)
+    ap.add_argument("--cnn-test", type=int, default=4096, help="held-out galaxies of the seed comparison")
     ap.add_argument("--path", default="fused", choices=["fused", "staged"],
                     help="fused (default) or staged (cube materialised in HBM) evaluation")
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
@@ -305,6 +310,139 @@ def run_survey(gbk, torch, n, n_plain, device):
     return out
 
 
+CNN_LAYER_MNK = ((256, 64, 48), (64, 128, 256), (16, 256, 512), (1, 256, 4096), (1, 16, 256))
+
+
+def cnn_flops_per_sample():
+    """GEMM flops of one training sample: forward, weight gradient (with the
+    bias column) and input gradient of every layer but the first."""
+    f = 0
+    for l, (rows, c, k) in enumerate(CNN_LAYER_MNK):
+        f += 2 * rows * c * k            # forward
+        f += 2 * rows * c * (k + 1)      # dW (and db)
+        if l > 0:
+            f += 2 * rows * c * k        # dX
+    return f
+
+
+def cnn_data(gbk, torch, n, seed, device, chunk=65536):
+    """n synthetic galaxies of the CNN workload: parameters from the prior,
+    maps from the library (64 x 64 x 64 cubes), observations with 5 km/s
+    noise and 2 % dead fibres from the library's counter-based streams."""
+    rng = np.random.default_rng(seed)
+    p = synth.draw_cnn_params(rng, n)
+    dp = torch.from_numpy(p).to(device)
+    v = torch.empty((n, 64, 64), dtype=torch.float32, device=device)
+    s = torch.empty_like(v)
+    m = torch.empty((n, 64, 64), dtype=torch.uint8, device=device)
+    t = torch.empty((n, 10), dtype=torch.float32, device=device)
+    for i in range(0, n, chunk):
+        j = min(n, i + chunk)
+        maps = gbk.eval_maps(synth.CNN_GEOM, dp[i:j], device=device)
+        gbk.gbk_cnn_synth_obs(maps, seed * 1000003 + i, 5.0, 0.02, v[i:j], s[i:j], m[i:j])
+        del maps
+    gbk.gbk_cnn_targets(dp, t)
+    return p, v, s, m, t
+
+
+def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device):
+    """Learned seed: train the CNN on synthetic maps, then compare batched LM
+    started from its predictions with LM started from 20 %-perturbed truths
+    on held-out galaxies (fits/s, iterations, recovery)."""
+    out = {"workload": "%d training + %d held-out galaxies, 64x64 maps of 64x64x64 cubes (dv 20, PSF 2.5 px, "
+                       "LSF 30 km/s), noise 5 / 5 sqrt(2) km/s, 2%% dead fibres" % (n_train, n_test)}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, v, s, m, t = cnn_data(gbk, torch, n_train, 11, device)
+    torch.cuda.synchronize()
+    out["data_seconds"] = time.perf_counter() - t0
+    net = gbk.CnnSeed(batch, seed=3, device=device)
+    steps_per_epoch = n_train // batch
+    lr0 = 1e-3
+    for w in range(3):  # warm-up steps (not timed)
+        net.train_step(v[:batch], s[:batch], m[:batch], t[:batch], lr0)
+    first_loss = float(net.loss)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    total = epochs * steps_per_epoch
+    for it in range(total):
+        i = (it % steps_per_epoch) * batch
+        lr = lr0 * (0.1 if it >= 0.8 * total else 1.0)
+        net.train_step(v[i:i + batch], s[i:i + batch], m[i:i + batch], t[i:i + batch], lr)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    flops = cnn_flops_per_sample() * batch * total
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    out["train"] = {"steps": total, "batch": batch, "epochs": epochs, "ms": ms, "samples_per_s": batch * total / (ms * 1e-3),
+                    "gemm_tflops": flops / (ms * 1e-3) / 1e12, "bf16_peak_tflops": peak,
+                    "tensor_frac": flops / (ms * 1e-3) / 1e12 / peak, "first_loss": first_loss,
+                    "final_loss": float(net.loss),
+                    "note": "whole training step (encode, 5 forward, 5+4 backward GEMMs, split-K sums, Adam) per "
+                            "launch sequence; flops count the GEMMs only; peak = measured cuBLAS bf16 sustained"}
+    del v, s, m, t
+    # held-out galaxies (seed 5)
+    ptest, vt, st, mt, _ = cnn_data(gbk, torch, n_test, 5, device)
+    torch.cuda.synchronize()
+    a.record()
+    pred = net.predict(vt, st, mt)
+    b.record()
+    b.synchronize()
+    out["predict"] = {"galaxies": n_test, "ms": a.elapsed_time(b)}
+    pred = pred.cpu().numpy()
+    g = synth.CNN_GEOM
+    wv, ws_ = synth.weights((64, 64), 5.0)
+    dwv, dws = torch.from_numpy(wv).to(device), torch.from_numpy(ws_).to(device)
+    obs = [gbk.Obs(vt[i], st[i], dwv, dws, mt[i]) for i in range(n_test)]
+    lo = np.tile(ptest[0], (n_test, 1))
+    hi = lo.copy()
+    lo[:, synth.X0], hi[:, synth.X0] = 0.0, 63.0
+    lo[:, synth.Y0], hi[:, synth.Y0] = 0.0, 63.0
+    lo[:, synth.PA], hi[:, synth.PA] = -360.0, 720.0
+    lo[:, synth.INCL], hi[:, synth.INCL] = 1.0, 89.0
+    lo[:, synth.VSYS], hi[:, synth.VSYS] = -200.0, 200.0
+    lo[:, synth.VMAX], hi[:, synth.VMAX] = 1.0, 600.0
+    lo[:, synth.RT], hi[:, synth.RT] = 0.05, 30.0
+    lo[:, synth.SIG0], hi[:, synth.SIG0] = 1.0, 300.0
+    for k in (synth.I0, synth.H):  # fixed at the truth in every fit (Sec. 2.1.9)
+        lo[:, k] = hi[:, k] = ptest[:, k]
+    seed_p = np.clip(pred, lo, hi)
+    seed_p[:, synth.I0], seed_p[:, synth.H] = ptest[:, synth.I0], ptest[:, synth.H]
+    rng = np.random.default_rng(55)
+    pert = np.array([synth.perturb(rng, ptest[i], FIT_FREE, 0.2, lo[i], hi[i]) for i in range(n_test)])
+
+    def err(q, tr):
+        dv = np.abs(q[:, synth.VMAX] - tr[:, synth.VMAX])
+        dpa = np.abs((q[:, synth.PA] - tr[:, synth.PA] + 180.0) % 360.0 - 180.0)
+        return dv, dpa
+
+    dv0, dpa0 = err(seed_p, ptest)
+    out["seed_error"] = {"median_dvmax": float(np.median(dv0)), "median_dpa": float(np.median(dpa0)),
+                         "p90_dvmax": float(np.percentile(dv0, 90)), "p90_dpa": float(np.percentile(dpa0, 90))}
+    for name, mode, start, sub in (("batched_cnn_seed", gbk.LM_BATCHED, seed_p, n_test),
+                                   ("batched_perturbed", gbk.LM_BATCHED, pert, n_test),
+                                   ("plain_perturbed", gbk.LM_PLAIN, pert, n_plain)):
+        opts = gbk.lm_opts(max_iter=200, jacobian=gbk.JAC_FD_FORWARD, mode=mode, free=FIT_FREE)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q, c, it, stt = gbk.fit_lm(g, obs[:sub], start[:sub], lo[:sub], hi[:sub], opts, device=device)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dv, dpa = err(q, ptest[:sub])
+        out[name] = {"galaxies": sub, "fits_per_s": sub / dt, "p50_iters": float(np.percentile(it, 50)),
+                     "p99_iters": float(np.percentile(it, 99)), "converged_frac": float(np.mean(np.isin(stt, [1, 2]))),
+                     "recovered_frac": float(np.mean((dv < 2.0) & (dpa < 1.0))),
+                     "median_dvmax": float(np.median(dv)), "median_dpa": float(np.median(dpa))}
+    out["batched_cnn_seed"]["speedup_vs_plain"] = out["batched_cnn_seed"]["fits_per_s"] / out["plain_perturbed"]["fits_per_s"]
+    return out
+
+
 def make_galaxy(gbk, torch, g, seed, device):
     """One synthetic Fabry-Perot galaxy: true parameters from the prior, maps
     from the library at those parameters, seeded noise (5 km/s on v,
@@ -544,6 +682,8 @@ def run_gbk(args):
                                 ("batched_tangent", gbk.LM_BATCHED, gbk.JAC_TANGENT)])
     if not args.no_survey:
         out["survey"] = run_survey(gbk, torch, args.survey_galaxies, args.survey_plain, dev)
+    if not args.no_cnn:
+        out["cnn"] = run_cnn(gbk, torch, args.cnn_train, args.cnn_epochs, args.cnn_batch, args.cnn_test, 64, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, obs_np, n, 2015)
     if rank == 0:

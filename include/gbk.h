@@ -404,6 +404,61 @@ GBK_API gbk_status gbk_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A,
                                  int32_t ldb, const float *bias, int32_t relu, const void *mask, int32_t ldm,
                                  float alpha, void *out_bf16, float *out_f32, int32_t ldo, void *stream);
 
+/* ------------------------------------------------------------------------
+ * CNN seed: a convolutional network that maps a galaxy's observed velocity
+ * and dispersion maps to model parameters, the learned replacement for the
+ * heuristic initial guess of the optimisers (Sec. 2.1.9).  Fixed
+ * architecture for 64 x 64 maps (all convolutions stride = kernel):
+ *   input 64x64x3 (v / 200 km/s, sigma / 100 km/s, mask; masked -> 0)
+ *   conv 4x4 -> 16x16x64, ReLU; conv 2x2 -> 8x8x128, ReLU;
+ *   conv 2x2 -> 4x4x256, ReLU; dense 4096 -> 256, ReLU; dense 256 -> 16.
+ * Parameters are one FP32 vector of gbk_cnn_param_count() floats: layer l
+ * is [C_l][K_l + 1] (weights W_l[o][k], bias in column K_l), layers in
+ * order; patch index k = (dy * p + dx) * C_in + c, and the dense layer's
+ * flatten index is morton(y, x) * 256 + c with morton interleaving the bits
+ * of x (even) and y (odd).  Outputs 0..9 are the normalised targets
+ *   (x0 - 31.5) / 8, (y0 - 31.5) / 8, cos PA, sin PA, (i - 50) / 20,
+ *   Vsys / 30, (Vmax - 175) / 75, (r_t - 4.5) / 2.5, (sigma0 - 45) / 25,
+ *   (h - 7) / 3;
+ * the loss is their mean squared error.  Dense products run on the tensor
+ * cores (BF16 operands, FP32 accumulation); master weights, gradients and
+ * Adam moments are FP32.  Maps are device FP32 [n][64][64] (v, sigma) and
+ * uint8 (mask, 1 = use); n and the batch B must be multiples of 8.  All
+ * calls are asynchronous on `stream`; the workspace of
+ * gbk_cnn_workspace_bytes(B) serves calls with exactly B samples.
+ * ------------------------------------------------------------------------ */
+GBK_API size_t gbk_cnn_param_count(void);
+GBK_API size_t gbk_cnn_workspace_bytes(int32_t batch);
+/* He-normal weights from a counter-based SplitMix64 stream, zero biases. */
+GBK_API gbk_status gbk_cnn_init(float *params, uint64_t seed, void *stream);
+/* targets [n][10] FP32 from parameter vectors [n][GBK_NPAR] FP64, and
+ * parameters back from network outputs [n][16] (I0 := 1, PA in [0, 360)). */
+GBK_API gbk_status gbk_cnn_targets(int32_t n, const double *params, float *targets, void *stream);
+GBK_API gbk_status gbk_cnn_decode(int32_t n, const float *out, double *params, void *stream);
+/* Training observations from model maps [n][3][64][64] (gbk_eval_cubes):
+ * v = m1 + N(0, noise_v), sigma = m2 + N(0, sqrt(2) noise_v), mask 0 with
+ * probability dead_frac or where m0 == 0.  Normal number j of the stream is
+ * Box-Muller (cosine branch) of outputs 2j+1 and 2j+2 of SplitMix64 seeded
+ * with `seed`; pixel i uses j = 2i (v) and 2i+1 (sigma); the dead-fibre
+ * uniforms are output i+1 of SplitMix64 seeded with seed ^ 0xD1B54A32D192ED03. */
+GBK_API gbk_status gbk_cnn_synth_obs(int32_t n, const float *maps, uint64_t seed, float noise_v, float dead_frac,
+                                     float *v, float *sigma, uint8_t *mask, void *stream);
+/* Network outputs out [n][16] FP32 for n samples (workspace for batch n). */
+GBK_API gbk_status gbk_cnn_forward(const float *params, int32_t n, const float *v, const float *sigma,
+                                   const uint8_t *mask, float *out, void *workspace, size_t ws_bytes, void *stream);
+/* Loss and its gradient (parameter layout) for a batch of B samples with
+ * targets [B][10]; grad and loss (device, 1 float) may be NULL. */
+GBK_API gbk_status gbk_cnn_grad(const float *params, int32_t B, const float *v, const float *sigma,
+                                const uint8_t *mask, const float *targets, float *grad, float *loss, void *workspace,
+                                size_t ws_bytes, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; `step`
+ * counts from 1) on params with moments adam_m, adam_v (same layout,
+ * caller-zeroed before step 1). */
+GBK_API gbk_status gbk_cnn_train_step(float *params, float *adam_m, float *adam_v, int32_t step, float lr,
+                                      int32_t B, const float *v, const float *sigma, const uint8_t *mask,
+                                      const float *targets, float *loss, void *workspace, size_t ws_bytes,
+                                      void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 GBK_API const char *gbk_last_error(void);
 

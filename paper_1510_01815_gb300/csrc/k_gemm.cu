@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "gbk_api_internal.h"
 #include "k_gemm.h"
 
@@ -91,7 +93,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int BN = a.bn;
     const int m0 = blockIdx.x * kGBM, n0 = blockIdx.y * BN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int KT = (a.K + kGBK - 1) / kGBK;
+    const int KT_all = (a.K + kGBK - 1) / kGBK;
+    const int kt0 = a.kt_split > 0 ? blockIdx.z * a.kt_split : 0;
+    const int KT = a.kt_split > 0 ? min(a.kt_split, KT_all - kt0) : KT_all;
+    float *const out_f32 = a.out_f32 ? a.out_f32 + (size_t)blockIdx.z * a.split_stride : nullptr;
     const uint32_t bytesA = kGBM * kGBK * 2, bytesB = (uint32_t)BN * kGBK * 2;
 
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
@@ -134,8 +139,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(g_smem_u32(&full[s])),
                          "r"(bytesA + bytesB)
                          : "memory");
-            g_tma_2d(&tmA, sA + (size_t)s * bytesA, &full[s], kt * kGBK, m0);
-            g_tma_2d(&tmB, sB + (size_t)s * bytesB, &full[s], kt * kGBK, n0);
+            g_tma_2d(&tmA, sA + (size_t)s * bytesA, &full[s], (kt0 + kt) * kGBK, m0);
+            g_tma_2d(&tmB, sB + (size_t)s * bytesB, &full[s], (kt0 + kt) * kGBK, n0);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int m = m0 + warp * 32 + lane;
     // 16-byte vector stores need 16-byte aligned rows and base pointers
     const bool vec_bf = a.out_bf16 && (a.ldo % 8) == 0 && ((uintptr_t)a.out_bf16 % 16) == 0;
-    const bool vec_f = a.out_f32 && (a.ldo % 4) == 0 && ((uintptr_t)a.out_f32 % 16) == 0;
+    const bool vec_f = out_f32 && (a.ldo % 4) == 0 && ((uintptr_t)out_f32 % 16) == 0 && (a.split_stride % 4) == 0;
     if (have) {
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
@@ -211,13 +216,28 @@ __global__ void __launch_bounds__(kGThreads, 1)
             }
             const size_t o = (size_t)m * a.ldo + nb;
             const bool full_chunk = nb + 16 <= a.N;
-            if (a.out_f32) {
+            if (out_f32) {
                 if (full_chunk && vec_f) {
-                    float4 *q = reinterpret_cast<float4 *>(a.out_f32 + o);
+                    float4 *q = reinterpret_cast<float4 *>(out_f32 + o);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) q[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 } else {
-                    for (int j = 0; j < 16 && nb + j < a.N; ++j) a.out_f32[o + j] = v[j];
+                    for (int j = 0; j < 16 && nb + j < a.N; ++j) out_f32[o + j] = v[j];
+                }
+            }
+            if (a.out_t) {
+                if (a.t_mode == 1) {
+                    const int q = 1 << a.t_log2;
+                    const size_t rowb = (size_t)(m & (q - 1)) * a.N, col = (size_t)(m >> a.t_log2);
+                    for (int j = 0; j < 16 && nb + j < a.N; ++j)
+                        a.out_t[(rowb + nb + j) * a.ldt + col] = __float2bfloat16_rn(v[j]);
+                } else {
+                    const int c = 1 << a.t_log2;
+                    const size_t colb = (size_t)m * (a.N >> a.t_log2);
+                    for (int j = 0; j < 16 && nb + j < a.N; ++j) {
+                        const int n = nb + j;
+                        a.out_t[(size_t)(n & (c - 1)) * a.ldt + colb + (n >> a.t_log2)] = __float2bfloat16_rn(v[j]);
+                    }
                 }
             }
             if (a.out_bf16) {
@@ -305,11 +325,46 @@ gbk_status launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, cons
         if (e != cudaSuccess) return cuda_fail(e, "GEMM: setting dynamic shared memory");
         configured = smem;
     }
-    dim3 grid((a.M + kGBM - 1) / kGBM, (a.N + a.bn - 1) / a.bn);
+    int splits = 1;
+    if (a.kt_split > 0) {
+        if (!a.out_f32 || a.out_bf16 || a.out_t) return fail(GBK_EINVAL, "split-K writes FP32 slices only");
+        int KT = (a.K + kGBK - 1) / kGBK;
+        splits = (KT + a.kt_split - 1) / a.kt_split;
+        if (splits > 65535) return fail(GBK_EINVAL, "too many K splits");
+    }
+    if (a.out_t) {
+        if (a.t_mode != 1 && a.t_mode != 2) return fail(GBK_EINVAL, "unknown transposed-output mode");
+        if (a.t_log2 < 0 || a.t_log2 > 16) return fail(GBK_EINVAL, "transposed-output factor out of range");
+        if (a.t_mode == 1 && (a.M & ((1 << a.t_log2) - 1))) return fail(GBK_EINVAL, "M must be a multiple of q");
+        if (a.t_mode == 2 && (a.N & ((1 << a.t_log2) - 1))) return fail(GBK_EINVAL, "N must be a multiple of c");
+    }
+    dim3 grid((a.M + kGBM - 1) / kGBM, (a.N + a.bn - 1) / a.bn, splits);
     if (grid.y > 65535) return fail(GBK_EINVAL, "N too large");
     gemm_bf16_kernel<<<grid, kGThreads, smem, st>>>(ta, tb, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "GEMM launch");
+    return GBK_OK;
+}
+
+__global__ void splitk_reduce_kernel(const float *part, int splits, size_t stride, int M, int N, int ldo, float *out)
+{
+    const size_t total = (size_t)M * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t m = i / N, n = i - m * N, o = m * ldo + n;
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * stride + o];
+        out[o] = s;
+    }
+}
+
+gbk_status launch_splitk_reduce(const float *part, int splits, size_t stride, int M, int N, int ldo, float *out,
+                                cudaStream_t st)
+{
+    size_t total = (size_t)M * N;
+    int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, splits, stride, M, N, ldo, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "split-K reduction launch");
     return GBK_OK;
 }
 

@@ -98,6 +98,15 @@ def lib():
             "gbk_survey_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz,
                                         vp]),
             "gbk_device_status": (i32, [ctypes.POINTER(ctypes.c_int32)]),
+            "gbk_cnn_param_count": (sz, []),
+            "gbk_cnn_workspace_bytes": (sz, [i32]),
+            "gbk_cnn_init": (i32, [vp, ctypes.c_uint64, vp]),
+            "gbk_cnn_targets": (i32, [i32, vp, vp, vp]),
+            "gbk_cnn_decode": (i32, [i32, vp, vp, vp]),
+            "gbk_cnn_synth_obs": (i32, [i32, vp, ctypes.c_uint64, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp]),
+            "gbk_cnn_forward": (i32, [vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+            "gbk_cnn_grad": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "gbk_cnn_train_step": (i32, [vp, vp, vp, i32, ctypes.c_float, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "gbk_gemm_bf16": (i32, [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, i32, ctypes.c_float, vp, vp, i32,
                                     vp]),
             "gbk_last_error": (ctypes.c_char_p, []),
@@ -116,7 +125,9 @@ def exported_symbols():
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
-            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_device_status", "gbk_gemm_bf16",
+            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_device_status", "gbk_gemm_bf16", "gbk_cnn_param_count",
+            "gbk_cnn_workspace_bytes", "gbk_cnn_init", "gbk_cnn_targets", "gbk_cnn_decode", "gbk_cnn_synth_obs",
+            "gbk_cnn_forward", "gbk_cnn_grad", "gbk_cnn_train_step",
             "gbk_last_error", "gbk_version"]
 
 
@@ -405,6 +416,100 @@ def gbk_gemm_bf16(A, B, out_bf16=None, out_f32=None, bias=None, relu=False, mask
                                int(mask.stride(0)) if mask is not None else 0, float(alpha),
                                _strided(out_bf16, torch.bfloat16, "out_bf16"), _strided(out_f32, torch.float32, "out_f32"),
                                int(ldo), _stream(stream)))
+
+
+def gbk_cnn_param_count():
+    return int(lib().gbk_cnn_param_count())
+
+
+def gbk_cnn_workspace_bytes(batch):
+    nb = lib().gbk_cnn_workspace_bytes(int(batch))
+    if nb == 0:
+        raise GbkError(GBK_EINVAL, lib().gbk_last_error().decode())
+    return nb
+
+
+def gbk_cnn_init(params, seed, stream=None):
+    _check(lib().gbk_cnn_init(_ptr(params, torch.float32, "params"), int(seed) & ((1 << 64) - 1), _stream(stream)))
+
+
+def gbk_cnn_targets(params, targets, stream=None):
+    _check(lib().gbk_cnn_targets(int(params.shape[0]), _ptr(params, torch.float64, "params"),
+                                 _ptr(targets, torch.float32, "targets"), _stream(stream)))
+
+
+def gbk_cnn_decode(out, params, stream=None):
+    _check(lib().gbk_cnn_decode(int(out.shape[0]), _ptr(out, torch.float32, "out"),
+                                _ptr(params, torch.float64, "params"), _stream(stream)))
+
+
+def gbk_cnn_synth_obs(maps, seed, noise_v, dead_frac, v, sigma, mask, stream=None):
+    _check(lib().gbk_cnn_synth_obs(int(maps.shape[0]), _ptr(maps, torch.float32, "maps"),
+                                   int(seed) & ((1 << 64) - 1), float(noise_v), float(dead_frac),
+                                   _ptr(v, torch.float32, "v"), _ptr(sigma, torch.float32, "sigma"),
+                                   _ptr(mask, torch.uint8, "mask"), _stream(stream)))
+
+
+def gbk_cnn_forward(params, v, sigma, mask, out, workspace, stream=None):
+    _check(lib().gbk_cnn_forward(_ptr(params, torch.float32, "params"), int(v.shape[0]), _ptr(v, torch.float32, "v"),
+                                 _ptr(sigma, torch.float32, "sigma"), _ptr(mask, torch.uint8, "mask"),
+                                 _ptr(out, torch.float32, "out"), _ptr(workspace, None, "workspace"),
+                                 workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def gbk_cnn_grad(params, v, sigma, mask, targets, grad, loss, workspace, stream=None):
+    _check(lib().gbk_cnn_grad(_ptr(params, torch.float32, "params"), int(v.shape[0]), _ptr(v, torch.float32, "v"),
+                              _ptr(sigma, torch.float32, "sigma"), _ptr(mask, torch.uint8, "mask"),
+                              _ptr(targets, torch.float32, "targets"), _ptr(grad, torch.float32, "grad"),
+                              _ptr(loss, torch.float32, "loss"), _ptr(workspace, None, "workspace"),
+                              workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def gbk_cnn_train_step(params, adam_m, adam_v, step, lr, v, sigma, mask, targets, loss, workspace, stream=None):
+    _check(lib().gbk_cnn_train_step(_ptr(params, torch.float32, "params"), _ptr(adam_m, torch.float32, "adam_m"),
+                                    _ptr(adam_v, torch.float32, "adam_v"), int(step), float(lr), int(v.shape[0]),
+                                    _ptr(v, torch.float32, "v"), _ptr(sigma, torch.float32, "sigma"),
+                                    _ptr(mask, torch.uint8, "mask"), _ptr(targets, torch.float32, "targets"),
+                                    _ptr(loss, torch.float32, "loss"), _ptr(workspace, None, "workspace"),
+                                    workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+class CnnSeed:
+    """Convenience owner of the network's parameters, Adam state and
+    workspace; every computation runs in the library's kernels."""
+
+    def __init__(self, batch, seed=1, device="cuda"):
+        self.batch, self.device = batch, device
+        n = gbk_cnn_param_count()
+        self.params = torch.empty(n, dtype=torch.float32, device=device)
+        self.m = torch.zeros(n, dtype=torch.float32, device=device)
+        self.v = torch.zeros(n, dtype=torch.float32, device=device)
+        self.ws = torch.empty(gbk_cnn_workspace_bytes(batch), dtype=torch.uint8, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.step = 0
+        gbk_cnn_init(self.params, seed)
+
+    def train_step(self, v, sigma, mask, targets, lr):
+        self.step += 1
+        gbk_cnn_train_step(self.params, self.m, self.v, self.step, lr, v, sigma, mask, targets, self.loss, self.ws)
+
+    def predict(self, v, sigma, mask):
+        """Parameter vectors [n][10] (FP64, device) for n maps, in batches."""
+        n = v.shape[0]
+        B = self.batch
+        out = torch.empty((B, 16), dtype=torch.float32, device=self.device)
+        res = torch.empty((n, NPAR), dtype=torch.float64, device=self.device)
+        for i in range(0, n, B):
+            j = min(n, i + B)
+            if j - i == B:
+                gbk_cnn_forward(self.params, v[i:j], sigma[i:j], mask[i:j], out, self.ws)
+            else:  # pad the last batch
+                pv, ps = torch.zeros_like(v[:B]), torch.zeros_like(sigma[:B])
+                pm = torch.zeros_like(mask[:B])
+                pv[:j - i], ps[:j - i], pm[:j - i] = v[i:j], sigma[i:j], mask[i:j]
+                gbk_cnn_forward(self.params, pv, ps, pm, out, self.ws)
+            gbk_cnn_decode(out[:j - i].contiguous(), res[i:j])
+        return res
 
 
 def _strided(t, dtype, name):

@@ -70,6 +70,20 @@ GRID_GEOM = Geometry(64, 64, 64, 20.0, 0.0, 2.5, 30.0)
 CNN_GEOM = Geometry(64, 64, 64, 20.0, 0.0, 2.5, 30.0)
 
 
+# CNN seed workload: 64 x 64 maps; Table 2-like ranges extended to the
+# Fabry-Perot ones, centre within 0.4-0.6 of the frame, I0 = 1.
+CNN_RANGES = {X0: (25.6, 38.4), Y0: (25.6, 38.4), PA: (0.0, 360.0), INCL: (20.0, 80.0), VSYS: (-30.0, 30.0),
+              VMAX: (50.0, 300.0), RT: (1.0, 8.0), SIG0: (10.0, 80.0), H: (4.0, 10.0)}
+
+
+def draw_cnn_params(rng, n):
+    p = np.zeros((n, NPAR))
+    for k, (lo, hi) in CNN_RANGES.items():
+        p[:, k] = rng.uniform(lo, hi, n)
+    p[:, I0] = 1.0
+    return p
+
+
 def draw_fp_params(rng, n, geom=FP_GEOM, h=FP_SCALE_LENGTH):
     """Parameter sets over the Fabry-Perot ranges; x0, y0 in 0.4-0.6 N."""
     p = np.zeros((n, NPAR))

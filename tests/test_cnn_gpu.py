@@ -1,0 +1,178 @@
+"""The CNN seed on the GPU (tcgen05 GEMMs, BF16 operands, FP32 accumulation)
+against the FP64 oracle of the same network (oracle/cnn.py): forward,
+gradient, the target map, the initialisation and noise streams, Adam's first
+step, and that training on synthetic maps learns."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn
+from paper_1510_01815_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1510_01815_gb300 import build, gbk
+    build.build()
+    assert torch.cuda.is_available()
+    return gbk
+
+
+def _problem(seed, n):
+    rng = np.random.default_rng(seed)
+    P = np.zeros(cnn.param_count())
+    off = cnn.param_offsets()
+    for l in range(5):
+        blk = rng.normal(size=(cnn.C[l], cnn.K[l] + 1)) * math.sqrt(2.0 / cnn.K[l])
+        blk[:, -1] = rng.normal(size=cnn.C[l]) * 0.05
+        P[off[l]:off[l + 1]] = blk.ravel()
+    P = P.astype(np.float32).astype(np.float64)  # what the device holds
+    v = rng.normal(0, 100, size=(n, 64, 64)).astype(np.float32)
+    s = rng.uniform(20, 80, size=(n, 64, 64)).astype(np.float32)
+    mask = (rng.uniform(size=(n, 64, 64)) > 0.1).astype(np.uint8)
+    t = rng.normal(size=(n, 10)).astype(np.float32)
+    return P, v, s, mask, t
+
+
+def _dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def test_forward_vs_oracle(G):
+    P, v, s, mask, _ = _problem(11, 16)
+    dP, dv, ds, dm = _dev(P.astype(np.float32), v, s, mask)
+    out = torch.empty((16, 16), dtype=torch.float32, device="cuda")
+    ws = torch.empty(G.gbk_cnn_workspace_bytes(16), dtype=torch.uint8, device="cuda")
+    G.gbk_cnn_forward(dP, dv, ds, dm, out, ws)
+    ref, _ = cnn.forward(P, cnn.encode(v, s, mask))
+    got = out.cpu().double().numpy()
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel < 2e-2, rel
+    assert G.gbk_device_status() == 0
+
+
+def test_gradient_vs_oracle(G):
+    P, v, s, mask, t = _problem(12, 16)
+    dP, dv, ds, dm, dt = _dev(P.astype(np.float32), v, s, mask, t)
+    grad = torch.empty(cnn.param_count(), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    ws = torch.empty(G.gbk_cnn_workspace_bytes(16), dtype=torch.uint8, device="cuda")
+    G.gbk_cnn_grad(dP, dv, ds, dm, dt, grad, loss, ws)
+    ref_loss, ref_g = cnn.loss_and_grad(P, cnn.encode(v, s, mask), t.astype(np.float64))
+    assert abs(float(loss) - ref_loss) <= 2e-2 * ref_loss
+    g = grad.cpu().double().numpy()
+    off = cnn.param_offsets()
+    for l in range(5):
+        blk = slice(off[l], off[l + 1])
+        rel = np.linalg.norm(g[blk] - ref_g[blk]) / np.linalg.norm(ref_g[blk])
+        assert rel < 5e-2, (l, rel)
+        # the bias gradients (column K_l) come from the ones row of the GEMM
+        gb = g[blk].reshape(cnn.C[l], cnn.K[l] + 1)[:, -1]
+        rb = ref_g[blk].reshape(cnn.C[l], cnn.K[l] + 1)[:, -1]
+        assert np.linalg.norm(gb - rb) <= 5e-2 * np.linalg.norm(rb) + 1e-9, l
+    assert G.gbk_device_status() == 0
+
+
+def test_targets_and_decode(G):
+    rng = np.random.default_rng(13)
+    p = synth.draw_cnn_params(rng, 64)
+    dp = torch.from_numpy(p).cuda()
+    t = torch.empty((64, 10), dtype=torch.float32, device="cuda")
+    G.gbk_cnn_targets(dp, t)
+    np.testing.assert_allclose(t.cpu().numpy(), cnn.targets(p), rtol=1e-5, atol=1e-6)
+    y = torch.zeros((64, 16), dtype=torch.float32, device="cuda")
+    y[:, :10] = t
+    q = torch.empty((64, 10), dtype=torch.float64, device="cuda")
+    G.gbk_cnn_decode(y, q)
+    np.testing.assert_allclose(q.cpu().numpy(), cnn.decode(y.cpu().double().numpy()), rtol=1e-9, atol=1e-9)
+
+
+def test_init_stream(G):
+    n = G.gbk_cnn_param_count()
+    assert n == cnn.param_count()
+    P = torch.empty(n, dtype=torch.float32, device="cuda")
+    G.gbk_cnn_init(P, 2015)
+    P = P.cpu().double().numpy()
+    off = cnn.param_offsets()
+    rng = np.random.default_rng(14)
+    for l in range(5):
+        sd = math.sqrt((1.0 if l == 4 else 2.0) / cnn.K[l])
+        for j in rng.choice(cnn.C[l] * (cnn.K[l] + 1), size=20, replace=False):
+            i = off[l] + int(j)
+            ref = 0.0 if j % (cnn.K[l] + 1) == cnn.K[l] else sd * cnn.sm_normal(2015, i)
+            assert P[i] == pytest.approx(ref, rel=1e-6, abs=1e-9), (l, j)
+
+
+def test_synth_obs_stream(G):
+    rng = np.random.default_rng(15)
+    maps = np.zeros((8, 3, 64, 64), np.float32)
+    maps[:, 0] = rng.uniform(0, 1, size=(8, 64, 64)) * (rng.uniform(size=(8, 64, 64)) > 0.05)
+    maps[:, 1] = rng.normal(0, 100, size=(8, 64, 64))
+    maps[:, 2] = rng.uniform(20, 60, size=(8, 64, 64))
+    dmaps = torch.from_numpy(maps).cuda()
+    v = torch.empty((8, 64, 64), dtype=torch.float32, device="cuda")
+    s, m = torch.empty_like(v), torch.empty((8, 64, 64), dtype=torch.uint8, device="cuda")
+    G.gbk_cnn_synth_obs(dmaps, 77, 5.0, 0.02, v, s, m)
+    pix = rng.choice(8 * 4096, size=400, replace=False)
+    ref = cnn.synth_obs(maps, 77, 5.0, 0.02, pixels=pix)
+    vf, sf, mf = v.cpu().numpy().ravel(), s.cpu().numpy().ravel(), m.cpu().numpy().ravel()
+    for i, (rv, rs, rm) in zip(pix, ref):
+        assert abs(vf[i] - rv) < 1e-3 and abs(sf[i] - rs) < 1e-3 and mf[i] == rm, i
+    assert 0.05 < 1.0 - mf.mean() < 0.09  # 2 % dead + ~5 % invalid
+
+
+def test_adam_first_step(G):
+    P, v, s, mask, t = _problem(16, 16)
+    dP, dv, ds, dm, dt = _dev(P.astype(np.float32), v, s, mask, t)
+    n = cnn.param_count()
+    m0, v0 = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    ws = torch.empty(G.gbk_cnn_workspace_bytes(16), dtype=torch.uint8, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    lr = 1e-3
+    G.gbk_cnn_train_step(dP, m0, v0, 1, lr, dv, ds, dm, dt, loss, ws)
+    _, g = cnn.loss_and_grad(P, cnn.encode(v, s, mask), t.astype(np.float64))
+    step = dP.cpu().double().numpy() - P
+    big = np.abs(g) > 0.2 * np.sqrt(np.mean(g * g))
+    # the first bias-corrected Adam step is -lr sign(g) where |g| >> eps: its
+    # size is lr exactly; its sign follows the BF16 gradient, which may
+    # differ from the FP64 one on a few coordinates with cancelling sums
+    size_ok = np.mean(np.abs(np.abs(step[big]) - lr) <= 2e-3 * lr + 1e-7)
+    agree = np.mean(np.sign(step[big]) == -np.sign(g[big]))
+    assert size_ok > 0.999 and agree > 0.999, (size_ok, agree)
+    # everywhere: no step is larger than lr (up to FP32 rounding of the parameters)
+    assert np.max(np.abs(step)) <= lr * (1 + 1e-3) + 1e-7
+
+
+def test_training_learns(G):
+    """Synthetic maps of the CNN workload (64 x 64 x 64, noise 5 km/s, 2 %
+    dead fibres): the loss falls and held-out predictions improve on the
+    prior's centre."""
+    rng = np.random.default_rng(17)
+    n_train, n_test, B = 8192, 512, 256
+    p = synth.draw_cnn_params(rng, n_train + n_test)
+    dp = torch.from_numpy(p).cuda()
+    maps = G.eval_maps(synth.CNN_GEOM, dp)
+    v = torch.empty((len(p), 64, 64), dtype=torch.float32, device="cuda")
+    s, m = torch.empty_like(v), torch.empty((len(p), 64, 64), dtype=torch.uint8, device="cuda")
+    G.gbk_cnn_synth_obs(maps, 5, 5.0, 0.02, v, s, m)
+    t = torch.empty((len(p), 10), dtype=torch.float32, device="cuda")
+    G.gbk_cnn_targets(dp, t)
+    net = G.CnnSeed(B, seed=3)
+    losses = []
+    for it in range(600):
+        i = (it * B) % n_train
+        net.train_step(v[i:i + B], s[i:i + B], m[i:i + B], t[i:i + B], 1e-3)
+        if it % 50 == 0 or it == 599:
+            losses.append(float(net.loss))
+    assert losses[-1] < 0.25 * losses[0], losses
+    pred = net.predict(v[n_train:], s[n_train:], m[n_train:]).cpu().numpy()
+    truth = p[n_train:]
+    dv = np.abs(pred[:, synth.VMAX] - truth[:, synth.VMAX])
+    dpa = np.abs((pred[:, synth.PA] - truth[:, synth.PA] + 180.0) % 360.0 - 180.0)
+    prior_dv = np.abs(175.0 - truth[:, synth.VMAX])
+    assert np.median(dv) < 0.5 * np.median(prior_dv), (np.median(dv), np.median(prior_dv))
+    assert np.median(dpa) < 20.0, np.median(dpa)
