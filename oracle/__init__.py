@@ -28,7 +28,7 @@ class _Geom(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("upsample", ctypes.c_int32), ("dv", ctypes.c_double), ("vc", ctypes.c_double),
                 ("psf_fwhm", ctypes.c_double), ("lsf_fwhm", ctypes.c_double),
-                ("lsf_mode", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("lsf_mode", ctypes.c_int32), ("model", ctypes.c_int32),
                 ("halo_sigmas", ctypes.c_double)]
 
 
@@ -48,10 +48,11 @@ class Geom:
     lsf_mode: int = 0
     upsample: int = 1
     halo_sigmas: float = 4.0
+    model: int = 0  # 0 intensity cube; 1 velocity field (arctan); 2 velocity field (Epinat)
 
     def c(self):
         return _Geom(self.nx, self.ny, self.nz, self.upsample, self.dv, self.vc,
-                     self.psf_fwhm, self.lsf_fwhm, self.lsf_mode, 0, self.halo_sigmas)
+                     self.psf_fwhm, self.lsf_fwhm, self.lsf_mode, self.model, self.halo_sigmas)
 
 
 _lib = None

@@ -57,7 +57,9 @@ enum { OG_X0, OG_Y0, OG_PA, OG_INCL, OG_VSYS, OG_VMAX, OG_RT, OG_SIG0, OG_I0, OG
 typedef struct {
     int32_t nx, ny, nz, upsample;
     double dv, vc, psf_fwhm, lsf_fwhm;
-    int32_t lsf_mode, pad_;
+    int32_t lsf_mode;
+    int32_t model;  /* 0 intensity cube (arctan curve); 1 velocity field,
+                       arctan curve; 2 velocity field, Epinat curve */
     double halo_sigmas;
 } og_geom;
 
@@ -117,9 +119,9 @@ void og_dims_array(const og_geom *g, int32_t *out)
 }
 
 /* ------------------------------------------------------------------ */
-/* Sec. 2.1: line-of-sight velocity and surface brightness at sky position
- * (x, y), in data-pixel units. */
-void og_los(const double *p, double x, double y, double *v_los, double *bright)
+/* Sec. 2.1.1, Eqs. 1-3: disc-plane coordinate x_e, deprojected radius r
+ * and sin(i) for sky position (x, y), in data-pixel units. */
+static void og_disc_coords(const double *p, double x, double y, double *xe_out, double *r_out, double *sin_i)
 {
     double pa = p[OG_PA] * OG_PI / 180.0;
     double inc = p[OG_INCL] * OG_PI / 180.0;
@@ -127,15 +129,33 @@ void og_los(const double *p, double x, double y, double *v_los, double *bright)
     double xe = -dx * sin(pa) + dy * cos(pa);                 /* Eq. 1 */
     double ye = -dx * cos(pa) - dy * sin(pa);                 /* Eq. 2 */
     double yd = ye / cos(inc);
-    double r = sqrt(xe * xe + yd * yd);                       /* Eq. 3 */
-    /* Eq. 6 divided by r, times x_e, gives Vrot(r) cos(theta) with
-     * cos(theta) = x_e / r (Eq. 4). */
-    double vrot_over_r;
-    if (r > 0.0)
-        vrot_over_r = (2.0 / OG_PI) * p[OG_VMAX] * atan(r / p[OG_RT]) / r;
-    else
-        vrot_over_r = (2.0 / OG_PI) * p[OG_VMAX] / p[OG_RT];
-    *v_los = p[OG_VSYS] + vrot_over_r * xe * sin(inc);        /* Eq. 8 */
+    *xe_out = xe;
+    *r_out = sqrt(xe * xe + yd * yd);                         /* Eq. 3 */
+    *sin_i = sin(inc);
+}
+
+/* Vrot(r) / r for the arctan curve (Eq. 6; r -> 0 limit 2 Vmax / (pi r_t))
+ * or the Epinat curve (Eq. 7, V_t (r/r_t)^g / (1 + (r/r_t)^a) with a = p[8],
+ * g = p[9]; 0 at r = 0, where x_e = 0 and cos(theta) has no limit).  Times
+ * x_e it gives Vrot(r) cos(theta) with cos(theta) = x_e / r (Eq. 4). */
+static double og_vrot_over_r(int epinat, const double *p, double r)
+{
+    if (epinat) {
+        if (!(r > 0.0)) return 0.0;
+        double q = r / p[OG_RT];
+        return p[OG_VMAX] * pow(q, p[OG_H]) / (1.0 + pow(q, p[OG_I0])) / r;
+    }
+    if (r > 0.0) return (2.0 / OG_PI) * p[OG_VMAX] * atan(r / p[OG_RT]) / r;
+    return (2.0 / OG_PI) * p[OG_VMAX] / p[OG_RT];
+}
+
+/* Sec. 2.1: line-of-sight velocity (Eq. 8, arctan curve) and surface
+ * brightness (Eq. 5) at sky position (x, y), in data-pixel units. */
+void og_los(const double *p, double x, double y, double *v_los, double *bright)
+{
+    double xe, r, si;
+    og_disc_coords(p, x, y, &xe, &r, &si);
+    *v_los = p[OG_VSYS] + og_vrot_over_r(0, p, r) * xe * si;  /* Eq. 8 */
     *bright = p[OG_I0] * exp(-r / p[OG_H]);                   /* Eq. 5 */
 }
 
@@ -292,9 +312,37 @@ void og_moments(const double *cube, int nx, int ny, int nz, double dv, double vc
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Velocity-field strategy (Sec. 2.2.1 with Sec. 2.1.5): Eq. 8 evaluated at
+ * every data pixel -- no cube, no PSF or LSF.  The strategy has no intensity
+ * model, so every pixel is valid (m0 = 1); m2 is the constant dispersion
+ * model sigma_model = p[SIG0] (Sec. 2.1.4).  Rotation curve: the arctan
+ * function (Eq. 6) for model 1; the Epinat function (Eq. 7),
+ *   Vrot(r) = V_t (r/r_t)^g / (1 + (r/r_t)^a),
+ * for model 2, with a = p[8] and g = p[9] (the intensity slots, unused by a
+ * velocity field).  Vrot(r) cos(theta) = [Vrot(r)/r] x_e as in og_los; at
+ * r = 0 the Epinat field is Vsys (cos(theta) has no limit there). */
+void og_vfield(const og_geom *g, const double *p, double *maps)
+{
+    const int np = g->nx * g->ny;
+    for (int y = 0; y < g->ny; ++y)
+        for (int x = 0; x < g->nx; ++x) {
+            double xe, r, si;
+            og_disc_coords(p, x, y, &xe, &r, &si);
+            int s = y * g->nx + x;
+            maps[s] = 1.0;
+            maps[np + s] = p[OG_VSYS] + og_vrot_over_r(g->model == 2, p, r) * xe * si;  /* Eq. 8 */
+            maps[2 * np + s] = p[OG_SIG0];
+        }
+}
+
 /* Steps 1-5 of one model: cube (optional output, data resolution) and maps. */
 void og_eval(const og_geom *g, const double *p, double *cube_out, double *maps_out)
 {
+    if (g->model != 0) {  /* velocity field: no cube */
+        if (maps_out) og_vfield(g, p, maps_out);
+        return;
+    }
     og_dims d; og_get_dims(g, &d);
     double *wx = (double *)malloc(sizeof(double) * (2 * d.rxy + 1));
     double *wz = (double *)malloc(sizeof(double) * (2 * d.rz + 1));

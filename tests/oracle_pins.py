@@ -408,4 +408,76 @@ def pin_chi2_statistics(og):
     assert abs(mean - 2 * N) < 4 * math.sqrt(2 * 2 * N / 100.0), mean
 
 
+# --------------------------------------------------------------------------
+# Velocity-field strategy (Sec. 2.2.1): Eq. 8 per pixel, arctan (Eq. 6) or
+# Epinat (Eq. 7) rotation curve; slots 8, 9 hold the Epinat slopes a, g.
+
+def _vf(og, model, nx=21, ny=17):
+    return og.Geom(nx, ny, 1, 10.0, 0.0, 0.0, 0.0, 0, model=model)
+
+
+def pin_vfield_face_on(og):
+    """i = 0: the field is Vsys everywhere, for both curves; m0 = 1 (every
+    pixel valid) and m2 = sigma_model."""
+    for model in (1, 2):
+        p = P(incl=0.0, sig0=37.0, i0=1.5, h=0.8)
+        m = og.evaluate(_vf(og, model), p)
+        np.testing.assert_allclose(m[1], 12.0, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(m[0], 1.0)
+        np.testing.assert_array_equal(m[2], 37.0)
+
+
+def pin_vfield_pa_flip(og):
+    """PA -> PA + 180 deg reverses the rotation: v - Vsys changes sign."""
+    for model in (1, 2):
+        p = P(pa=35.0, i0=2.0, h=1.3)
+        q = P(pa=215.0, i0=2.0, h=1.3)
+        a = og.evaluate(_vf(og, model), p)[1] - 12.0
+        b = og.evaluate(_vf(og, model), q)[1] - 12.0
+        np.testing.assert_allclose(b, -a, rtol=0, atol=1e-9)
+        assert np.max(np.abs(a)) > 10.0
+
+
+def pin_vfield_major_axis_values(og):
+    """PA = 90 deg puts the major axis on the row y = y0 with x_e = -(x - x0),
+    so v = Vsys - sign(x - x0) Vrot(|x - x0|) sin i.  Hand values at
+    r_t = 2 px, V_t = 200 km/s, i = 30 deg (sin i = 1/2):
+      arctan: Vrot(r_t) = V_t / 2 = 100; Vrot(sqrt(3) r_t) is off the grid,
+              Vrot(2 r_t) = (2/pi) V_t atan 2 = 140.9666...;
+      Epinat a = g = 1: Vrot(r_t) = V_t / 2, Vrot(2 r_t) = 2 V_t / 3;
+      Epinat a = 2, g = 1 (declining): Vrot(r_t) = V_t / 2, Vrot(2 r_t) = 2 V_t / 5;
+      Epinat a = 1, g = 2 (rising):    Vrot(2 r_t) = 4 V_t / 3."""
+    x0, y0 = 10.0, 8.0
+    cases = [(1, 1.0, 1.0, 100.0, 200.0 * 2.0 / math.pi * math.atan(2.0)),
+             (2, 1.0, 1.0, 100.0, 400.0 / 3.0),
+             (2, 2.0, 1.0, 100.0, 80.0),
+             (2, 1.0, 2.0, 100.0, 800.0 / 3.0)]
+    for model, a, g, v_rt, v_2rt in cases:
+        p = P(x0=x0, y0=y0, pa=90.0, incl=30.0, vsys=12.0, vmax=200.0, rt=2.0, i0=a, h=g)
+        m = og.evaluate(_vf(og, model), p)
+        row = m[1][int(y0)]
+        for dx, vr in ((2, v_rt), (4, v_2rt)):
+            assert abs(row[int(x0) + dx] - (12.0 - 0.5 * vr)) < 1e-9, (model, a, g, dx)
+            assert abs(row[int(x0) - dx] - (12.0 + 0.5 * vr)) < 1e-9, (model, a, g, -dx)
+
+
+def pin_vfield_minor_axis_and_centre(og):
+    """On the minor axis (x_e = 0: the column x = x0 at PA = 90 deg) and at the
+    centre itself the field is Vsys, for both curves and any slopes."""
+    for model, a, g in ((1, 1.0, 1.0), (2, 1.0, 0.5), (2, 3.0, 0.2)):
+        p = P(x0=10.0, y0=8.0, pa=90.0, incl=60.0, vsys=-7.0, vmax=250.0, rt=3.0, i0=a, h=g)
+        col = og.evaluate(_vf(og, model), p)[1][:, 10]
+        np.testing.assert_allclose(col, -7.0, rtol=0, atol=1e-9)
+
+
+def pin_vfield_equals_unconvolved_cube(og):
+    """The two strategies share Eq. 8: the arctan velocity field equals m1 of
+    an unconvolved cube whose lines sit far from the band edges (Poisson
+    summation makes the discrete mean exact to ~exp(-2 pi^2 sigma^2/dv^2))."""
+    p = P(x0=5.3, y0=4.6, pa=70.0, incl=40.0, vsys=15.0, vmax=150.0, sig0=25.0)
+    cube = og.evaluate(og.Geom(12, 10, 160, 10.0, 0.0, 0.0, 0.0, 0), p)
+    vf = og.evaluate(og.Geom(12, 10, 1, 10.0, 0.0, 0.0, 0.0, 0, model=1), p)
+    np.testing.assert_allclose(vf[1], cube[1], rtol=0, atol=1e-8)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

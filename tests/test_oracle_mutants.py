@@ -22,10 +22,16 @@ MUTANTS = [
     ("eq3_no_deprojection", "double yd = ye / cos(inc);", "double yd = ye;"),
     ("eq3_cos_as_sin", "double yd = ye / cos(inc);", "double yd = ye / sin(inc);"),
     ("eq5_scale_inverted", "exp(-r / p[OG_H])", "exp(-r * p[OG_H])"),
-    ("eq6_missing_2_over_pi", "vrot_over_r = (2.0 / OG_PI) * p[OG_VMAX] * atan(r / p[OG_RT]) / r;",
-     "vrot_over_r = p[OG_VMAX] * atan(r / p[OG_RT]) / r;"),
+    ("eq6_missing_2_over_pi", "return (2.0 / OG_PI) * p[OG_VMAX] * atan(r / p[OG_RT]) / r;",
+     "return p[OG_VMAX] * atan(r / p[OG_RT]) / r;"),
     ("eq6_rt_inverted", "atan(r / p[OG_RT]) / r;", "atan(r * p[OG_RT]) / r;"),
-    ("eq8_cos_i", "vrot_over_r * xe * sin(inc);", "vrot_over_r * xe * cos(inc);"),
+    ("eq8_cos_i", "*sin_i = sin(inc);", "*sin_i = cos(inc);"),
+    ("eq7_a_g_swapped", "pow(q, p[OG_H]) / (1.0 + pow(q, p[OG_I0]))", "pow(q, p[OG_I0]) / (1.0 + pow(q, p[OG_H]))"),
+    ("eq7_one_dropped", "pow(q, p[OG_H]) / (1.0 + pow(q, p[OG_I0]))", "pow(q, p[OG_H]) / pow(q, p[OG_I0])"),
+    ("eq7_rt_inverted", "double q = r / p[OG_RT];", "double q = r * p[OG_RT];"),
+    ("eq7_centre_undefined", "if (!(r > 0.0)) return 0.0;", "if (!(r > 0.0)) return NAN;"),
+    ("vfield_sigma_model_dropped", "maps[2 * np + s] = p[OG_SIG0];", "maps[2 * np + s] = 0.0;"),
+    ("vfield_curve_ignored", "og_vrot_over_r(g->model == 2, p, r)", "og_vrot_over_r(0, p, r)"),
     ("eq8_degrees", "double inc = p[OG_INCL] * OG_PI / 180.0;", "double inc = p[OG_INCL];"),
     ("line_width_sqrt2", "ext[(size_t)ze * d.exf * d.eyf + i] = br[i] * norm * exp(-0.5 * t * t);",
      "ext[(size_t)ze * d.exf * d.eyf + i] = br[i] * norm * exp(-t * t);"),
