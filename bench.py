@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--survey-galaxies", type=int, default=2048)
     ap.add_argument("--survey-plain", type=int, default=64, help="galaxies the plain survey LM is timed on")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned-seed (CNN) measurement")
+    ap.add_argument("--no-vfield", action="store_true", help="skip the velocity-field (Epinat) measurement")
     ap.add_argument("--cnn-train", type=int, default=262144, help="training galaxies of the CNN seed")
     ap.add_argument("--cnn-epochs", type=int, default=4)
     ap.add_argument("--cnn-batch", type=int, default=1024)
@@ -443,6 +444,80 @@ def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device):
     return out
 
 
+def run_vfield(gbk, torch, n_models, n_fit, n_plain, device):
+    """Velocity-field strategy with the Epinat curve (the GHASP setting,
+    Sec. 4.2): 256 x 256 fields, evaluation throughput, and batched vs plain
+    LM over the nine free parameters from 10 %-perturbed starts on fields
+    with 5 km/s noise."""
+    g = synth.Geometry(256, 256, 1, 10.0, model=2)
+    rng = np.random.default_rng(21)
+
+    def draw(n):
+        p = np.zeros((n, synth.NPAR))
+        p[:, 0] = rng.uniform(115, 140, n)
+        p[:, 1] = rng.uniform(115, 140, n)
+        p[:, 2] = rng.uniform(0, 360, n)
+        p[:, 3] = rng.uniform(30, 70, n)
+        p[:, 4] = rng.uniform(-50, 50, n)
+        p[:, 5] = rng.uniform(100, 300, n)
+        p[:, 6] = rng.uniform(5, 30, n)
+        p[:, 7] = 30.0
+        p[:, 8] = rng.uniform(0.6, 2.5, n)
+        p[:, 9] = rng.uniform(0.5, 1.5, n)
+        return p
+
+    truth = draw(n_models)
+    maps = gbk.eval_maps(g, torch.from_numpy(truth[:1]), device=device).cpu().numpy()[0]
+    wv, ws_ = synth.weights((256, 256), 5.0)
+    ws_[:] = 0.0  # velocity only: the nine-parameter problem has no dispersion model
+    v = (maps[1] + synth.gaussian_noise(rng, (256, 256), 5.0)).astype(np.float32)
+    obs = gbk.Obs.from_numpy(v, maps[2], wv, ws_, np.ones((256, 256), np.uint8), device=device)
+    d_p = torch.from_numpy(truth).to(device)
+    c2 = torch.empty(n_models, dtype=torch.float64, device=device)
+    for _ in range(3):
+        gbk.gbk_chi2(g, d_p, obs, c2, None, gbk.PATH_FUSED, None)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(20):
+        gbk.gbk_chi2(g, d_p, obs, c2, None, gbk.PATH_FUSED, None)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / 20
+    out = {"workload": "Epinat velocity fields 256x256 (nine free parameters), %d models per launch" % n_models,
+           "eval": {"ms_per_launch": ms, "evals_per_s": n_models / (ms * 1e-3),
+                    "pixels_per_s": n_models * 65536 / (ms * 1e-3)}}
+    # fits: fields of n_fit galaxies with 5 km/s noise
+    ft = draw(n_fit)
+    fm = gbk.eval_maps(g, torch.from_numpy(ft), device=device)
+    noise = rng.normal(0.0, 5.0, size=(n_fit, 256, 256)).astype(np.float32)
+    fm[:, 1] += torch.from_numpy(noise).to(device)
+    wz = torch.zeros((256, 256), dtype=torch.float32, device=device)
+    dwv = torch.from_numpy(wv).to(device)
+    ones = torch.ones((256, 256), dtype=torch.uint8, device=device)
+    fobs = [gbk.Obs(fm[i, 1], fm[i, 2], dwv, wz, ones) for i in range(n_fit)]
+    free = (0, 1, 2, 3, 4, 5, 6, 8, 9)
+    lo, hi = ft.copy(), ft.copy()
+    for k, (l, h) in {0: (0, 255), 1: (0, 255), 2: (-360, 720), 3: (1, 89), 4: (-200, 200), 5: (1, 600),
+                      6: (0.05, 100), 8: (0.1, 5), 9: (0.05, 5)}.items():
+        lo[:, k], hi[:, k] = l, h
+    p0 = np.array([synth.perturb(rng, ft[i], free, 0.1, lo[i], hi[i]) for i in range(n_fit)])
+    for name, mode, sub in (("batched_fd", gbk.LM_BATCHED, n_fit), ("plain_fd", gbk.LM_PLAIN, n_plain)):
+        opts = gbk.lm_opts(max_iter=200, mode=mode, free=free)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q, c, it, st = gbk.fit_lm(g, fobs[:sub], p0[:sub], lo[:sub], hi[:sub], opts, device=device)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dv = np.abs(q[:, 5] - ft[:sub, 5])
+        dpa = np.abs((q[:, 2] - ft[:sub, 2] + 180.0) % 360.0 - 180.0)
+        out[name] = {"galaxies": sub, "fits_per_s": sub / dt, "p50_iters": float(np.percentile(it, 50)),
+                     "p99_iters": float(np.percentile(it, 99)), "converged_frac": float(np.mean(np.isin(st, [1, 2]))),
+                     "median_dpa": float(np.median(dpa)), "median_dvt": float(np.median(dv))}
+    out["batched_fd"]["speedup_vs_plain"] = out["batched_fd"]["fits_per_s"] / out["plain_fd"]["fits_per_s"]
+    return out
+
+
 def make_galaxy(gbk, torch, g, seed, device):
     """One synthetic Fabry-Perot galaxy: true parameters from the prior, maps
     from the library at those parameters, seeded noise (5 km/s on v,
@@ -682,6 +757,8 @@ def run_gbk(args):
                                 ("batched_tangent", gbk.LM_BATCHED, gbk.JAC_TANGENT)])
     if not args.no_survey:
         out["survey"] = run_survey(gbk, torch, args.survey_galaxies, args.survey_plain, dev)
+    if not args.no_vfield:
+        out["vfield"] = run_vfield(gbk, torch, 1024, 512, 32, dev)
     if not args.no_cnn:
         out["cnn"] = run_cnn(gbk, torch, args.cnn_train, args.cnn_epochs, args.cnn_batch, args.cnn_test, 64, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

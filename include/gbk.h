@@ -87,9 +87,29 @@ typedef struct gbk_geom {
     double psf_fwhm;
     double lsf_fwhm;
     int32_t lsf_mode;
-    int32_t reserved;   /* must be 0 */
+    int32_t model;      /* GBK_MODEL_*: 0 (the default) is the intensity cube */
     double halo_sigmas;
 } gbk_geom;
+
+/* Modelling strategies (Sec. 2.2.1).  The intensity cube (Sec. 2.2.2-2.2.5,
+ * arctan rotation curve, Eq. 6) is the default.  The velocity-field models
+ * evaluate Eq. 8 at every data pixel directly -- no cube, no PSF or LSF --
+ * with the arctan curve or the Epinat curve (Eq. 7),
+ *   Vrot(r) = V_t (r/r_t)^g / (1 + (r/r_t)^a),
+ * whose slopes a and g occupy parameter slots GBK_EPI_A = GBK_I0 and
+ * GBK_EPI_G = GBK_H (a velocity field has no intensity model).  Their maps
+ * are m0 = 1 (every pixel valid), m1 = the field, m2 = sigma0 (the constant
+ * dispersion model, Sec. 2.1.4); nz, dv, vc, the PSF and the LSF are not
+ * used, upsample must be 1; at r = 0 the field is Vsys.  Parameter domain:
+ * 0 <= i < 90, r_t > 0, sigma0 >= 0, the used parameters finite.  Served by
+ * the fused entry points (gbk_eval_cubes maps, gbk_chi2, gbk_fit_lm with
+ * finite differences, gbk_grid, gbk_nested_sample); the staged path, cubes,
+ * the tangent Jacobian and survey batches answer GBK_EUNSUPPORTED. */
+#define GBK_MODEL_CUBE           0
+#define GBK_MODEL_VFIELD_ARCTAN  1
+#define GBK_MODEL_VFIELD_EPINAT  2
+#define GBK_EPI_A GBK_I0
+#define GBK_EPI_G GBK_H
 
 /* Observed maps of one galaxy, each ny*nx, device memory.
  *  v_obs, s_obs  observed velocity and dispersion maps (km/s)

@@ -50,7 +50,10 @@ gbk_status derive_geom(const gbk_geom *in, Geom *g)
     if (!finite_nonneg(in->psf_fwhm)) return fail(GBK_EINVAL, "psf_fwhm must be finite and >= 0");
     if (!finite_nonneg(in->lsf_fwhm)) return fail(GBK_EINVAL, "lsf_fwhm must be finite and >= 0");
     if (in->lsf_mode != 0 && in->lsf_mode != 1) return fail(GBK_EINVAL, "lsf_mode must be 0 or 1");
-    if (in->reserved != 0) return fail(GBK_EINVAL, "reserved must be 0");
+    if (in->model < GBK_MODEL_CUBE || in->model > GBK_MODEL_VFIELD_EPINAT)
+        return fail(GBK_EINVAL, "unknown model %d", in->model);
+    if (in->model != GBK_MODEL_CUBE && in->upsample != 1)
+        return fail(GBK_EINVAL, "velocity-field models need upsample == 1");
     if (!(std::isfinite(in->halo_sigmas) && in->halo_sigmas > 0.0 && in->halo_sigmas <= 16.0))
         return fail(GBK_EINVAL, "halo_sigmas must be in (0, 16]");
     const int u = in->upsample;
@@ -77,6 +80,7 @@ gbk_status derive_geom(const gbk_geom *in, Geom *g)
     g->sig_z = (float)sz;
     g->sig_lsf_kms = (float)(in->lsf_fwhm / kFwhmPerSigma);
     g->lsf_mode = in->lsf_mode;
+    g->model = in->model;
     return GBK_OK;
 }
 
@@ -167,6 +171,7 @@ size_t gbk_workspace_bytes(const gbk_geom *gin, int32_t n_models, uint32_t flags
     if (n_models < 0) { fail(GBK_EINVAL, "n_models must be >= 0"); return 0; }
     FusedConfig fc;
     bool fused_ok = fused_config(g, &fc);
+    if (g.model != GBK_MODEL_CUBE) return 0;
     if (flags == GBK_PATH_FUSED || (flags == GBK_PATH_AUTO && fused_ok)) return 0;
     return staged_layout(g, n_models, true, true).total;
 }
@@ -175,6 +180,8 @@ static gbk_status run_staged(const Geom &g, int32_t n, const double *params, flo
                              const gbk_obs *obs, double *chi2, float *resid, void *ws, size_t ws_bytes,
                              cudaStream_t st)
 {
+    if (g.model != GBK_MODEL_CUBE)
+        return fail(GBK_EUNSUPPORTED, "velocity-field models have no cube (the staged path does not apply)");
     bool own_data = (cubes == nullptr);
     StagedLayout L = staged_layout(g, n, own_data, chi2 != nullptr);
     if (L.total > 0) {

@@ -27,6 +27,7 @@ struct Geom {
     float sig_z;           // LSF sigma, fine channels (mode 0)
     float sig_lsf_kms;     // LSF sigma, km/s (mode 1 folds it into the line)
     int lsf_mode;
+    int model;             // GBK_MODEL_*
 };
 
 // Per-model constants, derived once per block.

@@ -589,6 +589,7 @@ static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_
 
 gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
 {
+    if (!args.geoms && args.g.model != GBK_MODEL_CUBE) return launch_vfield(args, stream);
     if (args.geoms) {
         if (args.models_per_gal < 1 || args.n_models % args.models_per_gal != 0 || !args.pix_off)
             return fail(GBK_EINVAL, "ragged fused launch: inconsistent batch description");

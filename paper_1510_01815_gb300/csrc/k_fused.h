@@ -51,5 +51,7 @@ bool fused_config_ragged(const Geom *geoms, int n, int cs, int threads, size_t *
 bool fused_config(const Geom &g, FusedConfig *cfg);
 bool fused_config_valid(const Geom &g, int cs, int threads, int persistent, FusedConfig *cfg);
 gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream);
+// Velocity-field models (k_vfield.cu); launch_fused dispatches to it.
+gbk_status launch_vfield(const FusedArgs &args, cudaStream_t stream);
 
 }  // namespace gbk

@@ -387,6 +387,8 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     if (pl.tangent) {
         if (t.sp) return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves one geometry per batch");
         const Geom &g = *t.g;
+        if (g.model != GBK_MODEL_CUBE)
+            return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves the intensity-cube model");
         if (!tangent_config(g, &ta.cs, &ta.band))
             return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
         ta.g = g;

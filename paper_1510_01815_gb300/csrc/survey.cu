@@ -37,6 +37,8 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
         if (s) return fail(s, "galaxy %d: %s", i, gbk_last_error());
         const Geom &g = sp->geo[i];
         if (g.u != 1) return fail(GBK_EUNSUPPORTED, "galaxy %d: survey batches need upsample == 1", i);
+        if (g.model != GBK_MODEL_CUBE)
+            return fail(GBK_EUNSUPPORTED, "galaxy %d: survey batches serve the intensity-cube model", i);
         sp->pix_off[i + 1] = sp->pix_off[i] + (int64_t)g.nx * g.ny;
         int pick = 0;
         for (int pass = 0; pass < 2 && !pick; ++pass) {

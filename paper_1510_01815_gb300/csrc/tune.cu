@@ -39,6 +39,12 @@ static size_t occupancy_smem(int threads)
 bool fused_config_valid(const Geom &g, int cs, int threads, int persistent, FusedConfig *cfg)
 {
     if (persistent != 0 && persistent != 1) return false;
+    if (g.model != GBK_MODEL_CUBE) {
+        // the velocity-field kernel has one launch shape (one CTA per model)
+        if (cs != 1 || threads != 256 || persistent != 0) return false;
+        *cfg = FusedConfig{1, g.ey, 256, 0};
+        return true;
+    }
     if (g.u != 1 || cs < 1 || cs > kFusedMaxCluster || cs > g.ey) return false;
     if (threads != 512 && threads != 384 && threads != 256) return false;
     int band = (g.ey + cs - 1) / cs;
@@ -84,6 +90,7 @@ static bool heuristic(const Geom &g, FusedConfig *cfg)
 bool fused_config(const Geom &g, FusedConfig *cfg)
 {
     if (g.u != 1) return false;
+    if (g.model != GBK_MODEL_CUBE) return fused_config_valid(g, 1, 256, 0, cfg);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key_of(g));

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libgbk.so")
 NPAR = 10
 GBK_OK, GBK_EINVAL, GBK_ECUDA, GBK_EWORKSPACE, GBK_EUNSUPPORTED = 0, 1, 2, 3, 4
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
+MODEL_CUBE, MODEL_VFIELD_ARCTAN, MODEL_VFIELD_EPINAT = 0, 1, 2
 JAC_FD_FORWARD, JAC_FD_CENTRAL, JAC_TANGENT = 0, 1, 2
 LM_BATCHED, LM_PLAIN = 0, 1
 FIT_STATUS = {0: "running", 1: "ftol", 2: "xtol", 3: "maxiter", 4: "lambda", 5: "nonfinite"}
@@ -31,7 +32,7 @@ class CGeom(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("upsample", ctypes.c_int32), ("dv", ctypes.c_double), ("vc", ctypes.c_double),
                 ("psf_fwhm", ctypes.c_double), ("lsf_fwhm", ctypes.c_double),
-                ("lsf_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lsf_mode", ctypes.c_int32), ("model", ctypes.c_int32),
                 ("halo_sigmas", ctypes.c_double)]
 
 
@@ -135,7 +136,7 @@ def cgeom(g):
     """A gbk_geom from any object with the Geometry attributes."""
     return CGeom(int(g.nx), int(g.ny), int(g.nz), int(getattr(g, "upsample", 1)), float(g.dv),
                  float(getattr(g, "vc", 0.0)), float(getattr(g, "psf_fwhm", 0.0)),
-                 float(getattr(g, "lsf_fwhm", 0.0)), int(getattr(g, "lsf_mode", 0)), 0,
+                 float(getattr(g, "lsf_fwhm", 0.0)), int(getattr(g, "lsf_mode", 0)), int(getattr(g, "model", 0)),
                  float(getattr(g, "halo_sigmas", 4.0)))
 
 

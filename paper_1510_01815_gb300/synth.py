@@ -37,6 +37,7 @@ class Geometry:
     lsf_mode: int = 0
     upsample: int = 1
     halo_sigmas: float = 4.0
+    model: int = 0  # 0 intensity cube; 1 velocity field (arctan); 2 velocity field (Epinat)
 
     def asdict(self):
         return asdict(self)
