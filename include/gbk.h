@@ -442,8 +442,9 @@ GBK_API gbk_status gbk_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A,
  *   (h - 7) / 3;
  * the loss is their mean squared error.  Dense products run on the tensor
  * cores (BF16 operands, FP32 accumulation); master weights, gradients and
- * Adam moments are FP32.  Maps are device FP32 [n][64][64] (v, sigma) and
- * uint8 (mask, 1 = use); n and the batch B must be multiples of 8.  All
+ * Adam moments are FP32.  Maps are device FP32 [n][64][64] (v, sigma;
+ * 16-byte aligned) and uint8 (mask, 1 = use; 4-byte aligned); n and the
+ * batch B must be multiples of 8.  All
  * calls are asynchronous on `stream`; the workspace of
  * gbk_cnn_workspace_bytes(B) serves calls with exactly B samples.
  * ------------------------------------------------------------------------ */

@@ -130,30 +130,45 @@ __global__ void cnn_publish_kernel(const float *P, CnnTables t)
 
 // Input encoding: sample b, 4 x 4 patch (Y, X) -> row b * 256 + morton(Y, X);
 // column (dy * 4 + dx) * 3 + ch.  Also the transposed matrix with a row of
-// ones at index 48.
+// ones at index 48.  One thread per patch: four 16-byte loads of v and sigma
+// and four 4-byte mask loads, one 96-byte row store, and 49 transposed stores
+// that are coalesced across the warp (consecutive threads, consecutive rows).
 __global__ void cnn_encode_kernel(int n, const float *v, const float *s, const uint8_t *mask, __nv_bfloat16 *A,
                                   __nv_bfloat16 *AT)
 {
     const size_t rows = (size_t)n * 256;
-    const size_t total = rows * 48;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = i % rows;  // row fastest: coalesced transposed writes
-        const int e = (int)(i / rows);
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < rows; r += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(r / 256), q = (int)(r % 256);
         int Y = 0, X = 0;
         for (int k = 0; k < 4; ++k) {
             X |= ((q >> (2 * k)) & 1) << k;
             Y |= ((q >> (2 * k + 1)) & 1) << k;
         }
-        const int ch = e % 3, pp = e / 3, dy = pp / 4, dx = pp % 4;
-        const size_t pix = (size_t)b * kCnnMap * kCnnMap + (size_t)(4 * Y + dy) * kCnnMap + (4 * X + dx);
-        const bool on = mask[pix] != 0;
-        float val = 0.f;
-        if (on) val = ch == 0 ? v[pix] / kVScale : (ch == 1 ? s[pix] / kSScale : 1.f);
-        const __nv_bfloat16 h = __float2bfloat16_rn(val);
-        A[r * 48 + e] = h;
-        AT[(size_t)e * rows + r] = h;
-        if (e == 0) AT[(size_t)48 * rows + r] = __float2bfloat16_rn(1.f);
+        __align__(16) __nv_bfloat16 h[48];
+#pragma unroll
+        for (int dy = 0; dy < 4; ++dy) {
+            const size_t pix = (size_t)b * kCnnMap * kCnnMap + (size_t)(4 * Y + dy) * kCnnMap + 4 * X;
+            const float4 vv = *reinterpret_cast<const float4 *>(v + pix);
+            const float4 ss = *reinterpret_cast<const float4 *>(s + pix);
+            const uchar4 mm = *reinterpret_cast<const uchar4 *>(mask + pix);
+            const float vx[4] = {vv.x, vv.y, vv.z, vv.w}, sx[4] = {ss.x, ss.y, ss.z, ss.w};
+            const unsigned char mx[4] = {mm.x, mm.y, mm.z, mm.w};
+#pragma unroll
+            for (int dx = 0; dx < 4; ++dx) {
+                const bool on = mx[dx] != 0;
+                const int e = (dy * 4 + dx) * 3;
+                h[e] = __float2bfloat16_rn(on ? vx[dx] / kVScale : 0.f);
+                h[e + 1] = __float2bfloat16_rn(on ? sx[dx] / kSScale : 0.f);
+                h[e + 2] = __float2bfloat16_rn(on ? 1.f : 0.f);
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(A + r * 48);
+        const uint4 *src = reinterpret_cast<const uint4 *>(h);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) dst[k] = src[k];
+#pragma unroll
+        for (int e = 0; e < 48; ++e) AT[(size_t)e * rows + r] = h[e];
+        AT[(size_t)48 * rows + r] = __float2bfloat16_rn(1.f);
     }
 }
 
@@ -287,10 +302,11 @@ struct CnnWs {
 static int split_of(int l, int B, int *kt_split)
 {
     const int M = kCnnC[l], N = kCnnK[l] + 1, Kc = B * kCnnRows[l];
-    const int bn = N >= 128 ? 128 : ((N + 15) / 16) * 16;
+    const int bn = N >= 256 ? 256 : (N >= 128 ? 128 : ((N + 15) / 16) * 16);
     const int tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
     const int KT = (Kc + 63) / 64;
     int splits = (2 * 152 + tiles - 1) / tiles;
+    if (splits > 128) splits = 128;  // bounds the slices the reduction reads
     if (splits > KT) splits = KT;
     if (splits < 1) splits = 1;
     *kt_split = (KT + splits - 1) / splits;
@@ -385,7 +401,7 @@ static gbk_status cnn_forward_ws(const CnnWs &w, int B, bool want_transposed, cu
 static gbk_status cnn_encode(const CnnWs &w, int B, const float *v, const float *sg, const uint8_t *mask,
                              cudaStream_t st)
 {
-    cnn_encode_kernel<<<grid_for((size_t)B * 256 * 48), 256, 0, st>>>(B, v, sg, mask, w.A[0], w.AT[0]);
+    cnn_encode_kernel<<<grid_for((size_t)B * 256), 256, 0, st>>>(B, v, sg, mask, w.A[0], w.AT[0]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "CNN encode launch");
     return GBK_OK;
@@ -522,11 +538,12 @@ gbk_status gbk_cnn_synth_obs(int32_t n, const float *maps, uint64_t seed, float 
     return ok();
 }
 
+// The encoding reads 4-pixel runs as 16-byte (maps) and 4-byte (mask) vectors.
 static gbk_status check_maps_in(const float *v, const float *sg, const uint8_t *mask)
 {
     gbk_status s;
-    if ((s = check_device_ptr(v, "v", 4)) || (s = check_device_ptr(sg, "sigma", 4)) ||
-        (s = check_device_ptr(mask, "mask", 1)))
+    if ((s = check_device_ptr(v, "v", 16)) || (s = check_device_ptr(sg, "sigma", 16)) ||
+        (s = check_device_ptr(mask, "mask", 4)))
         return s;
     return GBK_OK;
 }

@@ -5,7 +5,7 @@
 //
 // A [M][K] and B [N][K] are BF16, row-major (both "K-major"); D is written as
 // BF16 and/or FP32 with leading dimension ldo.  One CTA of 128 threads owns a
-// 128 x BN output tile (BN = 16..128, a multiple of 16):
+// 128 x BN output tile (BN = 16..256, a multiple of 16; 256 when N allows):
 //   - warp 0 lane 0 streams 64-wide K slabs of A and B with TMA
 //     (cp.async.bulk.tensor.2d, 128-byte swizzle) into a 4-stage ring,
 //     completion counted on "full" mbarriers;
@@ -28,7 +28,7 @@
 
 namespace gbk {
 
-constexpr int kGBM = 128, kGBK = 64, kGStages = 4, kGThreads = 128;
+constexpr int kGBM = 128, kGBK = 64, kGStages = 4, kGThreads = 128, kGGroup = 16;
 constexpr long kGWaitLimit = 1L << 26;
 
 __device__ int g_gemm_status;  // 0 fine; 1 a pipeline wait timed out
@@ -91,7 +91,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs a)
 {
     const int BN = a.bn;
-    const int m0 = blockIdx.x * kGBM, n0 = blockIdx.y * BN;
+    // Grouped tile order: blockIdx.x runs over groups of kGGroup M-tiles with
+    // the N-tiles fastest inside a group, so the CTAs resident at one time
+    // share their A and B strips in L2.
+    const int tiles_m = (a.M + kGBM - 1) / kGBM, tiles_n = (a.N + BN - 1) / BN;
+    const int per_group = kGGroup * tiles_n;
+    const int grp = blockIdx.x / per_group, in_grp = blockIdx.x - grp * per_group;
+    const int gm = min(kGGroup, tiles_m - grp * kGGroup);
+    const int tm = grp * kGGroup + in_grp % gm, tn = in_grp / gm;
+    const int m0 = tm * kGBM, n0 = tn * BN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KT_all = (a.K + kGBK - 1) / kGBK;
     const int kt0 = a.kt_split > 0 ? blockIdx.z * a.kt_split : 0;
@@ -107,7 +115,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], accum;
     __shared__ uint32_t s_tmem;
 
-    const uint32_t ncols = BN <= 32 ? 32u : (BN <= 64 ? 64u : 128u);
+    const uint32_t ncols = BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(g_smem_u32(&s_tmem)),
                      "r"(ncols)
@@ -313,7 +321,7 @@ gbk_status launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, cons
     if (((uintptr_t)A % 16) || ((uintptr_t)B % 16)) return fail(GBK_EINVAL, "A and B must be 16-byte aligned");
     if (a.ldo < a.N) return fail(GBK_EINVAL, "ldo must be >= N");
     if (!a.out_bf16 && !a.out_f32) return fail(GBK_EINVAL, "no output");
-    a.bn = a.N >= 128 ? 128 : ((a.N + 15) / 16) * 16;
+    a.bn = a.N >= 256 ? 256 : (a.N >= 128 ? 128 : ((a.N + 15) / 16) * 16);
     CUtensorMap ta, tb;
     gbk_status s = encode_kmajor(&ta, A, a.M, a.K, lda, kGBM);
     if (s) return s;
@@ -338,8 +346,9 @@ gbk_status launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, cons
         if (a.t_mode == 1 && (a.M & ((1 << a.t_log2) - 1))) return fail(GBK_EINVAL, "M must be a multiple of q");
         if (a.t_mode == 2 && (a.N & ((1 << a.t_log2) - 1))) return fail(GBK_EINVAL, "N must be a multiple of c");
     }
-    dim3 grid((a.M + kGBM - 1) / kGBM, (a.N + a.bn - 1) / a.bn, splits);
-    if (grid.y > 65535) return fail(GBK_EINVAL, "N too large");
+    const long tiles = (long)((a.M + kGBM - 1) / kGBM) * ((a.N + a.bn - 1) / a.bn);
+    if (tiles > 0x7fffffffL) return fail(GBK_EINVAL, "GEMM too large");
+    dim3 grid((unsigned)tiles, 1, splits);
     gemm_bf16_kernel<<<grid, kGThreads, smem, st>>>(ta, tb, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "GEMM launch");
@@ -351,9 +360,17 @@ __global__ void splitk_reduce_kernel(const float *part, int splits, size_t strid
     const size_t total = (size_t)M * N;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t m = i / N, n = i - m * N, o = m * ldo + n;
-        float s = 0.f;
-        for (int z = 0; z < splits; ++z) s += part[(size_t)z * stride + o];
-        out[o] = s;
+        // four independent partial sums (slices z = 4k + j), added in a fixed order
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int z = 0;
+        for (; z + 4 <= splits; z += 4) {
+            s0 += part[(size_t)z * stride + o];
+            s1 += part[(size_t)(z + 1) * stride + o];
+            s2 += part[(size_t)(z + 2) * stride + o];
+            s3 += part[(size_t)(z + 3) * stride + o];
+        }
+        for (; z < splits; ++z) s0 += part[(size_t)z * stride + o];
+        out[o] = (s0 + s1) + (s2 + s3);
     }
 }
 
