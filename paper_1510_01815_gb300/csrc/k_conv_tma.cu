@@ -22,6 +22,7 @@
 #include "gbk_api_internal.h"
 #include "gbk_internal.cuh"
 #include "k_staged.h"
+#include "tma_util.cuh"
 
 namespace gbk {
 
@@ -39,43 +40,6 @@ struct ConvTmaArgs {
     float *fine;                   // [n][nzf][nyf][nxf]
     size_t f_model_stride;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_slab(const CUtensorMap *tmap, float *dst, uint64_t *bar, int x, int y,
-                                              int z, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-            "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Bounded wait for the given phase; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
-{
-    for (long it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 template <int W>
 __global__ void __launch_bounds__(kCThreads, (W <= 15 ? 2 : 1)) conv3d_tma_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -147,14 +111,14 @@ __global__ void __launch_bounds__(kCThreads, (W <= 15 ? 2 : 1)) conv3d_tma_kerne
 
     for (int e = 0; e < g.ez; ++e) {
         float *slab = (e & 1) ? slab1 : slab0;
-        if (!mbar_wait(&bar[e & 1], (uint32_t)((e >> 1) & 1))) {
+        if (!mbar_wait(&bar[e & 1], (uint32_t)((e >> 1) & 1), kWaitLimit)) {
             if (atomicExch(&s_abort, 1) == 0) atomicExch(&g_conv_status, 1);
         }
         __syncthreads();
         if (s_abort) {
             // give the other buffer's copy, if one is in flight, a bounded
             // chance to land before the CTA leaves
-            if (tid == 0 && e + 1 < g.ez) mbar_wait(&bar[(e + 1) & 1], (uint32_t)(((e + 1) >> 1) & 1));
+            if (tid == 0 && e + 1 < g.ez) mbar_wait(&bar[(e + 1) & 1], (uint32_t)(((e + 1) >> 1) & 1), kWaitLimit);
             return;  // every thread sees the same flag after the barrier
         }
         // x pass: X[r][4 m .. 4 m + 3] from slab[r][4 m .. 4 m + 3 + 2R]

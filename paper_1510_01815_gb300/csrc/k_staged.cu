@@ -300,7 +300,10 @@ gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t st
         model_cube_kernel<<<(unsigned)(bpm * a.n_models), 256, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "model cube kernel launch");
     }
-    if (conv_tma_supported(g)) {
+    if (conv_pair_supported(g)) {
+        gbk_status s = launch_conv_pair(a, stream);
+        if (s) return s;
+    } else if (conv_tma_supported(g)) {
         gbk_status s = launch_conv_tma(a, stream);
         if (s) return s;
     } else {
