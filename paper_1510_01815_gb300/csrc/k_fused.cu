@@ -596,7 +596,7 @@ gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
         switch (args.threads) {
         case 512: return launch_variant<512, 2, true>(args, args.smem, stream);
         case 384: return launch_variant<384, 2, true>(args, args.smem, stream);
-        case 256: return launch_variant<256, 2, true>(args, args.smem, stream);
+        case 256: return launch_variant<256, 4, true>(args, args.smem, stream);
         default: return fail(GBK_EINVAL, "unsupported fused block size %d", args.threads);
         }
     }
@@ -604,7 +604,7 @@ gbk_status launch_fused(const FusedArgs &args, cudaStream_t stream)
     switch (args.threads) {
     case 512: return launch_variant<512, 2, false>(args, smem, stream);
     case 384: return launch_variant<384, 2, false>(args, smem, stream);
-    case 256: return launch_variant<256, 2, false>(args, smem, stream);
+    case 256: return launch_variant<256, 4, false>(args, smem, stream);
     default: return fail(GBK_EINVAL, "unsupported fused block size %d", args.threads);
     }
 }
