@@ -52,6 +52,11 @@ OPS_PER_DATA_SPAXEL = 10
 # convolution + moments) at the Fabry-Perot size: FP32 instructions per data
 # voxel, as the hot-path scope table states it.
 SURVEY_FP32_PER_DATA_VOXEL = 47.0
+# DRAM bytes (read + write) of one fused launch of 400 Fabry-Perot models at
+# the tuning (12 CTAs, 512 threads, one cluster per model), from the ncu
+# capture summarised in profiles/fused_eval_fabry_perot_400models.md.
+FUSED_TRAFFIC_400 = 745984
+FUSED_TRAFFIC_TUNING = (12, 512, 0)
 FLUSH_BYTES = 256 << 20
 
 
@@ -765,8 +770,13 @@ def run_gbk(args):
     t_min = max(fma_model / rfma, mufu_model / rmu)
     peak_ops = (fma_model + mufu_model) / t_min
     achieved_ops = (fma_model + mufu_model) * n / (ms_step * 1e-3)
+    tuned = (tuning["cluster_ctas"], tuning["threads"], tuning["persistent"])
+    traffic = FUSED_TRAFFIC_400 if (n == 400 and tuned == FUSED_TRAFFIC_TUNING) else None
     out["roofline"] = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                       "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                       "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
+                       "traffic_note": "DRAM bytes per launch from one ncu capture at this tuning "
+                                       "(algorithmic: 0.66 MB of parameters, observed maps and chi2)"
+                                       if traffic else "no capture at this configuration",
                        "kernel": "fused_eval_kernel",
                        "basis": "per model %.1f M FP32 + %.1f M ex2 lane ops: %d FP32 + %d ex2 per extended voxel "
                                 "(%d x %d x %d), %d per PSF tap on the moment triplets (%d taps; x pass %d x %d, "
