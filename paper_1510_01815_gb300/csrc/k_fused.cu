@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             f32x2 S0 = Z2, S1 = Z2, S2 = Z2;
             f32x2 FE = pk2((float)elo, (float)(elo + 1));
             int e = elo;
-#pragma unroll 2
+#pragma unroll 6
             for (; e + 2 <= ehi; e += 2) {
                 f32x2 U = fma2(FE, ADV, UB);
                 f32x2 W = mul2(U, U);
@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             f32x2 E0 = Z2, B1 = Z2, B2 = Z2;
             f32x2 FK = pk2((float)eb, (float)(eb + 1));
             int k = eb;
+#pragma unroll 3
             for (; k + 2 <= ee; k += 2) {
                 f32x2 U = fma2(FK, ADV, UB);
                 f32x2 W = mul2(U, U);
@@ -403,6 +404,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         const float4 *row = Q + (size_t)r * g.ex + x;  // row[j] = extended column x + j
         float cen = row[R].w;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
         for (int j = 0; j <= 2 * R; ++j) accum_shift(row[j], cen, wxy[j], s0, s1, s2);
         P[idx] = make_float4(s0, s1, s2, cen);
         x += dx_x; r += dr_x;
@@ -471,6 +473,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         int k0 = y - (row0 - R);  // row-offset index of extended row y (tap j = 0)
         float cen = Q[rowoff[k0 + R] + x].w;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
         for (int j = 0; j <= 2 * R; ++j) accum_shift(Q[rowoff[k0 + j] + x], cen, wxy[j], s0, s1, s2);
         float m0, m1, m2;
         bool valid = s0 > thr;
