@@ -98,14 +98,18 @@ size_t fused_smem_bytes_host(const Geom &g, int band) { return fused_smem_bytes(
 
 // Moves a (q0, q1, q2) triple centred on q.w to centre c and accumulates it
 // with weight w (identity 3 above).
+// With t0 = w q0, t1 = w q1 and u = t1 + D t0 the three contributions are
+// t0, u and w q2 + D (u + t1): nine FP32 operations.
 __device__ __forceinline__ void accum_shift(float4 q, float c, float w, float &s0, float &s1, float &s2)
 {
-    float D = q.w - c;
-    float t0 = w * q.x;
-    float t1 = w * q.y;
+    const float D = q.w - c;
+    const float t0 = w * q.x;
+    const float t1 = w * q.y;
+    const float u = fmaf(D, t0, t1);
     s0 += t0;
-    s1 += fmaf(D, t0, t1);
-    s2 += fmaf(w, q.z, D * fmaf(D, t0, 2.f * t1));
+    s1 += u;
+    s2 = fmaf(w, q.z, s2);
+    s2 = fmaf(D, u + t1, s2);
 }
 
 // Unnormalised tap and the full normalisation sum (computed by each thread
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     // ---- phase 1: Gaussian line of every extended spaxel of the band ----
     // Interior channels [elo, ehi) have their whole LSF window inside the band.
     const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;  // v of e = 0
-    const float al = c.alpha, adv = c.alpha * g.dv, inv_al = 1.f / c.alpha;
+    const float al = c.alpha, adv = c.alpha * g.dv, inv_al = 1.f / c.alpha, inv_adv = 1.f / adv;
     const float v_lo = g.vc - 0.5f * (float)(g.nz - 1) * g.dv;  // first and last data channel
     const float v_hi = g.vc + 0.5f * (float)(g.nz - 1) * g.dv;
     const float eref_lo = 0.5f * (float)(elo - 1), eref_hi = 0.5f * (float)(ehi + g.ez - 1);
@@ -314,13 +318,25 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
 
         // interior: sums of g, g m, g m^2 with m = alpha (v_e - a)
         float s0, s1, s2;
-        if (!__any_sync(__activemask(), sh != 0.f)) {
-            // m = u: the Gaussian argument is also the moment variable
+        const unsigned am = __activemask();
+        if (!__any_sync(am, sh != 0.f)) {
+            // m = u: the Gaussian argument is also the moment variable.
+            // Where |u| > 11.25, ex2(-u^2) is below 2^-126 and flushes to +0,
+            // so those channels add exact zeros: the warp runs only the union
+            // of its lanes' windows |u| <= 11.25 (one channel of margin each
+            // side), starting at an even offset to keep the pairing.
+            float flo = (-11.25f - ub) * inv_adv - 1.f, fhi = (11.25f - ub) * inv_adv + 1.f;
+            if (!(flo > -1e6f)) flo = -1e6f;
+            if (!(fhi < 1e6f)) fhi = 1e6f;
+            const int wlo = __reduce_min_sync(am, (int)floorf(flo));
+            const int whi = __reduce_max_sync(am, (int)ceilf(fhi));
+            int e = elo, e_stop = ehi;
+            if (wlo > elo) e = min(ehi, elo + ((wlo - elo) & ~1));
+            if (whi < ehi) e_stop = max(e, whi);
             f32x2 S0 = Z2, S1 = Z2, S2 = Z2;
-            f32x2 FE = pk2((float)elo, (float)(elo + 1));
-            int e = elo;
+            f32x2 FE = pk2((float)e, (float)(e + 1));
 #pragma unroll 6
-            for (; e + 2 <= ehi; e += 2) {
+            for (; e + 2 <= e_stop; e += 2) {
                 f32x2 U = fma2(FE, ADV, UB);
                 f32x2 W = mul2(U, U);
                 float w0, w1;
@@ -333,7 +349,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             s1 = hsum2(S1);
             s2 = hsum2(S2);
             float fe = (float)e;
-            for (; e < ehi; ++e, fe += 1.f) {
+            for (; e < e_stop; ++e, fe += 1.f) {
                 float u0 = fmaf(fe, adv, ub);
                 float w0 = u0 * u0;
                 float g0 = ex2_approx(-w0);
@@ -358,6 +374,13 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         for (int blk = 0; blk < 2; ++blk) {
             int eb = blk ? ehi : 0, ee = blk ? g.ez : elo;
             if (eb >= ee) continue;
+            {
+                // the block adds exact zeros when every lane's |u| > 11.25 over
+                // all of it (u is monotone in the channel: test the ends)
+                const float ua = fmaf((float)eb, adv, ub), uz = fmaf((float)(ee - 1), adv, ub);
+                const bool zero = (ua > 11.25f && uz > 11.25f) || (ua < -11.25f && uz < -11.25f);
+                if (__all_sync(am, zero)) continue;
+            }
             const int toff = blk ? hi_off - ehi : 0;  // table slot = e + toff
             f32x2 E0 = Z2, B1 = Z2, B2 = Z2;
             f32x2 FK = pk2((float)eb, (float)(eb + 1));
