@@ -291,9 +291,10 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
  * options for fitting).  Galaxies are grouped by the thread-block cluster
  * size they need, one launch per group, costliest galaxies first.
  * gbk_survey_fit_lm is gbk_fit_lm per galaxy; the batched mode advances all
- * galaxies together in one CUDA graph, the plain mode fits one galaxy after
- * the other with the host solve; the tangent Jacobian is not served here
- * (GBK_EUNSUPPORTED).
+ * galaxies together in one CUDA graph (finite-difference or analytic tangent
+ * Jacobian; the Jacobian kernel has its own galaxy groups, since its
+ * per-spaxel records are larger), the plain mode fits one galaxy after the
+ * other with the host solve and finite differences.
  * ------------------------------------------------------------------------ */
 GBK_API size_t gbk_survey_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, const gbk_lm_opts *opts);
 GBK_API gbk_status gbk_survey_eval(const gbk_geom *geoms, int32_t n_gal, const double *params, const gbk_obs *obs,

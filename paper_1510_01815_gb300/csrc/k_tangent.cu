@@ -76,16 +76,18 @@ __device__ __forceinline__ void accum_rec(const float *rec, float c, float w, fl
 __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
 {
     cg::cluster_group cluster = cg::this_cluster();
-    const Geom &g = a.g;
     const int cs = a.cs;
     const int rank = (int)cluster.block_rank();
-    const int model = blockIdx.x / cs;
-    const int band = a.band;
+    const int w = blockIdx.x / cs;
+    // ragged batches: one model per galaxy, geometry from the table
+    const int model = a.geoms ? (a.order ? a.order[w] : w) : w;
+    const Geom g = a.geoms ? a.geoms[model] : a.g;
+    const int band = a.geoms ? (g.ey + cs - 1) / cs : a.band;
     const int row0 = tg_band_begin(rank, g.ey, cs), row1 = tg_band_begin(rank + 1, g.ey, cs);
     const int nrows = row1 - row0;
     const int R = g.R;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int gal = a.models_per_gal > 0 ? model / a.models_per_gal : 0;
+    const int gal = a.geoms ? model : (a.models_per_gal > 0 ? model / a.models_per_gal : 0);
     if (a.skip && a.skip[gal] != 0) return;  // the whole cluster returns together
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -385,7 +387,8 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
 
 gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
 {
-    size_t smem = tangent_smem_bytes(args.g, args.band, kTangentThreads);
+    if (args.geoms && args.jac) return fail(GBK_EINVAL, "ragged tangent launches do not write J");
+    size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads);
     static size_t configured = 0;
     static bool cl = false;
     if (smem > configured) {
@@ -413,6 +416,12 @@ gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
     cudaError_t e = cudaLaunchKernelEx(&cfg, tangent_kernel, args);
     if (e != cudaSuccess) return cuda_fail(e, "tangent kernel launch");
     return GBK_OK;
+}
+
+int tangent_cluster_for(const Geom &g)
+{
+    int cs, band;
+    return tangent_config(g, &cs, &band) ? cs : 0;
 }
 
 bool tangent_config(const Geom &g, int *cs, int *band)

@@ -23,10 +23,17 @@ struct TangentArgs {
     double *chi2;            // [n_models] or null: sum of squared residuals
     float *jac;              // [n_models][GBK_NPAR][2][ny][nx] or null
     int cs, band;            // cluster size, most extended rows per CTA
+    // Ragged batches (geoms != null): cluster w serves galaxy order[w] (or w)
+    // with geometry geoms[gal], one model per galaxy; jac must be null.
+    const Geom *geoms;
+    const int32_t *order;
+    size_t smem;             // dynamic shared memory (ragged: the largest need)
 };
 
 size_t tangent_smem_bytes_host(const Geom &g, int band, int threads);
 bool tangent_config(const Geom &g, int *cs, int *band);
+// Smallest cluster size whose CTAs fit the tangent kernel's shared memory.
+int tangent_cluster_for(const Geom &g);
 gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream);
 
 }  // namespace gbk

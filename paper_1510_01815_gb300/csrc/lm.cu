@@ -320,7 +320,7 @@ static gbk_status lm_iteration(const EvalTarget &t, const LmArgs &a, const gbk_o
     gbk_status s;
     if (tangent) {
         // analytic J^T J and J^T r at the current point
-        if ((s = launch_tangent(ta, st))) return s;
+        if ((s = t.sp ? survey_tangent(*t.sp, ta, st) : launch_tangent(ta, st))) return s;
     } else {
         lm_launch_build_fd(a, st);
         s = eval_for(t, a.n_gal, a.m, a.pbatch, obs, a.done, a.chi2_batch, a.resid, st);
@@ -385,13 +385,17 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     lm_launch_init(a, o->lambda0, st);
     TangentArgs ta = {};
     if (pl.tangent) {
-        if (t.sp) return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves one geometry per batch");
-        const Geom &g = *t.g;
-        if (g.model != GBK_MODEL_CUBE)
-            return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves the intensity-cube model");
-        if (!tangent_config(g, &ta.cs, &ta.band))
-            return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
-        ta.g = g;
+        if (t.sp) {
+            if (!t.sp->tangent_ok)
+                return fail(GBK_EUNSUPPORTED, "a galaxy of the batch is too large for the Jacobian kernel");
+        } else {
+            const Geom &g = *t.g;
+            if (g.model != GBK_MODEL_CUBE)
+                return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves the intensity-cube model");
+            if (!tangent_config(g, &ta.cs, &ta.band))
+                return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
+            ta.g = g;
+        }
         ta.n_models = n_gal;
         ta.params = params;
         ta.obs_list = obs;
@@ -403,7 +407,7 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
         ta.jtv = a.jtr;
         // chi2 at the start point from the fused kernel: accept/reject
         // decisions always compare fused-kernel chi2 values
-        gbk_status s0 = fused_for(g, n_gal, params, obs, nullptr, 1, nullptr, a.chi2_cur, nullptr, st);
+        gbk_status s0 = eval_for(t, n_gal, 1, params, obs, nullptr, a.chi2_cur, nullptr, st);
         if (s0) return s0;
     }
     // The first iteration runs eagerly (it also settles the kernels' launch
@@ -443,30 +447,134 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
 
 // Survey batches: the batched mode over a ragged plan, or the plain mode one
 // galaxy (and geometry) at a time.
-size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_lm_opts *o)
+// Galaxies of a plan the Jacobian kernel fits (A) and the rest (B).
+static void tangent_split(const SurveyPlan &sp, std::vector<int32_t> &A, std::vector<int32_t> &B)
+{
+    A.clear();
+    B.clear();
+    for (int i = 0; i < sp.n_gal; ++i) (tangent_cluster_for(sp.geo[i]) > 0 ? A : B).push_back(i);
+}
+
+// Workspace of one batched part of a survey split: its plan's tables and LM state.
+static size_t split_part_bytes(const gbk_geom *geoms, const std::vector<int32_t> &idx, const LmPlan &pl)
+{
+    if (idx.empty()) return 0;
+    std::vector<gbk_geom> sub;
+    for (int32_t i : idx) sub.push_back(geoms[i]);
+    SurveyPlan p;
+    if (survey_plan(sub.data(), (int)sub.size(), &p)) return 0;
+    return p.table_bytes + lm_layout_pix((size_t)p.total_pix(), p.n_gal, pl).total;
+}
+
+// Gathered rows of one part: indices, parameters, bounds, observations and results.
+static size_t split_rows_bytes(int n)
+{
+    return al256(sizeof(int32_t) * n) + 3 * al256(sizeof(double) * GBK_NPAR * n) + al256(sizeof(gbk_obs) * n) +
+           al256(sizeof(double) * n) + 2 * al256(sizeof(int32_t) * n);
+}
+
+size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_geom *geoms, const gbk_lm_opts *o)
 {
     LmPlan pl;
     if (lm_plan(o, &pl)) return 0;
-    if (pl.tangent) {
-        fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves one geometry per batch; use finite differences");
-        return 0;
-    }
     if (o->mode == GBK_LM_PLAIN) {
         size_t m = 256;
         for (const Geom &g : sp.geo) m = std::max(m, lm_layout(g, 1, pl).total);
         return m;
     }
+    if (pl.tangent && !sp.tangent_ok) {
+        // split: the Jacobian kernel where it fits, finite differences elsewhere
+        std::vector<int32_t> A, B;
+        tangent_split(sp, A, B);
+        gbk_lm_opts ofd = *o;
+        ofd.jacobian = GBK_JAC_FD_FORWARD;
+        LmPlan pfd;
+        lm_plan(&ofd, &pfd);
+        size_t a = split_part_bytes(geoms, A, pl), b = split_part_bytes(geoms, B, pfd);
+        if ((!A.empty() && a == 0) || b == 0) return 0;
+        return split_rows_bytes(std::max((int)A.size(), (int)B.size())) + std::max(a, b);
+    }
     return lm_layout_pix((size_t)sp.total_pix(), sp.n_gal, pl).total;
 }
 
-gbk_status lm_survey(SurveyPlan &sp, const gbk_obs *obs, const double *lo, const double *hi, double *params,
-                     const gbk_lm_opts *o, double *chi2_out, int32_t *iters_out, int32_t *status_out, char *ws,
-                     size_t ws_bytes, cudaStream_t st)
+__global__ void rows_copy_kernel(const uint32_t *src, uint32_t *dst, const int32_t *idx, int n, int row_words,
+                                 int scatter)
+{
+    const long total = (long)n * row_words;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(t / row_words), w = (int)(t - (long)r * row_words);
+        const long a = (long)idx[r] * row_words + w, b = (long)r * row_words + w;
+        if (scatter) dst[a] = src[b];
+        else dst[b] = src[a];
+    }
+}
+
+static gbk_status rows_copy(const void *src, void *dst, const int32_t *idx, int n, size_t row_bytes, bool scatter,
+                            cudaStream_t st)
+{
+    if (n == 0) return GBK_OK;
+    const int words = (int)(row_bytes / 4);
+    const long total = (long)n * words;
+    const int blocks = (int)std::min<long>((total + 255) / 256, 152 * 8);
+    rows_copy_kernel<<<blocks, 256, 0, st>>>((const uint32_t *)src, (uint32_t *)dst, idx, n, words, scatter ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "survey split: row copy");
+    return GBK_OK;
+}
+
+// One part of a split survey fit: gather its rows, plan it, fit it batched,
+// scatter the results back.
+static gbk_status fit_part(const gbk_geom *geoms, const std::vector<int32_t> &idx, const gbk_obs *obs,
+                           const double *lo, const double *hi, double *params, const gbk_lm_opts *o,
+                           double *chi2_out, int32_t *iters_out, int32_t *status_out, char *ws, cudaStream_t st)
+{
+    const int n = (int)idx.size();
+    if (n == 0) return GBK_OK;
+    LmPlan pl;
+    gbk_status s = lm_plan(o, &pl);
+    if (s) return s;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char *p = ws + off; off += al256(bytes); return p; };
+    int32_t *d_idx = (int32_t *)take(sizeof(int32_t) * n);
+    double *d_p = (double *)take(sizeof(double) * GBK_NPAR * n);
+    double *d_lo = (double *)take(sizeof(double) * GBK_NPAR * n);
+    double *d_hi = (double *)take(sizeof(double) * GBK_NPAR * n);
+    gbk_obs *d_obs = (gbk_obs *)take(sizeof(gbk_obs) * n);
+    double *d_c = (double *)take(sizeof(double) * n);
+    int32_t *d_it = (int32_t *)take(sizeof(int32_t) * n);
+    int32_t *d_st = (int32_t *)take(sizeof(int32_t) * n);
+    char *rest = ws + split_rows_bytes(n);
+    cudaError_t e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "survey split: index upload");
+    const size_t prow = sizeof(double) * GBK_NPAR;
+    if ((s = rows_copy(params, d_p, d_idx, n, prow, false, st)) || (s = rows_copy(lo, d_lo, d_idx, n, prow, false, st)) ||
+        (s = rows_copy(hi, d_hi, d_idx, n, prow, false, st)) ||
+        (s = rows_copy(obs, d_obs, d_idx, n, sizeof(gbk_obs), false, st)))
+        return s;
+    std::vector<gbk_geom> sub;
+    for (int32_t i : idx) sub.push_back(geoms[i]);
+    SurveyPlan sp;
+    if ((s = survey_plan(sub.data(), n, &sp))) return s;
+    if ((s = survey_upload(&sp, rest, st))) return s;
+    EvalTarget t = {nullptr, &sp};
+    if ((s = lm_batched(t, n, d_obs, d_lo, d_hi, d_p, o, pl, d_c, d_it, d_st, rest + sp.table_bytes, st))) return s;
+    if ((s = rows_copy(d_p, params, d_idx, n, prow, true, st)) || (s = rows_copy(d_c, chi2_out, d_idx, n, 8, true, st)) ||
+        (s = rows_copy(d_it, iters_out, d_idx, n, 4, true, st)) || (s = rows_copy(d_st, status_out, d_idx, n, 4, true, st)))
+        return s;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "survey split: results");
+    return GBK_OK;
+}
+
+gbk_status lm_survey(SurveyPlan &sp, const gbk_geom *geoms, const gbk_obs *obs, const double *lo, const double *hi,
+                     double *params, const gbk_lm_opts *o, double *chi2_out, int32_t *iters_out, int32_t *status_out,
+                     char *ws, size_t ws_bytes, cudaStream_t st)
 {
     LmPlan pl;
     gbk_status s = lm_plan(o, &pl);
     if (s) return s;
-    if (ws_bytes < lm_survey_workspace(sp, o)) return fail(GBK_EWORKSPACE, "survey LM workspace too small");
+    const size_t need = lm_survey_workspace(sp, geoms, o);
+    if (need == 0 || ws_bytes < need) return fail(GBK_EWORKSPACE, "survey LM workspace too small");
     if (o->mode == GBK_LM_PLAIN) {
         for (int i = 0; i < sp.n_gal; ++i) {
             const size_t q = (size_t)i * GBK_NPAR;
@@ -474,6 +582,16 @@ gbk_status lm_survey(SurveyPlan &sp, const gbk_obs *obs, const double *lo, const
                          status_out + i, ws, st);
             if (s) return s;
         }
+        return ok();
+    }
+    if (pl.tangent && !sp.tangent_ok) {
+        std::vector<int32_t> A, B;
+        tangent_split(sp, A, B);
+        gbk_lm_opts ofd = *o;
+        ofd.jacobian = GBK_JAC_FD_FORWARD;
+        if ((s = fit_part(geoms, A, obs, lo, hi, params, o, chi2_out, iters_out, status_out, ws, st)) ||
+            (s = fit_part(geoms, B, obs, lo, hi, params, &ofd, chi2_out, iters_out, status_out, ws, st)))
+            return s;
         return ok();
     }
     EvalTarget t = {nullptr, &sp};

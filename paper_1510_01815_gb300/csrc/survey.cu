@@ -15,6 +15,7 @@
 
 #include "gbk_api_internal.h"
 #include "k_fused.h"
+#include "k_tangent.h"
 #include "survey.h"
 
 namespace gbk {
@@ -82,9 +83,39 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
         sp->classes.push_back(c);
         k = e;
     }
+    // classes of the analytic Jacobian kernel: smallest cluster whose CTAs fit
+    std::vector<int> tcs(n_gal);
+    sp->tangent_ok = true;
+    for (int i = 0; i < n_gal; ++i) {
+        tcs[i] = tangent_cluster_for(sp->geo[i]);
+        if (tcs[i] == 0) sp->tangent_ok = false;
+    }
+    sp->torder.resize(n_gal);
+    std::iota(sp->torder.begin(), sp->torder.end(), 0);
+    std::stable_sort(sp->torder.begin(), sp->torder.end(), [&](int a, int b) {
+        if (tcs[a] != tcs[b]) return tcs[a] > tcs[b];
+        return cost(a) > cost(b);
+    });
+    sp->tclasses.clear();
+    for (int k = 0; k < n_gal && sp->tangent_ok;) {
+        int i0 = sp->torder[k], e = k;
+        while (e < n_gal && tcs[sp->torder[e]] == tcs[i0]) ++e;
+        SurveyClass c;
+        c.cs = tcs[i0];
+        c.threads = kTangentThreads;
+        c.beg = k;
+        c.end = e;
+        c.smem = 0;
+        for (int j = k; j < e; ++j) {
+            const Geom &g = sp->geo[sp->torder[j]];
+            c.smem = std::max(c.smem, tangent_smem_bytes_host(g, (g.ey + c.cs - 1) / c.cs, kTangentThreads));
+        }
+        sp->tclasses.push_back(c);
+        k = e;
+    }
     sp->table_bytes = n_gal == 0 ? 0
                                  : al256(sizeof(Geom) * n_gal) + al256(sizeof(int64_t) * (n_gal + 1)) +
-                                       al256(sizeof(int32_t) * n_gal);
+                                       2 * al256(sizeof(int32_t) * n_gal);
     return GBK_OK;
 }
 
@@ -92,10 +123,12 @@ gbk_status survey_upload(SurveyPlan *sp, char *ws, cudaStream_t st)
 {
     const int n = sp->n_gal;
     size_t o_geo = 0, o_pix = al256(sizeof(Geom) * n), o_ord = o_pix + al256(sizeof(int64_t) * (n + 1));
+    size_t o_tord = o_ord + al256(sizeof(int32_t) * n);
     std::vector<char> h(sp->table_bytes, 0);
     std::memcpy(h.data() + o_geo, sp->geo.data(), sizeof(Geom) * n);
     std::memcpy(h.data() + o_pix, sp->pix_off.data(), sizeof(int64_t) * (n + 1));
     std::memcpy(h.data() + o_ord, sp->order.data(), sizeof(int32_t) * n);
+    std::memcpy(h.data() + o_tord, sp->torder.data(), sizeof(int32_t) * n);
     // From pageable memory the copy returns once the source has been staged,
     // so h may be released afterwards.
     cudaError_t e = cudaMemcpyAsync(ws, h.data(), h.size(), cudaMemcpyHostToDevice, st);
@@ -103,6 +136,28 @@ gbk_status survey_upload(SurveyPlan *sp, char *ws, cudaStream_t st)
     sp->d_geo = (Geom *)(ws + o_geo);
     sp->d_pix_off = (int64_t *)(ws + o_pix);
     sp->d_order = (int32_t *)(ws + o_ord);
+    sp->d_torder = (int32_t *)(ws + o_tord);
+    return GBK_OK;
+}
+
+gbk_status survey_tangent(const SurveyPlan &sp, const TangentArgs &proto, cudaStream_t st)
+{
+    if (!sp.tangent_ok) return fail(GBK_EUNSUPPORTED, "a galaxy of the batch is too large for the Jacobian kernel");
+    for (const SurveyClass &c : sp.tclasses) {
+        TangentArgs a = proto;
+        a.g = sp.geo[sp.torder[c.beg]];
+        a.n_models = c.end - c.beg;
+        a.models_per_gal = 1;
+        a.jac = nullptr;
+        a.cot = nullptr;
+        a.cs = c.cs;
+        a.band = 0;
+        a.geoms = sp.d_geo;
+        a.order = sp.d_torder + c.beg;
+        a.smem = c.smem;
+        gbk_status s = launch_tangent(a, st);
+        if (s) return s;
+    }
     return GBK_OK;
 }
 
@@ -135,10 +190,10 @@ gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, cons
 }
 
 // Batched LM over a plan (lm.cu).
-gbk_status lm_survey(SurveyPlan &sp, const gbk_obs *obs, const double *lo, const double *hi, double *params,
-                     const gbk_lm_opts *o, double *chi2_out, int32_t *iters_out, int32_t *status_out, char *ws,
-                     size_t ws_bytes, cudaStream_t st);
-size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_lm_opts *o);
+gbk_status lm_survey(SurveyPlan &sp, const gbk_geom *geoms, const gbk_obs *obs, const double *lo, const double *hi,
+                     double *params, const gbk_lm_opts *o, double *chi2_out, int32_t *iters_out, int32_t *status_out,
+                     char *ws, size_t ws_bytes, cudaStream_t st);
+size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_geom *geoms, const gbk_lm_opts *o);
 
 }  // namespace gbk
 
@@ -152,7 +207,7 @@ size_t gbk_survey_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, const gb
     SurveyPlan sp;
     if (survey_plan(geoms, n_gal, &sp)) return 0;
     if (!opts) return sp.table_bytes;
-    size_t lm = lm_survey_workspace(sp, opts);
+    size_t lm = lm_survey_workspace(sp, geoms, opts);
     if (lm == 0) return 0;
     return sp.table_bytes + lm;
 }
@@ -187,7 +242,7 @@ gbk_status gbk_survey_fit_lm(const gbk_geom *geoms, int32_t n_gal, const gbk_obs
     gbk_status s = survey_plan(geoms, n_gal, &sp);
     if (s) return s;
     if (!opts) return fail(GBK_EINVAL, "opts is NULL");
-    size_t lm = lm_survey_workspace(sp, opts);
+    size_t lm = lm_survey_workspace(sp, geoms, opts);
     if (lm == 0) return fail(GBK_EINVAL, "%s", gbk_last_error());
     if (n_gal == 0) return ok();
     if ((s = check_device_ptr(obs, "obs", 8)) || (s = check_device_ptr(lo, "lo", 8)) ||
@@ -201,7 +256,7 @@ gbk_status gbk_survey_fit_lm(const gbk_geom *geoms, int32_t n_gal, const gbk_obs
     if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = survey_upload(&sp, (char *)workspace, st))) return s;
-    return lm_survey(sp, obs, lo, hi, params, opts, chi2_out, iters_out, status_out,
+    return lm_survey(sp, geoms, obs, lo, hi, params, opts, chi2_out, iters_out, status_out,
                      (char *)workspace + sp.table_bytes, ws_bytes - sp.table_bytes, st);
 }
 

@@ -21,11 +21,16 @@ struct SurveyPlan {
     std::vector<int64_t> pix_off;   // n_gal + 1 prefix sums of nx * ny
     std::vector<int32_t> order;     // galaxies grouped by class, costliest first
     std::vector<SurveyClass> classes;
+    // the same for the analytic Jacobian kernel (larger per-spaxel records)
+    std::vector<int32_t> torder;
+    std::vector<SurveyClass> tclasses;
+    bool tangent_ok = true;         // every galaxy fits the Jacobian kernel
     size_t table_bytes = 0;         // device tables at the start of the workspace
     // device copies (inside the workspace) after survey_upload
     Geom *d_geo = nullptr;
     int64_t *d_pix_off = nullptr;
     int32_t *d_order = nullptr;
+    int32_t *d_torder = nullptr;
     int64_t total_pix() const { return pix_off.empty() ? 0 : pix_off.back(); }
 };
 
@@ -35,5 +40,9 @@ gbk_status survey_upload(SurveyPlan *sp, char *ws, cudaStream_t st);
 // packed maps / residuals (galaxy gal at pixel offset pix_off[gal] * mpg).
 gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, const gbk_obs *obs_list,
                        const int32_t *skip, float *maps, double *chi2, float *resid, cudaStream_t st);
+struct TangentArgs;
+// J^T J, J^T r and chi2 of one model per galaxy (the analytic Jacobian):
+// `proto` supplies params, obs_list, skip, the free parameters and outputs.
+gbk_status survey_tangent(const SurveyPlan &sp, const TangentArgs &proto, cudaStream_t st);
 
 }  // namespace gbk

@@ -164,8 +164,10 @@ def test_survey_host_logic(gbk):
     # the plain mode needs room for one galaxy at a time
     assert gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(mode=gbk.LM_PLAIN)) < lm
     assert gbk.gbk_survey_workspace_bytes([], None) == 0
+    # the analytic Jacobian needs no finite-difference batch
+    assert tables < gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT)) < lm
     with pytest.raises(gbk.GbkError):
-        gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT))
+        gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT, mode=gbk.LM_PLAIN))
     with pytest.raises(gbk.GbkError):
         gbk.gbk_survey_workspace_bytes(geoms + [SINGLE_GEOM.with_(upsample=2)])
     with pytest.raises(gbk.GbkError):
