@@ -55,7 +55,7 @@ SURVEY_FP32_PER_DATA_VOXEL = 47.0
 # DRAM bytes (read + write) of one fused launch of 400 Fabry-Perot models at
 # the tuning (12 CTAs, 512 threads, one cluster per model), from the ncu
 # capture summarised in profiles/fused_eval_fabry_perot_400models.md.
-FUSED_TRAFFIC_400 = None  # the kernel changed since the last capture
+FUSED_TRAFFIC_400 = 744448.0
 FUSED_TRAFFIC_TUNING = (12, 512, 0)
 FLUSH_BYTES = 256 << 20
 
@@ -76,8 +76,8 @@ def parse():
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned-seed (CNN) measurement")
     ap.add_argument("--no-vfield", action="store_true", help="skip the velocity-field (Epinat) measurement")
     ap.add_argument("--no-gemm", action="store_true", help="skip the tensor-core GEMM measurement")
-    ap.add_argument("--cnn-train", type=int, default=262144, help="training galaxies of the CNN seed")
-    ap.add_argument("--cnn-epochs", type=int, default=4)
+    ap.add_argument("--cnn-train", type=int, default=1048576, help="training galaxies of the CNN seed")
+    ap.add_argument("--cnn-epochs", type=int, default=2)
     ap.add_argument("--cnn-batch", type=int, default=1024)
     ap.add_argument("--cnn-test", type=int, default=4096, help="held-out galaxies of the seed comparison")
     ap.add_argument("--path", default="fused", choices=["fused", "staged"],
@@ -328,7 +328,7 @@ def run_survey(gbk, torch, n, n_plain, device):
     return out
 
 
-CNN_LAYER_MNK = ((256, 64, 48), (64, 128, 256), (16, 256, 512), (1, 256, 4096), (1, 16, 256))
+CNN_LAYER_MNK = ((1024, 32, 16), (256, 64, 128), (64, 128, 256), (16, 256, 512), (1, 256, 4096), (1, 16, 256))
 
 
 def cnn_flops_per_sample():
@@ -402,7 +402,7 @@ def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device):
                     "gemm_tflops": flops / (ms * 1e-3) / 1e12, "bf16_peak_tflops": peak,
                     "tensor_frac": flops / (ms * 1e-3) / 1e12 / peak, "first_loss": first_loss,
                     "final_loss": float(net.loss),
-                    "note": "whole training step (encode, 5 forward, 5+4 backward GEMMs, split-K sums, Adam) per "
+                    "note": "whole training step (encode, 6 forward, 6+5 backward GEMMs, split-K sums, Adam) per "
                             "launch sequence; flops count the GEMMs only; peak = measured cuBLAS bf16 sustained"}
     del v, s, m, t
     # held-out galaxies (seed 5)

@@ -429,10 +429,11 @@ GBK_API gbk_status gbk_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A,
  * CNN seed: a convolutional network that maps a galaxy's observed velocity
  * and dispersion maps to model parameters, the learned replacement for the
  * heuristic initial guess of the optimisers (Sec. 2.1.9).  Fixed
- * architecture for 64 x 64 maps (all convolutions stride = kernel):
- *   input 64x64x3 (v / 200 km/s, sigma / 100 km/s, mask; masked -> 0)
- *   conv 4x4 -> 16x16x64, ReLU; conv 2x2 -> 8x8x128, ReLU;
- *   conv 2x2 -> 4x4x256, ReLU; dense 4096 -> 256, ReLU; dense 256 -> 16.
+ * architecture for 64 x 64 maps (all convolutions 2 x 2, stride 2), four
+ * convolutions and a two-layer MLP head, 1,225,968 parameters:
+ *   input 64x64x4 (v / 200 km/s, sigma / 100 km/s, mask, 0; masked -> 0)
+ *   conv -> 32x32x32, ReLU; conv -> 16x16x64, ReLU; conv -> 8x8x128, ReLU;
+ *   conv -> 4x4x256, ReLU; dense 4096 -> 256, ReLU; dense 256 -> 16.
  * Parameters are one FP32 vector of gbk_cnn_param_count() floats: layer l
  * is [C_l][K_l + 1] (weights W_l[o][k], bias in column K_l), layers in
  * order; patch index k = (dy * p + dx) * C_in + c, and the dense layer's

@@ -4,8 +4,9 @@ check and the bench's CPU leg use it).
 The network maps observed velocity and dispersion maps (64 x 64) to the
 parameters the optimisers of Sec. 2.3 start from, replacing the heuristic
 initial guess of Sec. 2.1.9.  It is defined as:
-  input  x[n][64][64][3] = (v / 200, sigma / 100, mask), 0 where masked
-  conv   4 x 4 stride 4 -> 16 x 16 x 64,  ReLU
+  input  x[n][64][64][4] = (v / 200, sigma / 100, mask, 0), 0 where masked
+  conv   2 x 2 stride 2 -> 32 x 32 x 32,  ReLU
+  conv   2 x 2 stride 2 -> 16 x 16 x 64,  ReLU
   conv   2 x 2 stride 2 ->  8 x  8 x 128, ReLU
   conv   2 x 2 stride 2 ->  4 x  4 x 256, ReLU
   dense  flatten f[morton(y, x) * 256 + c] -> 256, ReLU
@@ -22,9 +23,10 @@ import math
 import numpy as np
 
 MAP = 64
-C = (64, 128, 256, 256, 16)
-K = (48, 256, 512, 4096, 256)
-P_SIZE = (4, 2, 2)          # conv kernel = stride of the three convolutions
+C = (32, 64, 128, 256, 256, 16)
+K = (16, 128, 256, 512, 4096, 256)
+P_SIZE = (2, 2, 2, 2)       # conv kernel = stride of the four convolutions
+NL = len(C)
 N_OUT, N_T = 16, 10
 V_SCALE, S_SCALE = 200.0, 100.0
 GOLDEN = 0x9E3779B97F4A7C15
@@ -46,7 +48,7 @@ def unpack(P):
     """[(W_l [C_l][K_l], b_l [C_l])] from the parameter vector."""
     off = param_offsets()
     out = []
-    for l in range(5):
+    for l in range(NL):
         blk = np.asarray(P[off[l]:off[l + 1]], dtype=np.float64).reshape(C[l], K[l] + 1)
         out.append((blk[:, :K[l]], blk[:, K[l]]))
     return out
@@ -65,9 +67,10 @@ def morton(y, x, bits):
 
 
 def encode(v, s, mask):
-    """x [n][64][64][3] from maps [n][64][64]."""
+    """x [n][64][64][4] from maps [n][64][64] (the fourth channel is zero)."""
     m = (np.asarray(mask) != 0).astype(np.float64)
-    return np.stack([np.asarray(v, np.float64) / V_SCALE * m, np.asarray(s, np.float64) / S_SCALE * m, m], axis=-1)
+    return np.stack([np.asarray(v, np.float64) / V_SCALE * m, np.asarray(s, np.float64) / S_SCALE * m, m,
+                     np.zeros_like(m)], axis=-1)
 
 
 def conv(x, W, b, p):
@@ -121,34 +124,35 @@ def unflatten(f):
 def forward(P, x):
     """Outputs [n][16] and the activations needed by backward()."""
     L = unpack(P)
-    h1 = np.maximum(conv(x, *L[0], 4), 0.0)
-    h2 = np.maximum(conv(h1, *L[1], 2), 0.0)
-    h3 = np.maximum(conv(h2, *L[2], 2), 0.0)
-    f = flatten(h3)
-    h4 = np.maximum(f @ L[3][0].T + L[3][1], 0.0)
-    y = h4 @ L[4][0].T + L[4][1]
-    return y, (x, h1, h2, h3, f, h4)
+    hs = [x]
+    for l in range(4):
+        hs.append(np.maximum(conv(hs[-1], *L[l], P_SIZE[l]), 0.0))
+    f = flatten(hs[-1])
+    h5 = np.maximum(f @ L[4][0].T + L[4][1], 0.0)
+    y = h5 @ L[5][0].T + L[5][1]
+    return y, (hs, f, h5)
 
 
 def loss_and_grad(P, x, t):
     """Mean squared error over the 10 used outputs and its gradient."""
     L = unpack(P)
-    y, (x, h1, h2, h3, f, h4) = forward(P, x)
+    y, (hs, f, h5) = forward(P, x)
     n = x.shape[0]
     d = np.zeros_like(y)
     d[:, :N_T] = y[:, :N_T] - t
     loss = float(np.sum(d * d) / (n * N_T))
     dy = 2.0 * d / (n * N_T)
-    g5 = (dy.T @ h4, dy.sum(0))
-    dz4 = (dy @ L[4][0]) * (h4 > 0)
-    g4 = (dz4.T @ f, dz4.sum(0))
-    dz3 = unflatten(dz4 @ L[3][0]) * (h3 > 0)
-    W3, b3, dh2 = conv_backward(h2, L[2][0], dz3, 2)
-    dz2 = dh2 * (h2 > 0)
-    W2, b2, dh1 = conv_backward(h1, L[1][0], dz2, 2)
-    dz1 = dh1 * (h1 > 0)
-    W1, b1, _ = conv_backward(x, L[0][0], dz1, 4)
-    return loss, pack([(W1, b1), (W2, b2), (W3, b3), g4, g5])
+    g6 = (dy.T @ h5, dy.sum(0))
+    dz5 = (dy @ L[5][0]) * (h5 > 0)
+    g5 = (dz5.T @ f, dz5.sum(0))
+    dz = unflatten(dz5 @ L[4][0]) * (hs[4] > 0)
+    grads = []
+    for l in range(3, -1, -1):
+        W, b, dh = conv_backward(hs[l], L[l][0], dz, P_SIZE[l])
+        grads.insert(0, (W, b))
+        if l > 0:
+            dz = dh * (hs[l] > 0)
+    return loss, pack(grads + [g5, g6])
 
 
 def targets(params):
@@ -204,8 +208,8 @@ def init(seed):
     parameter i uses normal number i of the stream."""
     off = param_offsets()
     P = np.zeros(off[-1])
-    for l in range(5):
-        sd = math.sqrt((1.0 if l == 4 else 2.0) / K[l])
+    for l in range(NL):
+        sd = math.sqrt((1.0 if l == NL - 1 else 2.0) / K[l])
         for j in range(C[l] * (K[l] + 1)):
             if j % (K[l] + 1) != K[l]:
                 P[off[l] + j] = sd * sm_normal(seed, off[l] + j)

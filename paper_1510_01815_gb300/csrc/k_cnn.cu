@@ -4,9 +4,10 @@
 // (Sec. 2.1.9); this learned guess replaces it.  Every dense operation runs
 // on the tensor cores through the tcgen05 GEMM of k_gemm.cu.
 //
-// Network (all convolutions have stride = kernel size):
-//   input  64 x 64 x 3   (v / 200 km/s, sigma / 100 km/s, mask; masked -> 0)
-//   conv   4 x 4 -> 16 x 16 x 64,  ReLU
+// Network (all convolutions have stride = kernel size), 1.23 M parameters:
+//   input  64 x 64 x 4   (v / 200 km/s, sigma / 100 km/s, mask, 0; masked -> 0)
+//   conv   2 x 2 -> 32 x 32 x 32,  ReLU
+//   conv   2 x 2 -> 16 x 16 x 64,  ReLU
 //   conv   2 x 2 ->  8 x  8 x 128, ReLU
 //   conv   2 x 2 ->  4 x  4 x 256, ReLU
 //   dense  4096  -> 256, ReLU       (flatten index = morton(y, x) * 256 + c)
@@ -32,10 +33,11 @@
 namespace gbk {
 
 constexpr int kCnnMap = 64;
-constexpr int kCnnL = 5;
-constexpr int kCnnC[kCnnL] = {64, 128, 256, 256, 16};     // outputs per layer
-constexpr int kCnnK[kCnnL] = {48, 256, 512, 4096, 256};   // inputs per layer
-constexpr int kCnnRows[kCnnL] = {256, 64, 16, 1, 1};      // matrix rows per sample
+constexpr int kCnnL = 6;
+constexpr int kCnnC[kCnnL] = {32, 64, 128, 256, 256, 16};      // outputs per layer
+constexpr int kCnnK[kCnnL] = {16, 128, 256, 512, 4096, 256};   // inputs per layer
+constexpr int kCnnRows[kCnnL] = {1024, 256, 64, 16, 1, 1};     // matrix rows per sample
+constexpr int kCnnIn = 4;                                      // input channels
 constexpr int kCnnOut = 16, kCnnTargets = 10;
 constexpr float kVScale = 200.f, kSScale = 100.f;
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
@@ -128,47 +130,50 @@ __global__ void cnn_publish_kernel(const float *P, CnnTables t)
     }
 }
 
-// Input encoding: sample b, 4 x 4 patch (Y, X) -> row b * 256 + morton(Y, X);
-// column (dy * 4 + dx) * 3 + ch.  Also the transposed matrix with a row of
-// ones at index 48.  One thread per patch: four 16-byte loads of v and sigma
-// and four 4-byte mask loads, one 96-byte row store, and 49 transposed stores
-// that are coalesced across the warp (consecutive threads, consecutive rows).
+// Input encoding: sample b, 2 x 2 patch (Y, X) -> row b * 1024 + morton(Y, X);
+// column (dy * 2 + dx) * 4 + ch.  Also the transposed matrix with a row of
+// ones at index 16.  One thread per patch: two 8-byte loads each of v and
+// sigma and two 2-byte mask loads, one 32-byte row store, and 17 transposed
+// stores that are coalesced across the warp (consecutive threads, consecutive
+// rows).
 __global__ void cnn_encode_kernel(int n, const float *v, const float *s, const uint8_t *mask, __nv_bfloat16 *A,
                                   __nv_bfloat16 *AT)
 {
-    const size_t rows = (size_t)n * 256;
+    constexpr int kRows = kCnnRows[0], kK = kCnnK[0];
+    const size_t rows = (size_t)n * kRows;
     for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < rows; r += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(r / 256), q = (int)(r % 256);
+        const int b = (int)(r / kRows), q = (int)(r % kRows);
         int Y = 0, X = 0;
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 5; ++k) {
             X |= ((q >> (2 * k)) & 1) << k;
             Y |= ((q >> (2 * k + 1)) & 1) << k;
         }
-        __align__(16) __nv_bfloat16 h[48];
+        __align__(16) __nv_bfloat16 h[kK];
 #pragma unroll
-        for (int dy = 0; dy < 4; ++dy) {
-            const size_t pix = (size_t)b * kCnnMap * kCnnMap + (size_t)(4 * Y + dy) * kCnnMap + 4 * X;
-            const float4 vv = *reinterpret_cast<const float4 *>(v + pix);
-            const float4 ss = *reinterpret_cast<const float4 *>(s + pix);
-            const uchar4 mm = *reinterpret_cast<const uchar4 *>(mask + pix);
-            const float vx[4] = {vv.x, vv.y, vv.z, vv.w}, sx[4] = {ss.x, ss.y, ss.z, ss.w};
-            const unsigned char mx[4] = {mm.x, mm.y, mm.z, mm.w};
+        for (int dy = 0; dy < 2; ++dy) {
+            const size_t pix = (size_t)b * kCnnMap * kCnnMap + (size_t)(2 * Y + dy) * kCnnMap + 2 * X;
+            const float2 vv = *reinterpret_cast<const float2 *>(v + pix);
+            const float2 ss = *reinterpret_cast<const float2 *>(s + pix);
+            const uchar2 mm = *reinterpret_cast<const uchar2 *>(mask + pix);
+            const float vx[2] = {vv.x, vv.y}, sx[2] = {ss.x, ss.y};
+            const unsigned char mx[2] = {mm.x, mm.y};
 #pragma unroll
-            for (int dx = 0; dx < 4; ++dx) {
+            for (int dx = 0; dx < 2; ++dx) {
                 const bool on = mx[dx] != 0;
-                const int e = (dy * 4 + dx) * 3;
+                const int e = (dy * 2 + dx) * kCnnIn;
                 h[e] = __float2bfloat16_rn(on ? vx[dx] / kVScale : 0.f);
                 h[e + 1] = __float2bfloat16_rn(on ? sx[dx] / kSScale : 0.f);
                 h[e + 2] = __float2bfloat16_rn(on ? 1.f : 0.f);
+                h[e + 3] = __float2bfloat16_rn(0.f);
             }
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(A + r * 48);
+        uint4 *dst = reinterpret_cast<uint4 *>(A + r * kK);
         const uint4 *src = reinterpret_cast<const uint4 *>(h);
+        dst[0] = src[0];
+        dst[1] = src[1];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) dst[k] = src[k];
-#pragma unroll
-        for (int e = 0; e < 48; ++e) AT[(size_t)e * rows + r] = h[e];
-        AT[(size_t)48 * rows + r] = __float2bfloat16_rn(1.f);
+        for (int e = 0; e < kK; ++e) AT[(size_t)e * rows + r] = h[e];
+        AT[(size_t)kK * rows + r] = __float2bfloat16_rn(1.f);
     }
 }
 
@@ -289,7 +294,7 @@ struct CnnWs {
     __nv_bfloat16 *AT[kCnnL];   // [K_l + 1][M_l], last row ones
     float *Y;                   // [B][16]
     __nv_bfloat16 *dY, *dYT;    // [B][16], [16][B]
-    __nv_bfloat16 *dZ[kCnnL];   // dZ_l (l < 4) stored in A_{l+1}'s layout
+    __nv_bfloat16 *dZ[kCnnL];   // dZ_l (l < L - 1) stored in A_{l+1}'s layout
     __nv_bfloat16 *dZT[kCnnL];  // [C_l][M_l]
     float *G;                   // gradient, parameter layout
     float *part;                // split-K slices
@@ -401,7 +406,7 @@ static gbk_status cnn_forward_ws(const CnnWs &w, int B, bool want_transposed, cu
 static gbk_status cnn_encode(const CnnWs &w, int B, const float *v, const float *sg, const uint8_t *mask,
                              cudaStream_t st)
 {
-    cnn_encode_kernel<<<grid_for((size_t)B * 256), 256, 0, st>>>(B, v, sg, mask, w.A[0], w.AT[0]);
+    cnn_encode_kernel<<<grid_for((size_t)B * kCnnRows[0]), 256, 0, st>>>(B, v, sg, mask, w.A[0], w.AT[0]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "CNN encode launch");
     return GBK_OK;
@@ -466,7 +471,11 @@ static gbk_status cnn_grad_ws(const CnnWs &w, const float *P, int B, const float
 static gbk_status check_batch(int B)
 {
     if (B < 8 || B % 8 != 0) return fail(GBK_EINVAL, "batch must be a positive multiple of 8 (got %d)", B);
-    if ((size_t)B * 256 * 64 > (size_t)1 << 31) return fail(GBK_EINVAL, "batch too large");
+    // every activation matrix (and its transpose) stays below 2^31 elements
+    for (int l = 0; l < kCnnL; ++l)
+        if ((size_t)B * kCnnRows[l] * (kCnnK[l] + 1) >= (size_t)1 << 31 ||
+            (size_t)B * kCnnRows[l] * kCnnC[l] >= (size_t)1 << 31)
+            return fail(GBK_EINVAL, "batch too large");
     return GBK_OK;
 }
 
@@ -538,7 +547,8 @@ gbk_status gbk_cnn_synth_obs(int32_t n, const float *maps, uint64_t seed, float 
     return ok();
 }
 
-// The encoding reads 4-pixel runs as 16-byte (maps) and 4-byte (mask) vectors.
+// The encoding reads 2-pixel runs as 8-byte (maps) and 2-byte (mask) vectors;
+// the contract asks for 16- and 4-byte alignment.
 static gbk_status check_maps_in(const float *v, const float *sg, const uint8_t *mask)
 {
     gbk_status s;

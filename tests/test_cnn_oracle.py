@@ -32,12 +32,12 @@ def test_conv_equals_direct_loops():
 
 
 def test_morton_structure():
-    q = np.array([[cnn.morton(y, x, 4) for x in range(16)] for y in range(16)])
-    assert sorted(q.ravel().tolist()) == list(range(256))            # a bijection
-    for y in range(16):
-        for x in range(16):
+    q = np.array([[cnn.morton(y, x, 5) for x in range(32)] for y in range(32)])
+    assert sorted(q.ravel().tolist()) == list(range(1024))           # a bijection
+    for y in range(32):
+        for x in range(32):
             # the 2 x 2 block of (y, x) is the run q >> 2, its position in the block q & 3
-            assert q[y, x] >> 2 == cnn.morton(y >> 1, x >> 1, 3)
+            assert q[y, x] >> 2 == cnn.morton(y >> 1, x >> 1, 4)
             assert q[y, x] & 3 == (y & 1) * 2 + (x & 1)
     f = np.random.default_rng(2).normal(size=(3, 4, 4, 256))
     np.testing.assert_array_equal(cnn.unflatten(cnn.flatten(f)), f)
@@ -47,7 +47,7 @@ def _small_problem(seed=3, n=2):
     rng = np.random.default_rng(seed)
     P = np.zeros(cnn.param_count())
     off = cnn.param_offsets()
-    for l in range(5):
+    for l in range(cnn.NL):
         blk = rng.normal(size=(cnn.C[l], cnn.K[l] + 1)) * math.sqrt(2.0 / cnn.K[l])
         blk[:, -1] = rng.normal(size=cnn.C[l]) * 0.1
         P[off[l]:off[l + 1]] = blk.ravel()
@@ -64,7 +64,7 @@ def test_gradient_matches_finite_differences():
     off = cnn.param_offsets()
     rng = np.random.default_rng(4)
     checked = 0
-    for l in range(5):
+    for l in range(cnn.NL):
         idx = list(rng.choice(np.arange(off[l], off[l + 1]), size=8, replace=False))
         idx.append(off[l] + cnn.K[l])  # a bias
         for i in idx:
@@ -82,7 +82,7 @@ def test_gradient_matches_finite_differences():
                     break
             assert ok, (l, i, fd, g[i])
             checked += 1
-    assert checked == 45
+    assert checked == 9 * cnn.NL
 
 
 def test_loss_definition():
@@ -98,8 +98,8 @@ def test_encode_masks_and_scales():
     m = np.ones((1, 64, 64), np.uint8)
     m[0, 3, 5] = 0
     x = cnn.encode(v, s, m)
-    assert x[0, 0, 0].tolist() == [0.5, 0.5, 1.0]
-    assert x[0, 3, 5].tolist() == [0.0, 0.0, 0.0]
+    assert x[0, 0, 0].tolist() == [0.5, 0.5, 1.0, 0.0]
+    assert x[0, 3, 5].tolist() == [0.0, 0.0, 0.0, 0.0]
 
 
 def test_targets_decode_round_trip():
