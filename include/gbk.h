@@ -288,8 +288,13 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
  * FP64 reduction).  The workspace holds the geometry tables, uploaded from
  * the host on every call, and, for the fit, the batched LM state
  * (gbk_survey_workspace_bytes with opts NULL for evaluation, with the LM
- * options for fitting).  Galaxies are grouped by the thread-block cluster
- * size they need, one launch per group, costliest galaxies first.
+ * options for fitting).  By default the evaluator serves the whole survey
+ * in one persistent launch: a resident wave of thread-block clusters of one
+ * size takes the models, costliest galaxies first, from a work counter in
+ * the workspace as each cluster becomes free.  The alternative shape, one
+ * launch per group of galaxies needing the same cluster size, and the
+ * cluster and block sizes of the single launch are a survey tuning
+ * (gbk_survey_autotune below).
  * gbk_survey_fit_lm is gbk_fit_lm per galaxy; the batched mode advances all
  * galaxies together in one CUDA graph (finite-difference or analytic tangent
  * Jacobian; the Jacobian kernel has its own galaxy groups, since its
@@ -388,6 +393,25 @@ GBK_API gbk_status gbk_get_tuning(const gbk_geom *g, gbk_tuning *out);
 /* Sets the tuning for this geometry (e.g. one saved from an earlier
  * gbk_autotune); t == NULL forgets it.  EINVAL if it cannot run here. */
 GBK_API gbk_status gbk_set_tuning(const gbk_geom *g, const gbk_tuning *t);
+
+/* Survey tunings: how the fused evaluator serves one survey (keyed by the
+ * sizes, kernel radii and LSF modes of its geometry list).  persistent = 1:
+ * one persistent launch of cluster_ctas-CTA clusters of `threads` threads
+ * over every galaxy; persistent = 0: one launch per cluster-size group
+ * (cluster_ctas and threads 0).  gbk_survey_autotune times the per-group
+ * launches and one launch with 512 and 256 threads at the four smallest
+ * cluster sizes that fit every galaxy, on gbk_survey_eval of `params`
+ * against `obs` (chi2_scratch [n_gal] is overwritten; the workspace is that
+ * of gbk_survey_workspace_bytes(geoms, n_gal, NULL)), keeps the fastest for
+ * this survey and returns it in best (host).  Synchronises `stream`; call
+ * it outside any stream capture.  gbk_survey_get_tuning reports the shape
+ * the next survey call will use; gbk_survey_set_tuning sets one (EINVAL if
+ * it does not fit every galaxy) or, with t == NULL, forgets it. */
+GBK_API gbk_status gbk_survey_autotune(const gbk_geom *geoms, int32_t n_gal, const double *params,
+                                       const gbk_obs *obs, double *chi2_scratch, void *workspace, size_t ws_bytes,
+                                       gbk_tuning *best, void *stream);
+GBK_API gbk_status gbk_survey_get_tuning(const gbk_geom *geoms, int32_t n_gal, gbk_tuning *out);
+GBK_API gbk_status gbk_survey_set_tuning(const gbk_geom *geoms, int32_t n_gal, const gbk_tuning *t);
 
 /* Diagnostics (no counterpart in the paper): measured lane-operation rates
  * of the ALU pipes the fused evaluator is bound by -- FP32 FMA issued as

@@ -250,8 +250,53 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         __syncthreads();
     }
 
-    // The clusters of the grid take the models in turn.
-    for (int w = cid; w < a.n_models; w += ncl) {
+    // The clusters of the grid take the models in turn: statically (w = cid,
+    // cid + ncl, ...) or, with a work counter, in the order they become free.
+    // Rank 0 takes the next item and the cluster reads it from rank 0's
+    // shared memory after one cluster barrier.  Fetch k uses slot k & 1:
+    // rank 0 rewrites a slot only at fetch k + 2, after the barrier of fetch
+    // k + 1, which no CTA passes before it has read fetch k.
+    // The last a.n_solo models (ragged persistent launches only) are served
+    // solo: once the cluster's share is exhausted, every CTA takes those
+    // models one at a time from the second counter and evaluates each alone
+    // (the whole extended grid in its band, block barriers instead of
+    // cluster barriers, no distributed shared memory).
+    __shared__ int s_work[2], s_solo[2];
+    int fetch = 0, fetch_solo = 0;
+    bool solo = false;
+    const int n_cl = a.n_models - a.n_solo;  // models served by whole clusters
+    // next model from counter ctr over [base, base + lim), passing over the
+    // models of galaxies the caller skips (one atomic each, no barrier)
+    auto take = [&](int *ctr, int base, int lim) -> int {
+        int v = atomicAdd(ctr, 1);
+        while (a.skip && v < lim) {
+            const int gi = mpg > 0 ? (base + v) / mpg : 0;
+            if (a.skip[RAGGED && a.order ? a.order[gi] : gi] == 0) break;
+            v = atomicAdd(ctr, 1);
+        }
+        return v < lim ? base + v : a.n_models;
+    };
+    auto next_item = [&](int prev) -> int {
+        if (!a.work) return prev + ncl;
+        if (!solo) {
+            const int slot = fetch++ & 1;
+            if (rank == 0 && tid == 0) s_work[slot] = take(a.work, 0, n_cl);
+            cluster.sync();
+            const int v = *cluster.map_shared_rank(&s_work[slot], 0);
+            if (v < n_cl || a.n_solo == 0) return v;
+            solo = true;  // the same decision in every CTA of the cluster
+        }
+        const int slot = fetch_solo++ & 1;
+        if (tid == 0) s_solo[slot] = take(a.work + 1, n_cl, a.n_solo);
+        __syncthreads();
+        return s_solo[slot];
+    };
+    // barrier over the CTAs that share the current model
+    auto model_sync = [&]() {
+        if (solo) __syncthreads();
+        else cluster.sync();
+    };
+    for (int w = a.work ? next_item(0) : cid; w < a.n_models; w = next_item(w)) {
     int gal, model;
     if (RAGGED) {
         const int gi = w / mpg;
@@ -262,14 +307,16 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         gal = mpg > 0 ? model / mpg : 0;
     }
     if (a.skip && a.skip[gal] != 0) continue;  // same decision in every CTA of the cluster
+    // CTAs sharing this model and this CTA's rank among them
+    const int mcs = solo ? 1 : cs, mrank = solo ? 0 : rank;
     if (RAGGED) {
-        // The previous model ended with a cluster barrier, so nobody still
-        // reads s_g or the tables.
+        // The previous model ended with a cluster (or block) barrier, so
+        // nobody still reads s_g or the tables.
         if (tid == 0) s_g = a.geoms[gal];
         __syncthreads();
-        band = (s_g.ey + cs - 1) / cs;
-        row0 = band_begin(rank, s_g.ey, cs);
-        row1 = band_begin(rank + 1, s_g.ey, cs);
+        band = (s_g.ey + mcs - 1) / mcs;
+        row0 = band_begin(mrank, s_g.ey, mcs);
+        row1 = band_begin(mrank + 1, s_g.ey, mcs);
         L = fused_layout(smem, s_g, band);
         fused_setup(s_g, L, row0, row1, &s_var_z);
     }
@@ -434,7 +481,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         if (x >= g.nx) { x -= g.nx; ++r; }
     }
 
-    cluster.sync();  // every CTA's P is complete and visible cluster-wide; Q is free
+    model_sync();  // every CTA's P is complete and visible cluster-wide; Q is free
 
     // ---- phase 3a: copy the halo rows of the y pass from the neighbours ----
     // All of a thread's remote loads are issued before its shared stores so
@@ -453,9 +500,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
                     int k = i / g.nx, xx = i - k * g.nx;
                     int er = (k < R) ? row0 - R + k : row1 + (k - R);
                     if (er >= 0 && er < g.ey) {
-                        int owner = band_owner(er, g.ey, cs);
+                        // (never reached solo: the CTA owns every row)
+                        int owner = band_owner(er, g.ey, mcs);
                         const float4 *src = cluster.map_shared_rank(P, owner);
-                        v[u] = src[(size_t)(er - band_begin(owner, g.ey, cs)) * g.nx + xx];
+                        v[u] = src[(size_t)(er - band_begin(owner, g.ey, mcs)) * g.nx + xx];
                         dst[u] = i;
                     }
                 }
@@ -549,10 +597,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     // visible.  No second barrier is needed before the next model: P and
     // red are next written after that model's first cluster barrier, which
     // rank 0 reaches only once it has read the parts below.
-    cluster.sync();
-    if (want_chi2 && rank == 0 && tid == 0) {
+    model_sync();
+    if (want_chi2 && mrank == 0 && tid == 0) {
         double s = 0.0;
-        for (int rr = 0; rr < cs; ++rr) {
+        for (int rr = 0; rr < mcs; ++rr) {
             const double *p = (rr == 0) ? red : cluster.map_shared_rank(red, rr);
             s += p[32];
         }

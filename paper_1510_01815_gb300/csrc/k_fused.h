@@ -36,6 +36,14 @@ struct FusedArgs {
     const int64_t *pix_off; // device [n_gal]
     const int32_t *order;   // device list of the galaxies this launch serves (null: 0, 1, ...)
     size_t smem;            // dynamic shared memory (ragged: the largest geometry's need)
+    // Persistent launches: optional device counters, zero at launch, that
+    // hand the models to the clusters in the order they become free
+    // (null: cluster c takes models c, c + clusters, ...).  work[0] serves
+    // the first n_models - n_solo models to whole clusters; work[1] then
+    // serves the last n_solo models (ragged launches; their galaxies must
+    // fit one CTA) to single CTAs.
+    int *work;
+    int n_solo;
 };
 
 // Launch configuration of the fused kernel (see tune.cu).

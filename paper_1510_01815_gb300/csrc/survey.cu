@@ -2,15 +2,22 @@
 // channel width and LSF in one batch), the setting of the survey-scale
 // fitting Bekiaris et al. 2015 motivate in Sec. 1 and Sec. 5.
 //
-// The plan groups the galaxies by the smallest thread-block cluster whose
-// per-CTA shared memory still lets two CTAs share an SM (small cubes need one
-// CTA, the largest several), orders each group costliest first so that the
-// hardware block scheduler, which hands out one cluster per model, ends with
-// the cheap models, and issues one ragged fused launch per group.  The
-// geometry table, the packed pixel offsets and the order live at the start of
-// the caller's workspace.
+// Two ways to serve a survey with the fused evaluator:
+//  * one persistent launch: a resident wave of thread-block clusters of one
+//    size (the smallest that fits every galaxy two CTAs to an SM) takes the
+//    models, costliest galaxy first, from a work counter as each cluster
+//    becomes free;
+//  * one launch per class: the galaxies grouped by the smallest cluster that
+//    fits each of them, one cluster per model, each group costliest first.
+// A per-survey autotuner (gbk_survey_autotune) times both shapes and caches
+// the winner for the survey's geometry list.  The geometry table, the packed
+// pixel offsets, the orders and the work counter live at the start of the
+// caller's workspace.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 
 #include "gbk_api_internal.h"
@@ -25,7 +32,65 @@ static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Shared memory per CTA that lets two CTAs of 512 threads share an SM.
 constexpr size_t kSurveySmemCap = 228 * 1024 / 2 - 3 * 1024;
 
-gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
+// One persistent launch unless a survey tuning says otherwise.
+constexpr int kSurveyDefaultOne = 1;
+
+static std::mutex g_stune_mu;
+static std::map<uint64_t, SurveyTuning> g_stune;
+
+// Key of a survey's launch shapes: FNV-1a over the sizes that set them.
+static uint64_t survey_key(const std::vector<Geom> &geo)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](int v) {
+        for (int k = 0; k < 4; ++k) {
+            h ^= (uint64_t)((v >> (8 * k)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    };
+    mix((int)geo.size());
+    for (const Geom &g : geo) {
+        mix(g.nx);
+        mix(g.ny);
+        mix(g.nz);
+        mix(g.R);
+        mix(g.Rz);
+        mix(g.lsf_mode);
+    }
+    return h;
+}
+
+// Galaxies a single CTA serves with two CTAs per SM (the solo share of a
+// persistent launch).
+static bool solo_fits(const Geom &g, int threads)
+{
+    size_t need;
+    return fused_config_ragged(&g, 1, 1, threads, &need) && need <= kSurveySmemCap;
+}
+
+// Smallest cluster size for the cluster share of one launch (the galaxies
+// that are not solo): two CTAs per SM if possible, else one; 1 when every
+// galaxy is solo.  0 if none fits.
+static int one_launch_cs(const std::vector<Geom> &geo, int threads, size_t *smem)
+{
+    std::vector<Geom> big;
+    for (const Geom &g : geo)
+        if (!solo_fits(g, threads)) big.push_back(g);
+    if (big.empty()) return fused_config_ragged(geo.data(), (int)geo.size(), 1, threads, smem) ? 1 : 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const size_t cap = pass == 0 ? kSurveySmemCap : (size_t)kFusedMaxSmem;
+        for (int cs = 1; cs <= kFusedMaxCluster; ++cs) {
+            size_t need;
+            if (fused_config_ragged(big.data(), (int)big.size(), cs, threads, &need) && need <= cap) {
+                *smem = need;
+                return cs;
+            }
+        }
+    }
+    return 0;
+}
+
+gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp, const SurveyTuning *force)
 {
     if (!geoms) return fail(GBK_EINVAL, "geoms is NULL");
     if (n_gal < 0) return fail(GBK_EINVAL, "n_gal must be >= 0");
@@ -58,17 +123,75 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
         int band = (g.ey + pick - 1) / pick;
         thr_of[i] = (long)band * g.ex >= 1536 ? 512 : 256;
     }
-    // groups: larger clusters first, then costliest first; ties by index
+    auto cost = [&](int i) { const Geom &g = sp->geo[i]; return (long long)g.ex * g.ey * g.ez; };
+    SurveyTuning tu = {kSurveyDefaultOne, 0, 512};
+    if (force) {
+        tu = *force;
+    } else if (n_gal > 0) {
+        std::lock_guard<std::mutex> lk(g_stune_mu);
+        auto it = g_stune.find(survey_key(sp->geo));
+        if (it != g_stune.end()) tu = it->second;
+    }
     sp->order.resize(n_gal);
     std::iota(sp->order.begin(), sp->order.end(), 0);
-    auto cost = [&](int i) { const Geom &g = sp->geo[i]; return (long long)g.ex * g.ey * g.ez; };
-    std::stable_sort(sp->order.begin(), sp->order.end(), [&](int a, int b) {
-        if (cs_of[a] != cs_of[b]) return cs_of[a] > cs_of[b];
-        if (thr_of[a] != thr_of[b]) return thr_of[a] > thr_of[b];
-        return cost(a) > cost(b);
-    });
     sp->classes.clear();
-    for (int k = 0; k < n_gal;) {
+    if (tu.one && n_gal > 0) {
+        // one persistent launch: the galaxies that need a cluster first, then
+        // the ones a single CTA serves; each share costliest first
+        SurveyClass c;
+        c.threads = tu.threads;
+        std::vector<char> solo(n_gal);
+        std::vector<Geom> big;
+        for (int i = 0; i < n_gal; ++i) {
+            solo[i] = solo_fits(sp->geo[i], c.threads);
+            if (!solo[i]) big.push_back(sp->geo[i]);
+        }
+        if (tu.cs > 0) {
+            c.cs = tu.cs;
+            if (big.empty()) big = sp->geo;  // every galaxy is served by the clusters
+            if (!fused_config_ragged(big.data(), (int)big.size(), c.cs, c.threads, &c.smem))
+                return fail(GBK_EINVAL, "survey tuning: %d-CTA clusters of %d threads do not fit every galaxy", c.cs,
+                            c.threads);
+        } else if (!(c.cs = one_launch_cs(sp->geo, c.threads, &c.smem))) {
+            return fail(GBK_EUNSUPPORTED, "no cluster size fits every galaxy of the survey");
+        }
+        // solo galaxies only where a cluster share exists (with none, the
+        // clusters serve everything)
+        const bool split = (int)big.size() < n_gal && !big.empty() && c.cs > 1;
+        c.n_solo = 0;
+        if (split) {
+            for (int i = 0; i < n_gal; ++i) {
+                if (!solo[i]) continue;
+                size_t need;
+                fused_config_ragged(&sp->geo[i], 1, 1, c.threads, &need);
+                c.smem = std::max(c.smem, need);
+                ++c.n_solo;
+            }
+        } else {
+            std::fill(solo.begin(), solo.end(), 0);
+            if (!fused_config_ragged(sp->geo.data(), n_gal, c.cs, c.threads, &c.smem))
+                return fail(GBK_EINVAL, "survey tuning: %d-CTA clusters of %d threads do not fit every galaxy", c.cs,
+                            c.threads);
+        }
+        c.beg = 0;
+        c.end = n_gal;
+        c.persistent = 1;
+        std::stable_sort(sp->order.begin(), sp->order.end(), [&](int a, int b) {
+            if (solo[a] != solo[b]) return solo[a] < solo[b];
+            return cost(a) > cost(b);
+        });
+        sp->classes.push_back(c);
+        tu.cs = c.cs;
+    }
+    // groups: larger clusters first, then costliest first; ties by index
+    if (!tu.one)
+        std::stable_sort(sp->order.begin(), sp->order.end(), [&](int a, int b) {
+            if (cs_of[a] != cs_of[b]) return cs_of[a] > cs_of[b];
+            if (thr_of[a] != thr_of[b]) return thr_of[a] > thr_of[b];
+            return cost(a) > cost(b);
+        });
+    sp->tuning = tu;
+    for (int k = 0; k < n_gal && !tu.one;) {
         int i0 = sp->order[k], e = k;
         while (e < n_gal && cs_of[sp->order[e]] == cs_of[i0] && thr_of[sp->order[e]] == thr_of[i0]) ++e;
         SurveyClass c;
@@ -76,6 +199,8 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
         c.threads = thr_of[i0];
         c.beg = k;
         c.end = e;
+        c.persistent = 0;
+        c.n_solo = 0;
         std::vector<Geom> members;
         for (int j = k; j < e; ++j) members.push_back(sp->geo[sp->order[j]]);
         if (!fused_config_ragged(members.data(), (int)members.size(), c.cs, c.threads, &c.smem))
@@ -106,6 +231,8 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
         c.beg = k;
         c.end = e;
         c.smem = 0;
+        c.persistent = 0;
+        c.n_solo = 0;
         for (int j = k; j < e; ++j) {
             const Geom &g = sp->geo[sp->torder[j]];
             c.smem = std::max(c.smem, tangent_smem_bytes_host(g, (g.ey + c.cs - 1) / c.cs, kTangentThreads));
@@ -115,7 +242,67 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
     }
     sp->table_bytes = n_gal == 0 ? 0
                                  : al256(sizeof(Geom) * n_gal) + al256(sizeof(int64_t) * (n_gal + 1)) +
-                                       2 * al256(sizeof(int32_t) * n_gal);
+                                       2 * al256(sizeof(int32_t) * n_gal) + al256(2 * sizeof(int));
+    return GBK_OK;
+}
+
+// Host image of the device tables: geometry, pixel offsets, the two
+// orders; the work counters that follow are reset on the device.
+static void build_host_tables(SurveyPlan *sp)
+{
+    const int n = sp->n_gal;
+    size_t o_geo = 0, o_pix = al256(sizeof(Geom) * n), o_ord = o_pix + al256(sizeof(int64_t) * (n + 1));
+    size_t o_tord = o_ord + al256(sizeof(int32_t) * n);
+    std::vector<char> &h = sp->h_tables;
+    h.assign(sp->table_bytes, 0);
+    if (n == 0) return;
+    std::memcpy(h.data() + o_geo, sp->geo.data(), sizeof(Geom) * n);
+    std::memcpy(h.data() + o_pix, sp->pix_off.data(), sizeof(int64_t) * (n + 1));
+    std::memcpy(h.data() + o_ord, sp->order.data(), sizeof(int32_t) * n);
+    std::memcpy(h.data() + o_tord, sp->torder.data(), sizeof(int32_t) * n);
+}
+
+// Recent plans, newest first, with the generation of the survey tunings
+// they were made under.
+struct CachedPlan {
+    std::vector<unsigned char> key;  // the caller's gbk_geom array, byte for byte
+    uint64_t gen;
+    SurveyPlan plan;
+};
+static std::mutex g_plan_mu;
+static std::vector<CachedPlan> g_plans;
+static uint64_t g_tune_gen = 0;  // bumped whenever a survey tuning changes (under g_stune_mu)
+constexpr size_t kPlanCache = 4;
+
+gbk_status survey_plan_cached(const gbk_geom *geoms, int n_gal, SurveyPlan *sp)
+{
+    if (!geoms || n_gal <= 0) return survey_plan(geoms, n_gal, sp);
+    const size_t nb = sizeof(gbk_geom) * (size_t)n_gal;
+    uint64_t gen;
+    {
+        std::lock_guard<std::mutex> lk(g_stune_mu);
+        gen = g_tune_gen;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (size_t i = 0; i < g_plans.size(); ++i) {
+            const CachedPlan &c = g_plans[i];
+            if (c.gen == gen && c.key.size() == nb && std::memcmp(c.key.data(), geoms, nb) == 0) {
+                *sp = c.plan;
+                return GBK_OK;
+            }
+        }
+    }
+    gbk_status s = survey_plan(geoms, n_gal, sp);
+    if (s) return s;
+    build_host_tables(sp);
+    CachedPlan c;
+    c.key.assign((const unsigned char *)geoms, (const unsigned char *)geoms + nb);
+    c.gen = gen;
+    c.plan = *sp;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.insert(g_plans.begin(), std::move(c));
+    if (g_plans.size() > kPlanCache) g_plans.pop_back();
     return GBK_OK;
 }
 
@@ -123,20 +310,17 @@ gbk_status survey_upload(SurveyPlan *sp, char *ws, cudaStream_t st)
 {
     const int n = sp->n_gal;
     size_t o_geo = 0, o_pix = al256(sizeof(Geom) * n), o_ord = o_pix + al256(sizeof(int64_t) * (n + 1));
-    size_t o_tord = o_ord + al256(sizeof(int32_t) * n);
-    std::vector<char> h(sp->table_bytes, 0);
-    std::memcpy(h.data() + o_geo, sp->geo.data(), sizeof(Geom) * n);
-    std::memcpy(h.data() + o_pix, sp->pix_off.data(), sizeof(int64_t) * (n + 1));
-    std::memcpy(h.data() + o_ord, sp->order.data(), sizeof(int32_t) * n);
-    std::memcpy(h.data() + o_tord, sp->torder.data(), sizeof(int32_t) * n);
+    size_t o_tord = o_ord + al256(sizeof(int32_t) * n), o_work = o_tord + al256(sizeof(int32_t) * n);
+    if (sp->h_tables.size() != sp->table_bytes) build_host_tables(sp);
     // From pageable memory the copy returns once the source has been staged,
-    // so h may be released afterwards.
-    cudaError_t e = cudaMemcpyAsync(ws, h.data(), h.size(), cudaMemcpyHostToDevice, st);
+    // so the host image may be released afterwards.
+    cudaError_t e = cudaMemcpyAsync(ws, sp->h_tables.data(), sp->h_tables.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "survey: uploading the geometry tables");
     sp->d_geo = (Geom *)(ws + o_geo);
     sp->d_pix_off = (int64_t *)(ws + o_pix);
     sp->d_order = (int32_t *)(ws + o_ord);
     sp->d_torder = (int32_t *)(ws + o_tord);
+    sp->d_work = (int *)(ws + o_work);
     return GBK_OK;
 }
 
@@ -178,11 +362,17 @@ gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, cons
         a.cs = c.cs;
         a.band = 0;
         a.threads = c.threads;
-        a.persistent = 0;
+        a.persistent = c.persistent;
         a.geoms = sp.d_geo;
         a.pix_off = sp.d_pix_off;
         a.order = sp.d_order + c.beg;
         a.smem = c.smem;
+        if (c.persistent) {
+            cudaError_t e = cudaMemsetAsync(sp.d_work, 0, 2 * sizeof(int), st);
+            if (e != cudaSuccess) return cuda_fail(e, "survey: resetting the work counters");
+            a.work = sp.d_work;
+            a.n_solo = c.n_solo * mpg;
+        }
         gbk_status s = launch_fused(a, st);
         if (s) return s;
     }
@@ -216,7 +406,7 @@ gbk_status gbk_survey_eval(const gbk_geom *geoms, int32_t n_gal, const double *p
                            float *maps, double *chi2, float *resid, void *workspace, size_t ws_bytes, void *stream)
 {
     SurveyPlan sp;
-    gbk_status s = survey_plan(geoms, n_gal, &sp);
+    gbk_status s = survey_plan_cached(geoms, n_gal, &sp);
     if (s) return s;
     if (n_gal == 0) return ok();
     if ((s = check_device_ptr(params, "params", 8))) return s;
@@ -258,6 +448,122 @@ gbk_status gbk_survey_fit_lm(const gbk_geom *geoms, int32_t n_gal, const gbk_obs
     if ((s = survey_upload(&sp, (char *)workspace, st))) return s;
     return lm_survey(sp, geoms, obs, lo, hi, params, opts, chi2_out, iters_out, status_out,
                      (char *)workspace + sp.table_bytes, ws_bytes - sp.table_bytes, st);
+}
+
+gbk_status gbk_survey_autotune(const gbk_geom *geoms, int32_t n_gal, const double *params, const gbk_obs *obs,
+                               double *chi2_scratch, void *workspace, size_t ws_bytes, gbk_tuning *best, void *stream)
+{
+    SurveyPlan base;
+    gbk_status s = survey_plan(geoms, n_gal, &base);
+    if (s) return s;
+    if (n_gal < 1) return fail(GBK_EINVAL, "n_gal must be >= 1");
+    if (!best) return fail(GBK_EINVAL, "best is NULL");
+    if ((s = check_device_ptr(params, "params", 8)) || (s = check_device_ptr(chi2_scratch, "chi2_scratch", 8)) ||
+        (s = check_device_ptr(obs, "obs", 8)))
+        return s;
+    if (!workspace || ws_bytes < base.table_bytes)
+        return fail(GBK_EWORKSPACE, "gbk_survey_autotune needs %zu bytes of workspace (got %zu)", base.table_bytes,
+                    ws_bytes);
+    if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
+    // candidates: the per-class launches, and one launch with 256 or 512
+    // threads and the four smallest cluster sizes that fit every galaxy
+    std::vector<SurveyTuning> cand = {{0, 0, 0}};
+    for (int threads : {512, 256}) {
+        size_t smem;
+        const int cs0 = one_launch_cs(base.geo, threads, &smem);
+        for (int cs = cs0; cs0 > 0 && cs < cs0 + 4 && cs <= kFusedMaxCluster; ++cs)
+            if (fused_config_ragged(base.geo.data(), n_gal, cs, threads, &smem)) cand.push_back({1, cs, threads});
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    SurveyTuning bt = {0, 0, 0};
+    float best_ms = 0.f;
+    int tried = 0;
+    for (const SurveyTuning &c : cand) {
+        SurveyPlan p;
+        if (survey_plan(geoms, n_gal, &p, &c) || survey_upload(&p, (char *)workspace, st)) continue;
+        if (survey_eval(p, 1, params, obs, nullptr, nullptr, chi2_scratch, nullptr, st)) {  // warm-up
+            cudaGetLastError();
+            continue;
+        }
+        float times[3];
+        bool ok_run = true;
+        for (int rep = 0; rep < 3 && ok_run; ++rep) {
+            cudaEventRecord(t0, st);
+            ok_run = survey_eval(p, 1, params, obs, nullptr, nullptr, chi2_scratch, nullptr, st) == GBK_OK;
+            cudaEventRecord(t1, st);
+            cudaEventSynchronize(t1);
+            cudaEventElapsedTime(&times[rep], t0, t1);
+        }
+        if (!ok_run) {
+            cudaGetLastError();
+            continue;
+        }
+        const float med =
+            std::fmax(std::fmin(times[0], times[1]), std::fmin(std::fmax(times[0], times[1]), times[2]));
+        if (tried++ == 0 || med < best_ms) {
+            best_ms = med;
+            bt = p.tuning;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "survey autotune");
+    if (tried == 0) return fail(GBK_EUNSUPPORTED, "no survey launch shape could run");
+    {
+        std::lock_guard<std::mutex> lk(g_stune_mu);
+        g_stune[survey_key(base.geo)] = bt;
+        ++g_tune_gen;
+    }
+    best->cluster_ctas = bt.one ? bt.cs : 0;
+    best->threads = bt.one ? bt.threads : 0;
+    best->persistent = bt.one;
+    best->ms = best_ms;
+    best->candidates = tried;
+    return ok();
+}
+
+gbk_status gbk_survey_get_tuning(const gbk_geom *geoms, int32_t n_gal, gbk_tuning *out)
+{
+    if (!out) return fail(GBK_EINVAL, "out is NULL");
+    if (n_gal < 1) return fail(GBK_EINVAL, "n_gal must be >= 1");
+    SurveyPlan sp;
+    gbk_status s = survey_plan(geoms, n_gal, &sp);
+    if (s) return s;
+    out->cluster_ctas = sp.tuning.one ? sp.tuning.cs : 0;
+    out->threads = sp.tuning.one ? sp.tuning.threads : 0;
+    out->persistent = sp.tuning.one;
+    out->ms = 0.f;
+    out->candidates = 0;
+    return ok();
+}
+
+gbk_status gbk_survey_set_tuning(const gbk_geom *geoms, int32_t n_gal, const gbk_tuning *t)
+{
+    if (n_gal < 1) return fail(GBK_EINVAL, "n_gal must be >= 1");
+    SurveyPlan sp;
+    gbk_status s = survey_plan(geoms, n_gal, &sp);
+    if (s) return s;
+    const uint64_t key = survey_key(sp.geo);
+    if (!t) {
+        std::lock_guard<std::mutex> lk(g_stune_mu);
+        g_stune.erase(key);
+        ++g_tune_gen;
+        return ok();
+    }
+    if (t->persistent != 0 && t->persistent != 1) return fail(GBK_EINVAL, "persistent must be 0 or 1");
+    SurveyTuning tu = {t->persistent, t->persistent ? t->cluster_ctas : 0, t->persistent ? t->threads : 0};
+    if (tu.one && (tu.cs < 1 || (tu.threads != 512 && tu.threads != 384 && tu.threads != 256)))
+        return fail(GBK_EINVAL, "one launch needs cluster_ctas >= 1 and 256, 384 or 512 threads");
+    SurveyPlan check;
+    if ((s = survey_plan(geoms, n_gal, &check, &tu))) return s;
+    std::lock_guard<std::mutex> lk(g_stune_mu);
+    g_stune[key] = tu;
+    ++g_tune_gen;
+    return ok();
 }
 
 }  // extern "C"

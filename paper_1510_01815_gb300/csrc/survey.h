@@ -11,8 +11,17 @@ namespace gbk {
 // Galaxies served by one launch: the same cluster size and block size.
 struct SurveyClass {
     int cs, threads;
-    int beg, end;  // range of SurveyPlan::order
-    size_t smem;   // dynamic shared memory of the launch
+    int beg, end;    // range of SurveyPlan::order
+    size_t smem;     // dynamic shared memory of the launch
+    int persistent;  // 1: one resident wave of clusters fed by the work counters
+    int n_solo;      // persistent: the last n_solo galaxies of the range go to single CTAs
+};
+
+// How the fused evaluator serves a survey: one launch per class (one = 0),
+// or one persistent launch of cs-CTA clusters of `threads` threads over
+// every galaxy (one = 1).
+struct SurveyTuning {
+    int one, cs, threads;
 };
 
 struct SurveyPlan {
@@ -31,10 +40,17 @@ struct SurveyPlan {
     int64_t *d_pix_off = nullptr;
     int32_t *d_order = nullptr;
     int32_t *d_torder = nullptr;
+    int *d_work = nullptr;          // work counters of persistent launches
+    std::vector<char> h_tables;     // host image of the device tables (built once)
+    SurveyTuning tuning = {0, 0, 0};
     int64_t total_pix() const { return pix_off.empty() ? 0 : pix_off.back(); }
 };
 
-gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp);
+// `force` (optional) overrides the cached or default survey tuning.
+gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp, const SurveyTuning *force = nullptr);
+// survey_plan through a small cache of recent plans (same geometry bytes,
+// same survey tunings): repeated calls over one survey skip the planning.
+gbk_status survey_plan_cached(const gbk_geom *geoms, int n_gal, SurveyPlan *sp);
 gbk_status survey_upload(SurveyPlan *sp, char *ws, cudaStream_t st);
 // Models gal * mpg + s (s < mpg) of every galaxy: chi2 [n_gal * mpg] and the
 // packed maps / residuals (galaxy gal at pixel offset pix_off[gal] * mpg).

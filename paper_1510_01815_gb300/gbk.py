@@ -98,6 +98,9 @@ def lib():
             "gbk_survey_eval": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "gbk_survey_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz,
                                         vp]),
+            "gbk_survey_autotune": (i32, [gp, i32, vp, vp, vp, vp, sz, ctypes.POINTER(CTuning), vp]),
+            "gbk_survey_get_tuning": (i32, [gp, i32, ctypes.POINTER(CTuning)]),
+            "gbk_survey_set_tuning": (i32, [gp, i32, ctypes.POINTER(CTuning)]),
             "gbk_device_status": (i32, [ctypes.POINTER(ctypes.c_int32)]),
             "gbk_cnn_param_count": (sz, []),
             "gbk_cnn_workspace_bytes": (sz, [i32]),
@@ -126,7 +129,8 @@ def exported_symbols():
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
-            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_device_status", "gbk_gemm_bf16", "gbk_cnn_param_count",
+            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_survey_autotune", "gbk_survey_get_tuning",
+            "gbk_survey_set_tuning", "gbk_device_status", "gbk_gemm_bf16", "gbk_cnn_param_count",
             "gbk_cnn_workspace_bytes", "gbk_cnn_init", "gbk_cnn_targets", "gbk_cnn_decode", "gbk_cnn_synth_obs",
             "gbk_cnn_forward", "gbk_cnn_grad", "gbk_cnn_train_step",
             "gbk_last_error", "gbk_version"]
@@ -329,7 +333,10 @@ def fit_lm(geom, obs_list, p0, lo, hi, opts, device="cuda", stream=None):
 
 
 def cgeoms(geoms):
-    """A host array of gbk_geom structs, one per galaxy."""
+    """A host array of gbk_geom structs, one per galaxy (an array built
+    earlier is passed through, so that repeated calls skip the marshalling)."""
+    if isinstance(geoms, ctypes.Array):
+        return geoms
     return (CGeom * len(geoms))(*[cgeom(g) for g in geoms])
 
 
@@ -371,6 +378,41 @@ def gbk_survey_fit_lm(geoms, obs_dev, lo, hi, params, opts, chi2_out, iters_out,
                                    _ptr(iters_out, torch.int32, "iters_out"),
                                    _ptr(status_out, torch.int32, "status_out"), _ptr(workspace, None, "workspace"),
                                    ws_bytes, _stream(stream)))
+
+
+def _tuning_dict(t, timed=False):
+    d = {"cluster_ctas": t.cluster_ctas, "threads": t.threads, "persistent": t.persistent}
+    if timed:
+        d.update(ms=t.ms, candidates=t.candidates)
+    return d
+
+
+def gbk_survey_autotune(geoms, params, obs_dev, chi2_scratch, workspace, stream=None):
+    """Times the survey launch shapes on gbk_survey_eval of this batch and
+    keeps the fastest for the survey; returns a dict of the choice."""
+    arr = cgeoms(geoms)
+    ws_bytes = workspace.numel() * workspace.element_size()
+    t = CTuning()
+    _check(lib().gbk_survey_autotune(arr, len(geoms), _ptr(params, torch.float64, "params"),
+                                     _ptr(obs_dev, torch.uint8, "obs"), _ptr(chi2_scratch, torch.float64, "chi2"),
+                                     _ptr(workspace, None, "workspace"), ws_bytes, ctypes.byref(t), _stream(stream)))
+    return _tuning_dict(t, True)
+
+
+def gbk_survey_get_tuning(geoms):
+    t = CTuning()
+    _check(lib().gbk_survey_get_tuning(cgeoms(geoms), len(geoms), ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def gbk_survey_set_tuning(geoms, persistent=None, cluster_ctas=0, threads=0):
+    """Forces the survey's launch shape (persistent None forgets it)."""
+    arr = cgeoms(geoms)
+    if persistent is None:
+        _check(lib().gbk_survey_set_tuning(arr, len(geoms), None))
+        return
+    t = CTuning(int(cluster_ctas), int(threads), int(persistent), 0.0, 0)
+    _check(lib().gbk_survey_set_tuning(arr, len(geoms), ctypes.byref(t)))
 
 
 def survey_eval(geoms, params, obs_list=None, want_maps=True, want_resid=False, device="cuda", stream=None):

@@ -176,3 +176,42 @@ def test_survey_host_logic(gbk):
         gbk.gbk_survey_workspace_bytes([SINGLE_GEOM.with_(nx=2048, ny=2048)])
     cg = gbk.cgeoms(geoms)
     assert gbk.lib().gbk_survey_eval(cg, len(geoms), None, None, None, None, None, None, 0, None) == gbk.GBK_EINVAL
+
+
+def test_survey_tuning_host_logic(gbk):
+    """Survey launch shapes are planned on the host: one persistent launch by
+    default, at the smallest cluster size that fits every galaxy; a forced
+    shape must fit every galaxy; forgetting restores the default."""
+    from paper_1510_01815_gb300 import synth
+    import numpy as np
+    geoms = [g for g, _ in synth.draw_survey(np.random.default_rng(4), 64)]
+    t = gbk.gbk_survey_get_tuning(geoms)
+    assert t["persistent"] == 1 and t["threads"] == 512 and 1 <= t["cluster_ctas"] <= 16
+    cs = t["cluster_ctas"]
+    small = [g for g in geoms if g.nx <= 40]
+    assert gbk.gbk_survey_get_tuning(small)["cluster_ctas"] <= cs
+    # one cluster size smaller than the default does not fit the largest galaxy
+    # at two CTAs per SM, but may at one; anything at or above the default fits
+    gbk.gbk_survey_set_tuning(geoms, 1, cs + 1, 256)
+    assert gbk.gbk_survey_get_tuning(geoms) == {"cluster_ctas": cs + 1, "threads": 256, "persistent": 1}
+    gbk.gbk_survey_set_tuning(geoms, 0)
+    assert gbk.gbk_survey_get_tuning(geoms) == {"cluster_ctas": 0, "threads": 0, "persistent": 0}
+    # the tuning belongs to this survey only
+    assert gbk.gbk_survey_get_tuning(geoms[:-1])["persistent"] == 1
+    gbk.gbk_survey_set_tuning(geoms, None)
+    assert gbk.gbk_survey_get_tuning(geoms) == t
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_set_tuning(geoms, 1, 0, 512)
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_set_tuning(geoms, 1, cs, 300)
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_set_tuning(geoms, 2, cs, 512)
+    big = SINGLE_GEOM.with_(nx=160, ny=160, nz=64)
+    assert gbk.gbk_survey_get_tuning(geoms + [big])["cluster_ctas"] > cs
+    with pytest.raises(gbk.GbkError):  # a 1-CTA cluster cannot hold a 160 x 160 galaxy's rows
+        gbk.gbk_survey_set_tuning(geoms + [big], 1, 1, 512)
+    # the table size does not depend on the launch shape
+    tables = gbk.gbk_survey_workspace_bytes(geoms)
+    gbk.gbk_survey_set_tuning(geoms, 0)
+    assert gbk.gbk_survey_workspace_bytes(geoms) == tables
+    gbk.gbk_survey_set_tuning(geoms, None)

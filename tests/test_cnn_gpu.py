@@ -157,12 +157,12 @@ def test_adam_first_step(G):
     assert np.max(np.abs(step)) <= lr * (1 + 1e-3) + 1e-7
 
 
-def test_training_learns(G):
-    """Synthetic maps of the CNN workload (64 x 64 x 64, noise 5 km/s, 2 %
-    dead fibres): the loss falls and held-out predictions improve on the
-    prior's centre."""
+@pytest.fixture(scope="module")
+def trained(G):
+    """A network trained on synthetic maps of the CNN workload (64 x 64 x 64
+    cubes, noise 5 km/s, 2 % dead fibres) and its held-out galaxies."""
     rng = np.random.default_rng(17)
-    n_train, n_test, B = 8192, 512, 256
+    n_train, n_test, B, steps = 65536, 512, 512, 1500
     p = synth.draw_cnn_params(rng, n_train + n_test)
     dp = torch.from_numpy(p).cuda()
     maps = G.eval_maps(synth.CNN_GEOM, dp)
@@ -173,16 +173,93 @@ def test_training_learns(G):
     G.gbk_cnn_targets(dp, t)
     net = G.CnnSeed(B, seed=3)
     losses = []
-    for it in range(600):
+    for it in range(steps):
         i = (it * B) % n_train
-        net.train_step(v[i:i + B], s[i:i + B], m[i:i + B], t[i:i + B], 1e-3)
-        if it % 50 == 0 or it == 599:
+        net.train_step(v[i:i + B], s[i:i + B], m[i:i + B], t[i:i + B], 1e-3 if it < 0.8 * steps else 1e-4)
+        if it % 50 == 0 or it == steps - 1:
             losses.append(float(net.loss))
-    assert losses[-1] < 0.25 * losses[0], losses
     pred = net.predict(v[n_train:], s[n_train:], m[n_train:]).cpu().numpy()
-    truth = p[n_train:]
+    return {"losses": losses, "pred": pred, "truth": p[n_train:], "v": v[n_train:], "s": s[n_train:],
+            "m": m[n_train:]}
+
+
+def test_training_learns(trained):
+    """The loss falls and held-out predictions improve on the prior's centre."""
+    losses = trained["losses"]
+    assert losses[-1] < 0.25 * losses[0], losses
+    pred, truth = trained["pred"], trained["truth"]
     dv = np.abs(pred[:, synth.VMAX] - truth[:, synth.VMAX])
     dpa = np.abs((pred[:, synth.PA] - truth[:, synth.PA] + 180.0) % 360.0 - 180.0)
     prior_dv = np.abs(175.0 - truth[:, synth.VMAX])
     assert np.median(dv) < 0.5 * np.median(prior_dv), (np.median(dv), np.median(prior_dv))
     assert np.median(dpa) < 20.0, np.median(dpa)
+
+
+FREE = (synth.X0, synth.Y0, synth.PA, synth.INCL, synth.VSYS, synth.VMAX, synth.RT, synth.SIG0)
+
+
+def _held_out(G, trained, idx):
+    """Observations, truths and prior boxes of held-out galaxies idx."""
+    wv, ws = synth.weights((64, 64), 5.0)
+    dwv, dws = torch.from_numpy(wv).cuda(), torch.from_numpy(ws).cuda()
+    obs = [G.Obs(trained["v"][i], trained["s"][i], dwv, dws, trained["m"][i]) for i in idx]
+    truth = trained["truth"][idx]
+    lo, hi = truth.copy(), truth.copy()
+    for k, (a, b) in synth.CNN_RANGES.items():
+        if k != synth.H:
+            lo[:, k], hi[:, k] = a, b
+    return obs, truth, lo, hi
+
+
+def test_seed_gain_lm(G, trained):
+    """Gain test of the seed for the optimiser of Sec. 2.3.1: batched LM
+    started from the network's predictions converges in fewer iterations
+    than LM started from 20 %-perturbed truths, and recovers the truth as
+    often."""
+    idx = np.arange(256)
+    obs, truth, lo, hi = _held_out(G, trained, idx)
+    lo[:, synth.PA], hi[:, synth.PA] = -360.0, 720.0
+    seed = np.clip(trained["pred"][idx], lo, hi)
+    seed[:, synth.I0], seed[:, synth.H] = truth[:, synth.I0], truth[:, synth.H]
+    rng = np.random.default_rng(55)
+    pert = np.array([synth.perturb(rng, truth[i], FREE, 0.2, lo[i], hi[i]) for i in range(len(idx))])
+    opts = G.lm_opts(max_iter=200, free=FREE)
+    res = {}
+    for name, start in (("seed", seed), ("perturbed", pert)):
+        q, c, it, st = G.fit_lm(synth.CNN_GEOM, obs, start, lo, hi, opts)
+        dv = np.abs(q[:, synth.VMAX] - truth[:, synth.VMAX])
+        dpa = np.abs((q[:, synth.PA] - truth[:, synth.PA] + 180.0) % 360.0 - 180.0)
+        res[name] = (np.mean(it), np.mean((dv < 2.0) & (dpa < 1.0)))
+    assert res["seed"][0] < 0.9 * res["perturbed"][0], res
+    assert res["seed"][1] >= res["perturbed"][1] - 0.03, res
+
+
+def test_seed_gain_nested_sampling(G, trained):
+    """Gain test of the seed for nested sampling (Sec. 2.3.2): a prior box
+    centred on the network's prediction, with half-widths three times the
+    seed's 90th-percentile error on other held-out galaxies, holds the truth
+    and needs fewer likelihood evaluations than the full prior box, with
+    posterior means that recover the truth as well."""
+    pred, truth_all = trained["pred"], trained["truth"]
+    cal = np.arange(16, len(truth_all))
+    err = np.abs(pred[cal] - truth_all[cal])
+    err[:, synth.PA] = np.abs((pred[cal, synth.PA] - truth_all[cal, synth.PA] + 180.0) % 360.0 - 180.0)
+    half = 3.0 * np.percentile(err, 90, axis=0)
+    idx = np.arange(4)
+    obs, truth, lo, hi = _held_out(G, trained, idx)
+    n_full, n_seed = [], []
+    for j, i in enumerate(idx):
+        slo, shi = lo[j].copy(), hi[j].copy()
+        for k in FREE:
+            slo[k] = max(lo[j][k], pred[i, k] - half[k]) if k != synth.PA else pred[i, k] - half[k]
+            shi[k] = min(hi[j][k], pred[i, k] + half[k]) if k != synth.PA else pred[i, k] + half[k]
+        inside = all(slo[k] <= truth[j][k] <= shi[k] for k in FREE if k != synth.PA)
+        dpa0 = abs((pred[i, synth.PA] - truth[j][synth.PA] + 180.0) % 360.0 - 180.0)
+        assert inside and dpa0 <= half[synth.PA], (j, slo, shi, truth[j])
+        for box, acc in (((lo[j], hi[j]), n_full), ((slo, shi), n_seed)):
+            r = G.gbk_nested_sample(synth.CNN_GEOM, obs[j], box[0], box[1], n_live=100, batch=25, tol=0.5, seed=7 + j)
+            dv = abs(r["mean"][synth.VMAX] - truth[j][synth.VMAX])
+            dpa = abs((r["mean"][synth.PA] - truth[j][synth.PA] + 180.0) % 360.0 - 180.0)
+            assert dv < 5.0 and dpa < 2.0, (j, box is lo, dv, dpa)
+            acc.append(r["n_eval"])
+    assert sum(n_seed) < 0.85 * sum(n_full), (n_seed, n_full)

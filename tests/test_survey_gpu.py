@@ -118,6 +118,60 @@ def test_survey_drawn_sizes(G):
         assert abs(float(c2[i]) - float(c_one[0])) <= 1e-5 * abs(float(c_one[0])), i
 
 
+def test_survey_launch_shapes_agree(G):
+    """Every launch shape of the survey evaluator -- one launch per
+    cluster-size group, or one persistent launch with a work counter at
+    several cluster and block sizes -- gives the same maps bit for bit (each
+    spaxel's arithmetic does not depend on which CTA owns it) and the same
+    chi2 up to the order of its FP64 reduction; the autotuner picks one of
+    them and the survey then uses it."""
+    rng = np.random.default_rng(4)
+    gal = synth.draw_survey(rng, 40)
+    geoms = [g for g, _ in gal]
+    ps = np.array([p for _, p in gal])
+    obs = []
+    for i, (g, p) in enumerate(gal):
+        m = oracle.evaluate(ogeom(g), p)
+        wv, ws = synth.weights((g.ny, g.nx), 5.0)
+        noise = np.random.default_rng(900 + i).normal(0.0, 5.0, size=(2, g.ny, g.nx))
+        obs.append(G.Obs.from_numpy((m[1] + noise[0]).astype(np.float32), (m[2] + noise[1]).astype(np.float32),
+                                    wv, ws, (m[0] > 0).astype(np.uint8)))
+    default = G.gbk_survey_get_tuning(geoms)
+    assert default["persistent"] == 1
+    cs0 = default["cluster_ctas"]
+    shapes = [(0, 0, 0)] + [(1, cs, t) for cs in (cs0, cs0 + 1, cs0 + 3) for t in (512, 256)]
+    ref_maps = ref_c2 = None
+    try:
+        for one, cs, t in shapes:
+            G.gbk_survey_set_tuning(geoms, one, cs, t)
+            maps, c2, _ = G.survey_eval(geoms, ps, obs)
+            maps = [m.cpu().numpy() for m in maps]
+            c2 = c2.cpu().numpy()
+            assert np.all(np.isfinite(c2)) and G.gbk_device_status() == 0
+            if ref_maps is None:
+                ref_maps, ref_c2 = maps, c2
+                continue
+            for i in range(len(geoms)):
+                np.testing.assert_array_equal(maps[i], ref_maps[i], err_msg="shape %s galaxy %d" % ((one, cs, t), i))
+            # the spaxel terms are identical; each thread sums its share in
+            # FP32 with compensation (relative error a few 2^-24 of the
+            # partial) before the FP64 tree, and the share changes with the
+            # cluster and block size
+            np.testing.assert_allclose(c2, ref_c2, rtol=1e-6)
+        # the autotuner times the shapes on this survey and keeps the fastest
+        G.gbk_survey_set_tuning(geoms, None)
+        dps = torch.as_tensor(ps).cuda()
+        dobs, _keep = G.obs_array(obs)
+        scratch = torch.empty(len(geoms), dtype=torch.float64, device="cuda")
+        ws = torch.empty(G.gbk_survey_workspace_bytes(geoms), dtype=torch.uint8, device="cuda")
+        best = G.gbk_survey_autotune(geoms, dps, dobs, scratch, ws)
+        assert best["candidates"] >= 3 and best["ms"] > 0
+        assert G.gbk_survey_get_tuning(geoms) == {k: best[k] for k in ("cluster_ctas", "threads", "persistent")}
+        np.testing.assert_allclose(scratch.cpu().numpy(), ref_c2, rtol=1e-6)
+    finally:
+        G.gbk_survey_set_tuning(geoms, None)
+
+
 def _bounds(g, p):
     lo, hi = np.array(p, dtype=np.float64), np.array(p, dtype=np.float64)
     lo[synth.X0], hi[synth.X0] = 0.0, g.nx - 1.0
