@@ -35,36 +35,49 @@ namespace cg = cooperative_groups;
 
 namespace gbk {
 
-constexpr int NPT = GBK_NPAR;        // derivatives carried for every parameter
-constexpr int kRec = 4 + 3 * NPT;    // floats per spaxel record: a, q0..q2, dq (3 per parameter)
-constexpr int kRec4 = (kRec + 3) / 4;
-constexpr int kJRow = NPT + 2;       // Jacobian row in shared memory: J[10], r, v
+// NP = derivatives carried: every parameter (GBK_NPAR), or the first eight
+// (x0 .. sigma0) when I0 and h are held fixed, as in every fit of the paper.
+template <int NP>
+struct TgDims {
+    static constexpr int kRec = 4 + 3 * NP;  // floats per spaxel record: a, q0..q2, dq (3 per parameter)
+    static constexpr int kRec4 = (kRec + 3) / 4;
+    static constexpr int RS = kRec4 * 4;     // record stride in floats
+    static constexpr int kTri = NP * (NP + 1) / 2;
+    static constexpr int kEnt = kTri + NP + 1;  // J^T J upper triangle, J^T v, sum r^2
+};
 
 __host__ __device__ inline int tg_band_begin(int rank, int ey, int cs) { return (int)(((long)rank * ey) / cs); }
 __device__ inline int tg_band_owner(int er, int ey, int cs) { return (int)((((long)er + 1) * cs - 1) / ey); }
 
-__host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads)
+__host__ __device__ inline size_t tangent_smem_bytes_np(const Geom &g, int band, int threads, int rec4)
 {
+    (void)threads;
     size_t q = (size_t)band * g.ex, h = (size_t)2 * g.R * g.nx;
-    size_t b = (q > h ? q : h) * kRec4 * 16;              // Q records / halo rows
-    b += (size_t)band * g.nx * kRec4 * 16;                // P records
+    size_t b = (q > h ? q : h) * rec4 * 16;               // Q records / halo rows
+    b += (size_t)band * g.nx * rec4 * 16;                 // P records
     b += (size_t)g.ez * 16;                               // per-channel (G0, H1, H2, -)
     b += (size_t)((2 * g.R + 1 + 3) & ~3) * 4;            // PSF taps
     b += (size_t)((band + 2 * g.R + 3) & ~3) * 4;         // row offsets
-    b += (size_t)2 * threads * kJRow * 4;                 // Jacobian rows of one chunk
-    b += 128 * 8;                                          // reductions
+    b += (size_t)TgDims<GBK_NPAR>::kEnt * 8 * 8;           // per-warp reduction slots
     return b;
+}
+
+// The size every launch is given: that of the widest records.
+__host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads)
+{
+    return tangent_smem_bytes_np(g, band, threads, TgDims<GBK_NPAR>::kRec4);
 }
 
 size_t tangent_smem_bytes_host(const Geom &g, int band, int threads) { return tangent_smem_bytes(g, band, threads); }
 
-// Re-centres the record at rec (centre rec.w... stored as r[0] = a) to centre c
+// Re-centres the record at rec (centre stored as rec[0] = a) to centre c
 // and accumulates it with weight w into acc[0..kRec).
+template <int NP>
 __device__ __forceinline__ void accum_rec(const float *rec, float c, float w, float *acc)
 {
     float D = rec[0] - c;
 #pragma unroll
-    for (int t = 0; t <= NPT; ++t) {  // triplet 0: values; 1..NPT: derivatives
+    for (int t = 0; t <= NP; ++t) {  // triplet 0: values; 1..NP: derivatives
         const float x0 = rec[1 + 3 * t], x1 = rec[2 + 3 * t], x2 = rec[3 + 3 * t];
         float t0 = w * x0, t1 = w * x1;
         acc[1 + 3 * t] += t0;
@@ -73,8 +86,11 @@ __device__ __forceinline__ void accum_rec(const float *rec, float c, float w, fl
     }
 }
 
+template <int NP>
 __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
 {
+    constexpr int NPT = NP;
+    constexpr int kRec = TgDims<NP>::kRec, kRec4 = TgDims<NP>::kRec4, kEnt = TgDims<NP>::kEnt;
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = a.cs;
     const int rank = (int)cluster.block_rank();
@@ -97,14 +113,13 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
     float4 *ztab = reinterpret_cast<float4 *>(P + (size_t)band * g.nx * kRec4 * 4);
     float *wxy = reinterpret_cast<float *>(ztab + g.ez);
     int *rowoff = reinterpret_cast<int *>(wxy + ((2 * R + 1 + 3) & ~3));
-    float *jrows = reinterpret_cast<float *>(rowoff + ((band + 2 * R + 3) & ~3));
-    double *red = reinterpret_cast<double *>(jrows + (size_t)2 * nthr * kJRow);
-    constexpr int RS = kRec4 * 4;  // record stride in floats
+    double *wred = reinterpret_cast<double *>(rowoff + ((band + 2 * R + 3) & ~3));  // [8 warps][kEnt]
+    constexpr int RS = TgDims<NP>::RS;
 
     __shared__ ModelConst mc;
     __shared__ gbk_obs s_ob;
     __shared__ float s_norm_xy, s_norm_z;
-    __shared__ double s_free_part[80];
+    __shared__ double s_part[TgDims<GBK_NPAR>::kEnt];
 
     if (tid == 0) {
         mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
@@ -193,8 +208,9 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
         dv[GBK_VMAX] = fv * w;
         dv[GBK_RT] = -0.63661977f * vmax / (rtv * rtv + r * r) * w;
         dlnA[GBK_SIG0] = -dsig_ds0 / sig;
-        dlnA[GBK_I0] = 1.f / c.i0;
-        dlnA[GBK_H] = r / (hv * hv);
+        if constexpr (NP > GBK_I0) dlnA[GBK_I0] = 1.f / c.i0;
+        if constexpr (NP > GBK_H) dlnA[GBK_H] = r / (hv * hv);
+        (void)hv;
         // channel sums: S_k^G = sum g d^k G0 (k <= 4), S_k^1 = sum g d^k H1 (k <= 3), S_k^2 = sum g d^k H2 (k <= 2)
         float a_c = fminf(fmaxf(vl, v_lo), v_hi);
         float sh = vl - a_c;
@@ -245,7 +261,7 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
         float acc[RS];
 #pragma unroll
         for (int t = 0; t < RS; ++t) acc[t] = 0.f;
-        for (int j = 0; j <= 2 * R; ++j) accum_rec(row + (size_t)j * RS, cen, wxy[j], acc);
+        for (int j = 0; j <= 2 * R; ++j) accum_rec<NP>(row + (size_t)j * RS, cen, wxy[j], acc);
         float *out = P + (size_t)idx * RS;
         out[0] = cen;
 #pragma unroll
@@ -265,113 +281,116 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
     }
     __syncthreads();
 
-    // ---- phase 3b: y pass, moments, Jacobian rows, chunked J^T J ----
+    // ---- phase 3b: y pass, moments, Jacobian rows; J^T J, J^T v and
+    // sum r^2 accumulated per thread, then reduced in a fixed order ----
     const int ylo = max(row0 - R, 0), yhi = min(row1 - R, g.ny);
     const int nout = max(0, yhi - ylo) * g.nx;
     const size_t np = (size_t)g.nx * g.ny;
     const float thr = kInvalidFraction * c.i0;
-    const int nf = a.np;
-    const int nent = nf * (nf + 1) / 2 + nf + 1;  // J^T J upper triangle, J^T v, sum r^2
-    double part = 0.0;                             // this thread's entry (tid < nent)
-    for (int base = 0; base < nout; base += nthr) {
-        int idx = base + tid;
+    float E[kEnt];
+#pragma unroll
+    for (int e = 0; e < kEnt; ++e) E[e] = 0.f;
+    for (int idx = tid; idx < nout; idx += nthr) {
         float jv[NPT], js[NPT], rv = 0.f, rs = 0.f, cv_ = 0.f, cs_ = 0.f;
 #pragma unroll
         for (int k = 0; k < NPT; ++k) { jv[k] = 0.f; js[k] = 0.f; }
-        if (idx < nout) {
-            int yy = idx / g.nx, xx = idx - yy * g.nx;
-            int y = ylo + yy;
-            size_t pix = (size_t)y * g.nx + xx;
-            int k0 = y - (row0 - R);
-            float cen = Q[((size_t)rowoff[k0 + R] + xx) * RS];
-            float acc[RS];
+        int yy = idx / g.nx, xx = idx - yy * g.nx;
+        int y = ylo + yy;
+        size_t pix = (size_t)y * g.nx + xx;
+        int k0 = y - (row0 - R);
+        float cen = Q[((size_t)rowoff[k0 + R] + xx) * RS];
+        float acc[RS];
 #pragma unroll
-            for (int t = 0; t < RS; ++t) acc[t] = 0.f;
-            for (int j = 0; j <= 2 * R; ++j) accum_rec(Q + ((size_t)rowoff[k0 + j] + xx) * RS, cen, wxy[j], acc);
-            float S0 = acc[1], S1v = acc[2], S2v = acc[3];
-            bool use = c.valid && S0 > thr && s_ob.mask[pix] != 0;
-            if (use) {
-                float inv = 1.f / S0;
-                float mu = S1v * inv;
-                float var = fmaxf(fmaf(-mu, mu, S2v * inv), 0.f);
-                float m2 = sqrtf(var);
-                float wv = s_ob.w_v[pix], ws = s_ob.w_s[pix];
-                rv = wv * (cen + mu - s_ob.v_obs[pix]);
-                rs = ws * (m2 - s_ob.s_obs[pix]);
-                float inv2m2 = m2 > 0.f ? 0.5f / m2 : 0.f;
+        for (int t = 0; t < RS; ++t) acc[t] = 0.f;
+        for (int j = 0; j <= 2 * R; ++j) accum_rec<NP>(Q + ((size_t)rowoff[k0 + j] + xx) * RS, cen, wxy[j], acc);
+        float S0 = acc[1], S1v = acc[2], S2v = acc[3];
+        bool use = c.valid && S0 > thr && s_ob.mask[pix] != 0;
+        if (use) {
+            float inv = 1.f / S0;
+            float mu = S1v * inv;
+            float var = fmaxf(fmaf(-mu, mu, S2v * inv), 0.f);
+            float m2 = sqrtf(var);
+            float wv = s_ob.w_v[pix], ws = s_ob.w_s[pix];
+            rv = wv * (cen + mu - s_ob.v_obs[pix]);
+            rs = ws * (m2 - s_ob.s_obs[pix]);
+            float inv2m2 = m2 > 0.f ? 0.5f / m2 : 0.f;
 #pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    float d0 = acc[4 + 3 * k], d1 = acc[5 + 3 * k], d2 = acc[6 + 3 * k];
-                    float dmu = (d1 - mu * d0) * inv;
-                    float dvar = (d2 - S2v * inv * d0) * inv - 2.f * mu * dmu;
-                    jv[k] = wv * dmu;
-                    js[k] = ws * dvar * inv2m2;
-                }
-                if (a.cot) {
-                    cv_ = a.cot[(size_t)model * 2 * np + pix];
-                    cs_ = a.cot[(size_t)model * 2 * np + np + pix];
-                } else {
-                    cv_ = rv;
-                    cs_ = rs;
-                }
+            for (int k = 0; k < NPT; ++k) {
+                float d0 = acc[4 + 3 * k], d1 = acc[5 + 3 * k], d2 = acc[6 + 3 * k];
+                float dmu = (d1 - mu * d0) * inv;
+                float dvar = (d2 - S2v * inv * d0) * inv - 2.f * mu * dmu;
+                jv[k] = wv * dmu;
+                js[k] = ws * dvar * inv2m2;
             }
-            if (a.jac) {
-                float *J = a.jac + (size_t)model * NPT * 2 * np;
-#pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    J[((size_t)k * 2) * np + pix] = jv[k];
-                    J[((size_t)k * 2 + 1) * np + pix] = js[k];
-                }
-            }
-        }
-        // rows of this chunk to shared memory
-        float *r0p = jrows + (size_t)(2 * tid) * kJRow, *r1p = r0p + kJRow;
-#pragma unroll
-        for (int k = 0; k < NPT; ++k) { r0p[k] = jv[k]; r1p[k] = js[k]; }
-        r0p[NPT] = rv; r0p[NPT + 1] = cv_;
-        r1p[NPT] = rs; r1p[NPT + 1] = cs_;
-        __syncthreads();
-        if (tid < nent) {
-            // entry tid: (j, k) of the upper triangle, then J^T v, then sum r^2
-            int j = -1, k = -1, t = tid, kind = 0;
-            int ntri = nf * (nf + 1) / 2;
-            if (t < ntri) {
-                j = 0;
-                while (t >= nf - j) { t -= nf - j; ++j; }
-                k = j + t;
-                j = a.free_idx[j];
-                k = a.free_idx[k];
-            } else if (t < ntri + nf) {
-                kind = 1;
-                j = a.free_idx[t - ntri];
+            if (a.cot) {
+                cv_ = a.cot[(size_t)model * 2 * np + pix];
+                cs_ = a.cot[(size_t)model * 2 * np + np + pix];
             } else {
-                kind = 2;
+                cv_ = rv;
+                cs_ = rs;
             }
-            float s = 0.f;
-            int rows = 2 * min(nthr, nout - base);
-            for (int q = 0; q < rows; ++q) {
-                const float *row = jrows + (size_t)q * kJRow;
-                s = (kind == 0) ? fmaf(row[j], row[k], s)
-                                : (kind == 1 ? fmaf(row[j], row[NPT + 1], s) : fmaf(row[NPT], row[NPT], s));
+        }
+        if (a.jac) {
+            float *J = a.jac + (size_t)model * GBK_NPAR * 2 * np;
+#pragma unroll
+            for (int k = 0; k < GBK_NPAR; ++k) {
+                J[((size_t)k * 2) * np + pix] = k < NPT ? jv[k < NPT ? k : 0] : 0.f;
+                J[((size_t)k * 2 + 1) * np + pix] = k < NPT ? js[k < NPT ? k : 0] : 0.f;
             }
-            part += (double)s;
+        }
+        // both rows (velocity and dispersion) of this spaxel
+        int e = 0;
+#pragma unroll
+        for (int j = 0; j < NPT; ++j)
+#pragma unroll
+            for (int k = j; k < NPT; ++k, ++e) E[e] = fmaf(jv[j], jv[k], fmaf(js[j], js[k], E[e]));
+#pragma unroll
+        for (int j = 0; j < NPT; ++j, ++e) E[e] = fmaf(jv[j], cv_, fmaf(js[j], cs_, E[e]));
+        E[e] = fmaf(rv, rv, fmaf(rs, rs, E[e]));
+    }
+    // CTA sum: warps in FP64 by shuffles, then the warps in order
+    {
+        const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+#pragma unroll
+        for (int e = 0; e < kEnt; ++e) {
+            double v = (double)E[e];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) wred[warp * kEnt + e] = v;
         }
         __syncthreads();
+        for (int e = tid; e < kEnt; e += nthr) {
+            double v = 0.0;
+            for (int q = 0; q < nw; ++q) v += wred[q * kEnt + e];
+            s_part[e] = v;
+        }
     }
-    if (tid < nent) s_free_part[tid] = part;
     cluster.sync();
+    // entry t of the free-parameter output: (j, k) of the upper triangle of
+    // J^T J, then J^T v, then sum r^2, gathered from the carried entries
+    const int nf = a.np;
+    const int nent = nf * (nf + 1) / 2 + nf + 1;
     if (rank == 0 && tid < nent) {
+        int ntri = nf * (nf + 1) / 2;
+        int src, j = 0, k = 0;
+        if (tid < ntri) {
+            int t = tid;
+            while (t >= nf - j) { t -= nf - j; ++j; }
+            k = j + t;
+            int p = a.free_idx[j], q = a.free_idx[k];
+            if (p > q) { int x = p; p = q; q = x; }
+            src = p * NPT - p * (p - 1) / 2 + (q - p);
+        } else if (tid < ntri + nf) {
+            src = TgDims<NP>::kTri + a.free_idx[tid - ntri];
+        } else {
+            src = kEnt - 1;
+        }
         double s = 0.0;
         for (int q = 0; q < cs; ++q) {
-            const double *p = (q == 0) ? s_free_part : cluster.map_shared_rank(s_free_part, q);
-            s += p[tid];
+            const double *p = (q == 0) ? s_part : cluster.map_shared_rank(s_part, q);
+            s += p[src];
         }
         if (!c.valid) s = (double)__int_as_float(0x7fc00000);
-        int ntri = nf * (nf + 1) / 2;
         if (tid < ntri) {
-            int j = 0, t = tid;
-            while (t >= nf - j) { t -= nf - j; ++j; }
-            int k = j + t;
             if (a.jtj) {
                 a.jtj[(size_t)model * nf * nf + j * nf + k] = s;
                 a.jtj[(size_t)model * nf * nf + k * nf + j] = s;
@@ -385,19 +404,19 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
     cluster.sync();
 }
 
-gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
+template <int NP>
+static gbk_status launch_np(const TangentArgs &args, size_t smem, cudaStream_t stream)
 {
-    if (args.geoms && args.jac) return fail(GBK_EINVAL, "ragged tangent launches do not write J");
-    size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads);
     static size_t configured = 0;
     static bool cl = false;
+    auto kern = tangent_kernel<NP>;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(tangent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "tangent kernel: setting dynamic shared memory");
         configured = smem;
     }
     if (!cl) {
-        cudaError_t e = cudaFuncSetAttribute(tangent_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return cuda_fail(e, "tangent kernel: allowing 16-CTA clusters");
         cl = true;
     }
@@ -413,9 +432,20 @@ gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, tangent_kernel, args);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
     if (e != cudaSuccess) return cuda_fail(e, "tangent kernel launch");
     return GBK_OK;
+}
+
+gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
+{
+    if (args.geoms && args.jac) return fail(GBK_EINVAL, "ragged tangent launches do not write J");
+    if (args.np < 1 || args.np > GBK_NPAR) return fail(GBK_EINVAL, "tangent launch: bad free-parameter count");
+    size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads);
+    // carry only x0 .. sigma0 when I0 and h are fixed and J is not written
+    bool narrow = !args.jac;
+    for (int k = 0; k < args.np; ++k) narrow = narrow && args.free_idx[k] < GBK_I0;
+    return narrow ? launch_np<GBK_I0>(args, smem, stream) : launch_np<GBK_NPAR>(args, smem, stream);
 }
 
 int tangent_cluster_for(const Geom &g)
