@@ -207,8 +207,12 @@ GBK_API gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, 
  *   chi2 = sum of squared residuals, device [n_models] (may be NULL).
  * Masked and invalid spaxels have zero rows.  At the disc centre (r = 0)
  * the brightness derivative with respect to the centre and the angles uses
- * the one-sided value 0.  Serves geometries whose per-CTA tables fit in
- * shared memory (EUNSUPPORTED otherwise, e.g. above about 64 x 64 spaxels). */
+ * the one-sided value 0.  A model is split over a thread-block cluster of
+ * up to 16 CTAs by rows; the y pass reads its halo rows from copies in each
+ * CTA's shared memory or, where those do not fit (wide maps, e.g. above
+ * about 64 x 64 spaxels at a 4-pixel PSF), in the neighbouring CTAs' shared
+ * memory.  EUNSUPPORTED where even that does not fit (about 100 x 100
+ * spaxels at a 4-pixel PSF). */
 GBK_API gbk_status gbk_jacobian(const gbk_geom *g, int32_t n_models, const double *params,
                                 const gbk_obs *obs, uint32_t free_mask, const float *cot, double *jtj,
                                 double *jtv, double *chi2, float *jac, void *stream);
@@ -298,8 +302,10 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
  * gbk_survey_fit_lm is gbk_fit_lm per galaxy; the batched mode advances all
  * galaxies together in one CUDA graph (finite-difference or analytic tangent
  * Jacobian; the Jacobian kernel has its own galaxy groups, since its
- * per-spaxel records are larger), the plain mode fits one galaxy after the
- * other with the host solve and finite differences.
+ * per-spaxel records are larger, and galaxies whose halo rows do not fit a
+ * CTA's shared memory are fitted in the same call with finite differences,
+ * which serve them faster), the plain mode fits one galaxy after the other
+ * with the host solve and finite differences.
  * ------------------------------------------------------------------------ */
 GBK_API size_t gbk_survey_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, const gbk_lm_opts *opts);
 GBK_API gbk_status gbk_survey_eval(const gbk_geom *geoms, int32_t n_gal, const double *params, const gbk_obs *obs,

@@ -17,7 +17,7 @@ extern "C" gbk_status gbk_jacobian(const gbk_geom *gin, int32_t n_models, const 
     if (g.model != GBK_MODEL_CUBE)
         return fail(GBK_EUNSUPPORTED, "the analytic Jacobian serves the intensity-cube model");
     TangentArgs a = {};
-    if (!tangent_config(g, &a.cs, &a.band))
+    if (!tangent_config(g, &a.cs, &a.band, &a.direct))
         return fail(GBK_EUNSUPPORTED, "geometry %d x %d too large for the Jacobian kernel", g.nx, g.ny);
     if (n_models == 0) return ok();
     if ((s = check_device_ptr(params, "params", 8))) return s;

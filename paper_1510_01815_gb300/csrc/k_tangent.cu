@@ -49,26 +49,33 @@ struct TgDims {
 __host__ __device__ inline int tg_band_begin(int rank, int ey, int cs) { return (int)(((long)rank * ey) / cs); }
 __device__ inline int tg_band_owner(int er, int ey, int cs) { return (int)((((long)er + 1) * cs - 1) / ey); }
 
-__host__ __device__ inline size_t tangent_smem_bytes_np(const Geom &g, int band, int threads, int rec4)
+// Shared memory of one CTA.  direct = 0: the y pass reads the 2R halo rows
+// from copies in Q (Q holds the larger of the band's extended records and
+// the halo rows); direct = 1: it reads them in the neighbours' P through
+// distributed shared memory and Q holds the band's extended records only.
+__host__ __device__ inline size_t tangent_smem_bytes_np(const Geom &g, int band, int threads, int rec4, int direct)
 {
     (void)threads;
-    size_t q = (size_t)band * g.ex, h = (size_t)2 * g.R * g.nx;
+    size_t q = (size_t)band * g.ex, h = direct ? 0 : (size_t)2 * g.R * g.nx;
     size_t b = (q > h ? q : h) * rec4 * 16;               // Q records / halo rows
     b += (size_t)band * g.nx * rec4 * 16;                 // P records
     b += (size_t)g.ez * 16;                               // per-channel (G0, H1, H2, -)
     b += (size_t)((2 * g.R + 1 + 3) & ~3) * 4;            // PSF taps
-    b += (size_t)((band + 2 * g.R + 3) & ~3) * 4;         // row offsets
+    b += (size_t)((band + 2 * g.R + 1) & ~1) * 8;         // y-pass row pointers
     b += (size_t)TgDims<GBK_NPAR>::kEnt * 8 * 8;           // per-warp reduction slots
     return b;
 }
 
 // The size every launch is given: that of the widest records.
-__host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads)
+__host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads, int direct)
 {
-    return tangent_smem_bytes_np(g, band, threads, TgDims<GBK_NPAR>::kRec4);
+    return tangent_smem_bytes_np(g, band, threads, TgDims<GBK_NPAR>::kRec4, direct);
 }
 
-size_t tangent_smem_bytes_host(const Geom &g, int band, int threads) { return tangent_smem_bytes(g, band, threads); }
+size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct)
+{
+    return tangent_smem_bytes(g, band, threads, direct);
+}
 
 // Re-centres the record at rec (centre stored as rec[0] = a) to centre c
 // and accumulates it with weight w into acc[0..kRec).
@@ -107,13 +114,13 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
     if (a.skip && a.skip[gal] != 0) return;  // the whole cluster returns together
 
     extern __shared__ __align__(16) unsigned char smem[];
-    size_t qn = (size_t)band * g.ex, hn = (size_t)2 * R * g.nx;
+    size_t qn = (size_t)band * g.ex, hn = a.direct ? 0 : (size_t)2 * R * g.nx;
     float *Q = reinterpret_cast<float *>(smem);                        // records, stride kRec4*4
     float *P = Q + (qn > hn ? qn : hn) * kRec4 * 4;
     float4 *ztab = reinterpret_cast<float4 *>(P + (size_t)band * g.nx * kRec4 * 4);
     float *wxy = reinterpret_cast<float *>(ztab + g.ez);
-    int *rowoff = reinterpret_cast<int *>(wxy + ((2 * R + 1 + 3) & ~3));
-    double *wred = reinterpret_cast<double *>(rowoff + ((band + 2 * R + 3) & ~3));  // [8 warps][kEnt]
+    const float **rowptr = reinterpret_cast<const float **>(wxy + ((2 * R + 1 + 3) & ~3));
+    double *wred = reinterpret_cast<double *>(rowptr + ((band + 2 * R + 1) & ~1));  // [8 warps][kEnt]
     constexpr int RS = TgDims<NP>::RS;
 
     __shared__ ModelConst mc;
@@ -144,13 +151,19 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
         }
         ztab[e] = make_float4(G0, g.dv * H1, g.dv * g.dv * H2, 0.f);
     }
+    // first record of extended row row0 - R + k for the y pass: own rows in
+    // P; halo rows in their copies in Q, or (direct) in the owner's P
     for (int k = tid; k < nrows + 2 * R; k += nthr) {
         int er = row0 - R + k;
-        int off;
-        if (er < row0) off = k * g.nx;
-        else if (er < row1) off = (int)((P - Q) / RS) + (er - row0) * g.nx;
-        else off = (R + (er - row1)) * g.nx;
-        rowoff[k] = off;  // in records
+        const float *ptr;
+        if (er >= row0 && er < row1) ptr = P + (size_t)(er - row0) * g.nx * RS;
+        else if (!a.direct) ptr = Q + (size_t)(er < row0 ? k : R + (er - row1)) * g.nx * RS;
+        else if (er < 0 || er >= g.ey) ptr = nullptr;  // never read: outside the image
+        else {
+            int owner = tg_band_owner(er, g.ey, cs);
+            ptr = cluster.map_shared_rank(P, owner) + (size_t)(er - tg_band_begin(owner, g.ey, cs)) * g.nx * RS;
+        }
+        rowptr[k] = ptr;
     }
     __syncthreads();
     const ModelConst &c = mc;
@@ -269,8 +282,8 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
     }
     cluster.sync();
 
-    // ---- phase 3a: halo records from the neighbours ----
-    for (int k = 0; k < 2 * R; ++k) {
+    // ---- phase 3a: halo records from the neighbours (copy mode) ----
+    for (int k = 0; k < 2 * R && !a.direct; ++k) {
         int er = (k < R) ? row0 - R + k : row1 + (k - R);
         if (er < 0 || er >= g.ey) continue;
         int owner = tg_band_owner(er, g.ey, cs);
@@ -298,11 +311,11 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
         int y = ylo + yy;
         size_t pix = (size_t)y * g.nx + xx;
         int k0 = y - (row0 - R);
-        float cen = Q[((size_t)rowoff[k0 + R] + xx) * RS];
+        float cen = rowptr[k0 + R][(size_t)xx * RS];
         float acc[RS];
 #pragma unroll
         for (int t = 0; t < RS; ++t) acc[t] = 0.f;
-        for (int j = 0; j <= 2 * R; ++j) accum_rec<NP>(Q + ((size_t)rowoff[k0 + j] + xx) * RS, cen, wxy[j], acc);
+        for (int j = 0; j <= 2 * R; ++j) accum_rec<NP>(rowptr[k0 + j] + (size_t)xx * RS, cen, wxy[j], acc);
         float S0 = acc[1], S1v = acc[2], S2v = acc[3];
         bool use = c.valid && S0 > thr && s_ob.mask[pix] != 0;
         if (use) {
@@ -441,7 +454,7 @@ gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
 {
     if (args.geoms && args.jac) return fail(GBK_EINVAL, "ragged tangent launches do not write J");
     if (args.np < 1 || args.np > GBK_NPAR) return fail(GBK_EINVAL, "tangent launch: bad free-parameter count");
-    size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads);
+    size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads, args.direct);
     // carry only x0 .. sigma0 when I0 and h are fixed and J is not written
     bool narrow = !args.jac;
     for (int k = 0; k < args.np; ++k) narrow = narrow && args.free_idx[k] < GBK_I0;
@@ -450,20 +463,26 @@ gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
 
 int tangent_cluster_for(const Geom &g)
 {
-    int cs, band;
-    return tangent_config(g, &cs, &band) ? cs : 0;
+    int cs, band, direct;
+    return tangent_config(g, &cs, &band, &direct) ? cs + 32 * direct : 0;
 }
 
-bool tangent_config(const Geom &g, int *cs, int *band)
+// Halo copies while they fit (200 KB per CTA); otherwise direct reads of the
+// neighbours' records, up to 220 KB per CTA.  The smallest cluster first.
+bool tangent_config(const Geom &g, int *cs, int *band, int *direct)
 {
     if (g.u != 1) return false;
-    for (int c = 1; c <= 16; ++c) {
-        int b = (g.ey + c - 1) / c;
-        if (c > g.ey) break;
-        if (tangent_smem_bytes(g, b, kTangentThreads) <= (size_t)200 * 1024) {
-            *cs = c;
-            *band = b;
-            return true;
+    for (int d = 0; d < 2; ++d) {
+        const size_t cap = d == 0 ? (size_t)200 * 1024 : (size_t)220 * 1024;
+        for (int c = 1; c <= 16; ++c) {
+            int b = (g.ey + c - 1) / c;
+            if (c > g.ey) break;
+            if (tangent_smem_bytes(g, b, kTangentThreads, d) <= cap) {
+                *cs = c;
+                *band = b;
+                *direct = d;
+                return true;
+            }
         }
     }
     return false;

@@ -23,6 +23,7 @@ struct TangentArgs {
     double *chi2;            // [n_models] or null: sum of squared residuals
     float *jac;              // [n_models][GBK_NPAR][2][ny][nx] or null
     int cs, band;            // cluster size, most extended rows per CTA
+    int direct;              // 1: the y pass reads halo rows in the neighbours' shared memory
     // Ragged batches (geoms != null): cluster w serves galaxy order[w] (or w)
     // with geometry geoms[gal], one model per galaxy; jac must be null.
     const Geom *geoms;
@@ -30,10 +31,13 @@ struct TangentArgs {
     size_t smem;             // dynamic shared memory (ragged: the largest need)
 };
 
-size_t tangent_smem_bytes_host(const Geom &g, int band, int threads);
-bool tangent_config(const Geom &g, int *cs, int *band);
-// Smallest cluster size whose CTAs fit the tangent kernel's shared memory.
+size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct);
+bool tangent_config(const Geom &g, int *cs, int *band, int *direct);
+// Launch shape of a galaxy as one key: cluster size + 32 * direct (0: no
+// shape fits).
 int tangent_cluster_for(const Geom &g);
+inline int tangent_key_cs(int key) { return key & 31; }
+inline int tangent_key_direct(int key) { return key >> 5; }
 gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream);
 
 }  // namespace gbk

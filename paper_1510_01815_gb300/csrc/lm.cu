@@ -392,7 +392,7 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
             const Geom &g = *t.g;
             if (g.model != GBK_MODEL_CUBE)
                 return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves the intensity-cube model");
-            if (!tangent_config(g, &ta.cs, &ta.band))
+            if (!tangent_config(g, &ta.cs, &ta.band, &ta.direct))
                 return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
             ta.g = g;
         }
@@ -447,12 +447,17 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
 
 // Survey batches: the batched mode over a ragged plan, or the plain mode one
 // galaxy (and geometry) at a time.
-// Galaxies of a plan the Jacobian kernel fits (A) and the rest (B).
+// Galaxies of a plan the Jacobian kernel serves with halo copies (A) and the
+// rest (B), which the finite-difference Jacobian of the fused evaluator
+// serves faster than the direct-halo shape.
 static void tangent_split(const SurveyPlan &sp, std::vector<int32_t> &A, std::vector<int32_t> &B)
 {
     A.clear();
     B.clear();
-    for (int i = 0; i < sp.n_gal; ++i) (tangent_cluster_for(sp.geo[i]) > 0 ? A : B).push_back(i);
+    for (int i = 0; i < sp.n_gal; ++i) {
+        const int key = tangent_cluster_for(sp.geo[i]);
+        (key > 0 && !tangent_key_direct(key) ? A : B).push_back(i);
+    }
 }
 
 // Workspace of one batched part of a survey split: its plan's tables and LM state.

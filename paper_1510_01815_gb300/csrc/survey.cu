@@ -213,7 +213,9 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp, const S
     sp->tangent_ok = true;
     for (int i = 0; i < n_gal; ++i) {
         tcs[i] = tangent_cluster_for(sp->geo[i]);
-        if (tcs[i] == 0) sp->tangent_ok = false;
+        // galaxies whose halo rows do not fit the CTA (direct shape) are
+        // fitted faster with finite differences of the fused evaluator
+        if (tcs[i] == 0 || tangent_key_direct(tcs[i])) sp->tangent_ok = false;
     }
     sp->torder.resize(n_gal);
     std::iota(sp->torder.begin(), sp->torder.end(), 0);
@@ -226,7 +228,8 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp, const S
         int i0 = sp->torder[k], e = k;
         while (e < n_gal && tcs[sp->torder[e]] == tcs[i0]) ++e;
         SurveyClass c;
-        c.cs = tcs[i0];
+        c.cs = tangent_key_cs(tcs[i0]);
+        c.direct = tangent_key_direct(tcs[i0]);
         c.threads = kTangentThreads;
         c.beg = k;
         c.end = e;
@@ -235,7 +238,8 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp, const S
         c.n_solo = 0;
         for (int j = k; j < e; ++j) {
             const Geom &g = sp->geo[sp->torder[j]];
-            c.smem = std::max(c.smem, tangent_smem_bytes_host(g, (g.ey + c.cs - 1) / c.cs, kTangentThreads));
+            c.smem = std::max(c.smem,
+                              tangent_smem_bytes_host(g, (g.ey + c.cs - 1) / c.cs, kTangentThreads, c.direct));
         }
         sp->tclasses.push_back(c);
         k = e;
@@ -336,6 +340,7 @@ gbk_status survey_tangent(const SurveyPlan &sp, const TangentArgs &proto, cudaSt
         a.cot = nullptr;
         a.cs = c.cs;
         a.band = 0;
+        a.direct = c.direct;
         a.geoms = sp.d_geo;
         a.order = sp.d_torder + c.beg;
         a.smem = c.smem;

@@ -15,6 +15,7 @@ struct SurveyClass {
     size_t smem;     // dynamic shared memory of the launch
     int persistent;  // 1: one resident wave of clusters fed by the work counters
     int n_solo;      // persistent: the last n_solo galaxies of the range go to single CTAs
+    int direct = 0;  // Jacobian classes: halo rows read in the neighbours' shared memory
 };
 
 // How the fused evaluator serves a survey: one launch per class (one = 0),

@@ -43,6 +43,9 @@ CASES = {
     "single_mode1": (synth.SINGLE_GEOM.with_(lsf_mode=1), synth.SINGLE_TRUTH),
     "nonsquare": (Geometry(40, 24, 32, 15.0, 0.0, 2.0, 35.0), P(19.7, 12.2, 145, 58, 0, 210, 3, 35, 1, 5)),
     "narrow_band": (Geometry(9, 7, 4, 10.0, 0.0, 2.0, 60.0), P(4.1, 3.2, 10, 40, 0, 30, 2, 20, 1, 3)),
+    # too wide for halo copies in shared memory: the y pass reads the halo
+    # rows in the neighbouring CTAs' shared memory
+    "direct_halo": (Geometry(72, 72, 40, 20.0, 0.0, 4.0, 30.0), P(35.2, 36.1, 30, 55, 0, 180, 5, 40, 1, 9)),
 }
 
 
