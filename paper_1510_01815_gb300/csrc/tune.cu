@@ -7,8 +7,11 @@
 // register budget and the warps per SM.  The autotuner times every valid
 // candidate on the caller's own batch and keeps the fastest for that
 // geometry; later calls with the same geometry use it.
+#include <algorithm>
 #include <cmath>
 #include <map>
+#include <utility>
+#include <vector>
 #include <mutex>
 #include <tuple>
 
@@ -127,6 +130,7 @@ gbk_status gbk_autotune(const gbk_geom *gin, int32_t n_models, const double *par
     FusedConfig bestc = {0, 0, 0, 0};
     float best_ms = 0.f;
     int tried = 0;
+    std::vector<std::pair<float, FusedConfig>> finalists;  // (screen median, configuration)
     for (int pers = 0; pers < 2; ++pers) {
     for (int ti = 0; ti < 3; ++ti) {
         for (int cs = 1; cs <= kFusedMaxCluster; ++cs) {
@@ -161,12 +165,56 @@ gbk_status gbk_autotune(const gbk_geom *gin, int32_t n_models, const double *par
             }
             float med = std::fmax(std::fmin(times[0], times[1]), std::fmin(std::fmax(times[0], times[1]), times[2]));
             ++tried;
+            finalists.push_back({med, c});
             if (bestc.cs == 0 || med < best_ms) {
                 best_ms = med;
                 bestc = c;
             }
         }
     }
+    }
+    // The screen above takes a median of 3; its four fastest candidates,
+    // often within a few per cent of each other, are re-timed with 9
+    // launches each, interleaved so that clock or thermal drift affects them
+    // alike, and the median decides.
+    if (finalists.size() > 1) {
+        std::sort(finalists.begin(), finalists.end(),
+                  [](const std::pair<float, FusedConfig> &x, const std::pair<float, FusedConfig> &y) {
+                      return x.first < y.first;
+                  });
+        if (finalists.size() > 4) finalists.resize(4);
+        std::vector<std::vector<float>> reps(finalists.size());
+        for (int rep = 0; rep < 9; ++rep) {
+            for (size_t i = 0; i < finalists.size(); ++i) {
+                const FusedConfig &c = finalists[i].second;
+                FusedArgs a = {};
+                a.g = g;
+                a.n_models = n_models;
+                a.params = params;
+                a.obs = *obs;
+                a.chi2 = chi2_scratch;
+                a.cs = c.cs;
+                a.band = c.band;
+                a.threads = c.threads;
+                a.persistent = c.persistent;
+                float ms = 0.f;
+                cudaEventRecord(t0, st);
+                const bool ok_run = launch_fused(a, st) == GBK_OK;
+                cudaEventRecord(t1, st);
+                cudaEventSynchronize(t1);
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (ok_run) reps[i].push_back(ms);
+            }
+        }
+        for (size_t i = 0; i < finalists.size(); ++i) {
+            if (reps[i].size() < 9) continue;
+            std::nth_element(reps[i].begin(), reps[i].begin() + 4, reps[i].end());
+            const float med = reps[i][4];
+            if (i == 0 || med < best_ms) {
+                best_ms = med;
+                bestc = finalists[i].second;
+            }
+        }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
