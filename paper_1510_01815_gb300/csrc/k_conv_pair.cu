@@ -12,10 +12,13 @@
 //     them to a buffer whose rows are interleaved in pairs;
 //   - pass 2 (PSF along x) then reads ROW pairs from that buffer, again one
 //     8-byte load and one packed FMA per tap for two outputs, and writes
-//     into a ring of the last W + 1 x-pass results (W = 2 Rz + 1);
-//   - pass 3 (LSF along z) gathers output channel e - W from the ring while
-//     pass 2 of channel e fills the next slot, so each channel needs two
-//     block barriers; finished rows of 32 floats are written coalesced.
+//     into a ring of the last W + 4 x-pass results (W = 2 Rz + 1);
+//   - pass 3 (LSF along z) runs every fourth channel, while pass 2 of the
+//     channel fills the next slot: each thread computes FOUR consecutive
+//     output channels of its column pairs from the 4 + W - 1 ring entries
+//     they need (register blocking along z: 4 + W - 1 shared loads for 4
+//     outputs instead of 4 W), so each channel needs two block barriers;
+//     finished rows of 32 floats are written coalesced.
 // The separable passes are exact in real arithmetic in any order; here y
 // comes before x.
 #include <cuda.h>
@@ -31,6 +34,8 @@ constexpr int kPT = 32;            // output tile edge
 constexpr int kPThreads = 256;
 constexpr int kPRmax = 8;          // largest PSF radius served
 constexpr int kXP = kPT + 1;       // pair pitch of a ring row (conflict-free pass-2 stores)
+constexpr int kZT = 4;             // output channels per pass-3 group
+constexpr int kWmax = 2 * 8 + 1;   // widest LSF window served (Rz <= 8)
 constexpr long kPWaitLimit = 1L << 24;
 
 __device__ int g_conv_pair_status;  // 0 fine; 1 a TMA wait timed out
@@ -71,7 +76,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     conv3d_pair_kernel(const __grid_constant__ CUtensorMap tmap, ConvPairArgs a)
 {
     const Geom &g = a.g;
-    const int W = 2 * g.Rz + 1, NR = W + 1;  // ring of NR x-pass results
+    const int W = 2 * g.Rz + 1, NR = W + kZT;  // ring of NR x-pass results
     const int SY = kPT + 2 * R, BW = a.box_w, C1W = kPT + 2 * R, C1P = C1W / 2;
     // Pair-row pitches of the two buffers (in pairs), chosen odd / 33 so that a
     // warp's 8-byte accesses spread over all 32 banks.
@@ -130,10 +135,11 @@ __global__ void __launch_bounds__(kPThreads, 2)
     const int ox = tx0 + c;
     const int oy0 = ty0 + 2 * rp;
 
-    // Step e runs passes 1 and 2 of channel e (e < ez) and pass 3 of output
-    // channel k = e - W, whose inputs e - W .. e - 1 are in ring slots
-    // (k + q) % NR; channel e goes to slot e % NR, which none of them uses.
-    for (int e = 0; e <= g.ez; ++e) {
+    // Step e runs passes 1 and 2 of channel e (e < ez) into ring slot e % NR
+    // and, when k0 = e - (kZT + W - 1) is a multiple of kZT, pass 3 of output
+    // channels k0 .. k0 + kZT - 1, whose inputs k0 .. e - 1 sit in the other
+    // kZT + W - 1 slots.
+    for (int e = 0; e < g.ez + kZT; ++e) {
         if (e < g.ez) {
             float *slab = (e & 1) ? slab1 : slab0;
             if (!mbar_wait(&bar[e & 1], (uint32_t)((e >> 1) & 1), kPWaitLimit)) {
@@ -183,27 +189,48 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 dst[3] = A3;
             }
         }
-        // ---- pass 3: z for output channel k = e - W ----
-        const int k = e - W;
-        if (k >= 0) {
-            f32x2 B0 = Z, B1 = Z;
-            int slot = k % NR;
-            for (int q = 0; q < W; ++q) {
-                const f32x2 wq = wz2[q];
-                const float *xs = Xr + (size_t)slot * 16 * kXP * 2;
-                B0 = fma2(wq, ld2(xs + (rp * kXP + c) * 2), B0);
-                B1 = fma2(wq, ld2(xs + ((rp + 8) * kXP + c) * 2), B1);
-                slot = (slot + 1 == NR) ? 0 : slot + 1;
-            }
-            if (ox < g.nxf) {
-                float v0, v1, v2, v3;
-                upk2(B0, v0, v1);
-                upk2(B1, v2, v3);
-                float *Fk = F + (size_t)k * fplane + ox;
-                if (oy0 < g.nyf) Fk[(size_t)oy0 * g.nxf] = v0;
-                if (oy0 + 1 < g.nyf) Fk[(size_t)(oy0 + 1) * g.nxf] = v1;
-                if (oy0 + 16 < g.nyf) Fk[(size_t)(oy0 + 16) * g.nxf] = v2;
-                if (oy0 + 17 < g.nyf) Fk[(size_t)(oy0 + 17) * g.nxf] = v3;
+        // ---- pass 3: z for output channels k0 .. k0 + kZT - 1 ----
+        const int k0 = e - (kZT + W - 1);
+        if (k0 >= 0 && k0 % kZT == 0 && k0 < g.nzf) {
+            const int s0 = k0 % NR;
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+                const int prow = rp + 8 * half;  // row pair of this thread's column
+                const float *col = Xr + (size_t)(prow * kXP + c) * 2;
+                // inputs k0 .. k0 + kZT + W - 2 (the guards are warp-uniform)
+                f32x2 xin[kZT + kWmax - 1];
+#pragma unroll
+                for (int i = 0; i < kZT + kWmax - 1; ++i) {
+                    if (i < kZT + W - 1) {
+                        int slot = s0 + i;
+                        if (slot >= NR) slot -= NR;
+                        xin[i] = ld2(col + (size_t)slot * 16 * kXP * 2);
+                    }
+                }
+                f32x2 B[kZT];
+#pragma unroll
+                for (int t = 0; t < kZT; ++t) B[t] = Z;
+#pragma unroll
+                for (int j = 0; j < kWmax; ++j) {
+                    if (j < W) {
+                        const f32x2 wq = wz2[j];
+#pragma unroll
+                        for (int t = 0; t < kZT; ++t) B[t] = fma2(wq, xin[t + j], B[t]);
+                    }
+                }
+                const int oy = oy0 + 16 * half;
+                if (ox < g.nxf) {
+#pragma unroll
+                    for (int t = 0; t < kZT; ++t) {
+                        if (k0 + t < g.nzf) {
+                            float v0, v1;
+                            upk2(B[t], v0, v1);
+                            float *Fk = F + (size_t)(k0 + t) * fplane + ox;
+                            if (oy < g.nyf) Fk[(size_t)oy * g.nxf] = v0;
+                            if (oy + 1 < g.nyf) Fk[(size_t)(oy + 1) * g.nxf] = v1;
+                        }
+                    }
+                }
             }
         }
     }
@@ -233,14 +260,15 @@ static EncodeTiledFnP encode_fn_p()
 static size_t conv_pair_smem_bytes(const Geom &g)
 {
     const int SY = kPT + 2 * g.R, BW = (kPT + 2 * g.R + 3) & ~3, C1W = kPT + 2 * g.R;
-    const int SS = (SY * BW + 31) & ~31, NR = 2 * g.Rz + 2;
+    const int SS = (SY * BW + 31) & ~31, NR = 2 * g.Rz + 1 + kZT;
     return 128 + sizeof(float) * ((size_t)2 * SS + 32 * (C1W + 1) + (size_t)NR * 32 * kXP) +
            sizeof(f32x2) * (2 * g.R + 1 + 2 * g.Rz + 1);
 }
 
 bool conv_pair_supported(const Geom &g)
 {
-    return g.R <= kPRmax && conv_pair_smem_bytes(g) <= 200 * 1024 && encode_fn_p() != nullptr;
+    return g.R <= kPRmax && 2 * g.Rz + 1 <= kWmax && conv_pair_smem_bytes(g) <= 200 * 1024 &&
+           encode_fn_p() != nullptr;
 }
 
 template <int R>
