@@ -586,8 +586,10 @@ def run_vfield(gbk, torch, n_models, n_fit, n_plain, device):
                       6: (0.05, 100), 8: (0.1, 5), 9: (0.05, 5)}.items():
         lo[:, k], hi[:, k] = l, h
     p0 = np.array([synth.perturb(rng, ft[i], free, 0.1, lo[i], hi[i]) for i in range(n_fit)])
-    for name, mode, sub in (("batched_fd", gbk.LM_BATCHED, n_fit), ("plain_fd", gbk.LM_PLAIN, n_plain)):
-        opts = gbk.lm_opts(max_iter=200, mode=mode, free=free)
+    for name, mode, jac, sub in (("batched_tangent", gbk.LM_BATCHED, gbk.JAC_TANGENT, n_fit),
+                                 ("batched_fd", gbk.LM_BATCHED, gbk.JAC_FD_FORWARD, n_fit),
+                                 ("plain_fd", gbk.LM_PLAIN, gbk.JAC_FD_FORWARD, n_plain)):
+        opts = gbk.lm_opts(max_iter=200, mode=mode, free=free, jacobian=jac)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         q, c, it, st = gbk.fit_lm(g, fobs[:sub], p0[:sub], lo[:sub], hi[:sub], opts, device=device)
@@ -598,7 +600,8 @@ def run_vfield(gbk, torch, n_models, n_fit, n_plain, device):
         out[name] = {"galaxies": sub, "fits_per_s": sub / dt, "p50_iters": float(np.percentile(it, 50)),
                      "p99_iters": float(np.percentile(it, 99)), "converged_frac": float(np.mean(np.isin(st, [1, 2]))),
                      "median_dpa": float(np.median(dpa)), "median_dvt": float(np.median(dv))}
-    out["batched_fd"]["speedup_vs_plain"] = out["batched_fd"]["fits_per_s"] / out["plain_fd"]["fits_per_s"]
+    for name in ("batched_tangent", "batched_fd"):
+        out[name]["speedup_vs_plain"] = out[name]["fits_per_s"] / out["plain_fd"]["fits_per_s"]
     return out
 
 

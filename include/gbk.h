@@ -103,8 +103,10 @@ typedef struct gbk_geom {
  * used, upsample must be 1; at r = 0 the field is Vsys.  Parameter domain:
  * 0 <= i < 90, r_t > 0, sigma0 >= 0, the used parameters finite.  Served by
  * the fused entry points (gbk_eval_cubes maps, gbk_chi2, gbk_fit_lm with
- * finite differences, gbk_grid, gbk_nested_sample); the staged path, cubes,
- * the tangent Jacobian and survey batches answer GBK_EUNSUPPORTED. */
+ * finite differences or the analytic Jacobian, gbk_jacobian, gbk_grid,
+ * gbk_nested_sample); the staged path, cubes and survey batches answer
+ * GBK_EUNSUPPORTED.  The analytic Jacobian of a field is zero at r = 0 for
+ * the radius-dependent terms (the cusp of r), as for the cube. */
 #define GBK_MODEL_CUBE           0
 #define GBK_MODEL_VFIELD_ARCTAN  1
 #define GBK_MODEL_VFIELD_EPINAT  2

@@ -14,10 +14,9 @@ extern "C" gbk_status gbk_jacobian(const gbk_geom *gin, int32_t n_models, const 
     if (n_models < 0) return fail(GBK_EINVAL, "n_models must be >= 0");
     if (free_mask == 0 || (free_mask >> GBK_NPAR)) return fail(GBK_EINVAL, "free_mask must select 1..10 parameters");
     if (g.u != 1) return fail(GBK_EUNSUPPORTED, "the Jacobian kernel needs upsample == 1");
-    if (g.model != GBK_MODEL_CUBE)
-        return fail(GBK_EUNSUPPORTED, "the analytic Jacobian serves the intensity-cube model");
     TangentArgs a = {};
-    if (!tangent_config(g, &a.cs, &a.band, &a.direct))
+    // velocity fields: one CTA per model, no shared-memory records
+    if (g.model == GBK_MODEL_CUBE && !tangent_config(g, &a.cs, &a.band, &a.direct))
         return fail(GBK_EUNSUPPORTED, "geometry %d x %d too large for the Jacobian kernel", g.nx, g.ny);
     if (n_models == 0) return ok();
     if ((s = check_device_ptr(params, "params", 8))) return s;

@@ -452,6 +452,7 @@ static gbk_status launch_np(const TangentArgs &args, size_t smem, cudaStream_t s
 
 gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
 {
+    if (!args.geoms && args.g.model != GBK_MODEL_CUBE) return launch_vfield_tangent(args, stream);
     if (args.geoms && args.jac) return fail(GBK_EINVAL, "ragged tangent launches do not write J");
     if (args.np < 1 || args.np > GBK_NPAR) return fail(GBK_EINVAL, "tangent launch: bad free-parameter count");
     size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads, args.direct);

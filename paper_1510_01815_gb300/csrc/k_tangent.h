@@ -39,5 +39,7 @@ int tangent_cluster_for(const Geom &g);
 inline int tangent_key_cs(int key) { return key & 31; }
 inline int tangent_key_direct(int key) { return key >> 5; }
 gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream);
+// Velocity-field models (k_vfield.cu); launch_tangent dispatches to it.
+gbk_status launch_vfield_tangent(const TangentArgs &args, cudaStream_t stream);
 
 }  // namespace gbk

@@ -10,6 +10,7 @@
 // block reduction, so chi2 is bitwise reproducible.
 #include "gbk_api_internal.h"
 #include "k_fused.h"
+#include "k_tangent.h"
 
 namespace gbk {
 
@@ -127,6 +128,198 @@ __global__ void __launch_bounds__(kVfThreads) vfield_kernel(FusedArgs a)
         }
         __syncthreads();  // s_c, s_ob and red are rewritten by the next model
     }
+}
+
+// ---------------------------------------------------------------------------
+// Analytic Jacobian of the velocity-field residuals.  With F(r) = Vrot(r) / r,
+// m1 = Vsys + F(r) x_e sin i and m2 = sigma0; by the chain rule through
+// Eqs. 1-4 (angles in degrees):
+//   d x_e = (sin PA, -cos PA, y_e k)  and  d y_e = (cos PA, sin PA, -x_e k)
+//   for (x0, y0, PA), k = pi / 180;  d y_d = d y_e / cos i, and for the
+//   inclination d y_d / di = y_d tan i k;  d r = (x_e dx_e + y_d dy_d) / r;
+//   dm1 = sin i (F'(r) dr x_e + F dx_e) for (x0, y0, PA),
+//   dm1/di = F x_e cos i k + sin i F'(r) dr_i x_e,  dm1/dVsys = 1,
+//   dm1/dtheta = sin i x_e dF/dtheta for the curve's parameters;
+//   arctan (Eq. 6, c = 2 Vmax / pi, u = r / r_t):
+//     F' = c (u / (1 + u^2) - atan u) / r^2 (series for small u),
+//     dF/dVmax = (2 / pi) atan(u) / r,  dF/dr_t = -c / (r_t^2 + r^2);
+//   Epinat (Eq. 7, q = r / r_t, D = 1 + q^a):
+//     F' = (F / r) ((g - 1) - a q^a / D),  dF/dV_t = q^g / (D r),
+//     dF/dr_t = -(F / r_t) (g - a q^a / D),  dF/da = -F q^a ln q / D,
+//     dF/dg = F ln q;
+//   dm2/dsigma0 = 1.  At r = 0 the cusp of r gets the one-sided value 0 (and
+//   the Epinat curve, whose F is 0 there, zero derivatives).  Rows are
+//   J_v = w_v dm1, J_s = w_s dm2 on unmasked pixels.  Every thread keeps its
+//   pixels' J^T J, J^T v and sum r^2 for all ten parameters in registers;
+//   the CTA reduces them in FP64 in a fixed order.
+constexpr int kVfEnt = GBK_NPAR * (GBK_NPAR + 1) / 2 + GBK_NPAR + 1;
+
+__global__ void __launch_bounds__(kVfThreads) vfield_tangent_kernel(TangentArgs a)
+{
+    __shared__ VfConst s_c;
+    __shared__ gbk_obs s_ob;
+    __shared__ double wred[kVfThreads / 32][kVfEnt];
+    __shared__ double s_part[kVfEnt];
+    const int tid = threadIdx.x;
+    const int nx = a.g.nx, np = a.g.nx * a.g.ny;
+    const int mpg = a.models_per_gal;
+    const float kdeg = 0.017453292519943295f;
+    for (int model = blockIdx.x; model < a.n_models; model += gridDim.x) {
+        const int gal = mpg > 0 ? model / mpg : 0;
+        if (a.skip && a.skip[gal] != 0) continue;
+        if (tid == 0) {
+            s_c = vf_const(a.params + (size_t)model * GBK_NPAR, a.g.model);
+            s_ob = a.obs_list ? a.obs_list[gal] : a.obs;
+        }
+        __syncthreads();
+        const VfConst c = s_c;
+        const float si = c.sin_i, ci = 1.f / c.inv_cos_i, ti = si * c.inv_cos_i;
+        const float vmax = (float)a.params[(size_t)model * GBK_NPAR + GBK_VMAX];
+        float E[kVfEnt];
+#pragma unroll
+        for (int e = 0; e < kVfEnt; ++e) E[e] = 0.f;
+        for (int pix = tid; pix < np; pix += kVfThreads) {
+            const int y = pix / nx, x = pix - y * nx;
+            float dx = (float)x - c.x0, dy = (float)y - c.y0;
+            float xe = -dx * c.sin_pa + dy * c.cos_pa;
+            float ye = -dx * c.cos_pa - dy * c.sin_pa;
+            float yd = ye * c.inv_cos_i;
+            float r = sqrtf(xe * xe + yd * yd);
+            float F, Fr, Fv, Frt, Fa = 0.f, Fg = 0.f;
+            if (c.epinat) {
+                if (r > 0.f) {
+                    float q = r * c.inv_rt, lq = logf(q);
+                    float qg = expf(c.g * lq), qa = expf(c.a * lq), D = 1.f + qa;
+                    Fv = qg / (D * r);
+                    F = c.vk * Fv;
+                    float aq = c.a * qa / D;
+                    Fr = F / r * ((c.g - 1.f) - aq);
+                    Frt = -F * c.inv_rt * (c.g - aq);
+                    Fa = -F * qa * lq / D;
+                    Fg = F * lq;
+                } else {
+                    F = Fr = Fv = Frt = 0.f;
+                }
+            } else {
+                float u = r * c.inv_rt, at = atanf(u);
+                Fv = 0.63661977f * ((r > 0.f) ? at / r : c.inv_rt);
+                F = vmax * Fv;
+                if (r <= 0.f) Fr = 0.f;
+                else if (u < 0.1f) Fr = c.vk * c.inv_rt * c.inv_rt * u * (-2.f / 3.f + 0.8f * u * u);
+                else Fr = c.vk * (u / (1.f + u * u) - at) / (r * r);
+                float rt = 1.f / c.inv_rt;
+                Frt = -c.vk / (rt * rt + r * r);
+            }
+            float m1 = c.vsys + F * xe * si;
+            float rx = 0.f, ry = 0.f, ri = 0.f;  // dr per unit dx_e, dy_e; dr/di
+            if (r > 0.f) {
+                rx = xe / r;
+                ry = yd * c.inv_cos_i / r;
+                ri = yd * yd * ti * kdeg / r;
+            }
+            float jv[GBK_NPAR], js[GBK_NPAR];
+#pragma unroll
+            for (int k = 0; k < GBK_NPAR; ++k) { jv[k] = 0.f; js[k] = 0.f; }
+            float rv = 0.f, rs = 0.f, cv = 0.f, cs = 0.f;
+            if (c.valid && s_ob.mask[pix] != 0) {
+                const float wv = s_ob.w_v[pix], ws = s_ob.w_s[pix];
+                const float dxe[3] = {c.sin_pa, -c.cos_pa, ye * kdeg};
+                const float dye[3] = {c.cos_pa, c.sin_pa, -xe * kdeg};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float dr = rx * dxe[k] + ry * dye[k];
+                    jv[k] = wv * si * (Fr * dr * xe + F * dxe[k]);
+                }
+                jv[GBK_INCL] = wv * (F * xe * ci * kdeg + si * Fr * ri * xe);
+                jv[GBK_VSYS] = wv;
+                jv[GBK_VMAX] = wv * si * xe * Fv;
+                jv[GBK_RT] = wv * si * xe * Frt;
+                jv[GBK_EPI_A] = wv * si * xe * Fa;
+                jv[GBK_EPI_G] = wv * si * xe * Fg;
+                js[GBK_SIG0] = ws;
+                rv = wv * (m1 - s_ob.v_obs[pix]);
+                rs = ws * (c.sig0 - s_ob.s_obs[pix]);
+                if (a.cot) {
+                    cv = a.cot[(size_t)model * 2 * np + pix];
+                    cs = a.cot[(size_t)model * 2 * np + np + pix];
+                } else {
+                    cv = rv;
+                    cs = rs;
+                }
+            }
+            if (a.jac) {
+                float *J = a.jac + (size_t)model * GBK_NPAR * 2 * np;
+#pragma unroll
+                for (int k = 0; k < GBK_NPAR; ++k) {
+                    J[((size_t)k * 2) * np + pix] = jv[k];
+                    J[((size_t)k * 2 + 1) * np + pix] = js[k];
+                }
+            }
+            int e = 0;
+#pragma unroll
+            for (int j = 0; j < GBK_NPAR; ++j)
+#pragma unroll
+                for (int k = j; k < GBK_NPAR; ++k, ++e) E[e] = fmaf(jv[j], jv[k], fmaf(js[j], js[k], E[e]));
+#pragma unroll
+            for (int j = 0; j < GBK_NPAR; ++j, ++e) E[e] = fmaf(jv[j], cv, fmaf(js[j], cs, E[e]));
+            E[e] = fmaf(rv, rv, fmaf(rs, rs, E[e]));
+        }
+        // CTA sum: warps by shuffles in FP64, then the warps in order
+        const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+        for (int e = 0; e < kVfEnt; ++e) {
+            double v = (double)E[e];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) wred[warp][e] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < kVfEnt; e += kVfThreads) {
+            double v = 0.0;
+            for (int q = 0; q < kVfThreads / 32; ++q) v += wred[q][e];
+            s_part[e] = v;
+        }
+        __syncthreads();
+        const int nf = a.np, ntri = nf * (nf + 1) / 2;
+        if (tid < ntri + nf + 1) {
+            int src, j = 0, k = 0;
+            if (tid < ntri) {
+                int t = tid;
+                while (t >= nf - j) { t -= nf - j; ++j; }
+                k = j + t;
+                int p = a.free_idx[j], q = a.free_idx[k];
+                if (p > q) { int w = p; p = q; q = w; }
+                src = p * GBK_NPAR - p * (p - 1) / 2 + (q - p);
+            } else if (tid < ntri + nf) {
+                src = GBK_NPAR * (GBK_NPAR + 1) / 2 + a.free_idx[tid - ntri];
+            } else {
+                src = kVfEnt - 1;
+            }
+            double v = c.valid ? s_part[src] : (double)__int_as_float(0x7fc00000);
+            if (tid < ntri) {
+                if (a.jtj) {
+                    a.jtj[(size_t)model * nf * nf + j * nf + k] = v;
+                    a.jtj[(size_t)model * nf * nf + k * nf + j] = v;
+                }
+            } else if (tid < ntri + nf) {
+                if (a.jtv) a.jtv[(size_t)model * nf + (tid - ntri)] = v;
+            } else if (a.chi2) {
+                a.chi2[model] = v;
+            }
+        }
+        __syncthreads();  // s_c, s_ob, wred and s_part are rewritten by the next model
+    }
+}
+
+gbk_status launch_vfield_tangent(const TangentArgs &a, cudaStream_t st)
+{
+    if (a.geoms) return fail(GBK_EUNSUPPORTED, "survey batches serve the intensity-cube model");
+    if (a.np < 1 || a.np > GBK_NPAR) return fail(GBK_EINVAL, "velocity-field Jacobian: bad free-parameter count");
+    if (a.n_models <= 0) return GBK_OK;
+    int blocks = a.n_models < 152 * 8 ? a.n_models : 152 * 8;
+    vfield_tangent_kernel<<<blocks, kVfThreads, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "velocity-field Jacobian launch");
+    return GBK_OK;
 }
 
 gbk_status launch_vfield(const FusedArgs &a, cudaStream_t st)

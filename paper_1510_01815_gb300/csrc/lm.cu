@@ -390,9 +390,7 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
                 return fail(GBK_EUNSUPPORTED, "a galaxy of the batch is too large for the Jacobian kernel");
         } else {
             const Geom &g = *t.g;
-            if (g.model != GBK_MODEL_CUBE)
-                return fail(GBK_EUNSUPPORTED, "the tangent Jacobian serves the intensity-cube model");
-            if (!tangent_config(g, &ta.cs, &ta.band, &ta.direct))
+            if (g.model == GBK_MODEL_CUBE && !tangent_config(g, &ta.cs, &ta.band, &ta.direct))
                 return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
             ta.g = g;
         }

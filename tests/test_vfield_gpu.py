@@ -104,12 +104,67 @@ def test_vfield_refusals(G):
     with pytest.raises(G.GbkError):
         G.chi2(g, p, d, flags=G.PATH_STAGED)
     with pytest.raises(G.GbkError):
-        G.jacobian(g, p, d)
-    with pytest.raises(G.GbkError):
         G.gbk_survey_workspace_bytes([g])
 
 
-def _fit_case(G, model, seed, frac):
+def _vf_obs(G, g, truth, seed, noise=3.0):
+    """Oracle field of `truth` plus noise, with a masked block."""
+    m = oracle.evaluate(ogeom(g), truth)
+    rng = np.random.default_rng(seed)
+    wv, ws = synth.weights((g.ny, g.nx), 5.0)
+    mask = np.ones((g.ny, g.nx), np.uint8)
+    mask[2:5, 3:9] = 0
+    v = (m[1] + rng.normal(0, noise, m[1].shape)).astype(np.float32)
+    sg = (m[2] + rng.normal(0, noise, m[2].shape)).astype(np.float32)
+    return oracle.Obs(v, sg, wv, ws, mask)
+
+
+def _oracle_vf_jacobian(g, p, obs, steps):
+    og = ogeom(g)
+    cols = []
+    for k in range(10):
+        a, b = p.copy(), p.copy()
+        a[k] += steps[k]
+        b[k] -= steps[k]
+        _, r = oracle.chi2_batch(og, np.array([a, b]), obs, want_resid=True)
+        cols.append((r[0] - r[1]) / (2 * steps[k]))
+    return np.array(cols)  # [10][2][ny][nx]
+
+
+@pytest.mark.parametrize("model", [VF_ARCTAN, VF_EPINAT])
+def test_vfield_jacobian_matches_central_differences(G, model):
+    """Analytic Jacobian of the velocity-field residuals (every parameter,
+    both curves) against FP64 central differences of the oracle; its J^T J,
+    J^T r and chi2 against the J it writes."""
+    nx, ny = 40, 34
+    g = vgeom(nx, ny, model)
+    ps = vparams(3, 21, nx, ny, model)
+    ps[0, 0] += 0.37  # keep the centre off the pixel grid for central differences
+    obs = _vf_obs(G, g, ps[1], 5)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    jac, jtj, jtv, c2 = G.jacobian(g, torch.from_numpy(ps), dobs, free=tuple(range(10)))
+    jac = jac.cpu().numpy()
+    steps = np.array([1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-4, 1e-3, 1e-5, 1e-5])
+    for i in range(ps.shape[0]):
+        ref = _oracle_vf_jacobian(g, ps[i], obs, steps)
+        used = [k for k in range(10) if model == VF_EPINAT or k not in (8, 9)]
+        for k in used:
+            scale = np.abs(ref[k]).max() + 1e-6
+            err = np.abs(jac[i, k] - ref[k]).max()
+            assert err <= 2e-3 * scale + 1e-4, (i, k, err, scale)
+        if model == VF_ARCTAN:
+            assert np.all(jac[i, 8:] == 0.0)
+        # reductions of the rows the kernel wrote
+        J = jac[i].reshape(10, -1).astype(np.float64)
+        _, r = oracle.chi2_batch(ogeom(g), ps[i:i + 1], obs, want_resid=True)
+        r = r[0].reshape(-1)
+        np.testing.assert_allclose(jtj[i].cpu().numpy(), J @ J.T, rtol=2e-4, atol=1e-3 * np.abs(J @ J.T).max())
+        np.testing.assert_allclose(jtv[i].cpu().numpy(), J @ r, rtol=2e-3, atol=2e-3 * np.abs(J @ r).max())
+        assert abs(float(c2[i]) - float(r @ r)) <= 1e-4 * float(r @ r)
+    assert G.gbk_device_status() == 0
+
+
+def _fit_case(G, model, seed, frac, jacobian=None):
     nx, ny = 48, 48
     g = vgeom(nx, ny, model)
     rng = np.random.default_rng(seed)
@@ -126,9 +181,20 @@ def _fit_case(G, model, seed, frac):
     for k in free:
         lo[k], hi[k] = bounds[k]
     p0 = np.array([synth.perturb(rng, truth, free, frac, lo, hi) for _ in range(6)])
-    opts = G.lm_opts(max_iter=200, free=free)
+    opts = G.lm_opts(max_iter=200, free=free, jacobian=jacobian if jacobian is not None else G.JAC_FD_FORWARD)
     q, c, it, st = G.fit_lm(g, [d] * 6, p0, [lo] * 6, [hi] * 6, opts)
     return truth, q, c, it, st
+
+
+@pytest.mark.parametrize("model", [VF_ARCTAN, VF_EPINAT])
+def test_vfield_tangent_fit_recovers(G, model):
+    """LM with the analytic velocity-field Jacobian recovers the truth from
+    perturbed starts (20 % arctan, 5 % Epinat) like the FD LM does."""
+    truth, q, c, it, st = _fit_case(G, model, 9, 0.2 if model == VF_ARCTAN else 0.05, G.JAC_TANGENT)
+    assert np.all(np.isin(st, [1, 2])), (st, it)
+    assert np.all(c < 1e-3), c
+    assert np.all(np.abs(q[:, 2] - truth[2]) < 1.0), q[:, 2]
+    assert np.all(np.abs(q[:, 5] - truth[5]) < 2.0), q[:, 5]
 
 
 def test_vfield_arctan_fit_recovers(G):
