@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--survey-plain", type=int, default=64, help="galaxies the plain survey LM is timed on")
     ap.add_argument("--no-cnn", action="store_true", help="skip the learned-seed (CNN) measurement")
     ap.add_argument("--no-vfield", action="store_true", help="skip the velocity-field (Epinat) measurement")
+    ap.add_argument("--no-degeneracy", action="store_true", help="skip the V_t - i degeneracy chi2 maps")
     ap.add_argument("--no-gemm", action="store_true", help="skip the tensor-core GEMM measurement")
     ap.add_argument("--cnn-train", type=int, default=1048576, help="training galaxies of the CNN seed")
     ap.add_argument("--cnn-epochs", type=int, default=2)
@@ -605,6 +606,59 @@ def run_vfield(gbk, torch, n_models, n_fit, n_plain, device):
     return out
 
 
+def run_degeneracy(gbk, torch, device):
+    """The V_t - i degeneracy (Sec. 6.1): reduced chi-squared maps over
+    (i, V_t) of C1-like mocks with V_t = 200 km/s at i = 20, 40, 60, 70 deg and
+    5 / 5 sqrt(2) km/s noise; every map is one gbk_chi2 launch over a
+    0.25 deg x 1 km/s grid.  Reports the best node and the extents of the
+    1 and 3 sigma regions (chi2 - min <= 2.30, 11.83)."""
+    g = synth.SINGLE_GEOM
+    inc_ax = np.arange(5.0, 85.0 + 1e-9, 0.25)
+    vt_ax = np.arange(50.0, 600.0 + 1e-9, 1.0)
+    ii, vv = np.meshgrid(inc_ax, vt_ax, indexing="ij")
+    wv, ws = synth.weights((g.ny, g.nx), 5.0)
+    dwv, dws = torch.from_numpy(wv).to(device), torch.from_numpy(ws).to(device)
+    ones = torch.ones((g.ny, g.nx), dtype=torch.uint8, device=device)
+    out = {"workload": "C1 geometry (32x32x64), V_t = 200 km/s, noise 5 / 5 sqrt(2) km/s, %d x %d (i, V_t) nodes "
+                       "per map, other parameters at the truth" % (len(inc_ax), len(vt_ax)), "maps": {}}
+    total_ms, total_models = 0.0, 0
+    for inc in (20.0, 40.0, 60.0, 70.0):
+        p = synth.SINGLE_TRUTH.copy()
+        p[synth.INCL], p[synth.VMAX] = inc, 200.0
+        m = gbk.eval_maps(g, torch.from_numpy(p[None]), device=device)[0]
+        rng = np.random.default_rng(100 + int(inc))
+        v = m[1] + torch.from_numpy(rng.normal(0.0, 5.0, (g.ny, g.nx)).astype(np.float32)).to(device)
+        s = m[2] + torch.from_numpy(rng.normal(0.0, 5.0 * np.sqrt(2.0), (g.ny, g.nx)).astype(np.float32)).to(device)
+        obs = gbk.Obs(v.contiguous(), s.contiguous(), dwv, dws, ones)
+        grid = np.repeat(p[None], ii.size, 0)
+        grid[:, synth.INCL], grid[:, synth.VMAX] = ii.ravel(), vv.ravel()
+        dg = torch.from_numpy(grid).to(device)
+        gbk.chi2(g, dg, obs, device=device)  # warm-up (and the launch tuning)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        c = gbk.chi2(g, dg, obs, device=device)
+        b.record()
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        total_models += ii.size
+        c = c.cpu().numpy().reshape(ii.shape)
+        d = c - c.min()
+        k = np.unravel_index(np.argmin(c), c.shape)
+        r1, r3 = d <= 2.30, d <= 11.83
+        vs = vv[r3] * np.sin(np.radians(ii[r3]))
+        out["maps"]["%g" % inc] = {
+            "best_incl": float(inc_ax[k[0]]), "best_vt": float(vt_ax[k[1]]),
+            "min_reduced_chi2": float(c.min() / (2 * g.nx * g.ny - 2)),
+            "sigma1_incl": [float(ii[r1].min()), float(ii[r1].max())],
+            "sigma1_vt": [float(vv[r1].min()), float(vv[r1].max())],
+            "sigma3_incl": [float(ii[r3].min()), float(ii[r3].max())],
+            "sigma3_vt": [float(vv[r3].min()), float(vv[r3].max())],
+            "sigma3_vt_sini_rel_spread": float(np.ptp(vs) / np.mean(vs))}
+    out["evals_per_s"] = total_models / (total_ms * 1e-3)
+    return out
+
+
 def run_gemm(gbk, torch, device, sizes=((8192, 8192, 8192), (32768, 256, 4096), (262144, 64, 48))):
     """The tcgen05 BF16 GEMM on large shapes against the measured bf16
     peak; cuBLAS (torch.matmul) on the same shapes is timed beside it for
@@ -915,6 +969,8 @@ def run_gbk(args):
         out["gemm"] = run_gemm(gbk, torch, dev)
     if not args.no_vfield:
         out["vfield"] = run_vfield(gbk, torch, 1024, 512, 8, dev)
+    if not args.no_degeneracy:
+        out["degeneracy"] = run_degeneracy(gbk, torch, dev)
     if not args.no_cnn:
         out["cnn"] = run_cnn(gbk, torch, args.cnn_train, args.cnn_epochs, args.cnn_batch, args.cnn_test, 64, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
