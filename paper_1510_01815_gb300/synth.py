@@ -158,11 +158,13 @@ def weights(shape, e_v, w_sigma=1.0):
 SURVEY_PSF_FWHM = 4.0
 
 
-def draw_survey(rng, n):
-    """Returns a list of (Geometry, true params) for n survey galaxies."""
+def draw_survey(rng, n, nxy_range=(24, 96)):
+    """Returns a list of (Geometry, true params) for n survey galaxies
+    (spatial size log-uniform over nxy_range; the mock dataset of Sec. 3.1
+    uses 32 - 96)."""
     out = []
     for _ in range(n):
-        nxy = int(round(np.exp(rng.uniform(np.log(24), np.log(96)))))
+        nxy = int(round(np.exp(rng.uniform(np.log(nxy_range[0]), np.log(nxy_range[1])))))
         nz = int(round(np.exp(rng.uniform(np.log(32), np.log(128)))))
         pa = rng.uniform(0.0, 45.0)
         incl = rng.uniform(5.0, 85.0)
