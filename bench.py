@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--no-vfield", action="store_true", help="skip the velocity-field (Epinat) measurement")
     ap.add_argument("--no-degeneracy", action="store_true", help="skip the V_t - i degeneracy chi2 maps")
     ap.add_argument("--no-mock", action="store_true", help="skip the mock-dataset recovery study")
+    ap.add_argument("--no-ns", action="store_true", help="skip nested sampling of Fabry-Perot galaxies")
     ap.add_argument("--mock-galaxies", type=int, default=1000, help="galaxies per noise level of the mock study")
     ap.add_argument("--no-gemm", action="store_true", help="skip the tensor-core GEMM measurement")
     ap.add_argument("--cnn-train", type=int, default=1048576, help="training galaxies of the CNN seed")
@@ -706,6 +707,46 @@ def run_mock_study(gbk, torch, n, device):
     return out
 
 
+def run_ns_fp(gbk, torch, device, n_gal=2, n_live=400, batch=100):
+    """Nested sampling (Sec. 2.3.2) of Fabry-Perot galaxies (192 x 192 x 48,
+    the workload of the headline number): n_live live points, `batch`
+    proposals per iteration evaluated in one fused launch, uniform prior over
+    the workload's ranges (x0, y0 in 0.35 - 0.65 N, V_sys +-30 km/s);
+    observations with 5 / 5 sqrt(2) km/s noise, S/N < 3 and 2 % dead-fibre
+    masks."""
+    g = synth.FP_GEOM
+    rng = np.random.default_rng(77)
+    truth = synth.draw_fp_params(rng, n_gal)
+    maps = gbk.eval_maps(g, torch.from_numpy(truth), device=device).cpu().numpy()
+    shape = (g.ny, g.nx)
+    wv, ws = synth.weights(shape, 5.0)
+    rows = []
+    for j in range(n_gal):
+        m = maps[j]
+        v = (m[1] + rng.normal(0.0, 5.0, shape)).astype(np.float32)
+        s = (m[2] + rng.normal(0.0, 5.0 * np.sqrt(2.0), shape)).astype(np.float32)
+        mask = (synth.sn_mask(m[0]) * synth.dead_fibre_mask(rng, shape)).astype(np.uint8)
+        obs = gbk.Obs.from_numpy(v, s, wv, ws, mask, device=device)
+        lo, hi = truth[j].copy(), truth[j].copy()
+        lo[synth.X0], hi[synth.X0] = 0.35 * g.nx, 0.65 * g.nx
+        lo[synth.Y0], hi[synth.Y0] = 0.35 * g.ny, 0.65 * g.ny
+        lo[synth.VSYS], hi[synth.VSYS] = -30.0, 30.0
+        for k, (a_, b_) in synth.FP_RANGES.items():
+            lo[k], hi[k] = a_, b_
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = gbk.gbk_nested_sample(g, obs, lo, hi, n_live=n_live, batch=batch, tol=0.5, seed=11 + j, device=device)
+        dt = time.perf_counter() - t0
+        dpa = abs((r["mean"][synth.PA] - truth[j, synth.PA] + 180.0) % 360.0 - 180.0)
+        rows.append({"seconds": dt, "n_eval": r["n_eval"], "n_iter": r["n_iter"], "evals_per_s": r["n_eval"] / dt,
+                     "log_z": r["log_z"], "dvmax": float(abs(r["mean"][synth.VMAX] - truth[j, synth.VMAX])),
+                     "dpa": float(dpa), "dincl": float(abs(r["mean"][synth.INCL] - truth[j, synth.INCL])),
+                     "post_std_vmax": float(r["std"][synth.VMAX])})
+    return {"workload": "Fabry-Perot 192x192x48 galaxies, %d live points, %d proposals per launch, 8 free "
+                        "parameters" % (n_live, batch), "galaxies": rows,
+            "mean_seconds_per_galaxy": float(np.mean([x["seconds"] for x in rows]))}
+
+
 def run_degeneracy(gbk, torch, device):
     """The V_t - i degeneracy (Sec. 6.1): reduced chi-squared maps over
     (i, V_t) of C1-like mocks with V_t = 200 km/s at i = 20, 40, 60, 70 deg and
@@ -827,12 +868,19 @@ def cpu_baseline(g, obs_np, n_models, seed):
     rng = np.random.default_rng(seed + 99)
     ps = synth.draw_fp_params(rng, n)
     o = oracle.Obs(*obs_np)
+    og = oracle.Geom(**g.asdict())
     t = time.perf_counter()
-    oracle.chi2_batch(oracle.Geom(**g.asdict()), ps, o, nthreads=cores)
+    oracle.chi2_batch(og, ps, o, nthreads=cores)
     dt = time.perf_counter() - t
+    # and one core: two models, one after the other
+    t = time.perf_counter()
+    oracle.chi2_batch(og, ps[:2], o, nthreads=1)
+    dt1 = time.perf_counter() - t
     return {"value": n / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
             "sample": "%d of the %d models of one step (192x192x48, direct 3-D convolution, FP64), "
-                      "OpenMP over models, %.1f s" % (n, n_models, dt)}
+                      "OpenMP over models, %.1f s" % (n, n_models, dt),
+            "single_core": {"value": 2 / dt1, "unit": "evals/s", "cores": 1,
+                            "sample": "2 models on one thread, %.1f s" % dt1}}
 
 
 def run_reference(args):
@@ -1069,6 +1117,8 @@ def run_gbk(args):
         out["gemm"] = run_gemm(gbk, torch, dev)
     if not args.no_vfield:
         out["vfield"] = run_vfield(gbk, torch, 1024, 512, 8, dev)
+    if not args.no_ns:
+        out["nested_sampling_fp"] = run_ns_fp(gbk, torch, dev)
     if not args.no_degeneracy:
         out["degeneracy"] = run_degeneracy(gbk, torch, dev)
     if not args.no_mock:
