@@ -52,11 +52,10 @@ OPS_PER_DATA_SPAXEL = 10
 # convolution + moments) at the Fabry-Perot size: FP32 instructions per data
 # voxel, as the hot-path scope table states it.
 SURVEY_FP32_PER_DATA_VOXEL = 47.0
-# DRAM bytes (read + write) of one fused launch of 400 Fabry-Perot models at
-# the tuning (12 CTAs, 512 threads, one cluster per model), from the ncu
-# capture summarised in profiles/fused_eval_fabry_perot_400models.md.
-FUSED_TRAFFIC_400 = 744448.0
-FUSED_TRAFFIC_TUNING = (12, 512, 0)
+# DRAM bytes (read + write) of one fused launch of 400 Fabry-Perot models per
+# tuning (CTAs per model, threads, persistent), from the one-pass ncu
+# captures summarised in profiles/fused_eval_fabry_perot_400models.md.
+FUSED_TRAFFIC_400 = {(12, 512, 0): 744448.0, (12, 512, 1): 1318144.0}
 FLUSH_BYTES = 256 << 20
 
 
@@ -1045,7 +1044,7 @@ def run_gbk(args):
     peak_ops = (fma_model + mufu_model) / t_min
     achieved_ops = (fma_model + mufu_model) * n / (ms_step * 1e-3)
     tuned = (tuning["cluster_ctas"], tuning["threads"], tuning["persistent"])
-    traffic = FUSED_TRAFFIC_400 if (FUSED_TRAFFIC_400 and n == 400 and tuned == FUSED_TRAFFIC_TUNING) else None
+    traffic = FUSED_TRAFFIC_400.get(tuned) if n == 400 else None
     out["roofline"] = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                        "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
                        "traffic_note": "DRAM bytes per launch from one ncu capture at this tuning "
