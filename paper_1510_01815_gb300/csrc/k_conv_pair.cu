@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 upk2(A2, a2x, a2y);
                 upk2(A3, a3x, a3y);
                 // rows (4 rb, 4 rb + 1) -> row pair 2 rb; (4 rb + 2, 4 rb + 3) -> 2 rb + 1
+                // (8-byte stores: with P1 odd, an odd row pair starts at 2 mod 4 floats)
                 f32x2 *d0 = reinterpret_cast<f32x2 *>(Y1 + ((2 * rb) * P1 + 2 * cp) * 2);
                 f32x2 *d1 = reinterpret_cast<f32x2 *>(Y1 + ((2 * rb + 1) * P1 + 2 * cp) * 2);
                 d0[0] = pk2(a0x, a1x);
@@ -178,8 +179,11 @@ __global__ void __launch_bounds__(kPThreads, 2)
             if (tid == 0 && e + 2 < g.ez)
                 tma_load_slab(&tmap, (e & 1) ? slab1 : slab0, &bar[e & 1], tx0, ty0, zbase + e + 2, bytes);
             // ---- pass 2: x, on row pairs; 4 columns per item, into ring slot e % NR ----
+            // (the 16 lanes of a half-warp take 16 row pairs of one column block:
+            // with pitches of P1 = 32 + 2R + 1 and 33 pairs their 8-byte loads and
+            // stores fall on distinct bank pairs)
             if (tid < 16 * 8) {
-                const int p2 = tid >> 3, cb = tid & 7;
+                const int p2 = tid & 15, cb = tid >> 4;
                 f32x2 A0, A1, A2, A3;
                 pass4<R>(Y1 + (p2 * P1 + 4 * cb) * 2, 2, w2, A0, A1, A2, A3);
                 f32x2 *dst = reinterpret_cast<f32x2 *>(Xr + ((size_t)(e % NR) * 16 * kXP + p2 * kXP + 4 * cb) * 2);
