@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--no-degeneracy", action="store_true", help="skip the V_t - i degeneracy chi2 maps")
     ap.add_argument("--no-mock", action="store_true", help="skip the mock-dataset recovery study")
     ap.add_argument("--no-ns", action="store_true", help="skip nested sampling of Fabry-Perot galaxies")
+    ap.add_argument("--no-jacobian", action="store_true", help="skip the analytic Jacobian kernel timing")
     ap.add_argument("--mock-galaxies", type=int, default=1000, help="galaxies per noise level of the mock study")
     ap.add_argument("--no-gemm", action="store_true", help="skip the tensor-core GEMM measurement")
     ap.add_argument("--cnn-train", type=int, default=1048576, help="training galaxies of the CNN seed")
@@ -746,6 +747,49 @@ def run_ns_fp(gbk, torch, device, n_gal=2, n_live=400, batch=100):
             "mean_seconds_per_galaxy": float(np.mean([x["seconds"] for x in rows]))}
 
 
+def run_jacobian(gbk, torch, device, n=2048, geom=None):
+    """The analytic Jacobian kernel (gbk_jacobian: J^T J, J^T r and chi2 of
+    the eight free parameters, J not written) on n models of one geometry
+    (default the single-galaxy C1 cube), against the 1 + 8 fused
+    evaluations a forward-difference Jacobian needs for the same models."""
+    g = geom or synth.SINGLE_GEOM
+    rng = np.random.default_rng(9)
+    truth = synth.SINGLE_TRUTH.copy()
+    ps = np.array([synth.perturb(rng, truth, FIT_FREE, 0.2) for _ in range(n)])
+    m = gbk.eval_maps(g, torch.from_numpy(truth[None]), device=device)[0]
+    shape = (g.ny, g.nx)
+    wv, ws = synth.weights(shape, 5.0)
+    v = m[1] + torch.from_numpy(rng.normal(0.0, 5.0, shape).astype(np.float32)).to(device)
+    s = m[2] + torch.from_numpy(rng.normal(0.0, 5.0 * np.sqrt(2.0), shape).astype(np.float32)).to(device)
+    obs = gbk.Obs(v.contiguous(), s.contiguous(), torch.from_numpy(wv).to(device), torch.from_numpy(ws).to(device),
+                  torch.ones(shape, dtype=torch.uint8, device=device))
+    dp = torch.from_numpy(ps).to(device)
+    nf = len(FIT_FREE)
+    jtj = torch.empty((n, nf, nf), dtype=torch.float64, device=device)
+    jtv = torch.empty((n, nf), dtype=torch.float64, device=device)
+    c2 = torch.empty(n, dtype=torch.float64, device=device)
+    dfd = dp.repeat(1 + nf, 1).contiguous()
+    cfd = torch.empty(dfd.shape[0], dtype=torch.float64, device=device)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    tj = timed(lambda: gbk.gbk_jacobian(g, dp, obs, FIT_FREE, None, jtj, jtv, c2, None))
+    tf = timed(lambda: gbk.gbk_chi2(g, dfd, obs, cfd, None, gbk.PATH_FUSED, None))
+    return {"workload": "%d models of a %dx%dx%d cube, 8 free parameters" % (n, g.nx, g.ny, g.nz),
+            "jacobian_ms": tj, "fd_evals_ms": tf, "jacobian_vs_fd_evals": tj / tf,
+            "jacobians_per_s": n / (tj * 1e-3)}
+
+
 def run_degeneracy(gbk, torch, device):
     """The V_t - i degeneracy (Sec. 6.1): reduced chi-squared maps over
     (i, V_t) of C1-like mocks with V_t = 200 km/s at i = 20, 40, 60, 70 deg and
@@ -1118,6 +1162,8 @@ def run_gbk(args):
         out["vfield"] = run_vfield(gbk, torch, 1024, 512, 8, dev)
     if not args.no_ns:
         out["nested_sampling_fp"] = run_ns_fp(gbk, torch, dev)
+    if not args.no_jacobian:
+        out["jacobian"] = run_jacobian(gbk, torch, dev)
     if not args.no_degeneracy:
         out["degeneracy"] = run_degeneracy(gbk, torch, dev)
     if not args.no_mock:

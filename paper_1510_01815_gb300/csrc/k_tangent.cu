@@ -40,8 +40,9 @@ namespace gbk {
 template <int NP>
 struct TgDims {
     static constexpr int kRec = 4 + 3 * NP;  // floats per spaxel record: a, q0..q2, dq (3 per parameter)
-    static constexpr int kRec4 = (kRec + 3) / 4;
-    static constexpr int RS = kRec4 * 4;     // record stride in floats
+    // record stride in floats, odd: consecutive threads' records then start
+    // on distinct banks, so the scalar record accesses are conflict-free
+    static constexpr int RS = kRec | 1;
     static constexpr int kTri = NP * (NP + 1) / 2;
     static constexpr int kEnt = kTri + NP + 1;  // J^T J upper triangle, J^T v, sum r^2
 };
@@ -53,23 +54,25 @@ __device__ inline int tg_band_owner(int er, int ey, int cs) { return (int)((((lo
 // from copies in Q (Q holds the larger of the band's extended records and
 // the halo rows); direct = 1: it reads them in the neighbours' P through
 // distributed shared memory and Q holds the band's extended records only.
-__host__ __device__ inline size_t tangent_smem_bytes_np(const Geom &g, int band, int threads, int rec4, int direct)
+// Records are rs floats; Q and P start on 16-byte boundaries.
+__host__ __device__ inline size_t tg_align4(size_t f) { return (f + 3) & ~(size_t)3; }
+
+__host__ __device__ inline size_t tangent_smem_bytes_np(const Geom &g, int band, int threads, int rs, int direct)
 {
-    (void)threads;
     size_t q = (size_t)band * g.ex, h = direct ? 0 : (size_t)2 * g.R * g.nx;
-    size_t b = (q > h ? q : h) * rec4 * 16;               // Q records / halo rows
-    b += (size_t)band * g.nx * rec4 * 16;                 // P records
+    size_t b = tg_align4((q > h ? q : h) * rs) * 4;       // Q records / halo rows
+    b += tg_align4((size_t)band * g.nx * rs) * 4;          // P records
     b += (size_t)g.ez * 16;                               // per-channel (G0, H1, H2, -)
     b += (size_t)((2 * g.R + 1 + 3) & ~3) * 4;            // PSF taps
     b += (size_t)((band + 2 * g.R + 1) & ~1) * 8;         // y-pass row pointers
-    b += (size_t)TgDims<GBK_NPAR>::kEnt * 8 * 8;           // per-warp reduction slots
+    b += (size_t)TgDims<GBK_NPAR>::kEnt * (threads / 32) * 8;  // per-warp reduction slots
     return b;
 }
 
 // The size every launch is given: that of the widest records.
 __host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads, int direct)
 {
-    return tangent_smem_bytes_np(g, band, threads, TgDims<GBK_NPAR>::kRec4, direct);
+    return tangent_smem_bytes_np(g, band, threads, TgDims<GBK_NPAR>::RS, direct);
 }
 
 size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct)
@@ -94,10 +97,11 @@ __device__ __forceinline__ void accum_rec(const float *rec, float c, float w, fl
 }
 
 template <int NP>
-__global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
+__global__ void __launch_bounds__(kTangentThreads, 1) tangent_kernel(TangentArgs a)
 {
     constexpr int NPT = NP;
-    constexpr int kRec = TgDims<NP>::kRec, kRec4 = TgDims<NP>::kRec4, kEnt = TgDims<NP>::kEnt;
+    constexpr int kRec = TgDims<NP>::kRec, kEnt = TgDims<NP>::kEnt;
+    constexpr int RS = TgDims<NP>::RS;  // record stride (odd)
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = a.cs;
     const int rank = (int)cluster.block_rank();
@@ -115,13 +119,12 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
 
     extern __shared__ __align__(16) unsigned char smem[];
     size_t qn = (size_t)band * g.ex, hn = a.direct ? 0 : (size_t)2 * R * g.nx;
-    float *Q = reinterpret_cast<float *>(smem);                        // records, stride kRec4*4
-    float *P = Q + (qn > hn ? qn : hn) * kRec4 * 4;
-    float4 *ztab = reinterpret_cast<float4 *>(P + (size_t)band * g.nx * kRec4 * 4);
+    float *Q = reinterpret_cast<float *>(smem);                        // records, stride RS
+    float *P = Q + tg_align4((qn > hn ? qn : hn) * RS);
+    float4 *ztab = reinterpret_cast<float4 *>(P + tg_align4((size_t)band * g.nx * RS));
     float *wxy = reinterpret_cast<float *>(ztab + g.ez);
     const float **rowptr = reinterpret_cast<const float **>(wxy + ((2 * R + 1 + 3) & ~3));
-    double *wred = reinterpret_cast<double *>(rowptr + ((band + 2 * R + 1) & ~1));  // [8 warps][kEnt]
-    constexpr int RS = TgDims<NP>::RS;
+    double *wred = reinterpret_cast<double *>(rowptr + ((band + 2 * R + 1) & ~1));  // [warps][kEnt]
 
     __shared__ ModelConst mc;
     __shared__ gbk_obs s_ob;
@@ -229,13 +232,16 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
         float sh = vl - a_c;
         float base = vz0 - vl;
         float SG[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, S1[4] = {0.f, 0.f, 0.f, 0.f}, S2[3] = {0.f, 0.f, 0.f};
-        float fe = 0.f;
-        for (int e = 0; e < g.ez; ++e, fe += 1.f) {
-            float d = fmaf(fe, g.dv, base);
+        // (unrolled so that the latency chains of independent channels overlap;
+        // the powers of d form a shallow tree)
+#pragma unroll 4
+        for (int e = 0; e < g.ez; ++e) {
+            float d = fmaf((float)e, g.dv, base);
             float t = c.alpha * d;
             float gg = ex2_approx(-t * t);
             float4 T = ztab[e];
-            float g1 = gg * d, g2 = g1 * d, g3 = g2 * d, g4 = g3 * d;
+            float d2 = d * d;
+            float g1 = gg * d, g2 = gg * d2, g3 = g1 * d2, g4 = g2 * d2;
             SG[0] = fmaf(gg, T.x, SG[0]); SG[1] = fmaf(g1, T.x, SG[1]); SG[2] = fmaf(g2, T.x, SG[2]);
             SG[3] = fmaf(g3, T.x, SG[3]); SG[4] = fmaf(g4, T.x, SG[4]);
             S1[0] = fmaf(gg, T.y, S1[0]); S1[1] = fmaf(g1, T.y, S1[1]); S1[2] = fmaf(g2, T.y, S1[2]);
@@ -287,10 +293,9 @@ __global__ void __launch_bounds__(256, 1) tangent_kernel(TangentArgs a)
         int er = (k < R) ? row0 - R + k : row1 + (k - R);
         if (er < 0 || er >= g.ey) continue;
         int owner = tg_band_owner(er, g.ey, cs);
-        const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(P, owner)) +
-                            (size_t)(er - tg_band_begin(owner, g.ey, cs)) * g.nx * kRec4;
-        float4 *dst = reinterpret_cast<float4 *>(Q) + (size_t)k * g.nx * kRec4;
-        for (int i = tid; i < g.nx * kRec4; i += nthr) dst[i] = src[i];
+        const float *src = cluster.map_shared_rank(P, owner) + (size_t)(er - tg_band_begin(owner, g.ey, cs)) * g.nx * RS;
+        float *dst = Q + (size_t)k * g.nx * RS;
+        for (int i = tid; i < g.nx * RS; i += nthr) dst[i] = src[i];
     }
     __syncthreads();
 

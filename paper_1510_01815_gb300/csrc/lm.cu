@@ -17,6 +17,8 @@
 #include <cmath>
 #include <algorithm>
 #include <cstring>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "gbk_api_internal.h"
@@ -495,7 +497,8 @@ size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_geom *geoms, const gb
         lm_plan(&ofd, &pfd);
         size_t a = split_part_bytes(geoms, A, pl), b = split_part_bytes(geoms, B, pfd);
         if ((!A.empty() && a == 0) || b == 0) return 0;
-        return split_rows_bytes(std::max((int)A.size(), (int)B.size())) + std::max(a, b);
+        // the two parts run concurrently, each in its own region
+        return al256(split_rows_bytes((int)A.size()) + a) + split_rows_bytes((int)B.size()) + b;
     }
     return lm_layout_pix((size_t)sp.total_pix(), sp.n_gal, pl).total;
 }
@@ -588,13 +591,36 @@ gbk_status lm_survey(SurveyPlan &sp, const gbk_geom *geoms, const gbk_obs *obs, 
         return ok();
     }
     if (pl.tangent && !sp.tangent_ok) {
+        // The Jacobian-kernel part (A) and the finite-difference part (B) are
+        // independent batched LMs on disjoint galaxies and workspace regions;
+        // B runs in a second host thread (its own LM stream) so that the two
+        // overlap on the device, each while the other waits or polls.
         std::vector<int32_t> A, B;
         tangent_split(sp, A, B);
         gbk_lm_opts ofd = *o;
         ofd.jacobian = GBK_JAC_FD_FORWARD;
-        if ((s = fit_part(geoms, A, obs, lo, hi, params, o, chi2_out, iters_out, status_out, ws, st)) ||
-            (s = fit_part(geoms, B, obs, lo, hi, params, &ofd, chi2_out, iters_out, status_out, ws, st)))
-            return s;
+        LmPlan pfd;
+        if ((s = lm_plan(&ofd, &pfd))) return s;
+        char *wsB = ws + al256(split_rows_bytes((int)A.size()) + split_part_bytes(geoms, A, pl));
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "survey split: current device");
+        gbk_status sb = GBK_OK;
+        std::string eb;
+        std::thread tb([&]() {
+            cudaError_t ee = cudaSetDevice(dev);
+            if (ee != cudaSuccess) {
+                sb = GBK_ECUDA;
+                eb = cudaGetErrorString(ee);
+                return;
+            }
+            sb = fit_part(geoms, B, obs, lo, hi, params, &ofd, chi2_out, iters_out, status_out, wsB, st);
+            if (sb) eb = gbk_last_error();
+        });
+        gbk_status sa = fit_part(geoms, A, obs, lo, hi, params, o, chi2_out, iters_out, status_out, ws, st);
+        tb.join();
+        if (sa) return sa;
+        if (sb) return fail(sb, "survey split (finite-difference part): %s", eb.c_str());
         return ok();
     }
     EvalTarget t = {nullptr, &sp};
