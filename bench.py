@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--no-mock", action="store_true", help="skip the mock-dataset recovery study")
     ap.add_argument("--no-ns", action="store_true", help="skip nested sampling of Fabry-Perot galaxies")
     ap.add_argument("--no-jacobian", action="store_true", help="skip the analytic Jacobian kernel timing")
+    ap.add_argument("--no-grid", action="store_true", help="skip the full-size nested-grid search")
     ap.add_argument("--mock-galaxies", type=int, default=1000, help="galaxies per noise level of the mock study")
     ap.add_argument("--no-gemm", action="store_true", help="skip the tensor-core GEMM measurement")
     ap.add_argument("--cnn-train", type=int, default=1048576, help="training galaxies of the CNN seed")
@@ -790,6 +791,42 @@ def run_jacobian(gbk, torch, device, n=2048, geom=None):
             "jacobians_per_s": n / (tj * 1e-3)}
 
 
+def run_grid(gbk, torch, device):
+    """Nested grids (Sec. 2.3.3) at full size: a 64 x 64 x 64 cube, 10^5
+    nodes per level over PA, i, V_max, r_t, sigma0 (10 each), 3 levels,
+    evaluated 2^14 models per launch; x0, y0, V_sys, I0, h fixed at the
+    truth; 5 / 5 sqrt(2) km/s noise."""
+    g = synth.Geometry(64, 64, 64, 20.0, 0.0, 2.5, 30.0)
+    rng = np.random.default_rng(3)
+    truth = synth.params(31.5, 31.5, rng.uniform(0, 360), rng.uniform(20, 80), 0.0, rng.uniform(50, 300),
+                         rng.uniform(1, 8), rng.uniform(10, 80), 1.0, 8.0)
+    m = gbk.eval_maps(g, torch.from_numpy(truth[None]), device=device)[0].cpu().numpy()
+    shape = (g.ny, g.nx)
+    wv, ws = synth.weights(shape, 5.0)
+    obs = gbk.Obs.from_numpy((m[1] + rng.normal(0, 5.0, shape)).astype(np.float32),
+                             (m[2] + rng.normal(0, 5.0 * np.sqrt(2.0), shape)).astype(np.float32), wv, ws,
+                             np.ones(shape, np.uint8), device=device)
+    nodes = [1] * 10
+    lo, hi = truth.copy(), truth.copy()
+    for k, (a_, b_) in {synth.PA: (0.0, 360.0), synth.INCL: (20.0, 80.0), synth.VMAX: (50.0, 300.0),
+                        synth.RT: (1.0, 8.0), synth.SIG0: (10.0, 80.0)}.items():
+        nodes[k] = 10
+        lo[k], hi[k] = a_, b_
+    gbk.gbk_grid(g, obs, lo, hi, nodes, truth, levels=1, chunk=16384, device=device)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bp, bi, bc = gbk.gbk_grid(g, obs, lo, hi, nodes, truth, levels=3, chunk=16384, device=device)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"workload": "64x64x64 cube, 10^5 nodes per level x 3 levels (PA, i, V_max, r_t, sigma0), 2^14 models "
+                        "per launch", "seconds": dt, "nodes_per_s": 3e5 / dt,
+            "best": {synth.PARAM_NAMES[k]: float(bp[k]) for k in (synth.PA, synth.INCL, synth.VMAX, synth.RT,
+                                                                   synth.SIG0)},
+            "truth": {synth.PARAM_NAMES[k]: float(truth[k]) for k in (synth.PA, synth.INCL, synth.VMAX, synth.RT,
+                                                                      synth.SIG0)},
+            "best_chi2_per_level": [float(c) for c in bc]}
+
+
 def run_degeneracy(gbk, torch, device):
     """The V_t - i degeneracy (Sec. 6.1): reduced chi-squared maps over
     (i, V_t) of C1-like mocks with V_t = 200 km/s at i = 20, 40, 60, 70 deg and
@@ -1164,6 +1201,8 @@ def run_gbk(args):
         out["nested_sampling_fp"] = run_ns_fp(gbk, torch, dev)
     if not args.no_jacobian:
         out["jacobian"] = run_jacobian(gbk, torch, dev)
+    if not args.no_grid:
+        out["grid"] = run_grid(gbk, torch, dev)
     if not args.no_degeneracy:
         out["degeneracy"] = run_degeneracy(gbk, torch, dev)
     if not args.no_mock:

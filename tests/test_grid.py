@@ -86,3 +86,79 @@ def test_gpu_grid_argmin_matches_oracle(noise, chunk):
             break  # later levels depend on the undecided tie
     if noise == 0.0:
         assert bi[0] == TRUTH_INDEX
+
+
+# Full-size nested grid (10^5 nodes per level over PA, i, V_max, r_t, sigma0;
+# 3 levels) on a 64 x 64 x 64 cube.  The oracle cannot sweep 3 x 10^5 cubes
+# in a test, so the GPU's answer is checked by properties that hold at any
+# size: at every level the chi2 of the chosen node equals the oracle's within
+# the bound its map deviations imply, and neither 48 sampled nodes nor the
+# chosen node's axis neighbours beat it by more than that bound.
+G3 = Geometry(64, 64, 64, 20.0, 0.0, 2.5, 30.0)
+AXES3 = (2, 3, 5, 6, 7)
+
+
+def _c3_truth():
+    rng = np.random.default_rng(3)
+    return P(31.5, 31.5, rng.uniform(0, 360), rng.uniform(20, 80), 0.0, rng.uniform(50, 300),
+             rng.uniform(1, 8), rng.uniform(10, 80), 1.0, 8.0)
+
+
+def _node_params(i, box_lo, steps, fixed, nodes):
+    p = fixed.copy()
+    idx = np.unravel_index(i, [nodes[k] for k in AXES3])
+    for a, k in enumerate(AXES3):
+        p[k] = box_lo[k] + idx[a] * steps[k]
+    return p
+
+
+@pytest.mark.gpu
+def test_gpu_grid_full_size_properties():
+    import torch
+    from cases import chi2_bound
+    from paper_1510_01815_gb300 import build, gbk
+    build.build()
+    truth = _c3_truth()
+    obs = make_obs(G3, truth, seed=31, noise_v=5.0, dead=0.0)
+    nodes = [1] * 10
+    for k in AXES3:
+        nodes[k] = 10
+    lo, hi = truth.copy(), truth.copy()
+    for k, (a, b) in {2: (0.0, 360.0), 3: (20.0, 80.0), 5: (50.0, 300.0), 6: (1.0, 8.0), 7: (10.0, 80.0)}.items():
+        lo[k], hi[k] = a, b
+    dobs = gbk.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    levels = 3
+    bp, bi, bc = gbk.gbk_grid(G3, dobs, lo, hi, nodes, truth, levels=levels, chunk=16384)
+    og = ogeom(G3)
+    rng = np.random.default_rng(5)
+    clo, chi = lo.copy(), hi.copy()
+    n_nodes = 10 ** 5
+    for lev in range(levels):
+        steps = {k: (chi[k] - clo[k]) / (nodes[k] - 1) for k in AXES3}
+        best = _node_params(int(bi[lev]), clo, steps, truth, nodes)
+        gm = gbk.eval_maps(G3, torch.from_numpy(best[None]))[0].cpu().numpy()
+        ref_maps = oracle.evaluate(og, best)
+        ref_best = oracle.chi2_maps(ref_maps, obs)
+        b = chi2_bound(ref_maps, gm, obs, ref_best)
+        assert abs(bc[lev] - ref_best) <= b, (lev, bc[lev], ref_best, b)
+        # sampled nodes and the axis neighbours of the chosen node
+        picks = list(rng.choice(n_nodes, size=48, replace=False))
+        idx = np.array(np.unravel_index(int(bi[lev]), [10] * 5))
+        for a in range(5):
+            for d in (-1, 1):
+                j = idx.copy()
+                j[a] += d
+                if 0 <= j[a] < 10:
+                    picks.append(int(np.ravel_multi_index(j, [10] * 5)))
+        ps = np.array([_node_params(i, clo, steps, truth, nodes) for i in picks])
+        oc = oracle.chi2_batch(og, ps, obs)
+        assert np.all(oc >= ref_best - 2.0 * b), (lev, float(oc.min()), ref_best, b)
+        for k in AXES3:
+            clo[k] = max(lo[k], best[k] - steps[k])
+            chi[k] = min(hi[k], best[k] + steps[k])
+    # the final node recovers what the data fix: PA, and V_max sin i (V_max and
+    # i alone slide along the degeneracy valley of Sec. 6.1, which a grid
+    # refined around its first level's choice cannot leave)
+    vs, vs_t = bp[5] * np.sin(np.radians(bp[3])), truth[5] * np.sin(np.radians(truth[3]))
+    assert abs(vs - vs_t) < 0.03 * vs_t, (bp, truth)
+    assert abs(((bp[2] - truth[2] + 180) % 360) - 180) < 3.0, (bp, truth)
