@@ -263,3 +263,19 @@ def test_seed_gain_nested_sampling(G, trained):
             assert dv < 5.0 and dpa < 2.0, (j, box is lo, dv, dpa)
             acc.append(r["n_eval"])
     assert sum(n_seed) < 0.85 * sum(n_full), (n_seed, n_full)
+
+
+def test_forward_full_batch_sampled(G):
+    """The training batch size (1024 samples: 1 M rows in the first layer's
+    matrix) against the oracle on 8 sampled samples."""
+    P, v, s, mask, _ = _problem(19, 1024)
+    dP, dv, ds, dm = _dev(P.astype(np.float32), v, s, mask)
+    out = torch.empty((1024, 16), dtype=torch.float32, device="cuda")
+    ws = torch.empty(G.gbk_cnn_workspace_bytes(1024), dtype=torch.uint8, device="cuda")
+    G.gbk_cnn_forward(dP, dv, ds, dm, out, ws)
+    got = out.cpu().double().numpy()
+    pick = np.random.default_rng(3).choice(1024, size=8, replace=False)
+    ref, _ = cnn.forward(P, cnn.encode(v[pick], s[pick], mask[pick]))
+    rel = np.linalg.norm(got[pick] - ref) / np.linalg.norm(ref)
+    assert rel < 2e-2, rel
+    assert G.gbk_device_status() == 0

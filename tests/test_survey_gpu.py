@@ -278,3 +278,36 @@ def test_survey_rejects_plain_tangent_and_large(G):
         G.gbk_survey_workspace_bytes([g], G.lm_opts(jacobian=G.JAC_TANGENT, mode=G.LM_PLAIN))
     with pytest.raises(G.GbkError):
         G.gbk_survey_workspace_bytes([g, Geometry(1024, 1024, 8, 20.0, 0.0, 4.0, 30.0)])
+
+
+def test_survey_full_size_sampled(G):
+    """The 2048-galaxy survey workload through the default single persistent
+    launch: maps and chi2 of sampled galaxies (sizes the FP64 oracle
+    evaluates in seconds) against the oracle."""
+    rng = np.random.default_rng(4)
+    gal = synth.draw_survey(rng, 2048)
+    geoms = [g for g, _ in gal]
+    ps = np.array([p for _, p in gal])
+    assert G.gbk_survey_get_tuning(geoms)["persistent"] == 1
+    small = [i for i, g in enumerate(geoms) if g.nx * g.ny * g.nz <= 40 * 40 * 64]
+    pick = np.random.default_rng(8).choice(small, size=12, replace=False)
+    obs = [make_obs(geoms[i], synth.perturb(np.random.default_rng(i), ps[i], frac=0.05), seed=500 + i)
+           if i in pick else None for i in range(len(geoms))]
+    # observations for the rest: the model of the truth itself (chi2 unused)
+    dobs = []
+    for i, g in enumerate(geoms):
+        if obs[i] is not None:
+            dobs.append(_dobs(G, obs[i]))
+        else:
+            z = np.zeros((g.ny, g.nx), np.float32)
+            dobs.append(G.Obs.from_numpy(z, z, z + 1, z + 1, np.ones((g.ny, g.nx), np.uint8)))
+    maps, c2, _ = G.survey_eval(geoms, ps, dobs)
+    c2 = c2.cpu().numpy()
+    for i in pick:
+        g = geoms[i]
+        ref = oracle.evaluate(ogeom(g), ps[i])
+        m = maps[i].cpu().numpy()
+        check_maps(m[None], ref[None], ps[i:i + 1], label="survey galaxy %d" % i)
+        ref_c = oracle.chi2_maps(ref, obs[i])
+        assert abs(c2[i] - ref_c) <= chi2_bound(ref, m, obs[i], ref_c), (i, c2[i], ref_c)
+    assert G.gbk_device_status() == 0
