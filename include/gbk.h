@@ -306,8 +306,10 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
  * Jacobian; the Jacobian kernel has its own galaxy groups, since its
  * per-spaxel records are larger, and galaxies whose halo rows do not fit a
  * CTA's shared memory are fitted in the same call with finite differences,
- * which serve them faster), the plain mode fits one galaxy after the other
- * with the host solve and finite differences.
+ * which serve them faster; the survey Jacobian carries the eight derivatives
+ * x0 .. sigma0, so a fit that frees I0 or h uses finite differences for
+ * every galaxy), the plain mode fits one galaxy after the other with the
+ * host solve and finite differences.
  * ------------------------------------------------------------------------ */
 GBK_API size_t gbk_survey_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, const gbk_lm_opts *opts);
 GBK_API gbk_status gbk_survey_eval(const gbk_geom *geoms, int32_t n_gal, const double *params, const gbk_obs *obs,

@@ -15,8 +15,12 @@ extern "C" gbk_status gbk_jacobian(const gbk_geom *gin, int32_t n_models, const 
     if (free_mask == 0 || (free_mask >> GBK_NPAR)) return fail(GBK_EINVAL, "free_mask must select 1..10 parameters");
     if (g.u != 1) return fail(GBK_EUNSUPPORTED, "the Jacobian kernel needs upsample == 1");
     TangentArgs a = {};
+    a.jac = jac;
+    a.np = 0;
+    for (int k = 0; k < GBK_NPAR; ++k)
+        if (free_mask & (1u << k)) a.free_idx[a.np++] = k;
     // velocity fields: one CTA per model, no shared-memory records
-    if (g.model == GBK_MODEL_CUBE && !tangent_config(g, &a.cs, &a.band, &a.direct))
+    if (g.model == GBK_MODEL_CUBE && !tangent_config(g, &a.cs, &a.band, &a.direct, tangent_narrow(a)))
         return fail(GBK_EUNSUPPORTED, "geometry %d x %d too large for the Jacobian kernel", g.nx, g.ny);
     if (n_models == 0) return ok();
     if ((s = check_device_ptr(params, "params", 8))) return s;
@@ -30,9 +34,6 @@ extern "C" gbk_status gbk_jacobian(const gbk_geom *gin, int32_t n_models, const 
     a.n_models = n_models;
     a.params = params;
     a.obs = *obs;
-    a.np = 0;
-    for (int k = 0; k < GBK_NPAR; ++k)
-        if (free_mask & (1u << k)) a.free_idx[a.np++] = k;
     a.cot = cot;
     a.jtj = jtj;
     a.jtv = jtv;

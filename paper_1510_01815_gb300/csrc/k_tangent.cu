@@ -69,15 +69,15 @@ __host__ __device__ inline size_t tangent_smem_bytes_np(const Geom &g, int band,
     return b;
 }
 
-// The size every launch is given: that of the widest records.
-__host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads, int direct)
+// The size of a launch carrying eight (narrow) or ten derivatives.
+__host__ __device__ inline size_t tangent_smem_bytes(const Geom &g, int band, int threads, int direct, bool narrow)
 {
-    return tangent_smem_bytes_np(g, band, threads, TgDims<GBK_NPAR>::RS, direct);
+    return tangent_smem_bytes_np(g, band, threads, narrow ? TgDims<GBK_I0>::RS : TgDims<GBK_NPAR>::RS, direct);
 }
 
-size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct)
+size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct, bool narrow)
 {
-    return tangent_smem_bytes(g, band, threads, direct);
+    return tangent_smem_bytes(g, band, threads, direct, narrow);
 }
 
 // Re-centres the record at rec (centre stored as rec[0] = a) to centre c
@@ -96,8 +96,11 @@ __device__ __forceinline__ void accum_rec(const float *rec, float c, float w, fl
     }
 }
 
+// The eight-derivative build fits 128 registers without spills, so two
+// CTAs share an SM when their shared memory allows; the ten-derivative
+// build keeps one.
 template <int NP>
-__global__ void __launch_bounds__(kTangentThreads, 1) tangent_kernel(TangentArgs a)
+__global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent_kernel(TangentArgs a)
 {
     constexpr int NPT = NP;
     constexpr int kRec = TgDims<NP>::kRec, kEnt = TgDims<NP>::kEnt;
@@ -460,30 +463,41 @@ gbk_status launch_tangent(const TangentArgs &args, cudaStream_t stream)
     if (!args.geoms && args.g.model != GBK_MODEL_CUBE) return launch_vfield_tangent(args, stream);
     if (args.geoms && args.jac) return fail(GBK_EINVAL, "ragged tangent launches do not write J");
     if (args.np < 1 || args.np > GBK_NPAR) return fail(GBK_EINVAL, "tangent launch: bad free-parameter count");
-    size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads, args.direct);
     // carry only x0 .. sigma0 when I0 and h are fixed and J is not written
-    bool narrow = !args.jac;
-    for (int k = 0; k < args.np; ++k) narrow = narrow && args.free_idx[k] < GBK_I0;
+    const bool narrow = tangent_narrow(args);
+    if (args.geoms && !narrow)
+        return fail(GBK_EUNSUPPORTED, "ragged Jacobian launches carry the eight parameters x0 .. sigma0");
+    size_t smem = args.geoms ? args.smem : tangent_smem_bytes(args.g, args.band, kTangentThreads, args.direct, narrow);
     return narrow ? launch_np<GBK_I0>(args, smem, stream) : launch_np<GBK_NPAR>(args, smem, stream);
+}
+
+bool tangent_narrow(const TangentArgs &a)
+{
+    bool narrow = !a.jac;
+    for (int k = 0; k < a.np; ++k) narrow = narrow && a.free_idx[k] < GBK_I0;
+    return narrow;
 }
 
 int tangent_cluster_for(const Geom &g)
 {
     int cs, band, direct;
-    return tangent_config(g, &cs, &band, &direct) ? cs + 32 * direct : 0;
+    return tangent_config(g, &cs, &band, &direct, true) ? cs + 32 * direct : 0;
 }
 
-// Halo copies while they fit (200 KB per CTA); otherwise direct reads of the
-// neighbours' records, up to 220 KB per CTA.  The smallest cluster first.
-bool tangent_config(const Geom &g, int *cs, int *band, int *direct)
+// Halo copies while they fit -- first two CTAs per SM (narrow launches: 110 KB
+// per CTA), then one (200 KB) -- otherwise direct reads of the neighbours'
+// records, up to 220 KB per CTA.  The smallest cluster of the first shape
+// that fits.
+bool tangent_config(const Geom &g, int *cs, int *band, int *direct, bool narrow)
 {
     if (g.u != 1) return false;
-    for (int d = 0; d < 2; ++d) {
-        const size_t cap = d == 0 ? (size_t)200 * 1024 : (size_t)220 * 1024;
+    const size_t caps[3] = {(size_t)110 * 1024, (size_t)200 * 1024, (size_t)220 * 1024};
+    for (int pass = narrow ? 0 : 1; pass < 3; ++pass) {
+        const int d = pass == 2 ? 1 : 0;
         for (int c = 1; c <= 16; ++c) {
             int b = (g.ey + c - 1) / c;
             if (c > g.ey) break;
-            if (tangent_smem_bytes(g, b, kTangentThreads, d) <= cap) {
+            if (tangent_smem_bytes(g, b, kTangentThreads, d, narrow) <= caps[pass]) {
                 *cs = c;
                 *band = b;
                 *direct = d;

@@ -31,10 +31,13 @@ struct TangentArgs {
     size_t smem;             // dynamic shared memory (ragged: the largest need)
 };
 
-size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct);
-bool tangent_config(const Geom &g, int *cs, int *band, int *direct);
-// Launch shape of a galaxy as one key: cluster size + 32 * direct (0: no
-// shape fits).
+size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct, bool narrow);
+// Launch shape for the eight-derivative (narrow) or the ten-derivative build.
+bool tangent_config(const Geom &g, int *cs, int *band, int *direct, bool narrow);
+// Whether a launch carries only x0 .. sigma0 (I0 and h fixed, J not written).
+bool tangent_narrow(const TangentArgs &a);
+// Launch shape of a galaxy for the narrow build as one key: cluster size +
+// 32 * direct (0: no shape fits).
 int tangent_cluster_for(const Geom &g);
 inline int tangent_key_cs(int key) { return key & 31; }
 inline int tangent_key_direct(int key) { return key >> 5; }

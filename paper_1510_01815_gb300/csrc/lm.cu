@@ -387,12 +387,14 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     lm_launch_init(a, o->lambda0, st);
     TangentArgs ta = {};
     if (pl.tangent) {
+        ta.np = pl.np;
+        for (int j = 0; j < pl.np; ++j) ta.free_idx[j] = pl.idx[j];
         if (t.sp) {
-            if (!t.sp->tangent_ok)
+            if (!t.sp->tangent_ok || !tangent_narrow(ta))
                 return fail(GBK_EUNSUPPORTED, "a galaxy of the batch is too large for the Jacobian kernel");
         } else {
             const Geom &g = *t.g;
-            if (g.model == GBK_MODEL_CUBE && !tangent_config(g, &ta.cs, &ta.band, &ta.direct))
+            if (g.model == GBK_MODEL_CUBE && !tangent_config(g, &ta.cs, &ta.band, &ta.direct, tangent_narrow(ta)))
                 return fail(GBK_EUNSUPPORTED, "geometry too large for the tangent Jacobian kernel");
             ta.g = g;
         }
@@ -401,8 +403,6 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
         ta.obs_list = obs;
         ta.models_per_gal = 1;
         ta.skip = a.done;
-        ta.np = pl.np;
-        for (int j = 0; j < pl.np; ++j) ta.free_idx[j] = pl.idx[j];
         ta.jtj = a.jtj;
         ta.jtv = a.jtr;
         // chi2 at the start point from the fused kernel: accept/reject
@@ -443,6 +443,15 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
         (e = cudaStreamSynchronize(st)))
         return cuda_fail(e, "LM: results");
     return ok();
+}
+
+// Whether the plan's free parameters are all among x0 .. sigma0 (the
+// eight-derivative build of the Jacobian kernel serves them).
+static bool lm_plan_narrow(const LmPlan &pl)
+{
+    for (int j = 0; j < pl.np; ++j)
+        if (pl.idx[j] >= GBK_I0) return false;
+    return true;
 }
 
 // Survey batches: the batched mode over a ragged plan, or the plain mode one
@@ -486,6 +495,13 @@ size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_geom *geoms, const gb
         size_t m = 256;
         for (const Geom &g : sp.geo) m = std::max(m, lm_layout(g, 1, pl).total);
         return m;
+    }
+    if (pl.tangent && !lm_plan_narrow(pl)) {
+        // survey batches carry the eight derivatives x0 .. sigma0; fits that
+        // free I0 or h use finite differences throughout
+        gbk_lm_opts ofd = *o;
+        ofd.jacobian = GBK_JAC_FD_FORWARD;
+        return lm_survey_workspace(sp, geoms, &ofd);
     }
     if (pl.tangent && !sp.tangent_ok) {
         // split: the Jacobian kernel where it fits, finite differences elsewhere
@@ -589,6 +605,11 @@ gbk_status lm_survey(SurveyPlan &sp, const gbk_geom *geoms, const gbk_obs *obs, 
             if (s) return s;
         }
         return ok();
+    }
+    if (pl.tangent && !lm_plan_narrow(pl)) {
+        gbk_lm_opts ofd = *o;
+        ofd.jacobian = GBK_JAC_FD_FORWARD;
+        return lm_survey(sp, geoms, obs, lo, hi, params, &ofd, chi2_out, iters_out, status_out, ws, ws_bytes, st);
     }
     if (pl.tangent && !sp.tangent_ok) {
         // The Jacobian-kernel part (A) and the finite-difference part (B) are

@@ -239,7 +239,7 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp, const S
         for (int j = k; j < e; ++j) {
             const Geom &g = sp->geo[sp->torder[j]];
             c.smem = std::max(c.smem,
-                              tangent_smem_bytes_host(g, (g.ey + c.cs - 1) / c.cs, kTangentThreads, c.direct));
+                              tangent_smem_bytes_host(g, (g.ey + c.cs - 1) / c.cs, kTangentThreads, c.direct, true));
         }
         sp->tclasses.push_back(c);
         k = e;
