@@ -62,7 +62,7 @@ __host__ __device__ inline size_t tangent_smem_bytes_np(const Geom &g, int band,
     size_t q = (size_t)band * g.ex, h = direct ? 0 : (size_t)2 * g.R * g.nx;
     size_t b = tg_align4((q > h ? q : h) * rs) * 4;       // Q records / halo rows
     b += tg_align4((size_t)band * g.nx * rs) * 4;          // P records
-    b += (size_t)g.ez * 16;                               // per-channel (G0, H1, H2, -)
+    b += (size_t)(g.ez + 2) * 16;                         // per-channel G0, H1, H2 (three padded arrays)
     b += (size_t)((2 * g.R + 1 + 3) & ~3) * 4;            // PSF taps
     b += (size_t)((band + 2 * g.R + 1) & ~1) * 8;         // y-pass row pointers
     b += (size_t)TgDims<GBK_NPAR>::kEnt * (threads / 32) * 8;  // per-warp reduction slots
@@ -124,8 +124,12 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
     size_t qn = (size_t)band * g.ex, hn = a.direct ? 0 : (size_t)2 * R * g.nx;
     float *Q = reinterpret_cast<float *>(smem);                        // records, stride RS
     float *P = Q + tg_align4((qn > hn ? qn : hn) * RS);
-    float4 *ztab = reinterpret_cast<float4 *>(P + tg_align4((size_t)band * g.nx * RS));
-    float *wxy = reinterpret_cast<float *>(ztab + g.ez);
+    // per-channel LSF tap moments, three arrays of ezp (even) floats so that
+    // (channel e, e + 1) pairs load as one aligned 8-byte word
+    const int ezp = (g.ez + 1) & ~1;
+    float *tzx = P + tg_align4((size_t)band * g.nx * RS);
+    float *tzy = tzx + ezp, *tzz = tzy + ezp;
+    float *wxy = tzx + ((3 * ezp + 3) & ~3);
     const float **rowptr = reinterpret_cast<const float **>(wxy + ((2 * R + 1 + 3) & ~3));
     double *wred = reinterpret_cast<double *>(rowptr + ((band + 2 * R + 1) & ~1));  // [warps][kEnt]
 
@@ -155,7 +159,10 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
             H1 = fmaf(w, (float)j, H1);
             H2 = fmaf(w, (float)(j * j), H2);
         }
-        ztab[e] = make_float4(G0, g.dv * H1, g.dv * g.dv * H2, 0.f);
+        tzx[e] = G0;
+        tzy[e] = g.dv * H1;
+        tzz[e] = g.dv * g.dv * H2;
+        if (e + 1 == g.ez && g.ez < ezp) tzx[e + 1] = tzy[e + 1] = tzz[e + 1] = 0.f;  // pad of an odd ez
     }
     // first record of extended row row0 - R + k for the y pass: own rows in
     // P; halo rows in their copies in Q, or (direct) in the owner's P
@@ -234,22 +241,40 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
         float a_c = fminf(fmaxf(vl, v_lo), v_hi);
         float sh = vl - a_c;
         float base = vz0 - vl;
-        float SG[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, S1[4] = {0.f, 0.f, 0.f, 0.f}, S2[3] = {0.f, 0.f, 0.f};
-        // (unrolled so that the latency chains of independent channels overlap;
-        // the powers of d form a shallow tree)
-#pragma unroll 4
-        for (int e = 0; e < g.ez; ++e) {
-            float d = fmaf((float)e, g.dv, base);
-            float t = c.alpha * d;
-            float gg = ex2_approx(-t * t);
-            float4 T = ztab[e];
-            float d2 = d * d;
-            float g1 = gg * d, g2 = gg * d2, g3 = g1 * d2, g4 = g2 * d2;
-            SG[0] = fmaf(gg, T.x, SG[0]); SG[1] = fmaf(g1, T.x, SG[1]); SG[2] = fmaf(g2, T.x, SG[2]);
-            SG[3] = fmaf(g3, T.x, SG[3]); SG[4] = fmaf(g4, T.x, SG[4]);
-            S1[0] = fmaf(gg, T.y, S1[0]); S1[1] = fmaf(g1, T.y, S1[1]); S1[2] = fmaf(g2, T.y, S1[2]);
-            S1[3] = fmaf(g3, T.y, S1[3]);
-            S2[0] = fmaf(gg, T.z, S2[0]); S2[1] = fmaf(g1, T.z, S2[1]); S2[2] = fmaf(g2, T.z, S2[2]);
+        // Channels in pairs (e, e + 1) on packed FP32 lanes: per pair one
+        // argument, two ex2, the powers of d as a shallow tree and twelve
+        // packed accumulations; an odd last channel pairs with the padding,
+        // whose tap moments are 0.  The two lanes are added at the end.
+        float SG[5], S1[4], S2[3];
+        {
+            const f32x2 Z2 = pk2(0.f, 0.f), AL = pk2(c.alpha, c.alpha), DV = pk2(g.dv, g.dv);
+            const f32x2 BASE = pk2(base, base), TWO = pk2(2.f, 2.f);
+            f32x2 A0 = Z2, A1 = Z2, A2 = Z2, A3 = Z2, A4 = Z2, B0 = Z2, B1 = Z2, B2 = Z2, B3 = Z2, C0 = Z2, C1 = Z2,
+                  C2 = Z2;
+            f32x2 FE = pk2(0.f, 1.f);
+#pragma unroll 2
+            for (int e = 0; e < ezp; e += 2) {
+                const f32x2 D = fma2(FE, DV, BASE);
+                const f32x2 T = mul2(D, AL);
+                const f32x2 W = mul2(T, T);
+                float w0, w1;
+                upk2(W, w0, w1);
+                const f32x2 G0 = pk2(ex2_approx(-w0), ex2_approx(-w1));
+                const f32x2 D2 = mul2(D, D);
+                const f32x2 G1 = mul2(G0, D), G2 = mul2(G0, D2);
+                const f32x2 G3 = mul2(G1, D2), G4 = mul2(G2, D2);
+                const f32x2 TX = *reinterpret_cast<const f32x2 *>(tzx + e);
+                const f32x2 TY = *reinterpret_cast<const f32x2 *>(tzy + e);
+                const f32x2 TZ = *reinterpret_cast<const f32x2 *>(tzz + e);
+                A0 = fma2(G0, TX, A0); A1 = fma2(G1, TX, A1); A2 = fma2(G2, TX, A2);
+                A3 = fma2(G3, TX, A3); A4 = fma2(G4, TX, A4);
+                B0 = fma2(G0, TY, B0); B1 = fma2(G1, TY, B1); B2 = fma2(G2, TY, B2); B3 = fma2(G3, TY, B3);
+                C0 = fma2(G0, TZ, C0); C1 = fma2(G1, TZ, C1); C2 = fma2(G2, TZ, C2);
+                FE = add2(FE, TWO);
+            }
+            SG[0] = hsum2(A0); SG[1] = hsum2(A1); SG[2] = hsum2(A2); SG[3] = hsum2(A3); SG[4] = hsum2(A4);
+            S1[0] = hsum2(B0); S1[1] = hsum2(B1); S1[2] = hsum2(B2); S1[3] = hsum2(B3);
+            S2[0] = hsum2(C0); S2[1] = hsum2(C1); S2[2] = hsum2(C2);
         }
         // B_km (k: power of d from the derivative; m: moment weight about a)
         float B[3][3];
