@@ -355,22 +355,31 @@ gbk_status launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, cons
     return GBK_OK;
 }
 
-__global__ void splitk_reduce_kernel(const float *part, int splits, size_t stride, int M, int N, int ldo, float *out)
+// Sum of the split-K slices: a block takes 32 consecutive outputs (one per
+// lane: coalesced loads) and its 8 warps the slices z = w, w + 8, ... in
+// increasing order; the 8 partial sums are added in a fixed tree, so the
+// result does not depend on timing.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(32 * kRedWarps) splitk_reduce_kernel(const float *part, int splits, size_t stride,
+                                                                     int M, int N, int ldo, float *out)
 {
+    __shared__ float red[kRedWarps][32];
     const size_t total = (size_t)M * N;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t m = i / N, n = i - m * N, o = m * ldo + n;
-        // four independent partial sums (slices z = 4k + j), added in a fixed order
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int z = 0;
-        for (; z + 4 <= splits; z += 4) {
-            s0 += part[(size_t)z * stride + o];
-            s1 += part[(size_t)(z + 1) * stride + o];
-            s2 += part[(size_t)(z + 2) * stride + o];
-            s3 += part[(size_t)(z + 3) * stride + o];
-        }
-        for (; z < splits; ++z) s0 += part[(size_t)z * stride + o];
-        out[o] = (s0 + s1) + (s2 + s3);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (size_t base = (size_t)blockIdx.x * 32; base < total; base += (size_t)gridDim.x * 32) {
+        const size_t i = base + lane;
+        const bool ok = i < total;
+        const size_t m = ok ? i / N : 0, o = ok ? m * ldo + (i - m * N) : 0;
+        float s = 0.f;
+        if (ok)
+            for (int z = w; z < splits; z += kRedWarps) s += part[(size_t)z * stride + o];
+        red[w][lane] = s;
+        __syncthreads();
+        if (w == 0 && ok)
+            out[o] = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                     ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+        __syncthreads();
     }
 }
 
@@ -378,8 +387,8 @@ gbk_status launch_splitk_reduce(const float *part, int splits, size_t stride, in
                                 cudaStream_t st)
 {
     size_t total = (size_t)M * N;
-    int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
-    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, splits, stride, M, N, ldo, out);
+    int blocks = (int)std::min<size_t>((total + 31) / 32, 152 * 16);
+    splitk_reduce_kernel<<<blocks, 32 * kRedWarps, 0, st>>>(part, splits, stride, M, N, ldo, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "split-K reduction launch");
     return GBK_OK;
