@@ -1197,6 +1197,11 @@ def run_gbk(args):
     out["e2e"]["matches_device_run"] = bool(ok)
     out["gpu_launches_e2e"] = K
 
+    # The single-GPU measurements below describe one GPU; a multi-GPU run
+    # (weak scaling of the headline) skips them.
+    if ws > 1:
+        args.no_fits = args.no_survey = args.no_gemm = args.no_vfield = args.no_ns = True
+        args.no_jacobian = args.no_grid = args.no_degeneracy = args.no_mock = args.no_cnn = True
     if not args.no_fits:
         out["fits"] = run_fits(gbk, torch, args.fit_galaxies, dev,
                                [("plain_fd", gbk.LM_PLAIN, gbk.JAC_FD_FORWARD),
