@@ -367,10 +367,11 @@ def cnn_flops_per_sample():
     return f
 
 
-def cnn_data(gbk, torch, n, seed, device, chunk=65536):
+def cnn_data(gbk, torch, n, seed, device, chunk=65536, continuum=False):
     """n synthetic galaxies of the CNN workload: parameters from the prior,
     maps from the library (64 x 64 x 64 cubes), observations with 5 km/s
-    noise and 2 % dead fibres from the library's counter-based streams."""
+    noise and 2 % dead fibres from the library's counter-based streams (and,
+    on request, the continuum maps m0)."""
     rng = np.random.default_rng(seed)
     p = synth.draw_cnn_params(rng, n)
     dp = torch.from_numpy(p).to(device)
@@ -378,13 +379,16 @@ def cnn_data(gbk, torch, n, seed, device, chunk=65536):
     s = torch.empty_like(v)
     m = torch.empty((n, 64, 64), dtype=torch.uint8, device=device)
     t = torch.empty((n, 10), dtype=torch.float32, device=device)
+    c = torch.empty_like(v) if continuum else None
     for i in range(0, n, chunk):
         j = min(n, i + chunk)
         maps = gbk.eval_maps(synth.CNN_GEOM, dp[i:j], device=device)
         gbk.gbk_cnn_synth_obs(maps, seed * 1000003 + i, 5.0, 0.02, v[i:j], s[i:j], m[i:j])
+        if continuum:
+            c[i:j] = maps[:, 0]
         del maps
     gbk.gbk_cnn_targets(dp, t)
-    return p, v, s, m, t
+    return (p, v, s, m, t, c) if continuum else (p, v, s, m, t)
 
 
 def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device, n_ns=8):
@@ -430,7 +434,7 @@ def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device, n_ns=8)
                             "launch sequence; flops count the GEMMs only; peak = measured cuBLAS bf16 sustained"}
     del v, s, m, t
     # held-out galaxies (seed 5)
-    ptest, vt, st, mt, _ = cnn_data(gbk, torch, n_test, 5, device)
+    ptest, vt, st, mt, _, ct = cnn_data(gbk, torch, n_test, 5, device, continuum=True)
     torch.cuda.synchronize()
     a.record()
     pred = net.predict(vt, st, mt)
@@ -458,6 +462,11 @@ def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device, n_ns=8)
     seed_p[:, synth.I0], seed_p[:, synth.H] = ptest[:, synth.I0], ptest[:, synth.H]
     rng = np.random.default_rng(55)
     pert = np.array([synth.perturb(rng, ptest[i], FIT_FREE, 0.2, lo[i], hi[i]) for i in range(n_test)])
+    # the paper's own starting point (Sec. 2.1.9), measured on the maps
+    obs_dev, _keep = gbk.obs_array(obs, device)
+    heur = torch.empty((n_test, synth.NPAR), dtype=torch.float64, device=device)
+    gbk.gbk_initial_guess(g, obs_dev, torch.from_numpy(ptest).to(device), heur, ct)
+    heur = np.clip(heur.cpu().numpy(), lo, hi)
 
     def err(q, tr):
         dv = np.abs(q[:, synth.VMAX] - tr[:, synth.VMAX])
@@ -467,7 +476,12 @@ def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device, n_ns=8)
     dv0, dpa0 = err(seed_p, ptest)
     out["seed_error"] = {"median_dvmax": float(np.median(dv0)), "median_dpa": float(np.median(dpa0)),
                          "p90_dvmax": float(np.percentile(dv0, 90)), "p90_dpa": float(np.percentile(dpa0, 90))}
+    dvh, dpah = err(heur, ptest)
+    out["heuristic_start_error"] = {"median_dvmax": float(np.median(dvh)), "median_dpa": float(np.median(dpah)),
+                                    "p90_dvmax": float(np.percentile(dvh, 90)),
+                                    "p90_dpa": float(np.percentile(dpah, 90))}
     for name, mode, start, sub in (("batched_cnn_seed", gbk.LM_BATCHED, seed_p, n_test),
+                                   ("batched_heuristic", gbk.LM_BATCHED, heur, n_test),
                                    ("batched_perturbed", gbk.LM_BATCHED, pert, n_test),
                                    ("plain_perturbed", gbk.LM_PLAIN, pert, n_plain)):
         opts = gbk.lm_opts(max_iter=200, jacobian=gbk.JAC_FD_FORWARD, mode=mode, free=FIT_FREE)

@@ -278,6 +278,35 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
                               void *stream);
 
 /* ------------------------------------------------------------------------
+ * Initial model parameter values (Sec. 2.1.9), measured on each galaxy's
+ * maps -- the optimisers' starting point when no better one (e.g. the CNN
+ * seed below) is at hand:
+ *   x0, y0  intensity-weighted mean position of the continuum map (negative
+ *           values count as 0; no light: the image centre);
+ *   V_sys   mean velocity of the unmasked pixels within 2.5 pixels of that
+ *           centre (none that close: of all unmasked pixels; none: 0);
+ *   PA      the whole degree whose split of the velocity field into the
+ *           halves x_e > 0 and x_e < 0 (Eqs. 1-2) maximises the difference
+ *           of their mean velocities, pixels binned by whole degrees of
+ *           polar angle about the centre (ties to the smaller PA);
+ *   i       from the continuum's intensity-weighted second central moments:
+ *           their eigenvalues less the PSF variance have the ratio cos^2 i
+ *           (the paper uses a catalogue inclination); clipped to [5, 85];
+ *   r_t     h for the cube model (the photometric scale length), the
+ *           caller's value for velocity fields;
+ *   V_t = 150 km/s, sigma0 = 30 km/s; a = g = 1 for the Epinat curve; every
+ *   other slot (I0, h) is copied from `fixed`.
+ *  continuum  device [n_gal][ny][nx] FP32 continuum (intensity) maps, or
+ *             NULL: the unmasked pixels then weigh 1 each
+ *  obs        device [n_gal] gbk_obs (v_obs and mask are read)
+ *  fixed      device [n_gal][GBK_NPAR] (I0 and h, or r_t, as above)
+ *  params_out device [n_gal][GBK_NPAR]
+ * Asynchronous; FP64 arithmetic, deterministic; GBK_EINVAL on bad arguments
+ * and for maps above 2^26 pixels. */
+GBK_API gbk_status gbk_initial_guess(const gbk_geom *g, int32_t n_gal, const float *continuum, const gbk_obs *obs,
+                                     const double *fixed, double *params_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Survey batches: galaxies of different geometry (cube size, channel width,
  * LSF, PSF) evaluated or fitted together -- the survey-scale setting of
  * Sec. 1 and Sec. 5, with the model of Sec. 2.1-2.2 and the optimiser of

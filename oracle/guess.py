@@ -24,8 +24,9 @@ open, which are read as follows:
     intensity-weighted second central moments, less the PSF variance (the
     moments of a convolution with a Gaussian add), give cos^2 i as their
     ratio; i is clipped to [INCL_MIN, INCL_MAX];
-  - r_t: the photometric scale radius, i.e. the scale length h, which is
-    known and fixed (as is I0);
+  - r_t: the photometric scale radius: for the cube model the scale length
+    h, which is known and fixed (as is I0); for a velocity field (no
+    intensity model) the caller's value in the r_t slot;
   - V_t = 150 km/s, sigma0 = 30 km/s; for the Epinat curve a = g = 1.
 """
 import math
@@ -110,8 +111,8 @@ def position_angle(v, mask, x0, y0):
 
 def initial_guess(cont, v, mask, fixed, psf_sigma, model=0):
     """Parameter vector of Sec. 2.1.9 for one galaxy; `fixed` supplies I0 and
-    h (cube model) -- the Epinat slopes, in those slots for a velocity field,
-    are set to 1."""
+    h (cube model, r_t := h) or r_t (velocity fields); the Epinat slopes, in
+    the I0 and h slots of a velocity field, are set to 1."""
     p = np.array(fixed, dtype=np.float64, copy=True)
     x0, y0, _ = centroid(cont)
     p[X0], p[Y0] = x0, y0
@@ -120,9 +121,8 @@ def initial_guess(cont, v, mask, fixed, psf_sigma, model=0):
     p[INCL] = photometric_inclination(cont, x0, y0, psf_sigma)
     p[VMAX] = VT0
     p[SIG] = SIG0
+    if model == 0:
+        p[RT] = float(fixed[H])
     if model == 2:
         p[I0] = p[H] = 1.0
-        p[RT] = float(fixed[RT])
-    else:
-        p[RT] = float(fixed[H])
     return p

@@ -98,6 +98,7 @@ def lib():
             "gbk_survey_eval": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "gbk_survey_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz,
                                         vp]),
+            "gbk_initial_guess": (i32, [gp, i32, vp, vp, vp, vp, vp]),
             "gbk_survey_autotune": (i32, [gp, i32, vp, vp, vp, vp, sz, ctypes.POINTER(CTuning), vp]),
             "gbk_survey_get_tuning": (i32, [gp, i32, ctypes.POINTER(CTuning)]),
             "gbk_survey_set_tuning": (i32, [gp, i32, ctypes.POINTER(CTuning)]),
@@ -129,7 +130,7 @@ def exported_symbols():
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
-            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_survey_autotune", "gbk_survey_get_tuning",
+            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_initial_guess", "gbk_survey_autotune", "gbk_survey_get_tuning",
             "gbk_survey_set_tuning", "gbk_device_status", "gbk_gemm_bf16", "gbk_cnn_param_count",
             "gbk_cnn_workspace_bytes", "gbk_cnn_init", "gbk_cnn_targets", "gbk_cnn_decode", "gbk_cnn_synth_obs",
             "gbk_cnn_forward", "gbk_cnn_grad", "gbk_cnn_train_step",
@@ -666,6 +667,31 @@ def gbk_nested_sample(geom, obs, lo, hi, n_live=400, batch=None, tol=0.5, efr=1.
                                    _stream(stream)))
     return {"mean": np.array(mean[:]), "std": np.array(std[:]), "log_z": lz.value, "n_eval": ne.value,
             "n_iter": ni.value}
+
+
+def gbk_initial_guess(geom, obs_dev, fixed, params_out, continuum=None, stream=None):
+    """Initial parameter values (Sec. 2.1.9) of n galaxies sharing `geom`:
+    obs_dev a device array of gbk_obs (obs_array), fixed / params_out
+    [n][NPAR] FP64 device tensors, continuum [n][ny][nx] FP32 or None."""
+    g = cgeom(geom)
+    n = params_out.shape[0]
+    _check(lib().gbk_initial_guess(ctypes.byref(g), int(n), _ptr(continuum, torch.float32, "continuum"),
+                                   _ptr(obs_dev, torch.uint8, "obs"), _ptr(fixed, torch.float64, "fixed"),
+                                   _ptr(params_out, torch.float64, "params_out"), _stream(stream)))
+
+
+def initial_guess(geom, obs_list, fixed, continuum=None, device="cuda", stream=None):
+    """Convenience: initial parameter values as a numpy array [n][NPAR]."""
+    import numpy as np
+    n = len(obs_list)
+    obs_dev, _keep = obs_array(obs_list, device)
+    f = torch.as_tensor(np.ascontiguousarray(fixed, dtype=np.float64).reshape(n, NPAR)).to(device)
+    out = torch.empty((n, NPAR), dtype=torch.float64, device=device)
+    c = None
+    if continuum is not None:
+        c = torch.as_tensor(continuum, dtype=torch.float32).reshape(n, geom.ny, geom.nx).to(device).contiguous()
+    gbk_initial_guess(geom, obs_dev, f, out, c, stream)
+    return out.cpu().numpy()
 
 
 def gbk_device_status():
