@@ -54,6 +54,14 @@ namespace gbk {
 
 __host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
 
+// Line-sampling window: channels with |u| = alpha |v_e - v_los| > kUCut
+// (beyond 7.06 sigma) are left out.  There 2^(-u^2) < 2^-36 of the line's
+// peak, and the terms fall off geometrically beyond, so the dropped tails
+// change the line's three sums by under 1e-9 of their values -- far below
+// the FP32 resolution of the sums (6e-8).  The one-channel margin of the
+// window keeps the channel nearest the line centre in it for any width.
+constexpr float kUCut = 6.0f;
+
 // Extended rows [band_begin(r), band_begin(r+1)) belong to cluster rank r.
 __host__ __device__ inline int band_begin(int rank, int ey, int cs) { return (int)(((long)rank * ey) / cs); }
 
@@ -368,11 +376,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
         const unsigned am = __activemask();
         if (!__any_sync(am, sh != 0.f)) {
             // m = u: the Gaussian argument is also the moment variable.
-            // Where |u| > 11.25, ex2(-u^2) is below 2^-126 and flushes to +0,
-            // so those channels add exact zeros: the warp runs only the union
-            // of its lanes' windows |u| <= 11.25 (one channel of margin each
-            // side), starting at an even offset to keep the pairing.
-            float flo = (-11.25f - ub) * inv_adv - 1.f, fhi = (11.25f - ub) * inv_adv + 1.f;
+            // The warp runs only the union of its lanes' windows |u| <= kUCut
+            // (one channel of margin each side), starting at an even offset
+            // to keep the pairing.
+            float flo = (-kUCut - ub) * inv_adv - 1.f, fhi = (kUCut - ub) * inv_adv + 1.f;
             if (!(flo > -1e6f)) flo = -1e6f;
             if (!(fhi < 1e6f)) fhi = 1e6f;
             const int wlo = __reduce_min_sync(am, (int)floorf(flo));
@@ -422,10 +429,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             int eb = blk ? ehi : 0, ee = blk ? g.ez : elo;
             if (eb >= ee) continue;
             {
-                // the block adds exact zeros when every lane's |u| > 11.25 over
+                // the block is passed over when every lane's |u| > kUCut over
                 // all of it (u is monotone in the channel: test the ends)
                 const float ua = fmaf((float)eb, adv, ub), uz = fmaf((float)(ee - 1), adv, ub);
-                const bool zero = (ua > 11.25f && uz > 11.25f) || (ua < -11.25f && uz < -11.25f);
+                const bool zero = (ua > kUCut && uz > kUCut) || (ua < -kUCut && uz < -kUCut);
                 if (__all_sync(am, zero)) continue;
             }
             const int toff = blk ? hi_off - ehi : 0;  // table slot = e + toff
