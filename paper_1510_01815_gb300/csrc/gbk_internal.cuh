@@ -13,6 +13,19 @@ namespace gbk {
 
 constexpr double kFwhmPerSigma = 2.3548200450309493;  // 2 sqrt(2 ln 2)
 constexpr float kInvalidFraction = 1e-20f;            // m0 <= this * I0: invalid spectrum
+
+// Line-sampling window of the fused evaluator, in u =
+// alpha (v_e - v_los), the Gaussian being 2^(-u^2).  For a line centred in
+// the band, channels with |u| > kUCut (beyond 7.06 sigma, below 2^-36 of the
+// peak) are left out: the terms fall off geometrically beyond, so the dropped
+// tails change the spectrum's sums by under 1e-9 of their values, far below
+// their FP32 resolution (6e-8); a one-channel margin keeps the channel
+// nearest the centre in the window for any width.  A line centred outside
+// the band keeps every channel whose Gaussian is not an exact FP32 zero
+// (|u| <= kUFlush): its in-band tail may be all the spaxel has, and whether
+// that is above the invalid-spectrum threshold must not change.
+constexpr float kUCut = 6.0f;
+constexpr float kUFlush = 11.25f;  // beyond it ex2(-u^2) < 2^-126 flushes to +0
 constexpr int kMaxRadius = 64;                        // largest kernel radius served
 
 // Geometry after host-side derivation of kernel radii and sizes.

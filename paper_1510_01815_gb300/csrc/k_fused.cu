@@ -54,13 +54,6 @@ namespace gbk {
 
 __host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
 
-// Line-sampling window: channels with |u| = alpha |v_e - v_los| > kUCut
-// (beyond 7.06 sigma) are left out.  There 2^(-u^2) < 2^-36 of the line's
-// peak, and the terms fall off geometrically beyond, so the dropped tails
-// change the line's three sums by under 1e-9 of their values -- far below
-// the FP32 resolution of the sums (6e-8).  The one-channel margin of the
-// window keeps the channel nearest the line centre in it for any width.
-constexpr float kUCut = 6.0f;
 
 // Extended rows [band_begin(r), band_begin(r+1)) belong to cluster rank r.
 __host__ __device__ inline int band_begin(int rank, int ey, int cs) { return (int)(((long)rank * ey) / cs); }
@@ -429,10 +422,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
             int eb = blk ? ehi : 0, ee = blk ? g.ez : elo;
             if (eb >= ee) continue;
             {
-                // the block is passed over when every lane's |u| > kUCut over
-                // all of it (u is monotone in the channel: test the ends)
+                // the block is passed over when every lane's |u| exceeds its
+                // cut over all of it (u is monotone in the channel: test the ends)
                 const float ua = fmaf((float)eb, adv, ub), uz = fmaf((float)(ee - 1), adv, ub);
-                const bool zero = (ua > kUCut && uz > kUCut) || (ua < -kUCut && uz < -kUCut);
+                const float cut = (sh != 0.f) ? kUFlush : kUCut;
+                const bool zero = (ua > cut && uz > cut) || (ua < -cut && uz < -cut);
                 if (__all_sync(am, zero)) continue;
             }
             const int toff = blk ? hi_off - ehi : 0;  // table slot = e + toff
