@@ -55,7 +55,7 @@ SURVEY_FP32_PER_DATA_VOXEL = 47.0
 # DRAM bytes (read + write) of one fused launch of 400 Fabry-Perot models per
 # tuning (CTAs per model, threads, persistent), from the one-pass ncu
 # captures summarised in profiles/fused_eval_fabry_perot_400models.md.
-FUSED_TRAFFIC_400 = {(12, 512, 0): 744448.0, (12, 512, 1): 1318144.0}
+FUSED_TRAFFIC_400 = {(12, 512, 0): 1433600.0, (12, 512, 1): 1318400.0}
 FLUSH_BYTES = 256 << 20
 
 

@@ -33,6 +33,11 @@ CASES = {
     "nonsquare": (Geometry(40, 24, 32, 15.0, 0.0, 2.0, 35.0), P(19.7, 12.2, 145, 58, 0, 210, 3, 35, 1, 5)),
     "edge_on": (synth.SINGLE_GEOM, P(15.5, 15.5, 120, 88.5, 0, 200, 3, 40, 1, 1.0)),
     "vc_offset": (synth.SINGLE_GEOM.with_(vc=100.0), P(15.2, 16.1, 30, 50, 100, 200, 3, 40, 1, 4)),
+    # every line centred 7-7.5 sigma beyond the last extended channel (690
+    # km/s): each spaxel's in-band flux is its Gaussian tail at |u| in
+    # (6, 11.25), 1e-20 .. 7e-17 of I0 -- valid spectra (above the 1e-20 I0
+    # threshold) that a channel window cut at |u| = 6 would empty
+    "line_beyond_band": (synth.SINGLE_GEOM, P(15.5, 15.5, 120, 55, 988.8, 10, 3, 40, 1, 4)),
 }
 
 
@@ -49,10 +54,12 @@ def test_maps_fused_vs_oracle(G, case):
     ref = oracle.evaluate_batch(ogeom(g), ps)
     maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
     check_maps(maps, ref, ps, case)
+    if case == "line_beyond_band":  # the case has the valid tail spectra it is meant to have
+        assert (ref[0, 0] >= 2e-20).sum() > 900 and ref[0, 0].max() < 1e-16
 
 
 @pytest.mark.parametrize("case", ["single", "single_mode1", "tiny_1x1x1", "odd_3x5x7", "narrow_band",
-                                  "wide_kernels", "nonsquare", "edge_on"])
+                                  "wide_kernels", "nonsquare", "edge_on", "line_beyond_band"])
 def test_cube_and_maps_staged_vs_oracle(G, case):
     g, p, ps = _params(case, n=3)
     cubes, maps = G.eval_cubes(g, torch.from_numpy(ps))
