@@ -18,7 +18,10 @@
 //     output channels of its column pairs from the 4 + W - 1 ring entries
 //     they need (register blocking along z: 4 + W - 1 shared loads for 4
 //     outputs instead of 4 W), so each channel needs two block barriers;
-//     finished rows of 32 floats are written coalesced.
+//     finished rows of 32 floats are written coalesced.  Pass 3 is
+//     compiled for each window width W, and the ring has a multiple of four
+//     slots, so every aligned group of four ring entries is contiguous: one
+//     slot base per four loads and no runtime bounds in its loops.
 // The separable passes are exact in real arithmetic in any order; here y
 // comes before x.
 #include <cuda.h>
@@ -71,12 +74,68 @@ __device__ __forceinline__ void pass4(const float *src, int stride, const f32x2 
     }
 }
 
+// Ring slots: at least W + kZT (the window of a pass-3 group plus the slot
+// pass 2 fills meanwhile), rounded up to a multiple of kZT.
+__host__ __device__ inline int conv_ring_slots(int Rz) { return (2 * Rz + 1 + kZT + kZT - 1) / kZT * kZT; }
+
+// Pass 3 for output channels k0 .. k0 + kZT - 1 (k0 a multiple of kZT, ring
+// slot s0 = k0 % NR): the thread's column c at row pairs rp and rp + 8.
+// Entries 4q .. 4q + 3 of the window sit in slots (s0 + 4q) % NR + 0..3:
+// s0 and NR are multiples of four, so such a group never wraps.
+template <int W>
+__device__ __forceinline__ void conv_pass3(const float *Xr, const f32x2 *wz2, int s0, int NR, int c, int rp, int k0,
+                                           float *F, size_t fplane, int ox, int oy0, const Geom &g)
+{
+    constexpr int NI = kZT + W - 1;         // ring entries read
+    constexpr int NQ = (NI + 3) / 4;        // groups of four entries
+    constexpr int SLOT = 16 * kXP * 2;      // floats per ring slot
+    int qb[NQ];                             // first float of each group's slot
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        int sl = s0 + 4 * q;                // < 2 NR: 4 q <= NI - 1 < NR
+        if (sl >= NR) sl -= NR;
+        qb[q] = sl * SLOT;
+    }
+    const f32x2 Z = pk2(0.f, 0.f);
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int prow = rp + 8 * half;  // row pair of this thread's column
+        const float *col = Xr + (size_t)(prow * kXP + c) * 2;
+        f32x2 xin[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) xin[i] = ld2(col + qb[i >> 2] + (i & 3) * SLOT);
+        f32x2 B[kZT];
+#pragma unroll
+        for (int t = 0; t < kZT; ++t) B[t] = Z;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const f32x2 wq = wz2[j];
+#pragma unroll
+            for (int t = 0; t < kZT; ++t) B[t] = fma2(wq, xin[t + j], B[t]);
+        }
+        const int oy = oy0 + 16 * half;
+        if (ox < g.nxf) {
+            const bool y0 = oy < g.nyf, y1 = oy + 1 < g.nyf;
+            float *Fk = F + (size_t)k0 * fplane + (size_t)oy * g.nxf + ox;
+#pragma unroll
+            for (int t = 0; t < kZT; ++t, Fk += fplane) {
+                if (k0 + t < g.nzf) {
+                    float v0, v1;
+                    upk2(B[t], v0, v1);
+                    if (y0) Fk[0] = v0;
+                    if (y1) Fk[g.nxf] = v1;
+                }
+            }
+        }
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(kPThreads, 2)
     conv3d_pair_kernel(const __grid_constant__ CUtensorMap tmap, ConvPairArgs a)
 {
     const Geom &g = a.g;
-    const int W = 2 * g.Rz + 1, NR = W + kZT;  // ring of NR x-pass results
+    const int W = 2 * g.Rz + 1, NR = conv_ring_slots(g.Rz);  // ring of NR x-pass results
     const int SY = kPT + 2 * R, BW = a.box_w, C1W = kPT + 2 * R, C1P = C1W / 2;
     // Pair-row pitches of the two buffers (in pairs), chosen odd / 33 so that a
     // warp's 8-byte accesses spread over all 32 banks.
@@ -129,7 +188,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
     // pass-3 ownership: column c, row pairs rp and rp + 8 (rows 2 rp, 2 rp + 1,
     // 2 rp + 16, 2 rp + 17)
     const int c = tid & 31, rp = tid >> 5;
-    const f32x2 Z = pk2(0.f, 0.f);
     float *F = a.fine + (size_t)model * a.f_model_stride;
     const size_t fplane = (size_t)g.nyf * g.nxf;
     const int ox = tx0 + c;
@@ -197,44 +255,16 @@ __global__ void __launch_bounds__(kPThreads, 2)
         const int k0 = e - (kZT + W - 1);
         if (k0 >= 0 && k0 % kZT == 0 && k0 < g.nzf) {
             const int s0 = k0 % NR;
-#pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
-                const int prow = rp + 8 * half;  // row pair of this thread's column
-                const float *col = Xr + (size_t)(prow * kXP + c) * 2;
-                // inputs k0 .. k0 + kZT + W - 2 (the guards are warp-uniform)
-                f32x2 xin[kZT + kWmax - 1];
-#pragma unroll
-                for (int i = 0; i < kZT + kWmax - 1; ++i) {
-                    if (i < kZT + W - 1) {
-                        int slot = s0 + i;
-                        if (slot >= NR) slot -= NR;
-                        xin[i] = ld2(col + (size_t)slot * 16 * kXP * 2);
-                    }
-                }
-                f32x2 B[kZT];
-#pragma unroll
-                for (int t = 0; t < kZT; ++t) B[t] = Z;
-#pragma unroll
-                for (int j = 0; j < kWmax; ++j) {
-                    if (j < W) {
-                        const f32x2 wq = wz2[j];
-#pragma unroll
-                        for (int t = 0; t < kZT; ++t) B[t] = fma2(wq, xin[t + j], B[t]);
-                    }
-                }
-                const int oy = oy0 + 16 * half;
-                if (ox < g.nxf) {
-#pragma unroll
-                    for (int t = 0; t < kZT; ++t) {
-                        if (k0 + t < g.nzf) {
-                            float v0, v1;
-                            upk2(B[t], v0, v1);
-                            float *Fk = F + (size_t)(k0 + t) * fplane + ox;
-                            if (oy < g.nyf) Fk[(size_t)oy * g.nxf] = v0;
-                            if (oy + 1 < g.nyf) Fk[(size_t)(oy + 1) * g.nxf] = v1;
-                        }
-                    }
-                }
+            switch (g.Rz) {  // the same case in every thread
+            case 0: conv_pass3<1>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            case 1: conv_pass3<3>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            case 2: conv_pass3<5>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            case 3: conv_pass3<7>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            case 4: conv_pass3<9>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            case 5: conv_pass3<11>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            case 6: conv_pass3<13>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            case 7: conv_pass3<15>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
+            default: conv_pass3<17>(Xr, wz2, s0, NR, c, rp, k0, F, fplane, ox, oy0, g); break;
             }
         }
     }
@@ -264,7 +294,7 @@ static EncodeTiledFnP encode_fn_p()
 static size_t conv_pair_smem_bytes(const Geom &g)
 {
     const int SY = kPT + 2 * g.R, BW = (kPT + 2 * g.R + 3) & ~3, C1W = kPT + 2 * g.R;
-    const int SS = (SY * BW + 31) & ~31, NR = 2 * g.Rz + 1 + kZT;
+    const int SS = (SY * BW + 31) & ~31, NR = conv_ring_slots(g.Rz);
     return 128 + sizeof(float) * ((size_t)2 * SS + 32 * (C1W + 1) + (size_t)NR * 32 * kXP) +
            sizeof(f32x2) * (2 * g.R + 1 + 2 * g.Rz + 1);
 }
