@@ -56,7 +56,7 @@ typedef int32_t gbk_status;
 #define GBK_EINVAL      1  /* an argument failed validation                    */
 #define GBK_ECUDA       2  /* a CUDA runtime call failed (message has details) */
 #define GBK_EWORKSPACE  3  /* the workspace is missing or too small            */
-#define GBK_EUNSUPPORTED 4 /* a valid request this build cannot serve          */
+#define GBK_EUNSUPPORTED 4 /* a valid request the library does not serve       */
 
 /* Parameter order (Sec. 2.1; Vmax is the paper's V_t, h its r_0). */
 enum {
