@@ -480,6 +480,7 @@ def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device, n_ns=8)
     out["heuristic_start_error"] = {"median_dvmax": float(np.median(dvh)), "median_dpa": float(np.median(dpah)),
                                     "p90_dvmax": float(np.percentile(dvh, 90)),
                                     "p90_dpa": float(np.percentile(dpah, 90))}
+    fits = {}
     for name, mode, start, sub in (("batched_cnn_seed", gbk.LM_BATCHED, seed_p, n_test),
                                    ("batched_heuristic", gbk.LM_BATCHED, heur, n_test),
                                    ("batched_perturbed", gbk.LM_BATCHED, pert, n_test),
@@ -491,11 +492,36 @@ def run_cnn(gbk, torch, n_train, epochs, batch, n_test, n_plain, device, n_ns=8)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         dv, dpa = err(q, ptest[:sub])
+        fits[name] = q
         out[name] = {"galaxies": sub, "fits_per_s": sub / dt, "p50_iters": float(np.percentile(it, 50)),
                      "p99_iters": float(np.percentile(it, 99)), "converged_frac": float(np.mean(np.isin(stt, [1, 2]))),
                      "recovered_frac": float(np.mean((dv < 2.0) & (dpa < 1.0))),
                      "median_dvmax": float(np.median(dv)), "median_dpa": float(np.median(dpa))}
     out["batched_cnn_seed"]["speedup_vs_plain"] = out["batched_cnn_seed"]["fits_per_s"] / out["plain_perturbed"]["fits_per_s"]
+    # the seed with the plain fit as its fallback: galaxies whose seeded fit
+    # does not converge or ends above 1.5 x the number of residuals are
+    # refitted from the Sec. 2.1.9 start, and the lower chi2 is kept
+    nres = 2.0 * (mt != 0).sum(dim=(1, 2)).double().cpu().numpy()
+    opts = gbk.lm_opts(max_iter=200, jacobian=gbk.JAC_FD_FORWARD, mode=gbk.LM_BATCHED, free=FIT_FREE)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q, c, it, stt, used = gbk.fit_lm_fallback(g, obs, seed_p, heur, lo, hi, opts, chi2_accept=1.5 * nres,
+                                              device=device)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dv, dpa = err(q, ptest)
+    out["batched_cnn_seed_fallback"] = {
+        "galaxies": n_test, "fits_per_s": n_test / dt, "refitted_frac": float(np.mean(used > 0)),
+        "fallback_kept_frac": float(np.mean(used == 1)), "chi2_accept": "1.5 x unmasked residuals",
+        "converged_frac": float(np.mean(np.isin(stt, [1, 2]))), "within_accept_frac": float(np.mean(c <= 1.5 * nres)),
+        "recovered_frac": float(np.mean((dv < 2.0) & (dpa < 1.0))),
+        "median_dvmax": float(np.median(dv)), "median_dpa": float(np.median(dpa))}
+    # the plain fit as the judge of the seed's error (what real data allow):
+    # the seed against the fit from the Sec. 2.1.9 start
+    dvj, dpaj = err(seed_p, fits["batched_heuristic"])
+    out["seed_error_vs_plain_fit"] = {"median_dvmax": float(np.median(dvj)), "median_dpa": float(np.median(dpaj)),
+                                      "p90_dvmax": float(np.percentile(dvj, 90)),
+                                      "p90_dpa": float(np.percentile(dpaj, 90))}
     out["nested_sampling"] = run_cnn_ns(gbk, torch, g, obs, ptest, pred, lo, hi, n_ns, device)
     return out
 

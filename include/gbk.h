@@ -277,6 +277,30 @@ GBK_API gbk_status gbk_fit_lm(const gbk_geom *g, int32_t n_gal, const gbk_obs *o
                               int32_t *iters_out, int32_t *status_out, void *workspace, size_t ws_bytes,
                               void *stream);
 
+/* LM from a learned start with the plain fit as its fallback (how the CNN
+ * seed below is used): every galaxy is fitted from `params` (the seed); a
+ * galaxy whose seeded fit did not converge (status other than GBK_FIT_FTOL
+ * or GBK_FIT_XTOL) or ended with chi2 above chi2_accept[g] is fitted again,
+ * with the same options, from fallback_start[g] (the method's own start,
+ * e.g. gbk_initial_guess), and of its two fits the one with the lower chi2
+ * is returned.  Arguments as gbk_fit_lm, plus
+ *  fallback_start device [n_gal][GBK_NPAR]
+ *  chi2_accept    device [n_gal], or NULL (then only unconverged fits fall
+ *                 back); e.g. 1.5 x the number of unmasked residuals
+ *  used_fallback  device [n_gal] int32: 0 the seeded fit was not redone,
+ *                 1 the fallback fit is returned, 2 it ran but the seeded
+ *                 fit had the lower chi2 (iters_out and status_out belong to
+ *                 the fit returned)
+ *  workspace      gbk_fit_lm_fallback_workspace_bytes(g, n_gal, opts)
+ * Synchronises `stream`; both passes run batched on the device, the
+ * selection of the galaxies to refit on the host. */
+GBK_API size_t gbk_fit_lm_fallback_workspace_bytes(const gbk_geom *g, int32_t n_gal, const gbk_lm_opts *opts);
+GBK_API gbk_status gbk_fit_lm_fallback(const gbk_geom *g, int32_t n_gal, const gbk_obs *obs, const double *lo,
+                                       const double *hi, double *params, const double *fallback_start,
+                                       const double *chi2_accept, const gbk_lm_opts *opts, double *chi2_out,
+                                       int32_t *iters_out, int32_t *status_out, int32_t *used_fallback,
+                                       void *workspace, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Initial model parameter values (Sec. 2.1.9), measured on each galaxy's
  * maps -- the optimisers' starting point when no better one (e.g. the CNN

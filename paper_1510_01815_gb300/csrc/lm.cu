@@ -652,7 +652,111 @@ gbk_status lm_survey(SurveyPlan &sp, const gbk_geom *geoms, const gbk_obs *obs, 
 
 using namespace gbk;
 
+// Keeps, for each galaxy r of a refitted part (galaxy idx[r]), the refit when
+// its chi2 is lower than the first fit's (or the first is not finite).
+__global__ void keep_better_kernel(const int32_t *idx, int n, const double *p_b, const double *c_b, const int32_t *it_b,
+                                   const int32_t *st_b, double *params, double *chi2, int32_t *iters, int32_t *status,
+                                   int32_t *used)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int g = idx[r];
+        const double ca = chi2[g], cb = c_b[r];
+        const bool take_b = (cb < ca) || (!(ca == ca) && cb == cb);
+        used[g] = take_b ? 1 : 2;
+        if (!take_b) continue;
+        for (int k = 0; k < GBK_NPAR; ++k) params[(size_t)g * GBK_NPAR + k] = p_b[(size_t)r * GBK_NPAR + k];
+        chi2[g] = cb;
+        iters[g] = it_b[r];
+        status[g] = st_b[r];
+    }
+}
+
 extern "C" {
+
+size_t gbk_fit_lm_fallback_workspace_bytes(const gbk_geom *gin, int32_t n_gal, const gbk_lm_opts *opts)
+{
+    const size_t a = gbk_fit_lm_workspace_bytes(gin, n_gal, opts);
+    if (a == 0) return 0;
+    return al256(a) + split_rows_bytes(n_gal);
+}
+
+gbk_status gbk_fit_lm_fallback(const gbk_geom *gin, int32_t n_gal, const gbk_obs *obs, const double *lo,
+                               const double *hi, double *params, const double *fallback_start,
+                               const double *chi2_accept, const gbk_lm_opts *opts, double *chi2_out,
+                               int32_t *iters_out, int32_t *status_out, int32_t *used_fallback, void *workspace,
+                               size_t ws_bytes, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    if (n_gal < 0) return fail(GBK_EINVAL, "n_gal must be >= 0");
+    if (n_gal == 0) return ok();
+    const size_t need = gbk_fit_lm_fallback_workspace_bytes(gin, n_gal, opts);
+    if (need == 0) return GBK_EINVAL;
+    if (!workspace || ws_bytes < need)
+        return fail(GBK_EWORKSPACE, "gbk_fit_lm_fallback needs %zu bytes of workspace (got %zu)", need, ws_bytes);
+    if ((s = check_device_ptr(fallback_start, "fallback_start", 8)) ||
+        (s = check_device_ptr(used_fallback, "used_fallback", 4)))
+        return s;
+    if (chi2_accept && (s = check_device_ptr(chi2_accept, "chi2_accept", 8))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t fit_bytes = gbk_fit_lm_workspace_bytes(gin, n_gal, opts);
+    char *ws = (char *)workspace;
+    // 1. every galaxy from the learned start
+    if ((s = gbk_fit_lm(gin, n_gal, obs, lo, hi, params, opts, chi2_out, iters_out, status_out, ws, fit_bytes,
+                        stream)))
+        return s;
+    cudaError_t e = cudaMemsetAsync(used_fallback, 0, sizeof(int32_t) * n_gal, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fallback: clearing used_fallback");
+    // 2. the galaxies whose fit did not converge or ended above chi2_accept
+    std::vector<int32_t> st_h(n_gal);
+    std::vector<double> c_h(n_gal), acc_h;
+    e = cudaMemcpyAsync(st_h.data(), status_out, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c_h.data(), chi2_out, sizeof(double) * n_gal, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && chi2_accept) {
+        acc_h.resize(n_gal);
+        e = cudaMemcpyAsync(acc_h.data(), chi2_accept, sizeof(double) * n_gal, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "fallback: reading the first fits");
+    std::vector<int32_t> idx;
+    for (int i = 0; i < n_gal; ++i) {
+        const bool conv = st_h[i] == GBK_FIT_FTOL || st_h[i] == GBK_FIT_XTOL;
+        const bool high = chi2_accept && !(c_h[i] <= acc_h[i]);
+        if (!conv || high) idx.push_back(i);
+    }
+    const int n = (int)idx.size();
+    if (n == 0) return ok();
+    // 3. those galaxies from the fallback start, packed after the fit's region
+    char *rows = ws + al256(fit_bytes);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char *p = rows + off; off += al256(bytes); return p; };
+    int32_t *d_idx = (int32_t *)take(sizeof(int32_t) * n);
+    double *d_p = (double *)take(sizeof(double) * GBK_NPAR * n);
+    double *d_lo = (double *)take(sizeof(double) * GBK_NPAR * n);
+    double *d_hi = (double *)take(sizeof(double) * GBK_NPAR * n);
+    gbk_obs *d_obs = (gbk_obs *)take(sizeof(gbk_obs) * n);
+    double *d_c = (double *)take(sizeof(double) * n);
+    int32_t *d_it = (int32_t *)take(sizeof(int32_t) * n);
+    int32_t *d_st = (int32_t *)take(sizeof(int32_t) * n);
+    e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fallback: index upload");
+    const size_t prow = sizeof(double) * GBK_NPAR;
+    if ((s = rows_copy(fallback_start, d_p, d_idx, n, prow, false, st)) ||
+        (s = rows_copy(lo, d_lo, d_idx, n, prow, false, st)) || (s = rows_copy(hi, d_hi, d_idx, n, prow, false, st)) ||
+        (s = rows_copy(obs, d_obs, d_idx, n, sizeof(gbk_obs), false, st)))
+        return s;
+    const size_t part_bytes = gbk_fit_lm_workspace_bytes(gin, n, opts);
+    if ((s = gbk_fit_lm(gin, n, d_obs, d_lo, d_hi, d_p, opts, d_c, d_it, d_st, ws, part_bytes, stream))) return s;
+    // 4. keep the better of the two fits
+    keep_better_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_idx, n, d_p, d_c, d_it, d_st, params, chi2_out, iters_out,
+                                                        status_out, used_fallback);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "fallback: merging the fits");
+    return ok();
+}
 
 size_t gbk_fit_lm_workspace_bytes(const gbk_geom *gin, int32_t n_gal, const gbk_lm_opts *opts)
 {

@@ -83,6 +83,9 @@ def lib():
             "gbk_set_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
             "gbk_fit_lm_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
             "gbk_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz, vp]),
+            "gbk_fit_lm_fallback_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
+            "gbk_fit_lm_fallback": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp,
+                                          vp, sz, vp]),
             "gbk_jacobian": (i32, [gp, i32, vp, op, u32, vp, vp, vp, vp, vp, vp]),
             "gbk_grid_workspace_bytes": (sz, [gp, ctypes.POINTER(ctypes.c_int32), i32]),
             "gbk_grid": (i32, [gp, op, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -128,7 +131,8 @@ def lib():
 def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
-            "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
+            "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_fit_lm_fallback_workspace_bytes", "gbk_fit_lm_fallback",
+            "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
             "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_initial_guess", "gbk_survey_autotune", "gbk_survey_get_tuning",
             "gbk_survey_set_tuning", "gbk_device_status", "gbk_gemm_bf16", "gbk_cnn_param_count",
@@ -331,6 +335,55 @@ def fit_lm(geom, obs_list, p0, lo, hi, opts, device="cuda", stream=None):
     ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
     gbk_fit_lm(geom, obs_dev, dlo, dhi, p, opts, chi2, iters, status, ws, stream)
     return p.cpu().numpy(), chi2.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
+
+
+def gbk_fit_lm_fallback_workspace_bytes(geom, n_gal, opts):
+    g = cgeom(geom)
+    n = lib().gbk_fit_lm_fallback_workspace_bytes(ctypes.byref(g), int(n_gal), ctypes.byref(opts))
+    err = lib().gbk_last_error().decode()
+    if n == 0 and err:
+        raise GbkError(GBK_EINVAL, err)
+    return int(n)
+
+
+def gbk_fit_lm_fallback(geom, obs_dev, lo, hi, params, fallback_start, chi2_accept, opts, chi2_out, iters_out,
+                        status_out, used_fallback, workspace, stream=None):
+    g = cgeom(geom)
+    n = params.shape[0]
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_fit_lm_fallback(ctypes.byref(g), int(n), _ptr(obs_dev, torch.uint8, "obs"),
+                                     _ptr(lo, torch.float64, "lo"), _ptr(hi, torch.float64, "hi"),
+                                     _ptr(params, torch.float64, "params"),
+                                     _ptr(fallback_start, torch.float64, "fallback_start"),
+                                     _ptr(chi2_accept, torch.float64, "chi2_accept"), ctypes.byref(opts),
+                                     _ptr(chi2_out, torch.float64, "chi2_out"),
+                                     _ptr(iters_out, torch.int32, "iters_out"),
+                                     _ptr(status_out, torch.int32, "status_out"),
+                                     _ptr(used_fallback, torch.int32, "used_fallback"),
+                                     _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def fit_lm_fallback(geom, obs_list, seed, fallback, lo, hi, opts, chi2_accept=None, device="cuda", stream=None):
+    """Convenience: LM from `seed` with the fit from `fallback` as fallback
+    (gbk_fit_lm_fallback); returns (params, chi2, iters, status,
+    used_fallback) as numpy arrays."""
+    import numpy as np
+    n = len(obs_list)
+    obs_dev, _keep = obs_array(obs_list, device)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).reshape(n, NPAR)).to(device)
+    p, fb, dlo, dhi = t(seed), t(fallback), t(lo), t(hi)
+    acc = None
+    if chi2_accept is not None:
+        acc = torch.as_tensor(np.ascontiguousarray(chi2_accept, dtype=np.float64).reshape(n)).to(device)
+    chi2 = torch.empty(n, dtype=torch.float64, device=device)
+    iters = torch.empty(n, dtype=torch.int32, device=device)
+    status = torch.empty(n, dtype=torch.int32, device=device)
+    used = torch.empty(n, dtype=torch.int32, device=device)
+    nb = gbk_fit_lm_fallback_workspace_bytes(geom, n, opts)
+    ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
+    gbk_fit_lm_fallback(geom, obs_dev, dlo, dhi, p, fb, acc, opts, chi2, iters, status, used, ws, stream)
+    return (p.cpu().numpy(), chi2.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy(),
+            used.cpu().numpy())
 
 
 def cgeoms(geoms):

@@ -146,6 +146,17 @@ def test_jacobian_and_lm_validation(gbk):
     cg = gbk.cgeom(g)
     st = gbk.lib().gbk_jacobian(ctypes.byref(cg), 1, None, None, 0, None, None, None, None, None, None)
     assert st == gbk.GBK_EINVAL
+    # the seeded fit with a fallback needs the fit's workspace plus room for
+    # the packed rows of every galaxy, and rejects what gbk_fit_lm rejects
+    o = gbk.lm_opts()
+    assert gbk.gbk_fit_lm_fallback_workspace_bytes(g, 64, o) > gbk.gbk_fit_lm_workspace_bytes(g, 64, o)
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_fit_lm_fallback_workspace_bytes(g, 4, gbk.lm_opts(free=()))
+    st = gbk.lib().gbk_fit_lm_fallback(ctypes.byref(cg), 4, None, None, None, None, None, None, ctypes.byref(o),
+                                       None, None, None, None, None, 0, None)
+    assert st == gbk.GBK_EWORKSPACE
+    assert gbk.lib().gbk_fit_lm_fallback(ctypes.byref(cg), 0, None, None, None, None, None, None, ctypes.byref(o),
+                                         None, None, None, None, None, 0, None) == gbk.GBK_OK
 
 
 def test_survey_host_logic(gbk):

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from oracle import guess
-from cases import ogeom
+from cases import ogeom, noisy_mocks
 from paper_1510_01815_gb300 import synth
 from paper_1510_01815_gb300.synth import Geometry
 
@@ -26,23 +26,7 @@ def G():
 
 
 def _mocks(g, n, seed, noise=5.0):
-    rng = np.random.default_rng(seed)
-    truth, cont, obs = [], [], []
-    for _ in range(n):
-        p = synth.params(rng.uniform(0.4, 0.6) * (g.nx - 1), rng.uniform(0.4, 0.6) * (g.ny - 1),
-                         rng.uniform(0.0, 360.0), rng.uniform(25.0, 70.0), rng.uniform(-20.0, 20.0),
-                         rng.uniform(100.0, 250.0), rng.uniform(1.5, 4.0), rng.uniform(20.0, 60.0), 1.0,
-                         rng.uniform(3.0, 6.0))
-        m = oracle.evaluate(ogeom(g), p)
-        shape = (g.ny, g.nx)
-        v = (m[1] + rng.normal(0.0, noise, shape)).astype(np.float32)
-        s = (m[2] + rng.normal(0.0, noise * math.sqrt(2.0), shape)).astype(np.float32)
-        wv, ws = synth.weights(shape, max(noise, 1.0))
-        mask = synth.dead_fibre_mask(rng, shape).astype(np.uint8)
-        truth.append(p)
-        cont.append(m[0].astype(np.float32))
-        obs.append(oracle.Obs(v, s, wv, ws, mask))
-    return np.array(truth), np.array(cont), obs
+    return noisy_mocks(g, n, seed, noise)
 
 
 def _dobs(G, o):
