@@ -831,10 +831,10 @@ def run_jacobian(gbk, torch, device, n=2048, geom=None):
             "jacobians_per_s": n / (tj * 1e-3)}
 
 
-def run_grid(gbk, torch, device):
+def run_grid(gbk, torch, device, chunk=1 << 17):
     """Nested grids (Sec. 2.3.3) at full size: a 64 x 64 x 64 cube, 10^5
     nodes per level over PA, i, V_max, r_t, sigma0 (10 each), 3 levels,
-    evaluated 2^14 models per launch; x0, y0, V_sys, I0, h fixed at the
+    evaluated `chunk` models per launch; x0, y0, V_sys, I0, h fixed at the
     truth; 5 / 5 sqrt(2) km/s noise."""
     g = synth.Geometry(64, 64, 64, 20.0, 0.0, 2.5, 30.0)
     rng = np.random.default_rng(3)
@@ -852,14 +852,14 @@ def run_grid(gbk, torch, device):
                         synth.RT: (1.0, 8.0), synth.SIG0: (10.0, 80.0)}.items():
         nodes[k] = 10
         lo[k], hi[k] = a_, b_
-    gbk.gbk_grid(g, obs, lo, hi, nodes, truth, levels=1, chunk=16384, device=device)  # warm-up
+    gbk.gbk_grid(g, obs, lo, hi, nodes, truth, levels=1, chunk=chunk, device=device)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    bp, bi, bc = gbk.gbk_grid(g, obs, lo, hi, nodes, truth, levels=3, chunk=16384, device=device)
+    bp, bi, bc = gbk.gbk_grid(g, obs, lo, hi, nodes, truth, levels=3, chunk=chunk, device=device)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"workload": "64x64x64 cube, 10^5 nodes per level x 3 levels (PA, i, V_max, r_t, sigma0), 2^14 models "
-                        "per launch", "seconds": dt, "nodes_per_s": 3e5 / dt,
+    return {"workload": "64x64x64 cube, 10^5 nodes per level x 3 levels (PA, i, V_max, r_t, sigma0), %d models "
+                        "per launch" % min(chunk, 100000), "seconds": dt, "nodes_per_s": 3e5 / dt,
             "best": {synth.PARAM_NAMES[k]: float(bp[k]) for k in (synth.PA, synth.INCL, synth.VMAX, synth.RT,
                                                                    synth.SIG0)},
             "truth": {synth.PARAM_NAMES[k]: float(truth[k]) for k in (synth.PA, synth.INCL, synth.VMAX, synth.RT,
