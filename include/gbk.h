@@ -491,8 +491,23 @@ GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ffm
  * every bounded device-side wait since the last call completed; bit 0 set
  * when a TMA load of the staged convolution did not complete in time, bit 1
  * when a pipeline wait of the tensor-core GEMM did not (the affected blocks
- * stopped early and their output is incomplete).  Synchronising. */
+ * stopped early and their output is incomplete), bit 2 when the wait of
+ * gbk_wait_selfcheck ran out.  Synchronising. */
 GBK_API gbk_status gbk_device_status(int32_t *status);
+
+/* Self-check of the bounded device waits: one thread runs the library's
+ * mbarrier wait (at most `limit` try_wait attempts, each of which the
+ * hardware may suspend for a bounded time, then give up) -- the wait the
+ * TMA-fed convolution and the tensor-core GEMM use -- on a barrier that
+ * nothing completes (complete = 0) or that one arrival completes first
+ * (complete = 1).  A wait that runs out sets bit 2 of the device status
+ * word and the kernel returns, so the timeout path is exercised without a
+ * fault, a trap or a hang and the context stays usable.
+ *  limit       1 .. 2^24 tries (the production waits allow 2^24)
+ *  elapsed_ns  host output (or NULL): the wait's duration on the device
+ *              clock (%globaltimer)
+ * Synchronises `stream`; GBK_EINVAL on bad arguments. */
+GBK_API gbk_status gbk_wait_selfcheck(int64_t limit, int32_t complete, int64_t *elapsed_ns, void *stream);
 
 /* ------------------------------------------------------------------------
  * BF16 tensor-core GEMM (tcgen05, TMA-fed, FP32 accumulation in tensor

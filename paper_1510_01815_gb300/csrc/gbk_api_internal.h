@@ -11,5 +11,7 @@ gbk_status cuda_fail(cudaError_t e, const char *what);
 gbk_status derive_geom(const gbk_geom *in, Geom *g);
 gbk_status check_device_ptr(const void *p, const char *name, size_t align);
 gbk_status check_obs(const gbk_obs *obs);
+// reads and clears the wait self-check's status (k_selfcheck.cu)
+gbk_status selfcheck_status_read(int *v);
 
 }  // namespace gbk

@@ -84,6 +84,7 @@ def lib():
             "gbk_fit_lm_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
             "gbk_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz, vp]),
             "gbk_fit_lm_fallback_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
+            "gbk_wait_selfcheck": (i32, [ctypes.c_int64, i32, ctypes.POINTER(ctypes.c_int64), vp]),
             "gbk_fit_lm_fallback": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp,
                                           vp, sz, vp]),
             "gbk_jacobian": (i32, [gp, i32, vp, op, u32, vp, vp, vp, vp, vp, vp]),
@@ -132,6 +133,7 @@ def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_fit_lm_fallback_workspace_bytes", "gbk_fit_lm_fallback",
+            "gbk_wait_selfcheck",
             "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
             "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_initial_guess", "gbk_survey_autotune", "gbk_survey_get_tuning",
@@ -745,6 +747,15 @@ def initial_guess(geom, obs_list, fixed, continuum=None, device="cuda", stream=N
         c = torch.as_tensor(continuum, dtype=torch.float32).reshape(n, geom.ny, geom.nx).to(device).contiguous()
     gbk_initial_guess(geom, obs_dev, f, out, c, stream)
     return out.cpu().numpy()
+
+
+def gbk_wait_selfcheck(limit, complete, stream=None):
+    """Runs the bounded device wait on a barrier that nothing completes
+    (complete=False) or that one arrival completes; returns the wait's
+    duration in ns.  A wait that runs out sets bit 2 of gbk_device_status()."""
+    ns = ctypes.c_int64()
+    _check(lib().gbk_wait_selfcheck(int(limit), 1 if complete else 0, ctypes.byref(ns), _stream(stream)))
+    return ns.value
 
 
 def gbk_device_status():

@@ -157,6 +157,10 @@ def test_jacobian_and_lm_validation(gbk):
     assert st == gbk.GBK_EWORKSPACE
     assert gbk.lib().gbk_fit_lm_fallback(ctypes.byref(cg), 0, None, None, None, None, None, None, ctypes.byref(o),
                                          None, None, None, None, None, 0, None) == gbk.GBK_OK
+    # the wait self-check validates its arguments before any launch
+    assert gbk.lib().gbk_wait_selfcheck(0, 0, None, None) == gbk.GBK_EINVAL
+    assert gbk.lib().gbk_wait_selfcheck((1 << 24) + 1, 0, None, None) == gbk.GBK_EINVAL
+    assert gbk.lib().gbk_wait_selfcheck(16, 2, None, None) == gbk.GBK_EINVAL
 
 
 def test_survey_host_logic(gbk):
