@@ -37,14 +37,28 @@ namespace gbk {
 
 // NP = derivatives carried: every parameter (GBK_NPAR), or the first eight
 // (x0 .. sigma0) when I0 and h are held fixed, as in every fit of the paper.
+// A spaxel record holds kTrip = NP + 1 moment triplets (x0, x1, x2) -- the
+// values (triplet 0) and the NP derivatives -- and the centre a.  Triplets
+// 2q and 2q + 1 are packed as pairs, (x0, x0'), (x1, x1'), (x2, x2') at
+// floats 6q .. 6q + 5, so the spatial passes treat two triplets per packed
+// f32x2 operation; an odd last triplet follows unpaired, then a.
 template <int NP>
 struct TgDims {
-    static constexpr int kRec = 4 + 3 * NP;  // floats per spaxel record: a, q0..q2, dq (3 per parameter)
-    // record stride in floats, odd: consecutive threads' records then start
-    // on distinct banks, so the scalar record accesses are conflict-free
-    static constexpr int RS = kRec | 1;
+    static constexpr int kTrip = NP + 1;
+    static constexpr int kPairs = kTrip / 2;
+    static constexpr int kSingle = 6 * kPairs;               // the unpaired triplet
+    static constexpr int kA = kSingle + 3 * (kTrip & 1);     // the centre a
+    static constexpr int kRec = kA + 1;                      // floats per record
+    // record stride in floats, 2 mod 4: records start 8-byte aligned and a
+    // half-warp's 8-byte loads of consecutive records fall on distinct banks
+    static constexpr int RS = ((kRec + 1) & ~3) + 2;
     static constexpr int kTri = NP * (NP + 1) / 2;
     static constexpr int kEnt = kTri + NP + 1;  // J^T J upper triangle, J^T v, sum r^2
+    // float offset of component m of triplet t
+    __host__ __device__ static constexpr int off(int t, int m)
+    {
+        return t < 2 * kPairs ? 6 * (t >> 1) + 2 * m + (t & 1) : kSingle + m;
+    }
 };
 
 __host__ __device__ inline int tg_band_begin(int rank, int ey, int cs) { return (int)(((long)rank * ey) / cs); }
@@ -80,19 +94,66 @@ size_t tangent_smem_bytes_host(const Geom &g, int band, int threads, int direct,
     return tangent_smem_bytes(g, band, threads, direct, narrow);
 }
 
-// Re-centres the record at rec (centre stored as rec[0] = a) to centre c
-// and accumulates it with weight w into acc[0..kRec).
+// Accumulated triplets of one output spaxel, in the record's pairing.
 template <int NP>
-__device__ __forceinline__ void accum_rec(const float *rec, float c, float w, float *acc)
-{
-    float D = rec[0] - c;
+struct TgAcc {
+    f32x2 p[3 * TgDims<NP>::kPairs];  // pair q: x0, x1, x2 of triplets 2q, 2q + 1
+    float s[3];                       // the unpaired triplet
+    __device__ __forceinline__ void zero()
+    {
 #pragma unroll
-    for (int t = 0; t <= NP; ++t) {  // triplet 0: values; 1..NP: derivatives
-        const float x0 = rec[1 + 3 * t], x1 = rec[2 + 3 * t], x2 = rec[3 + 3 * t];
-        float t0 = w * x0, t1 = w * x1;
-        acc[1 + 3 * t] += t0;
-        acc[2 + 3 * t] += fmaf(D, t0, t1);
-        acc[3 + 3 * t] += fmaf(w, x2, D * fmaf(D, t0, 2.f * t1));
+        for (int i = 0; i < 3 * TgDims<NP>::kPairs; ++i) p[i] = pk2(0.f, 0.f);
+        s[0] = s[1] = s[2] = 0.f;
+    }
+    // component m of triplet t
+    __device__ __forceinline__ float get(int t, int m) const
+    {
+        if (t < 2 * TgDims<NP>::kPairs) {
+            float lo, hi;
+            upk2(p[3 * (t >> 1) + m], lo, hi);
+            return (t & 1) ? hi : lo;
+        }
+        return s[m];
+    }
+    // the accumulated triplets and the centre c as a record at out
+    __device__ __forceinline__ void store(float *out, float c) const
+    {
+#pragma unroll
+        for (int i = 0; i < 3 * TgDims<NP>::kPairs; ++i) *reinterpret_cast<f32x2 *>(out + 2 * i) = p[i];
+        if (TgDims<NP>::kTrip & 1) {
+            out[TgDims<NP>::kSingle] = s[0];
+            out[TgDims<NP>::kSingle + 1] = s[1];
+            out[TgDims<NP>::kSingle + 2] = s[2];
+        }
+        out[TgDims<NP>::kA] = c;
+    }
+};
+
+// Re-centres the record at rec (centre a at rec[kA]) to centre c and adds it
+// with weight w: x0 += w x0, x1 += w (x1 + D x0), x2 += w (x2 + D (2 x1 +
+// D x0)), D = a - c, two triplets per packed operation.
+template <int NP>
+__device__ __forceinline__ void accum_rec(const float *rec, float c, float w, TgAcc<NP> &acc)
+{
+    using Dm = TgDims<NP>;
+    const float D = rec[Dm::kA] - c;
+    const f32x2 W = pk2(w, w), DD = pk2(D, D);
+#pragma unroll
+    for (int q = 0; q < Dm::kPairs; ++q) {
+        const f32x2 X0 = *reinterpret_cast<const f32x2 *>(rec + 6 * q);
+        const f32x2 X1 = *reinterpret_cast<const f32x2 *>(rec + 6 * q + 2);
+        const f32x2 X2 = *reinterpret_cast<const f32x2 *>(rec + 6 * q + 4);
+        const f32x2 T0 = mul2(W, X0), T1 = mul2(W, X1);
+        acc.p[3 * q] = add2(acc.p[3 * q], T0);
+        acc.p[3 * q + 1] = add2(acc.p[3 * q + 1], fma2(DD, T0, T1));
+        acc.p[3 * q + 2] = add2(acc.p[3 * q + 2], fma2(W, X2, mul2(DD, fma2(DD, T0, add2(T1, T1)))));
+    }
+    if (Dm::kTrip & 1) {
+        const float x0 = rec[Dm::kSingle], x1 = rec[Dm::kSingle + 1], x2 = rec[Dm::kSingle + 2];
+        const float t0 = w * x0, t1 = w * x1;
+        acc.s[0] += t0;
+        acc.s[1] += fmaf(D, t0, t1);
+        acc.s[2] += fmaf(w, x2, D * fmaf(D, t0, 2.f * t1));
     }
 }
 
@@ -103,8 +164,8 @@ template <int NP>
 __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent_kernel(TangentArgs a)
 {
     constexpr int NPT = NP;
-    constexpr int kRec = TgDims<NP>::kRec, kEnt = TgDims<NP>::kEnt;
-    constexpr int RS = TgDims<NP>::RS;  // record stride (odd)
+    constexpr int kEnt = TgDims<NP>::kEnt;
+    constexpr int RS = TgDims<NP>::RS;  // record stride (2 mod 4)
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = a.cs;
     const int rank = (int)cluster.block_rank();
@@ -286,16 +347,17 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
         }
         float A = c.amp * br;
         float *rec = Q + (size_t)idx * RS;
-        rec[0] = a_c;
-        rec[1] = A * B[0][0];
-        rec[2] = A * B[0][1];
-        rec[3] = A * B[0][2];
+        rec[TgDims<NP>::kA] = a_c;
+        rec[TgDims<NP>::off(0, 0)] = A * B[0][0];
+        rec[TgDims<NP>::off(0, 1)] = A * B[0][1];
+        rec[TgDims<NP>::off(0, 2)] = A * B[0][2];
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             float ds = (k == GBK_SIG0) ? dsig_ds0 : 0.f;
             float cA = dlnA[k], cv = dv[k] * isig2, cs3 = ds * isig3;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) rec[4 + 3 * k + m] = A * (cA * B[0][m] + cv * B[1][m] + cs3 * B[2][m]);
+            for (int m = 0; m < 3; ++m)
+                rec[TgDims<NP>::off(k + 1, m)] = A * (cA * B[0][m] + cv * B[1][m] + cs3 * B[2][m]);
         }
     }
     __syncthreads();
@@ -304,15 +366,11 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
     for (int idx = tid; idx < nrows * g.nx; idx += nthr) {
         int rr = idx / g.nx, xx = idx - rr * g.nx;
         const float *row = Q + ((size_t)rr * g.ex + xx) * RS;
-        float cen = row[(size_t)R * RS];
-        float acc[RS];
-#pragma unroll
-        for (int t = 0; t < RS; ++t) acc[t] = 0.f;
+        float cen = row[(size_t)R * RS + TgDims<NP>::kA];
+        TgAcc<NP> acc;
+        acc.zero();
         for (int j = 0; j <= 2 * R; ++j) accum_rec<NP>(row + (size_t)j * RS, cen, wxy[j], acc);
-        float *out = P + (size_t)idx * RS;
-        out[0] = cen;
-#pragma unroll
-        for (int t = 1; t < kRec; ++t) out[t] = acc[t];
+        acc.store(P + (size_t)idx * RS, cen);
     }
     cluster.sync();
 
@@ -344,12 +402,11 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
         int y = ylo + yy;
         size_t pix = (size_t)y * g.nx + xx;
         int k0 = y - (row0 - R);
-        float cen = rowptr[k0 + R][(size_t)xx * RS];
-        float acc[RS];
-#pragma unroll
-        for (int t = 0; t < RS; ++t) acc[t] = 0.f;
+        float cen = rowptr[k0 + R][(size_t)xx * RS + TgDims<NP>::kA];
+        TgAcc<NP> acc;
+        acc.zero();
         for (int j = 0; j <= 2 * R; ++j) accum_rec<NP>(rowptr[k0 + j] + (size_t)xx * RS, cen, wxy[j], acc);
-        float S0 = acc[1], S1v = acc[2], S2v = acc[3];
+        float S0 = acc.get(0, 0), S1v = acc.get(0, 1), S2v = acc.get(0, 2);
         bool use = c.valid && S0 > thr && s_ob.mask[pix] != 0;
         if (use) {
             float inv = 1.f / S0;
@@ -362,7 +419,7 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
             float inv2m2 = m2 > 0.f ? 0.5f / m2 : 0.f;
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                float d0 = acc[4 + 3 * k], d1 = acc[5 + 3 * k], d2 = acc[6 + 3 * k];
+                float d0 = acc.get(k + 1, 0), d1 = acc.get(k + 1, 1), d2 = acc.get(k + 1, 2);
                 float dmu = (d1 - mu * d0) * inv;
                 float dvar = (d2 - S2v * inv * d0) * inv - 2.f * mu * dmu;
                 jv[k] = wv * dmu;
