@@ -503,7 +503,9 @@ GBK_API gbk_status gbk_device_status(int32_t *status);
  * (complete = 1).  A wait that runs out sets bit 2 of the device status
  * word and the kernel returns, so the timeout path is exercised without a
  * fault, a trap or a hang and the context stays usable.
- *  limit       1 .. 2^24 tries (the production waits allow 2^24)
+ *  limit       1 .. 2^24 tries (the production waits allow 2^18: a try
+ *              that finds its phase incomplete suspends about 3.75 us on
+ *              GB300, so about one second)
  *  elapsed_ns  host output (or NULL): the wait's duration on the device
  *              clock (%globaltimer)
  * Synchronises `stream`; GBK_EINVAL on bad arguments. */

@@ -39,7 +39,7 @@ constexpr int kPRmax = 8;          // largest PSF radius served
 constexpr int kXP = kPT + 1;       // pair pitch of a ring row (conflict-free pass-2 stores)
 constexpr int kZT = 4;             // output channels per pass-3 group
 constexpr int kWmax = 2 * 8 + 1;   // widest LSF window served (Rz <= 8)
-constexpr long kPWaitLimit = 1L << 24;
+constexpr long kPWaitLimit = 1L << 18;  // tries: about one second (3.75 us per failed try_wait)
 
 __device__ int g_conv_pair_status;  // 0 fine; 1 a TMA wait timed out
 

@@ -28,7 +28,7 @@ namespace gbk {
 
 constexpr int kCT = 32;            // output tile edge
 constexpr int kCThreads = 256;     // 8 warps
-constexpr long kWaitLimit = 1L << 24;
+constexpr long kWaitLimit = 1L << 18;  // tries: about one second (3.75 us per failed try_wait)
 
 __device__ int g_conv_status;      // 0 = fine; 1 = a TMA wait timed out
 

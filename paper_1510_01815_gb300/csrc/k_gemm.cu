@@ -29,7 +29,10 @@
 namespace gbk {
 
 constexpr int kGBM = 128, kGBK = 64, kGStages = 4, kGThreads = 128, kGGroup = 16;
-constexpr long kGWaitLimit = 1L << 26;
+// Bounded waits: 2^18 try_wait attempts, about one second (a try that finds
+// its phase incomplete suspends about 3.75 us on GB300, as gbk_wait_selfcheck
+// measures); a TMA load or an MMA stage completes in microseconds.
+constexpr long kGWaitLimit = 1L << 18;
 
 __device__ int g_gemm_status;  // 0 fine; 1 a pipeline wait timed out
 
