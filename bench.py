@@ -1156,6 +1156,20 @@ def run_gbk(args):
                            "traffic": None, "kernel": "staged chain (model cube, conv, moments)",
                            "basis": "%.1f MB algorithmic traffic per model" % (per_model / 1e6),
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+        # per-stage times (CUDA events between the stages, median of 5 calls
+        # with L2 flushed before each) and each stage's algorithmic bytes
+        reps = []
+        for r in range(5):
+            flush.fill_(r & 0xFF)
+            reps.append(gbk.gbk_chi2_stage_times(g, pool[0], obs, chi2[0], ws_staged, stream))
+        med = np.median(np.array(reps), axis=0)
+        ext_b, data_b = 4.0 * ex * ey * ez * n, 4.0 * g.nx * g.ny * g.nz * n
+        stage_bytes = (ext_b, ext_b + data_b, 0.0, data_b)
+        out["stages"] = [{"stage": name, "ms": float(t), "algorithmic_bytes": b_,
+                          "gbs": (b_ / (t * 1e-3) / 1e9) if t > 0 and b_ > 0 else None,
+                          "frac": (b_ / (t * 1e-3) / 1e9 / hbm) if t > 0 and b_ > 0 else None}
+                         for name, t, b_ in zip(("model cube (a1-a2)", "PSF x LSF convolution (a3)",
+                                                 "down-sampling (a4)", "moments + chi2 (a5-a6)"), med, stage_bytes)]
         out["clocks"] = clk
         if rank == 0:
             print(json.dumps(out))

@@ -190,6 +190,16 @@ GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *p
 GBK_API gbk_status gbk_chi2_noalloc(const gbk_geom *g, int32_t n_models, const double *params,
                                     const gbk_obs *obs, double *chi2, float *resid, void *stream);
 
+/* gbk_chi2 on the staged path (GBK_PATH_STAGED), timed per stage with CUDA
+ * events on `stream` -- the per-step timings of the paper's GPU pipeline
+ * (Sec. 5): stage_ms (host [4]) receives the milliseconds of the model cube
+ * (a1-a2), the PSF x LSF convolution (a3), the down-sampling (a4; 0 at
+ * u = 1) and the moments with the masked chi2 (a5-a6).  Workspace as for
+ * gbk_chi2 on the staged path; synchronises `stream`. */
+GBK_API gbk_status gbk_chi2_stage_times(const gbk_geom *g, int32_t n_models, const double *params, const gbk_obs *obs,
+                                        double *chi2, void *workspace, size_t ws_bytes, float *stage_ms,
+                                        void *stream);
+
 /* Eq. 11 alone, from caller-supplied FP32 maps [n_models][3][ny][nx]
  * (device).  Spaxels with m0 <= 0 count as invalid.  Asynchronous; needs
  * no workspace. */

@@ -180,7 +180,7 @@ size_t gbk_workspace_bytes(const gbk_geom *gin, int32_t n_models, uint32_t flags
 
 static gbk_status run_staged(const Geom &g, int32_t n, const double *params, float *cubes, float *maps,
                              const gbk_obs *obs, double *chi2, float *resid, void *ws, size_t ws_bytes,
-                             cudaStream_t st)
+                             cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
     if (g.model != GBK_MODEL_CUBE)
         return fail(GBK_EUNSUPPORTED, "velocity-field models have no cube (the staged path does not apply)");
@@ -216,7 +216,7 @@ static gbk_status run_staged(const Geom &g, int32_t n, const double *params, flo
     a.partials = chi2 ? (double *)(base + L.off_part) : nullptr;
     if (obs) a.obs = *obs;
     bool want_moments = (maps || chi2 || resid);
-    gbk_status s = launch_staged(a, want_moments, st);
+    gbk_status s = launch_staged(a, want_moments, st, ev);
     if (s) return s;
     return ok();
 }
@@ -284,6 +284,32 @@ gbk_status gbk_chi2(const gbk_geom *gin, int32_t n_models, const double *params,
     if (flags == GBK_PATH_STAGED || (flags == GBK_PATH_AUTO && !fused_ok))
         return run_staged(g, n_models, params, nullptr, nullptr, obs, chi2, resid, workspace, ws_bytes, st);
     return run_fused(g, n_models, params, nullptr, obs, chi2, resid, st);
+}
+
+gbk_status gbk_chi2_stage_times(const gbk_geom *gin, int32_t n_models, const double *params, const gbk_obs *obs,
+                                double *chi2, void *workspace, size_t ws_bytes, float *stage_ms, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    if (n_models < 1) return fail(GBK_EINVAL, "n_models must be >= 1");
+    if (!stage_ms) return fail(GBK_EINVAL, "stage_ms is NULL");
+    if ((s = check_device_ptr(params, "params", 8)) || (s = check_device_ptr(chi2, "chi2", 8)) || (s = check_obs(obs)))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[5] = {};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    if (e == cudaSuccess) {
+        s = run_staged(g, n_models, params, nullptr, nullptr, obs, chi2, nullptr, workspace, ws_bytes, st, ev);
+        if (!s) e = cudaEventSynchronize(ev[4]);
+        for (int i = 0; i < 4 && !s && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]);
+    }
+    for (int i = 0; i < 5; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    if (s) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "stage timing");
+    return ok();
 }
 
 gbk_status gbk_chi2_from_maps(int32_t nx, int32_t ny, int32_t n_models, const float *maps, const gbk_obs *obs,

@@ -289,17 +289,24 @@ size_t conv_smem_bytes(const Geom &g)
     return sizeof(float) * (size_t)((2 * g.R + 1) + W + SY * SX + SY * kConvTX + W * kConvTX * kConvTY);
 }
 
-gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream)
+gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream, cudaEvent_t *ev)
 {
     const Geom &g = a.g;
     if (a.n_models == 0) return GBK_OK;
     cudaError_t e;
+    auto mark = [&](int i) -> gbk_status {
+        if (ev && (e = cudaEventRecord(ev[i], stream)) != cudaSuccess) return cuda_fail(e, "stage event");
+        return GBK_OK;
+    };
+    gbk_status sm;
+    if ((sm = mark(0))) return sm;
     {
         long per_model = (long)g.ey * (a.e_pitch / 4);
         long bpm = (per_model + 255) / 256;
         model_cube_kernel<<<(unsigned)(bpm * a.n_models), 256, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "model cube kernel launch");
     }
+    if ((sm = mark(1))) return sm;
     if (conv_pair_supported(g)) {
         gbk_status s = launch_conv_pair(a, stream);
         if (s) return s;
@@ -318,6 +325,7 @@ gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t st
         conv3d_kernel<<<(unsigned)(tiles * a.n_models), kConvTX * kConvTY, smem, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "conv kernel launch");
     }
+    if ((sm = mark(2))) return sm;
     if (g.u > 1) {
         long total = (long)g.nx * g.ny * g.nz * a.n_models;
         long blocks = (total + 255) / 256;
@@ -325,6 +333,7 @@ gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t st
         downsample_kernel<<<(unsigned)blocks, 256, 0, stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "down-sampling kernel launch");
     }
+    if ((sm = mark(3))) return sm;
     if (want_moments) {
         int np = g.nx * g.ny;
         int bpm = (np + 255) / 256;
@@ -335,7 +344,7 @@ gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t st
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "chi2 final kernel launch");
         }
     }
-    return GBK_OK;
+    return mark(4);
 }
 
 cudaError_t launch_chi2_maps(int nx, int ny, int n_models, const float *maps, const gbk_obs &obs,

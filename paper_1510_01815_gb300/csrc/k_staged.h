@@ -29,7 +29,11 @@ struct StagedArgs {
 size_t conv_smem_bytes(const Geom &g);
 bool conv_tma_supported(const Geom &g);
 gbk_status launch_conv_tma(const StagedArgs &a, cudaStream_t stream);
-gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream);
+// ev (optional): five events recorded at the stage boundaries -- before the
+// model cube, after it, after the convolution, after the down-sampling and
+// after the moments and chi2.
+gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t stream,
+                         cudaEvent_t *ev = nullptr);
 cudaError_t launch_chi2_maps(int nx, int ny, int n_models, const float *maps, const gbk_obs &obs,
                              double *chi2, float *resid, cudaStream_t stream);
 

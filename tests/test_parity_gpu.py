@@ -112,6 +112,29 @@ def test_chi2_vs_oracle(G, case, path):
         assert np.all(resid[i][:, obs.mask == 0] == 0)
 
 
+@pytest.mark.parametrize("u", [1, 2])
+def test_stage_times_run_the_staged_chi2(G, u):
+    """gbk_chi2_stage_times computes exactly gbk_chi2 on the staged path and
+    times its stages; the down-sampling stage is empty at u = 1."""
+    g, p, ps = _params("nonsquare", n=4, seed=5)
+    g = g.with_(upsample=u)
+    obs = make_obs(g.with_(upsample=1), p, seed=3)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    par = torch.from_numpy(ps).cuda()
+    ws = G.workspace_for(g, ps.shape[0], G.PATH_STAGED, "cuda")
+    c0 = torch.empty(ps.shape[0], dtype=torch.float64, device="cuda")
+    c1 = torch.empty_like(c0)
+    G.gbk_chi2(g, par, dobs, c0, None, G.PATH_STAGED, ws)
+    ms = G.gbk_chi2_stage_times(g, par, dobs, c1, ws)
+    assert torch.equal(c0, c1)
+    assert len(ms) == 4 and all(t >= 0.0 for t in ms)
+    assert ms[0] > 0.0 and ms[1] > 0.0 and ms[3] > 0.0
+    if u == 1:
+        assert ms[2] < 0.02  # back-to-back events: a few microseconds
+    else:
+        assert ms[2] > 0.0
+
+
 def test_chi2_reduction_on_identical_maps(G):
     """The reduction alone, on the same FP32 maps: 1e-5 relative."""
     g = synth.SINGLE_GEOM
