@@ -1,0 +1,166 @@
+"""Pins of the CNN oracle (oracle/cnn.py) as functions of the module under
+test, so that the same pins check the oracle and the mistakes planted in
+copies of it.  They test it against things it does not compute itself:
+direct convolution loops, finite differences of its own loss, the bit
+structure of the Morton order, the sequential SplitMix64 generator (in
+oracle/fit.py), the He-normal statistics of its initial weights, and closed
+forms of the target map and of Adam's first step."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fit
+
+
+def pin_conv_equals_direct_loops(cnn):
+    rng = np.random.default_rng(1)
+    for p, H, cin, cout in ((4, 8, 3, 5), (2, 6, 4, 3)):
+        x = rng.normal(size=(2, H, H, cin))
+        W = rng.normal(size=(cout, p * p * cin))
+        b = rng.normal(size=cout)
+        got = cnn.conv(x, W, b, p)
+        ref = np.zeros_like(got)
+        for n in range(2):
+            for Y in range(H // p):
+                for X in range(H // p):
+                    for o in range(cout):
+                        acc = b[o]
+                        for dy in range(p):
+                            for dx in range(p):
+                                for c in range(cin):
+                                    acc += W[o, (dy * p + dx) * cin + c] * x[n, p * Y + dy, p * X + dx, c]
+                        ref[n, Y, X, o] = acc
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def pin_morton_structure(cnn):
+    q = np.array([[cnn.morton(y, x, 5) for x in range(32)] for y in range(32)])
+    assert sorted(q.ravel().tolist()) == list(range(1024))           # a bijection
+    for y in range(32):
+        for x in range(32):
+            # the 2 x 2 block of (y, x) is the run q >> 2, its position in the block q & 3
+            assert q[y, x] >> 2 == cnn.morton(y >> 1, x >> 1, 4)
+            assert q[y, x] & 3 == (y & 1) * 2 + (x & 1)
+    f = np.random.default_rng(2).normal(size=(3, 4, 4, 256))
+    np.testing.assert_array_equal(cnn.unflatten(cnn.flatten(f)), f)
+
+
+def _small_problem(cnn, seed=3, n=2):
+    rng = np.random.default_rng(seed)
+    P = np.zeros(cnn.param_count())
+    off = cnn.param_offsets()
+    for l in range(cnn.NL):
+        blk = rng.normal(size=(cnn.C[l], cnn.K[l] + 1)) * math.sqrt(2.0 / cnn.K[l])
+        blk[:, -1] = rng.normal(size=cnn.C[l]) * 0.1
+        P[off[l]:off[l + 1]] = blk.ravel()
+    v = rng.normal(0, 100, size=(n, 64, 64))
+    s = rng.uniform(20, 80, size=(n, 64, 64))
+    mask = (rng.uniform(size=(n, 64, 64)) > 0.1).astype(np.uint8)
+    t = rng.normal(size=(n, 10))
+    return P, cnn.encode(v, s, mask), t
+
+
+def pin_gradient_matches_finite_differences(cnn):
+    P, x, t = _small_problem(cnn)
+    loss, g = cnn.loss_and_grad(P, x, t)
+    off = cnn.param_offsets()
+    rng = np.random.default_rng(4)
+    checked = 0
+    for l in range(cnn.NL):
+        idx = list(rng.choice(np.arange(off[l], off[l + 1]), size=8, replace=False))
+        idx.append(off[l] + cnn.K[l])  # a bias
+        for i in idx:
+            # central differences; a step that crosses a ReLU kink shows as a
+            # step-dependent error, so a miss is re-measured with a smaller step
+            ok = False
+            for h in (1e-6, 1e-7):
+                Pp, Pm = P.copy(), P.copy()
+                Pp[i] += h
+                Pm[i] -= h
+                fd = (cnn.loss_and_grad(Pp, x, t)[0] - cnn.loss_and_grad(Pm, x, t)[0]) / (2 * h)
+                scale = max(abs(fd), abs(g[i]), 1e-8)
+                if abs(fd - g[i]) <= 1e-5 * scale + 1e-9:
+                    ok = True
+                    break
+            assert ok, (l, i, fd, g[i])
+            checked += 1
+    assert checked == 9 * cnn.NL
+
+
+def pin_loss_definition(cnn):
+    P, x, t = _small_problem(cnn, n=3)
+    y, _ = cnn.forward(P, x)
+    loss, _ = cnn.loss_and_grad(P, x, t)
+    assert loss == pytest.approx(float(np.mean((y[:, :10] - t) ** 2)), rel=1e-12)
+
+
+def pin_encode_masks_and_scales(cnn):
+    v = np.full((1, 64, 64), 100.0)
+    s = np.full((1, 64, 64), 50.0)
+    m = np.ones((1, 64, 64), np.uint8)
+    m[0, 3, 5] = 0
+    x = cnn.encode(v, s, m)
+    assert x[0, 0, 0].tolist() == [0.5, 0.5, 1.0, 0.0]
+    assert x[0, 3, 5].tolist() == [0.0, 0.0, 0.0, 0.0]
+
+
+def pin_targets_decode_round_trip(cnn):
+    rng = np.random.default_rng(5)
+    p = np.stack([rng.uniform(25, 38, 50), rng.uniform(25, 38, 50), rng.uniform(0, 360, 50), rng.uniform(20, 80, 50),
+                  rng.uniform(-30, 30, 50), rng.uniform(50, 300, 50), rng.uniform(1, 8, 50), rng.uniform(10, 80, 50),
+                  np.ones(50), rng.uniform(4, 10, 50)], axis=1)
+    t = cnn.targets(p)
+    y = np.zeros((50, 16))
+    y[:, :10] = t
+    q = cnn.decode(y)
+    np.testing.assert_allclose(q, p, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(t[:, 2] ** 2 + t[:, 3] ** 2, 1.0, rtol=1e-12)
+
+
+def pin_counter_splitmix_equals_sequential(cnn):
+    for seed in (0, 12345, (1 << 63) + 7):
+        r = fit.SplitMix64(seed)
+        seq = [r.next() for _ in range(12)]
+        assert [cnn.sm_output(seed, k) for k in range(1, 13)] == seq
+        # normal j = Box-Muller (cosine) of outputs 2j+1, 2j+2 (u1 shifted into (0, 1])
+        for j in range(5):
+            u1 = ((seq[2 * j] >> 11) + 1) / 9007199254740992.0
+            u2 = (seq[2 * j + 1] >> 11) / 9007199254740992.0
+            assert cnn.sm_normal(seed, j) == pytest.approx(math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2),
+                                                           rel=1e-15)
+
+
+def pin_normal_stream_statistics(cnn):
+    z = np.array([cnn.sm_normal(99, j) for j in range(20000)])
+    assert abs(z.mean()) < 4 / math.sqrt(20000)
+    assert abs(z.std() - 1.0) < 0.02
+
+
+def pin_adam_first_step(cnn):
+    g = np.array([1e-3, -2.0, 5e-2, 0.0])
+    P = np.zeros(4)
+    P1, m, v = cnn.adam(P, np.zeros(4), np.zeros(4), g, 1, 1e-2)
+    # bias-corrected first step: -lr g / (|g| + eps)
+    np.testing.assert_allclose(P1, -1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def pin_init_statistics(cnn):
+    """He-normal weights: standard deviation sqrt(2 / K) (sqrt(1 / K) for the
+    last layer) within sampling error, biases zero."""
+    P = cnn.init(7)
+    off = cnn.param_offsets()
+    for l in range(cnn.NL):
+        blk = P[off[l]:off[l + 1]].reshape(cnn.C[l], cnn.K[l] + 1)
+        w, b = blk[:, :-1].ravel(), blk[:, -1]
+        sd = math.sqrt((1.0 if l == cnn.NL - 1 else 2.0) / cnn.K[l])
+        assert np.all(b == 0.0)
+        assert abs(w.std() / sd - 1.0) < 6.0 / math.sqrt(2.0 * w.size), (l, w.std(), sd)
+        assert abs(w.mean()) < 6.0 * sd / math.sqrt(w.size)
+
+
+# fastest first: a mutant test stops at the first pin that fails
+ALL_CNN_PINS = [pin_morton_structure, pin_encode_masks_and_scales, pin_conv_equals_direct_loops,
+                pin_targets_decode_round_trip, pin_adam_first_step, pin_counter_splitmix_equals_sequential,
+                pin_normal_stream_statistics, pin_init_statistics, pin_loss_definition,
+                pin_gradient_matches_finite_differences]

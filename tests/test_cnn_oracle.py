@@ -1,142 +1,11 @@
-"""Pins of the CNN oracle (oracle/cnn.py) against things it does not compute
-itself: direct convolution loops, finite differences of its own loss, the
-bit structure of the Morton order, the sequential SplitMix64 generator, and
-closed forms of the target map and of Adam's first step."""
-import math
-
-import numpy as np
+"""Pins of the CNN oracle (oracle/cnn.py); the pins are in tests/cnn_pins.py,
+shared with the mutant tests."""
 import pytest
 
-from oracle import cnn, fit
+from oracle import cnn
+from cnn_pins import ALL_CNN_PINS
 
 
-def test_conv_equals_direct_loops():
-    rng = np.random.default_rng(1)
-    for p, H, cin, cout in ((4, 8, 3, 5), (2, 6, 4, 3)):
-        x = rng.normal(size=(2, H, H, cin))
-        W = rng.normal(size=(cout, p * p * cin))
-        b = rng.normal(size=cout)
-        got = cnn.conv(x, W, b, p)
-        ref = np.zeros_like(got)
-        for n in range(2):
-            for Y in range(H // p):
-                for X in range(H // p):
-                    for o in range(cout):
-                        acc = b[o]
-                        for dy in range(p):
-                            for dx in range(p):
-                                for c in range(cin):
-                                    acc += W[o, (dy * p + dx) * cin + c] * x[n, p * Y + dy, p * X + dx, c]
-                        ref[n, Y, X, o] = acc
-        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
-
-
-def test_morton_structure():
-    q = np.array([[cnn.morton(y, x, 5) for x in range(32)] for y in range(32)])
-    assert sorted(q.ravel().tolist()) == list(range(1024))           # a bijection
-    for y in range(32):
-        for x in range(32):
-            # the 2 x 2 block of (y, x) is the run q >> 2, its position in the block q & 3
-            assert q[y, x] >> 2 == cnn.morton(y >> 1, x >> 1, 4)
-            assert q[y, x] & 3 == (y & 1) * 2 + (x & 1)
-    f = np.random.default_rng(2).normal(size=(3, 4, 4, 256))
-    np.testing.assert_array_equal(cnn.unflatten(cnn.flatten(f)), f)
-
-
-def _small_problem(seed=3, n=2):
-    rng = np.random.default_rng(seed)
-    P = np.zeros(cnn.param_count())
-    off = cnn.param_offsets()
-    for l in range(cnn.NL):
-        blk = rng.normal(size=(cnn.C[l], cnn.K[l] + 1)) * math.sqrt(2.0 / cnn.K[l])
-        blk[:, -1] = rng.normal(size=cnn.C[l]) * 0.1
-        P[off[l]:off[l + 1]] = blk.ravel()
-    v = rng.normal(0, 100, size=(n, 64, 64))
-    s = rng.uniform(20, 80, size=(n, 64, 64))
-    mask = (rng.uniform(size=(n, 64, 64)) > 0.1).astype(np.uint8)
-    t = rng.normal(size=(n, 10))
-    return P, cnn.encode(v, s, mask), t
-
-
-def test_gradient_matches_finite_differences():
-    P, x, t = _small_problem()
-    loss, g = cnn.loss_and_grad(P, x, t)
-    off = cnn.param_offsets()
-    rng = np.random.default_rng(4)
-    checked = 0
-    for l in range(cnn.NL):
-        idx = list(rng.choice(np.arange(off[l], off[l + 1]), size=8, replace=False))
-        idx.append(off[l] + cnn.K[l])  # a bias
-        for i in idx:
-            # central differences; a step that crosses a ReLU kink shows as a
-            # step-dependent error, so a miss is re-measured with a smaller step
-            ok = False
-            for h in (1e-6, 1e-7):
-                Pp, Pm = P.copy(), P.copy()
-                Pp[i] += h
-                Pm[i] -= h
-                fd = (cnn.loss_and_grad(Pp, x, t)[0] - cnn.loss_and_grad(Pm, x, t)[0]) / (2 * h)
-                scale = max(abs(fd), abs(g[i]), 1e-8)
-                if abs(fd - g[i]) <= 1e-5 * scale + 1e-9:
-                    ok = True
-                    break
-            assert ok, (l, i, fd, g[i])
-            checked += 1
-    assert checked == 9 * cnn.NL
-
-
-def test_loss_definition():
-    P, x, t = _small_problem(n=3)
-    y, _ = cnn.forward(P, x)
-    loss, _ = cnn.loss_and_grad(P, x, t)
-    assert loss == pytest.approx(float(np.mean((y[:, :10] - t) ** 2)), rel=1e-12)
-
-
-def test_encode_masks_and_scales():
-    v = np.full((1, 64, 64), 100.0)
-    s = np.full((1, 64, 64), 50.0)
-    m = np.ones((1, 64, 64), np.uint8)
-    m[0, 3, 5] = 0
-    x = cnn.encode(v, s, m)
-    assert x[0, 0, 0].tolist() == [0.5, 0.5, 1.0, 0.0]
-    assert x[0, 3, 5].tolist() == [0.0, 0.0, 0.0, 0.0]
-
-
-def test_targets_decode_round_trip():
-    rng = np.random.default_rng(5)
-    p = np.stack([rng.uniform(25, 38, 50), rng.uniform(25, 38, 50), rng.uniform(0, 360, 50), rng.uniform(20, 80, 50),
-                  rng.uniform(-30, 30, 50), rng.uniform(50, 300, 50), rng.uniform(1, 8, 50), rng.uniform(10, 80, 50),
-                  np.ones(50), rng.uniform(4, 10, 50)], axis=1)
-    t = cnn.targets(p)
-    y = np.zeros((50, 16))
-    y[:, :10] = t
-    q = cnn.decode(y)
-    np.testing.assert_allclose(q, p, rtol=1e-12, atol=1e-9)
-    np.testing.assert_allclose(t[:, 2] ** 2 + t[:, 3] ** 2, 1.0, rtol=1e-12)
-
-
-def test_counter_splitmix_equals_sequential():
-    for seed in (0, 12345, (1 << 63) + 7):
-        r = fit.SplitMix64(seed)
-        seq = [r.next() for _ in range(12)]
-        assert [cnn.sm_output(seed, k) for k in range(1, 13)] == seq
-        # normal j = Box-Muller (cosine) of outputs 2j+1, 2j+2 (u1 shifted into (0, 1])
-        for j in range(5):
-            u1 = ((seq[2 * j] >> 11) + 1) / 9007199254740992.0
-            u2 = (seq[2 * j + 1] >> 11) / 9007199254740992.0
-            assert cnn.sm_normal(seed, j) == pytest.approx(math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2),
-                                                           rel=1e-15)
-
-
-def test_normal_stream_statistics():
-    z = np.array([cnn.sm_normal(99, j) for j in range(20000)])
-    assert abs(z.mean()) < 4 / math.sqrt(20000)
-    assert abs(z.std() - 1.0) < 0.02
-
-
-def test_adam_first_step():
-    g = np.array([1e-3, -2.0, 5e-2, 0.0])
-    P = np.zeros(4)
-    P1, m, v = cnn.adam(P, np.zeros(4), np.zeros(4), g, 1, 1e-2)
-    # bias-corrected first step: -lr g / (|g| + eps)
-    np.testing.assert_allclose(P1, -1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+@pytest.mark.parametrize("pin", ALL_CNN_PINS, ids=[p.__name__ for p in ALL_CNN_PINS])
+def test_pin(pin):
+    pin(cnn)
