@@ -336,9 +336,35 @@ void og_vfield(const og_geom *g, const double *p, double *maps)
         }
 }
 
+/* Parameter domain (the reading of the parameter ranges shared with the
+ * library): 0 <= i < 90 degrees and r_t > 0 for every model; the cube model
+ * also needs sigma0, I0, h > 0 and all ten values finite; a velocity field
+ * needs sigma0 >= 0 and x0 .. sigma0 finite (and, for the Epinat curve, its
+ * slopes a, g).  Outside it the maps and chi2 are NaN. */
+int og_param_valid(const og_geom *g, const double *p)
+{
+    int ok = p[OG_INCL] >= 0.0 && p[OG_INCL] < 90.0 && p[OG_RT] > 0.0;
+    if (g->model == 0) {
+        ok = ok && p[OG_SIG0] > 0.0 && p[OG_I0] > 0.0 && p[OG_H] > 0.0;
+        for (int k = 0; k < OG_NPAR; ++k) ok = ok && isfinite(p[k]);
+    } else {
+        ok = ok && p[OG_SIG0] >= 0.0;
+        for (int k = 0; k <= OG_SIG0; ++k) ok = ok && isfinite(p[k]);
+        if (g->model == 2) ok = ok && isfinite(p[OG_I0]) && isfinite(p[OG_H]);
+    }
+    return ok;
+}
+
 /* Steps 1-5 of one model: cube (optional output, data resolution) and maps. */
 void og_eval(const og_geom *g, const double *p, double *cube_out, double *maps_out)
 {
+    if (!og_param_valid(g, p)) {
+        if (maps_out)
+            for (int s = 0; s < 3 * g->nx * g->ny; ++s) maps_out[s] = NAN;
+        if (cube_out && g->model == 0)
+            for (size_t s = 0; s < (size_t)g->nx * g->ny * g->nz; ++s) cube_out[s] = NAN;
+        return;
+    }
     if (g->model != 0) {  /* velocity field: no cube */
         if (maps_out) og_vfield(g, p, maps_out);
         return;
@@ -417,9 +443,17 @@ void og_chi2_batch(const og_geom *g, int n, const double *params, const float *v
 #endif
     for (int m = 0; m < n; ++m) {
         double *maps = (double *)malloc(sizeof(double) * 3 * np);
-        og_eval(g, params + (size_t)m * OG_NPAR, NULL, maps);
-        chi2[m] = og_chi2_maps(maps, np, v_obs, s_obs, w_v, w_s, mask,
-                               resid ? resid + (size_t)m * 2 * np : NULL);
+        const double *pm = params + (size_t)m * OG_NPAR;
+        og_eval(g, pm, NULL, maps);
+        if (og_param_valid(g, pm)) {
+            chi2[m] = og_chi2_maps(maps, np, v_obs, s_obs, w_v, w_s, mask,
+                                   resid ? resid + (size_t)m * 2 * np : NULL);
+        } else {  /* outside the domain: NaN, as are the unmasked residuals */
+            chi2[m] = NAN;
+            if (resid)
+                for (int s = 0; s < np; ++s)
+                    resid[(size_t)m * 2 * np + s] = resid[(size_t)m * 2 * np + np + s] = mask[s] != 0 ? NAN : 0.0;
+        }
         free(maps);
     }
     (void)nthreads;

@@ -389,6 +389,39 @@ def pin_chi2_noiseless(og):
     assert c < 1e-9, c
 
 
+def pin_parameter_domain(og):
+    """Where the model is undefined -- i = 90 (Eq. 3 divides by cos i), r_t
+    = 0 (Eq. 6 divides by r_t), sigma0 = 0 (a zero-width Gaussian), h = 0
+    (Eq. 5), I0 <= 0 (no light), a non-finite value -- maps and chi2 are NaN,
+    and so are the residuals of unmasked spaxels (masked ones stay 0); just
+    inside (i = 89.9, i = 0) they are finite.  A velocity field needs only
+    the kinematic values (sigma0 = 0 is a valid constant dispersion)."""
+    G = og.Geom(8, 7, 24, 20.0, 0.0, 2.0, 30.0, 0)
+    ok = P(x0=3.6, y0=3.3)
+    m = np.ones((7, 8))
+    m[2, 3] = 0
+    obs = og.Obs(np.zeros((7, 8)), np.full((7, 8), 30.0), np.full((7, 8), 0.2), np.full((7, 8), 0.1), m)
+    for k, v in ((PAR["incl"], 90.0), (PAR["incl"], 95.0), (PAR["rt"], 0.0), (PAR["sig0"], 0.0),
+                 (PAR["h"], 0.0), (PAR["i0"], 0.0), (PAR["x0"], float("nan")), (PAR["vmax"], float("inf"))):
+        q = ok.copy()
+        q[k] = v
+        assert np.all(np.isnan(og.evaluate(G, q))), (k, v)
+        c, r = og.chi2_batch(G, q[None], obs, want_resid=True)
+        assert np.isnan(c[0]) and np.all(np.isnan(r[0][:, m != 0])) and np.all(r[0][:, m == 0] == 0.0), (k, v)
+    for incl in (0.0, 89.9):
+        q = ok.copy()
+        q[PAR["incl"]] = incl
+        assert np.all(np.isfinite(og.evaluate(G, q))) and np.isfinite(og.chi2_batch(G, q[None], obs)[0]), incl
+    for model in (1, 2):
+        V = og.Geom(8, 7, 1, 20.0, 0.0, 0.0, 0.0, model=model)
+        q = ok.copy()
+        q[PAR["sig0"]] = 0.0
+        q[PAR["i0"]], q[PAR["h"]] = 1.5, 0.8  # the Epinat slopes
+        assert np.all(np.isfinite(og.evaluate(V, q))), model
+        q[PAR["incl"]] = 90.0
+        assert np.all(np.isnan(og.evaluate(V, q))), model
+
+
 def pin_chi2_statistics(og):
     """At the true parameters with Gaussian noise of standard deviation E on
     both maps and weights 1/E, chi2 follows a chi-squared distribution with

@@ -57,6 +57,8 @@ MUTANTS = [
      "rv = (maps[np + s] - (double)v_obs[s]);"),
     ("chi2_mask_ignored", "if (mask[s] != 0 && maps[s] > 0.0) {", "if (maps[s] > 0.0) {"),
     ("chi2_dispersion_term_dropped", "og_add(&acc, rs * rs);", "(void)rs;"),
+    ("parameter_domain_dropped", "int ok = p[OG_INCL] >= 0.0 && p[OG_INCL] < 90.0 && p[OG_RT] > 0.0;", "int ok = 1;"),
+    ("inclination_domain_closed", "p[OG_INCL] < 90.0 && p[OG_RT] > 0.0;", "p[OG_INCL] <= 90.0 && p[OG_RT] > 0.0;"),
 ]
 
 
