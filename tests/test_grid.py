@@ -1,60 +1,20 @@
-"""Nested grids (Sec. 2.3.3): the oracle's search pinned on a case with a
-known answer, then the GPU's gbk_grid against it (argmin index per level)."""
+"""Nested grids (Sec. 2.3.3): the GPU's gbk_grid against the oracle's search
+(argmin index per level) on the case the oracle's pins fix (tests/fit_pins.py)."""
 import numpy as np
 import pytest
 
 import oracle
 from oracle import fit
 from cases import ogeom, make_obs
+from fit_pins import (GRID_GEOM, GRID_HI, GRID_LO, GRID_NODES, GRID_TRUTH, GRID_TRUTH_INDEX,
+                      grid_noiseless_obs)
 from paper_1510_01815_gb300 import synth
 from paper_1510_01815_gb300.synth import Geometry, params as P
 
-GEOM = Geometry(24, 24, 32, 20.0, 0.0, 2.5, 30.0)
-TRUTH = P(11.5, 11.5, 60.0, 50.0, 0.0, 180.0, 3.0, 40.0, 1.0, 4.0)
-NODES = [1, 1, 5, 4, 1, 5, 3, 3, 1, 1]
-# bounds chosen so that the truth sits on node (PA 2, i 2, Vmax 2, rt 1, sig 1)
-LO = TRUTH.copy(); HI = TRUTH.copy()
-LO[2], HI[2] = 40.0, 80.0          # step 10
-LO[3], HI[3] = 30.0, 60.0          # step 10
-LO[5], HI[5] = 140.0, 220.0        # step 20
-LO[6], HI[6] = 2.0, 4.0            # step 1
-LO[7], HI[7] = 30.0, 50.0          # step 10
-TRUTH_INDEX = (((2 * 4 + 2) * 5 + 2) * 3 + 1) * 3 + 1
-
-
-def noiseless_obs():
-    m = oracle.evaluate(ogeom(GEOM), TRUTH)
-    wv, ws = synth.weights((GEOM.ny, GEOM.nx), 5.0)
-    return oracle.Obs(m[1].astype(np.float32), m[2].astype(np.float32), wv, ws,
-                      np.ones((GEOM.ny, GEOM.nx), np.uint8))
-
-
-def test_oracle_grid_finds_truth_on_a_node():
-    obs = noiseless_obs()
-    bp, bi, bc, allc = fit.grid_search(ogeom(GEOM), obs, LO, HI, NODES, TRUTH, levels=2)
-    assert bi[0] == TRUTH_INDEX, bi
-    assert bc[0] < 1e-8
-    assert np.sum(allc[0] < 1e-8) == 1           # unique minimum
-    # level 1 spans truth +- one level-0 step (4 inclination nodes put no
-    # node on the centre): its optimum stays within one step of the truth
-    steps0 = (HI - LO) / np.maximum(np.array(NODES) - 1, 1)
-    assert np.all(np.abs(bp - TRUTH) <= steps0 + 1e-12), bp - TRUTH
-    assert bc[1] >= 0.0
-
-
-def test_oracle_grid_row_major_order():
-    """A 1-D grid over PA: chi2 per node equals the direct evaluation at the
-    node's value, in order."""
-    obs = noiseless_obs()
-    nodes = [1] * 10
-    nodes[2] = 7
-    lo, hi = TRUTH.copy(), TRUTH.copy()
-    lo[2], hi[2] = 0.0, 120.0
-    bp, bi, bc, allc = fit.grid_search(ogeom(GEOM), obs, lo, hi, nodes, TRUTH, levels=1)
-    vals = np.array([TRUTH] * 7)
-    vals[:, 2] = np.arange(7) * 20.0
-    np.testing.assert_allclose(allc[0], oracle.chi2_batch(ogeom(GEOM), vals, obs), rtol=1e-12)
-    assert bi[0] == 3
+# the case with the truth on a node, shared with the oracle's pins (fit_pins)
+GEOM, TRUTH, NODES, LO, HI = GRID_GEOM, GRID_TRUTH, GRID_NODES, GRID_LO, GRID_HI
+TRUTH_INDEX = GRID_TRUTH_INDEX
+noiseless_obs = grid_noiseless_obs
 
 
 @pytest.mark.gpu
