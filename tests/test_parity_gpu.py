@@ -184,11 +184,14 @@ def test_invalid_parameters_give_nan(G):
     ps[3, synth.RT] = np.nan
     obs = make_obs(g, synth.SINGLE_TRUTH, seed=1)
     dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    ref = oracle.chi2_batch(ogeom(g), ps, obs)  # the same parameter domain on both sides
     for flags in (G.PATH_FUSED, G.PATH_STAGED):
         c = G.chi2(g, torch.from_numpy(ps), dobs, flags=flags).cpu().numpy()
         assert np.isfinite(c[0]) and np.all(np.isnan(c[1:])), (flags, c)
+        assert np.array_equal(np.isnan(c), np.isnan(ref)), (flags, c, ref)
     maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
     assert np.isfinite(maps[0]).all() and np.isnan(maps[1:]).all()
+    assert np.array_equal(np.isnan(maps), np.isnan(oracle.evaluate_batch(ogeom(g), ps)))
 
 
 def test_fused_and_staged_agree(G):
