@@ -49,9 +49,11 @@ OPS_PER_EXT_VOXEL = FMA_OPS_PER_EXT_VOXEL + MUFU_OPS_PER_EXT_VOXEL
 OPS_PER_PSF_TAP = 9
 OPS_PER_DATA_SPAXEL = 10
 # Per-unit work of the unfolded method (cube + separable PSF x LSF
-# convolution + moments) at the Fabry-Perot size: FP32 instructions per data
-# voxel, as the hot-path scope table states it.
-SURVEY_FP32_PER_DATA_VOXEL = 47.0
+# convolution + moments) at the Fabry-Perot size, in FP32 instructions per
+# data voxel: the line (an ex2 and 3 FP32 per extended voxel, 1.41 extended
+# voxels per data voxel), the separable convolution's 13-tap passes on the
+# shrinking cube (about 40) and the moments (3) -- about 47.
+UNFOLDED_FP32_PER_DATA_VOXEL = 47.0
 # DRAM bytes (read + write) of one fused launch of 400 Fabry-Perot models per
 # tuning (CTAs per model, threads, persistent), from the one-pass ncu
 # captures summarised in profiles/fused_eval_fabry_perot_400models.md.
@@ -1206,13 +1208,13 @@ def run_gbk(args):
                                    rfma / 1e12, r32 / 1e12, r32x2 / 1e12, rmu / 1e12),
                        "peak_source": "measured on this device by gbk_measure_alu_peak"}
     data_vox = g.nx * g.ny * g.nz
-    sv = SURVEY_FP32_PER_DATA_VOXEL * data_vox * n / (ms_step * 1e-3)
+    sv = UNFOLDED_FP32_PER_DATA_VOXEL * data_vox * n / (ms_step * 1e-3)
     out["roofline_unfolded_basis"] = {
         "achieved": sv / 1e12, "peak": rfma / 1e12, "unit": "T FP32 instr/s", "frac": sv / rfma,
         "basis": "%.0f FP32 instructions per data voxel of the unfolded cube + separable convolution + moments "
                  "method; the fused kernel reaches the same result with far fewer operations (z convolution "
                  "folded into channel weights, PSF applied to moment triplets), so this is an effective rate"
-                 % SURVEY_FP32_PER_DATA_VOXEL}
+                 % UNFOLDED_FP32_PER_DATA_VOXEL}
     out["clocks"] = clk
 
     # ---- end to end through the public API with host buffers ----
