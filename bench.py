@@ -793,7 +793,7 @@ def run_ns_fp(gbk, torch, device, n_gal=2, n_live=400, batch=100):
 def run_jacobian(gbk, torch, device, n=2048, geom=None):
     """The analytic Jacobian kernel (gbk_jacobian: J^T J, J^T r and chi2 of
     the eight free parameters, J not written) on n models of one geometry
-    (default the single-galaxy C1 cube), against the 1 + 8 fused
+    (default the single-galaxy 32 x 32 x 64 cube), against the 1 + 8 fused
     evaluations a forward-difference Jacobian needs for the same models."""
     g = geom or synth.SINGLE_GEOM
     rng = np.random.default_rng(9)
@@ -871,7 +871,7 @@ def run_grid(gbk, torch, device, chunk=1 << 17):
 
 def run_degeneracy(gbk, torch, device):
     """The V_t - i degeneracy (Sec. 6.1): reduced chi-squared maps over
-    (i, V_t) of C1-like mocks with V_t = 200 km/s at i = 20, 40, 60, 70 deg and
+    (i, V_t) of single-galaxy 32 x 32 x 64 mocks with V_t = 200 km/s at i = 20, 40, 60, 70 deg and
     5 / 5 sqrt(2) km/s noise; every map is one gbk_chi2 launch over a
     0.25 deg x 1 km/s grid.  Reports the best node and the extents of the
     1 and 3 sigma regions (chi2 - min <= 2.30, 11.83)."""
@@ -882,7 +882,7 @@ def run_degeneracy(gbk, torch, device):
     wv, ws = synth.weights((g.ny, g.nx), 5.0)
     dwv, dws = torch.from_numpy(wv).to(device), torch.from_numpy(ws).to(device)
     ones = torch.ones((g.ny, g.nx), dtype=torch.uint8, device=device)
-    out = {"workload": "C1 geometry (32x32x64), V_t = 200 km/s, noise 5 / 5 sqrt(2) km/s, %d x %d (i, V_t) nodes "
+    out = {"workload": "single-galaxy geometry (32x32x64), V_t = 200 km/s, noise 5 / 5 sqrt(2) km/s, %d x %d (i, V_t) nodes "
                        "per map, other parameters at the truth" % (len(inc_ax), len(vt_ax)), "maps": {}}
     total_ms, total_models = 0.0, 0
     for inc in (20.0, 40.0, 60.0, 70.0):
