@@ -85,6 +85,18 @@ def pin_lm_solves_a_linear_problem_in_one_step(fit):
     assert abs(q[synth.VSYS]) < 25.0 * 2e-3, q[synth.VSYS]
 
 
+def pin_lm_central_differences_solve_the_linear_problem(fit):
+    """The same linear problem with central differences: (r(p + h) - r(p -
+    h)) / 2h of a linear residual is its exact slope, so the first step lands
+    within the damping's 0.1 percent as well."""
+    g, p, obs = galaxy(noise_v=0.0)
+    lo, hi = bounds(p)
+    p0 = p.copy()
+    p0[synth.VSYS] = 25.0
+    q, c, it, st = fit.fit_lm(ogeom(g), obs, p0, lo, hi, [synth.VSYS], max_iter=1, fd_step=0.1, central=True)
+    assert abs(q[synth.VSYS]) < 25.0 * 2e-3, q[synth.VSYS]
+
+
 def pin_lm_optimum_outside_the_box_ends_on_its_face(fit):
     """Noiseless data with V_max = 200 fitted with V_max free and capped at
     180: chi2 falls monotonically towards the cap, so the fit ends exactly on
@@ -163,6 +175,7 @@ def pin_grid_finds_truth_on_a_node(fit):
 
 # fastest first: a mutant test stops at the first pin that fails
 ALL_FIT_PINS = [pin_splitmix64_reference_values, pin_sampler_gaussian_evidence,
-                pin_lm_solves_a_linear_problem_in_one_step, pin_grid_row_major_order, pin_grid_invalid_nodes_lose,
+                pin_lm_solves_a_linear_problem_in_one_step, pin_lm_central_differences_solve_the_linear_problem,
+                pin_grid_row_major_order, pin_grid_invalid_nodes_lose,
                 pin_lm_optimum_outside_the_box_ends_on_its_face, pin_lm_recovers_noiseless_parameters,
                 pin_grid_finds_truth_on_a_node]

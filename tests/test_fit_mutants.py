@@ -17,6 +17,8 @@ MUTANTS = [
     ("lm_accepts_rises", "if np.isfinite(ct) and ct <= cc and dn > 0:", "if np.isfinite(ct) and ct >= cc and dn > 0:"),
     ("lm_jacobian_sign", "J = np.stack([(r[1 + j].ravel() - r0) / hs[j] for j in range(nf)], axis=1)",
      "J = np.stack([(r0 - r[1 + j].ravel()) / hs[j] for j in range(nf)], axis=1)"),
+    ("lm_central_step_not_doubled", "hs.append(2 * h)", "hs.append(h)"),
+    ("lm_central_minus_side_forward", "q[k] = p[k] - steps[k]", "q[k] = p[k] + steps[k]"),
     ("lm_trial_not_clipped", "pt[k] = min(max(p[k] + d[j], lo[k]), hi[k])", "pt[k] = p[k] + d[j]"),
     ("lm_damping_grows_on_success", "lam = max(lam * 0.1, 1e-12)", "lam = lam * 10.0"),
     ("grid_nan_not_worst", "key = np.where(np.isnan(c), np.inf, c)", "key = c"),
