@@ -159,8 +159,35 @@ def pin_init_statistics(cnn):
         assert abs(w.mean()) < 6.0 * sd / math.sqrt(w.size)
 
 
+def pin_synthetic_observations(cnn):
+    """synth_obs on one 64 x 64 map: with no noise and no dead fibres it
+    returns the model maps (masked where m0 = 0); with every fibre dead it
+    masks everything; with noise, (v - m1) / noise and (s - m2) / (sqrt 2
+    noise) are standard normal and uncorrelated (distinct numbers of the
+    stream), and the dead fraction is the one asked for."""
+    rng = np.random.default_rng(8)
+    maps = np.stack([rng.uniform(0.0, 1.0, (64, 64)), rng.normal(0, 100, (64, 64)),
+                     rng.uniform(10, 80, (64, 64))])[None]
+    maps[0, 0, :3, :] = 0.0  # three rows without light
+    out = np.array(cnn.synth_obs(maps, 5, 0.0, 0.0))
+    np.testing.assert_array_equal(out[:, 0], maps[0, 1].ravel())
+    np.testing.assert_array_equal(out[:, 1], maps[0, 2].ravel())
+    np.testing.assert_array_equal(out[:, 2], (maps[0, 0].ravel() > 0).astype(float))
+    assert np.all(np.array(cnn.synth_obs(maps, 5, 0.0, 1.0))[:, 2] == 0)
+    out = np.array(cnn.synth_obs(maps, 5, 5.0, 0.02))
+    zv = (out[:, 0] - maps[0, 1].ravel()) / 5.0
+    zs = (out[:, 1] - maps[0, 2].ravel()) / (5.0 * math.sqrt(2.0))
+    n = zv.size
+    for z in (zv, zs):
+        assert abs(z.mean()) < 5.0 / math.sqrt(n) and abs(z.std() - 1.0) < 0.05
+    assert abs(np.corrcoef(zv, zs)[0, 1]) < 5.0 / math.sqrt(n)
+    lit = maps[0, 0].ravel() > 0
+    dead = np.mean(out[lit, 2] == 0)
+    assert abs(dead - 0.02) < 5.0 * math.sqrt(0.02 * 0.98 / lit.sum()), dead
+
+
 # fastest first: a mutant test stops at the first pin that fails
 ALL_CNN_PINS = [pin_morton_structure, pin_encode_masks_and_scales, pin_conv_equals_direct_loops,
                 pin_targets_decode_round_trip, pin_adam_first_step, pin_counter_splitmix_equals_sequential,
-                pin_normal_stream_statistics, pin_init_statistics, pin_loss_definition,
+                pin_normal_stream_statistics, pin_synthetic_observations, pin_init_statistics, pin_loss_definition,
                 pin_gradient_matches_finite_differences]

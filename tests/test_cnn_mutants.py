@@ -42,6 +42,12 @@ MUTANTS = [
      "z = ((z ^ (z >> 31)) * 0xBF58476D1CE4E5B9) & M64"),
     ("box_muller_sine_branch", "return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)",
      "return math.sqrt(-2.0 * math.log(u1)) * math.sin(2.0 * math.pi * u2)"),
+    ("synth_same_normal_for_v_and_s", "s = m2 + math.sqrt(2.0) * noise_v * sm_normal(seed, 2 * i + 1)",
+     "s = m2 + math.sqrt(2.0) * noise_v * sm_normal(seed, 2 * i)"),
+    ("synth_sigma_noise_not_scaled", "s = m2 + math.sqrt(2.0) * noise_v * sm_normal(seed, 2 * i + 1)",
+     "s = m2 + noise_v * sm_normal(seed, 2 * i + 1)"),
+    ("synth_dead_test_inverted", "dead = sm_uniform(seed ^ 0xD1B54A32D192ED03, i) < dead_frac",
+     "dead = sm_uniform(seed ^ 0xD1B54A32D192ED03, i) > dead_frac"),
     ("init_std_halved", "sd = math.sqrt((1.0 if l == NL - 1 else 2.0) / K[l])",
      "sd = math.sqrt((1.0 if l == NL - 1 else 1.0) / K[l])"),
 ]
