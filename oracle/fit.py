@@ -169,7 +169,7 @@ class SplitMix64:
         return float(np.sqrt(-2.0 * np.log(u1)) * np.cos(2 * np.pi * u2))
 
 
-def nested_sample(loglike, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, max_iter=100000):
+def nested_sample(loglike, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, max_iter=100000, trace=None):
     """Vanilla nested sampling with an ellipsoidal bound (Sec. 2.3.2 reading):
     live points from the uniform prior over [lo, hi]; each iteration draws
     `batch` points uniformly in the live points' bounding ellipsoid (volume
@@ -178,7 +178,10 @@ def nested_sample(loglike, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, max_
     stop when ln(Z + Lmax X) - ln Z < tol.  `loglike(params [n][10])`
     returns log L per row.  Returns dict(mean, std, log_z, n_eval, n_iter,
     info) where info is the information H used for the log Z error
-    sqrt(H / N)."""
+    sqrt(H / N).  A dict passed as `trace` receives the trajectory: the
+    initial live points and their log L ("live0", "live0_logl"), and per
+    iteration the proposals in draw order, their log L and the index of the
+    live point each replaced, -1 for none ("props", "logl", "replaced")."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     ax = [k for k in range(10) if hi[k] > lo[k]]
@@ -191,6 +194,8 @@ def nested_sample(loglike, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, max_
             live[i, k] = lo[k] + (hi[k] - lo[k]) * rng.uniform() if hi[k] > lo[k] else lo[k]
     logl = np.asarray(loglike(live), dtype=np.float64)
     n_eval = N
+    if trace is not None:
+        trace.update(live0=live.copy(), live0_logl=logl.copy(), props=[], logl=[], replaced=[])
     dead_p, dead_lw, dead_l = [], [], []
     logz, logx = -np.inf, 0.0
     log_shrink = np.log(-np.expm1(-1.0 / N))
@@ -221,10 +226,16 @@ def nested_sample(loglike, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, max_
         props = np.array(props)
         lp = np.asarray(loglike(props), dtype=np.float64)
         n_eval += len(props)
+        repl = np.full(len(props), -1)
+        if trace is not None:
+            trace["props"].append(props.copy())
+            trace["logl"].append(lp.copy())
+            trace["replaced"].append(repl)
         for j in range(len(props)):
             w = int(np.argmin(logl))
             if not lp[j] > logl[w]:
                 continue
+            repl[j] = w
             lw = logx + log_shrink + logl[w]
             logz = np.logaddexp(logz, lw)
             dead_p.append(live[w].copy())
@@ -248,7 +259,11 @@ def nested_sample(loglike, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, max_
     return {"mean": mean, "std": std, "log_z": float(logz), "n_eval": n_eval, "n_iter": it, "info": info}
 
 
-def nested_sample_model(geom, obs, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, nthreads=0):
-    """Nested sampling of the disc model: L = exp(-chi2 / 2) from the oracle."""
-    return nested_sample(lambda p: -0.5 * chi2_batch(geom, p, obs, nthreads=nthreads), lo, hi, n_live, batch,
-                         tol, efr, seed)
+def nested_sample_model(geom, obs, lo, hi, n_live, batch, tol=0.5, efr=1.0, seed=1, nthreads=0, max_iter=100000,
+                        trace=None):
+    """Nested sampling of the disc model: L = exp(-chi2 / 2) from the oracle;
+    outside the parameter domain (chi2 NaN) the likelihood is 0, log L = -inf."""
+    def loglike(p):
+        c = chi2_batch(geom, p, obs, nthreads=nthreads)
+        return np.where(np.isfinite(c), -0.5 * c, -np.inf)
+    return nested_sample(loglike, lo, hi, n_live, batch, tol, efr, seed, max_iter=max_iter, trace=trace)

@@ -12,7 +12,8 @@ violated.  They test it against what fixes the answer independently:
           node's value; invalid (NaN) nodes lose to finite ones; the next
           level's nodes are the documented box around the best node;
   NS   -- SplitMix64's published first outputs; the closed-form evidence of
-          a Gaussian likelihood in a box."""
+          a Gaussian likelihood in a box; the recorded trajectory replays
+          as the run; L = 0 outside the parameter domain."""
 import math
 
 import numpy as np
@@ -174,8 +175,60 @@ def pin_grid_finds_truth_on_a_node(fit):
 
 
 # fastest first: a mutant test stops at the first pin that fails
+def pin_sampler_trace_replays(fit):
+    """The recorded trajectory is the run: replaying the replacements from
+    the initial live points, each proposal either beat the worst live point
+    of that moment and took its place, or did not beat it and was dropped;
+    every proposal lies inside the prior box."""
+    d = 3
+    lo, hi = np.zeros(10), np.zeros(10)
+    lo[:d], hi[:d] = -2.0, 2.0
+
+    def loglike(p):
+        x = p[:, :d] - 0.3
+        return -0.5 * np.sum(x * x, axis=1) / 0.09
+
+    tr = {}
+    r = fit.nested_sample(loglike, lo, hi, n_live=40, batch=10, tol=1e-6, seed=3, max_iter=30, trace=tr)
+    assert r["n_iter"] == 30 and len(tr["props"]) == 30
+    logl = tr["live0_logl"].copy()
+    np.testing.assert_array_equal(logl, loglike(tr["live0"]))
+    n_repl = 0
+    for props, lp, repl in zip(tr["props"], tr["logl"], tr["replaced"]):
+        assert np.all(props >= lo) and np.all(props <= hi)
+        np.testing.assert_array_equal(lp, loglike(props))
+        for j in range(len(props)):
+            w = int(np.argmin(logl))
+            if lp[j] > logl[w]:
+                assert repl[j] == w, (j, repl[j], w)
+                logl[w] = lp[j]
+                n_repl += 1
+            else:
+                assert repl[j] == -1, (j, repl[j])
+    assert n_repl > 50
+
+
+def pin_sampler_outside_the_domain_has_zero_likelihood(fit):
+    """A prior box that reaches past the parameter domain (i up to 100 deg;
+    the disc model is undefined at i >= 90) on noiseless data: points outside
+    have L = 0, so they are the first replaced and never come back; the
+    evidence and the posterior stay finite, the posterior inside the domain."""
+    g = Geometry(10, 10, 16, 20.0, 0.0, 2.0, 30.0)
+    p = P(4.6, 4.4, 40.0, 60.0, 0.0, 150.0, 2.0, 40.0, 1.0, 3.0)
+    m = oracle.evaluate(ogeom(g), p)
+    wv, ws = synth.weights((g.ny, g.nx), 5.0)
+    obs = oracle.Obs(m[1].astype(np.float32), m[2].astype(np.float32), wv, ws, np.ones((g.ny, g.nx), np.uint8))
+    lo, hi = p.copy(), p.copy()
+    lo[synth.INCL], hi[synth.INCL] = 30.0, 100.0
+    lo[synth.VMAX], hi[synth.VMAX] = 80.0, 250.0
+    r = fit.nested_sample_model(ogeom(g), obs, lo, hi, n_live=30, batch=8, tol=0.5, seed=4, max_iter=400)
+    assert np.isfinite(r["log_z"]) and np.all(np.isfinite(r["mean"]))
+    assert r["mean"][synth.INCL] < 90.0 and abs(r["mean"][synth.INCL] - 60.0) < 5.0, r["mean"][synth.INCL]
+
+
 ALL_FIT_PINS = [pin_splitmix64_reference_values, pin_sampler_gaussian_evidence,
                 pin_lm_solves_a_linear_problem_in_one_step, pin_lm_central_differences_solve_the_linear_problem,
                 pin_grid_row_major_order, pin_grid_invalid_nodes_lose,
                 pin_lm_optimum_outside_the_box_ends_on_its_face, pin_lm_recovers_noiseless_parameters,
-                pin_grid_finds_truth_on_a_node]
+                pin_grid_finds_truth_on_a_node, pin_sampler_trace_replays,
+                pin_sampler_outside_the_domain_has_zero_likelihood]

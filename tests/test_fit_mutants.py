@@ -32,6 +32,8 @@ MUTANTS = [
     ("ns_takes_worse_points", "if not lp[j] > logl[w]:", "if not lp[j] < logl[w]:"),
     ("ns_final_live_points_unweighted", "lw = logx - np.log(N) + logl[i]", "lw = logx + logl[i]"),
     ("ns_posterior_weights_unnormalised", "wgt = np.exp(np.array(dead_lw) - logz)", "wgt = np.exp(np.array(dead_lw))"),
+    ("ns_nan_likelihood_outside_domain", "return np.where(np.isfinite(c), -0.5 * c, -np.inf)", "return -0.5 * c"),
+    ("ns_trace_records_the_best_not_the_worst", "w = int(np.argmin(logl))", "w = int(np.argmax(logl))"),
 ]
 
 
