@@ -66,9 +66,24 @@ def morton(y, x, bits):
     return q
 
 
-def encode(v, s, mask):
-    """x [n][64][64][4] from maps [n][64][64] (the fourth channel is zero)."""
+def bf16(x):
+    """Round to the nearest BF16 value (8 significant bits, ties to even),
+    returned in FP64.  For the BF16 form of the network below; the values
+    met there are normal numbers of FP32's exponent range, and 0."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)  # x = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)
+
+
+def encode(v, s, mask, rounding=None):
+    """x [n][64][64][4] from maps [n][64][64] (the fourth channel is zero).
+    rounding="bf16": the BF16 input of the low-precision form (the scaled
+    values taken in FP32, then rounded to BF16)."""
     m = (np.asarray(mask) != 0).astype(np.float64)
+    if rounding == "bf16":
+        sv = (np.asarray(v, np.float32) / np.float32(V_SCALE)).astype(np.float64)
+        ss = (np.asarray(s, np.float32) / np.float32(S_SCALE)).astype(np.float64)
+        return np.stack([bf16(sv) * m, bf16(ss) * m, m, np.zeros_like(m)], axis=-1)
     return np.stack([np.asarray(v, np.float64) / V_SCALE * m, np.asarray(s, np.float64) / S_SCALE * m, m,
                      np.zeros_like(m)], axis=-1)
 
@@ -121,37 +136,57 @@ def unflatten(f):
     return h
 
 
-def forward(P, x):
-    """Outputs [n][16] and the activations needed by backward()."""
-    L = unpack(P)
+def _rounder(rounding):
+    if rounding is None:
+        return lambda a: a
+    if rounding == "bf16":
+        return bf16
+    raise ValueError("rounding must be None or 'bf16'")
+
+
+def forward(P, x, rounding=None):
+    """Outputs [n][16] and the activations needed by backward().
+
+    rounding=None: the network in FP64.  rounding="bf16": its low-precision
+    form, the values the products read rounded to BF16 -- the weights (the
+    biases stay as given), and each hidden layer's output after the ReLU --
+    with every sum still exact in FP64; x is then expected from
+    encode(..., rounding="bf16")."""
+    q = _rounder(rounding)
+    L = [(q(W), b) for W, b in unpack(P)]
     hs = [x]
     for l in range(4):
-        hs.append(np.maximum(conv(hs[-1], *L[l], P_SIZE[l]), 0.0))
+        hs.append(q(np.maximum(conv(hs[-1], *L[l], P_SIZE[l]), 0.0)))
     f = flatten(hs[-1])
-    h5 = np.maximum(f @ L[4][0].T + L[4][1], 0.0)
+    h5 = q(np.maximum(f @ L[4][0].T + L[4][1], 0.0))
     y = h5 @ L[5][0].T + L[5][1]
     return y, (hs, f, h5)
 
 
-def loss_and_grad(P, x, t):
-    """Mean squared error over the 10 used outputs and its gradient."""
-    L = unpack(P)
-    y, (hs, f, h5) = forward(P, x)
+def loss_and_grad(P, x, t, rounding=None):
+    """Mean squared error over the 10 used outputs and its gradient.
+    rounding="bf16" (see forward): also the output gradient dL/dy and each
+    back-propagated gradient (after its ReLU mask) are rounded to BF16
+    before the products that read them; the parameter gradients are exact
+    sums of those products."""
+    q = _rounder(rounding)
+    L = [(q(W), b) for W, b in unpack(P)]
+    y, (hs, f, h5) = forward(P, x, rounding)
     n = x.shape[0]
     d = np.zeros_like(y)
     d[:, :N_T] = y[:, :N_T] - t
     loss = float(np.sum(d * d) / (n * N_T))
-    dy = 2.0 * d / (n * N_T)
+    dy = q(2.0 * d / (n * N_T))
     g6 = (dy.T @ h5, dy.sum(0))
-    dz5 = (dy @ L[5][0]) * (h5 > 0)
+    dz5 = q((dy @ L[5][0]) * (h5 > 0))
     g5 = (dz5.T @ f, dz5.sum(0))
-    dz = unflatten(dz5 @ L[4][0]) * (hs[4] > 0)
+    dz = q(unflatten(dz5 @ L[4][0]) * (hs[4] > 0))
     grads = []
     for l in range(3, -1, -1):
         W, b, dh = conv_backward(hs[l], L[l][0], dz, P_SIZE[l])
         grads.insert(0, (W, b))
         if l > 0:
-            dz = dh * (hs[l] > 0)
+            dz = q(dh * (hs[l] > 0))
     return loss, pack(grads + [g5, g6])
 
 

@@ -2,7 +2,7 @@
 test, so that the same pins check the oracle and the mistakes planted in
 copies of it.  They test it against things it does not compute itself:
 direct convolution loops, finite differences of its own loss, the bit
-structure of the Morton order, the sequential SplitMix64 generator (in
+structure of the Morton order, PyTorch's BF16 conversion, the sequential SplitMix64 generator (in
 oracle/fit.py), the He-normal statistics of its initial weights, and closed
 forms of the target map and of Adam's first step."""
 import math
@@ -186,8 +186,53 @@ def pin_synthetic_observations(cnn):
     assert abs(dead - 0.02) < 5.0 * math.sqrt(0.02 * 0.98 / lit.sum()), dead
 
 
+def pin_bf16_rounding_matches_the_library(cnn):
+    """bf16() is round-to-nearest-even to 8 significant bits: on FP32 values
+    (random, and exact ties, halfway between two BF16 neighbours) it equals
+    PyTorch's float32 -> bfloat16 conversion."""
+    import torch
+    rng = np.random.default_rng(21)
+    x = (rng.normal(size=4000) * 10.0 ** rng.uniform(-6, 6, size=4000)).astype(np.float32)
+    bits = x.view(np.uint32)
+    ties = ((bits & np.uint32(0xFFFF0000)) | np.uint32(0x8000)).view(np.float32)  # halfway cases
+    for v in (x, ties, np.array([0.0, -0.0, 1.0, -3.0, 2.0 ** -120], np.float32)):
+        ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+        np.testing.assert_array_equal(cnn.bf16(v.astype(np.float64)), ref)
+
+
+def pin_bf16_form_rounds_where_stated(cnn):
+    """The BF16 form reads BF16 values only: its encoded input, every hidden
+    activation and the flattened features are BF16 numbers (bf16(h) == h) and
+    non-negative after the ReLU; it stays within BF16 rounding (relative
+    2^-9 per value, compounded over six layers) of the FP64 network; and
+    with no rounding it is the FP64 network itself."""
+    rng = np.random.default_rng(22)
+    n = 2
+    P = np.zeros(cnn.param_count())
+    off = cnn.param_offsets()
+    for l in range(cnn.NL):
+        blk = rng.normal(size=(cnn.C[l], cnn.K[l] + 1)) * math.sqrt(2.0 / cnn.K[l])
+        blk[:, -1] = 0.05 * rng.normal(size=cnn.C[l])
+        P[off[l]:off[l + 1]] = blk.ravel()
+    v = rng.normal(0, 100, size=(n, 64, 64)).astype(np.float32)
+    s = rng.uniform(20, 80, size=(n, 64, 64)).astype(np.float32)
+    m = (rng.uniform(size=(n, 64, 64)) > 0.1).astype(np.uint8)
+    xb = cnn.encode(v, s, m, rounding="bf16")
+    np.testing.assert_array_equal(cnn.bf16(xb), xb)
+    assert np.all(xb[..., 2] == (m != 0)) and np.all(xb[..., 3] == 0) and np.all(xb[m == 0] == 0)
+    yb, (hs, f, h5) = cnn.forward(P, xb, rounding="bf16")
+    for h in hs[1:] + [f, h5]:
+        np.testing.assert_array_equal(cnn.bf16(h), h)
+        assert h.min() >= 0.0
+    x = cnn.encode(v, s, m)
+    y, _ = cnn.forward(P, x)
+    assert np.linalg.norm(yb - y) <= 2e-2 * np.linalg.norm(y), np.linalg.norm(yb - y) / np.linalg.norm(y)
+    np.testing.assert_array_equal(cnn.forward(P, x, rounding=None)[0], y)
+
+
 # fastest first: a mutant test stops at the first pin that fails
-ALL_CNN_PINS = [pin_morton_structure, pin_encode_masks_and_scales, pin_conv_equals_direct_loops,
+ALL_CNN_PINS = [pin_morton_structure, pin_encode_masks_and_scales, pin_bf16_rounding_matches_the_library,
+                pin_conv_equals_direct_loops, pin_bf16_form_rounds_where_stated,
                 pin_targets_decode_round_trip, pin_adam_first_step, pin_counter_splitmix_equals_sequential,
                 pin_normal_stream_statistics, pin_synthetic_observations, pin_init_statistics, pin_loss_definition,
                 pin_gradient_matches_finite_differences]

@@ -27,9 +27,9 @@ MUTANTS = [
     ("conv_bias_dropped", "out = np.zeros((x.shape[0], x.shape[1] // p, x.shape[2] // p, Cout)) + b",
      "out = np.zeros((x.shape[0], x.shape[1] // p, x.shape[2] // p, Cout))"),
     ("loss_mean_over_samples_only", "loss = float(np.sum(d * d) / (n * N_T))", "loss = float(np.sum(d * d) / n)"),
-    ("gradient_factor_two_dropped", "dy = 2.0 * d / (n * N_T)", "dy = d / (n * N_T)"),
-    ("dense_relu_mask_dropped", "dz5 = (dy @ L[5][0]) * (h5 > 0)", "dz5 = (dy @ L[5][0])"),
-    ("conv_relu_mask_dropped", "dz = dh * (hs[l] > 0)", "dz = dh"),
+    ("gradient_factor_two_dropped", "dy = q(2.0 * d / (n * N_T))", "dy = q(d / (n * N_T))"),
+    ("dense_relu_mask_dropped", "dz5 = q((dy @ L[5][0]) * (h5 > 0))", "dz5 = q(dy @ L[5][0])"),
+    ("conv_relu_mask_dropped", "dz = q(dh * (hs[l] > 0))", "dz = q(dh)"),
     ("bias_gradient_halved", "return dW.reshape(Cout, -1), dz.sum(axis=(0, 1, 2)), dx_",
      "return dW.reshape(Cout, -1), 0.5 * dz.sum(axis=(0, 1, 2)), dx_"),
     ("input_gradient_offsets_swapped", "dx_[:, dy::p, dx::p, :] = np.einsum(\"nyxo,oc->nyxc\", dz, Wr[:, dy, dx, :])",
@@ -48,6 +48,12 @@ MUTANTS = [
      "s = m2 + noise_v * sm_normal(seed, 2 * i + 1)"),
     ("synth_dead_test_inverted", "dead = sm_uniform(seed ^ 0xD1B54A32D192ED03, i) < dead_frac",
      "dead = sm_uniform(seed ^ 0xD1B54A32D192ED03, i) > dead_frac"),
+    ("bf16_seven_bits", "return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)", "return np.ldexp(np.rint(np.ldexp(m, 7)), e - 7)"),
+    ("bf16_truncates", "return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)", "return np.ldexp(np.trunc(np.ldexp(m, 8)), e - 8)"),
+    ("bf16_encode_unrounded", "return np.stack([bf16(sv) * m, bf16(ss) * m, m, np.zeros_like(m)], axis=-1)",
+     "return np.stack([sv * m, ss * m, m, np.zeros_like(m)], axis=-1)"),
+    ("bf16_activations_before_relu", "hs.append(q(np.maximum(conv(hs[-1], *L[l], P_SIZE[l]), 0.0)))",
+     "hs.append(np.maximum(q(conv(hs[-1], *L[l], P_SIZE[l])) - 1e-3, 0.0))"),
     ("init_std_halved", "sd = math.sqrt((1.0 if l == NL - 1 else 2.0) / K[l])",
      "sd = math.sqrt((1.0 if l == NL - 1 else 1.0) / K[l])"),
 ]
