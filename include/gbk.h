@@ -181,7 +181,10 @@ GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *p
  *    with GBK_PATH_STAGED) are rejected with GBK_EWORKSPACE before anything
  *    is launched.
  *  - The first call on a device looks up the array's device address; make
- *    it before any stream capture.
+ *    it before any stream capture (a first call on a capturing stream is
+ *    refused with GBK_EUNSUPPORTED).  A device reset (cudaDeviceReset, or a
+ *    primary context destroyed and created again) invalidates the address
+ *    the library keeps, so this entry point must not be used after one.
  *  - All calls share the array: calls that overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the
  *    caller.  Nothing in the array has to start at zero.
@@ -435,6 +438,40 @@ GBK_API gbk_status gbk_nested_sample(const gbk_geom *g, const gbk_obs *obs, cons
                                      const gbk_ns_opts *opts, double *post_mean, double *post_std, double *log_z,
                                      int64_t *n_eval, int32_t *n_iter, void *workspace, size_t ws_bytes,
                                      void *stream);
+
+/* The sampler's trajectory (Sec. 2.3.2), for checking it step by step
+ * against another implementation of the same algorithm: the initial live
+ * points, and for each of the first max_iter iterations every proposal in
+ * draw order, its chi2 and the live point it replaced.  All arrays are host
+ * memory owned by the caller; every pointer may be NULL to skip that record.
+ *  max_iter    iterations to record (>= 0)
+ *  n_iter      out: iterations recorded (<= max_iter)
+ *  live0       [n_live][GBK_NPAR] initial live points
+ *  live0_chi2  [n_live] their chi2 (NaN outside the parameter domain)
+ *  n_props     [max_iter] proposals drawn in the iteration
+ *  props       [max_iter][batch][GBK_NPAR] the proposals (rows past n_props unset)
+ *  chi2        [max_iter][batch] their chi2
+ *  replaced    [max_iter][batch] index of the live point a proposal replaced,
+ *              -1 if it did not beat the worst live point */
+typedef struct gbk_ns_trace {
+    int32_t max_iter;
+    int32_t n_iter;
+    double *live0;
+    double *live0_chi2;
+    int32_t *n_props;
+    double *props;
+    double *chi2;
+    int32_t *replaced;
+} gbk_ns_trace;
+
+/* gbk_nested_sample with its trajectory recorded in *trace (NULL: no
+ * record).  The sampling is the same code path, so the results equal
+ * gbk_nested_sample's for the same inputs.  Errors: as gbk_nested_sample;
+ * GBK_EINVAL if trace->max_iter < 0. */
+GBK_API gbk_status gbk_nested_sample_traced(const gbk_geom *g, const gbk_obs *obs, const double *lo,
+                                            const double *hi, const gbk_ns_opts *opts, double *post_mean,
+                                            double *post_std, double *log_z, int64_t *n_eval, int32_t *n_iter,
+                                            void *workspace, size_t ws_bytes, void *stream, gbk_ns_trace *trace);
 
 /* Launch tuning of the fused path (no counterpart in the paper).  A tuning
  * is the number of CTAs that cooperate on one model (a thread-block cluster

@@ -92,10 +92,13 @@ size_t gbk_nested_sample_workspace_bytes(const gbk_geom *gin, const gbk_ns_opts 
     return ns_layout(std::max(opts->n_live, opts->batch)).total;
 }
 
-gbk_status gbk_nested_sample(const gbk_geom *gin, const gbk_obs *obs, const double *lo, const double *hi,
-                             const gbk_ns_opts *opts, double *post_mean, double *post_std, double *log_z,
-                             int64_t *n_eval, int32_t *n_iter, void *workspace, size_t ws_bytes, void *stream)
+gbk_status gbk_nested_sample_traced(const gbk_geom *gin, const gbk_obs *obs, const double *lo, const double *hi,
+                                    const gbk_ns_opts *opts, double *post_mean, double *post_std, double *log_z,
+                                    int64_t *n_eval, int32_t *n_iter, void *workspace, size_t ws_bytes,
+                                    void *stream, gbk_ns_trace *trace)
 {
+    if (trace && trace->max_iter < 0) return fail(GBK_EINVAL, "trace->max_iter must be >= 0");
+    if (trace) trace->n_iter = 0;
     Geom g;
     gbk_status s = derive_geom(gin, &g);
     if (s) return s;
@@ -153,6 +156,8 @@ gbk_status gbk_nested_sample(const gbk_geom *gin, const gbk_obs *obs, const doub
             live[(size_t)i * GBK_NPAR + k] = (hi[k] > lo[k]) ? lo[k] + (hi[k] - lo[k]) * rng.uniform() : lo[k];
     if ((s = evaluate(live, N, chi2))) return s;
     for (int i = 0; i < N; ++i) logl[i] = std::isfinite(chi2[i]) ? -0.5 * chi2[i] : -INFINITY;
+    if (trace && trace->live0) std::copy(live.begin(), live.end(), trace->live0);
+    if (trace && trace->live0_chi2) std::copy(chi2.begin(), chi2.begin() + N, trace->live0_chi2);
 
     // dead points: parameters and log weights (log L + log w)
     std::vector<double> dead_p, dead_lw;
@@ -223,11 +228,22 @@ gbk_status gbk_nested_sample(const gbk_geom *gin, const gbk_obs *obs, const doub
         }
         if (made == 0) break;
         if ((s = evaluate(prop, made, chi2))) return s;
+        // the iteration's record, when one is kept
+        const bool rec = trace && it < trace->max_iter;
+        if (rec) {
+            const size_t t = (size_t)it;
+            if (trace->n_props) trace->n_props[t] = made;
+            if (trace->props) std::copy(prop.begin(), prop.begin() + (size_t)made * GBK_NPAR, trace->props + t * K * GBK_NPAR);
+            if (trace->chi2) std::copy(chi2.begin(), chi2.begin() + made, trace->chi2 + t * K);
+            if (trace->replaced) std::fill(trace->replaced + t * K, trace->replaced + t * K + made, -1);
+            trace->n_iter = it + 1;
+        }
         // replacements in draw order
         for (int j = 0; j < made; ++j) {
             double lj = std::isfinite(chi2[j]) ? -0.5 * chi2[j] : -INFINITY;
             int w = (int)(std::min_element(logl.begin(), logl.end()) - logl.begin());
             if (!(lj > logl[w])) continue;
+            if (rec && trace->replaced) trace->replaced[(size_t)it * K + j] = w;
             double lw = logx + log_shrink + logl[w];  // log(L_w (X_{i-1} - X_i))
             logz = logaddexp(logz, lw);
             dead_p.insert(dead_p.end(), &live[(size_t)w * GBK_NPAR], &live[(size_t)w * GBK_NPAR] + GBK_NPAR);
@@ -263,6 +279,14 @@ gbk_status gbk_nested_sample(const gbk_geom *gin, const gbk_obs *obs, const doub
     *n_eval = evals;
     *n_iter = it;
     return ok();
+}
+
+gbk_status gbk_nested_sample(const gbk_geom *gin, const gbk_obs *obs, const double *lo, const double *hi,
+                             const gbk_ns_opts *opts, double *post_mean, double *post_std, double *log_z,
+                             int64_t *n_eval, int32_t *n_iter, void *workspace, size_t ws_bytes, void *stream)
+{
+    return gbk_nested_sample_traced(gin, obs, lo, hi, opts, post_mean, post_std, log_z, n_eval, n_iter, workspace,
+                                    ws_bytes, stream, nullptr);
 }
 
 }  // extern "C"

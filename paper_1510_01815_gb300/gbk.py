@@ -53,6 +53,12 @@ class CNsOpts(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class CNsTrace(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("n_iter", ctypes.c_int32), ("live0", ctypes.c_void_p),
+                ("live0_chi2", ctypes.c_void_p), ("n_props", ctypes.c_void_p), ("props", ctypes.c_void_p),
+                ("chi2", ctypes.c_void_p), ("replaced", ctypes.c_void_p)]
+
+
 class CObs(ctypes.Structure):
     _fields_ = [("v_obs", ctypes.c_void_p), ("s_obs", ctypes.c_void_p), ("w_v", ctypes.c_void_p),
                 ("w_s", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
@@ -99,6 +105,12 @@ def lib():
                                         ctypes.POINTER(CNsOpts), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), vp, sz, vp]),
+            "gbk_nested_sample_traced": (i32, [gp, op, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(CNsOpts),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(ctypes.c_int32), vp, sz, vp,
+                                               ctypes.POINTER(CNsTrace)]),
             "gbk_survey_workspace_bytes": (sz, [gp, i32, ctypes.POINTER(CLmOpts)]),
             "gbk_survey_eval": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "gbk_survey_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz,
@@ -136,7 +148,8 @@ def exported_symbols():
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_fit_lm_fallback_workspace_bytes", "gbk_fit_lm_fallback",
             "gbk_wait_selfcheck",
             "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
-            "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_survey_workspace_bytes",
+            "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_nested_sample_traced",
+            "gbk_survey_workspace_bytes",
             "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_initial_guess", "gbk_survey_autotune", "gbk_survey_get_tuning",
             "gbk_survey_set_tuning", "gbk_device_status", "gbk_gemm_bf16", "gbk_cnn_param_count",
             "gbk_cnn_workspace_bytes", "gbk_cnn_init", "gbk_cnn_targets", "gbk_cnn_decode", "gbk_cnn_synth_obs",
@@ -736,6 +749,43 @@ def gbk_nested_sample(geom, obs, lo, hi, n_live=400, batch=None, tol=0.5, efr=1.
                                    _stream(stream)))
     return {"mean": np.array(mean[:]), "std": np.array(std[:]), "log_z": lz.value, "n_eval": ne.value,
             "n_iter": ni.value}
+
+
+def gbk_nested_sample_traced(geom, obs, lo, hi, n_live=400, batch=None, tol=0.5, efr=1.0, seed=1, max_iter=100000,
+                             trace_iters=0, device="cuda", stream=None):
+    """gbk_nested_sample with its first trace_iters iterations recorded:
+    returns the result dict plus "trace" = dict(live0 [n_live][NPAR],
+    live0_chi2 [n_live], n_props [T], props [T][batch][NPAR], chi2
+    [T][batch], replaced [T][batch]) for the T <= trace_iters iterations run."""
+    import numpy as np
+    K = int(batch if batch else max(1, n_live // 4))
+    g = cgeom(geom)
+    o = CNsOpts(int(n_live), K, float(tol), float(efr), int(seed), int(max_iter), 0)
+    nb = lib().gbk_nested_sample_workspace_bytes(ctypes.byref(g), ctypes.byref(o))
+    if nb == 0:
+        raise GbkError(GBK_EINVAL, lib().gbk_last_error().decode())
+    ws = torch.empty(nb, dtype=torch.uint8, device=device)
+    T = int(trace_iters)
+    live0 = np.zeros((n_live, NPAR))
+    live0_c = np.zeros(n_live)
+    n_props = np.zeros(max(T, 1), np.int32)
+    props = np.zeros((max(T, 1), K, NPAR))
+    chi2 = np.zeros((max(T, 1), K))
+    repl = np.zeros((max(T, 1), K), np.int32)
+    tr = CNsTrace(T, 0, live0.ctypes.data, live0_c.ctypes.data, n_props.ctypes.data, props.ctypes.data,
+                  chi2.ctypes.data, repl.ctypes.data)
+    D = ctypes.c_double * NPAR
+    mean, std, lz = D(), D(), ctypes.c_double()
+    ne, ni = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().gbk_nested_sample_traced(ctypes.byref(g), ctypes.byref(obs.c()), D(*[float(v) for v in lo]),
+                                          D(*[float(v) for v in hi]), ctypes.byref(o), mean, std, ctypes.byref(lz),
+                                          ctypes.byref(ne), ctypes.byref(ni), _ptr(ws, None, "workspace"), nb,
+                                          _stream(stream), ctypes.byref(tr)))
+    n = tr.n_iter
+    return {"mean": np.array(mean[:]), "std": np.array(std[:]), "log_z": lz.value, "n_eval": ne.value,
+            "n_iter": ni.value,
+            "trace": {"live0": live0, "live0_chi2": live0_c, "n_props": n_props[:n], "props": props[:n],
+                      "chi2": chi2[:n], "replaced": repl[:n]}}
 
 
 def gbk_initial_guess(geom, obs_dev, fixed, params_out, continuum=None, stream=None):
