@@ -1,6 +1,7 @@
 // gbk_api.cu -- C ABI entry points of libgbk.so: argument validation, path
 // selection, workspace layout and kernel launches.  All model arithmetic is in
 // the kernels (k_fused.cu, k_staged.cu).
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -29,6 +30,28 @@ gbk_status fail(gbk_status code, const char *fmt, ...)
 gbk_status ok()
 {
     t_last_error.clear();
+    return GBK_OK;
+}
+
+gbk_status ensure_kernel_attrs(const void *kernel, size_t smem, bool cluster16, KernelAttrMemo &memo,
+                               const char *what)
+{
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(GBK_EUNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem > memo.smem[dev]) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        memo.smem[dev] = smem;
+    }
+    if (cluster16 && !memo.cluster16[dev]) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        memo.cluster16[dev] = true;
+    }
     return GBK_OK;
 }
 

@@ -308,13 +308,10 @@ bool conv_pair_supported(const Geom &g)
 template <int R>
 static gbk_status launch_pr(const CUtensorMap &tm, const ConvPairArgs &a, size_t smem, int blocks, cudaStream_t st)
 {
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(conv3d_pair_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "pair convolution: setting dynamic shared memory");
-        configured = smem;
-    }
+    static KernelAttrMemo memo;
+    gbk_status s = ensure_kernel_attrs((const void *)conv3d_pair_kernel<R>, smem, false, memo,
+                                       "pair convolution: setting dynamic shared memory");
+    if (s) return s;
     conv3d_pair_kernel<R><<<blocks, kPThreads, smem, st>>>(tm, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pair convolution launch");

@@ -219,13 +219,10 @@ bool conv_tma_supported(const Geom &g)
 template <int W>
 static gbk_status launch_w(const CUtensorMap &tm, const ConvTmaArgs &a, size_t smem, int blocks, cudaStream_t st)
 {
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(conv3d_tma_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "TMA convolution: setting dynamic shared memory");
-        configured = smem;
-    }
+    static KernelAttrMemo memo;
+    gbk_status s = ensure_kernel_attrs((const void *)conv3d_tma_kernel<W>, smem, false, memo,
+                                       "TMA convolution: setting dynamic shared memory");
+    if (s) return s;
     conv3d_tma_kernel<W><<<blocks, kCThreads, smem, st>>>(tm, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "TMA convolution launch");

@@ -44,6 +44,8 @@
 // is fixed, so results are bitwise reproducible.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "gbk_api_internal.h"
 #include "gbk_internal.cuh"
 #include "k_fused.h"
@@ -616,19 +618,11 @@ static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_
 {
     // Shared-memory opt-in is set to what this launch needs (static shared
     // memory of the kernel counts against the same per-block limit).
-    static size_t configured = 0;
-    static bool cluster_configured = false;
+    static KernelAttrMemo memo;
     auto kern = fused_eval_kernel<NT, MINB, RAGGED>;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "fused kernel: setting dynamic shared memory");
-        configured = smem;
-    }
-    if (!cluster_configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return cuda_fail(e, "fused kernel: allowing 16-CTA clusters");
-        cluster_configured = true;
-    }
+    gbk_status s0 = ensure_kernel_attrs((const void *)kern, smem, true, memo,
+                                        "fused kernel: setting its shared memory and cluster attributes");
+    if (s0) return s0;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = smem;
@@ -641,21 +635,30 @@ static gbk_status launch_variant(const FusedArgs &args, size_t smem, cudaStream_
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     // One wave of clusters: as many as can be resident at once (cached per
-    // cluster size and shared-memory size), each looping over models.
-    static int cached_cs = -1, cached_clusters = 0;
-    static size_t cached_smem = 0;
-    if (args.persistent && (cached_cs != args.cs || cached_smem != smem)) {
-        cfg.gridDim = dim3((unsigned)args.cs, 1, 1);
-        int ncl = 0;
-        cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
-        if (e != cudaSuccess) return cuda_fail(e, "fused kernel: cluster occupancy query");
-        if (ncl < 1) return fail(GBK_EUNSUPPORTED, "no %d-CTA cluster of the fused kernel fits on this device", args.cs);
-        cached_cs = args.cs;
-        cached_smem = smem;
-        cached_clusters = ncl;
-    }
+    // device, cluster size and shared-memory size), each looping over models.
     int ncl = args.n_models;
-    if (args.persistent && cached_clusters < ncl) ncl = cached_clusters;
+    if (args.persistent) {
+        struct Wave { int cs = -1, clusters = 0; size_t smem = 0; };
+        static Wave cache[kMaxDevices];
+        static std::mutex mu;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        if (dev < 0 || dev >= kMaxDevices) return fail(GBK_EUNSUPPORTED, "device ordinal %d out of range", dev);
+        std::lock_guard<std::mutex> lk(mu);
+        Wave &w = cache[dev];
+        if (w.cs != args.cs || w.smem != smem) {
+            cfg.gridDim = dim3((unsigned)args.cs, 1, 1);
+            int n = 0;
+            e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+            if (e != cudaSuccess) return cuda_fail(e, "fused kernel: cluster occupancy query");
+            if (n < 1) return fail(GBK_EUNSUPPORTED, "no %d-CTA cluster of the fused kernel fits on this device", args.cs);
+            w.cs = args.cs;
+            w.smem = smem;
+            w.clusters = n;
+        }
+        if (w.clusters < ncl) ncl = w.clusters;
+    }
     cfg.gridDim = dim3((unsigned)(ncl * args.cs), 1, 1);
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");

@@ -330,12 +330,10 @@ gbk_status launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, cons
     if (s) return s;
     if ((s = encode_kmajor(&tb, B, a.N, a.K, ldb, a.bn))) return s;
     size_t smem = gemm_smem_bytes(a.bn);
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "GEMM: setting dynamic shared memory");
-        configured = smem;
-    }
+    static KernelAttrMemo memo;
+    if ((s = ensure_kernel_attrs((const void *)gemm_bf16_kernel, smem, false, memo,
+                                 "GEMM: setting dynamic shared memory")))
+        return s;
     int splits = 1;
     if (a.kt_split > 0) {
         if (!a.out_f32 || a.out_bf16 || a.out_t) return fail(GBK_EINVAL, "split-K writes FP32 slices only");

@@ -315,11 +315,11 @@ gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t st
         if (s) return s;
     } else {
         size_t smem = conv_smem_bytes(g);
-        static size_t configured = 0;
-        if (smem > 48 * 1024 && smem > configured) {
-            e = cudaFuncSetAttribute(conv3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return cuda_fail(e, "conv kernel: setting dynamic shared memory");
-            configured = smem;
+        static KernelAttrMemo memo;
+        if (smem > 48 * 1024) {
+            gbk_status s = ensure_kernel_attrs((const void *)conv3d_kernel, smem, false, memo,
+                                               "conv kernel: setting dynamic shared memory");
+            if (s) return s;
         }
         int tiles = ((g.nxf + kConvTX - 1) / kConvTX) * ((g.nyf + kConvTY - 1) / kConvTY);
         conv3d_kernel<<<(unsigned)(tiles * a.n_models), kConvTX * kConvTY, smem, stream>>>(a);

@@ -510,19 +510,11 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
 template <int NP>
 static gbk_status launch_np(const TangentArgs &args, size_t smem, cudaStream_t stream)
 {
-    static size_t configured = 0;
-    static bool cl = false;
+    static KernelAttrMemo memo;
     auto kern = tangent_kernel<NP>;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "tangent kernel: setting dynamic shared memory");
-        configured = smem;
-    }
-    if (!cl) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return cuda_fail(e, "tangent kernel: allowing 16-CTA clusters");
-        cl = true;
-    }
+    gbk_status s0 = ensure_kernel_attrs((const void *)kern, smem, true, memo,
+                                        "tangent kernel: setting its shared memory and cluster attributes");
+    if (s0) return s0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(args.n_models * args.cs), 1, 1);
     cfg.blockDim = dim3(kTangentThreads, 1, 1);

@@ -15,9 +15,13 @@
 // address, so its device address is looked up once per device with
 // cudaGetSymbolAddress (with that device current) and cached.  The first call
 // on a device does that look-up, so make the first call before any stream
-// capture.  Every call shares the one array: calls that overlap on the GPU
-// (on different streams, or from different host threads) race on it and must
-// be serialised by the caller.  No byte of the array needs to start at zero:
+// capture; a first call made while its stream is capturing is refused with
+// GBK_EUNSUPPORTED before the look-up.  A device reset (cudaDeviceReset, or
+// a primary context torn down and made again) reloads the module, and the
+// cached address is then stale: such a caller must not use this entry point
+// after the reset.  Every call shares the one array: calls that overlap on
+// the GPU (on different streams, or from different host threads) race on it
+// and must be serialised by the caller.  No byte of the array needs to start at zero:
 // the kernels of the staged path write every value (including row padding)
 // before any kernel of the same call reads it.  The entry point calls no
 // cudaMalloc, cudaFree or allocating library routine.
@@ -35,8 +39,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_ptr[kNoAllocMaxDevices];
 
-// Device address of the scratch array on the current device.
-static gbk_status noalloc_scratch(void **out)
+// Device address of the scratch array on the current device.  The look-up is
+// not made while `stream` is capturing (it would end the capture).
+static gbk_status noalloc_scratch(void **out, cudaStream_t stream)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -44,6 +49,12 @@ static gbk_status noalloc_scratch(void **out)
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(GBK_EUNSUPPORTED, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(stream, &cap);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(GBK_EUNSUPPORTED, "gbk_chi2_noalloc: the first call on device %d must not be captured "
+                        "(it looks up the built-in scratch's address); call it once before capturing", dev);
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the built-in scratch");
@@ -69,7 +80,7 @@ extern "C" gbk_status gbk_chi2_noalloc(const gbk_geom *g, int32_t n_models, cons
                     "(split the batch, or use gbk_chi2 with a workspace)",
                     n_models, need, kNoAllocScratchBytes);
     void *ws = nullptr;
-    gbk_status s = noalloc_scratch(&ws);
+    gbk_status s = noalloc_scratch(&ws, (cudaStream_t)stream);
     if (s) return s;
     return gbk_chi2(g, n_models, params, obs, chi2, resid, GBK_PATH_STAGED, ws, kNoAllocScratchBytes, stream);
 }
