@@ -91,6 +91,8 @@ def use_library(path):
         "og_eval_batch": (None, [gp, i, dp, dp, i]),
         "og_chi2_batch": (None, [gp, i, dp, fp, fp, fp, fp, up, dp, dp, i]),
         "og_max_threads": (i, []),
+        "og_set_conv_form": (None, [i]),
+        "og_get_conv_form": (i, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -244,3 +246,19 @@ def chi2_batch(g: Geom, params, obs: Obs, want_resid=False, nthreads=0):
 
 def max_threads():
     return lib().og_max_threads()
+
+
+class separable_convolution:
+    """Context manager: inside it every evaluation convolves with the three
+    1-D passes (``og_conv3d_separable``) instead of the direct 3-D sum.  The
+    two forms are the same linear map (pinned term by term on small cubes and
+    on whole models); the passes make sweeps over 10^5 models affordable."""
+
+    def __enter__(self):
+        self._prev = lib().og_get_conv_form()
+        lib().og_set_conv_form(1)
+        return self
+
+    def __exit__(self, *exc):
+        lib().og_set_conv_form(self._prev)
+        return False

@@ -18,7 +18,7 @@
  *   moments         Sec. 2.2.5 (first/second moments of each spectrum)
  *   chi-squared     Sec. 2.2.6, Eq. 11 (W folded into the dispersion error)
  *
- * Readings where the paper is silent (all documented in the design notes):
+ * Readings where the paper is silent:
  *   - pixel centres sit at integer coordinates 0..N-1; channel k has velocity
  *     v_k = vc + (k - (nz-1)/2) dv;
  *   - the line is point-sampled and area-normalised:
@@ -355,6 +355,17 @@ int og_param_valid(const og_geom *g, const double *p)
     return ok;
 }
 
+/* Which form of the Sec. 2.2.3 convolution og_eval uses: 0 = the direct,
+ * unfactored 3-D sum (the default and the definition); 1 = the three 1-D
+ * passes of og_conv3d_separable, which equal it up to rounding (the two are
+ * compared term by term on small cubes) and cost about 3(2R+1) instead of
+ * (2R+1)^3 products per voxel, so that sweeps of 10^5 models finish.  The
+ * choice is process-wide and is made before any evaluation starts. */
+static int og_conv_form = 0;
+
+void og_set_conv_form(int separable) { og_conv_form = separable ? 1 : 0; }
+int og_get_conv_form(void) { return og_conv_form; }
+
 /* Steps 1-5 of one model: cube (optional output, data resolution) and maps. */
 void og_eval(const og_geom *g, const double *p, double *cube_out, double *maps_out)
 {
@@ -381,7 +392,8 @@ void og_eval(const og_geom *g, const double *p, double *cube_out, double *maps_o
     double *fine = (double *)malloc(sizeof(double) * nfine);
     double *data = cube_out ? cube_out : (double *)malloc(sizeof(double) * ndata);
     og_model_cube(g, p, ext);
-    og_conv3d_direct(ext, d.exf, d.eyf, d.ezf, wx, d.rxy, wx, d.rxy, wz, d.rz, fine);
+    if (og_conv_form) og_conv3d_separable(ext, d.exf, d.eyf, d.ezf, wx, d.rxy, wx, d.rxy, wz, d.rz, fine);
+    else og_conv3d_direct(ext, d.exf, d.eyf, d.ezf, wx, d.rxy, wx, d.rxy, wz, d.rz, fine);
     if (d.u == 1) memcpy(data, fine, sizeof(double) * ndata);
     else og_downsample(fine, d.u, g->nx, g->ny, g->nz, data);
     if (maps_out)
