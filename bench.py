@@ -89,8 +89,9 @@ def parse():
     ap.add_argument("--cnn-epochs", type=int, default=2)
     ap.add_argument("--cnn-batch", type=int, default=1024)
     ap.add_argument("--cnn-test", type=int, default=4096, help="held-out galaxies of the seed comparison")
-    ap.add_argument("--path", default="fused", choices=["fused", "staged"],
-                    help="fused (default) or staged (cube materialised in HBM) evaluation")
+    ap.add_argument("--path", default="fused", choices=["fused", "staged", "split"],
+                    help="fused (default), staged (cube materialised in HBM) or split (line and PSF stages "
+                         "through an L2-resident buffer) evaluation")
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
     ap.add_argument("--tuning", default=None,
                     help="CTAS,THREADS,PERSISTENT: use this fused-kernel tuning instead of autotuning")
@@ -1090,15 +1091,19 @@ def run_gbk(args):
     stream = torch.cuda.current_stream(dev)
 
     staged = args.path == "staged"
+    split = args.path == "split"
     ws_staged = gbk.workspace_for(g, n, gbk.PATH_STAGED, dev) if staged else None
+    ws_split = gbk.workspace_for(g, n, gbk.PATH_SPLIT, dev) if split else None
 
     def step(s):
         if staged:
             gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_STAGED, ws_staged, stream)
+        elif split:
+            gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_SPLIT, ws_split, stream)
         else:
             gbk.gbk_chi2(g, pool[s], obs, chi2[s], None, gbk.PATH_FUSED, None, stream)
 
-    if staged:
+    if staged or split:
         tuning = {"cluster_ctas": 0, "threads": 0, "persistent": 0, "candidates": 0}
     elif args.tuning:
         cs_, nt_, pe_ = (int(v) for v in args.tuning.split(","))
@@ -1138,7 +1143,7 @@ def run_gbk(args):
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": "fabry-perot 192x192x48 at 10 km/s, PSF 3 px, LSF 30 km/s, "
                                   "400 live points per step (one batched launch)",
-                      "models_per_step": n, "path": "fused", "l2": "flushed between steps (256 MiB write)",
+                      "models_per_step": n, "path": args.path, "l2": "flushed between steps (256 MiB write)",
                       "tuning": {"cluster_ctas": tuning["cluster_ctas"], "threads": tuning["threads"],
                                  "persistent": tuning["persistent"], "candidates": tuning["candidates"]},
                       "parallelism": "replicas" if ws > 1 else "single"},

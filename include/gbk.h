@@ -125,14 +125,30 @@ typedef struct gbk_obs {
     const uint8_t *mask;
 } gbk_obs;
 
-/* Evaluation paths (the `flags` argument of gbk_chi2). */
-#define GBK_PATH_AUTO    0u  /* fused unless the request needs the staged path    */
-#define GBK_PATH_FUSED   1u  /* one kernel; the cube never leaves the SM           */
-#define GBK_PATH_STAGED  2u  /* model cube -> separable conv -> moments, via HBM   */
+/* Evaluation paths (the `flags` argument of gbk_chi2).  All compute the
+ * same maps and chi-squared (Sec. 2.2.2-2.2.6); they differ in where the
+ * intermediate values live.
+ *  GBK_PATH_FUSED   one kernel, a thread-block cluster per model; the cube
+ *                   never leaves the SM; needs no workspace.
+ *  GBK_PATH_STAGED  model cube -> separable convolution -> moments, each
+ *                   stage through HBM (the paper's pipeline).
+ *  GBK_PATH_SPLIT   two kernels: each extended spaxel's line folded into a
+ *                   moment triplet (16 bytes, in the workspace, sized to stay
+ *                   in L2), then the PSF passes, moments and chi-squared in
+ *                   tiles; the cube is never formed.  Cube model, u = 1, PSF
+ *                   radius <= 8 px.
+ *  GBK_PATH_AUTO    the split path when it serves the geometry and the
+ *                   workspace holds what it needs, else the fused path when
+ *                   it serves the geometry, else the staged path. */
+#define GBK_PATH_AUTO    0u
+#define GBK_PATH_FUSED   1u
+#define GBK_PATH_STAGED  2u
+#define GBK_PATH_SPLIT   3u
 
 /* Bytes of workspace gbk_eval_cubes / gbk_chi2 need for n_models models on
- * the given path (0 when the path needs none).  Host function; returns 0 and
- * sets the last error on invalid arguments. */
+ * the given path (0 when the path needs none; GBK_PATH_AUTO: the bytes of the
+ * path it prefers for this geometry).  Host function; returns 0 and sets the
+ * last error on invalid arguments. */
 GBK_API size_t gbk_workspace_bytes(const gbk_geom *g, int32_t n_models, uint32_t flags);
 
 /* Forward model, Sec. 2.2.2-2.2.5.  Asynchronous.
@@ -145,9 +161,12 @@ GBK_API size_t gbk_workspace_bytes(const gbk_geom *g, int32_t n_models, uint32_t
  *            m0 = sum over channels, m1 = intensity-weighted mean velocity,
  *            m2 = intensity-weighted standard deviation.  A spectrum with
  *            m0 <= 1e-20 * I0 is invalid and gets (0, Vsys, 0).
- *  workspace device scratch of gbk_workspace_bytes(g, n_models,
- *            cubes ? GBK_PATH_STAGED : GBK_PATH_FUSED) bytes (may be NULL
- *            when that is 0).
+ *  workspace device scratch (may be NULL): with cubes, at least
+ *            gbk_workspace_bytes(g, n_models, GBK_PATH_STAGED) bytes; without,
+ *            the maps come from the split path when the workspace holds
+ *            gbk_workspace_bytes(g, n_models, GBK_PATH_SPLIT) bytes, else
+ *            from the fused path, else (geometries neither serves) from the
+ *            staged path.
  * Validation: sizes >= 1, dv > 0, psf/lsf >= 0, halo_sigmas > 0, and for
  * every model 0 <= i < 90 deg, r_t > 0, sigma0 > 0, I0 > 0, h > 0 -- the
  * parameter checks run on the device and invalid models get NaN maps and
@@ -163,8 +182,11 @@ GBK_API gbk_status gbk_eval_cubes(const gbk_geom *g, int32_t n_models, const dou
  *  resid   device, [n_models][2][ny][nx] FP32 weighted residuals
  *          w_v (m1 - v_obs) and w_s (m2 - s_obs), 0 where masked or
  *          invalid; or NULL
- *  flags   GBK_PATH_AUTO, GBK_PATH_FUSED or GBK_PATH_STAGED.
- * The reduction order is fixed, so results are bitwise reproducible. */
+ *  flags   GBK_PATH_AUTO, GBK_PATH_FUSED, GBK_PATH_STAGED or GBK_PATH_SPLIT
+ *  workspace, ws_bytes  device scratch for the path (see
+ *          gbk_workspace_bytes); NULL / 0 when the path needs none.
+ * The reduction order is fixed for each path, so results are bitwise
+ * reproducible. */
 GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *params,
                     const gbk_obs *obs, double *chi2, float *resid, uint32_t flags,
                     void *workspace, size_t ws_bytes, void *stream);
@@ -539,7 +561,9 @@ GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ffm
  * when a TMA load of the staged convolution did not complete in time, bit 1
  * when a pipeline wait of the tensor-core GEMM did not (the affected blocks
  * stopped early and their output is incomplete), bit 2 when the wait of
- * gbk_wait_selfcheck ran out.  Synchronising. */
+ * gbk_wait_selfcheck ran out, bit 3 when a tile load of the split path's PSF
+ * stage did not complete in time (that model's chi2 is not written).
+ * Synchronising. */
 GBK_API gbk_status gbk_device_status(int32_t *status);
 
 /* Self-check of the bounded device waits: one thread runs the library's

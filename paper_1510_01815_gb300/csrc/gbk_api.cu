@@ -9,6 +9,7 @@
 
 #include "gbk_api_internal.h"
 #include "k_fused.h"
+#include "k_split.h"
 #include "k_gemm.h"
 #include "k_staged.h"
 
@@ -179,12 +180,12 @@ const char *gbk_version(void) { return "gbk 0.1 (sm_103a)"; }
 gbk_status gbk_device_status(int32_t *status)
 {
     if (!status) return fail(GBK_EINVAL, "status is NULL");
-    int c = 0, c2 = 0, g = 0, w = 0;
+    int c = 0, c2 = 0, g = 0, w = 0, sp = 0;
     gbk_status s;
     if ((s = conv_status_read(&c)) || (s = conv_pair_status_read(&c2)) || (s = gemm_status_read(&g)) ||
-        (s = selfcheck_status_read(&w)))
+        (s = selfcheck_status_read(&w)) || (s = split_status_read(&sp)))
         return s;
-    *status = ((c || c2) ? 1 : 0) | (g ? 2 : 0) | (w ? 4 : 0);
+    *status = ((c || c2) ? 1 : 0) | (g ? 2 : 0) | (w ? 4 : 0) | (sp ? 8 : 0);
     return ok();
 }
 
@@ -194,11 +195,21 @@ size_t gbk_workspace_bytes(const gbk_geom *gin, int32_t n_models, uint32_t flags
     Geom g;
     if (derive_geom(gin, &g) != GBK_OK) return 0;
     if (n_models < 0) { fail(GBK_EINVAL, "n_models must be >= 0"); return 0; }
+    if (flags > GBK_PATH_SPLIT) { fail(GBK_EINVAL, "unknown flags 0x%x", flags); return 0; }
     FusedConfig fc;
     bool fused_ok = fused_config(g, &fc);
     if (g.model != GBK_MODEL_CUBE) return 0;
+    if (flags == GBK_PATH_SPLIT || (flags == GBK_PATH_AUTO && split_supported(g)))
+        return split_workspace_bytes(g, n_models);
     if (flags == GBK_PATH_FUSED || (flags == GBK_PATH_AUTO && fused_ok)) return 0;
     return staged_layout(g, n_models, true, true).total;
+}
+
+// The split path serves the request: its geometry, and a workspace that
+// holds its triplets.
+static bool split_fits(const Geom &g, int32_t n, const void *ws, size_t ws_bytes)
+{
+    return ws && split_supported(g) && ws_bytes >= split_workspace_bytes(g, n);
 }
 
 static gbk_status run_staged(const Geom &g, int32_t n, const double *params, float *cubes, float *maps,
@@ -283,6 +294,12 @@ gbk_status gbk_eval_cubes(const gbk_geom *gin, int32_t n_models, const double *p
     if (!cubes && !maps) return ok();
     cudaStream_t st = (cudaStream_t)stream;
     FusedConfig fc;
+    if (!cubes && split_fits(g, n_models, workspace, ws_bytes)) {
+        if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
+        if ((s = launch_split(g, n_models, params, nullptr, maps, nullptr, nullptr, workspace, ws_bytes, st)))
+            return s;
+        return ok();
+    }
     if (cubes || !fused_config(g, &fc))
         return run_staged(g, n_models, params, cubes, maps, nullptr, nullptr, nullptr, workspace, ws_bytes, st);
     return run_fused(g, n_models, params, maps, nullptr, nullptr, nullptr, st);
@@ -295,7 +312,7 @@ gbk_status gbk_chi2(const gbk_geom *gin, int32_t n_models, const double *params,
     gbk_status s = derive_geom(gin, &g);
     if (s) return s;
     if (n_models < 0) return fail(GBK_EINVAL, "n_models must be >= 0");
-    if (flags > GBK_PATH_STAGED) return fail(GBK_EINVAL, "unknown flags 0x%x", flags);
+    if (flags > GBK_PATH_SPLIT) return fail(GBK_EINVAL, "unknown flags 0x%x", flags);
     if (n_models == 0) return ok();
     if ((s = check_device_ptr(params, "params", 8))) return s;
     if ((s = check_device_ptr(chi2, "chi2", 8))) return s;
@@ -304,6 +321,11 @@ gbk_status gbk_chi2(const gbk_geom *gin, int32_t n_models, const double *params,
     cudaStream_t st = (cudaStream_t)stream;
     FusedConfig fc;
     bool fused_ok = fused_config(g, &fc);
+    if (flags == GBK_PATH_SPLIT || (flags == GBK_PATH_AUTO && split_fits(g, n_models, workspace, ws_bytes))) {
+        if (workspace && (s = check_device_ptr(workspace, "workspace", 256))) return s;
+        if ((s = launch_split(g, n_models, params, obs, nullptr, chi2, resid, workspace, ws_bytes, st))) return s;
+        return ok();
+    }
     if (flags == GBK_PATH_STAGED || (flags == GBK_PATH_AUTO && !fused_ok))
         return run_staged(g, n_models, params, nullptr, nullptr, obs, chi2, resid, workspace, ws_bytes, st);
     return run_fused(g, n_models, params, nullptr, obs, chi2, resid, st);

@@ -48,14 +48,12 @@
 
 #include "gbk_api_internal.h"
 #include "gbk_internal.cuh"
+#include "fused_line.cuh"
 #include "k_fused.h"
 
 namespace cg = cooperative_groups;
 
 namespace gbk {
-
-__host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
-
 
 // Extended rows [band_begin(r), band_begin(r+1)) belong to cluster rank r.
 __host__ __device__ inline int band_begin(int rank, int ey, int cs) { return (int)(((long)rank * ey) / cs); }
@@ -71,21 +69,6 @@ __host__ __device__ inline size_t fused_q_floats4(const Geom &g, int band)
     return q > h ? q : h;
 }
 
-// Edge channels of the extended band: the lower block [0, elo) and the upper
-// block [ehi, ez) have part of their LSF window outside the data band.
-__host__ __device__ inline int edge_lo_end(const Geom &g) { return g.ez < 2 * g.Rz ? g.ez : 2 * g.Rz; }
-__host__ __device__ inline int edge_hi_begin(const Geom &g)
-{
-    int elo = edge_lo_end(g);
-    return g.nz > elo ? g.nz : elo;
-}
-// Floats per edge table: both blocks, each padded to an even length.
-__host__ __device__ inline int edge_table_len(const Geom &g)
-{
-    int lo = edge_lo_end(g), hi = g.ez - edge_hi_begin(g);
-    return pad4(((lo + 1) & ~1) + ((hi + 1) & ~1));
-}
-
 __host__ __device__ inline size_t fused_smem_bytes(const Geom &g, int band)
 {
     size_t b = 0;
@@ -98,49 +81,6 @@ __host__ __device__ inline size_t fused_smem_bytes(const Geom &g, int band)
 }
 
 size_t fused_smem_bytes_host(const Geom &g, int band) { return fused_smem_bytes(g, band); }
-
-// Moves a (q0, q1, q2) triple centred on q.w to centre c and accumulates it
-// with weight w (identity 3 above).
-// With t0 = w q0, t1 = w q1 and u = t1 + D t0 the three contributions are
-// t0, u and w q2 + D (u + t1): nine FP32 operations.
-__device__ __forceinline__ void accum_shift(float4 q, float c, float w, float &s0, float &s1, float &s2)
-{
-    const float D = q.w - c;
-    const float t0 = w * q.x;
-    const float t1 = w * q.y;
-    const float u = fmaf(D, t0, t1);
-    s0 += t0;
-    s1 += u;
-    s2 = fmaf(w, q.z, s2);
-    s2 = fmaf(D, u + t1, s2);
-}
-
-// Unnormalised tap and the full normalisation sum (computed by each thread
-// that needs it, so no serial section or extra barrier is required).
-__device__ __forceinline__ float tap_raw(int j, float sigma, int R)
-{
-    return (R == 0) ? 1.f : gauss_tap(j, sigma);
-}
-
-__device__ __forceinline__ float tap_sum(float sigma, int R)
-{
-    if (R == 0) return 1.f;
-    float s = 0.f;
-    for (int j = -R; j <= R; ++j) s += gauss_tap(j, sigma);
-    return s;
-}
-
-// Kahan-compensated FP32 accumulation (a thread adds a handful of terms).
-struct KahanF {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x)
-    {
-        float y = x - c;
-        float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
 
 // Dynamic shared memory of one model's geometry.
 struct FusedSmem {
@@ -173,42 +113,8 @@ __device__ void fused_setup(const Geom &g, const FusedSmem &L, int row0, int row
         for (int j = tid - (nthr - 32); j <= 2 * R; j += 32)
             L.wxy[j] = tap_raw(j - R, g.sig_xy, R) / tap_sum(g.sig_xy, R);
     }
-    if (tid == nthr - 64) {
-        float S = tap_sum(g.sig_z, g.Rz), V = 0.f;
-        for (int j = -g.Rz; j <= g.Rz; ++j) V = fmaf(tap_raw(j, g.sig_z, g.Rz), (float)(j * j), V);
-        *var_z = g.dv * g.dv * (V / S);
-    }
-    // Edge tables.  For an edge channel e with in-band LSF tap sums
-    // G0 = sum L_j, H1 = dv sum L_j j, H2 = dv^2 sum L_j j^2 (j = k - e over
-    // data channels k) and delta = (e - e_ref) dv from its block's middle
-    // channel e_ref:  A1 = delta G0 + H1,  A2 = delta^2 G0 + 2 delta H1 + H2,
-    // so that the moment weights are T0 = G0, T1 = d_ref G0 + A1 and
-    // T2 = d_ref^2 G0 + 2 d_ref A1 + A2 with d_ref = v(e_ref) - a.
-    const int elo = edge_lo_end(g), ehi = edge_hi_begin(g);
-    const int hi_off = (elo + 1) & ~1;  // table slot of channel ehi
-    for (int ee = tid - 32; ee < g.ez; ee += nthr) {  // warps 1.. (warp 0 holds thread 0)
-        if (ee < 0 || (ee >= elo && ee < ehi)) continue;
-        int kd = ee - g.Rz;  // data channel of extended channel ee
-        int jlo = max(0, kd - g.Rz) - kd, jhi = min(g.nz - 1, kd + g.Rz) - kd;
-        float S = tap_sum(g.sig_z, g.Rz);
-        float G0 = 0.f, H1 = 0.f, H2 = 0.f;
-        for (int j = jlo; j <= jhi; ++j) {
-            float w = tap_raw(j, g.sig_z, g.Rz);
-            G0 += w;
-            H1 = fmaf(w, (float)j, H1);
-            H2 = fmaf(w, (float)(j * j), H2);
-        }
-        G0 /= S;
-        H1 = g.dv * (H1 / S);
-        H2 = g.dv * g.dv * (H2 / S);
-        bool lower = ee < elo;
-        float eref = lower ? 0.5f * (float)(elo - 1) : 0.5f * (float)(ehi + g.ez - 1);
-        float delta = ((float)ee - eref) * g.dv;
-        int slot = lower ? ee : hi_off + (ee - ehi);
-        L.eG0[slot] = G0;
-        L.eA1[slot] = fmaf(delta, G0, H1);
-        L.eA2[slot] = fmaf(delta, fmaf(delta, G0, 2.f * H1), H2);
-    }
+    if (tid == nthr - 64) *var_z = lsf_var(g);
+    edge_tables(g, L.eG0, L.eA1, L.eA2, tid - 32, nthr);  // warps 1.. (warp 0 holds thread 0)
     // y-pass row offsets (in float4 units from Q) of extended rows [row0 - R, row1 + R)
     const int nrows = row1 - row0;
     for (int k = tid; k < nrows + 2 * R; k += nthr) {
@@ -329,8 +235,6 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     float4 *const Q = L.Q, *const P = L.P;
     const float *const eG0 = L.eG0, *const eA1 = L.eA1, *const eA2 = L.eA2, *const wxy = L.wxy;
     const int *const rowoff = L.rowoff;
-    const int elo = edge_lo_end(g), ehi = edge_hi_begin(g);
-    const int hi_off = (elo + 1) & ~1;  // table slot of channel ehi
     // pixel offset of this model's maps and residuals
     const size_t mo = RAGGED ? (size_t)a.pix_off[gal] * mpg + (size_t)(model - gal * mpg) * g.nx * g.ny
                              : (size_t)model * g.nx * g.ny;
@@ -344,125 +248,13 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
 
     // ---- phase 1: Gaussian line of every extended spaxel of the band ----
     // Interior channels [elo, ehi) have their whole LSF window inside the band.
-    const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;  // v of e = 0
-    const float al = c.alpha, adv = c.alpha * g.dv, inv_al = 1.f / c.alpha, inv_adv = 1.f / adv;
-    const float v_lo = g.vc - 0.5f * (float)(g.nz - 1) * g.dv;  // first and last data channel
-    const float v_hi = g.vc + 0.5f * (float)(g.nz - 1) * g.dv;
-    const float eref_lo = 0.5f * (float)(elo - 1), eref_hi = 0.5f * (float)(ehi + g.ez - 1);
-    const f32x2 ADV = pk2(adv, adv), TWO = pk2(2.f, 2.f), Z2 = pk2(0.f, 0.f);
+    const LineCtx lc = line_ctx(g, c, var_z);
     const int nsp = nrows * g.ex;
     int r = tid / g.ex, xe = tid - r * g.ex;
     const int dr_e = nthr / g.ex, dx_e = nthr - dr_e * g.ex;  // (row, col) step of idx += nthr
     for (int idx = tid; idx < nsp; idx += nthr) {
-        float x = (float)(xe - R), y = (float)(row0 + r - R);
-        float vl, br;
-        los(c, x, y, vl, br);
-        // Sums are taken about a = v_los clamped into the band: for a line
-        // inside the band a = v_los; for a line outside it the band edge keeps
-        // the FP32 second moment of the truncated spectrum free of
-        // cancellation.  (The moments do not depend on this choice.)
-        float a_c = fminf(fmaxf(vl, v_lo), v_hi);
-        float sh = vl - a_c;
-        float ub = al * (vz0 - vl);  // u = alpha (v_e - v_los) at e = 0
-        const f32x2 UB = pk2(ub, ub);
-
-        // interior: sums of g, g m, g m^2 with m = alpha (v_e - a)
-        float s0, s1, s2;
-        const unsigned am = __activemask();
-        if (!__any_sync(am, sh != 0.f)) {
-            // m = u: the Gaussian argument is also the moment variable.
-            // The warp runs only the union of its lanes' windows |u| <= kUCut
-            // (one channel of margin each side), starting at an even offset
-            // to keep the pairing.
-            float flo = (-kUCut - ub) * inv_adv - 1.f, fhi = (kUCut - ub) * inv_adv + 1.f;
-            if (!(flo > -1e6f)) flo = -1e6f;
-            if (!(fhi < 1e6f)) fhi = 1e6f;
-            const int wlo = __reduce_min_sync(am, (int)floorf(flo));
-            const int whi = __reduce_max_sync(am, (int)ceilf(fhi));
-            int e = elo, e_stop = ehi;
-            if (wlo > elo) e = min(ehi, elo + ((wlo - elo) & ~1));
-            if (whi < ehi) e_stop = max(e, whi);
-            f32x2 S0 = Z2, S1 = Z2, S2 = Z2;
-            f32x2 FE = pk2((float)e, (float)(e + 1));
-#pragma unroll 6
-            for (; e + 2 <= e_stop; e += 2) {
-                f32x2 U = fma2(FE, ADV, UB);
-                f32x2 W = mul2(U, U);
-                float w0, w1;
-                upk2(W, w0, w1);
-                f32x2 G = pk2(ex2_approx(-w0), ex2_approx(-w1));
-                S0 = add2(S0, G); S1 = fma2(G, U, S1); S2 = fma2(G, W, S2);
-                FE = add2(FE, TWO);
-            }
-            s0 = hsum2(S0);
-            s1 = hsum2(S1);
-            s2 = hsum2(S2);
-            float fe = (float)e;
-            for (; e < e_stop; ++e, fe += 1.f) {
-                float u0 = fmaf(fe, adv, ub);
-                float w0 = u0 * u0;
-                float g0 = ex2_approx(-w0);
-                s0 += g0; s1 = fmaf(g0, u0, s1); s2 = fmaf(g0, w0, s2);
-            }
-        } else {
-            // some lane of the warp has its line outside the band: m = u + alpha sh
-            float su = al * sh;
-            s0 = s1 = s2 = 0.f;
-            float fe = (float)elo;
-            for (int e = elo; e < ehi; ++e, fe += 1.f) {
-                float u0 = fmaf(fe, adv, ub);
-                float m0 = u0 + su;
-                float g0 = ex2_approx(-u0 * u0);
-                float t0 = g0 * m0;
-                s0 += g0; s1 += t0; s2 = fmaf(t0, m0, s2);
-            }
-        }
-        float q0 = s0, q1 = s1 * inv_al, q2 = fmaf(s2, inv_al * inv_al, var_z * s0);
-
-        // edge blocks: E0 = sum g G0, B1 = sum g A1, B2 = sum g A2
-        for (int blk = 0; blk < 2; ++blk) {
-            int eb = blk ? ehi : 0, ee = blk ? g.ez : elo;
-            if (eb >= ee) continue;
-            {
-                // the block is passed over when every lane's |u| exceeds its
-                // cut over all of it (u is monotone in the channel: test the ends)
-                const float ua = fmaf((float)eb, adv, ub), uz = fmaf((float)(ee - 1), adv, ub);
-                const float cut = (sh != 0.f) ? kUFlush : kUCut;
-                const bool zero = (ua > cut && uz > cut) || (ua < -cut && uz < -cut);
-                if (__all_sync(am, zero)) continue;
-            }
-            const int toff = blk ? hi_off - ehi : 0;  // table slot = e + toff
-            f32x2 E0 = Z2, B1 = Z2, B2 = Z2;
-            f32x2 FK = pk2((float)eb, (float)(eb + 1));
-            int k = eb;
-#pragma unroll 3
-            for (; k + 2 <= ee; k += 2) {
-                f32x2 U = fma2(FK, ADV, UB);
-                f32x2 W = mul2(U, U);
-                float w0, w1;
-                upk2(W, w0, w1);
-                f32x2 G = pk2(ex2_approx(-w0), ex2_approx(-w1));
-                const int t = k + toff;
-                E0 = fma2(G, *reinterpret_cast<const f32x2 *>(eG0 + t), E0);
-                B1 = fma2(G, *reinterpret_cast<const f32x2 *>(eA1 + t), B1);
-                B2 = fma2(G, *reinterpret_cast<const f32x2 *>(eA2 + t), B2);
-                FK = add2(FK, TWO);
-            }
-            float e0 = hsum2(E0), b1 = hsum2(B1), b2 = hsum2(B2);
-            if (k < ee) {
-                float u0 = fmaf((float)k, adv, ub);
-                float g0 = ex2_approx(-u0 * u0);
-                e0 = fmaf(g0, eG0[k + toff], e0);
-                b1 = fmaf(g0, eA1[k + toff], b1);
-                b2 = fmaf(g0, eA2[k + toff], b2);
-            }
-            float dref = fmaf(blk ? eref_hi : eref_lo, g.dv, vz0) - a_c;
-            q0 += e0;
-            q1 += fmaf(dref, e0, b1);
-            q2 += fmaf(dref, fmaf(dref, e0, 2.f * b1), b2);
-        }
-        float A = c.amp * br;
-        Q[idx] = make_float4(A * q0, A * q1, A * q2, a_c);
+        const float x = (float)(xe - R), y = (float)(row0 + r - R);
+        Q[idx] = line_sums(g, c, lc, eG0, eA1, eA2, x, y);
         xe += dx_e; r += dr_e;
         if (xe >= g.ex) { xe -= g.ex; ++r; }
     }

@@ -1,0 +1,20 @@
+// k_split.h -- launcher of the two-stage fused evaluator (k_split.cu).
+#pragma once
+
+#include "gbk_internal.cuh"
+
+namespace gbk {
+
+constexpr int kSplitMaxR = 8;  // largest PSF radius the PSF stage is compiled for
+
+// Geometries the two-stage evaluator serves (cube model, u = 1, R <= 8).
+bool split_supported(const Geom &g);
+// Workspace of a call over n_models (0 when the geometry is not served).
+size_t split_workspace_bytes(const Geom &g, int n_models);
+// chi2 (and optionally maps and residuals) of n models; asynchronous on st.
+// Reads and clears the PSF stage's TMA wait status (1 = a load timed out).
+gbk_status split_status_read(int *v);
+gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_obs *obs, float *maps, double *chi2,
+                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace gbk

@@ -1,5 +1,6 @@
 // tma_util.cuh -- shared-memory addresses, mbarriers with bounded waits and
-// 3-D TMA tile loads used by the staged convolution kernels.
+// 3-D TMA tile loads used by the staged convolution kernels and the split
+// evaluator's PSF stage.
 #pragma once
 
 #include <cuda.h>
@@ -23,6 +24,24 @@ __device__ __forceinline__ void tma_load_slab(const CUtensorMap *tmap, float *ds
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Arms `bar` for `bytes` of transfers that the next tma_load_3d calls bring.
+__device__ __forceinline__ void tma_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Loads the box at (x, y, z) of `tmap` into dst; completion is counted on
+// `bar` (armed beforehand by tma_expect for the sum of the boxes' bytes).
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap *tmap, void *dst, uint64_t *bar, int x, int y, int z)
+{
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
             "r"(smem_u32(dst)),

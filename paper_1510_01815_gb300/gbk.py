@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libgbk.so")
 
 NPAR = 10
 GBK_OK, GBK_EINVAL, GBK_ECUDA, GBK_EWORKSPACE, GBK_EUNSUPPORTED = 0, 1, 2, 3, 4
-PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
+PATH_AUTO, PATH_FUSED, PATH_STAGED, PATH_SPLIT = 0, 1, 2, 3
 MODEL_CUBE, MODEL_VFIELD_ARCTAN, MODEL_VFIELD_EPINAT = 0, 1, 2
 JAC_FD_FORWARD, JAC_FD_CENTRAL, JAC_TANGENT = 0, 1, 2
 LM_BATCHED, LM_PLAIN = 0, 1
@@ -842,11 +842,18 @@ def workspace_for(geom, n_models, flags=PATH_AUTO, device="cuda"):
     return torch.empty(max(nb, 1), dtype=torch.uint8, device=device) if nb else None
 
 
-def eval_maps(geom, params, device="cuda", stream=None):
+def eval_maps(geom, params, device="cuda", stream=None, split=False):
+    """Maps of a batch: from the fused path (split=False; the staged path
+    where the fused one does not serve) or from the split path (split=True)."""
     params = params.to(device=device, dtype=torch.float64).contiguous()
     n = params.shape[0]
     maps = torch.empty((n, 3, geom.ny, geom.nx), dtype=torch.float32, device=device)
-    ws = workspace_for(geom, n, PATH_AUTO, device) if getattr(geom, "upsample", 1) > 1 else None
+    if split:
+        ws = workspace_for(geom, n, PATH_SPLIT, device)
+        if ws is None:
+            raise GbkError(GBK_EUNSUPPORTED, "the split path does not serve this geometry")
+    else:
+        ws = workspace_for(geom, n, PATH_AUTO, device) if getattr(geom, "upsample", 1) > 1 else None
     gbk_eval_cubes(geom, params, maps=maps, workspace=ws, stream=stream)
     return maps
 

@@ -58,7 +58,8 @@ def test_workspace_sizes(gbk):
     # fused path needs none; the staged path holds the extended cube, the data
     # cube and the chi2 partials
     assert gbk.gbk_workspace_bytes(SINGLE_GEOM, 10, gbk.PATH_FUSED) == 0
-    assert gbk.gbk_workspace_bytes(SINGLE_GEOM, 10, gbk.PATH_AUTO) == 0
+    assert gbk.gbk_workspace_bytes(SINGLE_GEOM, 10, gbk.PATH_AUTO) == gbk.gbk_workspace_bytes(SINGLE_GEOM, 10,
+                                                                                               gbk.PATH_SPLIT) > 0
     n = 7
     ws = gbk.gbk_workspace_bytes(SINGLE_GEOM, n, gbk.PATH_STAGED)
     # 32x32x64, R = 5 (PSF FWHM 2.5), Rz = 3 (LSF 30 km/s at 20 km/s)
@@ -68,6 +69,15 @@ def test_workspace_sizes(gbk):
     al = lambda b: (b + 255) // 256 * 256
     assert ws == al(ext) + al(data) + al(part)
     assert gbk.gbk_workspace_bytes(GRID_GEOM.with_(upsample=2), 1, gbk.PATH_AUTO) > 0
+    # split path: per-model constants (60 B), the tables (taps and LSF edge
+    # tables: 24 + 3 x 12 floats at Rz = 3), then for the models of a chunk
+    # four x-filtered planes of ey x pad4(nx) floats (42 x 32), one chi2 part
+    # per 64 x 32 tile and an arrival counter
+    assert gbk.gbk_workspace_bytes(SINGLE_GEOM, n, gbk.PATH_SPLIT) == \
+        al(60 * n) + al(4 * (24 + 3 * 12)) + al(4 * 42 * 32 * 4 * n) + al(8 * n) + al(4 * n)
+    # the Fabry-Perot geometry: chunks of 48 MiB / (4 x 204 x 192 x 4 B) = 80 models
+    fp = gbk.gbk_workspace_bytes(FP_GEOM, 400, gbk.PATH_SPLIT)
+    assert fp == al(60 * 400) + al(4 * (24 + 3 * 24)) + al(4 * 204 * 192 * 4 * 80) + al(8 * 18 * 80) + al(4 * 80)
 
 
 @pytest.mark.parametrize("bad", [

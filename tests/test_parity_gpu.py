@@ -58,6 +58,57 @@ def test_maps_fused_vs_oracle(G, case):
         assert (ref[0, 0] >= 2e-20).sum() > 900 and ref[0, 0].max() < 1e-16
 
 
+# The split path (two stages meeting in an L2-resident buffer of moment
+# triplets) serves PSF radii up to 8 px: every case but wide_kernels.
+SPLIT_CASES = [c for c in sorted(CASES) if c != "wide_kernels"]
+
+
+@pytest.mark.parametrize("case", SPLIT_CASES)
+def test_maps_split_vs_oracle(G, case):
+    g, p, ps = _params(case)
+    ref = oracle.evaluate_batch(ogeom(g), ps)
+    maps = G.eval_maps(g, torch.from_numpy(ps), split=True).cpu().numpy()
+    check_maps(maps, ref, ps, case + " (split)")
+    # the fused path's arithmetic, spaxels grouped into warps differently:
+    # the sums differ only by terms below 2^-36 of the line peak and by FP32
+    # rounding, so the maps agree far inside the oracle tolerance
+    fused = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    for k in range(3):
+        scale = np.nanmax(np.abs(fused[:, k])) if np.isfinite(fused[:, k]).any() else 1.0
+        np.testing.assert_allclose(maps[:, k], fused[:, k], rtol=1e-5, atol=1e-6 * scale)
+
+
+def test_split_refuses_wide_kernels(G):
+    g, p, ps = _params("wide_kernels")
+    assert G.gbk_workspace_bytes(g, 4, G.PATH_SPLIT) == 0
+    obs = make_obs(g, p, seed=3)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(G.GbkError) as ei:
+        G.gbk_chi2(g, torch.from_numpy(ps).cuda(), dobs, out, None, G.PATH_SPLIT, None)
+    assert ei.value.status == G.GBK_EUNSUPPORTED
+    # the automatic choice falls back to the fused path
+    c = G.chi2(g, torch.from_numpy(ps), dobs).cpu().numpy()
+    np.testing.assert_allclose(c, oracle.chi2_batch(ogeom(g), ps, obs), rtol=1e-3)
+
+
+def test_split_needs_its_workspace(G):
+    g, p, ps = _params("single")
+    obs = make_obs(g, p, seed=3)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    need = G.gbk_workspace_bytes(g, 4, G.PATH_SPLIT)
+    assert need > 0 and G.gbk_workspace_bytes(g, 4, G.PATH_AUTO) == need
+    small = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(G.GbkError) as ei:
+        G.gbk_chi2(g, torch.from_numpy(ps).cuda(), dobs, out, None, G.PATH_SPLIT, small)
+    assert ei.value.status == G.GBK_EWORKSPACE
+    # AUTO with too small a workspace (or none) takes the fused path
+    G.gbk_chi2(g, torch.from_numpy(ps).cuda(), dobs, out, None, G.PATH_AUTO, small)
+    ref = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED)
+    assert torch.equal(out, ref)
+
+
 @pytest.mark.parametrize("case", ["single", "single_mode1", "tiny_1x1x1", "odd_3x5x7", "narrow_band",
                                   "wide_kernels", "nonsquare", "edge_on", "line_beyond_band"])
 def test_cube_and_maps_staged_vs_oracle(G, case):
@@ -86,17 +137,19 @@ def test_upsampled_staged_vs_oracle(G, u, case):
 
 
 @pytest.mark.parametrize("case", ["single", "single_mode1", "grid64", "nonsquare", "edge_on", "prime_13x11x17"])
-@pytest.mark.parametrize("path", ["fused", "staged"])
+@pytest.mark.parametrize("path", ["fused", "staged", "split"])
 def test_chi2_vs_oracle(G, case, path):
     g, p, ps = _params(case, n=5, seed=11)
     obs = make_obs(g, p, seed=3)
-    flags = G.PATH_FUSED if path == "fused" else G.PATH_STAGED
+    flags = {"fused": G.PATH_FUSED, "staged": G.PATH_STAGED, "split": G.PATH_SPLIT}[path]
     dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
     c, resid = G.chi2(g, torch.from_numpy(ps), dobs, flags=flags, want_resid=True)
     c, resid = c.cpu().numpy(), resid.cpu().numpy()
     ref_c, ref_r = oracle.chi2_batch(ogeom(g), ps, obs, want_resid=True)
     if path == "fused":
         gmaps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
+    elif path == "split":
+        gmaps = G.eval_maps(g, torch.from_numpy(ps), split=True).cpu().numpy()
     else:
         gmaps = G.eval_cubes(g, torch.from_numpy(ps))[1].cpu().numpy()
     rmaps = oracle.evaluate_batch(ogeom(g), ps)
@@ -185,13 +238,14 @@ def test_invalid_parameters_give_nan(G):
     obs = make_obs(g, synth.SINGLE_TRUTH, seed=1)
     dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
     ref = oracle.chi2_batch(ogeom(g), ps, obs)  # the same parameter domain on both sides
-    for flags in (G.PATH_FUSED, G.PATH_STAGED):
+    for flags in (G.PATH_FUSED, G.PATH_STAGED, G.PATH_SPLIT):
         c = G.chi2(g, torch.from_numpy(ps), dobs, flags=flags).cpu().numpy()
         assert np.isfinite(c[0]) and np.all(np.isnan(c[1:])), (flags, c)
         assert np.array_equal(np.isnan(c), np.isnan(ref)), (flags, c, ref)
-    maps = G.eval_maps(g, torch.from_numpy(ps)).cpu().numpy()
-    assert np.isfinite(maps[0]).all() and np.isnan(maps[1:]).all()
-    assert np.array_equal(np.isnan(maps), np.isnan(oracle.evaluate_batch(ogeom(g), ps)))
+    for split in (False, True):
+        maps = G.eval_maps(g, torch.from_numpy(ps), split=split).cpu().numpy()
+        assert np.isfinite(maps[0]).all() and np.isnan(maps[1:]).all()
+        assert np.array_equal(np.isnan(maps), np.isnan(oracle.evaluate_batch(ogeom(g), ps)))
 
 
 def test_fused_and_staged_agree(G):
@@ -201,6 +255,35 @@ def test_fused_and_staged_agree(G):
     a = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED).cpu().numpy()
     b = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_STAGED).cpu().numpy()
     np.testing.assert_allclose(a, b, rtol=2e-4)
+
+
+@pytest.mark.slow
+def test_fabry_perot_split_in_chunks(G):
+    """192 x 192 x 48, 150 models: more than one L2-sized chunk of the split
+    path (80 models each), each chunk's chi2 and maps against the fused
+    path and sampled models against the oracle, in the batch the benchmark
+    times (400 models) as well."""
+    g = synth.FP_GEOM
+    rng = np.random.default_rng(23)
+    for n in (150, 400):
+        ps = synth.draw_fp_params(rng, n)
+        p_true = ps[0]
+        m_true = oracle.evaluate(ogeom(g), p_true)
+        shape = (g.ny, g.nx)
+        obs = oracle.Obs((m_true[1] + rng.normal(0, 5, shape)).astype(np.float32),
+                         (m_true[2] + rng.normal(0, 7.07, shape)).astype(np.float32),
+                         *synth.weights(shape, 5.0),
+                         (synth.sn_mask(m_true[0]) * synth.dead_fibre_mask(rng, shape)).astype(np.uint8))
+        dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+        cs = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_SPLIT).cpu().numpy()
+        cf = G.chi2(g, torch.from_numpy(ps), dobs, flags=G.PATH_FUSED).cpu().numpy()
+        np.testing.assert_allclose(cs, cf, rtol=1e-5)
+        ms = G.eval_maps(g, torch.from_numpy(ps), split=True).cpu().numpy()
+        for i in (0, 79, 80, n - 1):
+            rm = oracle.evaluate(ogeom(g), ps[i])
+            check_maps(ms[i:i + 1], rm[None], ps[i:i + 1], "fp split model %d of %d" % (i, n))
+            rc = oracle.chi2_maps(rm, obs)
+            assert abs(cs[i] - rc) <= chi2_bound(rm, ms[i], obs, rc), (i, cs[i], rc)
 
 
 @pytest.mark.slow
