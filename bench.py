@@ -48,6 +48,10 @@ OPS_PER_EXT_VOXEL = FMA_OPS_PER_EXT_VOXEL + MUFU_OPS_PER_EXT_VOXEL
 # and of the moments, residuals and chi2 of one data spaxel.
 OPS_PER_PSF_TAP = 9
 OPS_PER_DATA_SPAXEL = 10
+# The split path's PSF tap: s0 and s1 accumulated about zero, s2 re-centred
+# exactly (s0 += w q0; s1 += w (q1 + a q0); s2 += w (q2 + D (2 q1 + D q0)),
+# D = a - c): six FP32 operations.
+OPS_PER_PSF_TAP_SPLIT = 6
 # Per-unit work of the unfolded method (cube + separable PSF x LSF
 # convolution + moments) at the Fabry-Perot size, in FP32 instructions per
 # data voxel: the line (an ex2 and 3 FP32 per extended voxel, 1.41 extended
@@ -89,9 +93,9 @@ def parse():
     ap.add_argument("--cnn-epochs", type=int, default=2)
     ap.add_argument("--cnn-batch", type=int, default=1024)
     ap.add_argument("--cnn-test", type=int, default=4096, help="held-out galaxies of the seed comparison")
-    ap.add_argument("--path", default="fused", choices=["fused", "staged", "split"],
-                    help="fused (default), staged (cube materialised in HBM) or split (line and PSF stages "
-                         "through an L2-resident buffer) evaluation")
+    ap.add_argument("--path", default="split", choices=["fused", "staged", "split"],
+                    help="split (default: line and PSF stages through an L2-resident buffer), fused (one "
+                         "cluster of CTAs per model) or staged (cube materialised in HBM) evaluation")
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
     ap.add_argument("--tuning", default=None,
                     help="CTAS,THREADS,PERSISTENT: use this fused-kernel tuning instead of autotuning")
@@ -1148,6 +1152,20 @@ def run_gbk(args):
                                  "persistent": tuning["persistent"], "candidates": tuning["candidates"]},
                       "parallelism": "replicas" if ws > 1 else "single"},
            "gpu_launches": K * (4 if staged else 1)}
+    if split:
+        # per-launch CUDA events (gbk_split_stage_times) over K further steps
+        # of the same batches, L2 flushed before each: the kernels' times
+        stage_reps, nl = [], 0
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            st_ms, nl = gbk.gbk_split_stage_times(g, pool[W + k], obs, chi2[W + k], ws_split, stream)
+            stage_reps.append(st_ms)
+        stage_mean = np.mean(np.array(stage_reps), axis=0)
+        out["gpu_launches"] = K * nl
+        out["stages"] = [{"stage": name, "kernel": kern, "ms_per_step": float(t), "share": float(t / sum(stage_mean))}
+                         for name, kern, t in zip(("set-up", "line sums + PSF along x", "PSF along y + moments + chi2"),
+                                                  ("split_setup_kernel", "split_line_kernel", "split_psf_kernel"),
+                                                  stage_mean)]
     if staged:
         out["config"]["path"] = "staged"
     if args.quick:
@@ -1190,36 +1208,71 @@ def run_gbk(args):
             print(json.dumps(out))
         return
 
-    # ---- roofline of the fused kernel: ALU (FP32 pipe + MUFU ex2) ----
-    # Algorithmic work per model of the folded method: the line sampling
-    # (5 FP32 + 1 ex2 per extended voxel), the two exact PSF passes on the
-    # moment triplets (x over ey * nx, y over ny * nx outputs, 2R + 1 taps)
-    # and the moments/residuals/chi2 of each data spaxel.
-    taps = 2 * ((ex - g.nx) // 2) + 1
-    fma_model = (FMA_OPS_PER_EXT_VOXEL * ex * ey * ez + OPS_PER_PSF_TAP * taps * (ey * g.nx + g.ny * g.nx)
-                 + OPS_PER_DATA_SPAXEL * g.nx * g.ny)
-    mufu_model = MUFU_OPS_PER_EXT_VOXEL * ex * ey * ez
-    r32, r32x2, rmu = gbk.gbk_measure_alu_peak(stream)
-    rfma = max(r32, r32x2)
-    t_min = max(fma_model / rfma, mufu_model / rmu)
-    peak_ops = (fma_model + mufu_model) / t_min
-    achieved_ops = (fma_model + mufu_model) * n / (ms_step * 1e-3)
-    tuned = (tuning["cluster_ctas"], tuning["threads"], tuning["persistent"])
-    traffic = FUSED_TRAFFIC_400.get(tuned) if n == 400 else None
-    out["roofline"] = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                       "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
-                       "traffic_note": "DRAM bytes per launch from one ncu capture at this tuning "
-                                       "(algorithmic: 0.66 MB of parameters, observed maps and chi2)"
-                                       if traffic else "no capture at this configuration",
-                       "kernel": "fused_eval_kernel",
-                       "basis": "per model %.1f M FP32 + %.1f M ex2 lane ops: %d FP32 + %d ex2 per extended voxel "
-                                "(%d x %d x %d), %d per PSF tap on the moment triplets (%d taps; x pass %d x %d, "
-                                "y pass %d x %d outputs), %d per data spaxel; measured FP32 pipe %.1f T lane-ops/s "
-                                "(scalar %.1f, f32x2 %.1f), ex2 %.1f T/s"
-                                % (fma_model / 1e6, mufu_model / 1e6, FMA_OPS_PER_EXT_VOXEL, MUFU_OPS_PER_EXT_VOXEL,
-                                   ex, ey, ez, OPS_PER_PSF_TAP, taps, ey, g.nx, g.ny, g.nx, OPS_PER_DATA_SPAXEL,
-                                   rfma / 1e12, r32 / 1e12, r32x2 / 1e12, rmu / 1e12),
-                       "peak_source": "measured on this device by gbk_measure_alu_peak"}
+    if split:
+        # ---- roofline of the dominant kernel: the line stage, ALU bound ----
+        # Algorithmic work per model: the line sampling (5 FP32 + 1 ex2 per
+        # extended voxel) and the PSF pass along x of every extended row
+        # (6 FP32 per tap per output, ey x nx outputs).
+        taps = 2 * ((ex - g.nx) // 2) + 1
+        fma_a = FMA_OPS_PER_EXT_VOXEL * ex * ey * ez + OPS_PER_PSF_TAP_SPLIT * taps * ey * g.nx
+        mufu_a = MUFU_OPS_PER_EXT_VOXEL * ex * ey * ez
+        r32, r32x2, rmu = gbk.gbk_measure_alu_peak(stream)
+        rfma = max(r32, r32x2)
+        t_min = max(fma_a / rfma, mufu_a / rmu)
+        peak_ops = (fma_a + mufu_a) / t_min
+        t_a = out["stages"][1]["ms_per_step"] * 1e-3
+        achieved_ops = (fma_a + mufu_a) * n / t_a
+        out["roofline"] = {
+            "bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved_ops / peak_ops, "traffic": None,
+            "traffic_note": "not captured by this run (the kernel's DRAM traffic is the 16 B x-filtered "
+                            "triplet per data-column spaxel of each row, written to an L2-resident buffer)",
+            "kernel": "split_line_kernel",
+            "basis": "per model %.1f M FP32 + %.1f M ex2 lane ops: %d FP32 + %d ex2 per extended voxel (%d x %d x "
+                     "%d), %d FP32 per PSF tap along x (%d taps, %d x %d outputs); its time per step from CUDA "
+                     "events around each launch (%.3f ms of %.3f); measured FP32 pipe %.1f T lane-ops/s (scalar "
+                     "%.1f, f32x2 %.1f), ex2 %.1f T/s"
+                     % (fma_a / 1e6, mufu_a / 1e6, FMA_OPS_PER_EXT_VOXEL, MUFU_OPS_PER_EXT_VOXEL, ex, ey, ez,
+                        OPS_PER_PSF_TAP_SPLIT, taps, ey, g.nx, t_a * 1e3, sum(st["ms_per_step"] for st in out["stages"]),
+                        rfma / 1e12, r32 / 1e12, r32x2 / 1e12, rmu / 1e12),
+            "peak_source": "measured on this device by gbk_measure_alu_peak"}
+        # the whole step on the same basis (both stages, every launch)
+        fma_all = fma_a + OPS_PER_PSF_TAP_SPLIT * taps * g.ny * g.nx + OPS_PER_DATA_SPAXEL * g.nx * g.ny
+        out["roofline_whole_step"] = {
+            "achieved": (fma_all + mufu_a) * n / (ms_step * 1e-3) / 1e12, "unit": "Tops/s",
+            "frac": (fma_all + mufu_a) * n / (ms_step * 1e-3) / ((fma_all + mufu_a) / max(fma_all / rfma, mufu_a / rmu)),
+            "basis": "both stages: %.1f M FP32 + %.1f M ex2 per model over the step time" % (fma_all / 1e6, mufu_a / 1e6)}
+    if not split:
+        # ---- roofline of the fused kernel: ALU (FP32 pipe + MUFU ex2) ----
+        # Algorithmic work per model of the folded method: the line sampling
+        # (5 FP32 + 1 ex2 per extended voxel), the two exact PSF passes on the
+        # moment triplets (x over ey * nx, y over ny * nx outputs, 2R + 1 taps)
+        # and the moments/residuals/chi2 of each data spaxel.
+        taps = 2 * ((ex - g.nx) // 2) + 1
+        fma_model = (FMA_OPS_PER_EXT_VOXEL * ex * ey * ez + OPS_PER_PSF_TAP * taps * (ey * g.nx + g.ny * g.nx)
+                     + OPS_PER_DATA_SPAXEL * g.nx * g.ny)
+        mufu_model = MUFU_OPS_PER_EXT_VOXEL * ex * ey * ez
+        r32, r32x2, rmu = gbk.gbk_measure_alu_peak(stream)
+        rfma = max(r32, r32x2)
+        t_min = max(fma_model / rfma, mufu_model / rmu)
+        peak_ops = (fma_model + mufu_model) / t_min
+        achieved_ops = (fma_model + mufu_model) * n / (ms_step * 1e-3)
+        tuned = (tuning["cluster_ctas"], tuning["threads"], tuning["persistent"])
+        traffic = FUSED_TRAFFIC_400.get(tuned) if n == 400 else None
+        out["roofline"] = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                           "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
+                           "traffic_note": "DRAM bytes per launch from one ncu capture at this tuning "
+                                           "(algorithmic: 0.66 MB of parameters, observed maps and chi2)"
+                                           if traffic else "no capture at this configuration",
+                           "kernel": "fused_eval_kernel",
+                           "basis": "per model %.1f M FP32 + %.1f M ex2 lane ops: %d FP32 + %d ex2 per extended voxel "
+                                    "(%d x %d x %d), %d per PSF tap on the moment triplets (%d taps; x pass %d x %d, "
+                                    "y pass %d x %d outputs), %d per data spaxel; measured FP32 pipe %.1f T lane-ops/s "
+                                    "(scalar %.1f, f32x2 %.1f), ex2 %.1f T/s"
+                                    % (fma_model / 1e6, mufu_model / 1e6, FMA_OPS_PER_EXT_VOXEL, MUFU_OPS_PER_EXT_VOXEL,
+                                       ex, ey, ez, OPS_PER_PSF_TAP, taps, ey, g.nx, g.ny, g.nx, OPS_PER_DATA_SPAXEL,
+                                       rfma / 1e12, r32 / 1e12, r32x2 / 1e12, rmu / 1e12),
+                           "peak_source": "measured on this device by gbk_measure_alu_peak"}
     data_vox = g.nx * g.ny * g.nz
     sv = UNFOLDED_FP32_PER_DATA_VOXEL * data_vox * n / (ms_step * 1e-3)
     out["roofline_unfolded_basis"] = {
@@ -1243,7 +1296,10 @@ def run_gbk(args):
         d_params.copy_(pin_params[s], non_blocking=True)
         for d, h in zip(d_obs, pin_obs):
             d.copy_(h, non_blocking=True)
-        gbk.gbk_chi2(g, d_params, e_obs, d_chi2, None, gbk.PATH_AUTO, None, stream)
+        if split:
+            gbk.gbk_chi2(g, d_params, e_obs, d_chi2, None, gbk.PATH_SPLIT, ws_split, stream)
+        else:
+            gbk.gbk_chi2(g, d_params, e_obs, d_chi2, None, gbk.PATH_AUTO, None, stream)
         pin_chi2[s].copy_(d_chi2, non_blocking=True)
 
     for s in range(W):
@@ -1264,7 +1320,7 @@ def run_gbk(args):
                   "d2h_bytes_per_step": n * 8}
     ok = np.allclose(pin_chi2[W:].numpy(), chi2[W:].cpu().numpy(), rtol=0, atol=0)
     out["e2e"]["matches_device_run"] = bool(ok)
-    out["gpu_launches_e2e"] = K
+    out["gpu_launches_e2e"] = out["gpu_launches"]
 
     # The single-GPU measurements below describe one GPU; a multi-GPU run
     # (weak scaling of the headline) skips them.

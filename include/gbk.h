@@ -215,6 +215,18 @@ GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *p
 GBK_API gbk_status gbk_chi2_noalloc(const gbk_geom *g, int32_t n_models, const double *params,
                                     const gbk_obs *obs, double *chi2, float *resid, void *stream);
 
+/* gbk_chi2 on the split path (GBK_PATH_SPLIT), timed per stage with CUDA
+ * events recorded on `stream` around every launch: stage_ms (host [3])
+ * receives the milliseconds of the set-up kernel, of the line stage (the
+ * Gaussian lines folded into moment triplets and the PSF along x,
+ * Sec. 2.2.2-2.2.3) and of the PSF-along-y stage with the moments and chi2
+ * (Sec. 2.2.3-2.2.6), each summed over the model chunks; launches (host, or
+ * NULL) the number of kernel launches.  Workspace as for gbk_chi2 on the split
+ * path; at most 31 chunks; synchronises `stream`. */
+GBK_API gbk_status gbk_split_stage_times(const gbk_geom *g, int32_t n_models, const double *params,
+                                         const gbk_obs *obs, double *chi2, void *workspace, size_t ws_bytes,
+                                         float *stage_ms, int32_t *launches, void *stream);
+
 /* gbk_chi2 on the staged path (GBK_PATH_STAGED), timed per stage with CUDA
  * events on `stream` -- the per-step timings of the paper's GPU pipeline
  * (Sec. 5): stage_ms (host [4]) receives the milliseconds of the model cube

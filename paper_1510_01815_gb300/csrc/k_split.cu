@@ -257,6 +257,24 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
     for (int t = tid; t < kSplitTX * (kSplitTY / 4); t += kSplitThreads) {
         const int x = t % kSplitTX, gy = 4 * (t / kSplitTX);
         if (x >= nxo || gy >= nyo) continue;
+        // the observed values of the four outputs first: their latency
+        // overlaps the y pass
+        uint8_t mk[4] = {0, 0, 0, 0};
+        float vo[4] = {0.f, 0.f, 0.f, 0.f}, so[4] = {0.f, 0.f, 0.f, 0.f};
+        float wv[4] = {0.f, 0.f, 0.f, 0.f}, ws[4] = {0.f, 0.f, 0.f, 0.f};
+        if (want_obs) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                if (gy + o < nyo) {
+                    const size_t pix = (size_t)(ty0 + gy + o) * g.nx + (tx0 + x);
+                    mk[o] = __ldg(s_ob.mask + pix);
+                    vo[o] = __ldg(s_ob.v_obs + pix);
+                    so[o] = __ldg(s_ob.s_obs + pix);
+                    wv[o] = __ldg(s_ob.w_v + pix);
+                    ws[o] = __ldg(s_ob.w_s + pix);
+                }
+            }
+        }
         float s[4][3], cen[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
@@ -279,15 +297,6 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
             const int yl = gy + o;
             if (yl >= nyo) break;
             const size_t pix = (size_t)(ty0 + yl) * g.nx + (tx0 + x);
-            uint8_t mk = 0;
-            float vo = 0.f, so = 0.f, wv = 0.f, ws = 0.f;
-            if (want_obs) {
-                mk = s_ob.mask[pix];
-                vo = s_ob.v_obs[pix];
-                so = s_ob.s_obs[pix];
-                wv = s_ob.w_v[pix];
-                ws = s_ob.w_s[pix];
-            }
             const float s0 = s[o][0], s1 = fmaf(-cen[o], s[o][0], s[o][1]), s2 = s[o][2];
             float m0, m1, m2;
             const bool valid = s0 > thr;
@@ -309,9 +318,9 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
             }
             if (want_obs) {
                 float rv = 0.f, rs = 0.f;
-                if (mk != 0 && (valid || !c.valid)) {
-                    rv = wv * (m1 - vo);
-                    rs = ws * (m2 - so);
+                if (mk[o] != 0 && (valid || !c.valid)) {
+                    rv = wv[o] * (m1 - vo[o]);
+                    rs = ws[o] * (m2 - so[o]);
                 }
                 acc.add(rv * rv);
                 acc.add(rs * rs);
@@ -424,7 +433,7 @@ gbk_status split_status_read(int *v)
 }
 
 template <int R>
-static gbk_status launch_stages(const CUtensorMap &tm, const SplitArgs &a, cudaStream_t st)
+static gbk_status launch_stages(const CUtensorMap &tm, const SplitArgs &a, cudaStream_t st, SplitTimer *timer)
 {
     static KernelAttrMemo memo_a, memo_b;
     const size_t sa = split_smem_a(a.g), sb = split_smem_b(R);
@@ -438,13 +447,15 @@ static gbk_status launch_stages(const CUtensorMap &tm, const SplitArgs &a, cudaS
     split_line_kernel<R><<<dim3(blocks_a, (unsigned)a.n_models), kSplitThreads, sa, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "split evaluator: line stage launch");
+    if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
     split_psf_kernel<R><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kSplitThreads, sb, st>>>(tm, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split evaluator: PSF stage launch");
+    if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
     return GBK_OK;
 }
 
 gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_obs *obs, float *maps, double *chi2,
-                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st)
+                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer)
 {
     if (!split_supported(g)) return fail(GBK_EUNSUPPORTED, "the split evaluator does not serve this geometry");
     if (n == 0) return GBK_OK;
@@ -472,8 +483,10 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(GBK_ECUDA, "split evaluator: cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
+    if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
     split_setup_kernel<<<(n + 127) / 128, 128, 0, st>>>(params, n, g, mcs, tab);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split evaluator: set-up launch");
+    if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
     const size_t np = (size_t)g.nx * g.ny;
     for (int m0 = 0; m0 < n; m0 += L.chunk) {
         SplitArgs a = {};
@@ -494,15 +507,15 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
         a.tiles = L.tiles;
         gbk_status s;
         switch (g.R) {
-        case 0: s = launch_stages<0>(tm, a, st); break;
-        case 1: s = launch_stages<1>(tm, a, st); break;
-        case 2: s = launch_stages<2>(tm, a, st); break;
-        case 3: s = launch_stages<3>(tm, a, st); break;
-        case 4: s = launch_stages<4>(tm, a, st); break;
-        case 5: s = launch_stages<5>(tm, a, st); break;
-        case 6: s = launch_stages<6>(tm, a, st); break;
-        case 7: s = launch_stages<7>(tm, a, st); break;
-        case 8: s = launch_stages<8>(tm, a, st); break;
+        case 0: s = launch_stages<0>(tm, a, st, timer); break;
+        case 1: s = launch_stages<1>(tm, a, st, timer); break;
+        case 2: s = launch_stages<2>(tm, a, st, timer); break;
+        case 3: s = launch_stages<3>(tm, a, st, timer); break;
+        case 4: s = launch_stages<4>(tm, a, st, timer); break;
+        case 5: s = launch_stages<5>(tm, a, st, timer); break;
+        case 6: s = launch_stages<6>(tm, a, st, timer); break;
+        case 7: s = launch_stages<7>(tm, a, st, timer); break;
+        case 8: s = launch_stages<8>(tm, a, st, timer); break;
         default: return fail(GBK_EUNSUPPORTED, "split evaluator: PSF radius %d > %d", g.R, kSplitMaxR);
         }
         if (s) return s;
@@ -511,3 +524,38 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
 }
 
 }  // namespace gbk
+
+using namespace gbk;
+
+extern "C" gbk_status gbk_split_stage_times(const gbk_geom *gin, int32_t n_models, const double *params,
+                                            const gbk_obs *obs, double *chi2, void *workspace, size_t ws_bytes,
+                                            float *stage_ms, int32_t *launches, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    if (n_models < 1) return fail(GBK_EINVAL, "n_models must be >= 1");
+    if (!stage_ms) return fail(GBK_EINVAL, "stage_ms is NULL");
+    if ((s = check_device_ptr(params, "params", 8)) || (s = check_device_ptr(chi2, "chi2", 8)) || (s = check_obs(obs)))
+        return s;
+    if (workspace && (s = check_device_ptr(workspace, "workspace", 256))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    SplitTimer timer;
+    s = launch_split(g, n_models, params, obs, nullptr, chi2, nullptr, workspace, ws_bytes, st, &timer);
+    cudaError_t e = cudaSuccess;
+    if (!s && timer.n > 0) e = cudaEventSynchronize(timer.ev[timer.n - 1]);
+    if (!s && e == cudaSuccess) {
+        // events: start, after set-up, then after each stage A and stage B launch
+        stage_ms[0] = stage_ms[1] = stage_ms[2] = 0.f;
+        for (int i = 1; i < timer.n && e == cudaSuccess; ++i) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, timer.ev[i - 1], timer.ev[i]);
+            stage_ms[i == 1 ? 0 : ((i % 2 == 0) ? 1 : 2)] += ms;
+        }
+        if (launches) *launches = timer.n - 1;
+    }
+    timer.release();
+    if (s) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "split stage times");
+    return ok();
+}

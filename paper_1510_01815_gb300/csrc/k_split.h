@@ -12,9 +12,29 @@ bool split_supported(const Geom &g);
 // Workspace of a call over n_models (0 when the geometry is not served).
 size_t split_workspace_bytes(const Geom &g, int n_models);
 // chi2 (and optionally maps and residuals) of n models; asynchronous on st.
+// CUDA events recorded on the launch stream around every launch of a call
+// (start, after the set-up, after each stage-A and stage-B launch), for the
+// per-stage timings of gbk_split_stage_times.
+struct SplitTimer {
+    cudaEvent_t ev[64] = {};
+    int n = 0;
+    cudaError_t mark(cudaStream_t st)
+    {
+        if (n >= 64) return cudaErrorInvalidValue;
+        cudaError_t e = cudaEventCreate(&ev[n]);
+        if (e != cudaSuccess) return e;
+        return cudaEventRecord(ev[n++], st);
+    }
+    void release()
+    {
+        for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+        n = 0;
+    }
+};
+
 // Reads and clears the PSF stage's TMA wait status (1 = a load timed out).
 gbk_status split_status_read(int *v);
 gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_obs *obs, float *maps, double *chi2,
-                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st);
+                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer = nullptr);
 
 }  // namespace gbk

@@ -83,6 +83,8 @@ def lib():
             "gbk_chi2": (i32, [gp, i32, vp, op, vp, vp, u32, vp, sz, vp]),
             "gbk_chi2_from_maps": (i32, [i32, i32, i32, vp, op, vp, vp, vp]),
             "gbk_chi2_stage_times": (i32, [gp, i32, vp, op, vp, vp, sz, ctypes.POINTER(ctypes.c_float), vp]),
+            "gbk_split_stage_times": (i32, [gp, i32, vp, op, vp, vp, sz, ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_int32), vp]),
             "gbk_chi2_noalloc": (i32, [gp, i32, vp, op, vp, vp, vp]),
             "gbk_measure_alu_peak": (i32, [ctypes.POINTER(ctypes.c_double)] * 3 + [vp]),
             "gbk_autotune": (i32, [gp, i32, vp, op, vp, ctypes.POINTER(CTuning), vp]),
@@ -143,7 +145,8 @@ def lib():
 
 
 def exported_symbols():
-    return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_stage_times", "gbk_chi2_noalloc",
+    return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_stage_times", "gbk_split_stage_times",
+            "gbk_chi2_noalloc",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_fit_lm_fallback_workspace_bytes", "gbk_fit_lm_fallback",
             "gbk_wait_selfcheck",
@@ -235,6 +238,21 @@ def gbk_chi2(geom, params, obs, chi2, resid=None, flags=PATH_AUTO, workspace=Non
                           ctypes.byref(obs.c()), _ptr(chi2, torch.float64, "chi2"),
                           _ptr(resid, torch.float32, "resid"), int(flags),
                           _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def gbk_split_stage_times(geom, params, obs, chi2, workspace, stream=None):
+    """gbk_chi2 on the split path, timed per stage; returns ([set-up, line
+    stage, PSF/moments stage] milliseconds, kernel launches)."""
+    g = cgeom(geom)
+    n = params.shape[0] if params.dim() == 2 else params.numel() // NPAR
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ms = (ctypes.c_float * 3)()
+    nl = ctypes.c_int32()
+    _check(lib().gbk_split_stage_times(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"),
+                                       ctypes.byref(obs.c()), _ptr(chi2, torch.float64, "chi2"),
+                                       _ptr(workspace, None, "workspace"), ws_bytes, ms, ctypes.byref(nl),
+                                       _stream(stream)))
+    return [float(v) for v in ms], nl.value
 
 
 def gbk_chi2_stage_times(geom, params, obs, chi2, workspace, stream=None):
