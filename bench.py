@@ -64,6 +64,11 @@ UNFOLDED_FP32_PER_DATA_VOXEL = 47.0
 # GB300 (dram__bytes_read.sum + dram__bytes_write.sum of the fused launch);
 # reported only for a run at that tuning and with that kernel build.
 FUSED_TRAFFIC_400 = {(12, 512, 0): 1433600.0, (12, 512, 1): 1318400.0}
+# DRAM bytes (read + write) of one launch of the split path's line stage
+# (80 Fabry-Perot models, the chunk of a 400-model step), as measured by a
+# one-pass ncu capture of `bench.py --quick --steps 5 --warmup 2` on a GB300:
+# 35 020 B read + 5 683 B written; reported only for the 400-model step.
+SPLIT_LINE_TRAFFIC_80 = 40704.0
 FLUSH_BYTES = 256 << 20
 
 
@@ -1224,9 +1229,10 @@ def run_gbk(args):
         achieved_ops = (fma_a + mufu_a) * n / t_a
         out["roofline"] = {
             "bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved_ops / peak_ops, "traffic": None,
-            "traffic_note": "not captured by this run (the kernel's DRAM traffic is the 16 B x-filtered "
-                            "triplet per data-column spaxel of each row, written to an L2-resident buffer)",
+            "frac": achieved_ops / peak_ops, "traffic": SPLIT_LINE_TRAFFIC_80 if n == 400 else None,
+            "traffic_note": ("DRAM bytes per launch (80 models) from one ncu capture of this kernel build: its "
+                             "51 MB of x-filtered planes per launch stay in L2" if n == 400 else
+                             "no capture at this batch size"),
             "kernel": "split_line_kernel",
             "basis": "per model %.1f M FP32 + %.1f M ex2 lane ops: %d FP32 + %d ex2 per extended voxel (%d x %d x "
                      "%d), %d FP32 per PSF tap along x (%d taps, %d x %d outputs); its time per step from CUDA "
