@@ -266,6 +266,22 @@ GBK_API gbk_status gbk_jacobian(const gbk_geom *g, int32_t n_models, const doubl
                                 const gbk_obs *obs, uint32_t free_mask, const float *cot, double *jtj,
                                 double *jtv, double *chi2, float *jac, void *stream);
 
+/* The same analytic Jacobian reductions as gbk_jacobian (J^T J, J^T v and
+ * the sum of squared residuals; no J maps), computed in the split
+ * evaluator's shape: a line stage forms every extended spaxel's value and
+ * derivative moment triplets and filters them along x, a PSF stage filters
+ * them along y and applies the quotient rule of the moments and the
+ * reductions, the two meeting in a caller workspace sized to stay in L2.
+ * Served: the cube model at u = 1, PSF radius <= 8 px, free parameters
+ * among x0 .. sigma0 (I0 and h fixed); otherwise GBK_EUNSUPPORTED.
+ * Arguments as gbk_jacobian (without jac); workspace device memory of
+ * gbk_jacobian_workspace_bytes(g, n_models, free_mask) bytes (GBK_EWORKSPACE
+ * if smaller).  Asynchronous; the reductions are in a fixed order. */
+GBK_API size_t gbk_jacobian_workspace_bytes(const gbk_geom *g, int32_t n_models, uint32_t free_mask);
+GBK_API gbk_status gbk_jacobian_ws(const gbk_geom *g, int32_t n_models, const double *params,
+                                   const gbk_obs *obs, uint32_t free_mask, const float *cot, double *jtj,
+                                   double *jtv, double *chi2, void *workspace, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Levenberg-Marquardt fitting (Sec. 2.3.1).  The paper drives the C mpfit
  * library on the CPU with a forward-difference Jacobian of step ~0.1 in every
@@ -573,8 +589,9 @@ GBK_API gbk_status gbk_measure_alu_peak(double *ffma_lane_ops_per_s, double *ffm
  * when a TMA load of the staged convolution did not complete in time, bit 1
  * when a pipeline wait of the tensor-core GEMM did not (the affected blocks
  * stopped early and their output is incomplete), bit 2 when the wait of
- * gbk_wait_selfcheck ran out, bit 3 when a tile load of the split path's PSF
- * stage did not complete in time (that model's chi2 is not written).
+ * gbk_wait_selfcheck ran out, bit 3 when a tile load of the PSF stage of the
+ * split path or of the split Jacobian did not complete in time (that model's
+ * outputs are not written).
  * Synchronising. */
 GBK_API gbk_status gbk_device_status(int32_t *status);
 

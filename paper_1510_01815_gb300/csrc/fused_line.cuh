@@ -46,6 +46,21 @@ __device__ __forceinline__ void accum_shift(float4 q, float c, float w, float &s
     s2 = fmaf(D, u + t1, s2);
 }
 
+// Accumulates input (q0, q1, q2 about a; l1 = q1 + a q0, h1 = 2 q1
+// precomputed per input) into output sums with weight w: s0 and s1 about 0,
+// s2 about the output's centre c, exactly re-centred (D = a - c): six FP32
+// operations.  The caller moves s1 to c once at the end (s1 - c s0).
+__device__ __forceinline__ void accum_lin(float q0, float l1, float h1, float q2, float a, float c, float w,
+                                          float &s0, float &s1, float &s2)
+{
+    const float D = a - c;
+    s0 = fmaf(w, q0, s0);
+    s1 = fmaf(w, l1, s1);
+    const float i1 = fmaf(D, q0, h1);
+    const float i2 = fmaf(D, i1, q2);
+    s2 = fmaf(w, i2, s2);
+}
+
 // Unnormalised tap and the full normalisation sum (computed by each thread
 // that needs it, so no serial section or extra barrier is required).
 __device__ __forceinline__ float tap_raw(int j, float sigma, int R)

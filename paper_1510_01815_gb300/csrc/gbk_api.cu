@@ -10,6 +10,7 @@
 #include "gbk_api_internal.h"
 #include "k_fused.h"
 #include "k_split.h"
+#include "k_tsplit.h"
 #include "k_gemm.h"
 #include "k_staged.h"
 
@@ -180,12 +181,12 @@ const char *gbk_version(void) { return "gbk 0.1 (sm_103a)"; }
 gbk_status gbk_device_status(int32_t *status)
 {
     if (!status) return fail(GBK_EINVAL, "status is NULL");
-    int c = 0, c2 = 0, g = 0, w = 0, sp = 0;
+    int c = 0, c2 = 0, g = 0, w = 0, sp = 0, ts = 0;
     gbk_status s;
     if ((s = conv_status_read(&c)) || (s = conv_pair_status_read(&c2)) || (s = gemm_status_read(&g)) ||
-        (s = selfcheck_status_read(&w)) || (s = split_status_read(&sp)))
+        (s = selfcheck_status_read(&w)) || (s = split_status_read(&sp)) || (s = tsplit_status_read(&ts)))
         return s;
-    *status = ((c || c2) ? 1 : 0) | (g ? 2 : 0) | (w ? 4 : 0) | (sp ? 8 : 0);
+    *status = ((c || c2) ? 1 : 0) | (g ? 2 : 0) | (w ? 4 : 0) | ((sp || ts) ? 8 : 0);
     return ok();
 }
 

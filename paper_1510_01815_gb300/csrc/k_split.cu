@@ -81,19 +81,6 @@ struct SplitArgs {
     int tiles_x, tiles;
 };
 
-// Accumulates input (q0, q1, q2 about a) into output sums about c with
-// weight w: s0, s1 about 0, s2 about c (six FP32 operations).
-__device__ __forceinline__ void accum_lin(float q0, float l1, float h1, float q2, float a, float c, float w,
-                                          float &s0, float &s1, float &s2)
-{
-    const float D = a - c;
-    s0 = fmaf(w, q0, s0);
-    s1 = fmaf(w, l1, s1);
-    const float i1 = fmaf(D, q0, h1);
-    const float i2 = fmaf(D, i1, q2);
-    s2 = fmaf(w, i2, s2);
-}
-
 // ---------------------------------------------------------------------------
 // Set-up: per-model constants (one thread each) and, in block 0, the tables.
 __global__ void split_setup_kernel(const double *params, int n, Geom g, ModelConst *mcs, float *tab)
@@ -358,11 +345,7 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
 
 // ---------------------------------------------------------------------------
 // Host side.
-typedef CUresult (*SplitEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static SplitEncodeFn split_encode_fn()
+SplitEncodeFn split_encode_fn()
 {
     static SplitEncodeFn fn = nullptr;
     static std::once_flag once;

@@ -1,6 +1,8 @@
 // k_split.h -- launcher of the two-stage fused evaluator (k_split.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "gbk_internal.cuh"
 
 namespace gbk {
@@ -31,6 +33,12 @@ struct SplitTimer {
         n = 0;
     }
 };
+
+// The driver's cuTensorMapEncodeTiled (null when the driver lacks it).
+typedef CUresult (*SplitEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+SplitEncodeFn split_encode_fn();
 
 // Reads and clears the PSF stage's TMA wait status (1 = a load timed out).
 gbk_status split_status_read(int *v);

@@ -1,0 +1,692 @@
+// k_tsplit.cu -- the analytic Jacobian of the residual maps (forward-mode
+// derivatives through Sec. 2.1-2.2.6 of Bekiaris et al. 2015) in the split
+// evaluator's shape: no thread-block cluster, the derivative triplets handed
+// from a line stage to a PSF stage through an L2-resident buffer.
+//
+// What it computes is k_tangent.cu's (the header there states the
+// derivative algebra): for every extended spaxel the moment triplet of its
+// line and its derivatives with respect to x0, y0, PA, i, Vsys, Vmax, r_t and
+// sigma0 (I0 and h held fixed, as in every fit here), through the PSF passes
+// (linear: the derivative triplets go through the same passes as the
+// values), then the quotient rule of the moments gives each spaxel's two
+// Jacobian rows, and J^T J, J^T v (v = the residuals or a caller's
+// cotangent) and the sum of squared residuals are reduced per model in a
+// fixed order.
+//
+//  set-up   (tsplit_setup_kernel) per-model constants, the PSF taps and the
+//           per-channel LSF tap moments (G0, H1, H2), once per call.
+//  stage A  (tsplit_line_kernel<R>) one CTA per few extended rows of a model:
+//           each spaxel's value and eight derivative triplets (its channel
+//           loop runs over the warp's window of channels where the line is
+//           not negligible, |u| <= 6, or up to the FP32 flush for lines
+//           centred outside the band), as 28 shared planes; then the PSF pass
+//           along x, four outputs per thread, one triplet at a time, written
+//           as 28 coalesced planes [model][28][ey][nxp].
+//  stage B  (tsplit_psf_kernel<R>) one CTA per 32 x 16 tile of data spaxels
+//           of a model: the tile's rows of all 28 planes in one TMA load
+//           (bounded mbarrier wait, status bit 3), the PSF pass along y for
+//           two outputs per thread, the moments, residuals and Jacobian rows,
+//           J^T J, J^T v and sum r^2 per thread, the CTA's sums in FP64 in a
+//           fixed order; the last tile of a model adds the tiles in order.
+//
+// The PSF passes accumulate as the split evaluator's (six FP32 operations
+// per tap and triplet).  Models go in chunks whose planes stay in L2.
+#include <algorithm>
+#include <mutex>
+
+#include "fused_line.cuh"
+#include "gbk_api_internal.h"
+#include "k_split.h"
+#include "k_tsplit.h"
+#include "tma_util.cuh"
+
+namespace gbk {
+
+constexpr int kTsThreads = 256;
+constexpr int kTsNP = GBK_I0;                  // derivatives carried: x0 .. sigma0
+constexpr int kTsNT = kTsNP + 1;               // triplets: the values and the derivatives
+constexpr int kTsPlanes = 3 * kTsNT + 1;       // and the centres
+constexpr int kTsTX = 32, kTsTY = 16;          // data spaxels per stage-B tile
+constexpr int kTsEnt = kTsNP * (kTsNP + 1) / 2 + kTsNP + 1;  // J^T J upper triangle, J^T v, sum r^2
+constexpr size_t kTsL2Budget = (size_t)48 << 20;
+constexpr size_t kTsSmemA = (size_t)100 * 1024;  // shared-memory target of a stage-A CTA
+constexpr long kTsWaitLimit = 1L << 18;        // tries: about one second
+
+__device__ int g_tsplit_status;  // 0 = fine; 1 = a tile's TMA load did not complete in time
+
+// Table layout in the workspace: PSF taps at [4, 4 + 2R + 1), then the three
+// per-channel LSF moment arrays of ezp floats each.
+constexpr int kTsTabTaps = 4;
+constexpr int kTsTabZ = kTsTabTaps + 2 * kTsplitMaxR + 4;
+
+__host__ __device__ inline int ts_rowpitch(int ex) { return ((ex + 3) & ~3) + 4; }
+__host__ __device__ inline int ts_ezp(const Geom &g) { return (g.ez + 1) & ~1; }
+
+struct TsArgs {
+    Geom g;
+    int n_models;             // models of this chunk
+    const double *params;     // [n_models][GBK_NPAR]
+    const ModelConst *mcs;    // [n_models]
+    const float *tab;         // taps and LSF channel moments
+    float *pl;                // [n_models][28][ey][nxp]
+    gbk_obs obs;              // every model's galaxy when obs_list is null
+    const gbk_obs *obs_list;  // or one per model
+    const int32_t *skip;      // per model: non-zero = leave alone (or null)
+    const float *cot;         // [n_models][2][ny][nx] cotangent (null: the residuals)
+    int np, free_idx[GBK_NPAR];
+    double *jtj, *jtv, *chi2; // outputs [n_models][np][np], [n_models][np], [n_models] (each may be null)
+    double *part;             // [n_models][tiles][kTsEnt]
+    unsigned *arrived;        // [n_models]
+    int nxp, ezp, ra, tiles_x, tiles;
+};
+
+// ---------------------------------------------------------------------------
+__global__ void tsplit_setup_kernel(const double *params, int n, Geom g, ModelConst *mcs, float *tab)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) mcs[i] = model_const(params + (size_t)i * GBK_NPAR, g);
+    if (blockIdx.x != 0) return;
+    const int tid = threadIdx.x, ezp = ts_ezp(g);
+    if (tid <= 2 * g.R) tab[kTsTabTaps + tid] = tap_raw(tid - g.R, g.sig_xy, g.R) / tap_sum(g.sig_xy, g.R);
+    float *tzx = tab + kTsTabZ, *tzy = tzx + ezp, *tzz = tzy + ezp;
+    const float S = tap_sum(g.sig_z, g.Rz);
+    for (int e = tid; e < ezp; e += blockDim.x) {
+        float G0 = 0.f, H1 = 0.f, H2 = 0.f;
+        if (e < g.ez) {
+            const int kd = e - g.Rz;  // data channel of extended channel e
+            const int jlo = max(0, kd - g.Rz) - kd, jhi = min(g.nz - 1, kd + g.Rz) - kd;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float w = tap_raw(j, g.sig_z, g.Rz) / S;
+                G0 += w;
+                H1 = fmaf(w, (float)j, H1);
+                H2 = fmaf(w, (float)(j * j), H2);
+            }
+        }
+        tzx[e] = G0;
+        tzy[e] = g.dv * H1;
+        tzz[e] = g.dv * g.dv * H2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The value triplet and the eight derivative triplets of one extended
+// spaxel at (x, y) (k_tangent.cu's phase 1, its channel loop limited to the
+// warp's window): rec[3 t + m] = component m of triplet t (t = 0: values,
+// t = k + 1: d/dp_k), about the centre a (returned).  Whole warps (inactive
+// lanes allowed).
+__device__ __forceinline__ float tangent_spaxel(const Geom &g, const ModelConst &c, const double *pm, const float *tzx,
+                                                const float *tzy, const float *tzz, int ezp, float x, float y,
+                                                float rec[3 * kTsNT])
+{
+    const float kdeg = 0.017453292519943295f;  // radians per degree
+    const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;
+    const float v_lo = g.vc - 0.5f * (float)(g.nz - 1) * g.dv, v_hi = g.vc + 0.5f * (float)(g.nz - 1) * g.dv;
+    const float sig = c.sigma, isig2 = 1.f / (sig * sig), isig3 = isig2 / sig;
+    const float s0p = (float)pm[GBK_SIG0];
+    const float dsig_ds0 = (g.lsf_mode == 1) ? s0p / sig : 1.f;
+    const float vmax = (float)pm[GBK_VMAX], rtv = (float)pm[GBK_RT];
+    const float ci = 1.f / c.inv_cos_i;
+    // geometry and its derivatives (Eqs. 1-8)
+    const float dx = x - c.x0, dy = y - c.y0;
+    const float xe = -dx * c.sin_pa + dy * c.cos_pa;
+    const float ye = -dx * c.cos_pa - dy * c.sin_pa;
+    const float yd = ye * c.inv_cos_i;
+    const float r = sqrtf(xe * xe + yd * yd);
+    const float u = r * c.inv_rt;
+    const float at = atanf(u);
+    const float fv = (r > 0.f) ? 0.63661977f * at / r : 0.63661977f * c.inv_rt;  // f / Vmax
+    const float f = vmax * fv;
+    const float w = xe * c.sin_i;
+    const float vl = c.vsys + f * w;
+    const float br = c.i0 * expf(-r * c.inv_h);
+    float fp;  // df/dr
+    if (u < 0.1f) fp = vmax * 0.63661977f * c.inv_rt * c.inv_rt * u * (-2.f / 3.f + 0.8f * u * u);
+    else fp = vmax * 0.63661977f * (u / (1.f + u * u) - at) / (r * r);
+    float rx = 0.f, ry = 0.f, ri = 0.f;
+    if (r > 0.f) {
+        rx = xe / r;
+        ry = ye * c.inv_cos_i * c.inv_cos_i / r;
+        ri = yd * yd * (c.sin_i * c.inv_cos_i) / r * kdeg;
+    }
+    const float dxe[3] = {c.sin_pa, -c.cos_pa, ye * kdeg};  // d x_e / d(x0, y0, PA)
+    const float dye[3] = {c.cos_pa, c.sin_pa, -xe * kdeg};  // d y_e / d(x0, y0, PA)
+    float dv[kTsNP], dlnA[kTsNP];
+#pragma unroll
+    for (int k = 0; k < kTsNP; ++k) { dv[k] = 0.f; dlnA[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float drk = rx * dxe[k] + ry * dye[k];
+        dv[k] = f * c.sin_i * dxe[k] + fp * drk * w;
+        dlnA[k] = -drk * c.inv_h;
+    }
+    dv[GBK_INCL] = kdeg * f * xe * ci + fp * ri * w;
+    dlnA[GBK_INCL] = -ri * c.inv_h;
+    dv[GBK_VSYS] = 1.f;
+    dv[GBK_VMAX] = fv * w;
+    dv[GBK_RT] = -0.63661977f * vmax / (rtv * rtv + r * r) * w;
+    dlnA[GBK_SIG0] = -dsig_ds0 / sig;
+    const float a_c = fminf(fmaxf(vl, v_lo), v_hi);
+    const float sh = vl - a_c;
+    const float base = vz0 - vl;  // d = v_e - v_los at e = 0
+
+    // the warp's channel window (the union of its lanes' |u| <= cut), whole
+    // channel pairs
+    const unsigned am = __activemask();
+    const float cut = (sh != 0.f) ? kUFlush : kUCut;
+    const float inv_adv = 1.f / (c.alpha * g.dv);
+    float flo = (-cut - c.alpha * base) * inv_adv - 1.f, fhi = (cut - c.alpha * base) * inv_adv + 2.f;
+    if (!(flo > -1e6f)) flo = -1e6f;
+    if (!(fhi < 1e6f)) fhi = 1e6f;
+    int e0 = __reduce_min_sync(am, (int)floorf(flo)), e1 = __reduce_max_sync(am, (int)ceilf(fhi));
+    e0 = max(0, e0) & ~1;
+    e1 = min(ezp, (e1 + 1) & ~1);
+
+    // channel sums: SG_k = sum g d^k G0 (k <= 4), S1_k = sum g d^k H1 (k <= 3), S2_k = sum g d^k H2 (k <= 2)
+    float SG[5], S1[4], S2[3];
+    {
+        const f32x2 Z2 = pk2(0.f, 0.f), AL = pk2(c.alpha, c.alpha), DV2 = pk2(2.f * g.dv, 2.f * g.dv);
+        f32x2 A0 = Z2, A1 = Z2, A2 = Z2, A3 = Z2, A4 = Z2, B0 = Z2, B1 = Z2, B2 = Z2, B3 = Z2, C0 = Z2, C1 = Z2,
+              C2 = Z2;
+        f32x2 D = pk2(fmaf((float)e0, g.dv, base), fmaf((float)(e0 + 1), g.dv, base));
+#pragma unroll 2
+        for (int e = e0; e < e1; e += 2) {
+            const f32x2 T = mul2(D, AL);
+            const f32x2 W = mul2(T, T);
+            float w0, w1;
+            upk2(W, w0, w1);
+            const f32x2 G0 = pk2(ex2_approx(-w0), ex2_approx(-w1));
+            const f32x2 D2 = mul2(D, D);
+            const f32x2 G1 = mul2(G0, D), G2 = mul2(G0, D2);
+            const f32x2 G3 = mul2(G1, D2), G4 = mul2(G2, D2);
+            const f32x2 TX = *reinterpret_cast<const f32x2 *>(tzx + e);
+            const f32x2 TY = *reinterpret_cast<const f32x2 *>(tzy + e);
+            const f32x2 TZ = *reinterpret_cast<const f32x2 *>(tzz + e);
+            A0 = fma2(G0, TX, A0); A1 = fma2(G1, TX, A1); A2 = fma2(G2, TX, A2);
+            A3 = fma2(G3, TX, A3); A4 = fma2(G4, TX, A4);
+            B0 = fma2(G0, TY, B0); B1 = fma2(G1, TY, B1); B2 = fma2(G2, TY, B2); B3 = fma2(G3, TY, B3);
+            C0 = fma2(G0, TZ, C0); C1 = fma2(G1, TZ, C1); C2 = fma2(G2, TZ, C2);
+            D = add2(D, DV2);
+        }
+        SG[0] = hsum2(A0); SG[1] = hsum2(A1); SG[2] = hsum2(A2); SG[3] = hsum2(A3); SG[4] = hsum2(A4);
+        S1[0] = hsum2(B0); S1[1] = hsum2(B1); S1[2] = hsum2(B2); S1[3] = hsum2(B3);
+        S2[0] = hsum2(C0); S2[1] = hsum2(C1); S2[2] = hsum2(C2);
+    }
+    // B_km (k: power of d from the derivative; m: moment weight about a)
+    float B[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        B[k][0] = SG[k];
+        B[k][1] = SG[k + 1] + sh * SG[k] + S1[k];
+        B[k][2] = SG[k + 2] + 2.f * sh * SG[k + 1] + 2.f * S1[k + 1] + sh * sh * SG[k] + 2.f * sh * S1[k] + S2[k];
+    }
+    const float A = c.amp * br;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) rec[m] = A * B[0][m];
+#pragma unroll
+    for (int k = 0; k < kTsNP; ++k) {
+        const float ds = (k == GBK_SIG0) ? dsig_ds0 : 0.f;
+        const float cA = dlnA[k], cv = dv[k] * isig2, cs3 = ds * isig3;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) rec[3 * (k + 1) + m] = A * (cA * B[0][m] + cv * B[1][m] + cs3 * B[2][m]);
+    }
+    return a_c;
+}
+
+// ---------------------------------------------------------------------------
+// Stage A: triplets of a.ra extended rows, then their x pass.
+template <int R>
+__global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
+{
+    constexpr int W = 2 * R + 1;
+    constexpr int NIN = 4 + 2 * R;      // inputs of four consecutive outputs
+    constexpr int NC4 = (NIN + 3) / 4;  // ... as float4 groups
+    extern __shared__ __align__(16) float sm[];
+    __shared__ ModelConst mc;
+    const Geom &g = a.g;
+    const int tid = threadIdx.x, model = blockIdx.y;
+    if (a.skip && a.skip[model] != 0) return;  // the whole CTA
+    const int row0 = blockIdx.x * a.ra, nrows = min(a.ra, g.ey - row0);
+    const int PA = ts_rowpitch(g.ex);
+    const int NPL = a.ra * PA;
+    float *const tz = sm + kTsPlanes * NPL;  // tzx, tzy, tzz
+    if (tid < (int)(sizeof(ModelConst) / 4))
+        reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
+    for (int i = tid; i < 3 * a.ezp; i += kTsThreads) tz[i] = a.tab[kTsTabZ + i];
+    float w[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) w[j] = a.tab[kTsTabTaps + j];
+    __syncthreads();
+
+    // phase 1: triplets of every extended spaxel of the rows
+    const double *pm = a.params + (size_t)model * GBK_NPAR;
+    {
+        const int nsp = nrows * g.ex;
+        int r = tid / g.ex, xe = tid - r * g.ex;
+        const int dr = kTsThreads / g.ex, dx = kTsThreads - dr * g.ex;
+        for (int idx = tid; idx < nsp; idx += kTsThreads) {
+            float rec[3 * kTsNT];
+            const float ac = tangent_spaxel(g, mc, pm, tz, tz + a.ezp, tz + 2 * a.ezp, a.ezp, (float)(xe - R),
+                                            (float)(row0 + r - R), rec);
+            const int o = r * PA + xe;
+#pragma unroll
+            for (int p = 0; p < 3 * kTsNT; ++p) sm[p * NPL + o] = rec[p];
+            sm[3 * kTsNT * NPL + o] = ac;
+            xe += dx; r += dr;
+            if (xe >= g.ex) { xe -= g.ex; ++r; }
+        }
+    }
+    __syncthreads();
+
+    // phase 2: x pass; task (row, outputs 4 gx .. 4 gx + 3), one triplet at a time
+    const int ngx = (g.nx + 3) / 4;
+    const size_t pstride = (size_t)g.ey * a.nxp;  // floats per plane
+    float *const P0 = a.pl + (size_t)model * kTsPlanes * pstride + (size_t)row0 * a.nxp;
+    const float *const QA = sm + 3 * kTsNT * NPL;
+    for (int t = tid; t < nrows * ngx; t += kTsThreads) {
+        const int rr = t / ngx, gx = 4 * (t - rr * ngx);
+        const int ro = rr * PA + gx;
+        float av[4 * NC4], cen[4];
+#pragma unroll
+        for (int c4 = 0; c4 < NC4; ++c4) {
+            const float4 v = *reinterpret_cast<const float4 *>(QA + ro + 4 * c4);
+            av[4 * c4] = v.x; av[4 * c4 + 1] = v.y; av[4 * c4 + 2] = v.z; av[4 * c4 + 3] = v.w;
+        }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) cen[o] = av[o + R];
+        float *const out = P0 + (size_t)rr * a.nxp + gx;
+#pragma unroll 1
+        for (int tr = 0; tr < kTsNT; ++tr) {
+            const float *Q0 = sm + (3 * tr) * NPL, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
+            float s[4][3];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s[o][0] = s[o][1] = s[o][2] = 0.f;
+#pragma unroll
+            for (int c4 = 0; c4 < NC4; ++c4) {
+                const float4 v0 = *reinterpret_cast<const float4 *>(Q0 + ro + 4 * c4);
+                const float4 v1 = *reinterpret_cast<const float4 *>(Q1 + ro + 4 * c4);
+                const float4 v2 = *reinterpret_cast<const float4 *>(Q2 + ro + 4 * c4);
+                const float q0[4] = {v0.x, v0.y, v0.z, v0.w}, q1[4] = {v1.x, v1.y, v1.z, v1.w};
+                const float q2[4] = {v2.x, v2.y, v2.z, v2.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = 4 * c4 + k;
+                    if (e >= NIN) break;
+                    const float ae = av[e];
+                    const float l1 = fmaf(ae, q0[k], q1[k]), h1 = q1[k] + q1[k];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        const int j = e - o;
+                        if (j >= 0 && j < W) accum_lin(q0[k], l1, h1, q2[k], ae, cen[o], w[j], s[o][0], s[o][1], s[o][2]);
+                    }
+                }
+            }
+            float *p = out + (size_t)(3 * tr) * pstride;
+            *reinterpret_cast<float4 *>(p) = make_float4(s[0][0], s[1][0], s[2][0], s[3][0]);
+            *reinterpret_cast<float4 *>(p + pstride) =
+                make_float4(fmaf(-cen[0], s[0][0], s[0][1]), fmaf(-cen[1], s[1][0], s[1][1]),
+                            fmaf(-cen[2], s[2][0], s[2][1]), fmaf(-cen[3], s[3][0], s[3][1]));
+            *reinterpret_cast<float4 *>(p + 2 * pstride) = make_float4(s[0][2], s[1][2], s[2][2], s[3][2]);
+        }
+        *reinterpret_cast<float4 *>(out + (size_t)(3 * kTsNT) * pstride) = make_float4(cen[0], cen[1], cen[2], cen[3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage B: y pass, moments, Jacobian rows and the per-model reductions.
+template <int R>
+__global__ void __launch_bounds__(kTsThreads, 2)
+    tsplit_psf_kernel(const __grid_constant__ CUtensorMap tmap, TsArgs a)
+{
+    constexpr int W = 2 * R + 1;
+    constexpr int NR = kTsTY + 2 * R;   // rows of the tile's planes
+    constexpr int NPL = NR * kTsTX;     // floats per plane
+    constexpr int NIN = 2 + 2 * R;      // inputs of two consecutive outputs
+    extern __shared__ __align__(128) unsigned char sraw[];
+    float *const sp = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sraw) + 127) & ~(uintptr_t)127);
+    __shared__ ModelConst mc;
+    __shared__ gbk_obs s_ob;
+    __shared__ double red[kTsThreads / 32][kTsEnt];
+    __shared__ double s_part[kTsEnt];
+    __shared__ bool s_last;
+    __shared__ __align__(8) uint64_t bar;
+
+    const Geom &g = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int model = blockIdx.y, tile = blockIdx.x;
+    if (a.skip && a.skip[model] != 0) return;  // the whole CTA
+    const int tx0 = (tile % a.tiles_x) * kTsTX, ty0 = (tile / a.tiles_x) * kTsTY;
+    const int nxo = min(kTsTX, g.nx - tx0), nyo = min(kTsTY, g.ny - ty0);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // the tile's rows of all 28 planes in one box (beyond the buffer: zeros)
+        tma_expect(&bar, (uint32_t)(kTsPlanes * NPL * sizeof(float)));
+        tma_load_3d(&tmap, sp, &bar, tx0, ty0, kTsPlanes * model);
+    }
+    if (tid < (int)(sizeof(ModelConst) / 4))
+        reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
+    if (tid == 32) s_ob = a.obs_list ? a.obs_list[model] : a.obs;
+    float w[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) w[j] = a.tab[kTsTabTaps + j];
+    const bool loaded = mbar_wait(&bar, 0, kTsWaitLimit);
+    if (__syncthreads_or(!loaded)) {  // the same decision in every thread
+        if (tid == 0) {
+            atomicExch(&g_tsplit_status, 1);
+            mbar_wait(&bar, 0, kTsWaitLimit);  // a bounded chance for the copy in flight to land
+        }
+        return;
+    }
+
+    const ModelConst &c = mc;
+    const size_t np = (size_t)g.nx * g.ny;
+    const float thr = kInvalidFraction * c.i0;
+    float E[kTsEnt];
+#pragma unroll
+    for (int e = 0; e < kTsEnt; ++e) E[e] = 0.f;
+    // task: column x, outputs gy, gy + 1
+    const int x = tid % kTsTX, gy = 2 * (tid / kTsTX);
+    if (x < nxo && gy < nyo) {
+        const float *const SA = sp + 3 * kTsNT * NPL;
+        float av[NIN], cen[2];
+#pragma unroll
+        for (int e = 0; e < NIN; ++e) av[e] = SA[(gy + e) * kTsTX + x];
+        cen[0] = av[R];
+        cen[1] = av[R + 1];
+        // y pass of triplet tr for both outputs
+        auto ypass = [&](int tr, float s[2][3]) {
+            const float *Q0 = sp + (3 * tr) * NPL, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) s[o][0] = s[o][1] = s[o][2] = 0.f;
+#pragma unroll
+            for (int e = 0; e < NIN; ++e) {
+                const int oi = (gy + e) * kTsTX + x;
+                const float q0 = Q0[oi], q1 = Q1[oi], q2 = Q2[oi], ae = av[e];
+                const float l1 = fmaf(ae, q0, q1), h1 = q1 + q1;
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const int j = e - o;
+                    if (j >= 0 && j < W) accum_lin(q0, l1, h1, q2, ae, cen[o], w[j], s[o][0], s[o][1], s[o][2]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; ++o) s[o][1] = fmaf(-cen[o], s[o][0], s[o][1]);
+        };
+        float v[2][3];
+        ypass(0, v);
+        bool use[2];
+        float inv[2], mu[2], inv2m2[2], s2i[2], wv[2], ws[2], cv[2], cs[2];
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            use[o] = false;
+            inv[o] = mu[o] = inv2m2[o] = s2i[o] = wv[o] = ws[o] = cv[o] = cs[o] = 0.f;
+            if (gy + o >= nyo) continue;
+            const size_t pix = (size_t)(ty0 + gy + o) * g.nx + (tx0 + x);
+            use[o] = c.valid && v[o][0] > thr && s_ob.mask[pix] != 0;
+            if (!use[o]) continue;
+            inv[o] = 1.f / v[o][0];
+            mu[o] = v[o][1] * inv[o];
+            s2i[o] = v[o][2] * inv[o];
+            const float m2 = sqrtf(fmaxf(fmaf(-mu[o], mu[o], s2i[o]), 0.f));
+            wv[o] = s_ob.w_v[pix];
+            ws[o] = s_ob.w_s[pix];
+            const float rv = wv[o] * (cen[o] + mu[o] - s_ob.v_obs[pix]);
+            const float rs = ws[o] * (m2 - s_ob.s_obs[pix]);
+            inv2m2[o] = m2 > 0.f ? 0.5f / m2 : 0.f;
+            if (a.cot) {
+                cv[o] = a.cot[(size_t)model * 2 * np + pix];
+                cs[o] = a.cot[(size_t)model * 2 * np + np + pix];
+            } else {
+                cv[o] = rv;
+                cs[o] = rs;
+            }
+            E[kTsEnt - 1] = fmaf(rv, rv, fmaf(rs, rs, E[kTsEnt - 1]));
+        }
+        // the Jacobian rows (quotient rule of the moments), one parameter at a time
+        float jv[2][kTsNP], js[2][kTsNP];
+#pragma unroll
+        for (int k = 0; k < kTsNP; ++k) {
+            float d[2][3];
+            ypass(k + 1, d);
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const float dmu = (d[o][1] - mu[o] * d[o][0]) * inv[o];
+                const float dvar = (d[o][2] - s2i[o] * d[o][0]) * inv[o] - 2.f * mu[o] * dmu;
+                jv[o][k] = use[o] ? wv[o] * dmu : 0.f;
+                js[o][k] = use[o] ? ws[o] * dvar * inv2m2[o] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            int e = 0;
+#pragma unroll
+            for (int j = 0; j < kTsNP; ++j)
+#pragma unroll
+                for (int k = j; k < kTsNP; ++k, ++e) E[e] = fmaf(jv[o][j], jv[o][k], fmaf(js[o][j], js[o][k], E[e]));
+#pragma unroll
+            for (int j = 0; j < kTsNP; ++j, ++e) E[e] = fmaf(jv[o][j], cv[o], fmaf(js[o][j], cs[o], E[e]));
+        }
+    }
+    // the CTA's sums: warps in FP64 by shuffles, then the warps in order
+#pragma unroll
+    for (int e = 0; e < kTsEnt; ++e) {
+        double vv = (double)E[e];
+        for (int off = 16; off > 0; off >>= 1) vv += __shfl_down_sync(0xffffffffu, vv, off);
+        if (lane == 0) red[warp][e] = vv;
+    }
+    __syncthreads();
+    if (tid < kTsEnt) {
+        double sum = 0.0;
+        for (int q = 0; q < kTsThreads / 32; ++q) sum += red[q][tid];
+        a.part[((size_t)model * a.tiles + tile) * kTsEnt + tid] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.arrived[model], 1u);
+        s_last = (prev == (unsigned)a.tiles - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid < kTsEnt) {
+        const volatile double *p = a.part + (size_t)model * a.tiles * kTsEnt + tid;
+        double sum = 0.0;
+        for (int k = 0; k < a.tiles; ++k) sum += p[(size_t)k * kTsEnt];
+        s_part[tid] = sum;
+    }
+    __syncthreads();
+    // entry t of the free-parameter output: (j, k) of the upper triangle of
+    // J^T J, then J^T v, then sum r^2, gathered from the carried entries
+    const int nf = a.np;
+    const int ntri = nf * (nf + 1) / 2, nent = ntri + nf + 1;
+    if (tid < nent) {
+        int src, j = 0, k = 0;
+        if (tid < ntri) {
+            int t = tid;
+            while (t >= nf - j) { t -= nf - j; ++j; }
+            k = j + t;
+            int p = a.free_idx[j], q = a.free_idx[k];
+            if (p > q) { const int x2 = p; p = q; q = x2; }
+            src = p * kTsNP - p * (p - 1) / 2 + (q - p);
+        } else if (tid < ntri + nf) {
+            src = kTsNP * (kTsNP + 1) / 2 + a.free_idx[tid - ntri];
+        } else {
+            src = kTsEnt - 1;
+        }
+        double sv = s_part[src];
+        if (!c.valid) sv = (double)__int_as_float(0x7fc00000);
+        if (tid < ntri) {
+            if (a.jtj) {
+                a.jtj[(size_t)model * nf * nf + j * nf + k] = sv;
+                a.jtj[(size_t)model * nf * nf + k * nf + j] = sv;
+            }
+        } else if (tid < ntri + nf) {
+            if (a.jtv) a.jtv[(size_t)model * nf + (tid - ntri)] = sv;
+        } else if (a.chi2) {
+            a.chi2[model] = sv;
+        }
+    }
+    if (tid == 0) a.arrived[model] = 0u;  // ready for the next chunk or call
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+struct TsLayout {
+    int chunk, nxp, ezp, ra, tiles_x, tiles;
+    size_t mc_off, tab_off, pl_off, part_off, arr_off, total;
+};
+
+static size_t ts_al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t ts_smem_a(const Geom &g, int ra)
+{
+    return (size_t)(kTsPlanes * ra * ts_rowpitch(g.ex) + 3 * ts_ezp(g)) * sizeof(float);
+}
+static size_t ts_smem_b(int R) { return 128 + (size_t)kTsPlanes * (kTsTY + 2 * R) * kTsTX * sizeof(float); }
+
+static TsLayout ts_layout(const Geom &g, int n_models)
+{
+    TsLayout L = {};
+    L.nxp = (g.nx + 3) & ~3;
+    L.ezp = ts_ezp(g);
+    L.ra = 8;
+    while (L.ra > 1 && ts_smem_a(g, L.ra) > kTsSmemA) --L.ra;
+    const size_t plb = (size_t)kTsPlanes * g.ey * L.nxp * sizeof(float);
+    size_t chunk = kTsL2Budget / plb;
+    if (chunk < 1) chunk = 1;
+    if (chunk > (size_t)n_models) chunk = (size_t)n_models;
+    L.chunk = (int)chunk;
+    L.tiles_x = (g.nx + kTsTX - 1) / kTsTX;
+    L.tiles = L.tiles_x * ((g.ny + kTsTY - 1) / kTsTY);
+    L.mc_off = 0;
+    L.tab_off = ts_al256((size_t)n_models * sizeof(ModelConst));
+    L.pl_off = L.tab_off + ts_al256((size_t)(kTsTabZ + 3 * L.ezp) * sizeof(float));
+    L.part_off = L.pl_off + ts_al256(chunk * plb);
+    L.arr_off = L.part_off + ts_al256(chunk * L.tiles * kTsEnt * sizeof(double));
+    L.total = L.arr_off + ts_al256(chunk * sizeof(unsigned));
+    return L;
+}
+
+bool tsplit_supported(const Geom &g, int np, const int *free_idx)
+{
+    if (g.model != GBK_MODEL_CUBE || g.u != 1 || g.R > kTsplitMaxR || g.ex > 1024) return false;
+    if (np < 1 || np > kTsNP) return false;
+    for (int k = 0; k < np; ++k)
+        if (free_idx[k] < 0 || free_idx[k] >= kTsNP) return false;
+    return ts_smem_a(g, 1) <= 200 * 1024 && ts_smem_b(g.R) <= 200 * 1024;
+}
+
+size_t tsplit_workspace_bytes(const Geom &g, int n_models)
+{
+    if (g.model != GBK_MODEL_CUBE || g.u != 1 || g.R > kTsplitMaxR || n_models < 1) return 0;
+    return ts_layout(g, n_models).total;
+}
+
+gbk_status tsplit_status_read(int *v)
+{
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_tsplit_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tsplit_status, &zero, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "reading the split Jacobian's status");
+    return GBK_OK;
+}
+
+template <int R>
+static gbk_status ts_launch_stages(const CUtensorMap &tm, const TsArgs &a, cudaStream_t st)
+{
+    static KernelAttrMemo memo_a, memo_b;
+    const size_t sa = ts_smem_a(a.g, a.ra), sb = ts_smem_b(R);
+    gbk_status s;
+    if ((s = ensure_kernel_attrs((const void *)tsplit_line_kernel<R>, sa, false, memo_a,
+                                 "split Jacobian: setting the line stage's shared memory")) ||
+        (s = ensure_kernel_attrs((const void *)tsplit_psf_kernel<R>, sb, false, memo_b,
+                                 "split Jacobian: setting the PSF stage's shared memory")))
+        return s;
+    const unsigned blocks_a = (unsigned)((a.g.ey + a.ra - 1) / a.ra);
+    tsplit_line_kernel<R><<<dim3(blocks_a, (unsigned)a.n_models), kTsThreads, sa, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "split Jacobian: line stage launch");
+    tsplit_psf_kernel<R><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kTsThreads, sb, st>>>(tm, a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: PSF stage launch");
+    return GBK_OK;
+}
+
+gbk_status launch_tsplit(const TsplitCall &call, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    const Geom &g = call.g;
+    const int n = call.n_models;
+    if (!tsplit_supported(g, call.np, call.free_idx))
+        return fail(GBK_EUNSUPPORTED, "the split Jacobian serves the cube model at u = 1, PSF radius <= %d, with "
+                    "free parameters among x0 .. sigma0", kTsplitMaxR);
+    if (n == 0) return GBK_OK;
+    const TsLayout L = ts_layout(g, n);
+    if (!ws || ws_bytes < L.total)
+        return fail(GBK_EWORKSPACE, "the split Jacobian needs %zu bytes of workspace (got %zu)", L.total, ws_bytes);
+    if (!split_encode_fn()) return fail(GBK_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    char *base = (char *)ws;
+    ModelConst *mcs = (ModelConst *)(base + L.mc_off);
+    float *tab = (float *)(base + L.tab_off);
+    cudaError_t e = cudaMemsetAsync(base + L.arr_off, 0, (size_t)L.chunk * sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(e, "split Jacobian: clearing the arrival counters");
+    // the chunk's planes as a 3-D tensor [28 * chunk][ey][nxp] for the tile loads
+    CUtensorMap tm;
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)L.nxp, (cuuint64_t)g.ey, (cuuint64_t)kTsPlanes * L.chunk};
+        const cuuint64_t strides[2] = {(cuuint64_t)L.nxp * sizeof(float), (cuuint64_t)L.nxp * g.ey * sizeof(float)};
+        const cuuint32_t box[3] = {(cuuint32_t)kTsTX, (cuuint32_t)(kTsTY + 2 * g.R), (cuuint32_t)kTsPlanes};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = split_encode_fn()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base + L.pl_off, dims, strides, box,
+                                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(GBK_ECUDA, "split Jacobian: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    tsplit_setup_kernel<<<(n + 127) / 128, 128, 0, st>>>(call.params, n, g, mcs, tab);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: set-up launch");
+    const size_t npix = (size_t)g.nx * g.ny;
+    for (int m0 = 0; m0 < n; m0 += L.chunk) {
+        TsArgs a = {};
+        a.g = g;
+        a.n_models = std::min(L.chunk, n - m0);
+        a.params = call.params + (size_t)m0 * GBK_NPAR;
+        a.mcs = mcs + m0;
+        a.tab = tab;
+        a.pl = (float *)(base + L.pl_off);
+        a.obs = call.obs;
+        a.obs_list = call.obs_list ? call.obs_list + m0 : nullptr;
+        a.skip = call.skip ? call.skip + m0 : nullptr;
+        a.cot = call.cot ? call.cot + 2 * npix * m0 : nullptr;
+        a.np = call.np;
+        for (int k = 0; k < call.np; ++k) a.free_idx[k] = call.free_idx[k];
+        a.jtj = call.jtj ? call.jtj + (size_t)m0 * call.np * call.np : nullptr;
+        a.jtv = call.jtv ? call.jtv + (size_t)m0 * call.np : nullptr;
+        a.chi2 = call.chi2 ? call.chi2 + m0 : nullptr;
+        a.part = (double *)(base + L.part_off);
+        a.arrived = (unsigned *)(base + L.arr_off);
+        a.nxp = L.nxp;
+        a.ezp = L.ezp;
+        a.ra = L.ra;
+        a.tiles_x = L.tiles_x;
+        a.tiles = L.tiles;
+        gbk_status s;
+        switch (g.R) {
+        case 0: s = ts_launch_stages<0>(tm, a, st); break;
+        case 1: s = ts_launch_stages<1>(tm, a, st); break;
+        case 2: s = ts_launch_stages<2>(tm, a, st); break;
+        case 3: s = ts_launch_stages<3>(tm, a, st); break;
+        case 4: s = ts_launch_stages<4>(tm, a, st); break;
+        case 5: s = ts_launch_stages<5>(tm, a, st); break;
+        case 6: s = ts_launch_stages<6>(tm, a, st); break;
+        case 7: s = ts_launch_stages<7>(tm, a, st); break;
+        case 8: s = ts_launch_stages<8>(tm, a, st); break;
+        default: return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", g.R, kTsplitMaxR);
+        }
+        if (s) return s;
+    }
+    return GBK_OK;
+}
+
+}  // namespace gbk

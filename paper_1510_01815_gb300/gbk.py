@@ -97,6 +97,8 @@ def lib():
             "gbk_fit_lm_fallback": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp,
                                           vp, sz, vp]),
             "gbk_jacobian": (i32, [gp, i32, vp, op, u32, vp, vp, vp, vp, vp, vp]),
+            "gbk_jacobian_workspace_bytes": (sz, [gp, i32, u32]),
+            "gbk_jacobian_ws": (i32, [gp, i32, vp, op, u32, vp, vp, vp, vp, vp, sz, vp]),
             "gbk_grid_workspace_bytes": (sz, [gp, ctypes.POINTER(ctypes.c_int32), i32]),
             "gbk_grid": (i32, [gp, op, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), i32, i32,
@@ -150,7 +152,8 @@ def exported_symbols():
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_fit_lm_fallback_workspace_bytes", "gbk_fit_lm_fallback",
             "gbk_wait_selfcheck",
-            "gbk_jacobian", "gbk_grid_workspace_bytes", "gbk_grid",
+            "gbk_jacobian", "gbk_jacobian_workspace_bytes", "gbk_jacobian_ws", "gbk_grid_workspace_bytes",
+            "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_nested_sample_traced",
             "gbk_survey_workspace_bytes",
             "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_initial_guess", "gbk_survey_autotune", "gbk_survey_get_tuning",
@@ -678,6 +681,45 @@ def gbk_jacobian(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), cot=None, jtj
                               mask, _ptr(cot, torch.float32, "cot"), _ptr(jtj, torch.float64, "jtj"),
                               _ptr(jtv, torch.float64, "jtv"), _ptr(chi2, torch.float64, "chi2"),
                               _ptr(jac, torch.float32, "jac"), _stream(stream)))
+
+
+def gbk_jacobian_workspace_bytes(geom, n_models, free=(0, 1, 2, 3, 4, 5, 6, 7)):
+    g = cgeom(geom)
+    mask = 0
+    for k in free:
+        mask |= 1 << int(k)
+    n = lib().gbk_jacobian_workspace_bytes(ctypes.byref(g), int(n_models), mask)
+    err = lib().gbk_last_error().decode()
+    if n == 0 and err:
+        raise GbkError(GBK_EUNSUPPORTED if "serves" in err else GBK_EINVAL, err)
+    return n
+
+
+def gbk_jacobian_ws(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), cot=None, jtj=None, jtv=None, chi2=None,
+                    workspace=None, stream=None):
+    """The split-shape analytic Jacobian reductions (J^T J, J^T v, sum r^2)."""
+    g = cgeom(geom)
+    n = params.shape[0]
+    mask = 0
+    for k in free:
+        mask |= 1 << int(k)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_jacobian_ws(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"), ctypes.byref(obs.c()),
+                                 mask, _ptr(cot, torch.float32, "cot"), _ptr(jtj, torch.float64, "jtj"),
+                                 _ptr(jtv, torch.float64, "jtv"), _ptr(chi2, torch.float64, "chi2"),
+                                 _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def jacobian_split(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), device="cuda"):
+    """Convenience: (J^T J, J^T r, chi2) from the split-shape Jacobian."""
+    params = params.to(device=device, dtype=torch.float64).contiguous()
+    n, nf = params.shape[0], len(free)
+    jtj = torch.empty((n, nf, nf), dtype=torch.float64, device=device)
+    jtv = torch.empty((n, nf), dtype=torch.float64, device=device)
+    c2 = torch.empty(n, dtype=torch.float64, device=device)
+    ws = torch.empty(max(1, gbk_jacobian_workspace_bytes(geom, n, free)), dtype=torch.uint8, device=device)
+    gbk_jacobian_ws(geom, params, obs, free, None, jtj, jtv, c2, ws)
+    return jtj, jtv, c2
 
 
 def jacobian(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), device="cuda"):

@@ -127,3 +127,91 @@ def test_lm_with_tangent_jacobian(G):
     qt, ct, _, _ = G.fit_lm(g, [d], p0, lo[None], hi[None], opts)
     qf, cf, _, _ = G.fit_lm(g, [d], p0, lo[None], hi[None], G.lm_opts(max_iter=100, free=FREE))
     assert ct[0] <= cf[0] * (1 + 1e-4), (ct, cf)
+
+
+# The split-shape Jacobian (gbk_jacobian_ws): the same reductions as the
+# cluster kernel, whose J is checked above element by element against
+# central differences of the oracle, and against J^T J and J^T r formed from
+# the oracle's central-difference J directly.  Both kernels carry FP32
+# derivative triplets through the same arithmetic up to the order and form
+# of the PSF accumulation, so they agree to a few 1e-4 of the largest entry.
+SPLIT_CASES = ["single", "single_mode1", "nonsquare", "narrow_band", "direct_halo"]
+
+
+def _split_vs_cluster(G, g, ps, dobs, free, cot=None):
+    n, nf = ps.shape[0], len(free)
+    par = torch.from_numpy(ps).cuda()
+    out = {}
+    for name in ("cluster", "split"):
+        jtj = torch.empty((n, nf, nf), dtype=torch.float64, device="cuda")
+        jtv = torch.empty((n, nf), dtype=torch.float64, device="cuda")
+        c2 = torch.empty(n, dtype=torch.float64, device="cuda")
+        if name == "cluster":
+            G.gbk_jacobian(g, par, dobs, free, cot, jtj, jtv, c2, None)
+        else:
+            ws = torch.empty(G.gbk_jacobian_workspace_bytes(g, n, free), dtype=torch.uint8, device="cuda")
+            G.gbk_jacobian_ws(g, par, dobs, free, cot, jtj, jtv, c2, ws)
+        torch.cuda.synchronize()
+        out[name] = (jtj.cpu().numpy(), jtv.cpu().numpy(), c2.cpu().numpy())
+    return out["cluster"], out["split"]
+
+
+@pytest.mark.parametrize("case", SPLIT_CASES)
+def test_split_jacobian_matches_cluster_kernel_and_oracle(G, case):
+    g, p = CASES[case]
+    ps = model_params(g, p, 3, seed=17)
+    obs = make_obs(g, p, seed=3)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    (a_jtj, a_jtv, a_c), (b_jtj, b_jtv, b_c) = _split_vs_cluster(G, g, ps, dobs, FREE)
+    for i in range(ps.shape[0]):
+        s = np.abs(a_jtj[i]).max()
+        assert np.abs(b_jtj[i] - a_jtj[i]).max() <= 1e-3 * s, (case, i, np.abs(b_jtj[i] - a_jtj[i]).max() / s)
+        sv = np.abs(a_jtv[i]).max()
+        assert np.abs(b_jtv[i] - a_jtv[i]).max() <= 1e-3 * sv, (case, i)
+        assert abs(b_c[i] - a_c[i]) <= 1e-4 * a_c[i] + 1e-9, (case, i, b_c[i], a_c[i])
+    # against the oracle's central-difference Jacobian
+    _, r = oracle.chi2_batch(ogeom(g), ps, obs, want_resid=True)
+    for i in range(ps.shape[0]):
+        J = oracle_jacobian(g, ps[i], obs)[list(FREE)].reshape(len(FREE), -1).T
+        ref = J.T @ J
+        assert np.abs(b_jtj[i] - ref).max() <= 1e-2 * np.abs(ref).max(), (case, i)
+        gref = J.T @ r[i].ravel()
+        assert np.abs(b_jtv[i] - gref).max() <= 1e-2 * np.abs(gref).max(), (case, i)
+
+
+def test_split_jacobian_in_chunks_with_cotangent(G):
+    """More models than one L2-sized chunk (334 at 32 x 32), a
+    cotangent in place of the residuals, and fewer free parameters: the
+    output keeps the order of the free parameters."""
+    g, p = synth.SINGLE_GEOM, synth.SINGLE_TRUTH
+    n = 700
+    ps = model_params(g, p, n, seed=18)
+    obs = make_obs(g, p, seed=5)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    rng = np.random.default_rng(19)
+    cot = torch.from_numpy(rng.normal(size=(n, 2, g.ny, g.nx)).astype(np.float32)).cuda()
+    free = (synth.PA, synth.VMAX, synth.X0, synth.SIG0)
+    (a_jtj, a_jtv, a_c), (b_jtj, b_jtv, b_c) = _split_vs_cluster(G, g, ps, dobs, free, cot)
+    for i in (0, 1, 333, 334, 667, 668, n - 1):
+        s = np.abs(a_jtj[i]).max()
+        assert np.abs(b_jtj[i] - a_jtj[i]).max() <= 1e-3 * s, i
+        assert np.abs(b_jtv[i] - a_jtv[i]).max() <= 1e-3 * np.abs(a_jtv[i]).max(), i
+    np.testing.assert_allclose(b_c, a_c, rtol=1e-4)
+
+
+def test_split_jacobian_refuses_what_it_does_not_serve(G):
+    g = synth.SINGLE_GEOM
+    with pytest.raises(G.GbkError):  # I0 and h are not carried
+        G.gbk_jacobian_workspace_bytes(g, 4, tuple(range(10)))
+    with pytest.raises(G.GbkError):  # PSF radius 16 > 8
+        G.gbk_jacobian_workspace_bytes(g.with_(psf_fwhm=9.0), 4, FREE)
+    ps = model_params(g, synth.SINGLE_TRUTH, 4, seed=20)
+    obs = make_obs(g, synth.SINGLE_TRUTH, seed=5)
+    dobs = G.Obs.from_numpy(obs.v, obs.s, obs.w_v, obs.w_s, obs.mask)
+    jtj = torch.full((4, 8, 8), -1.0, dtype=torch.float64, device="cuda")
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(G.GbkError) as ei:
+        G.gbk_jacobian_ws(g, torch.from_numpy(ps).cuda(), dobs, FREE, None, jtj, None, None, small)
+    assert ei.value.status == G.GBK_EWORKSPACE
+    torch.cuda.synchronize()
+    assert torch.all(jtj == -1.0)
