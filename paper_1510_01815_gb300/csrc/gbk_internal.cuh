@@ -177,4 +177,49 @@ __device__ inline void block_taps(float sigma, int R, float *w)
     __syncthreads();
 }
 
+// Warp reduce-scatter of N per-lane FP32 values: at each of five levels a
+// lane keeps one half of its values and receives the partner's copy of that
+// half (shuffle distance 16, 8, .., 1), so every sum over the 32 lanes ends
+// on one lane after about N shuffles instead of 5 N.  Afterwards a[0..cnt)
+// hold the warp sums of entries base .. base + cnt - 1; the tree is fixed,
+// so the result does not depend on timing.  Whole warps.
+template <int N, int OFF>
+struct WarpScatter {
+    static constexpr int M = (N + 1) / 2;  // values kept at this level
+    static constexpr int MF = WarpScatter<M, OFF / 2>::MF;
+    __device__ __forceinline__ static void run(float *a, int lane, int &base, int &cnt)
+    {
+        const bool hi = (lane & OFF) != 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const float lo = a[i], up = (i + M < N) ? a[i + M] : 0.f;
+            const float keep = hi ? up : lo, send = hi ? lo : up;
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+        }
+        if (hi) {
+            base += M;
+            cnt -= M;
+        }
+        cnt = cnt < 0 ? 0 : (cnt > M ? M : cnt);
+        WarpScatter<M, OFF / 2>::run(a, lane, base, cnt);
+    }
+};
+template <int N>
+struct WarpScatter<N, 0> {
+    static constexpr int MF = N;
+    __device__ __forceinline__ static void run(float *, int, int &, int &) {}
+};
+
+// Sums N values per lane over the warp into red[0..N) (one slot per entry,
+// written once by the lane that ends with it).  a[] is clobbered.
+template <int N>
+__device__ __forceinline__ void warp_sum_scatter(float (&a)[N], int lane, float *red)
+{
+    int base = 0, cnt = N;
+    WarpScatter<N, 16>::run(a, lane, base, cnt);
+#pragma unroll
+    for (int i = 0; i < WarpScatter<N, 16>::MF; ++i)
+        if (i < cnt) red[base + i] = a[i];
+}
+
 }  // namespace gbk

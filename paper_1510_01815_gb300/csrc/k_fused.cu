@@ -377,10 +377,12 @@ __global__ void __launch_bounds__(NT, MINB) fused_eval_kernel(FusedArgs a)
     }
 
     if (want_chi2) {
-        double v = (double)acc.s - (double)acc.c;
+        // each warp's sum in FP32 (the compensated per-thread sums, a fixed
+        // shuffle tree), the warps and the CTAs in FP64
+        float v = acc.s - acc.c;
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         int warp = tid >> 5, lane = tid & 31;
-        if (lane == 0) red[warp] = v;
+        if (lane == 0) red[warp] = (double)v;
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;

@@ -37,8 +37,8 @@ __global__ void lm_build_fd_kernel(LmArgs a)
 
 // ----------------------------------------------------------------------------
 // J^T J and J^T r from the batch residuals; one CTA per galaxy.  Products are
-// accumulated in FP32 per thread (a few residuals each) and reduced in FP64
-// in a fixed order.
+// accumulated in FP32 per thread (a few residuals each), summed over each
+// warp in FP32 and over the warps in FP64, in a fixed order.
 template <int NP>
 __global__ void __launch_bounds__(256) lm_normal_fd_kernel(LmArgs a)
 {
@@ -56,9 +56,9 @@ __global__ void __launch_bounds__(256) lm_normal_fd_kernel(LmArgs a)
     const float *R = a.resid + base;
     float inv_h[NP];
     for (int j = 0; j < NP; ++j) inv_h[j] = (float)(1.0 / a.hstep[(size_t)gal * NP + j]);
-    float jtj[NT], jtr[NP];
-    for (int t = 0; t < NT; ++t) jtj[t] = 0.f;
-    for (int j = 0; j < NP; ++j) jtr[j] = 0.f;
+    float E[NT + NP];  // J^T J upper triangle, then J^T r
+    float *const jtj = E, *const jtr = E + NT;
+    for (int t = 0; t < NT + NP; ++t) E[t] = 0.f;
     for (size_t i = threadIdx.x; i < n2; i += blockDim.x) {
         float r0 = R[i];
         float J[NP];
@@ -79,18 +79,14 @@ __global__ void __launch_bounds__(256) lm_normal_fd_kernel(LmArgs a)
             }
         }
     }
-    __shared__ double red[8][NT + NP];
+    // each warp's sums in FP32 by a reduce-scatter, the warps in FP64 in order
+    __shared__ float red[8][NT + NP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int t = 0; t < NT + NP; ++t) {
-        double v = (t < NT) ? (double)jtj[t] : (double)jtr[t - NT];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) red[warp][t] = v;
-    }
+    warp_sum_scatter<NT + NP>(E, lane, red[warp]);
     __syncthreads();
     for (int t = threadIdx.x; t < NT + NP; t += blockDim.x) {
         double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][t];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)red[w][t];
         if (t < NT) {
             // upper-triangle index t -> (j, k)
             int j = 0, rem = t;

@@ -320,9 +320,11 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
     }
     if (!want_chi2) return;
     // the tile's part, then the model's total from the last tile to finish
-    double v = (double)acc.s - (double)acc.c;
+    // each warp's sum in FP32 (the compensated per-thread sums, a fixed
+    // shuffle tree), the warps and tiles in FP64
+    float v = acc.s - acc.c;
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) red[tid >> 5] = v;
+    if (lane == 0) red[tid >> 5] = (double)v;
     __syncthreads();
     if (tid == 0) {
         double sum = 0.0;

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
     float *tzy = tzx + ezp, *tzz = tzy + ezp;
     float *wxy = tzx + ((3 * ezp + 3) & ~3);
     const float **rowptr = reinterpret_cast<const float **>(wxy + ((2 * R + 1 + 3) & ~3));
-    double *wred = reinterpret_cast<double *>(rowptr + ((band + 2 * R + 1) & ~1));  // [warps][kEnt]
+    float *wred = reinterpret_cast<float *>(rowptr + ((band + 2 * R + 1) & ~1));  // [warps][kEnt]
 
     __shared__ ModelConst mc;
     __shared__ gbk_obs s_ob;
@@ -451,19 +451,15 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
         for (int j = 0; j < NPT; ++j, ++e) E[e] = fmaf(jv[j], cv_, fmaf(js[j], cs_, E[e]));
         E[e] = fmaf(rv, rv, fmaf(rs, rs, E[e]));
     }
-    // CTA sum: warps in FP64 by shuffles, then the warps in order
+    // CTA sum: each warp's in FP32 by a reduce-scatter, then the warps in
+    // FP64 in order
     {
         const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
-#pragma unroll
-        for (int e = 0; e < kEnt; ++e) {
-            double v = (double)E[e];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) wred[warp * kEnt + e] = v;
-        }
+        warp_sum_scatter<kEnt>(E, lane, wred + warp * kEnt);
         __syncthreads();
         for (int e = tid; e < kEnt; e += nthr) {
             double v = 0.0;
-            for (int q = 0; q < nw; ++q) v += wred[q * kEnt + e];
+            for (int q = 0; q < nw; ++q) v += (double)wred[q * kEnt + e];
             s_part[e] = v;
         }
     }

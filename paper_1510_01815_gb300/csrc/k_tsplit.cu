@@ -26,8 +26,9 @@
 //           of a model: the tile's rows of all 28 planes in one TMA load
 //           (bounded mbarrier wait, status bit 3), the PSF pass along y for
 //           two outputs per thread, the moments, residuals and Jacobian rows,
-//           J^T J, J^T v and sum r^2 per thread, the CTA's sums in FP64 in a
-//           fixed order; the last tile of a model adds the tiles in order.
+//           J^T J, J^T v and sum r^2 per thread, the CTA's sums (FP32 within
+//           a warp, FP64 over the warps) in a fixed order; the last tile of
+//           a model adds the tiles in order.
 //
 // The PSF passes accumulate as the split evaluator's (six FP32 operations
 // per tap and triplet).  Models go in chunks whose planes stay in L2.
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kTsThreads, 2)
     float *const sp = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sraw) + 127) & ~(uintptr_t)127);
     __shared__ ModelConst mc;
     __shared__ gbk_obs s_ob;
-    __shared__ double red[kTsThreads / 32][kTsEnt];
+    __shared__ float red[kTsThreads / 32][kTsEnt];
     __shared__ double s_part[kTsEnt];
     __shared__ bool s_last;
     __shared__ __align__(8) uint64_t bar;
@@ -470,17 +471,13 @@ __global__ void __launch_bounds__(kTsThreads, 2)
             for (int j = 0; j < kTsNP; ++j, ++e) E[e] = fmaf(jv[o][j], cv[o], fmaf(js[o][j], cs[o], E[e]));
         }
     }
-    // the CTA's sums: warps in FP64 by shuffles, then the warps in order
-#pragma unroll
-    for (int e = 0; e < kTsEnt; ++e) {
-        double vv = (double)E[e];
-        for (int off = 16; off > 0; off >>= 1) vv += __shfl_down_sync(0xffffffffu, vv, off);
-        if (lane == 0) red[warp][e] = vv;
-    }
+    // the CTA's sums: each warp's in FP32 by a reduce-scatter, then the warps
+    // in FP64 in order
+    warp_sum_scatter<kTsEnt>(E, lane, red[warp]);
     __syncthreads();
     if (tid < kTsEnt) {
         double sum = 0.0;
-        for (int q = 0; q < kTsThreads / 32; ++q) sum += red[q][tid];
+        for (int q = 0; q < kTsThreads / 32; ++q) sum += (double)red[q][tid];
         a.part[((size_t)model * a.tiles + tile) * kTsEnt + tid] = sum;
     }
     __syncthreads();

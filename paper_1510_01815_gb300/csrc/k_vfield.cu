@@ -6,8 +6,8 @@
 //
 // One CTA per model (grid-stride over models), consecutive pixels on
 // consecutive threads (coalesced map reads and writes, as the paper's
-// evaluation kernel does), Kahan sums per thread and a fixed-order FP64
-// block reduction, so chi2 is bitwise reproducible.
+// evaluation kernel does), Kahan sums per thread, FP32 warp sums and a
+// fixed-order FP64 sum over the warps, so chi2 is bitwise reproducible.
 #include "gbk_api_internal.h"
 #include "k_fused.h"
 #include "k_tangent.h"
@@ -116,9 +116,10 @@ __global__ void __launch_bounds__(kVfThreads) vfield_kernel(FusedArgs a)
             }
         }
         if (a.chi2) {
-            double v = (double)s - (double)comp;
+            // each warp's sum in FP32 (a fixed shuffle tree), the warps in FP64
+            float v = s - comp;
             for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if ((tid & 31) == 0) red[tid >> 5] = v;
+            if ((tid & 31) == 0) red[tid >> 5] = (double)v;
             __syncthreads();
             if (tid == 0) {
                 double tot = 0.0;
@@ -151,14 +152,15 @@ __global__ void __launch_bounds__(kVfThreads) vfield_kernel(FusedArgs a)
 //   the Epinat curve, whose F is 0 there, zero derivatives).  Rows are
 //   J_v = w_v dm1, J_s = w_s dm2 on unmasked pixels.  Every thread keeps its
 //   pixels' J^T J, J^T v and sum r^2 for all ten parameters in registers;
-//   the CTA reduces them in FP64 in a fixed order.
+//   the CTA reduces them (FP32 within a warp, FP64 over the warps) in a
+//   fixed order.
 constexpr int kVfEnt = GBK_NPAR * (GBK_NPAR + 1) / 2 + GBK_NPAR + 1;
 
 __global__ void __launch_bounds__(kVfThreads) vfield_tangent_kernel(TangentArgs a)
 {
     __shared__ VfConst s_c;
     __shared__ gbk_obs s_ob;
-    __shared__ double wred[kVfThreads / 32][kVfEnt];
+    __shared__ float wred[kVfThreads / 32][kVfEnt];
     __shared__ double s_part[kVfEnt];
     const int tid = threadIdx.x;
     const int nx = a.g.nx, np = a.g.nx * a.g.ny;
@@ -264,18 +266,14 @@ __global__ void __launch_bounds__(kVfThreads) vfield_tangent_kernel(TangentArgs 
             for (int j = 0; j < GBK_NPAR; ++j, ++e) E[e] = fmaf(jv[j], cv, fmaf(js[j], cs, E[e]));
             E[e] = fmaf(rv, rv, fmaf(rs, rs, E[e]));
         }
-        // CTA sum: warps by shuffles in FP64, then the warps in order
+        // CTA sum: each warp's in FP32 by a reduce-scatter, then the warps in
+        // FP64 in order
         const int warp = tid >> 5, lane = tid & 31;
-#pragma unroll
-        for (int e = 0; e < kVfEnt; ++e) {
-            double v = (double)E[e];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) wred[warp][e] = v;
-        }
+        warp_sum_scatter<kVfEnt>(E, lane, wred[warp]);
         __syncthreads();
         for (int e = tid; e < kVfEnt; e += kVfThreads) {
             double v = 0.0;
-            for (int q = 0; q < kVfThreads / 32; ++q) v += wred[q][e];
+            for (int q = 0; q < kVfThreads / 32; ++q) v += (double)wred[q][e];
             s_part[e] = v;
         }
         __syncthreads();
