@@ -803,10 +803,12 @@ def run_ns_fp(gbk, torch, device, n_gal=2, n_live=400, batch=100):
 
 
 def run_jacobian(gbk, torch, device, n=2048, geom=None):
-    """The analytic Jacobian kernel (gbk_jacobian: J^T J, J^T r and chi2 of
-    the eight free parameters, J not written) on n models of one geometry
-    (default the single-galaxy 32 x 32 x 64 cube), against the 1 + 8 fused
-    evaluations a forward-difference Jacobian needs for the same models."""
+    """The analytic Jacobian (J^T J, J^T r and chi2 of the eight free
+    parameters, J not written) on n models of one geometry (default the
+    single-galaxy 32 x 32 x 64 cube), against the 1 + 8 evaluations a
+    forward-difference Jacobian needs for the same models: the two-stage
+    kernels (gbk_jacobian_ws, gbk_chi2 on the split path) as the headline,
+    the one-cluster-per-model kernels beside them."""
     g = geom or synth.SINGLE_GEOM
     rng = np.random.default_rng(9)
     truth = synth.SINGLE_TRUTH.copy()
@@ -838,11 +840,17 @@ def run_jacobian(gbk, torch, device, n=2048, geom=None):
         b.synchronize()
         return a.elapsed_time(b) / reps
 
-    tj = timed(lambda: gbk.gbk_jacobian(g, dp, obs, FIT_FREE, None, jtj, jtv, c2, None))
-    tf = timed(lambda: gbk.gbk_chi2(g, dfd, obs, cfd, None, gbk.PATH_FUSED, None))
+    wsj = torch.empty(gbk.gbk_jacobian_workspace_bytes(g, n, FIT_FREE), dtype=torch.uint8, device=device)
+    wse = gbk.workspace_for(g, dfd.shape[0], gbk.PATH_SPLIT)
+    tj = timed(lambda: gbk.gbk_jacobian_ws(g, dp, obs, FIT_FREE, None, jtj, jtv, c2, wsj))
+    tc = timed(lambda: gbk.gbk_jacobian(g, dp, obs, FIT_FREE, None, jtj, jtv, c2, None))
+    tf = timed(lambda: gbk.gbk_chi2(g, dfd, obs, cfd, None, gbk.PATH_SPLIT, wse))
+    tff = timed(lambda: gbk.gbk_chi2(g, dfd, obs, cfd, None, gbk.PATH_FUSED, None))
     return {"workload": "%d models of a %dx%dx%d cube, 8 free parameters" % (n, g.nx, g.ny, g.nz),
             "jacobian_ms": tj, "fd_evals_ms": tf, "jacobian_vs_fd_evals": tj / tf,
-            "jacobians_per_s": n / (tj * 1e-3)}
+            "jacobians_per_s": n / (tj * 1e-3),
+            "kernels": "two-stage Jacobian (gbk_jacobian_ws) against 1 + 8 two-stage evaluations",
+            "cluster_jacobian_ms": tc, "cluster_fd_evals_ms": tff}
 
 
 def run_grid(gbk, torch, device, chunk=1 << 17):

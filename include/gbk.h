@@ -319,6 +319,11 @@ typedef struct gbk_lm_opts {
     double ftol, xtol;         /* stopping tolerances (e.g. 1e-10)               */
     double lambda0;            /* initial damping (e.g. 1e-3)                    */
     double fd_step[GBK_NPAR];  /* absolute finite-difference steps (e.g. 0.1)    */
+    int32_t path;              /* batched mode, one geometry: GBK_PATH_AUTO (0)  */
+                               /* = the split evaluator and Jacobian where they  */
+                               /* serve the geometry, GBK_PATH_SPLIT = required, */
+                               /* GBK_PATH_FUSED = the cluster kernels           */
+    int32_t reserved;          /* 0                                              */
 } gbk_lm_opts;
 
 /* Workspace bytes gbk_fit_lm needs (0 and last error set on bad input). */

@@ -72,6 +72,9 @@ struct SplitArgs {
     const float *tab;        // split_tab_floats(g) floats
     float *pl;               // x-filtered planes, [n_models][4][ey][nxp]
     gbk_obs obs;
+    const gbk_obs *obs_list; // per galaxy (model m0 + i is galaxy (m0 + i) / mpg), or null: obs for all
+    const int32_t *skip;     // per galaxy: non-zero = leave the galaxy's models alone (or null)
+    int m0, mpg;             // first model of the chunk in the call, models per galaxy
     float *maps;             // [n_models][3][ny][nx] or null
     double *chi2;            // [n_models] or null
     float *resid;            // [n_models][2][ny][nx] or null
@@ -111,6 +114,7 @@ __global__ void __launch_bounds__(kSplitThreads, 4) split_line_kernel(SplitArgs 
     __shared__ ModelConst mc;
     const Geom &g = a.g;
     const int tid = threadIdx.x, model = blockIdx.y;
+    if (a.skip && a.skip[(a.m0 + model) / a.mpg] != 0) return;  // the whole CTA
     const int row0 = blockIdx.x * kSplitRA, nrows = min(kSplitRA, g.ey - row0);
     const int PA = split_rowpitch_a(g.ex);        // floats per plane row
     const int NPL = kSplitRA * PA;
@@ -206,6 +210,8 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
     const Geom &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31;
     const int model = blockIdx.y, tile = blockIdx.x;
+    const int gal = (a.m0 + model) / a.mpg;
+    if (a.skip && a.skip[gal] != 0) return;  // the whole CTA
     const int tx0 = (tile % a.tiles_x) * kSplitTX, ty0 = (tile / a.tiles_x) * kSplitTY;
     const int nxo = min(kSplitTX, g.nx - tx0), nyo = min(kSplitTY, g.ny - ty0);
     if (tid == 0) {
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
     }
     if (tid < (int)(sizeof(ModelConst) / 4))
         reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
-    if (tid == 32) s_ob = a.obs;
+    if (tid == 32) s_ob = a.obs_list ? a.obs_list[gal] : a.obs;
     float w[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) w[j] = a.tab[kTabTaps + j];
@@ -440,8 +446,12 @@ static gbk_status launch_stages(const CUtensorMap &tm, const SplitArgs &a, cudaS
 }
 
 gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_obs *obs, float *maps, double *chi2,
-                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer)
+                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer,
+                        const SplitBatch *batch)
 {
+    if (batch && batch->mpg < 1) return fail(GBK_EINVAL, "split evaluator: models per galaxy must be >= 1");
+    if ((chi2 || resid) && !obs && !(batch && batch->obs_list))
+        return fail(GBK_EINVAL, "split evaluator: chi2 and residuals need observed maps");
     if (!split_supported(g)) return fail(GBK_EUNSUPPORTED, "the split evaluator does not serve this geometry");
     if (n == 0) return GBK_OK;
     const SplitLayout L = split_layout(g, n);
@@ -482,6 +492,10 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
         a.tab = tab;
         a.pl = (float *)(base + L.pl_off);
         if (obs) a.obs = *obs;
+        a.obs_list = batch ? batch->obs_list : nullptr;
+        a.skip = batch ? batch->skip : nullptr;
+        a.m0 = m0;
+        a.mpg = batch ? batch->mpg : 1;
         a.maps = maps ? maps + 3 * np * m0 : nullptr;
         a.chi2 = chi2 ? chi2 + m0 : nullptr;
         a.resid = resid ? resid + 2 * np * m0 : nullptr;

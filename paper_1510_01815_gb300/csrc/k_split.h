@@ -42,7 +42,17 @@ SplitEncodeFn split_encode_fn();
 
 // Reads and clears the PSF stage's TMA wait status (1 = a load timed out).
 gbk_status split_status_read(int *v);
+
+// A batched call's galaxies: models i*mpg .. i*mpg + mpg - 1 belong to galaxy
+// i, which is compared with obs_list[i] (device, or null: *obs for all) and
+// left alone when skip[i] != 0 (device, or null).
+struct SplitBatch {
+    const gbk_obs *obs_list;
+    const int32_t *skip;
+    int mpg;
+};
 gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_obs *obs, float *maps, double *chi2,
-                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer = nullptr);
+                        float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer = nullptr,
+                        const SplitBatch *batch = nullptr);
 
 }  // namespace gbk

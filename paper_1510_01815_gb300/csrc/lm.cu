@@ -4,12 +4,16 @@
 // Batched mode: every galaxy advances together.  One iteration is
 //   Jacobian -> FP64 normal equations -> damped Cholesky solve -> fused
 //   evaluation of the trial points -> accept/reject,
-// where the Jacobian is either a finite-difference batch (fused evaluation
-// of chi2 and residual maps of 1 + P or 1 + 2P models per galaxy, then a
-// reduction kernel) or the analytic tangent kernel, which reduces J^T J and
-// J^T r directly;
+// where the Jacobian is either a finite-difference batch (evaluation of chi2
+// and residual maps of 1 + P or 1 + 2P models per galaxy, then a reduction
+// kernel) or the analytic tangent kernels, which reduce J^T J and J^T r
+// directly;
 // all on the device; it is captured once in a CUDA graph and replayed, and
-// the host reads the number of running galaxies every kPoll iterations.
+// the host reads the number of running galaxies every kPoll iterations.  The
+// evaluations and the analytic Jacobian take the two-stage (split) kernels
+// where they serve the geometry and the caller's path allows, else the
+// one-cluster-per-model kernels; chi2 values that accept/reject compares
+// always come from one evaluator.
 //
 // Plain mode: the paper's arrangement -- one galaxy at a time, the model
 // evaluations on the GPU, the residual maps copied to the host every
@@ -24,7 +28,9 @@
 #include "gbk_api_internal.h"
 #include "k_fused.h"
 #include "k_lm.h"
+#include "k_split.h"
 #include "k_tangent.h"
+#include "k_tsplit.h"
 #include "survey.h"
 
 namespace gbk {
@@ -68,11 +74,12 @@ static gbk_status lm_plan(const gbk_lm_opts *o, LmPlan *pl)
 // batched mode, 1 in the plain mode).
 struct LmLayout {
     size_t pbatch, resid, chi2b, hstep, jtj, jtr, ptrial, chi2t, chi2cur, chi2best, lambda, dnorm, pnorm;
-    size_t iters, status, done, nact, total;
+    size_t iters, status, done, nact, sws, sws_bytes, total;
 };
 
-// pix_total: pixels of all ng galaxies together.
-static LmLayout lm_layout_pix(size_t pix_total, int ng, const LmPlan &pl)
+// pix_total: pixels of all ng galaxies together; split_bytes: the region the
+// split evaluator and Jacobian share (they run one after the other).
+static LmLayout lm_layout_pix(size_t pix_total, int ng, const LmPlan &pl, size_t split_bytes = 0)
 {
     LmLayout L;
     size_t o = 0;
@@ -94,13 +101,38 @@ static LmLayout lm_layout_pix(size_t pix_total, int ng, const LmPlan &pl)
     L.status = take(sizeof(int32_t) * ng);
     L.done = take(sizeof(int32_t) * ng);
     L.nact = take(sizeof(int32_t));
+    L.sws = take(split_bytes);
+    L.sws_bytes = split_bytes;
     L.total = o;
     return L;
 }
 
-static LmLayout lm_layout(const Geom &g, int ng, const LmPlan &pl)
+static LmLayout lm_layout(const Geom &g, int ng, const LmPlan &pl, size_t split_bytes = 0)
 {
-    return lm_layout_pix((size_t)ng * g.nx * g.ny, ng, pl);
+    return lm_layout_pix((size_t)ng * g.nx * g.ny, ng, pl, split_bytes);
+}
+
+// Which split kernels a batched fit of ng galaxies of one geometry uses
+// (path: GBK_PATH_AUTO = where they serve, GBK_PATH_SPLIT = required,
+// GBK_PATH_FUSED = never) and the workspace they share.
+struct LmSplit {
+    bool eval, jac;
+    size_t bytes;
+};
+
+static gbk_status lm_split_plan(const Geom &g, int ng, const LmPlan &pl, int32_t path, LmSplit *sp)
+{
+    *sp = LmSplit{false, false, 0};
+    if (path == (int32_t)GBK_PATH_FUSED) return GBK_OK;
+    if (path != (int32_t)GBK_PATH_AUTO && path != (int32_t)GBK_PATH_SPLIT)
+        return fail(GBK_EINVAL, "LM evaluates on GBK_PATH_AUTO, GBK_PATH_FUSED or GBK_PATH_SPLIT (got %d)", path);
+    sp->eval = split_supported(g);
+    sp->jac = pl.tangent && tsplit_supported(g, pl.np, pl.idx);
+    if (path == (int32_t)GBK_PATH_SPLIT && (!sp->eval || (pl.tangent && !sp->jac)))
+        return fail(GBK_EUNSUPPORTED, "the split kernels do not serve this geometry and free-parameter set");
+    if (sp->eval) sp->bytes = split_workspace_bytes(g, ng * pl.m);
+    if (sp->jac) sp->bytes = std::max(sp->bytes, tsplit_workspace_bytes(g, ng));
+    return GBK_OK;
 }
 
 static gbk_status fused_for(const Geom &g, int n_models, const double *params, const gbk_obs *obs_list,
@@ -127,16 +159,24 @@ static gbk_status fused_for(const Geom &g, int n_models, const double *params, c
 }
 
 // What the batched LM evaluates: one geometry for every galaxy, or a ragged
-// survey plan.
+// survey plan; for one geometry, whether the split evaluator and Jacobian
+// serve it, and their workspace.
 struct EvalTarget {
     const Geom *g;
     const SurveyPlan *sp;
+    LmSplit split;
+    void *sws;
 };
 
 static gbk_status eval_for(const EvalTarget &t, int n_gal, int mpg, const double *params, const gbk_obs *obs_list,
                            const int32_t *skip, double *chi2, float *resid, cudaStream_t st)
 {
     if (t.sp) return survey_eval(*t.sp, mpg, params, obs_list, skip, nullptr, chi2, resid, st);
+    if (t.split.eval) {
+        const SplitBatch b = {obs_list, skip, mpg};
+        return launch_split(*t.g, n_gal * mpg, params, nullptr, nullptr, chi2, resid, t.sws, t.split.bytes, st,
+                            nullptr, &b);
+    }
     return fused_for(*t.g, n_gal * mpg, params, obs_list, nullptr, mpg, skip, chi2, resid, st);
 }
 
@@ -315,14 +355,17 @@ static gbk_status lm_plain(const Geom &g, int n_gal, const gbk_obs *obs, const d
 }
 
 static gbk_status lm_iteration(const EvalTarget &t, const LmArgs &a, const gbk_obs *obs, bool tangent,
-                               const TangentArgs &ta, cudaStream_t st)
+                               const TangentArgs &ta, const TsplitCall &tc, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(a.n_active, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "LM: clearing the running count");
     gbk_status s;
     if (tangent) {
         // analytic J^T J and J^T r at the current point
-        if ((s = t.sp ? survey_tangent(*t.sp, ta, st) : launch_tangent(ta, st))) return s;
+        if (t.sp) s = survey_tangent(*t.sp, ta, st);
+        else if (t.split.jac) s = launch_tsplit(tc, t.sws, t.split.bytes, st);
+        else s = launch_tangent(ta, st);
+        if (s) return s;
     } else {
         lm_launch_build_fd(a, st);
         s = eval_for(t, a.n_gal, a.m, a.pbatch, obs, a.done, a.chi2_batch, a.resid, st);
@@ -342,7 +385,8 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
                              double *params, const gbk_lm_opts *o, const LmPlan &pl, double *chi2_out,
                              int32_t *iters_out, int32_t *status_out, char *ws, cudaStream_t user)
 {
-    LmLayout L = t.sp ? lm_layout_pix((size_t)t.sp->total_pix(), n_gal, pl) : lm_layout(*t.g, n_gal, pl);
+    LmLayout L = t.sp ? lm_layout_pix((size_t)t.sp->total_pix(), n_gal, pl)
+                      : lm_layout(*t.g, n_gal, pl, t.split.bytes);
     LmArgs a = {};
     a.n_gal = n_gal;
     a.np = pl.np;
@@ -386,7 +430,20 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     cudaStream_t st = cg.s;
     lm_launch_init(a, o->lambda0, st);
     TangentArgs ta = {};
-    if (pl.tangent) {
+    TsplitCall tc = {};
+    if (pl.tangent && !t.sp && t.split.jac) {
+        tc.g = *t.g;
+        tc.n_models = n_gal;
+        tc.params = params;
+        tc.obs_list = obs;
+        tc.skip = a.done;
+        tc.np = pl.np;
+        for (int j = 0; j < pl.np; ++j) tc.free_idx[j] = pl.idx[j];
+        tc.jtj = a.jtj;
+        tc.jtv = a.jtr;
+        gbk_status s0 = eval_for(t, n_gal, 1, params, obs, nullptr, a.chi2_cur, nullptr, st);
+        if (s0) return s0;
+    } else if (pl.tangent) {
         ta.np = pl.np;
         for (int j = 0; j < pl.np; ++j) ta.free_idx[j] = pl.idx[j];
         if (t.sp) {
@@ -405,21 +462,21 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
         ta.skip = a.done;
         ta.jtj = a.jtj;
         ta.jtv = a.jtr;
-        // chi2 at the start point from the fused kernel: accept/reject
-        // decisions always compare fused-kernel chi2 values
+        // chi2 at the start point from the evaluator: accept/reject
+        // decisions always compare that evaluator's chi2 values
         gbk_status s0 = eval_for(t, n_gal, 1, params, obs, nullptr, a.chi2_cur, nullptr, st);
         if (s0) return s0;
     }
     // The first iteration runs eagerly (it also settles the kernels' launch
     // configurations); the rest replay a captured graph.
-    gbk_status s = lm_iteration(t, a, obs, pl.tangent, ta, st);
+    gbk_status s = lm_iteration(t, a, obs, pl.tangent, ta, tc, st);
     if (s) return s;
     int32_t h_active = n_gal;
     int done_iters = 1;
     if (o->max_iter > 1) {
         if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
             return cuda_fail(e, "LM: begin graph capture");
-        s = lm_iteration(t, a, obs, pl.tangent, ta, st);
+        s = lm_iteration(t, a, obs, pl.tangent, ta, tc, st);
         e = cudaStreamEndCapture(st, &cg.graph);
         if (s) return s;
         if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");
@@ -578,7 +635,7 @@ static gbk_status fit_part(const gbk_geom *geoms, const std::vector<int32_t> &id
     SurveyPlan sp;
     if ((s = survey_plan(sub.data(), n, &sp))) return s;
     if ((s = survey_upload(&sp, rest, st))) return s;
-    EvalTarget t = {nullptr, &sp};
+    EvalTarget t = {nullptr, &sp, LmSplit{false, false, 0}, nullptr};
     if ((s = lm_batched(t, n, d_obs, d_lo, d_hi, d_p, o, pl, d_c, d_it, d_st, rest + sp.table_bytes, st))) return s;
     if ((s = rows_copy(d_p, params, d_idx, n, prow, true, st)) || (s = rows_copy(d_c, chi2_out, d_idx, n, 8, true, st)) ||
         (s = rows_copy(d_it, iters_out, d_idx, n, 4, true, st)) || (s = rows_copy(d_st, status_out, d_idx, n, 4, true, st)))
@@ -644,7 +701,7 @@ gbk_status lm_survey(SurveyPlan &sp, const gbk_geom *geoms, const gbk_obs *obs, 
         if (sb) return fail(sb, "survey split (finite-difference part): %s", eb.c_str());
         return ok();
     }
-    EvalTarget t = {nullptr, &sp};
+    EvalTarget t = {nullptr, &sp, LmSplit{false, false, 0}, nullptr};
     return lm_batched(t, sp.n_gal, obs, lo, hi, params, o, pl, chi2_out, iters_out, status_out, ws, st);
 }
 
@@ -766,7 +823,10 @@ size_t gbk_fit_lm_workspace_bytes(const gbk_geom *gin, int32_t n_gal, const gbk_
     LmPlan pl;
     if (lm_plan(opts, &pl)) return 0;
     if (n_gal < 0) { fail(GBK_EINVAL, "n_gal must be >= 0"); return 0; }
-    return lm_layout(g, opts->mode == GBK_LM_PLAIN ? 1 : n_gal, pl).total;
+    if (opts->mode == GBK_LM_PLAIN) return lm_layout(g, 1, pl).total;
+    LmSplit spl;
+    if (lm_split_plan(g, n_gal, pl, opts->path, &spl)) return 0;
+    return lm_layout(g, n_gal, pl, spl.bytes).total;
 }
 
 gbk_status gbk_fit_lm(const gbk_geom *gin, int32_t n_gal, const gbk_obs *obs, const double *lo, const double *hi,
@@ -788,14 +848,16 @@ gbk_status gbk_fit_lm(const gbk_geom *gin, int32_t n_gal, const gbk_obs *obs, co
         (s = check_device_ptr(chi2_out, "chi2_out", 8)) || (s = check_device_ptr(iters_out, "iters_out", 4)) ||
         (s = check_device_ptr(status_out, "status_out", 4)))
         return s;
-    LmLayout L = lm_layout(g, opts->mode == GBK_LM_PLAIN ? 1 : n_gal, pl);
+    LmSplit spl = {};
+    if (opts->mode != GBK_LM_PLAIN && (s = lm_split_plan(g, n_gal, pl, opts->path, &spl))) return s;
+    LmLayout L = lm_layout(g, opts->mode == GBK_LM_PLAIN ? 1 : n_gal, pl, spl.bytes);
     if (!workspace || ws_bytes < L.total)
         return fail(GBK_EWORKSPACE, "gbk_fit_lm needs %zu bytes of workspace (got %zu)", L.total, ws_bytes);
     if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (opts->mode == GBK_LM_PLAIN)
         return lm_plain(g, n_gal, obs, lo, hi, params, opts, pl, chi2_out, iters_out, status_out, (char *)workspace, st);
-    EvalTarget t = {&g, nullptr};
+    EvalTarget t = {&g, nullptr, spl, (char *)workspace + L.sws};
     return lm_batched(t, n_gal, obs, lo, hi, params, opts, pl, chi2_out, iters_out, status_out, (char *)workspace, st);
 }
 

@@ -44,7 +44,8 @@ class CTuning(ctypes.Structure):
 class CLmOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("jacobian", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("free_mask", ctypes.c_uint32), ("ftol", ctypes.c_double), ("xtol", ctypes.c_double),
-                ("lambda0", ctypes.c_double), ("fd_step", ctypes.c_double * 10)]
+                ("lambda0", ctypes.c_double), ("fd_step", ctypes.c_double * 10), ("path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class CNsOpts(ctypes.Structure):
@@ -327,14 +328,15 @@ def gbk_set_tuning(geom, cluster_ctas=None, threads=None, persistent=0):
 
 
 def lm_opts(max_iter=200, jacobian=JAC_FD_FORWARD, mode=LM_BATCHED, free=(0, 1, 2, 3, 4, 5, 6, 7),
-            ftol=1e-10, xtol=1e-10, lambda0=1e-3, fd_step=0.1):
-    """Options of gbk_fit_lm; fd_step is a scalar or ten values."""
+            ftol=1e-10, xtol=1e-10, lambda0=1e-3, fd_step=0.1, path=PATH_AUTO):
+    """Options of gbk_fit_lm; fd_step is a scalar or ten values; path picks
+    the batched mode's kernels (PATH_AUTO, PATH_SPLIT or PATH_FUSED)."""
     steps = [float(fd_step)] * NPAR if the_scalar(fd_step) else [float(v) for v in fd_step]
     mask = 0
     for k in free:
         mask |= 1 << int(k)
     return CLmOpts(int(max_iter), int(jacobian), int(mode), mask, float(ftol), float(xtol), float(lambda0),
-                   (ctypes.c_double * 10)(*steps))
+                   (ctypes.c_double * 10)(*steps), int(path), 0)
 
 
 def the_scalar(v):

@@ -1,5 +1,7 @@
 """Levenberg-Marquardt on the GPU (gbk_fit_lm) against the paper's recovery
 targets and against the oracle's LM (matched chi2)."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -92,3 +94,70 @@ def test_fixed_parameters_untouched_and_statuses(G):
     q, c, it, st = G.fit_lm(g, [_dobs(G, obs)] * 4, p0, [lo] * 4, [hi] * 4, opts)
     assert np.all(q[:, synth.I0] == p0[:, synth.I0]) and np.all(q[:, synth.H] == p0[:, synth.H])
     assert np.all(it <= 3) and np.all(np.isin(st, [1, 2, 3]))
+
+
+@pytest.mark.parametrize("jac", [0, 2])
+@pytest.mark.parametrize("path", [1, 3])
+def test_batched_paths_recover_the_truth(G, jac, path):
+    """The batched mode on either kernel family (the one-cluster-per-model
+    evaluator and Jacobian, or the two-stage ones) from the same perturbed
+    starts: both reach the paper's recovery thresholds and chi2 ~ 0."""
+    g, p, obs = galaxy(noise_v=0.0)
+    lo, hi = bounds(p)
+    n = 10
+    p0 = starts(p, n, seed=31)
+    opts = G.lm_opts(max_iter=100, jacobian=jac, mode=0, free=FREE, path=path)
+    q, c, it, st = G.fit_lm(g, [_dobs(G, obs)] * n, p0, [lo] * n, [hi] * n, opts)
+    assert np.all(np.isin(st, [1, 2])), (st, it)
+    assert np.all(np.abs(q[:, synth.VMAX] - p[synth.VMAX]) < 2.0), q[:, synth.VMAX]
+    assert np.all(np.abs(q[:, synth.PA] - p[synth.PA]) < 1.0), q[:, synth.PA]
+    assert np.all(c < 1e-4), c
+
+
+@pytest.mark.parametrize("jac", [0, 2])
+def test_split_and_cluster_paths_reach_the_oracle_chi2(G, jac):
+    """Noisy galaxies (5 km/s), each against its own maps: the fit on the
+    two-stage kernels and the fit on the cluster kernels both reach the
+    oracle LM's chi2 (evaluated by the oracle at each result) within 1e-4."""
+    rng = np.random.default_rng(12)
+    gals, p0 = [], []
+    for k in range(3):
+        t = synth.SINGLE_TRUTH.copy()
+        t[synth.PA] = rng.uniform(0, 180)
+        t[synth.VMAX] = rng.uniform(150, 250)
+        gals.append(galaxy(noise_v=5.0, seed=40 + k, truth=t))
+        p0.append(starts(gals[-1][1], 1, seed=50 + k)[0])
+    g = gals[0][0]
+    p0 = np.array(p0)
+    lo_l, hi_l = zip(*[bounds(gp) for _, gp, _ in gals])
+    dobs = [_dobs(G, o) for _, _, o in gals]
+    for path in (1, 3):
+        opts = G.lm_opts(max_iter=100, jacobian=jac, mode=0, free=FREE, path=path)
+        q, c, it, st = G.fit_lm(g, dobs, p0, list(lo_l), list(hi_l), opts)
+        for k, (_, gp, o) in enumerate(gals):
+            lo, hi = bounds(gp)
+            qo, co, _, _ = fit.fit_lm(ogeom(g), o, p0[k], lo, hi, FREE, max_iter=100)
+            c_at_gpu = oracle.chi2_batch(ogeom(g), q[k:k + 1], o)[0]
+            assert c_at_gpu <= co * (1 + 1e-4) + 1e-9, (path, k, c_at_gpu, co)
+
+
+def test_lm_path_choice_is_checked(G):
+    """GBK_PATH_STAGED is not an LM path (EINVAL); GBK_PATH_SPLIT on a PSF
+    wider than the split kernels are built for is refused (EUNSUPPORTED),
+    while GBK_PATH_AUTO fits it on the cluster kernels."""
+    g, p, obs = galaxy(noise_v=0.0)
+    lo, hi = bounds(p)
+    d = _dobs(G, obs)
+    with pytest.raises(G.GbkError, match="GBK_PATH_AUTO"):
+        G.gbk_fit_lm_workspace_bytes(g, 2, G.lm_opts(free=FREE, path=2))
+    wide = dataclasses.replace(g, psf_fwhm=6.0)  # PSF radius 11 > 8
+    with pytest.raises(G.GbkError, match="do not serve"):
+        G.gbk_fit_lm_workspace_bytes(wide, 2, G.lm_opts(free=FREE, path=3))
+    assert G.gbk_fit_lm_workspace_bytes(wide, 2, G.lm_opts(free=FREE)) > 0
+    m = G.eval_maps(wide, torch.from_numpy(p[None]))[0].cpu().numpy()
+    dw = G.Obs.from_numpy(m[1].astype(np.float32), m[2].astype(np.float32), obs.w_v, obs.w_s, obs.mask)
+    p0 = starts(p, 2, seed=7)
+    q, c, it, st = G.fit_lm(wide, [dw] * 2, p0, [lo] * 2, [hi] * 2,
+                            G.lm_opts(max_iter=100, jacobian=2, free=FREE))
+    assert np.all(np.isin(st, [1, 2])), st
+    assert np.all(np.abs(q[:, synth.VMAX] - p[synth.VMAX]) < 2.0)
