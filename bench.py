@@ -1048,7 +1048,7 @@ def run_reference(args):
     # The value is a rate, models per second, so the bound does not bias it;
     # the steps actually run are reported.
     budget_s = float(os.environ.get("GBK_REFERENCE_BUDGET_S", "150"))
-    warm_budget_s = 90.0
+    warm_budget_s = float(os.environ.get("GBK_REFERENCE_WARM_BUDGET_S", "90"))
     pool = synth.draw_fp_params(rng, per_step * (args.warmup + args.steps))
     warm = 0
     tw = time.perf_counter()

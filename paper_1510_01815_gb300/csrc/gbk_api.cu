@@ -183,7 +183,7 @@ gbk_status gbk_device_status(int32_t *status)
     if (!status) return fail(GBK_EINVAL, "status is NULL");
     int c = 0, c2 = 0, g = 0, w = 0, sp = 0, ts = 0;
     gbk_status s;
-    if ((s = conv_status_read(&c)) || (s = conv_pair_status_read(&c2)) || (s = gemm_status_read(&g)) ||
+    if ((s = conv_status_read(&c)) || (s = conv_fir_status_read(&c2)) || (s = gemm_status_read(&g)) ||
         (s = selfcheck_status_read(&w)) || (s = split_status_read(&sp)) || (s = tsplit_status_read(&ts)))
         return s;
     *status = ((c || c2) ? 1 : 0) | (g ? 2 : 0) | (w ? 4 : 0) | ((sp || ts) ? 8 : 0);

@@ -307,8 +307,8 @@ gbk_status launch_staged(const StagedArgs &a, bool want_moments, cudaStream_t st
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "model cube kernel launch");
     }
     if ((sm = mark(1))) return sm;
-    if (conv_pair_supported(g)) {
-        gbk_status s = launch_conv_pair(a, stream);
+    if (conv_fir_supported(g)) {
+        gbk_status s = launch_conv_fir(a, stream);
         if (s) return s;
     } else if (conv_tma_supported(g)) {
         gbk_status s = launch_conv_tma(a, stream);

@@ -38,9 +38,9 @@ cudaError_t launch_chi2_maps(int nx, int ny, int n_models, const float *maps, co
                              double *chi2, float *resid, cudaStream_t stream);
 
 gbk_status conv_status_read(int *v);
-// Packed-pair convolution for PSF radii up to 8 (k_conv_pair.cu).
-bool conv_pair_supported(const Geom &g);
-gbk_status launch_conv_pair(const StagedArgs &a, cudaStream_t stream);
-gbk_status conv_pair_status_read(int *v);
+// Register-FIR convolution for PSF and LSF radii up to 8 (k_conv_fir.cu).
+bool conv_fir_supported(const Geom &g);
+gbk_status launch_conv_fir(const StagedArgs &a, cudaStream_t stream);
+gbk_status conv_fir_status_read(int *v);
 
 }  // namespace gbk

@@ -67,14 +67,15 @@ def test_single_rank_throughput():
 
 def test_reference_arm_is_bounded_and_complete():
     """bench.py --impl reference (the FP64 oracle as the reference arm) ends
-    within its time budget whatever K and W are, and prints one JSON line
-    with the contract's keys and the steps it actually timed."""
+    within its time budgets (timed steps and warm-up) whatever K and W are,
+    and prints one JSON line with the contract's keys, the steps it actually
+    warmed and timed, and the ones requested."""
     import json
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, GBK_REFERENCE_BUDGET_S="1")
+    env = dict(os.environ, GBK_REFERENCE_BUDGET_S="1", GBK_REFERENCE_WARM_BUDGET_S="1")
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2000",
                         "--warmup", "20"], capture_output=True, text=True, timeout=600, env=env, cwd=root)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -84,5 +85,5 @@ def test_reference_arm_is_bounded_and_complete():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1
-    assert d["steps_requested"] == 2000 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["steps_requested"] == 2000 and d["warmup_requested"] == 20 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]

@@ -121,10 +121,14 @@ def test_survey_drawn_sizes(G):
 def test_survey_launch_shapes_agree(G):
     """Every launch shape of the survey evaluator -- one launch per
     cluster-size group, or one persistent launch with a work counter at
-    several cluster and block sizes -- gives the same maps bit for bit (each
-    spaxel's arithmetic does not depend on which CTA owns it) and the same
-    chi2 up to the order of its FP64 reduction; the autotuner picks one of
-    them and the survey then uses it."""
+    several cluster and block sizes -- gives the same maps to the last bits
+    and the same chi2 up to the order of its reduction; the autotuner picks
+    one of them and the survey then uses it.  A warp samples the union of
+    its spaxels' channel windows, and which spaxels share a warp depends on
+    the shape: the extra channels carry Gaussian terms below 2^-36 of the
+    peak, which can still move a sum across a rounding boundary, so maps
+    are compared to a few FP32 ulps (of the value, or of the map's scale
+    where a velocity passes through zero) rather than bit for bit."""
     rng = np.random.default_rng(4)
     gal = synth.draw_survey(rng, 40)
     geoms = [g for g, _ in gal]
@@ -152,7 +156,10 @@ def test_survey_launch_shapes_agree(G):
                 ref_maps, ref_c2 = maps, c2
                 continue
             for i in range(len(geoms)):
-                np.testing.assert_array_equal(maps[i], ref_maps[i], err_msg="shape %s galaxy %d" % ((one, cs, t), i))
+                for k in range(3):  # per map: a few ulps of the value or of the map's scale
+                    scale = float(np.abs(ref_maps[i][k]).max())
+                    np.testing.assert_allclose(maps[i][k], ref_maps[i][k], rtol=1e-6, atol=1e-8 * scale,
+                                               err_msg="shape %s galaxy %d map %d" % ((one, cs, t), i, k))
             # the spaxel terms are identical; each thread sums its share in
             # FP32 with compensation (relative error a few 2^-24 of the
             # partial) before the FP64 tree, and the share changes with the
