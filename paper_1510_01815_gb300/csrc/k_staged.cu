@@ -182,6 +182,20 @@ __device__ __forceinline__ void finish_moments(float s0, float s1, float s2, flo
     }
 }
 
+// Block sum of one FP32 value per thread: FP32 within each warp (a fixed
+// shuffle tree), the warps in FP64 in order.  Result in thread 0.
+__device__ __forceinline__ double block_sum_f32(float v, double *red)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(256) moments_kernel(StagedArgs a)
     if (threadIdx.x == 0) mc = model_const(a.params + (size_t)model * GBK_NPAR, g);
     __syncthreads();
     const ModelConst c = mc;
-    double acc = 0.0;
+    float acc = 0.f;
     if (pix < np) {
         int y = pix / g.nx, x = pix - y * g.nx;
         float vl, br;
@@ -216,7 +230,20 @@ __global__ void __launch_bounds__(256) moments_kernel(StagedArgs a)
         const float *D = a.data + (size_t)model * a.d_model_stride + pix;
         float base = g.vc - 0.5f * (float)(g.nz - 1) * g.dv - cen;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int k = 0; k < g.nz; ++k) {
+        // eight channel loads in flight per step; the sums stay in channel order
+        int k = 0;
+        for (; k + 8 <= g.nz; k += 8) {
+            float cv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cv[q] = D[(size_t)(k + q) * np];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float d = fmaf((float)(k + q), g.dv, base);
+                const float t = cv[q] * d;
+                s0 += cv[q]; s1 += t; s2 = fmaf(t, d, s2);
+            }
+        }
+        for (; k < g.nz; ++k) {
             float cv = D[(size_t)k * np];
             float d = fmaf((float)k, g.dv, base);
             float t = cv * d;
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(256) moments_kernel(StagedArgs a)
                 rv = a.obs.w_v[pix] * (m1 - a.obs.v_obs[pix]);
                 rs = a.obs.w_s[pix] * (m2 - a.obs.s_obs[pix]);
             }
-            acc = (double)(rv * rv) + (double)(rs * rs);
+            acc = rv * rv + rs * rs;
             if (a.resid) {
                 float *rp = a.resid + (size_t)model * 2 * np;
                 rp[pix] = rv; rp[np + pix] = rs;
@@ -243,7 +270,7 @@ __global__ void __launch_bounds__(256) moments_kernel(StagedArgs a)
         }
     }
     if (a.chi2) {
-        double s = block_sum(acc, red);
+        double s = block_sum_f32(acc, red);
         if (threadIdx.x == 0) a.partials[blockIdx.x] = c.valid ? s : (double)__int_as_float(0x7fc00000);
     }
 }
