@@ -302,6 +302,23 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
         float a_c = fminf(fmaxf(vl, v_lo), v_hi);
         float sh = vl - a_c;
         float base = vz0 - vl;
+        // The warp's channel window: the union of its lanes' |u| <= cut (the
+        // evaluators' rule: beyond it the Gaussian is below 2^-36 of its
+        // peak, or flushed to zero for a line centred outside the band), in
+        // whole channel pairs.
+        int e0, e1;
+        {
+            const unsigned am = __activemask();
+            const float cut = (sh != 0.f) ? kUFlush : kUCut;
+            const float inv_adv = 1.f / (c.alpha * g.dv);
+            float flo = (-cut - c.alpha * base) * inv_adv - 1.f, fhi = (cut - c.alpha * base) * inv_adv + 2.f;
+            if (!(flo > -1e6f)) flo = -1e6f;
+            if (!(fhi < 1e6f)) fhi = 1e6f;
+            e0 = __reduce_min_sync(am, (int)floorf(flo));
+            e1 = __reduce_max_sync(am, (int)ceilf(fhi));
+            e0 = max(0, e0) & ~1;
+            e1 = min(ezp, (e1 + 1) & ~1);
+        }
         // Channels in pairs (e, e + 1) on packed FP32 lanes: per pair one
         // argument, two ex2, the powers of d as a shallow tree and twelve
         // packed accumulations; an odd last channel pairs with the padding,
@@ -312,9 +329,9 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
             const f32x2 BASE = pk2(base, base), TWO = pk2(2.f, 2.f);
             f32x2 A0 = Z2, A1 = Z2, A2 = Z2, A3 = Z2, A4 = Z2, B0 = Z2, B1 = Z2, B2 = Z2, B3 = Z2, C0 = Z2, C1 = Z2,
                   C2 = Z2;
-            f32x2 FE = pk2(0.f, 1.f);
+            f32x2 FE = pk2((float)e0, (float)(e0 + 1));
 #pragma unroll 2
-            for (int e = 0; e < ezp; e += 2) {
+            for (int e = e0; e < e1; e += 2) {
                 const f32x2 D = fma2(FE, DV, BASE);
                 const f32x2 T = mul2(D, AL);
                 const f32x2 W = mul2(T, T);
