@@ -200,7 +200,7 @@ def trained(G):
             losses.append(float(net.loss))
     pred = net.predict(v[n_train:], s[n_train:], m[n_train:]).cpu().numpy()
     return {"losses": losses, "pred": pred, "truth": p[n_train:], "v": v[n_train:], "s": s[n_train:],
-            "m": m[n_train:]}
+            "m": m[n_train:], "continuum": maps[n_train:, 0].contiguous()}
 
 
 def test_training_learns(trained):
@@ -252,6 +252,33 @@ def test_seed_gain_lm(G, trained):
         res[name] = (np.mean(it), np.mean((dv < 2.0) & (dpa < 1.0)))
     assert res["seed"][0] < 0.9 * res["perturbed"][0], res
     assert res["seed"][1] >= res["perturbed"][1] - 0.03, res
+
+
+def test_seed_beats_initial_values_lm(G, trained):
+    """Gain test against the method without the network: batched LM with the
+    analytic Jacobian started from the network's predictions needs fewer
+    iterations than LM started from the Sec. 2.1.9 values measured on the
+    same maps (the moment-0 map as the continuum image), and recovers the
+    truth as often."""
+    idx = np.arange(len(trained["truth"]))
+    obs, truth, lo, hi = _held_out(G, trained, idx)
+    lo[:, synth.PA], hi[:, synth.PA] = -360.0, 720.0
+    seed = np.clip(trained["pred"][idx], lo, hi)
+    seed[:, synth.I0], seed[:, synth.H] = truth[:, synth.I0], truth[:, synth.H]
+    obs_dev, _keep = G.obs_array(obs)
+    heur = torch.empty((len(idx), synth.NPAR), dtype=torch.float64, device="cuda")
+    G.gbk_initial_guess(synth.CNN_GEOM, obs_dev, torch.from_numpy(truth).cuda(), heur, trained["continuum"])
+    heur = np.clip(heur.cpu().numpy(), lo, hi)
+    opts = G.lm_opts(max_iter=200, jacobian=G.JAC_TANGENT, free=FREE)
+    res = {}
+    for name, start in (("seed", seed), ("initial_values", heur)):
+        q, c, it, st = G.fit_lm(synth.CNN_GEOM, obs, start, lo, hi, opts)
+        dv = np.abs(q[:, synth.VMAX] - truth[:, synth.VMAX])
+        dpa = np.abs((q[:, synth.PA] - truth[:, synth.PA] + 180.0) % 360.0 - 180.0)
+        res[name] = (np.mean(it), np.mean((dv < 2.0) & (dpa < 1.0)), np.mean(np.isin(st, [1, 2])))
+    assert res["seed"][0] < 0.95 * res["initial_values"][0], res
+    assert res["seed"][1] >= res["initial_values"][1] - 0.02, res
+    assert res["seed"][2] >= res["initial_values"][2] - 0.01, res
 
 
 def test_seed_gain_nested_sampling(G, trained):
