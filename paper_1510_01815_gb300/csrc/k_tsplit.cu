@@ -51,6 +51,7 @@ constexpr int kTsTX = 32, kTsTY = 16;          // data spaxels per stage-B tile
 constexpr int kTsEnt = kTsNP * (kTsNP + 1) / 2 + kTsNP + 1;  // J^T J upper triangle, J^T v, sum r^2
 constexpr size_t kTsL2Budget = (size_t)48 << 20;
 constexpr size_t kTsSmemA = (size_t)100 * 1024;  // shared-memory target of a stage-A CTA
+constexpr int kTsplitMaxRA = 12;               // most extended rows per stage-A CTA
 constexpr long kTsWaitLimit = 1L << 18;        // tries: about one second
 
 __device__ int g_tsplit_status;  // 0 = fine; 1 = a tile's TMA load did not complete in time
@@ -278,13 +279,16 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
     }
     __syncthreads();
 
-    // phase 2: x pass; task (row, outputs 4 gx .. 4 gx + 3), one triplet at a time
+    // phase 2: x pass; task (triplet, row, outputs 4 gx .. 4 gx + 3), the
+    // triplet slowest so that consecutive threads write consecutive outputs
     const int ngx = (g.nx + 3) / 4;
     const size_t pstride = (size_t)g.ey * a.nxp;  // floats per plane
     float *const P0 = a.pl + (size_t)model * kTsPlanes * pstride + (size_t)row0 * a.nxp;
     const float *const QA = sm + 3 * kTsNT * NPL;
-    for (int t = tid; t < nrows * ngx; t += kTsThreads) {
-        const int rr = t / ngx, gx = 4 * (t - rr * ngx);
+    const int ntask = nrows * ngx;
+    for (int t = tid; t < ntask * kTsNT; t += kTsThreads) {
+        const int tr = t / ntask, tk = t - tr * ntask;
+        const int rr = tk / ngx, gx = 4 * (tk - rr * ngx);
         const int ro = rr * PA + gx;
         float av[4 * NC4], cen[4];
 #pragma unroll
@@ -295,8 +299,7 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
 #pragma unroll
         for (int o = 0; o < 4; ++o) cen[o] = av[o + R];
         float *const out = P0 + (size_t)rr * a.nxp + gx;
-#pragma unroll 1
-        for (int tr = 0; tr < kTsNT; ++tr) {
+        {
             const float *Q0 = sm + (3 * tr) * NPL, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
             float s[4][3];
 #pragma unroll
@@ -328,7 +331,9 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
                             fmaf(-cen[2], s[2][0], s[2][1]), fmaf(-cen[3], s[3][0], s[3][1]));
             *reinterpret_cast<float4 *>(p + 2 * pstride) = make_float4(s[0][2], s[1][2], s[2][2], s[3][2]);
         }
-        *reinterpret_cast<float4 *>(out + (size_t)(3 * kTsNT) * pstride) = make_float4(cen[0], cen[1], cen[2], cen[3]);
+        if (tr == 0)
+            *reinterpret_cast<float4 *>(out + (size_t)(3 * kTsNT) * pstride) =
+                make_float4(cen[0], cen[1], cen[2], cen[3]);
     }
 }
 
@@ -550,8 +555,21 @@ static TsLayout ts_layout(const Geom &g, int n_models)
     TsLayout L = {};
     L.nxp = (g.nx + 3) & ~3;
     L.ezp = ts_ezp(g);
-    L.ra = 8;
-    while (L.ra > 1 && ts_smem_a(g, L.ra) > kTsSmemA) --L.ra;
+    // rows per stage-A CTA: within the shared-memory target, the count whose
+    // extended spaxels fill the most of whole rounds of the CTA's threads
+    // (the larger on a tie)
+    int ra_max = kTsplitMaxRA;
+    while (ra_max > 1 && ts_smem_a(g, ra_max) > kTsSmemA) --ra_max;
+    L.ra = ra_max;
+    double best = 0.0;
+    for (int ra = ra_max; ra >= 1; --ra) {
+        const int nsp = ra * g.ex, rounds = (nsp + kTsThreads - 1) / kTsThreads;
+        const double use = (double)nsp / (double)(rounds * kTsThreads);
+        if (use > best + 1e-9) {
+            best = use;
+            L.ra = ra;
+        }
+    }
     const size_t plb = (size_t)kTsPlanes * g.ey * L.nxp * sizeof(float);
     size_t chunk = kTsL2Budget / plb;
     if (chunk < 1) chunk = 1;
