@@ -48,7 +48,7 @@
 namespace gbk {
 
 constexpr int kSplitThreads = 256;
-constexpr int kSplitRA = 8;                          // extended rows per stage-A CTA
+constexpr int kSplitMaxRA = 12;                      // most extended rows per stage-A CTA
 constexpr int kSplitTX = 64, kSplitTY = 32;          // data spaxels per stage-B tile
 constexpr size_t kSplitL2Budget = (size_t)48 << 20;  // buffer bytes per chunk
 constexpr int kSplitMaxEx = 1024;                    // widest extended row served
@@ -81,6 +81,7 @@ struct SplitArgs {
     double *part;            // [n_models][tiles] chi2 parts of the tiles
     unsigned *arrived;       // [n_models] tiles done (zero at the start, reset by the last)
     int nxp;                 // plane row pitch (floats)
+    int ra;                  // extended rows per stage-A CTA
     int tiles_x, tiles;
 };
 
@@ -115,9 +116,9 @@ __global__ void __launch_bounds__(kSplitThreads, 4) split_line_kernel(SplitArgs 
     const Geom &g = a.g;
     const int tid = threadIdx.x, model = blockIdx.y;
     if (a.skip && a.skip[(a.m0 + model) / a.mpg] != 0) return;  // the whole CTA
-    const int row0 = blockIdx.x * kSplitRA, nrows = min(kSplitRA, g.ey - row0);
+    const int row0 = blockIdx.x * a.ra, nrows = min(a.ra, g.ey - row0);
     const int PA = split_rowpitch_a(g.ex);        // floats per plane row
-    const int NPL = kSplitRA * PA;
+    const int NPL = a.ra * PA;
     float *const Q0 = sm, *const Q1 = sm + NPL, *const Q2 = sm + 2 * NPL, *const QA = sm + 3 * NPL;
     const int etl = edge_table_len(g);
     float *const eG0 = sm + 4 * NPL, *const eA1 = eG0 + etl, *const eA2 = eA1 + etl;
@@ -395,9 +396,32 @@ static SplitLayout split_layout(const Geom &g, int n_models)
     return L;
 }
 
-static size_t split_smem_a(const Geom &g)
+static size_t split_smem_a(const Geom &g, int ra)
 {
-    return (size_t)(4 * kSplitRA * split_rowpitch_a(g.ex) + 3 * edge_table_len(g)) * sizeof(float);
+    return (size_t)(4 * ra * split_rowpitch_a(g.ex) + 3 * edge_table_len(g)) * sizeof(float);
+}
+
+// Extended rows per stage-A CTA: the count (up to kSplitMaxRA, within a
+// shared-memory target that keeps four CTAs per SM) with the least cost per
+// row, counting whole rounds of the CTA's threads in the line sums (about
+// 580 warp instructions a round) and in the x pass (about 330); the larger
+// count on a tie.
+static int split_rows_a(const Geom &g)
+{
+    const int ngx = (g.nx + 3) / 4;
+    int best_ra = 1;
+    double best = 1e30;
+    for (int ra = 1; ra <= kSplitMaxRA; ++ra) {
+        if (ra > 1 && split_smem_a(g, ra) > (size_t)56 * 1024) break;
+        const int r1 = (ra * g.ex + kSplitThreads - 1) / kSplitThreads;
+        const int r2 = (ra * ngx + kSplitThreads - 1) / kSplitThreads;
+        const double cost = (580.0 * r1 + 330.0 * r2) / ra;
+        if (cost <= best * (1.0 + 1e-9)) {
+            best = cost;
+            best_ra = ra;
+        }
+    }
+    return best_ra;
 }
 
 static size_t split_smem_b(int R) { return 128 + (size_t)4 * (kSplitTY + 2 * R) * kSplitTX * sizeof(float); }
@@ -405,7 +429,7 @@ static size_t split_smem_b(int R) { return 128 + (size_t)4 * (kSplitTY + 2 * R) 
 bool split_supported(const Geom &g)
 {
     return g.model == GBK_MODEL_CUBE && g.u == 1 && g.R <= kSplitMaxR && g.ex <= kSplitMaxEx &&
-           split_smem_a(g) <= 200 * 1024;
+           split_smem_a(g, 1) <= 200 * 1024;
 }
 
 size_t split_workspace_bytes(const Geom &g, int n_models)
@@ -427,14 +451,14 @@ template <int R>
 static gbk_status launch_stages(const CUtensorMap &tm, const SplitArgs &a, cudaStream_t st, SplitTimer *timer)
 {
     static KernelAttrMemo memo_a, memo_b;
-    const size_t sa = split_smem_a(a.g), sb = split_smem_b(R);
+    const size_t sa = split_smem_a(a.g, a.ra), sb = split_smem_b(R);
     gbk_status s;
     if ((s = ensure_kernel_attrs((const void *)split_line_kernel<R>, sa, false, memo_a,
                                  "split evaluator: setting the line stage's shared memory")) ||
         (s = ensure_kernel_attrs((const void *)split_psf_kernel<R>, sb, false, memo_b,
                                  "split evaluator: setting the PSF stage's shared memory")))
         return s;
-    const unsigned blocks_a = (unsigned)((a.g.ey + kSplitRA - 1) / kSplitRA);
+    const unsigned blocks_a = (unsigned)((a.g.ey + a.ra - 1) / a.ra);
     split_line_kernel<R><<<dim3(blocks_a, (unsigned)a.n_models), kSplitThreads, sa, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "split evaluator: line stage launch");
@@ -455,6 +479,7 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
     if (!split_supported(g)) return fail(GBK_EUNSUPPORTED, "the split evaluator does not serve this geometry");
     if (n == 0) return GBK_OK;
     const SplitLayout L = split_layout(g, n);
+    const int ra = split_rows_a(g);
     if (!ws || ws_bytes < L.total)
         return fail(GBK_EWORKSPACE, "the split evaluator needs %zu bytes of workspace (got %zu)", L.total, ws_bytes);
     char *base = (char *)ws;
@@ -502,6 +527,7 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
         a.part = (double *)(base + L.part_off);
         a.arrived = (unsigned *)(base + L.arr_off);
         a.nxp = L.nxp;
+        a.ra = ra;
         a.tiles_x = L.tiles_x;
         a.tiles = L.tiles;
         gbk_status s;
