@@ -4,20 +4,26 @@
 //   D[m][n] = alpha * sum_k A[m][k] * B[n][k]  (+ bias[n]) (ReLU) (* [mask[m][n] > 0])
 //
 // A [M][K] and B [N][K] are BF16, row-major (both "K-major"); D is written as
-// BF16 and/or FP32 with leading dimension ldo.  One CTA of 128 threads owns a
-// 128 x BN output tile (BN = 16..256, a multiple of 16; 256 when N allows):
+// BF16 and/or FP32 with leading dimension ldo.  The output is cut into
+// 128 x BN tiles (BN = 16..256, a multiple of 16; 256 when N allows), and a
+// persistent grid of one CTA per SM (at most) walks them in a grouped order;
+// each CTA of 192 threads is warp-specialised:
 //   - warp 0 lane 0 streams 64-wide K slabs of A and B with TMA
-//     (cp.async.bulk.tensor.2d, 128-byte swizzle) into a 4-stage ring,
-//     completion counted on "full" mbarriers;
+//     (cp.async.bulk.tensor.2d, 128-byte swizzle) into a 4-stage ring shared
+//     by all of the CTA's tiles, completion counted on "full" mbarriers;
 //   - warp 1 lane 0 issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate,
-//     M = 128, N = BN, K = 16 per instruction, four per slab) with the
-//     accumulator in tensor memory, and releases each slab with
-//     tcgen05.commit onto its "empty" mbarrier;
-//   - after the last slab a commit onto the "accumulator" mbarrier lets all
-//     four warps read their 32 TMEM lanes (= tile rows) with tcgen05.ld and
-//     apply the epilogue.
-// Every wait is bounded: a CTA that gives up records a status in
-// g_gemm_status, still frees its tensor memory and returns.
+//     M = 128, N = BN, K = 16 per instruction, four per slab) into one of two
+//     accumulators in tensor memory, releases each slab with tcgen05.commit
+//     onto its "empty" mbarrier and, after a tile's last slab, commits onto
+//     that accumulator's "full" mbarrier;
+//   - warps 2-5 read the accumulator's 128 TMEM lanes (each warp its quarter)
+//     with tcgen05.ld, apply the epilogue, store, and hand the accumulator
+//     back on its "empty" mbarrier -- so a tile's epilogue overlaps the next
+//     tile's loads and MMAs.
+// Every wait is bounded: a thread that gives up records a status in
+// g_gemm_status and raises a CTA-wide abort flag that every other wait
+// checks, the roles leave their loops, and the CTA still frees its tensor
+// memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -28,7 +34,7 @@
 
 namespace gbk {
 
-constexpr int kGBM = 128, kGBK = 64, kGStages = 4, kGThreads = 128, kGGroup = 16;
+constexpr int kGBM = 128, kGBK = 64, kGStages = 4, kGThreads = 192, kGGroup = 16;
 // Bounded waits: 2^18 try_wait attempts, about one second (a try that finds
 // its phase incomplete suspends about 3.75 us on GB300, as gbk_wait_selfcheck
 // measures); a TMA load or an MMA stage completes in microseconds.
@@ -55,6 +61,50 @@ __device__ __forceinline__ bool g_mbar_wait(uint64_t *bar, uint32_t phase)
         if (done) return true;
     }
     return false;
+}
+
+// Bounded wait that gives up early once another role of the CTA has raised
+// `abort`; on its own timeout it raises it and records the status.
+__device__ __forceinline__ bool g_mbar_wait_abortable(uint64_t *bar, uint32_t phase, volatile int *abort)
+{
+    for (long it = 0; it < kGWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(g_smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    atomicExch(&g_gemm_status, 1);
+    return false;
+}
+
+// One unit of work: an output tile (and, with split-K, a K range).
+struct GTile {
+    int m0, n0, z, kt0, KT;
+};
+
+__device__ __forceinline__ GTile gemm_unit(const GemmArgs &a, int u, int tiles_m, int tiles_n, int KT_all)
+{
+    GTile t;
+    const int tiles = tiles_m * tiles_n;
+    t.z = u / tiles;
+    const int tt = u - t.z * tiles;
+    // grouped order: groups of kGGroup M-tiles with the N-tiles fastest
+    // inside a group, so the tiles in flight at one time share their A and
+    // B strips in L2
+    const int per_group = kGGroup * tiles_n;
+    const int grp = tt / per_group, in_grp = tt - grp * per_group;
+    const int gm = min(kGGroup, tiles_m - grp * kGGroup);
+    const int tm = grp * kGGroup + in_grp % gm, tn = in_grp / gm;
+    t.m0 = tm * kGBM;
+    t.n0 = tn * a.bn;
+    t.kt0 = a.kt_split > 0 ? t.z * a.kt_split : 0;
+    t.KT = a.kt_split > 0 ? min(a.kt_split, KT_all - t.kt0) : KT_all;
+    return t;
 }
 
 __device__ __forceinline__ void g_tma_2d(const CUtensorMap *tmap, void *dst, uint64_t *bar, int x, int y)
@@ -90,35 +140,93 @@ __host__ __device__ __forceinline__ uint32_t idesc_bf16_f32(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Epilogue of 16 accumulator columns of row m (columns nb .. nb + 15).
+__device__ __forceinline__ void gemm_epilogue16(const GemmArgs &a, float *out_f32, int m, int nb, const uint32_t *r,
+                                                bool vec_bf, bool vec_f)
+{
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int n = nb + j;
+        float x = a.alpha * __uint_as_float(r[j]);
+        if (n < a.N) {
+            if (a.bias) x += a.bias[n];
+            if (a.relu) x = fmaxf(x, 0.f);
+            if (a.mask && !(__bfloat162float(a.mask[(size_t)m * a.ldm + n]) > 0.f)) x = 0.f;
+        }
+        v[j] = x;
+    }
+    const size_t o = (size_t)m * a.ldo + nb;
+    const bool full_chunk = nb + 16 <= a.N;
+    if (out_f32) {
+        if (full_chunk && vec_f) {
+            float4 *q = reinterpret_cast<float4 *>(out_f32 + o);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (nb + j < a.N) out_f32[o + j] = v[j];
+        }
+    }
+    if (a.out_t) {
+        if (a.t_mode == 1) {
+            const int q = 1 << a.t_log2;
+            const size_t rowb = (size_t)(m & (q - 1)) * a.N, col = (size_t)(m >> a.t_log2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (nb + j < a.N) a.out_t[(rowb + nb + j) * a.ldt + col] = __float2bfloat16_rn(v[j]);
+        } else {
+            const int c = 1 << a.t_log2;
+            const size_t colb = (size_t)m * (a.N >> a.t_log2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = nb + j;
+                if (n < a.N) a.out_t[(size_t)(n & (c - 1)) * a.ldt + colb + (n >> a.t_log2)] = __float2bfloat16_rn(v[j]);
+            }
+        }
+    }
+    if (a.out_bf16) {
+        if (full_chunk && vec_bf) {
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                w[j] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            uint4 *q = reinterpret_cast<uint4 *>(a.out_bf16 + o);
+            q[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            q[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (nb + j < a.N) a.out_bf16[o + j] = __float2bfloat16_rn(v[j]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kGThreads, 1)
-    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs a)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs a,
+                     int units)
 {
     const int BN = a.bn;
-    // Grouped tile order: blockIdx.x runs over groups of kGGroup M-tiles with
-    // the N-tiles fastest inside a group, so the CTAs resident at one time
-    // share their A and B strips in L2.
     const int tiles_m = (a.M + kGBM - 1) / kGBM, tiles_n = (a.N + BN - 1) / BN;
-    const int per_group = kGGroup * tiles_n;
-    const int grp = blockIdx.x / per_group, in_grp = blockIdx.x - grp * per_group;
-    const int gm = min(kGGroup, tiles_m - grp * kGGroup);
-    const int tm = grp * kGGroup + in_grp % gm, tn = in_grp / gm;
-    const int m0 = tm * kGBM, n0 = tn * BN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KT_all = (a.K + kGBK - 1) / kGBK;
-    const int kt0 = a.kt_split > 0 ? blockIdx.z * a.kt_split : 0;
-    const int KT = a.kt_split > 0 ? min(a.kt_split, KT_all - kt0) : KT_all;
-    float *const out_f32 = a.out_f32 ? a.out_f32 + (size_t)blockIdx.z * a.split_stride : nullptr;
     const uint32_t bytesA = kGBM * kGBK * 2, bytesB = (uint32_t)BN * kGBK * 2;
 
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     // 128-byte swizzled tiles must start on 1024-byte boundaries
     unsigned char *gsm = gsm_raw + ((1024u - (g_smem_u32(gsm_raw) & 1023u)) & 1023u);
-    unsigned char *sA = gsm;                                 // [stages][128][64] bf16
-    unsigned char *sB = gsm + kGStages * bytesA;             // [stages][BN][64] bf16
-    __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], accum;
+    unsigned char *sA = gsm;                      // [stages][128][64] bf16
+    unsigned char *sB = gsm + kGStages * bytesA;  // [stages][BN][64] bf16
+    __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    volatile int *abort = &s_abort;
 
-    const uint32_t ncols = BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
+    // two accumulators of nbuf columns each
+    const uint32_t nbuf = BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u)), ncols = 2 * nbuf;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(g_smem_u32(&s_tmem)),
                      "r"(ncols)
@@ -130,7 +238,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
             g_mbar_init(&full[s], 1);
             g_mbar_init(&empty[s], 1);
         }
-        g_mbar_init(&accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            g_mbar_init(&acc_full[b], 1);   // one tcgen05.commit per tile
+            g_mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
+        s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -138,134 +250,109 @@ __global__ void __launch_bounds__(kGThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    if (warp == 0 && lane == 0) {
-        // producer
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % kGStages;
-            const uint32_t ph = (uint32_t)((kt / kGStages) & 1);
-            if (kt >= kGStages && !g_mbar_wait(&empty[s], ph ^ 1u)) {
-                atomicExch(&g_gemm_status, 1);
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: one ring of slabs across all of the CTA's tiles
+            uint32_t slab = 0;
+            bool go = true;
+            for (int u = blockIdx.x; u < units && go; u += gridDim.x) {
+                const GTile t = gemm_unit(a, u, tiles_m, tiles_n, KT_all);
+                for (int kt = 0; kt < t.KT; ++kt, ++slab) {
+                    const int s = (int)(slab % kGStages);
+                    const uint32_t ph = (slab / kGStages) & 1u;
+                    if (slab >= (uint32_t)kGStages && !g_mbar_wait_abortable(&empty[s], ph ^ 1u, abort)) {
+                        go = false;
+                        break;
+                    }
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(g_smem_u32(&full[s])),
+                                 "r"(bytesA + bytesB)
+                                 : "memory");
+                    g_tma_2d(&tmA, sA + (size_t)s * bytesA, &full[s], (t.kt0 + kt) * kGBK, t.m0);
+                    g_tma_2d(&tmB, sB + (size_t)s * bytesB, &full[s], (t.kt0 + kt) * kGBK, t.n0);
+                }
             }
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(g_smem_u32(&full[s])),
-                         "r"(bytesA + bytesB)
-                         : "memory");
-            g_tma_2d(&tmA, sA + (size_t)s * bytesA, &full[s], (kt0 + kt) * kGBK, m0);
-            g_tma_2d(&tmB, sB + (size_t)s * bytesB, &full[s], (kt0 + kt) * kGBK, n0);
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        const uint32_t idesc = idesc_bf16_f32(kGBM, BN);
-        bool ok = true;
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % kGStages;
-            const uint32_t ph = (uint32_t)((kt / kGStages) & 1);
-            if (!g_mbar_wait(&full[s], ph)) {
-                ok = false;
-                atomicExch(&g_gemm_status, 1);
-                break;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: tile i accumulates into buffer i % 2
+            const uint32_t idesc = idesc_bf16_f32(kGBM, BN);
+            uint32_t slab = 0;
+            bool go = true;
+            int i = 0;
+            for (int u = blockIdx.x; u < units && go; u += gridDim.x, ++i) {
+                const GTile t = gemm_unit(a, u, tiles_m, tiles_n, KT_all);
+                const int buf = i & 1;
+                const uint32_t use = (uint32_t)(i >> 1);
+                // the epilogue must have read this buffer's previous tile
+                if (use > 0 && !g_mbar_wait_abortable(&acc_empty[buf], (use - 1) & 1u, abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dtm = tmem + (uint32_t)buf * nbuf;
+                for (int kt = 0; kt < t.KT; ++kt, ++slab) {
+                    const int s = (int)(slab % kGStages);
+                    const uint32_t ph = (slab / kGStages) & 1u;
+                    if (!g_mbar_wait_abortable(&full[s], ph, abort)) {
+                        go = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t da = smem_desc_k128(g_smem_u32(sA + (size_t)s * bytesA));
+                    const uint64_t db = smem_desc_k128(g_smem_u32(sB + (size_t)s * bytesB));
+#pragma unroll
+                    for (int kk = 0; kk < kGBK / 16; ++kk) {
+                        // advance 16 elements (32 B) along K inside the swizzle atom
+                        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+                            "l"(da + (uint64_t)(2 * kk)), "l"(db + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     g_smem_u32(&empty[s]))
+                                 : "memory");
+                }
+                if (!go) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 g_smem_u32(&acc_full[buf]))
+                             : "memory");
             }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows)
+        const int q = warp & 3;
+        float *const out_f32_base = a.out_f32;
+        // 16-byte vector stores need 16-byte aligned rows and base pointers
+        const bool vec_bf = a.out_bf16 && (a.ldo % 8) == 0 && ((uintptr_t)a.out_bf16 % 16) == 0;
+        const bool vec_f = a.out_f32 && (a.ldo % 4) == 0 && ((uintptr_t)a.out_f32 % 16) == 0 && (a.split_stride % 4) == 0;
+        int i = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++i) {
+            const GTile t = gemm_unit(a, u, tiles_m, tiles_n, KT_all);
+            const int buf = i & 1;
+            const uint32_t use = (uint32_t)(i >> 1);
+            // the loads below are warp-collective: one decision per warp
+            const bool have = __all_sync(0xffffffffu, g_mbar_wait_abortable(&acc_full[buf], use & 1u, abort));
+            if (!have) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t da = smem_desc_k128(g_smem_u32(sA + (size_t)s * bytesA));
-            const uint64_t db = smem_desc_k128(g_smem_u32(sB + (size_t)s * bytesB));
-#pragma unroll
-            for (int kk = 0; kk < kGBK / 16; ++kk) {
-                // advance 16 elements (32 B) along K inside the swizzle atom
-                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            const int m = t.m0 + q * 32 + lane;
+            float *const out_f32 = out_f32_base ? out_f32_base + (size_t)t.z * a.split_stride : nullptr;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * nbuf + (uint32_t)c0;
                 asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(da + (uint64_t)(2 * kk)), "l"(db + (uint64_t)(2 * kk)), "r"(idesc), "r"(acc)
-                    : "memory");
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (m < a.M) gemm_epilogue16(a, out_f32, m, t.n0 + c0, r, vec_bf, vec_f);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             g_smem_u32(&empty[s]))
-                         : "memory");
-        }
-        if (ok)
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             g_smem_u32(&accum))
-                         : "memory");
-    }
-    __syncwarp();
-
-    // epilogue: warp w holds tile rows 32 w .. 32 w + 31 in TMEM lanes; the
-    // loads below are warp-collective, so the decision to read is made per warp
-    bool have = g_mbar_wait(&accum, 0);
-    have = __all_sync(0xffffffffu, have);
-    if (!have && lane == 0) atomicExch(&g_gemm_status, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int m = m0 + warp * 32 + lane;
-    // 16-byte vector stores need 16-byte aligned rows and base pointers
-    const bool vec_bf = a.out_bf16 && (a.ldo % 8) == 0 && ((uintptr_t)a.out_bf16 % 16) == 0;
-    const bool vec_f = out_f32 && (a.ldo % 4) == 0 && ((uintptr_t)out_f32 % 16) == 0 && (a.split_stride % 4) == 0;
-    if (have) {
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m >= a.M) continue;
-            const int nb = n0 + c0;
-            float v[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int n = nb + j;
-                float x = a.alpha * __uint_as_float(r[j]);
-                if (n < a.N) {
-                    if (a.bias) x += a.bias[n];
-                    if (a.relu) x = fmaxf(x, 0.f);
-                    if (a.mask && !(__bfloat162float(a.mask[(size_t)m * a.ldm + n]) > 0.f)) x = 0.f;
-                }
-                v[j] = x;
-            }
-            const size_t o = (size_t)m * a.ldo + nb;
-            const bool full_chunk = nb + 16 <= a.N;
-            if (out_f32) {
-                if (full_chunk && vec_f) {
-                    float4 *q = reinterpret_cast<float4 *>(out_f32 + o);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) q[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                } else {
-                    for (int j = 0; j < 16 && nb + j < a.N; ++j) out_f32[o + j] = v[j];
-                }
-            }
-            if (a.out_t) {
-                if (a.t_mode == 1) {
-                    const int q = 1 << a.t_log2;
-                    const size_t rowb = (size_t)(m & (q - 1)) * a.N, col = (size_t)(m >> a.t_log2);
-                    for (int j = 0; j < 16 && nb + j < a.N; ++j)
-                        a.out_t[(rowb + nb + j) * a.ldt + col] = __float2bfloat16_rn(v[j]);
-                } else {
-                    const int c = 1 << a.t_log2;
-                    const size_t colb = (size_t)m * (a.N >> a.t_log2);
-                    for (int j = 0; j < 16 && nb + j < a.N; ++j) {
-                        const int n = nb + j;
-                        a.out_t[(size_t)(n & (c - 1)) * a.ldt + colb + (n >> a.t_log2)] = __float2bfloat16_rn(v[j]);
-                    }
-                }
-            }
-            if (a.out_bf16) {
-                if (full_chunk && vec_bf) {
-                    uint32_t w[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        w[j] = *reinterpret_cast<uint32_t *>(&h);
-                    }
-                    uint4 *q = reinterpret_cast<uint4 *>(a.out_bf16 + o);
-                    q[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                    q[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                } else {
-                    for (int j = 0; j < 16 && nb + j < a.N; ++j) a.out_bf16[o + j] = __float2bfloat16_rn(v[j]);
-                }
-            }
+            // hand the buffer back to the MMA issuer
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(g_smem_u32(&acc_empty[buf])) : "memory");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -347,11 +434,24 @@ gbk_status launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, cons
         if (a.t_mode == 1 && (a.M & ((1 << a.t_log2) - 1))) return fail(GBK_EINVAL, "M must be a multiple of q");
         if (a.t_mode == 2 && (a.N & ((1 << a.t_log2) - 1))) return fail(GBK_EINVAL, "N must be a multiple of c");
     }
-    const long tiles = (long)((a.M + kGBM - 1) / kGBM) * ((a.N + a.bn - 1) / a.bn);
-    if (tiles > 0x7fffffffL) return fail(GBK_EINVAL, "GEMM too large");
-    dim3 grid((unsigned)tiles, 1, splits);
-    gemm_bf16_kernel<<<grid, kGThreads, smem, st>>>(ta, tb, a);
-    cudaError_t e = cudaGetLastError();
+    const long units = (long)((a.M + kGBM - 1) / kGBM) * ((a.N + a.bn - 1) / a.bn) * splits;
+    if (units > 0x7fffffffL) return fail(GBK_EINVAL, "GEMM too large");
+    // persistent grid: at most one CTA per SM, each walking units
+    // blockIdx.x, blockIdx.x + gridDim.x, ...
+    static int sm_count[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "GEMM: current device");
+    if (dev < 0 || dev >= 64) return fail(GBK_EUNSUPPORTED, "GEMM: device index %d", dev);
+    if (sm_count[dev] == 0) {
+        int n = 0;
+        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e, "GEMM: SM count");
+        sm_count[dev] = n > 0 ? n : 1;
+    }
+    const int grid = (int)std::min<long>(units, sm_count[dev]);
+    gemm_bf16_kernel<<<grid, kGThreads, smem, st>>>(ta, tb, a, (int)units);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "GEMM launch");
     return GBK_OK;
 }

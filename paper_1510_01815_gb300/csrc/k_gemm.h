@@ -26,8 +26,8 @@ struct GemmArgs {
     // (q = 2^t_log2, c = 2^t_log2; q = 1 or c = N is the plain transpose).
     __nv_bfloat16 *out_t;
     int ldt, t_mode, t_log2;
-    // Split-K: blockIdx.z sums K tiles [z kt_split, (z+1) kt_split) into the
-    // FP32 slice out_f32 + z * split_stride (0: no split).
+    // Split-K: unit z of a tile sums K tiles [z kt_split, (z+1) kt_split) into
+    // the FP32 slice out_f32 + z * split_stride (0: no split).
     int kt_split;
     size_t split_stride;
 };
