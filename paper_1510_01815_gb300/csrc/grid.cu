@@ -1,6 +1,7 @@
 // grid.cu -- gbk_grid: the nested-grids optimiser of Sec. 2.3.3 of Bekiaris
 // et al. 2015.  Every node of a regular grid over the free parameters is
-// evaluated (batched fused chi2), the best node is selected, and a new grid
+// evaluated (batched chi2: the split evaluator where it serves the geometry,
+// else the cluster one), the best node is selected, and a new grid
 // with the same number of nodes is built around it over a smaller volume.
 //
 // Readings: level 0 spans [lo, hi] with n_j nodes per parameter including
@@ -14,6 +15,7 @@
 
 #include "gbk_api_internal.h"
 #include "k_fused.h"
+#include "k_split.h"
 
 namespace gbk {
 
@@ -86,10 +88,12 @@ __global__ void grid_argmin_kernel(const double *chi2, long long first, int coun
 static size_t al256g(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct GridLayout {
-    size_t params, chi2, bc, bi, total;
+    size_t params, chi2, bc, bi, split, split_bytes, total;
 };
 
-static GridLayout grid_layout(int chunk, long long nchunks)
+// split_bytes: the split evaluator's workspace for a chunk (0 where it does
+// not serve the geometry; the cluster evaluator then takes the chunks).
+static GridLayout grid_layout(int chunk, long long nchunks, size_t split_bytes)
 {
     GridLayout L;
     size_t o = 0;
@@ -97,8 +101,15 @@ static GridLayout grid_layout(int chunk, long long nchunks)
     L.chi2 = o; o += al256g(sizeof(double) * chunk);
     L.bc = o; o += al256g(sizeof(double) * nchunks);
     L.bi = o; o += al256g(sizeof(long long) * nchunks);
+    L.split = o; o += al256g(split_bytes);
+    L.split_bytes = split_bytes;
     L.total = o;
     return L;
+}
+
+static size_t grid_split_bytes(const Geom &g, int chunk)
+{
+    return split_supported(g) ? split_workspace_bytes(g, chunk) : 0;
 }
 
 static gbk_status grid_plan(const int32_t *nodes, int32_t chunk, GridSpec *s, long long *total)
@@ -137,7 +148,7 @@ size_t gbk_grid_workspace_bytes(const gbk_geom *gin, const int32_t *nodes, int32
     long long N;
     if (grid_plan(nodes, chunk, &s, &N)) return 0;
     long long nch = (N + chunk - 1) / chunk;
-    return grid_layout(chunk, nch).total;
+    return grid_layout(chunk, nch, grid_split_bytes(g, chunk)).total;
 }
 
 gbk_status gbk_grid(const gbk_geom *gin, const gbk_obs *obs, const double *lo, const double *hi,
@@ -162,7 +173,7 @@ gbk_status gbk_grid(const gbk_geom *gin, const gbk_obs *obs, const double *lo, c
     if (g.u != 1 || !fused_config(g, &fc)) return fail(GBK_EUNSUPPORTED, "the grid search uses the fused path");
     if ((s = check_obs(obs))) return s;
     long long nch = (N + chunk - 1) / chunk;
-    GridLayout L = grid_layout(chunk, nch);
+    GridLayout L = grid_layout(chunk, nch, grid_split_bytes(g, chunk));
     if (!workspace || ws_bytes < L.total)
         return fail(GBK_EWORKSPACE, "gbk_grid needs %zu bytes of workspace (got %zu)", L.total, ws_bytes);
     if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
@@ -189,17 +200,23 @@ gbk_status gbk_grid(const gbk_geom *gin, const gbk_obs *obs, const double *lo, c
             long long first = c * chunk;
             int count = (int)((N - first) < chunk ? (N - first) : chunk);
             grid_nodes_kernel<<<(count + 127) / 128, 128, 0, st>>>(spec, first, count, d_params);
-            FusedArgs a = {};
-            a.g = g;
-            a.n_models = count;
-            a.params = d_params;
-            a.obs = *obs;
-            a.chi2 = d_chi2;
-            a.cs = fc.cs;
-            a.band = fc.band;
-            a.threads = fc.threads;
-            a.persistent = fc.persistent;
-            if ((s = launch_fused(a, st))) return s;
+            if (L.split_bytes) {
+                if ((s = launch_split(g, count, d_params, obs, nullptr, d_chi2, nullptr, ws + L.split, L.split_bytes,
+                                      st)))
+                    return s;
+            } else {
+                FusedArgs a = {};
+                a.g = g;
+                a.n_models = count;
+                a.params = d_params;
+                a.obs = *obs;
+                a.chi2 = d_chi2;
+                a.cs = fc.cs;
+                a.band = fc.band;
+                a.threads = fc.threads;
+                a.persistent = fc.persistent;
+                if ((s = launch_fused(a, st))) return s;
+            }
             grid_argmin_kernel<<<1, 256, 0, st>>>(d_chi2, first, count, d_bc, d_bi, (int)c);
         }
         cudaError_t e = cudaGetLastError();

@@ -1,6 +1,7 @@
 // ns.cu -- gbk_nested_sample: nested sampling (Sec. 2.3.2 of Bekiaris et al.
 // 2015, which used MultiNest) with the likelihoods of each iteration's
-// proposals evaluated in one batched fused launch.
+// proposals evaluated in one batched launch (the split evaluator where it
+// serves the geometry, else the cluster one).
 //
 // Readings (MultiNest's ellipsoidal clustering and importance weighting are
 // not reproduced; the vanilla algorithm of Skilling 2004 with an ellipsoidal
@@ -26,6 +27,7 @@
 
 #include "gbk_api_internal.h"
 #include "k_fused.h"
+#include "k_split.h"
 
 namespace gbk {
 
@@ -56,15 +58,20 @@ static double logaddexp(double a, double b)
 }
 
 struct NsLayout {
-    size_t params, chi2, total;
+    size_t params, chi2, split, split_bytes, total;
 };
 
-static NsLayout ns_layout(int rows)
+// The batch's parameters and chi2, then the split evaluator's workspace for
+// a batch (0 where it does not serve the geometry: the cluster evaluator then
+// takes the batches).
+static NsLayout ns_layout(const Geom &g, int rows)
 {
     NsLayout L;
     L.params = 0;
     L.chi2 = ((size_t)rows * GBK_NPAR * sizeof(double) + 255) & ~(size_t)255;
-    L.total = L.chi2 + (((size_t)rows * sizeof(double) + 255) & ~(size_t)255);
+    L.split = L.chi2 + (((size_t)rows * sizeof(double) + 255) & ~(size_t)255);
+    L.split_bytes = split_supported(g) ? split_workspace_bytes(g, rows) : 0;
+    L.total = L.split + ((L.split_bytes + 255) & ~(size_t)255);
     return L;
 }
 
@@ -89,7 +96,7 @@ size_t gbk_nested_sample_workspace_bytes(const gbk_geom *gin, const gbk_ns_opts 
     ok();
     Geom g;
     if (derive_geom(gin, &g) || ns_check(opts)) return 0;
-    return ns_layout(std::max(opts->n_live, opts->batch)).total;
+    return ns_layout(g, std::max(opts->n_live, opts->batch)).total;
 }
 
 gbk_status gbk_nested_sample_traced(const gbk_geom *gin, const gbk_obs *obs, const double *lo, const double *hi,
@@ -117,7 +124,7 @@ gbk_status gbk_nested_sample_traced(const gbk_geom *gin, const gbk_obs *obs, con
     if (g.u != 1 || !fused_config(g, &fc)) return fail(GBK_EUNSUPPORTED, "nested sampling uses the fused path");
     if ((s = check_obs(obs))) return s;
     const int N = opts->n_live, K = opts->batch;
-    NsLayout L = ns_layout(std::max(N, K));
+    NsLayout L = ns_layout(g, std::max(N, K));
     if (!workspace || ws_bytes < L.total)
         return fail(GBK_EWORKSPACE, "gbk_nested_sample needs %zu bytes of workspace (got %zu)", L.total, ws_bytes);
     if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
@@ -128,17 +135,22 @@ gbk_status gbk_nested_sample_traced(const gbk_geom *gin, const gbk_obs *obs, con
     auto evaluate = [&](const std::vector<double> &pv, int n, std::vector<double> &chi2) -> gbk_status {
         cudaError_t e = cudaMemcpyAsync(d_p, pv.data(), sizeof(double) * GBK_NPAR * n, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "nested sampling: parameter upload");
-        FusedArgs a = {};
-        a.g = g;
-        a.n_models = n;
-        a.params = d_p;
-        a.obs = *obs;
-        a.chi2 = d_c;
-        a.cs = fc.cs;
-        a.band = fc.band;
-        a.threads = fc.threads;
-        a.persistent = fc.persistent;
-        gbk_status s2 = launch_fused(a, st);
+        gbk_status s2;
+        if (L.split_bytes) {
+            s2 = launch_split(g, n, d_p, obs, nullptr, d_c, nullptr, (char *)workspace + L.split, L.split_bytes, st);
+        } else {
+            FusedArgs a = {};
+            a.g = g;
+            a.n_models = n;
+            a.params = d_p;
+            a.obs = *obs;
+            a.chi2 = d_c;
+            a.cs = fc.cs;
+            a.band = fc.band;
+            a.threads = fc.threads;
+            a.persistent = fc.persistent;
+            s2 = launch_fused(a, st);
+        }
         if (s2) return s2;
         chi2.resize(n);
         e = cudaMemcpyAsync(chi2.data(), d_c, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
