@@ -424,13 +424,17 @@ GBK_API gbk_status gbk_initial_guess(const gbk_geom *g, int32_t n_gal, const flo
  * (gbk_survey_autotune below).
  * gbk_survey_fit_lm is gbk_fit_lm per galaxy; the batched mode advances all
  * galaxies together in one CUDA graph (finite-difference or analytic tangent
- * Jacobian; the Jacobian kernel has its own galaxy groups, since its
- * per-spaxel records are larger, and galaxies whose halo rows do not fit a
- * CTA's shared memory are fitted in the same call with finite differences,
- * which serve them faster; the survey Jacobian carries the eight derivatives
- * x0 .. sigma0, so a fit that frees I0 or h uses finite differences for
- * every galaxy), the plain mode fits one galaxy after the other with the
- * host solve and finite differences.
+ * Jacobian).  With the analytic Jacobian and opts->path GBK_PATH_AUTO (or
+ * GBK_PATH_SPLIT, which requires it) every galaxy takes the ragged split
+ * Jacobian below when every galaxy is a cube model at u = 1 with a PSF
+ * radius <= 8; with
+ * GBK_PATH_FUSED (or where the split one does not serve) the cluster
+ * Jacobian kernel takes the galaxies whose halo rows fit a CTA's shared
+ * memory and the others are fitted in the same call with finite
+ * differences.  The survey Jacobians carry the eight derivatives x0 ..
+ * sigma0, so a fit that frees I0 or h uses finite differences for every
+ * galaxy.  The plain mode fits one galaxy after the other with the host
+ * solve and finite differences.
  * ------------------------------------------------------------------------ */
 GBK_API size_t gbk_survey_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, const gbk_lm_opts *opts);
 GBK_API gbk_status gbk_survey_eval(const gbk_geom *geoms, int32_t n_gal, const double *params, const gbk_obs *obs,
@@ -440,6 +444,22 @@ GBK_API gbk_status gbk_survey_fit_lm(const gbk_geom *geoms, int32_t n_gal, const
                                      const double *hi, double *params, const gbk_lm_opts *opts, double *chi2_out,
                                      int32_t *iters_out, int32_t *status_out, void *workspace, size_t ws_bytes,
                                      void *stream);
+
+/* The analytic Jacobian of a ragged batch in the split evaluator's shape
+ * (the forward-mode derivatives of gbk_jacobian, Sec. 2.3.1): for galaxy i
+ * with geometry geoms[i], parameters params[i] and maps obs[i], J^T J
+ * [n_gal][nf][nf], J^T r [n_gal][nf] and sum r^2 [n_gal] (each may be
+ * NULL) over the nf parameters of free_mask, which must lie among x0 ..
+ * sigma0.  Per galaxy the arithmetic is that of gbk_jacobian_ws on that
+ * galaxy alone; the stages run over work lists of (galaxy, row block) and
+ * (galaxy, tile) in chunks whose planes stay in L2, galaxies grouped by PSF
+ * radius.  GBK_EUNSUPPORTED unless every galaxy is a cube model at u = 1
+ * with a PSF radius <= 8.  Workspace: gbk_survey_jacobian_workspace_bytes;
+ * asynchronous. */
+GBK_API size_t gbk_survey_jacobian_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, uint32_t free_mask);
+GBK_API gbk_status gbk_survey_jacobian(const gbk_geom *geoms, int32_t n_gal, const double *params,
+                                       const gbk_obs *obs, uint32_t free_mask, double *jtj, double *jtv,
+                                       double *chi2, void *workspace, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
  * Nested grids (Sec. 2.3.3): chi2 at every node of a regular grid, then a

@@ -33,6 +33,7 @@
 // The PSF passes accumulate as the split evaluator's (six FP32 operations
 // per tap and triplet).  Models go in chunks whose planes stay in L2.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "fused_line.cuh"
@@ -80,19 +81,27 @@ struct TsArgs {
     double *part;             // [n_models][tiles][kTsEnt]
     unsigned *arrived;        // [n_models]
     int nxp, ezp, ra, tiles_x, tiles;
+    // Ragged batches (a geometry per model; unused in the single-geometry
+    // form): model m's geometry, table offset (floats into tab), plane offset
+    // (floats into pl, relative to the chunk), rows per stage-A CTA and first
+    // part slot; the launch's work items (model, row block or tile).
+    const Geom *geo;
+    const int *tab_off;
+    const long long *pl_off;
+    const int *ra_m;
+    const int *tile_base;
+    const int2 *work;
 };
 
-// ---------------------------------------------------------------------------
-__global__ void tsplit_setup_kernel(const double *params, int n, Geom g, ModelConst *mcs, float *tab)
+// The tables of one geometry: PSF taps at [kTsTabTaps, + 2R + 1), then the
+// per-channel LSF tap moments G0, H1, H2 (ezp floats each) at kTsTabZ.
+__device__ void ts_tables(const Geom &g, float *tab, int tid, int nthr)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) mcs[i] = model_const(params + (size_t)i * GBK_NPAR, g);
-    if (blockIdx.x != 0) return;
-    const int tid = threadIdx.x, ezp = ts_ezp(g);
-    if (tid <= 2 * g.R) tab[kTsTabTaps + tid] = tap_raw(tid - g.R, g.sig_xy, g.R) / tap_sum(g.sig_xy, g.R);
+    const int ezp = ts_ezp(g);
+    for (int j = tid; j <= 2 * g.R; j += nthr) tab[kTsTabTaps + j] = tap_raw(j - g.R, g.sig_xy, g.R) / tap_sum(g.sig_xy, g.R);
     float *tzx = tab + kTsTabZ, *tzy = tzx + ezp, *tzz = tzy + ezp;
     const float S = tap_sum(g.sig_z, g.Rz);
-    for (int e = tid; e < ezp; e += blockDim.x) {
+    for (int e = tid; e < ezp; e += nthr) {
         float G0 = 0.f, H1 = 0.f, H2 = 0.f;
         if (e < g.ez) {
             const int kd = e - g.Rz;  // data channel of extended channel e
@@ -108,6 +117,28 @@ __global__ void tsplit_setup_kernel(const double *params, int n, Geom g, ModelCo
         tzy[e] = g.dv * H1;
         tzz[e] = g.dv * g.dv * H2;
     }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void tsplit_setup_kernel(const double *params, int n, Geom g, ModelConst *mcs, float *tab)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) mcs[i] = model_const(params + (size_t)i * GBK_NPAR, g);
+    if (blockIdx.x != 0) return;
+    ts_tables(g, tab, threadIdx.x, blockDim.x);
+}
+
+// Ragged batches: one block per model, its constants and its own tables
+// (models with skip[m] != 0 are left alone: a plan over the running
+// galaxies gives the others no table slot).
+__global__ void tsplit_setup_ragged_kernel(const double *params, const Geom *geo, const int *tab_off,
+                                           const int32_t *skip, ModelConst *mcs, float *tab)
+{
+    const int m = blockIdx.x;
+    if (skip && skip[m] != 0) return;
+    const Geom g = geo[m];
+    if (threadIdx.x == 0) mcs[m] = model_const(params + (size_t)m * GBK_NPAR, g);
+    ts_tables(g, tab + tab_off[m], threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -236,7 +267,7 @@ __device__ __forceinline__ float tangent_spaxel(const Geom &g, const ModelConst 
 
 // ---------------------------------------------------------------------------
 // Stage A: triplets of a.ra extended rows, then their x pass.
-template <int R>
+template <int R, bool RAG>
 __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
 {
     constexpr int W = 2 * R + 1;
@@ -244,19 +275,38 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
     constexpr int NC4 = (NIN + 3) / 4;  // ... as float4 groups
     extern __shared__ __align__(16) float sm[];
     __shared__ ModelConst mc;
-    const Geom &g = a.g;
-    const int tid = threadIdx.x, model = blockIdx.y;
+    __shared__ Geom s_g;
+    const int tid = threadIdx.x;
+    int model, blk;
+    if constexpr (RAG) {
+        const int2 wk = a.work[blockIdx.x];
+        model = wk.x;
+        blk = wk.y;
+    } else {
+        model = blockIdx.y;
+        blk = blockIdx.x;
+    }
     if (a.skip && a.skip[model] != 0) return;  // the whole CTA
-    const int row0 = blockIdx.x * a.ra, nrows = min(a.ra, g.ey - row0);
+    if constexpr (RAG) {
+        if (tid < (int)(sizeof(Geom) / 4))
+            reinterpret_cast<int *>(&s_g)[tid] = reinterpret_cast<const int *>(a.geo + model)[tid];
+        __syncthreads();
+    }
+    const Geom &g = RAG ? s_g : a.g;
+    const int ra = RAG ? a.ra_m[model] : a.ra;
+    const int ezp = RAG ? ts_ezp(g) : a.ezp;
+    const int nxp = RAG ? ((g.nx + 3) & ~3) : a.nxp;
+    const float *const tab = RAG ? a.tab + a.tab_off[model] : a.tab;
+    const int row0 = blk * ra, nrows = min(ra, g.ey - row0);
     const int PA = ts_rowpitch(g.ex);
-    const int NPL = a.ra * PA;
+    const int NPL = ra * PA;
     float *const tz = sm + kTsPlanes * NPL;  // tzx, tzy, tzz
     if (tid < (int)(sizeof(ModelConst) / 4))
         reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
-    for (int i = tid; i < 3 * a.ezp; i += kTsThreads) tz[i] = a.tab[kTsTabZ + i];
+    for (int i = tid; i < 3 * ezp; i += kTsThreads) tz[i] = tab[kTsTabZ + i];
     float w[W];
 #pragma unroll
-    for (int j = 0; j < W; ++j) w[j] = a.tab[kTsTabTaps + j];
+    for (int j = 0; j < W; ++j) w[j] = tab[kTsTabTaps + j];
     __syncthreads();
 
     // phase 1: triplets of every extended spaxel of the rows
@@ -267,7 +317,7 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
         const int dr = kTsThreads / g.ex, dx = kTsThreads - dr * g.ex;
         for (int idx = tid; idx < nsp; idx += kTsThreads) {
             float rec[3 * kTsNT];
-            const float ac = tangent_spaxel(g, mc, pm, tz, tz + a.ezp, tz + 2 * a.ezp, a.ezp, (float)(xe - R),
+            const float ac = tangent_spaxel(g, mc, pm, tz, tz + ezp, tz + 2 * ezp, ezp, (float)(xe - R),
                                             (float)(row0 + r - R), rec);
             const int o = r * PA + xe;
 #pragma unroll
@@ -282,8 +332,8 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
     // phase 2: x pass; task (triplet, row, outputs 4 gx .. 4 gx + 3), the
     // triplet slowest so that consecutive threads write consecutive outputs
     const int ngx = (g.nx + 3) / 4;
-    const size_t pstride = (size_t)g.ey * a.nxp;  // floats per plane
-    float *const P0 = a.pl + (size_t)model * kTsPlanes * pstride + (size_t)row0 * a.nxp;
+    const size_t pstride = (size_t)g.ey * nxp;  // floats per plane
+    float *const P0 = (RAG ? a.pl + a.pl_off[model] : a.pl + (size_t)model * kTsPlanes * pstride) + (size_t)row0 * nxp;
     const float *const QA = sm + 3 * kTsNT * NPL;
     const int ntask = nrows * ngx;
     for (int t = tid; t < ntask * kTsNT; t += kTsThreads) {
@@ -298,7 +348,7 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
         }
 #pragma unroll
         for (int o = 0; o < 4; ++o) cen[o] = av[o + R];
-        float *const out = P0 + (size_t)rr * a.nxp + gx;
+        float *const out = P0 + (size_t)rr * nxp + gx;
         {
             const float *Q0 = sm + (3 * tr) * NPL, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
             float s[4][3];
@@ -339,7 +389,7 @@ __global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
 
 // ---------------------------------------------------------------------------
 // Stage B: y pass, moments, Jacobian rows and the per-model reductions.
-template <int R>
+template <int R, bool RAG>
 __global__ void __launch_bounds__(kTsThreads, 2)
     tsplit_psf_kernel(const __grid_constant__ CUtensorMap tmap, TsArgs a)
 {
@@ -356,29 +406,64 @@ __global__ void __launch_bounds__(kTsThreads, 2)
     __shared__ bool s_last;
     __shared__ __align__(8) uint64_t bar;
 
-    const Geom &g = a.g;
+    __shared__ Geom s_g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int model = blockIdx.y, tile = blockIdx.x;
-    if (a.skip && a.skip[model] != 0) return;  // the whole CTA
-    const int tx0 = (tile % a.tiles_x) * kTsTX, ty0 = (tile / a.tiles_x) * kTsTY;
-    const int nxo = min(kTsTX, g.nx - tx0), nyo = min(kTsTY, g.ny - ty0);
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    int model, tile;
+    if constexpr (RAG) {
+        const int2 wk = a.work[blockIdx.x];
+        model = wk.x;
+        tile = wk.y;
+    } else {
+        model = blockIdx.y;
+        tile = blockIdx.x;
     }
-    __syncthreads();
-    if (tid == 0) {
-        // the tile's rows of all 28 planes in one box (beyond the buffer: zeros)
-        tma_expect(&bar, (uint32_t)(kTsPlanes * NPL * sizeof(float)));
-        tma_load_3d(&tmap, sp, &bar, tx0, ty0, kTsPlanes * model);
+    if (a.skip && a.skip[model] != 0) return;  // the whole CTA
+    if constexpr (RAG) {
+        if (tid < (int)(sizeof(Geom) / 4))
+            reinterpret_cast<int *>(&s_g)[tid] = reinterpret_cast<const int *>(a.geo + model)[tid];
+        __syncthreads();
+    }
+    const Geom &g = RAG ? s_g : a.g;
+    const int tiles_x = RAG ? (g.nx + kTsTX - 1) / kTsTX : a.tiles_x;
+    const int tiles = RAG ? tiles_x * ((g.ny + kTsTY - 1) / kTsTY) : a.tiles;
+    double *const part0 = a.part + (RAG ? (size_t)a.tile_base[model] : (size_t)model * a.tiles) * kTsEnt;
+    const float *const tab = RAG ? a.tab + a.tab_off[model] : a.tab;
+    const int tx0 = (tile % tiles_x) * kTsTX, ty0 = (tile / tiles_x) * kTsTY;
+    const int nxo = min(kTsTX, g.nx - tx0), nyo = min(kTsTY, g.ny - ty0);
+    bool loaded = true;
+    if constexpr (RAG) {
+        // the tile's rows of all 28 planes by coalesced 16-byte loads (beyond
+        // the model's planes: zeros); the plane pitch is a multiple of four
+        const int nxp = (g.nx + 3) & ~3;
+        const size_t pstride = (size_t)g.ey * nxp;
+        const float *const src = a.pl + a.pl_off[model];
+        constexpr int C4 = kTsTX / 4;
+        for (int i = tid; i < kTsPlanes * NR * C4; i += kTsThreads) {
+            const int c4 = i % C4, rr = (i / C4) % NR, pl = i / (C4 * NR);
+            const int y = ty0 + rr, xx = tx0 + 4 * c4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (y < g.ey && xx < nxp) v = *reinterpret_cast<const float4 *>(src + pl * pstride + (size_t)y * nxp + xx);
+            *reinterpret_cast<float4 *>(sp + pl * NPL + rr * kTsTX + 4 * c4) = v;
+        }
+    } else {
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // the tile's rows of all 28 planes in one box (beyond the buffer: zeros)
+            tma_expect(&bar, (uint32_t)(kTsPlanes * NPL * sizeof(float)));
+            tma_load_3d(&tmap, sp, &bar, tx0, ty0, kTsPlanes * model);
+        }
     }
     if (tid < (int)(sizeof(ModelConst) / 4))
         reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
     if (tid == 32) s_ob = a.obs_list ? a.obs_list[model] : a.obs;
     float w[W];
 #pragma unroll
-    for (int j = 0; j < W; ++j) w[j] = a.tab[kTsTabTaps + j];
-    const bool loaded = mbar_wait(&bar, 0, kTsWaitLimit);
+    for (int j = 0; j < W; ++j) w[j] = tab[kTsTabTaps + j];
+    if constexpr (!RAG) loaded = mbar_wait(&bar, 0, kTsWaitLimit);
     if (__syncthreads_or(!loaded)) {  // the same decision in every thread
         if (tid == 0) {
             atomicExch(&g_tsplit_status, 1);
@@ -483,21 +568,21 @@ __global__ void __launch_bounds__(kTsThreads, 2)
     if (tid < kTsEnt) {
         double sum = 0.0;
         for (int q = 0; q < kTsThreads / 32; ++q) sum += (double)red[q][tid];
-        a.part[((size_t)model * a.tiles + tile) * kTsEnt + tid] = sum;
+        part0[(size_t)tile * kTsEnt + tid] = sum;
     }
     __syncthreads();
     if (tid == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&a.arrived[model], 1u);
-        s_last = (prev == (unsigned)a.tiles - 1);
+        s_last = (prev == (unsigned)tiles - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     if (tid < kTsEnt) {
-        const volatile double *p = a.part + (size_t)model * a.tiles * kTsEnt + tid;
+        const volatile double *p = part0 + tid;
         double sum = 0.0;
-        for (int k = 0; k < a.tiles; ++k) sum += p[(size_t)k * kTsEnt];
+        for (int k = 0; k < tiles; ++k) sum += p[(size_t)k * kTsEnt];
         s_part[tid] = sum;
     }
     __syncthreads();
@@ -550,26 +635,32 @@ static size_t ts_smem_a(const Geom &g, int ra)
 }
 static size_t ts_smem_b(int R) { return 128 + (size_t)kTsPlanes * (kTsTY + 2 * R) * kTsTX * sizeof(float); }
 
-static TsLayout ts_layout(const Geom &g, int n_models)
+// Rows per stage-A CTA: within the shared-memory target, the count whose
+// extended spaxels fill the most of whole rounds of the CTA's threads (the
+// larger on a tie).
+static int ts_rows_a(const Geom &g)
 {
-    TsLayout L = {};
-    L.nxp = (g.nx + 3) & ~3;
-    L.ezp = ts_ezp(g);
-    // rows per stage-A CTA: within the shared-memory target, the count whose
-    // extended spaxels fill the most of whole rounds of the CTA's threads
-    // (the larger on a tie)
     int ra_max = kTsplitMaxRA;
     while (ra_max > 1 && ts_smem_a(g, ra_max) > kTsSmemA) --ra_max;
-    L.ra = ra_max;
+    int best_ra = ra_max;
     double best = 0.0;
     for (int ra = ra_max; ra >= 1; --ra) {
         const int nsp = ra * g.ex, rounds = (nsp + kTsThreads - 1) / kTsThreads;
         const double use = (double)nsp / (double)(rounds * kTsThreads);
         if (use > best + 1e-9) {
             best = use;
-            L.ra = ra;
+            best_ra = ra;
         }
     }
+    return best_ra;
+}
+
+static TsLayout ts_layout(const Geom &g, int n_models)
+{
+    TsLayout L = {};
+    L.nxp = (g.nx + 3) & ~3;
+    L.ezp = ts_ezp(g);
+    L.ra = ts_rows_a(g);
     const size_t plb = (size_t)kTsPlanes * g.ey * L.nxp * sizeof(float);
     size_t chunk = kTsL2Budget / plb;
     if (chunk < 1) chunk = 1;
@@ -616,16 +707,16 @@ static gbk_status ts_launch_stages(const CUtensorMap &tm, const TsArgs &a, cudaS
     static KernelAttrMemo memo_a, memo_b;
     const size_t sa = ts_smem_a(a.g, a.ra), sb = ts_smem_b(R);
     gbk_status s;
-    if ((s = ensure_kernel_attrs((const void *)tsplit_line_kernel<R>, sa, false, memo_a,
+    if ((s = ensure_kernel_attrs((const void *)tsplit_line_kernel<R, false>, sa, false, memo_a,
                                  "split Jacobian: setting the line stage's shared memory")) ||
-        (s = ensure_kernel_attrs((const void *)tsplit_psf_kernel<R>, sb, false, memo_b,
+        (s = ensure_kernel_attrs((const void *)tsplit_psf_kernel<R, false>, sb, false, memo_b,
                                  "split Jacobian: setting the PSF stage's shared memory")))
         return s;
     const unsigned blocks_a = (unsigned)((a.g.ey + a.ra - 1) / a.ra);
-    tsplit_line_kernel<R><<<dim3(blocks_a, (unsigned)a.n_models), kTsThreads, sa, st>>>(a);
+    tsplit_line_kernel<R, false><<<dim3(blocks_a, (unsigned)a.n_models), kTsThreads, sa, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "split Jacobian: line stage launch");
-    tsplit_psf_kernel<R><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kTsThreads, sb, st>>>(tm, a);
+    tsplit_psf_kernel<R, false><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kTsThreads, sb, st>>>(tm, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: PSF stage launch");
     return GBK_OK;
 }
@@ -698,6 +789,187 @@ gbk_status launch_tsplit(const TsplitCall &call, void *ws, size_t ws_bytes, cuda
         case 7: s = ts_launch_stages<7>(tm, a, st); break;
         case 8: s = ts_launch_stages<8>(tm, a, st); break;
         default: return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", g.R, kTsplitMaxR);
+        }
+        if (s) return s;
+    }
+    return GBK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches.
+void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std::vector<char> *active)
+{
+    *p = TsRaggedPlan();
+    const int n = (int)geo.size();
+    p->n = n;
+    if (n == 0) return;
+    for (const Geom &g : geo) {
+        if (g.model != GBK_MODEL_CUBE || g.u != 1 || g.R > kTsplitMaxR || g.ex > 1024 || ts_smem_a(g, 1) > 200 * 1024 ||
+            ts_smem_b(g.R) > 200 * 1024)
+            return;
+    }
+    // galaxies by PSF radius (the stages are compiled per radius), index
+    // order within a radius; a chunk never mixes radii
+    std::vector<int> ord(n);
+    for (int m = 0; m < n; ++m) ord[m] = m;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return geo[a].R < geo[b].R; });
+    p->tab_off.resize(n);
+    p->ra.resize(n);
+    p->tile_base.resize(n);
+    p->pl_off.resize(n);
+    const long long budget = (long long)(kTsL2Budget / sizeof(float));
+    long long tab = 0, chunk_start = 0, cum = 0, pl_max = 0;
+    int slots = 0;
+    p->chunk_a.push_back(0);
+    p->chunk_b.push_back(0);
+    bool first = true;
+    int prev_r = -1;
+    for (int j = 0; j < n; ++j) {
+        const int m = ord[j];
+        if (active && !(*active)[m]) continue;  // no work, no planes, no part slots
+        const Geom &g = geo[m];
+        const int nxp = (g.nx + 3) & ~3;
+        const long long planes = (long long)kTsPlanes * g.ey * nxp;
+        if (!first && (g.R != prev_r || cum + planes - chunk_start > budget)) {  // close the chunk before galaxy m
+            pl_max = std::max(pl_max, cum - chunk_start);
+            p->chunk_a.push_back((int)p->work_a.size());
+            p->chunk_b.push_back((int)p->work_b.size());
+            p->chunk_r.push_back(prev_r);
+            chunk_start = cum;
+        }
+        first = false;
+        prev_r = g.R;
+        p->pl_off[m] = cum - chunk_start;
+        cum += planes;
+        p->tab_off[m] = (int)tab;
+        tab += (kTsTabZ + 3 * ts_ezp(g) + 3) & ~3;
+        p->ra[m] = ts_rows_a(g);
+        p->smem_a = std::max(p->smem_a, ts_smem_a(g, p->ra[m]));
+        for (int b = 0; b * p->ra[m] < g.ey; ++b) p->work_a.push_back(make_int2(m, b));
+        const int tiles = ((g.nx + kTsTX - 1) / kTsTX) * ((g.ny + kTsTY - 1) / kTsTY);
+        p->tile_base[m] = slots;
+        slots += tiles;
+        for (int t = 0; t < tiles; ++t) p->work_b.push_back(make_int2(m, t));
+    }
+    pl_max = std::max(pl_max, cum - chunk_start);
+    if (!first) {
+        p->chunk_a.push_back((int)p->work_a.size());
+        p->chunk_b.push_back((int)p->work_b.size());
+        p->chunk_r.push_back(prev_r);
+    }
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t r = o; o += ts_al256(bytes); return r; };
+    p->o_mcs = take(sizeof(ModelConst) * n);
+    p->o_tab = take(sizeof(float) * (size_t)tab);
+    p->o_pl = take(sizeof(float) * (size_t)pl_max);
+    p->o_part = take(sizeof(double) * (size_t)slots * kTsEnt);
+    p->o_arr = take(sizeof(unsigned) * n);
+    p->o_taboff = take(sizeof(int) * n);
+    p->o_ra = take(sizeof(int) * n);
+    p->o_tbase = take(sizeof(int) * n);
+    p->o_ploff = take(sizeof(long long) * n);
+    p->o_wa = take(sizeof(int2) * p->work_a.size());
+    p->o_wb = take(sizeof(int2) * p->work_b.size());
+    p->total = o;
+    p->ok = true;
+}
+
+gbk_status tsplit_ragged_upload(const TsRaggedPlan &p, char *ws, cudaStream_t st)
+{
+    if (!p.ok) return fail(GBK_EUNSUPPORTED, "the split Jacobian does not serve this batch of geometries");
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ws + p.o_taboff, p.tab_off.data(), sizeof(int) * p.n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(ws + p.o_ra, p.ra.data(), sizeof(int) * p.n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(ws + p.o_tbase, p.tile_base.data(), sizeof(int) * p.n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(ws + p.o_ploff, p.pl_off.data(), sizeof(long long) * p.n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(ws + p.o_wa, p.work_a.data(), sizeof(int2) * p.work_a.size(), cudaMemcpyHostToDevice,
+                             st)) ||
+        (e = cudaMemcpyAsync(ws + p.o_wb, p.work_b.data(), sizeof(int2) * p.work_b.size(), cudaMemcpyHostToDevice,
+                             st)))
+        return cuda_fail(e, "split Jacobian: uploading the ragged plan");
+    return GBK_OK;
+}
+
+// The stages of chunk c (its galaxies share the PSF radius R).
+template <int R>
+static gbk_status ts_launch_ragged(const TsRaggedPlan &p, int c, TsArgs a, char *ws, cudaStream_t st)
+{
+    static KernelAttrMemo memo_a, memo_b;
+    const size_t sb = ts_smem_b(R);
+    gbk_status s;
+    if ((s = ensure_kernel_attrs((const void *)tsplit_line_kernel<R, true>, p.smem_a, false, memo_a,
+                                 "split Jacobian: setting the ragged line stage's shared memory")) ||
+        (s = ensure_kernel_attrs((const void *)tsplit_psf_kernel<R, true>, sb, false, memo_b,
+                                 "split Jacobian: setting the ragged PSF stage's shared memory")))
+        return s;
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    const int2 *wa = (const int2 *)(ws + p.o_wa), *wb = (const int2 *)(ws + p.o_wb);
+    const int na = p.chunk_a[c + 1] - p.chunk_a[c], nb = p.chunk_b[c + 1] - p.chunk_b[c];
+    cudaError_t e;
+    if (na > 0) {
+        a.work = wa + p.chunk_a[c];
+        tsplit_line_kernel<R, true><<<(unsigned)na, kTsThreads, p.smem_a, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: ragged line stage launch");
+    }
+    if (nb > 0) {
+        a.work = wb + p.chunk_b[c];
+        tsplit_psf_kernel<R, true><<<(unsigned)nb, kTsThreads, sb, st>>>(none, a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: ragged PSF stage launch");
+    }
+    return GBK_OK;
+}
+
+gbk_status launch_tsplit_ragged(const TsRaggedPlan &p, const TsplitRaggedCall &call, char *ws, cudaStream_t st)
+{
+    if (!p.ok) return fail(GBK_EUNSUPPORTED, "the split Jacobian does not serve this batch of geometries");
+    if (call.np < 1 || call.np > kTsNP) return fail(GBK_EUNSUPPORTED, "split Jacobian: free parameters among x0 .. sigma0");
+    for (int k = 0; k < call.np; ++k)
+        if (call.free_idx[k] < 0 || call.free_idx[k] >= kTsNP)
+            return fail(GBK_EUNSUPPORTED, "split Jacobian: free parameters among x0 .. sigma0");
+    if (p.n == 0) return GBK_OK;
+    ModelConst *mcs = (ModelConst *)(ws + p.o_mcs);
+    float *tab = (float *)(ws + p.o_tab);
+    cudaError_t e = cudaMemsetAsync(ws + p.o_arr, 0, sizeof(unsigned) * p.n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "split Jacobian: clearing the arrival counters");
+    tsplit_setup_ragged_kernel<<<(unsigned)p.n, 128, 0, st>>>(call.params, call.d_geo, (const int *)(ws + p.o_taboff),
+                                                              call.skip, mcs, tab);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: ragged set-up launch");
+    TsArgs a = {};
+    a.g = Geom();
+    a.n_models = p.n;
+    a.params = call.params;
+    a.mcs = mcs;
+    a.tab = tab;
+    a.pl = (float *)(ws + p.o_pl);
+    a.obs_list = call.obs_list;
+    a.skip = call.skip;
+    a.cot = nullptr;
+    a.np = call.np;
+    for (int k = 0; k < call.np; ++k) a.free_idx[k] = call.free_idx[k];
+    a.jtj = call.jtj;
+    a.jtv = call.jtv;
+    a.chi2 = call.chi2;
+    a.part = (double *)(ws + p.o_part);
+    a.arrived = (unsigned *)(ws + p.o_arr);
+    a.geo = call.d_geo;
+    a.tab_off = (const int *)(ws + p.o_taboff);
+    a.pl_off = (const long long *)(ws + p.o_ploff);
+    a.ra_m = (const int *)(ws + p.o_ra);
+    a.tile_base = (const int *)(ws + p.o_tbase);
+    for (int c = 0; c + 1 < (int)p.chunk_a.size(); ++c) {
+        gbk_status s;
+        switch (p.chunk_r[c]) {
+        case 0: s = ts_launch_ragged<0>(p, c, a, ws, st); break;
+        case 1: s = ts_launch_ragged<1>(p, c, a, ws, st); break;
+        case 2: s = ts_launch_ragged<2>(p, c, a, ws, st); break;
+        case 3: s = ts_launch_ragged<3>(p, c, a, ws, st); break;
+        case 4: s = ts_launch_ragged<4>(p, c, a, ws, st); break;
+        case 5: s = ts_launch_ragged<5>(p, c, a, ws, st); break;
+        case 6: s = ts_launch_ragged<6>(p, c, a, ws, st); break;
+        case 7: s = ts_launch_ragged<7>(p, c, a, ws, st); break;
+        case 8: s = ts_launch_ragged<8>(p, c, a, ws, st); break;
+        default: return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", p.chunk_r[c], kTsplitMaxR);
         }
         if (s) return s;
     }

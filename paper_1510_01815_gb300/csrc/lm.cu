@@ -166,6 +166,7 @@ struct EvalTarget {
     const SurveyPlan *sp;
     LmSplit split;
     void *sws;
+    const TsRaggedPlan *rag = nullptr;  // survey: the ragged split Jacobian's plan (its region at sws)
 };
 
 static gbk_status eval_for(const EvalTarget &t, int n_gal, int mpg, const double *params, const gbk_obs *obs_list,
@@ -355,14 +356,16 @@ static gbk_status lm_plain(const Geom &g, int n_gal, const gbk_obs *obs, const d
 }
 
 static gbk_status lm_iteration(const EvalTarget &t, const LmArgs &a, const gbk_obs *obs, bool tangent,
-                               const TangentArgs &ta, const TsplitCall &tc, cudaStream_t st)
+                               const TangentArgs &ta, const TsplitCall &tc, const TsplitRaggedCall &rc,
+                               cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(a.n_active, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "LM: clearing the running count");
     gbk_status s;
     if (tangent) {
         // analytic J^T J and J^T r at the current point
-        if (t.sp) s = survey_tangent(*t.sp, ta, st);
+        if (t.sp && t.rag) s = launch_tsplit_ragged(*t.rag, rc, (char *)t.sws, st);
+        else if (t.sp) s = survey_tangent(*t.sp, ta, st);
         else if (t.split.jac) s = launch_tsplit(tc, t.sws, t.split.bytes, st);
         else s = launch_tangent(ta, st);
         if (s) return s;
@@ -385,7 +388,7 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
                              double *params, const gbk_lm_opts *o, const LmPlan &pl, double *chi2_out,
                              int32_t *iters_out, int32_t *status_out, char *ws, cudaStream_t user)
 {
-    LmLayout L = t.sp ? lm_layout_pix((size_t)t.sp->total_pix(), n_gal, pl)
+    LmLayout L = t.sp ? lm_layout_pix((size_t)t.sp->total_pix(), n_gal, pl, t.split.bytes)
                       : lm_layout(*t.g, n_gal, pl, t.split.bytes);
     LmArgs a = {};
     a.n_gal = n_gal;
@@ -431,7 +434,19 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     lm_launch_init(a, o->lambda0, st);
     TangentArgs ta = {};
     TsplitCall tc = {};
-    if (pl.tangent && !t.sp && t.split.jac) {
+    TsplitRaggedCall rc = {};
+    if (pl.tangent && t.sp && t.rag) {
+        rc.d_geo = t.sp->d_geo;
+        rc.params = params;
+        rc.obs_list = obs;
+        rc.skip = a.done;
+        rc.np = pl.np;
+        for (int j = 0; j < pl.np; ++j) rc.free_idx[j] = pl.idx[j];
+        rc.jtj = a.jtj;
+        rc.jtv = a.jtr;
+        gbk_status s0 = eval_for(t, n_gal, 1, params, obs, nullptr, a.chi2_cur, nullptr, st);
+        if (s0) return s0;
+    } else if (pl.tangent && !t.sp && t.split.jac) {
         tc.g = *t.g;
         tc.n_models = n_gal;
         tc.params = params;
@@ -469,14 +484,16 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     }
     // The first iteration runs eagerly (it also settles the kernels' launch
     // configurations); the rest replay a captured graph.
-    gbk_status s = lm_iteration(t, a, obs, pl.tangent, ta, tc, st);
+    gbk_status s = lm_iteration(t, a, obs, pl.tangent, ta, tc, rc, st);
     if (s) return s;
     int32_t h_active = n_gal;
     int done_iters = 1;
+    int planned = n_gal;   // galaxies of the current ragged Jacobian plan
+    TsRaggedPlan live;     // its re-plan over the running galaxies
     if (o->max_iter > 1) {
         if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
             return cuda_fail(e, "LM: begin graph capture");
-        s = lm_iteration(t, a, obs, pl.tangent, ta, tc, st);
+        s = lm_iteration(t, a, obs, pl.tangent, ta, tc, rc, st);
         e = cudaStreamEndCapture(st, &cg.graph);
         if (s) return s;
         if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");
@@ -491,6 +508,36 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
                 (e = cudaStreamSynchronize(st)))
                 return cuda_fail(e, "LM: polling");
             if (h_active == 0) break;
+            if (t.rag && h_active * 4 <= planned && planned > 16) {
+                // Ragged split Jacobian: the finished galaxies' CTAs would only
+                // return at their skip test, so once a quarter of the planned
+                // galaxies are still running, plan the running ones alone and
+                // capture the iteration again.
+                std::vector<int32_t> h_done(n_gal);
+                if ((e = cudaMemcpyAsync(h_done.data(), a.done, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToHost,
+                                         st)) ||
+                    (e = cudaStreamSynchronize(st)))
+                    return cuda_fail(e, "LM: reading the running galaxies");
+                std::vector<char> act(n_gal);
+                for (int i = 0; i < n_gal; ++i) act[i] = h_done[i] == 0;
+                tsplit_ragged_plan(t.sp->geo, &live, &act);
+                if (!live.ok || live.total > t.split.bytes) return fail(GBK_EINVAL, "LM: re-planning the survey Jacobian");
+                if ((s = tsplit_ragged_upload(live, (char *)t.sws, st))) return s;
+                planned = h_active;
+                EvalTarget t2 = t;
+                t2.rag = &live;
+                cudaGraphExecDestroy(cg.exec);
+                cudaGraphDestroy(cg.graph);
+                cg.exec = nullptr;
+                cg.graph = nullptr;
+                if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
+                    return cuda_fail(e, "LM: begin graph capture");
+                s = lm_iteration(t2, a, obs, pl.tangent, ta, tc, rc, st);
+                e = cudaStreamEndCapture(st, &cg.graph);
+                if (s) return s;
+                if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");
+                if ((e = cudaGraphInstantiate(&cg.exec, cg.graph, 0))) return cuda_fail(e, "LM: graph instantiation");
+            }
         }
     }
     if ((e = cudaMemcpyAsync(chi2_out, a.chi2_best, sizeof(double) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
@@ -559,6 +606,20 @@ size_t lm_survey_workspace(const SurveyPlan &sp, const gbk_geom *geoms, const gb
         gbk_lm_opts ofd = *o;
         ofd.jacobian = GBK_JAC_FD_FORWARD;
         return lm_survey_workspace(sp, geoms, &ofd);
+    }
+    if (o->path != (int32_t)GBK_PATH_AUTO && o->path != (int32_t)GBK_PATH_FUSED && o->path != (int32_t)GBK_PATH_SPLIT) {
+        fail(GBK_EINVAL, "LM evaluates on GBK_PATH_AUTO, GBK_PATH_FUSED or GBK_PATH_SPLIT (got %d)", o->path);
+        return 0;
+    }
+    if (pl.tangent && o->path != (int32_t)GBK_PATH_FUSED) {
+        // the ragged split Jacobian for every galaxy, where it serves the batch
+        TsRaggedPlan rp;
+        tsplit_ragged_plan(sp.geo, &rp);
+        if (rp.ok) return lm_layout_pix((size_t)sp.total_pix(), sp.n_gal, pl, rp.total).total;
+        if (o->path == (int32_t)GBK_PATH_SPLIT) {
+            fail(GBK_EUNSUPPORTED, "the split Jacobian does not serve this batch (PSF radius <= 8, u = 1, cube model)");
+            return 0;
+        }
     }
     if (pl.tangent && !sp.tangent_ok) {
         // split: the Jacobian kernel where it fits, finite differences elsewhere
@@ -667,6 +728,21 @@ gbk_status lm_survey(SurveyPlan &sp, const gbk_geom *geoms, const gbk_obs *obs, 
         gbk_lm_opts ofd = *o;
         ofd.jacobian = GBK_JAC_FD_FORWARD;
         return lm_survey(sp, geoms, obs, lo, hi, params, &ofd, chi2_out, iters_out, status_out, ws, ws_bytes, st);
+    }
+    if (pl.tangent && o->path != (int32_t)GBK_PATH_FUSED) {
+        // every galaxy on the ragged split Jacobian where it serves the batch
+        // (the trial points on the survey's cluster evaluator)
+        TsRaggedPlan rp;
+        tsplit_ragged_plan(sp.geo, &rp);
+        if (rp.ok) {
+            const LmLayout L = lm_layout_pix((size_t)sp.total_pix(), sp.n_gal, pl, rp.total);
+            char *rws = ws + L.sws;
+            if ((s = tsplit_ragged_upload(rp, rws, st))) return s;
+            EvalTarget t = {nullptr, &sp, LmSplit{false, true, rp.total}, rws, &rp};
+            return lm_batched(t, sp.n_gal, obs, lo, hi, params, o, pl, chi2_out, iters_out, status_out, ws, st);
+        }
+        if (o->path == (int32_t)GBK_PATH_SPLIT)
+            return fail(GBK_EUNSUPPORTED, "the split Jacobian does not serve this batch (PSF radius <= 8, u = 1, cube model)");
     }
     if (pl.tangent && !sp.tangent_ok) {
         // The Jacobian-kernel part (A) and the finite-difference part (B) are

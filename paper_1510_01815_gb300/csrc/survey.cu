@@ -23,6 +23,7 @@
 #include "gbk_api_internal.h"
 #include "k_fused.h"
 #include "k_tangent.h"
+#include "k_tsplit.h"
 #include "survey.h"
 
 namespace gbk {
@@ -426,6 +427,62 @@ gbk_status gbk_survey_eval(const gbk_geom *geoms, int32_t n_gal, const double *p
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = survey_upload(&sp, (char *)workspace, st))) return s;
     if ((s = survey_eval(sp, 1, params, (chi2 || resid) ? obs : nullptr, nullptr, maps, chi2, resid, st))) return s;
+    return ok();
+}
+
+size_t gbk_survey_jacobian_workspace_bytes(const gbk_geom *geoms, int32_t n_gal, uint32_t free_mask)
+{
+    ok();
+    if (free_mask == 0 || (free_mask >> GBK_I0)) {
+        fail(GBK_EINVAL, "free_mask must select parameters among x0 .. sigma0");
+        return 0;
+    }
+    SurveyPlan sp;
+    if (survey_plan(geoms, n_gal, &sp)) return 0;
+    TsRaggedPlan rp;
+    tsplit_ragged_plan(sp.geo, &rp);
+    if (!rp.ok) {
+        fail(GBK_EUNSUPPORTED, "the split Jacobian does not serve this batch (PSF radius <= 8, u = 1, cube model)");
+        return 0;
+    }
+    return sp.table_bytes + rp.total;
+}
+
+gbk_status gbk_survey_jacobian(const gbk_geom *geoms, int32_t n_gal, const double *params, const gbk_obs *obs,
+                               uint32_t free_mask, double *jtj, double *jtv, double *chi2, void *workspace,
+                               size_t ws_bytes, void *stream)
+{
+    if (free_mask == 0 || (free_mask >> GBK_I0))
+        return fail(GBK_EINVAL, "free_mask must select parameters among x0 .. sigma0");
+    SurveyPlan sp;
+    gbk_status s = survey_plan_cached(geoms, n_gal, &sp);
+    if (s) return s;
+    if (n_gal == 0) return ok();
+    TsRaggedPlan rp;
+    tsplit_ragged_plan(sp.geo, &rp);
+    if (!rp.ok) return fail(GBK_EUNSUPPORTED, "the split Jacobian does not serve this batch (PSF radius <= 8, u = 1, cube model)");
+    if ((s = check_device_ptr(params, "params", 8)) || (s = check_device_ptr(obs, "obs", 8))) return s;
+    if (jtj && (s = check_device_ptr(jtj, "jtj", 8))) return s;
+    if (jtv && (s = check_device_ptr(jtv, "jtv", 8))) return s;
+    if (chi2 && (s = check_device_ptr(chi2, "chi2", 8))) return s;
+    const size_t need = sp.table_bytes + rp.total;
+    if (!workspace || ws_bytes < need)
+        return fail(GBK_EWORKSPACE, "gbk_survey_jacobian needs %zu bytes of workspace (got %zu)", need, ws_bytes);
+    if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    if ((s = survey_upload(&sp, ws, st)) || (s = tsplit_ragged_upload(rp, ws + sp.table_bytes, st))) return s;
+    TsplitRaggedCall c = {};
+    c.d_geo = sp.d_geo;
+    c.params = params;
+    c.obs_list = obs;
+    c.skip = nullptr;
+    for (int k = 0; k < GBK_I0; ++k)
+        if (free_mask & (1u << k)) c.free_idx[c.np++] = k;
+    c.jtj = jtj;
+    c.jtv = jtv;
+    c.chi2 = chi2;
+    if ((s = launch_tsplit_ragged(rp, c, ws + sp.table_bytes, st))) return s;
     return ok();
 }
 

@@ -120,6 +120,8 @@ def lib():
             "gbk_survey_eval": (i32, [gp, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
             "gbk_survey_fit_lm": (i32, [gp, i32, vp, vp, vp, vp, ctypes.POINTER(CLmOpts), vp, vp, vp, vp, sz,
                                         vp]),
+            "gbk_survey_jacobian_workspace_bytes": (sz, [gp, i32, u32]),
+            "gbk_survey_jacobian": (i32, [gp, i32, vp, vp, u32, vp, vp, vp, vp, sz, vp]),
             "gbk_initial_guess": (i32, [gp, i32, vp, vp, vp, vp, vp]),
             "gbk_survey_autotune": (i32, [gp, i32, vp, vp, vp, vp, sz, ctypes.POINTER(CTuning), vp]),
             "gbk_survey_get_tuning": (i32, [gp, i32, ctypes.POINTER(CTuning)]),
@@ -157,7 +159,8 @@ def exported_symbols():
             "gbk_grid",
             "gbk_nested_sample_workspace_bytes", "gbk_nested_sample", "gbk_nested_sample_traced",
             "gbk_survey_workspace_bytes",
-            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_initial_guess", "gbk_survey_autotune", "gbk_survey_get_tuning",
+            "gbk_survey_eval", "gbk_survey_fit_lm", "gbk_survey_jacobian_workspace_bytes", "gbk_survey_jacobian",
+            "gbk_initial_guess", "gbk_survey_autotune", "gbk_survey_get_tuning",
             "gbk_survey_set_tuning", "gbk_device_status", "gbk_gemm_bf16", "gbk_cnn_param_count",
             "gbk_cnn_workspace_bytes", "gbk_cnn_init", "gbk_cnn_targets", "gbk_cnn_decode", "gbk_cnn_synth_obs",
             "gbk_cnn_forward", "gbk_cnn_grad", "gbk_cnn_train_step",
@@ -710,6 +713,44 @@ def gbk_jacobian_ws(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), cot=None, 
                                  mask, _ptr(cot, torch.float32, "cot"), _ptr(jtj, torch.float64, "jtj"),
                                  _ptr(jtv, torch.float64, "jtv"), _ptr(chi2, torch.float64, "chi2"),
                                  _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def gbk_survey_jacobian_workspace_bytes(geoms, free=(0, 1, 2, 3, 4, 5, 6, 7)):
+    mask = 0
+    for k in free:
+        mask |= 1 << int(k)
+    nb = lib().gbk_survey_jacobian_workspace_bytes(cgeoms(geoms), len(geoms), mask)
+    if nb == 0 and len(geoms) > 0:
+        err = lib().gbk_last_error().decode()
+        raise GbkError(GBK_EUNSUPPORTED if "serve" in err else GBK_EINVAL, err)
+    return nb
+
+
+def gbk_survey_jacobian(geoms, params, obs_dev, free=(0, 1, 2, 3, 4, 5, 6, 7), jtj=None, jtv=None, chi2=None,
+                        workspace=None, stream=None):
+    """The ragged split-shape Jacobian reductions of a survey batch (one model
+    per galaxy; obs_dev a device array of gbk_obs, obs_array)."""
+    mask = 0
+    for k in free:
+        mask |= 1 << int(k)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().gbk_survey_jacobian(cgeoms(geoms), len(geoms), _ptr(params, torch.float64, "params"),
+                                     _ptr(obs_dev, torch.uint8, "obs"), mask, _ptr(jtj, torch.float64, "jtj"),
+                                     _ptr(jtv, torch.float64, "jtv"), _ptr(chi2, torch.float64, "chi2"),
+                                     _ptr(workspace, None, "workspace"), ws_bytes, _stream(stream)))
+
+
+def survey_jacobian(geoms, params, obs_list, free=(0, 1, 2, 3, 4, 5, 6, 7), device="cuda"):
+    """Convenience: (J^T J, J^T r, chi2) of a survey batch on the ragged split Jacobian."""
+    params = torch.as_tensor(params, dtype=torch.float64).reshape(len(geoms), NPAR).to(device).contiguous()
+    n, nf = len(geoms), len(free)
+    jtj = torch.empty((n, nf, nf), dtype=torch.float64, device=device)
+    jtv = torch.empty((n, nf), dtype=torch.float64, device=device)
+    c2 = torch.empty(n, dtype=torch.float64, device=device)
+    obs_dev, _keep = obs_array(obs_list, device)
+    ws = torch.empty(max(1, gbk_survey_jacobian_workspace_bytes(geoms, free)), dtype=torch.uint8, device=device)
+    gbk_survey_jacobian(geoms, params, obs_dev, free, jtj, jtv, c2, ws)
+    return jtj, jtv, c2
 
 
 def jacobian_split(geom, params, obs, free=(0, 1, 2, 3, 4, 5, 6, 7), device="cuda"):

@@ -189,8 +189,19 @@ def test_survey_host_logic(gbk):
     # the plain mode needs room for one galaxy at a time
     assert gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(mode=gbk.LM_PLAIN)) < lm
     assert gbk.gbk_survey_workspace_bytes([], None) == 0
-    # the analytic Jacobian needs no finite-difference batch
-    assert tables < gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT)) < lm
+    # the cluster Jacobian needs no finite-difference batch
+    cluster = gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT, path=gbk.PATH_FUSED))
+    assert tables < cluster < lm
+    # the ragged split Jacobian (the default) adds its planes: 28 per
+    # extended spaxel of the galaxies, up to an L2-sized chunk
+    rag = gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT))
+    ext = sum((g.nx + 2 * 7) * (g.nx + 3) for g in geoms)
+    assert rag > cluster and rag >= tables + 28 * 4 * ext
+    assert gbk.gbk_survey_jacobian_workspace_bytes(geoms) > tables
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_jacobian_workspace_bytes(geoms, free=(synth.I0,))
+    with pytest.raises(gbk.GbkError):
+        gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT, path=gbk.PATH_STAGED))
     with pytest.raises(gbk.GbkError):
         gbk.gbk_survey_workspace_bytes(geoms, gbk.lm_opts(jacobian=gbk.JAC_TANGENT, mode=gbk.LM_PLAIN))
     with pytest.raises(gbk.GbkError):

@@ -357,3 +357,54 @@ def test_survey_fit_tail_is_the_degeneracy_valley(G):
     assert np.all(ct[running] <= cf[running] * (1 + 1e-3) + 1e-6), (ct[running], cf[running])
     steep = (truth[:, synth.INCL] >= 35.0) & ~at_bound
     assert np.all(np.isin(stt[steep], [1, 2])), np.unique(stt[steep], return_counts=True)
+
+
+def test_survey_jacobian_equals_single_geometry_calls(G):
+    """The ragged split Jacobian of a survey batch (galaxies of different
+    size, band and LSF, wide ones included) equals, galaxy by galaxy and bit
+    for bit, the single-geometry split Jacobian of that galaxy alone."""
+    rng = np.random.default_rng(61)
+    gal = synth.draw_survey(rng, 10) + [(Geometry(96, 96, 40, 20.0, 0.0, 4.0, 30.0), None),
+                                        (Geometry(72, 80, 33, 25.0, 0.0, 4.0, 40.0), None)]
+    geoms = [g for g, _ in gal]
+    ps = np.array([p if p is not None else truth_for(g, rng) for g, p in gal])
+    p0 = np.array([synth.perturb(rng, p, synth.FREE_DEFAULT, 0.1) for p in ps])
+    obs = []
+    for g, p in zip(geoms, ps):
+        m = oracle.evaluate(ogeom(g), p)
+        wv, ws = synth.weights((g.ny, g.nx), 5.0)
+        noise = rng.normal(0.0, 5.0, size=(2, g.ny, g.nx))
+        obs.append(G.Obs.from_numpy((m[1] + noise[0]).astype(np.float32), (m[2] + noise[1]).astype(np.float32),
+                                    wv, ws, (m[0] > 0).astype(np.uint8)))
+    jtj, jtv, c2 = G.survey_jacobian(geoms, p0, obs)
+    jtj, jtv, c2 = jtj.cpu().numpy(), jtv.cpu().numpy(), c2.cpu().numpy()
+    assert G.gbk_device_status() == 0
+    for i, g in enumerate(geoms):
+        a, b, c = G.jacobian_split(g, torch.from_numpy(p0[i:i + 1]), obs[i])
+        np.testing.assert_array_equal(jtj[i], a.cpu().numpy()[0], err_msg="galaxy %d" % i)
+        np.testing.assert_array_equal(jtv[i], b.cpu().numpy()[0], err_msg="galaxy %d" % i)
+        assert c2[i] == c.cpu().numpy()[0], i
+
+
+def test_survey_fit_ragged_jacobian(G):
+    """The survey LM on the ragged split Jacobian (the default) recovers
+    noiseless galaxies of every size, including those too wide for the
+    cluster kernel's halo copies, and agrees with the cluster-kernel fit."""
+    geoms = [GEOMS[0], GEOMS[3], Geometry(72, 72, 40, 20.0, 0.0, 4.0, 30.0), Geometry(96, 96, 32, 25.0, 0.0, 4.0, 40.0)]
+    rng = np.random.default_rng(29)
+    ps = [truth_for(g, rng) for g in geoms]
+    for p in ps:
+        p[synth.INCL] = rng.uniform(40.0, 65.0)
+        p[synth.VMAX] = rng.uniform(120.0, 200.0)
+    obs = [_noiseless(G, g, p) for g, p in zip(geoms, ps)]
+    lo, hi = zip(*[_bounds(g, p) for g, p in zip(geoms, ps)])
+    p0 = [synth.perturb(rng, p, synth.FREE_DEFAULT, 0.2, l, h) for p, l, h in zip(ps, lo, hi)]
+    q, c, it, st = G.survey_fit_lm(geoms, obs, p0, lo, hi, G.lm_opts(max_iter=100, jacobian=G.JAC_TANGENT,
+                                                                      path=G.PATH_SPLIT))
+    ps = np.array(ps)
+    assert np.all(np.isin(st, [1, 2])), (st, it)
+    assert np.all(np.abs(q[:, synth.VMAX] - ps[:, synth.VMAX]) < 2.0), (q[:, synth.VMAX], ps[:, synth.VMAX])
+    assert np.all(np.abs(q[:, synth.PA] - ps[:, synth.PA]) < 1.0), (q[:, synth.PA], ps[:, synth.PA])
+    qc, cc, itc, stc = G.survey_fit_lm(geoms, obs, p0, lo, hi, G.lm_opts(max_iter=100, jacobian=G.JAC_TANGENT,
+                                                                         path=G.PATH_FUSED))
+    assert np.all(np.abs(q[:, synth.VMAX] - qc[:, synth.VMAX]) < 1.0)
