@@ -345,10 +345,12 @@ def run_survey(gbk, torch, n, n_plain, device):
                    "tuning": best, "shapes_ms": shapes,
                    "note": "time per call: cached plan, geometry-table upload, counter reset and the fused "
                            "launch(es); tuning = the survey autotuner's choice, used by the fits below"}
-    for name, mode, jac, sub in (("batched_tangent", gbk.LM_BATCHED, gbk.JAC_TANGENT, n),
-                                 ("batched_fd", gbk.LM_BATCHED, gbk.JAC_FD_FORWARD, n),
-                                 ("plain_fd", gbk.LM_PLAIN, gbk.JAC_FD_FORWARD, n_plain)):
-        opts = gbk.lm_opts(max_iter=200, jacobian=jac, mode=mode, free=FIT_FREE)
+    for name, mode, jac, sub, path in (("batched_tangent", gbk.LM_BATCHED, gbk.JAC_TANGENT, n, gbk.PATH_AUTO),
+                                       ("batched_tangent_cluster_kernels", gbk.LM_BATCHED, gbk.JAC_TANGENT, n,
+                                        gbk.PATH_FUSED),
+                                       ("batched_fd", gbk.LM_BATCHED, gbk.JAC_FD_FORWARD, n, gbk.PATH_AUTO),
+                                       ("plain_fd", gbk.LM_PLAIN, gbk.JAC_FD_FORWARD, n_plain, gbk.PATH_AUTO)):
+        opts = gbk.lm_opts(max_iter=200, jacobian=jac, mode=mode, free=FIT_FREE, path=path)
         gbk.survey_fit_lm(geoms[:4], obs[:4], p0[:4], lo[:4], hi[:4], opts, device=device)  # warm-up
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -363,11 +365,12 @@ def run_survey(gbk, torch, n, n_plain, device):
                      "converged_frac": float(np.mean(np.isin(st, [1, 2]))),
                      "recovered_frac": float(np.mean((dv < 2.0) & (dpa < 1.0))),
                      "median_dvmax": float(np.median(dv)), "median_dpa": float(np.median(dpa))}
-    for name in ("batched_tangent", "batched_fd"):
+    for name in ("batched_tangent", "batched_tangent_cluster_kernels", "batched_fd"):
         out[name]["speedup_vs_plain"] = out[name]["fits_per_s"] / out["plain_fd"]["fits_per_s"]
-    out["batched_tangent"]["note"] = ("analytic Jacobian kernel for the galaxies whose halo rows fit a CTA's "
-                                      "shared memory (up to about 64 px at PSF 4 px), finite differences for the "
-                                      "wider ones")
+    out["batched_tangent"]["note"] = ("every galaxy on the ragged two-stage analytic Jacobian; trial points on the "
+                                      "survey's cluster evaluator")
+    out["batched_tangent_cluster_kernels"]["note"] = ("cluster Jacobian kernel for the galaxies whose halo rows fit "
+                                                      "a CTA's shared memory, finite differences for the wider ones")
     return out
 
 
