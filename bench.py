@@ -65,10 +65,11 @@ UNFOLDED_FP32_PER_DATA_VOXEL = 47.0
 # reported only for a run at that tuning and with that kernel build.
 FUSED_TRAFFIC_400 = {(12, 512, 0): 1433600.0, (12, 512, 1): 1318400.0}
 # DRAM bytes (read + write) of one launch of the split path's line stage
-# (80 Fabry-Perot models, the chunk of a 400-model step), as measured by a
-# one-pass ncu capture of `bench.py --quick --steps 5 --warmup 2` on a GB300:
-# 35 020 B read + 5 683 B written; reported only for the 400-model step.
-SPLIT_LINE_TRAFFIC_80 = 40704.0
+# (80 Fabry-Perot models, the chunk of a 400-model step, 10 rows per CTA),
+# the mean of five launches of a one-pass ncu capture of `bench.py --quick
+# --steps 5 --warmup 2` on a GB300: 40 192 B read + 111 002 B written;
+# reported only for the 400-model step.
+SPLIT_LINE_TRAFFIC_80 = 151194.0
 FLUSH_BYTES = 256 << 20
 
 
