@@ -361,11 +361,15 @@ def test_survey_fit_tail_is_the_degeneracy_valley(G):
 
 def test_survey_jacobian_equals_single_geometry_calls(G):
     """The ragged split Jacobian of a survey batch (galaxies of different
-    size, band and LSF, wide ones included) equals, galaxy by galaxy and bit
-    for bit, the single-geometry split Jacobian of that galaxy alone."""
+    size, band, LSF and PSF, wide ones included, the PSF radii in separate
+    chunks) equals, galaxy by galaxy and bit for bit, the single-geometry
+    split Jacobian of that galaxy alone."""
     rng = np.random.default_rng(61)
     gal = synth.draw_survey(rng, 10) + [(Geometry(96, 96, 40, 20.0, 0.0, 4.0, 30.0), None),
-                                        (Geometry(72, 80, 33, 25.0, 0.0, 4.0, 40.0), None)]
+                                        (Geometry(72, 80, 33, 25.0, 0.0, 4.0, 40.0), None),
+                                        (Geometry(31, 27, 40, 15.0, 0.0, 2.5, 45.0), None),
+                                        (Geometry(17, 17, 33, 25.0, 10.0, 3.0, 20.0, lsf_mode=1), None),
+                                        (Geometry(40, 36, 48, 12.0, 0.0, 2.5, 60.0), None)]
     geoms = [g for g, _ in gal]
     ps = np.array([p if p is not None else truth_for(g, rng) for g, p in gal])
     p0 = np.array([synth.perturb(rng, p, synth.FREE_DEFAULT, 0.1) for p in ps])
