@@ -51,7 +51,7 @@ constexpr int kTsPlanes = 3 * kTsNT + 1;       // and the centres
 constexpr int kTsTX = 32, kTsTY = 16;          // data spaxels per stage-B tile
 constexpr int kTsEnt = kTsNP * (kTsNP + 1) / 2 + kTsNP + 1;  // J^T J upper triangle, J^T v, sum r^2
 constexpr size_t kTsL2Budget = (size_t)48 << 20;
-constexpr size_t kTsSmemA = (size_t)100 * 1024;  // shared-memory target of a stage-A CTA
+constexpr size_t kTsSmemA = (size_t)72 * 1024;   // shared-memory target of a stage-A CTA (three per SM)
 constexpr int kTsplitMaxRA = 12;               // most extended rows per stage-A CTA
 constexpr long kTsWaitLimit = 1L << 18;        // tries: about one second
 
@@ -268,7 +268,7 @@ __device__ __forceinline__ float tangent_spaxel(const Geom &g, const ModelConst 
 // ---------------------------------------------------------------------------
 // Stage A: triplets of a.ra extended rows, then their x pass.
 template <int R, bool RAG>
-__global__ void __launch_bounds__(kTsThreads, 2) tsplit_line_kernel(TsArgs a)
+__global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
 {
     constexpr int W = 2 * R + 1;
     constexpr int NIN = 4 + 2 * R;      // inputs of four consecutive outputs
