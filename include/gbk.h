@@ -288,11 +288,17 @@ GBK_API gbk_status gbk_jacobian_ws(const gbk_geom *g, int32_t n_models, const do
  * parameter, box constraints, one galaxy at a time; the model evaluations run
  * on the GPU.  Here the damped normal equations
  *     (J^T J + lambda diag(J^T J)) delta = -J^T r
- * are formed and solved in FP64; a step is accepted when it lowers chi2
- * (lambda /= 10, floor 1e-12), otherwise lambda *= 10; parameters are
- * clipped to [lo, hi].  A galaxy stops when an accepted step lowers chi2 by
- * less than ftol (relative), when |delta| <= xtol (|p| + xtol), when lambda
- * exceeds 1e12, or after max_iter iterations.
+ * are formed and solved in FP64; parameters are clipped to [lo, hi]; a step
+ * is accepted when it does not raise chi2.  lambda follows the gain ratio
+ * rho of the actual to the predicted chi2 decrease (-2 s.J^T r - s.J^T J s
+ * for the clipped step s; mpfit steers its step by the same ratio): on
+ * acceptance lambda *= max(1/10, 1 - (2 rho - 1)^3) (floor 1e-12) and
+ * nu = 2, on rejection lambda *= nu and nu *= 2 (Nielsen's rule).  After a
+ * rejected step the Jacobian at the unchanged point is reused.  A galaxy
+ * stops when an accepted step lowers chi2 by less than ftol (relative),
+ * when |delta| <= xtol (|p| + xtol), when lambda exceeds 1e12, or after
+ * max_iter iterations (an iteration: one damped solve and one trial
+ * evaluation, plus the Jacobian when the last step was accepted).
  * ------------------------------------------------------------------------ */
 #define GBK_JAC_FD_FORWARD  0  /* (r(p + h e_j) - r(p)) / h, h = fd_step[j]        */
 #define GBK_JAC_FD_CENTRAL  1  /* (r(p + h e_j) - r(p - h e_j)) / 2h               */
@@ -312,7 +318,7 @@ GBK_API gbk_status gbk_jacobian_ws(const gbk_geom *g, int32_t n_models, const do
 #define GBK_FIT_NONFINITE  5  /* chi2 at the current parameters is not finite   */
 
 typedef struct gbk_lm_opts {
-    int32_t max_iter;          /* iterations (each: Jacobian, solve, trial)       */
+    int32_t max_iter;          /* iterations (each: solve, trial; + Jacobian)     */
     int32_t jacobian;          /* GBK_JAC_*                                      */
     int32_t mode;              /* GBK_LM_*                                       */
     uint32_t free_mask;        /* bit k set: parameter k is fitted (1..10 bits)  */

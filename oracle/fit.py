@@ -7,8 +7,16 @@ details it leaves open are read as follows:
     taken backwards;
   - damping: solve (J^T J + lambda diag(J^T J)) delta = -J^T r by Cholesky;
     if that fails, lambda *= 10 and retry;
-  - trial point clipped to [lo, hi]; accepted when chi2 does not increase
-    (lambda /= 10, floor 1e-12), otherwise lambda *= 10;
+  - trial point clipped to [lo, hi]; accepted when chi2 does not increase;
+  - lambda follows the gain ratio rho = (chi2(p) - chi2(p + s)) / (predicted
+    decrease of the linearised model, -2 s.J^T r - s.J^T J s) of the clipped
+    step s (mpfit steers its step by the same ratio): an accepted step
+    multiplies lambda by max(1/10, 1 - (2 rho - 1)^3) (rho = 0 when the
+    predicted decrease is not positive; floor 1e-12) and resets nu = 2; a
+    rejected one multiplies it by nu and doubles nu (H. B. Nielsen's rule,
+    "Damping parameter in Marquardt's method", 1999, with a floor of 1/10
+    on the decrease);
+  - after a rejected step p is unchanged, so its Jacobian is reused;
   - stop when an accepted step lowers chi2 by less than ftol (relative), when
     |delta| <= xtol (|p| + xtol), when lambda > 1e12, or after max_iter
     iterations.
@@ -39,50 +47,57 @@ def _solve(JTJ, JTr, lam):
 
 def fit_lm(geom, obs, p0, lo, hi, free, fd_step=0.1, max_iter=200, ftol=1e-10, xtol=1e-10, lambda0=1e-3,
            central=False, nthreads=0):
-    """Returns (p, chi2, iterations, status)."""
+    """Returns (p, chi2, iterations, status).  An iteration is one damped
+    solve and one trial evaluation; the Jacobian is recomputed only after an
+    accepted step."""
     p = np.array(p0, dtype=np.float64)
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     free = list(free)
     steps = np.full(10, float(fd_step)) if np.isscalar(fd_step) else np.asarray(fd_step, dtype=np.float64)
     lam = lambda0
+    nu = 2.0
     best = np.nan
     status = 0
     it = 0
+    J = None  # Jacobian at p (None: p moved, recompute)
     while status == 0:
-        batch = [p.copy()]
-        hs = []
-        for k in free:
-            h = steps[k]
-            q = p.copy()
-            if central:
-                q[k] = p[k] + h
-                batch.append(q)
-                hs.append(2 * h)
-            else:
-                if p[k] + h > hi[k] and p[k] - h >= lo[k]:
-                    h = -h
-                q[k] = p[k] + h
-                batch.append(q)
-                hs.append(h)
-        if central:
+        if J is None:
+            batch = [p.copy()]
+            hs = []
             for k in free:
+                h = steps[k]
                 q = p.copy()
-                q[k] = p[k] - steps[k]
-                batch.append(q)
-        c, r = chi2_batch(geom, np.array(batch), obs, want_resid=True, nthreads=nthreads)
+                if central:
+                    q[k] = p[k] + h
+                    batch.append(q)
+                    hs.append(2 * h)
+                else:
+                    if p[k] + h > hi[k] and p[k] - h >= lo[k]:
+                        h = -h
+                    q[k] = p[k] + h
+                    batch.append(q)
+                    hs.append(h)
+            if central:
+                for k in free:
+                    q = p.copy()
+                    q[k] = p[k] - steps[k]
+                    batch.append(q)
+            c, r = chi2_batch(geom, np.array(batch), obs, want_resid=True, nthreads=nthreads)
+            cc = c[0]
+            if not np.isfinite(cc):
+                it += 1
+                status = NONFINITE
+                break
+            r0 = r[0].ravel()
+            nf = len(free)
+            if central:
+                J = np.stack([(r[1 + j].ravel() - r[1 + nf + j].ravel()) / hs[j] for j in range(nf)], axis=1)
+            else:
+                J = np.stack([(r[1 + j].ravel() - r0) / hs[j] for j in range(nf)], axis=1)
+            JTJ, JTr = J.T @ J, J.T @ r0
         it += 1
-        cc = c[0]
-        if not np.isfinite(cc):
-            status = NONFINITE
-            break
-        r0 = r[0].ravel()
-        nf = len(free)
-        if central:
-            J = np.stack([(r[1 + j].ravel() - r[1 + nf + j].ravel()) / hs[j] for j in range(nf)], axis=1)
-        else:
-            J = np.stack([(r[1 + j].ravel() - r0) / hs[j] for j in range(nf)], axis=1)
-        d, lam = _solve(J.T @ J, J.T @ r0, lam)
+        d, lam = _solve(JTJ, JTr, lam)
         ct = np.nan
         dn = pn = 0.0
         pt = p.copy()
@@ -94,16 +109,22 @@ def fit_lm(geom, obs, p0, lo, hi, free, fd_step=0.1, max_iter=200, ftol=1e-10, x
             if dn > 0:
                 ct = chi2_batch(geom, pt[None], obs, nthreads=nthreads)[0]
         if np.isfinite(ct) and ct <= cc and dn > 0:
+            s = pt[free] - p[free]
+            pred = -(2.0 * (s @ JTr) + s @ JTJ @ s)
+            rho = (cc - ct) / pred if pred > 0 else 0.0
+            lam = max(lam * max(0.1, 1.0 - (2.0 * rho - 1.0) ** 3), 1e-12)
+            nu = 2.0
             p = pt
             best = ct
-            lam = max(lam * 0.1, 1e-12)
+            J = None
             if (cc - ct) / max(cc, 1e-300) < ftol:
                 status = FTOL
             elif dn <= xtol * (pn + xtol):
                 status = XTOL
         else:
             best = cc
-            lam *= 10.0
+            lam *= nu
+            nu *= 2.0
             if lam > 1e12:
                 status = LAMBDA
         if status == 0 and it >= max_iter:

@@ -13,7 +13,7 @@ namespace gbk {
 __global__ void lm_build_fd_kernel(LmArgs a)
 {
     int gal = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gal >= a.n_gal || a.done[gal]) return;
+    if (gal >= a.n_gal || a.jskip[gal]) return;
     const double *p = a.params + (size_t)gal * GBK_NPAR;
     const double *hi = a.hi + (size_t)gal * GBK_NPAR;
     const double *lo = a.lo + (size_t)gal * GBK_NPAR;
@@ -43,7 +43,7 @@ template <int NP>
 __global__ void __launch_bounds__(256) lm_normal_fd_kernel(LmArgs a)
 {
     const int gal = blockIdx.x;
-    if (a.done[gal]) return;
+    if (a.jskip[gal]) return;
     constexpr int NT = NP * (NP + 1) / 2;
     size_t n2, base;
     if (a.pix_off) {
@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(256) lm_normal_fd_kernel(LmArgs a)
 
 // ----------------------------------------------------------------------------
 // Damped solve and trial point; one thread per galaxy.  A Cholesky failure
-// raises lambda tenfold and retries.
+// raises lambda tenfold and retries.  Also the chi2 decrease the linearised
+// model predicts for the (box-clipped) step, for the gain ratio.
 template <int NP>
 __global__ void lm_solve_kernel(LmArgs a)
 {
@@ -137,6 +138,7 @@ __global__ void lm_solve_kernel(LmArgs a)
     if (!ok) {  // no usable damping: the trial equals p and will be rejected
         a.dnorm[gal] = 0.0;
         a.pnorm[gal] = 1.0;
+        a.pred[gal] = 0.0;
         return;
     }
     // forward then back substitution: L L^T d = -JTr
@@ -151,7 +153,7 @@ __global__ void lm_solve_kernel(LmArgs a)
         for (int q = j + 1; q < NP; ++q) v -= L[q][j] * d[q];
         d[j] = v / L[j][j];
     }
-    double dn = 0.0, pn = 0.0;
+    double dn = 0.0, pn = 0.0, s[NP];
     for (int j = 0; j < NP; ++j) {
         int k = a.free_idx[j];
         double lo = a.lo[(size_t)gal * GBK_NPAR + k], hi = a.hi[(size_t)gal * GBK_NPAR + k];
@@ -159,9 +161,19 @@ __global__ void lm_solve_kernel(LmArgs a)
         v = v < lo ? lo : (v > hi ? hi : v);
         double step = v - p[k];
         pt[k] = v;
+        s[j] = step;
         dn += step * step;
         pn += p[k] * p[k];
     }
+    // predicted chi2 decrease of the clipped step s: -(2 s.J^T r + s.J^T J s)
+    double sg = 0.0, sas = 0.0;
+    for (int j = 0; j < NP; ++j) {
+        sg += s[j] * JTr[j];
+        double as = 0.0;
+        for (int k = 0; k < NP; ++k) as += JTJ[j * NP + k] * s[k];
+        sas += s[j] * as;
+    }
+    a.pred[gal] = -(2.0 * sg + sas);
     a.dnorm[gal] = sqrt(dn);
     a.pnorm[gal] = sqrt(pn);
 }
@@ -173,29 +185,45 @@ __global__ void lm_accept_kernel(LmArgs a)
     if (gal >= a.n_gal || a.done[gal]) return;
     double cc = a.chi2_cur[gal], ct = a.chi2_trial[gal];
     int st = GBK_FIT_RUNNING;
+    bool accepted = false;
     int it = a.iters[gal] + 1;
     a.iters[gal] = it;
     if (!isfinite(cc)) {
         st = GBK_FIT_NONFINITE;
     } else if (isfinite(ct) && ct <= cc && a.dnorm[gal] > 0.0) {
+        accepted = true;
         double *p = a.params + (size_t)gal * GBK_NPAR;
         const double *pt = a.ptrial + (size_t)gal * GBK_NPAR;
         for (int k = 0; k < GBK_NPAR; ++k) p[k] = pt[k];
         a.chi2_best[gal] = ct;
         a.chi2_cur[gal] = ct;
-        double lam = a.lambda[gal] * 0.1;
+        // gain ratio of the actual to the predicted decrease (0 when none is
+        // predicted); lambda x max(1/10, 1 - (2 rho - 1)^3), floor 1e-12
+        const double pr = a.pred[gal];
+        const double rho = pr > 0.0 ? (cc - ct) / pr : 0.0;
+        const double q = 2.0 * rho - 1.0;
+        double lam = a.lambda[gal] * fmax(0.1, 1.0 - q * q * q);
         a.lambda[gal] = lam < 1e-12 ? 1e-12 : lam;
+        a.nu[gal] = 2.0;
         double rel = (cc - ct) / (cc > 1e-300 ? cc : 1e-300);
         if (rel < a.ftol) st = GBK_FIT_FTOL;
         else if (a.dnorm[gal] <= a.xtol * (a.pnorm[gal] + a.xtol)) st = GBK_FIT_XTOL;
     } else {
         a.chi2_best[gal] = cc;
-        double lam = a.lambda[gal] * 10.0;
+        // rejected: lambda x nu, nu doubles
+        const double nu = a.nu[gal];
+        double lam = a.lambda[gal] * nu;
         a.lambda[gal] = lam;
+        a.nu[gal] = 2.0 * nu;
         if (lam > 1e12) st = GBK_FIT_LAMBDA;
     }
     if (st == GBK_FIT_RUNNING && it >= a.max_iter) st = GBK_FIT_MAXITER;
     a.status[gal] = st;
+    // A rejected step leaves params, and so J^T J, J^T r and chi2_cur, as
+    // they were: the next iteration's Jacobian stage skips the galaxy and
+    // its solve reuses them with the larger lambda (the values a new
+    // Jacobian would give, bit for bit: its kernels are deterministic).
+    a.jskip[gal] = (st != GBK_FIT_RUNNING || !accepted) ? 1 : 0;
     if (st != GBK_FIT_RUNNING) a.done[gal] = 1;
     else atomicAdd(a.n_active, 1);
 }
@@ -205,9 +233,11 @@ __global__ void lm_init_kernel(LmArgs a, double lambda0)
     int gal = blockIdx.x * blockDim.x + threadIdx.x;
     if (gal >= a.n_gal) return;
     a.lambda[gal] = lambda0;
+    a.nu[gal] = 2.0;
     a.iters[gal] = 0;
     a.status[gal] = GBK_FIT_RUNNING;
     a.done[gal] = 0;
+    a.jskip[gal] = 0;
     a.chi2_best[gal] = __longlong_as_double(0x7ff8000000000000LL);
 }
 

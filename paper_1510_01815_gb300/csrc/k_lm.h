@@ -28,7 +28,12 @@ struct LmArgs {
     double *chi2_cur;        // [n_gal] chi2 at params
     double *chi2_best;       // [n_gal] chi2 at the returned parameters
     double *lambda, *dnorm, *pnorm;  // [n_gal]
+    double *pred;            // [n_gal] chi2 decrease the linearised model predicts for the trial step
+    double *nu;              // [n_gal] factor of lambda's next rise on a rejection
     int32_t *iters, *status, *done;  // [n_gal]
+    int32_t *jskip;          // [n_gal] non-zero: the Jacobian stage leaves the galaxy
+                             // alone (finished, or its last step was rejected, so
+                             // J^T J and J^T r at params are still in place)
     int32_t *n_active;       // [1] galaxies still running after the last accept
     const int64_t *pix_off;  // ragged batches: [n_gal + 1] pixel offsets (galaxy gal's
                              // residuals start at 2 m pix_off[gal]); null: np_pix each

@@ -73,8 +73,8 @@ static gbk_status lm_plan(const gbk_lm_opts *o, LmPlan *pl)
 // Workspace layout; `ng` galaxies share one batch at a time (n_gal in the
 // batched mode, 1 in the plain mode).
 struct LmLayout {
-    size_t pbatch, resid, chi2b, hstep, jtj, jtr, ptrial, chi2t, chi2cur, chi2best, lambda, dnorm, pnorm;
-    size_t iters, status, done, nact, sws, sws_bytes, total;
+    size_t pbatch, resid, chi2b, hstep, jtj, jtr, ptrial, chi2t, chi2cur, chi2best, lambda, dnorm, pnorm, pred, nu;
+    size_t iters, status, done, jskip, nact, sws, sws_bytes, total;
 };
 
 // pix_total: pixels of all ng galaxies together; split_bytes: the region the
@@ -97,9 +97,12 @@ static LmLayout lm_layout_pix(size_t pix_total, int ng, const LmPlan &pl, size_t
     L.lambda = take(sizeof(double) * ng);
     L.dnorm = take(sizeof(double) * ng);
     L.pnorm = take(sizeof(double) * ng);
+    L.pred = take(sizeof(double) * ng);
+    L.nu = take(sizeof(double) * ng);
     L.iters = take(sizeof(int32_t) * ng);
     L.status = take(sizeof(int32_t) * ng);
     L.done = take(sizeof(int32_t) * ng);
+    L.jskip = take(sizeof(int32_t) * ng);
     L.nact = take(sizeof(int32_t));
     L.sws = take(split_bytes);
     L.sws_bytes = split_bytes;
@@ -261,51 +264,55 @@ static gbk_status lm_plain(const Geom &g, int n_gal, const gbk_obs *obs, const d
     for (int gal = 0; gal < n_gal; ++gal) {
         double *p = &h_p[(size_t)gal * GBK_NPAR];
         const double *plo = &h_lo[(size_t)gal * GBK_NPAR], *phi = &h_hi[(size_t)gal * GBK_NPAR];
-        double lam = o->lambda0, best = NAN;
+        double lam = o->lambda0, nu = 2.0, best = NAN, cc = NAN;
         int it = 0, status = GBK_FIT_RUNNING;
+        bool fresh = false;  // J^T J, J^T r and cc belong to p (kept after a rejected step)
         while (status == GBK_FIT_RUNNING) {
-            // Jacobian batch
-            for (int s = 0; s < m; ++s) std::memcpy(&pb[(size_t)s * GBK_NPAR], p, sizeof(double) * GBK_NPAR);
-            for (int j = 0; j < np; ++j) {
-                int k = pl.idx[j];
-                double h = o->fd_step[k];
-                if (pl.central) {
-                    pb[(size_t)(1 + j) * GBK_NPAR + k] = p[k] + h;
-                    pb[(size_t)(1 + np + j) * GBK_NPAR + k] = p[k] - h;
-                    hs[j] = 2.0 * h;
-                } else {
-                    if (p[k] + h > phi[k] && p[k] - h >= plo[k]) h = -h;
-                    pb[(size_t)(1 + j) * GBK_NPAR + k] = p[k] + h;
-                    hs[j] = h;
+            if (!fresh) {
+                // Jacobian batch
+                for (int s = 0; s < m; ++s) std::memcpy(&pb[(size_t)s * GBK_NPAR], p, sizeof(double) * GBK_NPAR);
+                for (int j = 0; j < np; ++j) {
+                    int k = pl.idx[j];
+                    double h = o->fd_step[k];
+                    if (pl.central) {
+                        pb[(size_t)(1 + j) * GBK_NPAR + k] = p[k] + h;
+                        pb[(size_t)(1 + np + j) * GBK_NPAR + k] = p[k] - h;
+                        hs[j] = 2.0 * h;
+                    } else {
+                        if (p[k] + h > phi[k] && p[k] - h >= plo[k]) h = -h;
+                        pb[(size_t)(1 + j) * GBK_NPAR + k] = p[k] + h;
+                        hs[j] = h;
+                    }
                 }
+                if ((e = cudaMemcpyAsync(d_pb, pb.data(), sizeof(double) * pb.size(), cudaMemcpyHostToDevice, st)))
+                    return cuda_fail(e, "plain LM: batch upload");
+                gbk_status sb = fused_for(g, m, d_pb, nullptr, &h_obs[gal], m, nullptr, d_chi2b, d_res, st);
+                if (sb) return sb;
+                if ((e = cudaMemcpyAsync(res.data(), d_res, sizeof(float) * res.size(), cudaMemcpyDeviceToHost, st)) ||
+                    (e = cudaMemcpyAsync(chi2b.data(), d_chi2b, sizeof(double) * m, cudaMemcpyDeviceToHost, st)) ||
+                    (e = cudaStreamSynchronize(st)))
+                    return cuda_fail(e, "plain LM: residual download");
+                cc = chi2b[0];
+                if (!std::isfinite(cc)) { ++it; status = GBK_FIT_NONFINITE; break; }
+                std::fill(JTJ.begin(), JTJ.end(), 0.0);
+                std::fill(JTr.begin(), JTr.end(), 0.0);
+                std::vector<double> J(np);
+                for (size_t i = 0; i < n2; ++i) {
+                    double r0 = res[i];
+                    for (int j = 0; j < np; ++j) {
+                        double rm = pl.central ? res[(size_t)(1 + np + j) * n2 + i] : r0;
+                        J[j] = ((double)res[(size_t)(1 + j) * n2 + i] - rm) / hs[j];
+                    }
+                    for (int j = 0; j < np; ++j) {
+                        JTr[j] += J[j] * r0;
+                        for (int k = 0; k <= j; ++k) JTJ[j * np + k] += J[j] * J[k];
+                    }
+                }
+                for (int j = 0; j < np; ++j)
+                    for (int k = 0; k < j; ++k) JTJ[k * np + j] = JTJ[j * np + k];
+                fresh = true;
             }
-            if ((e = cudaMemcpyAsync(d_pb, pb.data(), sizeof(double) * pb.size(), cudaMemcpyHostToDevice, st)))
-                return cuda_fail(e, "plain LM: batch upload");
-            gbk_status s = fused_for(g, m, d_pb, nullptr, &h_obs[gal], m, nullptr, d_chi2b, d_res, st);
-            if (s) return s;
-            if ((e = cudaMemcpyAsync(res.data(), d_res, sizeof(float) * res.size(), cudaMemcpyDeviceToHost, st)) ||
-                (e = cudaMemcpyAsync(chi2b.data(), d_chi2b, sizeof(double) * m, cudaMemcpyDeviceToHost, st)) ||
-                (e = cudaStreamSynchronize(st)))
-                return cuda_fail(e, "plain LM: residual download");
-            double cc = chi2b[0];
             ++it;
-            if (!std::isfinite(cc)) { status = GBK_FIT_NONFINITE; break; }
-            std::fill(JTJ.begin(), JTJ.end(), 0.0);
-            std::fill(JTr.begin(), JTr.end(), 0.0);
-            std::vector<double> J(np);
-            for (size_t i = 0; i < n2; ++i) {
-                double r0 = res[i];
-                for (int j = 0; j < np; ++j) {
-                    double rm = pl.central ? res[(size_t)(1 + np + j) * n2 + i] : r0;
-                    J[j] = ((double)res[(size_t)(1 + j) * n2 + i] - rm) / hs[j];
-                }
-                for (int j = 0; j < np; ++j) {
-                    JTr[j] += J[j] * r0;
-                    for (int k = 0; k <= j; ++k) JTJ[j * np + k] += J[j] * J[k];
-                }
-            }
-            for (int j = 0; j < np; ++j)
-                for (int k = 0; k < j; ++k) JTJ[k * np + j] = JTJ[j * np + k];
             // damped solve and trial point
             std::vector<double> pt(p, p + GBK_NPAR);
             double dn = 0.0, pn = 0.0;
@@ -322,22 +329,38 @@ static gbk_status lm_plain(const Geom &g, int n_gal, const gbk_obs *obs, const d
             if (solved && dn > 0.0) {
                 if ((e = cudaMemcpyAsync(d_pt, pt.data(), sizeof(double) * GBK_NPAR, cudaMemcpyHostToDevice, st)))
                     return cuda_fail(e, "plain LM: trial upload");
-                s = fused_for(g, 1, d_pt, nullptr, &h_obs[gal], 1, nullptr, d_ct, nullptr, st);
+                gbk_status s = fused_for(g, 1, d_pt, nullptr, &h_obs[gal], 1, nullptr, d_ct, nullptr, st);
                 if (s) return s;
                 if ((e = cudaMemcpyAsync(&ct, d_ct, sizeof(double), cudaMemcpyDeviceToHost, st)) ||
                     (e = cudaStreamSynchronize(st)))
                     return cuda_fail(e, "plain LM: trial download");
             }
             if (std::isfinite(ct) && ct <= cc && dn > 0.0) {
+                // gain ratio against the linearised model's decrease
+                // -(2 s.J^T r + s.J^T J s) of the clipped step s
+                double sg = 0.0, sas = 0.0;
+                for (int j = 0; j < np; ++j) {
+                    const double sj = pt[pl.idx[j]] - p[pl.idx[j]];
+                    double as = 0.0;
+                    for (int k = 0; k < np; ++k) as += JTJ[j * np + k] * (pt[pl.idx[k]] - p[pl.idx[k]]);
+                    sg += sj * JTr[j];
+                    sas += sj * as;
+                }
+                const double pred = -(2.0 * sg + sas);
+                const double rho = pred > 0.0 ? (cc - ct) / pred : 0.0;
+                const double q = 2.0 * rho - 1.0;
+                lam = std::fmax(lam * std::fmax(0.1, 1.0 - q * q * q), 1e-12);
+                nu = 2.0;
                 std::memcpy(p, pt.data(), sizeof(double) * GBK_NPAR);
                 best = ct;
-                lam = std::fmax(lam * 0.1, 1e-12);
+                fresh = false;
                 double rel = (cc - ct) / std::fmax(cc, 1e-300);
                 if (rel < o->ftol) status = GBK_FIT_FTOL;
                 else if (std::sqrt(dn) <= o->xtol * (std::sqrt(pn) + o->xtol)) status = GBK_FIT_XTOL;
             } else {
                 best = cc;
-                lam *= 10.0;
+                lam *= nu;
+                nu *= 2.0;
                 if (lam > 1e12) status = GBK_FIT_LAMBDA;
             }
             if (status == GBK_FIT_RUNNING && it >= o->max_iter) status = GBK_FIT_MAXITER;
@@ -371,7 +394,7 @@ static gbk_status lm_iteration(const EvalTarget &t, const LmArgs &a, const gbk_o
         if (s) return s;
     } else {
         lm_launch_build_fd(a, st);
-        s = eval_for(t, a.n_gal, a.m, a.pbatch, obs, a.done, a.chi2_batch, a.resid, st);
+        s = eval_for(t, a.n_gal, a.m, a.pbatch, obs, a.jskip, a.chi2_batch, a.resid, st);
         if (s) return s;
         lm_launch_normal_fd(a, st);
     }
@@ -418,9 +441,12 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     a.lambda = (double *)(ws + L.lambda);
     a.dnorm = (double *)(ws + L.dnorm);
     a.pnorm = (double *)(ws + L.pnorm);
+    a.pred = (double *)(ws + L.pred);
+    a.nu = (double *)(ws + L.nu);
     a.iters = (int32_t *)(ws + L.iters);
     a.status = (int32_t *)(ws + L.status);
     a.done = (int32_t *)(ws + L.done);
+    a.jskip = (int32_t *)(ws + L.jskip);
     a.n_active = (int32_t *)(ws + L.nact);
 
     CudaGuard cg;
@@ -439,7 +465,7 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
         rc.d_geo = t.sp->d_geo;
         rc.params = params;
         rc.obs_list = obs;
-        rc.skip = a.done;
+        rc.skip = a.jskip;
         rc.np = pl.np;
         for (int j = 0; j < pl.np; ++j) rc.free_idx[j] = pl.idx[j];
         rc.jtj = a.jtj;
@@ -451,7 +477,7 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
         tc.n_models = n_gal;
         tc.params = params;
         tc.obs_list = obs;
-        tc.skip = a.done;
+        tc.skip = a.jskip;
         tc.np = pl.np;
         for (int j = 0; j < pl.np; ++j) tc.free_idx[j] = pl.idx[j];
         tc.jtj = a.jtj;
@@ -474,7 +500,7 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
         ta.params = params;
         ta.obs_list = obs;
         ta.models_per_gal = 1;
-        ta.skip = a.done;
+        ta.skip = a.jskip;
         ta.jtj = a.jtj;
         ta.jtv = a.jtr;
         // chi2 at the start point from the evaluator: accept/reject

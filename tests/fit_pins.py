@@ -6,7 +6,10 @@ violated.  They test it against what fixes the answer independently:
   LM   -- noiseless data has its chi2 minimum at the truth (Sec. 4.1's
           thresholds from perturbed starts); with only V_sys free the
           residual is linear in it, so the first (lightly damped) step is
-          exact; an optimum outside the box ends on the box's face;
+          exact and the gain ratio is 1 (lambda / 10 per step: a closed
+          form for the offset); a fully masked galaxy rejects every step
+          (lambda x 2, 4, 8, ...: the stop at a known iteration); an optimum
+          outside the box ends on the box's face;
   NG   -- a truth placed on a node is the unique zero-chi2 node, at its
           row-major index; every node's chi2 is the direct evaluation at the
           node's value; invalid (NaN) nodes lose to finite ones; the next
@@ -96,6 +99,38 @@ def pin_lm_central_differences_solve_the_linear_problem(fit):
     p0[synth.VSYS] = 25.0
     q, c, it, st = fit.fit_lm(ogeom(g), obs, p0, lo, hi, [synth.VSYS], max_iter=1, fd_step=0.1, central=True)
     assert abs(q[synth.VSYS]) < 25.0 * 2e-3, q[synth.VSYS]
+
+
+def pin_lm_gain_ratio_on_a_linear_problem(fit):
+    """With only V_sys free the residual is linear in it, so the linearised
+    model predicts each step's chi2 decrease exactly: the gain ratio is 1 and
+    every step divides lambda by ten.  A damped step from offset x leaves
+    x lambda / (1 + lambda), so from lambda0 = 1e4 six steps leave
+    25 prod_j lambda_j / (1 + lambda_j) km/s, lambda_j = 1e4 / 10^j (1.02 km/s;
+    a damping that stayed at 1e4 would leave 24.99)."""
+    g, p, obs = galaxy(noise_v=0.0)
+    lo, hi = bounds(p)
+    p0 = p.copy()
+    p0[synth.VSYS] = p[synth.VSYS] + 25.0
+    q, c, it, st = fit.fit_lm(ogeom(g), obs, p0, lo, hi, [synth.VSYS], max_iter=6, fd_step=0.1, lambda0=1e4)
+    lam = 1e4 / 10.0 ** np.arange(6)
+    want = 25.0 * np.prod(lam / (1.0 + lam))
+    assert it == 6, (it, st)
+    assert abs((q[synth.VSYS] - p[synth.VSYS]) - want) < 1e-4 * want + 1e-5, (q[synth.VSYS] - p[synth.VSYS], want)
+
+
+def pin_lm_masked_galaxy_rejects_every_step(fit):
+    """Every spaxel masked: chi2 is 0 whatever the parameters, J = 0, the
+    damped step is zero and every trial is rejected, so lambda grows by nu =
+    2, 4, 8, ... from 1e-3: 1e-3 x 2^(k (k + 1) / 2) first exceeds 1e12 at
+    the 10th iteration, where the fit stops (status LAMBDA) at its start."""
+    g, p, obs = galaxy(noise_v=0.0)
+    obs = oracle.Obs(obs.v, obs.s, obs.w_v, obs.w_s, np.zeros_like(obs.mask))
+    lo, hi = bounds(p)
+    p0 = starts(p, 1, seed=5)[0]
+    q, c, it, st = fit.fit_lm(ogeom(g), obs, p0, lo, hi, FREE, max_iter=50, lambda0=1e-3)
+    assert (it, st) == (10, 4), (it, st)
+    assert np.array_equal(q, p0)
 
 
 def pin_lm_optimum_outside_the_box_ends_on_its_face(fit):
@@ -228,6 +263,7 @@ def pin_sampler_outside_the_domain_has_zero_likelihood(fit):
 
 ALL_FIT_PINS = [pin_splitmix64_reference_values, pin_sampler_gaussian_evidence,
                 pin_lm_solves_a_linear_problem_in_one_step, pin_lm_central_differences_solve_the_linear_problem,
+                pin_lm_masked_galaxy_rejects_every_step, pin_lm_gain_ratio_on_a_linear_problem,
                 pin_grid_row_major_order, pin_grid_invalid_nodes_lose,
                 pin_lm_optimum_outside_the_box_ends_on_its_face, pin_lm_recovers_noiseless_parameters,
                 pin_grid_finds_truth_on_a_node, pin_sampler_trace_replays,

@@ -20,7 +20,12 @@ MUTANTS = [
     ("lm_central_step_not_doubled", "hs.append(2 * h)", "hs.append(h)"),
     ("lm_central_minus_side_forward", "q[k] = p[k] - steps[k]", "q[k] = p[k] + steps[k]"),
     ("lm_trial_not_clipped", "pt[k] = min(max(p[k] + d[j], lo[k]), hi[k])", "pt[k] = p[k] + d[j]"),
-    ("lm_damping_grows_on_success", "lam = max(lam * 0.1, 1e-12)", "lam = lam * 10.0"),
+    ("lm_damping_grows_on_success", "lam = max(lam * max(0.1, 1.0 - (2.0 * rho - 1.0) ** 3), 1e-12)",
+     "lam = lam * 10.0"),
+    ("lm_predicted_decrease_sign", "pred = -(2.0 * (s @ JTr) + s @ JTJ @ s)", "pred = 2.0 * (s @ JTr) + s @ JTJ @ s"),
+    ("lm_predicted_decrease_drops_curvature", "pred = -(2.0 * (s @ JTr) + s @ JTJ @ s)", "pred = -(2.0 * (s @ JTr))"),
+    ("lm_rejection_factor_fixed", "            nu *= 2.0\n", "            nu *= 1.0\n"),
+    ("lm_rejection_tenfold", "            lam *= nu\n", "            lam *= 10.0\n"),
     ("grid_nan_not_worst", "key = np.where(np.isnan(c), np.inf, c)", "key = c"),
     ("grid_column_major", "mesh = np.meshgrid(*grids, indexing=\"ij\")", "mesh = np.meshgrid(*grids, indexing=\"xy\")"),
     ("grid_steps_off_by_one", "steps = {k: (chi[k] - clo[k]) / (nodes[k] - 1) for k in axes}",

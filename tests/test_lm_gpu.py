@@ -161,3 +161,26 @@ def test_lm_path_choice_is_checked(G):
                             G.lm_opts(max_iter=100, jacobian=2, free=FREE))
     assert np.all(np.isin(st, [1, 2])), st
     assert np.all(np.abs(q[:, synth.VMAX] - p[synth.VMAX]) < 2.0)
+
+
+@pytest.mark.parametrize("mode,jac", [(0, 0), (0, 1), (1, 0)])
+def test_fully_masked_galaxy_rejects_every_step(G, mode, jac):
+    """Every spaxel masked: chi2 is 0 at any point and J = 0, so the damped
+    step is zero and every trial is rejected; lambda grows by nu = 2, 4, 8,
+    ... from 1e-3 and first exceeds 1e12 at the 10th iteration (as the
+    oracle's pin), where the fit stops with status LAMBDA at its start.  Its
+    neighbours in the batch fit as usual."""
+    g, p, obs = galaxy(noise_v=0.0)
+    lo, hi = bounds(p)
+    blind = oracle.Obs(obs.v, obs.s, obs.w_v, obs.w_s, np.zeros_like(obs.mask))
+    n = 3 if mode == 0 else 1
+    p0 = starts(p, n, seed=5)
+    obs_l = [_dobs(G, blind)] + [_dobs(G, obs)] * (n - 1)
+    opts = G.lm_opts(max_iter=100, jacobian=jac, mode=mode, free=FREE, lambda0=1e-3)
+    q, c, it, st = G.fit_lm(g, obs_l, p0, [lo] * n, [hi] * n, opts)
+    assert (it[0], st[0]) == (10, 4), (it, st)
+    np.testing.assert_array_equal(q[0], p0[0])
+    assert c[0] == 0.0, c
+    if n > 1:
+        assert np.all(np.isin(st[1:], [1, 2])), st
+        assert np.all(np.abs(q[1:, synth.VMAX] - p[synth.VMAX]) < 2.0)
