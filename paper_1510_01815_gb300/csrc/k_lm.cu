@@ -242,6 +242,48 @@ __global__ void lm_init_kernel(LmArgs a, double lambda0)
 }
 
 // ----------------------------------------------------------------------------
+__global__ void lm_compact_kernel(LmCompactArgs c)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c.n_live) return;
+    const int s = c.live[j];
+    for (int k = 0; k < GBK_NPAR; ++k) {
+        c.params_n[(size_t)j * GBK_NPAR + k] = c.params[(size_t)s * GBK_NPAR + k];
+        c.lo_n[(size_t)j * GBK_NPAR + k] = c.lo[(size_t)s * GBK_NPAR + k];
+        c.hi_n[(size_t)j * GBK_NPAR + k] = c.hi[(size_t)s * GBK_NPAR + k];
+    }
+    c.obs_n[j] = c.obs[s];
+    c.map_n[j] = c.map ? c.map[s] : s;
+    c.lambda_n[j] = c.lambda[s];
+    c.nu_n[j] = c.nu[s];
+    c.chi2_cur_n[j] = c.chi2_cur[s];
+    c.iters_n[j] = c.iters[s];
+}
+
+__global__ void lm_scatter_kernel(LmScatterArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int o = a.map ? a.map[i] : i;
+    if (a.params_out)
+        for (int k = 0; k < GBK_NPAR; ++k)
+            a.params_out[(size_t)o * GBK_NPAR + k] = a.params[(size_t)i * GBK_NPAR + k];
+    a.chi2_out[o] = a.chi2_best[i];
+    a.iters_out[o] = a.iters[i];
+    a.status_out[o] = a.status[i];
+}
+
+void lm_launch_compact(const LmCompactArgs &c, cudaStream_t st)
+{
+    if (c.n_live > 0) lm_compact_kernel<<<(c.n_live + 127) / 128, 128, 0, st>>>(c);
+}
+
+void lm_launch_scatter(const LmScatterArgs &s, cudaStream_t st)
+{
+    if (s.n > 0) lm_scatter_kernel<<<(s.n + 127) / 128, 128, 0, st>>>(s);
+}
+
+// ----------------------------------------------------------------------------
 template <int NP>
 static void launch_np(const LmArgs &a, int which, cudaStream_t st)
 {

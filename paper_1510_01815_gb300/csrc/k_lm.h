@@ -39,6 +39,39 @@ struct LmArgs {
                              // residuals start at 2 m pix_off[gal]); null: np_pix each
 };
 
+// Tail compaction of a batch of one geometry: the running galaxies (current
+// slots live[0 .. n_live), increasing) move to slots 0 .. n_live of the next
+// buffers with the state that outlives an iteration; everything else is
+// recomputed (their Jacobian too: the kernels are deterministic, so it is
+// the one they hold).
+struct LmCompactArgs {
+    int n_live;
+    const int32_t *live;                  // [n_live]
+    const int32_t *map;                   // [n_cur] slot -> caller index, or null (identity)
+    const double *params, *lo, *hi;       // current [n_cur][NPAR]
+    const gbk_obs *obs;                   // current [n_cur]
+    const double *lambda, *nu, *chi2_cur; // current [n_cur]
+    const int32_t *iters;                 // current [n_cur]
+    double *params_n, *lo_n, *hi_n;       // next [n_live][NPAR]
+    gbk_obs *obs_n;                       // next [n_live]
+    int32_t *map_n;                       // next [n_live]
+    double *lambda_n, *nu_n, *chi2_cur_n; // next [n_live] (copied back by the caller)
+    int32_t *iters_n;                     // next [n_live]
+};
+
+// Writes the results of slots 0 .. n (finished or not) to the caller's
+// arrays at map[slot]; params too when params_out is not null.
+struct LmScatterArgs {
+    int n;
+    const int32_t *map;
+    const double *params, *chi2_best;
+    const int32_t *iters, *status;
+    double *params_out, *chi2_out;
+    int32_t *iters_out, *status_out;
+};
+
+void lm_launch_compact(const LmCompactArgs &c, cudaStream_t st);
+void lm_launch_scatter(const LmScatterArgs &s, cudaStream_t st);
 void lm_launch_init(const LmArgs &a, double lambda0, cudaStream_t st);
 void lm_launch_build_fd(const LmArgs &a, cudaStream_t st);
 void lm_launch_normal_fd(const LmArgs &a, cudaStream_t st);

@@ -36,6 +36,7 @@
 namespace gbk {
 
 constexpr int kPoll = 8;
+constexpr int kCompactMin = 32;  // smallest batch of one geometry that is compacted
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -75,6 +76,9 @@ static gbk_status lm_plan(const gbk_lm_opts *o, LmPlan *pl)
 struct LmLayout {
     size_t pbatch, resid, chi2b, hstep, jtj, jtr, ptrial, chi2t, chi2cur, chi2best, lambda, dnorm, pnorm, pred, nu;
     size_t iters, status, done, jskip, nact, sws, sws_bytes, total;
+    // tail compaction (one geometry): two sets of the moved per-galaxy
+    // inputs, the running slots, and the moved state
+    size_t cpar[2], clo[2], chi[2], cobs[2], cmap[2], clive, nlam, nnu, ncc, nit;
 };
 
 // pix_total: pixels of all ng galaxies together; split_bytes: the region the
@@ -104,6 +108,18 @@ static LmLayout lm_layout_pix(size_t pix_total, int ng, const LmPlan &pl, size_t
     L.done = take(sizeof(int32_t) * ng);
     L.jskip = take(sizeof(int32_t) * ng);
     L.nact = take(sizeof(int32_t));
+    for (int b = 0; b < 2; ++b) {
+        L.cpar[b] = take(sizeof(double) * ng * GBK_NPAR);
+        L.clo[b] = take(sizeof(double) * ng * GBK_NPAR);
+        L.chi[b] = take(sizeof(double) * ng * GBK_NPAR);
+        L.cobs[b] = take(sizeof(gbk_obs) * ng);
+        L.cmap[b] = take(sizeof(int32_t) * ng);
+    }
+    L.clive = take(sizeof(int32_t) * ng);
+    L.nlam = take(sizeof(double) * ng);
+    L.nnu = take(sizeof(double) * ng);
+    L.ncc = take(sizeof(double) * ng);
+    L.nit = take(sizeof(int32_t) * ng);
     L.sws = take(split_bytes);
     L.sws_bytes = split_bytes;
     L.total = o;
@@ -516,6 +532,12 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     int done_iters = 1;
     int planned = n_gal;   // galaxies of the current ragged Jacobian plan
     TsRaggedPlan live;     // its re-plan over the running galaxies
+    // one geometry: galaxies in slots 0 .. n_cur; after a compaction the
+    // inputs live in the workspace and cmap gives each slot's caller index
+    int n_cur = n_gal, flip = 0;
+    bool compacted = false;
+    const gbk_obs *obs_cur = obs;
+    std::vector<int32_t> h_flags, h_live;
     if (o->max_iter > 1) {
         if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
             return cuda_fail(e, "LM: begin graph capture");
@@ -534,6 +556,87 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
                 (e = cudaStreamSynchronize(st)))
                 return cuda_fail(e, "LM: polling");
             if (h_active == 0) break;
+            if (!t.sp && h_active * 4 <= n_cur && n_cur >= kCompactMin) {
+                // Finished galaxies' CTAs only return at their skip test, but
+                // at thousands per launch those returns cost most of a tail
+                // iteration: move the running galaxies to the front of fresh
+                // buffers and capture the iteration again for them alone.
+                h_flags.resize(n_cur);
+                if ((e = cudaMemcpyAsync(h_flags.data(), a.done, sizeof(int32_t) * n_cur, cudaMemcpyDeviceToHost,
+                                         st)) ||
+                    (e = cudaStreamSynchronize(st)))
+                    return cuda_fail(e, "LM: reading the running galaxies");
+                h_live.clear();
+                for (int i = 0; i < n_cur; ++i)
+                    if (h_flags[i] == 0) h_live.push_back(i);
+                const int n_live = (int)h_live.size();
+                const int nb = flip ^ 1;
+                int32_t *d_live = (int32_t *)(ws + L.clive);
+                if ((e = cudaMemcpyAsync(d_live, h_live.data(), sizeof(int32_t) * n_live, cudaMemcpyHostToDevice,
+                                         st)))
+                    return cuda_fail(e, "LM: uploading the running galaxies");
+                const int32_t *map = compacted ? (const int32_t *)(ws + L.cmap[flip]) : nullptr;
+                LmScatterArgs sc = {n_cur, map, a.params, a.chi2_best, a.iters, a.status,
+                                    compacted ? params : nullptr, chi2_out, iters_out, status_out};
+                lm_launch_scatter(sc, st);
+                LmCompactArgs cp = {};
+                cp.n_live = n_live;
+                cp.live = d_live;
+                cp.map = map;
+                cp.params = a.params;
+                cp.lo = a.lo;
+                cp.hi = a.hi;
+                cp.obs = obs_cur;
+                cp.lambda = a.lambda;
+                cp.nu = a.nu;
+                cp.chi2_cur = a.chi2_cur;
+                cp.iters = a.iters;
+                cp.params_n = (double *)(ws + L.cpar[nb]);
+                cp.lo_n = (double *)(ws + L.clo[nb]);
+                cp.hi_n = (double *)(ws + L.chi[nb]);
+                cp.obs_n = (gbk_obs *)(ws + L.cobs[nb]);
+                cp.map_n = (int32_t *)(ws + L.cmap[nb]);
+                cp.lambda_n = (double *)(ws + L.nlam);
+                cp.nu_n = (double *)(ws + L.nnu);
+                cp.chi2_cur_n = (double *)(ws + L.ncc);
+                cp.iters_n = (int32_t *)(ws + L.nit);
+                lm_launch_compact(cp, st);
+                if ((e = cudaMemcpyAsync(a.lambda, cp.lambda_n, sizeof(double) * n_live, cudaMemcpyDeviceToDevice, st)) ||
+                    (e = cudaMemcpyAsync(a.nu, cp.nu_n, sizeof(double) * n_live, cudaMemcpyDeviceToDevice, st)) ||
+                    (e = cudaMemcpyAsync(a.chi2_cur, cp.chi2_cur_n, sizeof(double) * n_live, cudaMemcpyDeviceToDevice,
+                                         st)) ||
+                    (e = cudaMemcpyAsync(a.iters, cp.iters_n, sizeof(int32_t) * n_live, cudaMemcpyDeviceToDevice, st)) ||
+                    (e = cudaMemsetAsync(a.status, 0, sizeof(int32_t) * n_live, st)) ||  // GBK_FIT_RUNNING
+                    (e = cudaMemsetAsync(a.done, 0, sizeof(int32_t) * n_live, st)) ||
+                    (e = cudaMemsetAsync(a.jskip, 0, sizeof(int32_t) * n_live, st)) ||
+                    (e = cudaGetLastError()))
+                    return cuda_fail(e, "LM: compacting the running galaxies");
+                a.n_gal = n_live;
+                a.params = cp.params_n;
+                a.lo = cp.lo_n;
+                a.hi = cp.hi_n;
+                obs_cur = cp.obs_n;
+                tc.n_models = n_live;
+                tc.params = cp.params_n;
+                tc.obs_list = cp.obs_n;
+                ta.n_models = n_live;
+                ta.params = cp.params_n;
+                ta.obs_list = cp.obs_n;
+                n_cur = n_live;
+                flip = nb;
+                compacted = true;
+                cudaGraphExecDestroy(cg.exec);
+                cudaGraphDestroy(cg.graph);
+                cg.exec = nullptr;
+                cg.graph = nullptr;
+                if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed)))
+                    return cuda_fail(e, "LM: begin graph capture");
+                s = lm_iteration(t, a, obs_cur, pl.tangent, ta, tc, rc, st);
+                e = cudaStreamEndCapture(st, &cg.graph);
+                if (s) return s;
+                if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");
+                if ((e = cudaGraphInstantiate(&cg.exec, cg.graph, 0))) return cuda_fail(e, "LM: graph instantiation");
+            }
             if (t.rag && h_active * 4 <= planned && planned > 16) {
                 // Ragged split Jacobian: the finished galaxies' CTAs would only
                 // return at their skip test, so once a quarter of the planned
@@ -566,10 +669,17 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
             }
         }
     }
-    if ((e = cudaMemcpyAsync(chi2_out, a.chi2_best, sizeof(double) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
-        (e = cudaMemcpyAsync(iters_out, a.iters, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
-        (e = cudaMemcpyAsync(status_out, a.status, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
-        (e = cudaEventRecord(cg.e1, st)) || (e = cudaStreamWaitEvent(user, cg.e1, 0)) ||
+    if (compacted) {
+        LmScatterArgs sc = {n_cur, (const int32_t *)(ws + L.cmap[flip]), a.params, a.chi2_best, a.iters, a.status,
+                            params, chi2_out, iters_out, status_out};
+        lm_launch_scatter(sc, st);
+        if ((e = cudaGetLastError())) return cuda_fail(e, "LM: results");
+    } else if ((e = cudaMemcpyAsync(chi2_out, a.chi2_best, sizeof(double) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
+               (e = cudaMemcpyAsync(iters_out, a.iters, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToDevice, st)) ||
+               (e = cudaMemcpyAsync(status_out, a.status, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToDevice, st))) {
+        return cuda_fail(e, "LM: results");
+    }
+    if ((e = cudaEventRecord(cg.e1, st)) || (e = cudaStreamWaitEvent(user, cg.e1, 0)) ||
         (e = cudaStreamSynchronize(st)))
         return cuda_fail(e, "LM: results");
     return ok();

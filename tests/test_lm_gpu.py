@@ -184,3 +184,30 @@ def test_fully_masked_galaxy_rejects_every_step(G, mode, jac):
     if n > 1:
         assert np.all(np.isin(st[1:], [1, 2])), st
         assert np.all(np.abs(q[1:, synth.VMAX] - p[synth.VMAX]) < 2.0)
+
+
+@pytest.mark.parametrize("jac", [0, 1])
+def test_tail_compaction_keeps_each_fit(G, jac):
+    """When a quarter or less of a batch of one geometry is still running,
+    the running galaxies move to the front of fresh buffers and the
+    iteration is captured again for them alone.  Each galaxy's fit in a
+    batch of 96 noisy galaxies (compacted as its fits finish) equals its fit
+    in a batch of 8 (too small to compact): iterations, status, chi2 and
+    parameters."""
+    g, p, obs = galaxy(noise_v=5.0, seed=4)
+    lo, hi = bounds(p)
+    n = 96
+    p0 = starts(p, n, seed=11, frac=0.3)
+    d = _dobs(G, obs)
+    opts = G.lm_opts(max_iter=200, jacobian=jac, free=FREE)
+    q, c, it, st = G.fit_lm(g, [d] * n, p0, [lo] * n, [hi] * n, opts)
+    # the host polls after iterations 9, 17, 25, ...: one of them must see a
+    # quarter or less of the batch still running
+    polls = 1 + 8 * np.arange(1, 26)
+    assert any(0 < np.sum(it > k) <= n // 4 for k in polls), it
+    for k in range(0, n, 8):
+        q8, c8, it8, st8 = G.fit_lm(g, [d] * 8, p0[k:k + 8], [lo] * 8, [hi] * 8, opts)
+        np.testing.assert_array_equal(it[k:k + 8], it8)
+        np.testing.assert_array_equal(st[k:k + 8], st8)
+        np.testing.assert_array_equal(c[k:k + 8], c8)
+        np.testing.assert_array_equal(q[k:k + 8], q8)
