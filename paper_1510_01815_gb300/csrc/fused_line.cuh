@@ -61,6 +61,26 @@ __device__ __forceinline__ void accum_lin(float q0, float l1, float h1, float q2
     s2 = fmaf(w, i2, s2);
 }
 
+// An input (q0, q1, q2 about its centre a) moved exactly to a reference
+// velocity r shared by a thread's outputs (d = a - r): l1 = q1 + d q0 and
+// l2 = q2 + d (2 q1 + d q0), both sums of non-negative or centred terms.
+// Each output then accumulates w q0, w l1, w l2 (three FMAs per tap) and
+// moves its sums from r to its own centre once at the end (shift_sums).
+__device__ __forceinline__ void about_ref(float q0, float q1, float q2, float a, float r, float &l1, float &l2)
+{
+    const float d = a - r;
+    l1 = fmaf(d, q0, q1);
+    l2 = fmaf(d, fmaf(d, q0, q1 + q1), q2);
+}
+
+// Sums about r moved to centre c (delta = c - r): s1 - delta s0 and
+// s2 - 2 delta s1 + delta^2 s0 (exact re-centring of moment sums).
+__device__ __forceinline__ void shift_sums(float delta, float s0, float &s1, float &s2)
+{
+    s2 = fmaf(delta, fmaf(delta, s0, -2.f * s1), s2);
+    s1 = fmaf(-delta, s0, s1);
+}
+
 // Unnormalised tap and the full normalisation sum (computed by each thread
 // that needs it, so no serial section or extra barrier is required).
 __device__ __forceinline__ float tap_raw(int j, float sigma, int R)

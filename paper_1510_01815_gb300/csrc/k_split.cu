@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(kSplitThreads, 4) split_line_kernel(SplitArgs 
             cen[o] = QA[ro + o + R];
             s[o][0] = s[o][1] = s[o][2] = 0.f;
         }
+        const float ref = cen[1];  // the task's reference velocity
 #pragma unroll
         for (int c4 = 0; c4 < NC4; ++c4) {
             const float4 v0 = *reinterpret_cast<const float4 *>(Q0 + ro + 4 * c4);
@@ -171,18 +172,24 @@ __global__ void __launch_bounds__(kSplitThreads, 4) split_line_kernel(SplitArgs 
             for (int k = 0; k < 4; ++k) {
                 const int e = 4 * c4 + k;
                 if (e >= NIN) break;
-                const float l1 = fmaf(qa[k], q0[k], q1[k]), h1 = q1[k] + q1[k];
+                float l1, l2;
+                about_ref(q0[k], q1[k], q2[k], qa[k], ref, l1, l2);
 #pragma unroll
                 for (int o = 0; o < 4; ++o) {
                     const int j = e - o;
-                    if (j >= 0 && j < W) accum_lin(q0[k], l1, h1, q2[k], qa[k], cen[o], w[j], s[o][0], s[o][1], s[o][2]);
+                    if (j >= 0 && j < W) {
+                        s[o][0] = fmaf(w[j], q0[k], s[o][0]);
+                        s[o][1] = fmaf(w[j], l1, s[o][1]);
+                        s[o][2] = fmaf(w[j], l2, s[o][2]);
+                    }
                 }
             }
         }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) shift_sums(cen[o] - ref, s[o][0], s[o][1], s[o][2]);
         float *const p = P0 + (size_t)rr * a.nxp + gx;
         *reinterpret_cast<float4 *>(p) = make_float4(s[0][0], s[1][0], s[2][0], s[3][0]);
-        *reinterpret_cast<float4 *>(p + pstride) = make_float4(fmaf(-cen[0], s[0][0], s[0][1]), fmaf(-cen[1], s[1][0], s[1][1]),
-                                                               fmaf(-cen[2], s[2][0], s[2][1]), fmaf(-cen[3], s[3][0], s[3][1]));
+        *reinterpret_cast<float4 *>(p + pstride) = make_float4(s[0][1], s[1][1], s[2][1], s[3][1]);
         *reinterpret_cast<float4 *>(p + 2 * pstride) = make_float4(s[0][2], s[1][2], s[2][2], s[3][2]);
         *reinterpret_cast<float4 *>(p + 3 * pstride) = make_float4(cen[0], cen[1], cen[2], cen[3]);
     }
@@ -275,23 +282,31 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
             cen[o] = SA[(gy + o + R) * kSplitTX + x];
             s[o][0] = s[o][1] = s[o][2] = 0.f;
         }
+        const float ref = cen[1];  // the task's reference velocity
 #pragma unroll
         for (int e = 0; e < NIN; ++e) {
             const int oi = (gy + e) * kSplitTX + x;
-            const float q0 = S0[oi], q1 = S1[oi], q2 = S2[oi], qa = SA[oi];
-            const float l1 = fmaf(qa, q0, q1), h1 = q1 + q1;
+            const float q0 = S0[oi];
+            float l1, l2;
+            about_ref(q0, S1[oi], S2[oi], SA[oi], ref, l1, l2);
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const int j = e - o;
-                if (j >= 0 && j < W) accum_lin(q0, l1, h1, q2, qa, cen[o], w[j], s[o][0], s[o][1], s[o][2]);
+                if (j >= 0 && j < W) {
+                    s[o][0] = fmaf(w[j], q0, s[o][0]);
+                    s[o][1] = fmaf(w[j], l1, s[o][1]);
+                    s[o][2] = fmaf(w[j], l2, s[o][2]);
+                }
             }
         }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) shift_sums(cen[o] - ref, s[o][0], s[o][1], s[o][2]);
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             const int yl = gy + o;
             if (yl >= nyo) break;
             const size_t pix = (size_t)(ty0 + yl) * g.nx + (tx0 + x);
-            const float s0 = s[o][0], s1 = fmaf(-cen[o], s[o][0], s[o][1]), s2 = s[o][2];
+            const float s0 = s[o][0], s1 = s[o][1], s2 = s[o][2];
             float m0, m1, m2;
             const bool valid = s0 > thr;
             if (!c.valid) {
