@@ -48,10 +48,19 @@ OPS_PER_EXT_VOXEL = FMA_OPS_PER_EXT_VOXEL + MUFU_OPS_PER_EXT_VOXEL
 # and of the moments, residuals and chi2 of one data spaxel.
 OPS_PER_PSF_TAP = 9
 OPS_PER_DATA_SPAXEL = 10
-# The split path's PSF tap: s0 and s1 accumulated about zero, s2 re-centred
-# exactly (s0 += w q0; s1 += w (q1 + a q0); s2 += w (q2 + D (2 q1 + D q0)),
-# D = a - c): six FP32 operations.
-OPS_PER_PSF_TAP_SPLIT = 6
+# The split path's PSF passes: each thread's inputs are moved once to a
+# reference velocity r (l1 = q1 + d q0, l2 = q2 + d (2 q1 + d q0), d = a - r:
+# five FP32 operations per input, 4 + 2R inputs per four outputs), a tap is
+# three FMAs (s0 += w q0, s1 += w l1, s2 += w l2), and each output moves its
+# sums from r to its own centre once (five operations).
+OPS_PER_PSF_TAP_SPLIT = 3
+OPS_PER_PSF_INPUT_SPLIT = 5
+OPS_PER_PSF_OUTPUT_SPLIT = 5
+
+
+def split_pass_ops_per_output(taps):
+    """FP32 operations of one output of a split-path PSF pass of `taps` taps."""
+    return OPS_PER_PSF_TAP_SPLIT * taps + OPS_PER_PSF_INPUT_SPLIT * (3 + taps) / 4.0 + OPS_PER_PSF_OUTPUT_SPLIT
 # Per-unit work of the unfolded method (cube + separable PSF x LSF
 # convolution + moments) at the Fabry-Perot size, in FP32 instructions per
 # data voxel: the line (an ex2 and 3 FP32 per extended voxel, 1.41 extended
@@ -65,11 +74,12 @@ UNFOLDED_FP32_PER_DATA_VOXEL = 47.0
 # reported only for a run at that tuning and with that kernel build.
 FUSED_TRAFFIC_400 = {(12, 512, 0): 1433600.0, (12, 512, 1): 1318400.0}
 # DRAM bytes (read + write) of one launch of the split path's line stage
-# (80 Fabry-Perot models, the chunk of a 400-model step, 10 rows per CTA),
-# the mean of five launches of a one-pass ncu capture of `bench.py --quick
-# --steps 5 --warmup 2` on a GB300: 40 192 B read + 111 002 B written;
-# reported only for the 400-model step.
-SPLIT_LINE_TRAFFIC_80 = 151194.0
+# per step size (models per step -> bytes), from a one-pass ncu capture of
+# `bench.py --quick --steps 5 --warmup 2` on a GB300 with the current kernel
+# build (dram__bytes_read.sum + dram__bytes_write.sum, mean over launches);
+# empty until that capture is taken.
+SPLIT_LINE_TRAFFIC = {}
+SPLIT_LINE_TRAFFIC_MODELS = 80  # models per line-stage launch of a 400-model step
 FLUSH_BYTES = 256 << 20
 
 
@@ -1245,7 +1255,7 @@ def run_gbk(args):
         # extended voxel) and the PSF pass along x of every extended row
         # (6 FP32 per tap per output, ey x nx outputs).
         taps = 2 * ((ex - g.nx) // 2) + 1
-        fma_a = FMA_OPS_PER_EXT_VOXEL * ex * ey * ez + OPS_PER_PSF_TAP_SPLIT * taps * ey * g.nx
+        fma_a = FMA_OPS_PER_EXT_VOXEL * ex * ey * ez + split_pass_ops_per_output(taps) * ey * g.nx
         mufu_a = MUFU_OPS_PER_EXT_VOXEL * ex * ey * ez
         r32, r32x2, rmu = gbk.gbk_measure_alu_peak(stream)
         rfma = max(r32, r32x2)
@@ -1255,21 +1265,24 @@ def run_gbk(args):
         achieved_ops = (fma_a + mufu_a) * n / t_a
         out["roofline"] = {
             "bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved_ops / peak_ops, "traffic": SPLIT_LINE_TRAFFIC_80 if n == 400 else None,
-            "traffic_note": ("DRAM bytes per launch (80 models) from one ncu capture of this kernel build: its "
-                             "51 MB of x-filtered planes per launch stay in L2" if n == 400 else
-                             "no capture at this batch size"),
+            "frac": achieved_ops / peak_ops, "traffic": SPLIT_LINE_TRAFFIC.get(n),
+            "traffic_note": ("DRAM bytes per launch (%d models) from one ncu capture of this kernel build: its "
+                             "x-filtered planes stay in L2" % SPLIT_LINE_TRAFFIC_MODELS if n in SPLIT_LINE_TRAFFIC
+                             else "no capture of this kernel build at this batch size"),
             "kernel": "split_line_kernel",
             "basis": "per model %.1f M FP32 + %.1f M ex2 lane ops: %d FP32 + %d ex2 per extended voxel (%d x %d x "
-                     "%d), %d FP32 per PSF tap along x (%d taps, %d x %d outputs); its time per step from CUDA "
-                     "events around each launch (%.3f ms of %.3f); measured FP32 pipe %.1f T lane-ops/s (scalar "
-                     "%.1f, f32x2 %.1f), ex2 %.1f T/s"
+                     "%d), %.1f FP32 per output of the PSF pass along x (%d taps x %d FMAs, %d per input and %d per "
+                     "output for the re-centring; %d x %d outputs); its time per step from CUDA events around each "
+                     "launch (%.3f ms of %.3f); measured FP32 pipe %.1f T lane-ops/s (scalar %.1f, f32x2 %.1f), "
+                     "ex2 %.1f T/s"
                      % (fma_a / 1e6, mufu_a / 1e6, FMA_OPS_PER_EXT_VOXEL, MUFU_OPS_PER_EXT_VOXEL, ex, ey, ez,
-                        OPS_PER_PSF_TAP_SPLIT, taps, ey, g.nx, t_a * 1e3, sum(st["ms_per_step"] for st in out["stages"]),
+                        split_pass_ops_per_output(taps), taps, OPS_PER_PSF_TAP_SPLIT, OPS_PER_PSF_INPUT_SPLIT,
+                        OPS_PER_PSF_OUTPUT_SPLIT, ey, g.nx, t_a * 1e3,
+                        sum(st["ms_per_step"] for st in out["stages"]),
                         rfma / 1e12, r32 / 1e12, r32x2 / 1e12, rmu / 1e12),
             "peak_source": "measured on this device by gbk_measure_alu_peak"}
         # the whole step on the same basis (both stages, every launch)
-        fma_all = fma_a + OPS_PER_PSF_TAP_SPLIT * taps * g.ny * g.nx + OPS_PER_DATA_SPAXEL * g.nx * g.ny
+        fma_all = fma_a + split_pass_ops_per_output(taps) * g.ny * g.nx + OPS_PER_DATA_SPAXEL * g.nx * g.ny
         out["roofline_whole_step"] = {
             "achieved": (fma_all + mufu_a) * n / (ms_step * 1e-3) / 1e12, "unit": "Tops/s",
             "frac": (fma_all + mufu_a) * n / (ms_step * 1e-3) / ((fma_all + mufu_a) / max(fma_all / rfma, mufu_a / rmu)),

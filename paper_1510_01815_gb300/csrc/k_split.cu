@@ -50,7 +50,7 @@ namespace gbk {
 constexpr int kSplitThreads = 256;
 constexpr int kSplitMaxRA = 12;                      // most extended rows per stage-A CTA
 constexpr int kSplitTX = 64, kSplitTY = 32;          // data spaxels per stage-B tile
-constexpr size_t kSplitL2Budget = (size_t)48 << 20;  // buffer bytes per chunk
+constexpr size_t kSplitL2Budget = (size_t)48 << 20;  // buffer bytes per chunk (two buffers in flight)
 constexpr int kSplitMaxEx = 1024;                    // widest extended row served
 constexpr long kSplitWaitLimit = 1L << 18;           // tries: about one second (3.75 us per failed try_wait)
 
@@ -71,6 +71,7 @@ struct SplitArgs {
     const ModelConst *mcs;   // [n_models] per-model constants
     const float *tab;        // split_tab_floats(g) floats
     float *pl;               // x-filtered planes, [n_models][4][ey][nxp]
+    int pl_z0;               // first plane of this buffer in the PSF stage's tensor map
     gbk_obs obs;
     const gbk_obs *obs_list; // per galaxy (model m0 + i is galaxy (m0 + i) / mpg), or null: obs for all
     const int32_t *skip;     // per galaxy: non-zero = leave the galaxy's models alone (or null)
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kSplitThreads, 4)
         // the tile's rows of the four planes (beyond the buffer: zeros)
         tma_expect(&bar, (uint32_t)(4 * NPL * sizeof(float)));
 #pragma unroll
-        for (int pl = 0; pl < 4; ++pl) tma_load_3d(&tmap, sp + pl * NPL, &bar, tx0, ty0, 4 * model + pl);
+        for (int pl = 0; pl < 4; ++pl) tma_load_3d(&tmap, sp + pl * NPL, &bar, tx0, ty0, a.pl_z0 + 4 * model + pl);
     }
     if (tid < (int)(sizeof(ModelConst) / 4))
         reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
@@ -385,8 +386,8 @@ SplitEncodeFn split_encode_fn()
 }
 
 struct SplitLayout {
-    int chunk, nxp, tiles_x, tiles;
-    size_t mc_off, tab_off, pl_off, part_off, arr_off, total;
+    int chunk, nbuf, nxp, tiles_x, tiles;
+    size_t mc_off, tab_off, pl_off, pl_bytes, part_off, arr_off, total;  // pl_bytes: one buffer
 };
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -399,13 +400,17 @@ static SplitLayout split_layout(const Geom &g, int n_models)
     size_t chunk = kSplitL2Budget / plb;
     if (chunk < 1) chunk = 1;
     if (chunk > (size_t)n_models) chunk = (size_t)n_models;
+    const size_t nchunks = ((size_t)n_models + chunk - 1) / chunk;
+    chunk = ((size_t)n_models + nchunks - 1) / nchunks;  // balanced chunks
     L.chunk = (int)chunk;
+    L.nbuf = (size_t)n_models > chunk ? 2 : 1;  // chunk k + 1's line stage runs beside chunk k's PSF stage
     L.tiles_x = (g.nx + kSplitTX - 1) / kSplitTX;
     L.tiles = L.tiles_x * ((g.ny + kSplitTY - 1) / kSplitTY);
     L.mc_off = 0;
     L.tab_off = al256((size_t)n_models * sizeof(ModelConst));
     L.pl_off = L.tab_off + al256((size_t)split_tab_floats(g) * sizeof(float));
-    L.part_off = L.pl_off + al256(chunk * plb);
+    L.pl_bytes = chunk * plb;  // a multiple of 16 bytes (nxp is a multiple of 4)
+    L.part_off = L.pl_off + al256(L.nbuf * L.pl_bytes);
     L.arr_off = L.part_off + al256(chunk * L.tiles * sizeof(double));
     L.total = L.arr_off + al256(chunk * sizeof(unsigned));
     return L;
@@ -463,7 +468,7 @@ gbk_status split_status_read(int *v)
 }
 
 template <int R>
-static gbk_status launch_stages(const CUtensorMap &tm, const SplitArgs &a, cudaStream_t st, SplitTimer *timer)
+static gbk_status launch_stage(int stage, const CUtensorMap &tm, const SplitArgs &a, cudaStream_t st)
 {
     static KernelAttrMemo memo_a, memo_b;
     const size_t sa = split_smem_a(a.g, a.ra), sb = split_smem_b(R);
@@ -473,14 +478,62 @@ static gbk_status launch_stages(const CUtensorMap &tm, const SplitArgs &a, cudaS
         (s = ensure_kernel_attrs((const void *)split_psf_kernel<R>, sb, false, memo_b,
                                  "split evaluator: setting the PSF stage's shared memory")))
         return s;
-    const unsigned blocks_a = (unsigned)((a.g.ey + a.ra - 1) / a.ra);
-    split_line_kernel<R><<<dim3(blocks_a, (unsigned)a.n_models), kSplitThreads, sa, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "split evaluator: line stage launch");
-    if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
-    split_psf_kernel<R><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kSplitThreads, sb, st>>>(tm, a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split evaluator: PSF stage launch");
-    if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
+    cudaError_t e;
+    if (stage == 0) {
+        const unsigned blocks_a = (unsigned)((a.g.ey + a.ra - 1) / a.ra);
+        split_line_kernel<R><<<dim3(blocks_a, (unsigned)a.n_models), kSplitThreads, sa, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split evaluator: line stage launch");
+    } else {
+        split_psf_kernel<R><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kSplitThreads, sb, st>>>(tm, a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split evaluator: PSF stage launch");
+    }
+    return GBK_OK;
+}
+
+static gbk_status launch_stage_r(int stage, const CUtensorMap &tm, const SplitArgs &a, cudaStream_t st)
+{
+    switch (a.g.R) {
+    case 0: return launch_stage<0>(stage, tm, a, st);
+    case 1: return launch_stage<1>(stage, tm, a, st);
+    case 2: return launch_stage<2>(stage, tm, a, st);
+    case 3: return launch_stage<3>(stage, tm, a, st);
+    case 4: return launch_stage<4>(stage, tm, a, st);
+    case 5: return launch_stage<5>(stage, tm, a, st);
+    case 6: return launch_stage<6>(stage, tm, a, st);
+    case 7: return launch_stage<7>(stage, tm, a, st);
+    case 8: return launch_stage<8>(stage, tm, a, st);
+    default: return fail(GBK_EUNSUPPORTED, "split evaluator: PSF radius %d > %d", a.g.R, kSplitMaxR);
+    }
+}
+
+// Per host thread and device: the stream the PSF stages run on while the
+// next chunk's line stage runs on the caller's stream, and the events that
+// order them (created on first use and kept for the process).
+struct SplitAux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t line[2] = {nullptr, nullptr}, psf[2] = {nullptr, nullptr};
+};
+
+static gbk_status split_aux(SplitAux **out)
+{
+    constexpr int kMaxDev = 64;
+    thread_local SplitAux aux[kMaxDev];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "split evaluator: current device");
+    if (dev < 0 || dev >= kMaxDev) return fail(GBK_EUNSUPPORTED, "split evaluator: device ordinal %d", dev);
+    SplitAux &x = aux[dev];
+    if (!x.s) {
+        SplitAux y;
+        if ((e = cudaStreamCreateWithFlags(&y.s, cudaStreamNonBlocking)) ||
+            (e = cudaEventCreateWithFlags(&y.line[0], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&y.line[1], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&y.psf[0], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&y.psf[1], cudaEventDisableTiming)))
+            return cuda_fail(e, "split evaluator: creating the PSF stages' stream");
+        x = y;
+    }
+    *out = &x;
     return GBK_OK;
 }
 
@@ -505,11 +558,11 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
         e = cudaMemsetAsync(base + L.arr_off, 0, (size_t)L.chunk * sizeof(unsigned), st);
         if (e != cudaSuccess) return cuda_fail(e, "split evaluator: clearing the arrival counters");
     }
-    // the chunk's planes as a 3-D tensor [4 * chunk][ey][nxp] for the PSF stage's tile loads
+    // the buffers' planes as one 3-D tensor [nbuf * 4 * chunk][ey][nxp] for the PSF stage's tile loads
     CUtensorMap tm;
     if (!split_encode_fn()) return fail(GBK_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
     {
-        const cuuint64_t dims[3] = {(cuuint64_t)L.nxp, (cuuint64_t)g.ey, (cuuint64_t)4 * L.chunk};
+        const cuuint64_t dims[3] = {(cuuint64_t)L.nxp, (cuuint64_t)g.ey, (cuuint64_t)4 * L.chunk * L.nbuf};
         const cuuint64_t strides[2] = {(cuuint64_t)L.nxp * sizeof(float), (cuuint64_t)L.nxp * g.ey * sizeof(float)};
         const cuuint32_t box[3] = {(cuuint32_t)kSplitTX, (cuuint32_t)(kSplitTY + 2 * g.R), 1};
         const cuuint32_t estr[3] = {1, 1, 1};
@@ -523,14 +576,28 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split evaluator: set-up launch");
     if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
     const size_t np = (size_t)g.nx * g.ny;
-    for (int m0 = 0; m0 < n; m0 += L.chunk) {
+    // Two plane buffers: chunk c fills buffer c % 2, so chunk c + 1's line
+    // stage (caller's stream) can run while chunk c's PSF stage (the
+    // auxiliary stream) reads the other buffer; chunk c + 2's line stage
+    // waits for chunk c's PSF stage.  Timed runs keep one stream.
+    const bool overlap = !timer && L.nbuf == 2;
+    SplitAux *aux = nullptr;
+    if (overlap) {
+        gbk_status s = split_aux(&aux);
+        if (s) return s;
+    }
+    cudaStream_t sb = overlap ? aux->s : st;
+    int c = 0;
+    for (int m0 = 0; m0 < n; m0 += L.chunk, ++c) {
+        const int b = c & (L.nbuf - 1);
         SplitArgs a = {};
         a.g = g;
         a.n_models = std::min(L.chunk, n - m0);
         a.params = params + (size_t)m0 * GBK_NPAR;
         a.mcs = mcs + m0;
         a.tab = tab;
-        a.pl = (float *)(base + L.pl_off);
+        a.pl = (float *)(base + L.pl_off + (size_t)b * L.pl_bytes);
+        a.pl_z0 = 4 * L.chunk * b;
         if (obs) a.obs = *obs;
         a.obs_list = batch ? batch->obs_list : nullptr;
         a.skip = batch ? batch->skip : nullptr;
@@ -545,21 +612,20 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
         a.ra = ra;
         a.tiles_x = L.tiles_x;
         a.tiles = L.tiles;
-        gbk_status s;
-        switch (g.R) {
-        case 0: s = launch_stages<0>(tm, a, st, timer); break;
-        case 1: s = launch_stages<1>(tm, a, st, timer); break;
-        case 2: s = launch_stages<2>(tm, a, st, timer); break;
-        case 3: s = launch_stages<3>(tm, a, st, timer); break;
-        case 4: s = launch_stages<4>(tm, a, st, timer); break;
-        case 5: s = launch_stages<5>(tm, a, st, timer); break;
-        case 6: s = launch_stages<6>(tm, a, st, timer); break;
-        case 7: s = launch_stages<7>(tm, a, st, timer); break;
-        case 8: s = launch_stages<8>(tm, a, st, timer); break;
-        default: return fail(GBK_EUNSUPPORTED, "split evaluator: PSF radius %d > %d", g.R, kSplitMaxR);
-        }
+        if (overlap && c >= 2 && (e = cudaStreamWaitEvent(st, aux->psf[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "split evaluator: ordering the stages");
+        gbk_status s = launch_stage_r(0, tm, a, st);
         if (s) return s;
+        if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
+        if (overlap && ((e = cudaEventRecord(aux->line[b], st)) || (e = cudaStreamWaitEvent(sb, aux->line[b], 0))))
+            return cuda_fail(e, "split evaluator: ordering the stages");
+        if ((s = launch_stage_r(1, tm, a, sb))) return s;
+        if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
+        if (overlap && (e = cudaEventRecord(aux->psf[b], sb)) != cudaSuccess)
+            return cuda_fail(e, "split evaluator: ordering the stages");
     }
+    if (overlap && (e = cudaStreamWaitEvent(st, aux->psf[(c - 1) & 1], 0)) != cudaSuccess)
+        return cuda_fail(e, "split evaluator: joining the stages");
     return GBK_OK;
 }
 
