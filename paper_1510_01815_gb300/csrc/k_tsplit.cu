@@ -350,6 +350,9 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
         for (int o = 0; o < 4; ++o) cen[o] = av[o + R];
         float *const out = P0 + (size_t)rr * nxp + gx;
         {
+            // inputs moved exactly to the task's reference velocity (three
+            // FMAs a tap), each output's sums moved to its centre at the end
+            const float ref = cen[1];
             const float *Q0 = sm + (3 * tr) * NPL, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
             float s[4][3];
 #pragma unroll
@@ -365,20 +368,24 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
                 for (int k = 0; k < 4; ++k) {
                     const int e = 4 * c4 + k;
                     if (e >= NIN) break;
-                    const float ae = av[e];
-                    const float l1 = fmaf(ae, q0[k], q1[k]), h1 = q1[k] + q1[k];
+                    float l1, l2;
+                    about_ref(q0[k], q1[k], q2[k], av[e], ref, l1, l2);
 #pragma unroll
                     for (int o = 0; o < 4; ++o) {
                         const int j = e - o;
-                        if (j >= 0 && j < W) accum_lin(q0[k], l1, h1, q2[k], ae, cen[o], w[j], s[o][0], s[o][1], s[o][2]);
+                        if (j >= 0 && j < W) {
+                            s[o][0] = fmaf(w[j], q0[k], s[o][0]);
+                            s[o][1] = fmaf(w[j], l1, s[o][1]);
+                            s[o][2] = fmaf(w[j], l2, s[o][2]);
+                        }
                     }
                 }
             }
+#pragma unroll
+            for (int o = 0; o < 4; ++o) shift_sums(cen[o] - ref, s[o][0], s[o][1], s[o][2]);
             float *p = out + (size_t)(3 * tr) * pstride;
             *reinterpret_cast<float4 *>(p) = make_float4(s[0][0], s[1][0], s[2][0], s[3][0]);
-            *reinterpret_cast<float4 *>(p + pstride) =
-                make_float4(fmaf(-cen[0], s[0][0], s[0][1]), fmaf(-cen[1], s[1][0], s[1][1]),
-                            fmaf(-cen[2], s[2][0], s[2][1]), fmaf(-cen[3], s[3][0], s[3][1]));
+            *reinterpret_cast<float4 *>(p + pstride) = make_float4(s[0][1], s[1][1], s[2][1], s[3][1]);
             *reinterpret_cast<float4 *>(p + 2 * pstride) = make_float4(s[0][2], s[1][2], s[2][2], s[3][2]);
         }
         if (tr == 0)
@@ -487,7 +494,12 @@ __global__ void __launch_bounds__(kTsThreads, 2)
         for (int e = 0; e < NIN; ++e) av[e] = SA[(gy + e) * kTsTX + x];
         cen[0] = av[R];
         cen[1] = av[R + 1];
-        // y pass of triplet tr for both outputs
+        // the inputs' offsets from the task's reference velocity (the first
+        // output's centre), shared by the nine triplets
+#pragma unroll
+        for (int e = 0; e < NIN; ++e) av[e] -= cen[0];
+        // y pass of triplet tr for both outputs: inputs moved exactly to the
+        // reference (three FMAs a tap), then each output to its centre
         auto ypass = [&](int tr, float s[2][3]) {
             const float *Q0 = sp + (3 * tr) * NPL, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
 #pragma unroll
@@ -495,16 +507,20 @@ __global__ void __launch_bounds__(kTsThreads, 2)
 #pragma unroll
             for (int e = 0; e < NIN; ++e) {
                 const int oi = (gy + e) * kTsTX + x;
-                const float q0 = Q0[oi], q1 = Q1[oi], q2 = Q2[oi], ae = av[e];
-                const float l1 = fmaf(ae, q0, q1), h1 = q1 + q1;
+                const float q0 = Q0[oi], q1 = Q1[oi], q2 = Q2[oi], d = av[e];
+                const float l1 = fmaf(d, q0, q1), l2 = fmaf(d, fmaf(d, q0, q1 + q1), q2);
 #pragma unroll
                 for (int o = 0; o < 2; ++o) {
                     const int j = e - o;
-                    if (j >= 0 && j < W) accum_lin(q0, l1, h1, q2, ae, cen[o], w[j], s[o][0], s[o][1], s[o][2]);
+                    if (j >= 0 && j < W) {
+                        s[o][0] = fmaf(w[j], q0, s[o][0]);
+                        s[o][1] = fmaf(w[j], l1, s[o][1]);
+                        s[o][2] = fmaf(w[j], l2, s[o][2]);
+                    }
                 }
             }
-#pragma unroll
-            for (int o = 0; o < 2; ++o) s[o][1] = fmaf(-cen[o], s[o][0], s[o][1]);
+            shift_sums(0.f, s[0][0], s[0][1], s[0][2]);
+            shift_sums(cen[1] - cen[0], s[1][0], s[1][1], s[1][2]);
         };
         float v[2][3];
         ypass(0, v);
