@@ -506,15 +506,7 @@ static gbk_status launch_stage_r(int stage, const CUtensorMap &tm, const SplitAr
     }
 }
 
-// Per host thread and device: the stream the PSF stages run on while the
-// next chunk's line stage runs on the caller's stream, and the events that
-// order them (created on first use and kept for the process).
-struct SplitAux {
-    cudaStream_t s = nullptr;
-    cudaEvent_t line[2] = {nullptr, nullptr}, psf[2] = {nullptr, nullptr};
-};
-
-static gbk_status split_aux(SplitAux **out)
+gbk_status split_aux(SplitAux **out)
 {
     constexpr int kMaxDev = 64;
     thread_local SplitAux aux[kMaxDev];

@@ -40,6 +40,16 @@ typedef CUresult (*SplitEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 SplitEncodeFn split_encode_fn();
 
+// Per host thread and device: a stream for the PSF stages of the two-stage
+// kernels, which run there while the next chunk's line stage runs on the
+// caller's stream, and the events that order them (two per stage, one per
+// plane buffer).  Created on first use and kept for the process.
+struct SplitAux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t line[2] = {nullptr, nullptr}, psf[2] = {nullptr, nullptr};
+};
+gbk_status split_aux(SplitAux **out);
+
 // Reads and clears the PSF stage's TMA wait status (1 = a load timed out).
 gbk_status split_status_read(int *v);
 

@@ -72,6 +72,7 @@ struct TsArgs {
     const ModelConst *mcs;    // [n_models]
     const float *tab;         // taps and LSF channel moments
     float *pl;                // [n_models][28][ey][nxp]
+    int pl_z0;                // first plane of this buffer in the PSF stage's tensor map
     gbk_obs obs;              // every model's galaxy when obs_list is null
     const gbk_obs *obs_list;  // or one per model
     const int32_t *skip;      // per model: non-zero = leave alone (or null)
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(kTsThreads, 2)
         if (tid == 0) {
             // the tile's rows of all 28 planes in one box (beyond the buffer: zeros)
             tma_expect(&bar, (uint32_t)(kTsPlanes * NPL * sizeof(float)));
-            tma_load_3d(&tmap, sp, &bar, tx0, ty0, kTsPlanes * model);
+            tma_load_3d(&tmap, sp, &bar, tx0, ty0, a.pl_z0 + kTsPlanes * model);
         }
     }
     if (tid < (int)(sizeof(ModelConst) / 4))
@@ -639,8 +640,8 @@ __global__ void __launch_bounds__(kTsThreads, 2)
 // ---------------------------------------------------------------------------
 // Host side.
 struct TsLayout {
-    int chunk, nxp, ezp, ra, tiles_x, tiles;
-    size_t mc_off, tab_off, pl_off, part_off, arr_off, total;
+    int chunk, nbuf, nxp, ezp, ra, tiles_x, tiles;
+    size_t mc_off, tab_off, pl_off, pl_bytes, part_off, arr_off, total;  // pl_bytes: one buffer
 };
 
 static size_t ts_al256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -681,13 +682,17 @@ static TsLayout ts_layout(const Geom &g, int n_models)
     size_t chunk = kTsL2Budget / plb;
     if (chunk < 1) chunk = 1;
     if (chunk > (size_t)n_models) chunk = (size_t)n_models;
+    const size_t nchunks = ((size_t)n_models + chunk - 1) / chunk;
+    chunk = ((size_t)n_models + nchunks - 1) / nchunks;  // balanced chunks
     L.chunk = (int)chunk;
+    L.nbuf = nchunks > 1 ? 2 : 1;  // chunk k + 1's line stage runs beside chunk k's PSF stage
     L.tiles_x = (g.nx + kTsTX - 1) / kTsTX;
     L.tiles = L.tiles_x * ((g.ny + kTsTY - 1) / kTsTY);
     L.mc_off = 0;
     L.tab_off = ts_al256((size_t)n_models * sizeof(ModelConst));
     L.pl_off = L.tab_off + ts_al256((size_t)(kTsTabZ + 3 * L.ezp) * sizeof(float));
-    L.part_off = L.pl_off + ts_al256(chunk * plb);
+    L.pl_bytes = chunk * plb;  // a multiple of 16 bytes (nxp is a multiple of 4)
+    L.part_off = L.pl_off + ts_al256(L.nbuf * L.pl_bytes);
     L.arr_off = L.part_off + ts_al256(chunk * L.tiles * kTsEnt * sizeof(double));
     L.total = L.arr_off + ts_al256(chunk * sizeof(unsigned));
     return L;
@@ -718,7 +723,7 @@ gbk_status tsplit_status_read(int *v)
 }
 
 template <int R>
-static gbk_status ts_launch_stages(const CUtensorMap &tm, const TsArgs &a, cudaStream_t st)
+static gbk_status ts_launch_stage(int stage, const CUtensorMap &tm, const TsArgs &a, cudaStream_t st)
 {
     static KernelAttrMemo memo_a, memo_b;
     const size_t sa = ts_smem_a(a.g, a.ra), sb = ts_smem_b(R);
@@ -728,13 +733,32 @@ static gbk_status ts_launch_stages(const CUtensorMap &tm, const TsArgs &a, cudaS
         (s = ensure_kernel_attrs((const void *)tsplit_psf_kernel<R, false>, sb, false, memo_b,
                                  "split Jacobian: setting the PSF stage's shared memory")))
         return s;
-    const unsigned blocks_a = (unsigned)((a.g.ey + a.ra - 1) / a.ra);
-    tsplit_line_kernel<R, false><<<dim3(blocks_a, (unsigned)a.n_models), kTsThreads, sa, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "split Jacobian: line stage launch");
-    tsplit_psf_kernel<R, false><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kTsThreads, sb, st>>>(tm, a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: PSF stage launch");
+    cudaError_t e;
+    if (stage == 0) {
+        const unsigned blocks_a = (unsigned)((a.g.ey + a.ra - 1) / a.ra);
+        tsplit_line_kernel<R, false><<<dim3(blocks_a, (unsigned)a.n_models), kTsThreads, sa, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: line stage launch");
+    } else {
+        tsplit_psf_kernel<R, false><<<dim3((unsigned)a.tiles, (unsigned)a.n_models), kTsThreads, sb, st>>>(tm, a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: PSF stage launch");
+    }
     return GBK_OK;
+}
+
+static gbk_status ts_launch_stage_r(int stage, const CUtensorMap &tm, const TsArgs &a, cudaStream_t st)
+{
+    switch (a.g.R) {
+    case 0: return ts_launch_stage<0>(stage, tm, a, st);
+    case 1: return ts_launch_stage<1>(stage, tm, a, st);
+    case 2: return ts_launch_stage<2>(stage, tm, a, st);
+    case 3: return ts_launch_stage<3>(stage, tm, a, st);
+    case 4: return ts_launch_stage<4>(stage, tm, a, st);
+    case 5: return ts_launch_stage<5>(stage, tm, a, st);
+    case 6: return ts_launch_stage<6>(stage, tm, a, st);
+    case 7: return ts_launch_stage<7>(stage, tm, a, st);
+    case 8: return ts_launch_stage<8>(stage, tm, a, st);
+    default: return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", a.g.R, kTsplitMaxR);
+    }
 }
 
 gbk_status launch_tsplit(const TsplitCall &call, void *ws, size_t ws_bytes, cudaStream_t st)
@@ -754,10 +778,10 @@ gbk_status launch_tsplit(const TsplitCall &call, void *ws, size_t ws_bytes, cuda
     float *tab = (float *)(base + L.tab_off);
     cudaError_t e = cudaMemsetAsync(base + L.arr_off, 0, (size_t)L.chunk * sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(e, "split Jacobian: clearing the arrival counters");
-    // the chunk's planes as a 3-D tensor [28 * chunk][ey][nxp] for the tile loads
+    // the buffers' planes as one 3-D tensor [nbuf * 28 * chunk][ey][nxp] for the tile loads
     CUtensorMap tm;
     {
-        const cuuint64_t dims[3] = {(cuuint64_t)L.nxp, (cuuint64_t)g.ey, (cuuint64_t)kTsPlanes * L.chunk};
+        const cuuint64_t dims[3] = {(cuuint64_t)L.nxp, (cuuint64_t)g.ey, (cuuint64_t)kTsPlanes * L.chunk * L.nbuf};
         const cuuint64_t strides[2] = {(cuuint64_t)L.nxp * sizeof(float), (cuuint64_t)L.nxp * g.ey * sizeof(float)};
         const cuuint32_t box[3] = {(cuuint32_t)kTsTX, (cuuint32_t)(kTsTY + 2 * g.R), (cuuint32_t)kTsPlanes};
         const cuuint32_t estr[3] = {1, 1, 1};
@@ -769,14 +793,27 @@ gbk_status launch_tsplit(const TsplitCall &call, void *ws, size_t ws_bytes, cuda
     tsplit_setup_kernel<<<(n + 127) / 128, 128, 0, st>>>(call.params, n, g, mcs, tab);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: set-up launch");
     const size_t npix = (size_t)g.nx * g.ny;
-    for (int m0 = 0; m0 < n; m0 += L.chunk) {
+    // Two plane buffers: chunk c fills buffer c % 2; chunk c's PSF stage
+    // runs on the auxiliary stream beside chunk c + 1's line stage, and
+    // chunk c + 2's line stage waits for it.
+    const bool overlap = L.nbuf == 2;
+    SplitAux *aux = nullptr;
+    if (overlap) {
+        gbk_status s = split_aux(&aux);
+        if (s) return s;
+    }
+    cudaStream_t sb = overlap ? aux->s : st;
+    int c = 0;
+    for (int m0 = 0; m0 < n; m0 += L.chunk, ++c) {
+        const int b = c & (L.nbuf - 1);
         TsArgs a = {};
         a.g = g;
         a.n_models = std::min(L.chunk, n - m0);
         a.params = call.params + (size_t)m0 * GBK_NPAR;
         a.mcs = mcs + m0;
         a.tab = tab;
-        a.pl = (float *)(base + L.pl_off);
+        a.pl = (float *)(base + L.pl_off + (size_t)b * L.pl_bytes);
+        a.pl_z0 = kTsPlanes * L.chunk * b;
         a.obs = call.obs;
         a.obs_list = call.obs_list ? call.obs_list + m0 : nullptr;
         a.skip = call.skip ? call.skip + m0 : nullptr;
@@ -793,21 +830,18 @@ gbk_status launch_tsplit(const TsplitCall &call, void *ws, size_t ws_bytes, cuda
         a.ra = L.ra;
         a.tiles_x = L.tiles_x;
         a.tiles = L.tiles;
-        gbk_status s;
-        switch (g.R) {
-        case 0: s = ts_launch_stages<0>(tm, a, st); break;
-        case 1: s = ts_launch_stages<1>(tm, a, st); break;
-        case 2: s = ts_launch_stages<2>(tm, a, st); break;
-        case 3: s = ts_launch_stages<3>(tm, a, st); break;
-        case 4: s = ts_launch_stages<4>(tm, a, st); break;
-        case 5: s = ts_launch_stages<5>(tm, a, st); break;
-        case 6: s = ts_launch_stages<6>(tm, a, st); break;
-        case 7: s = ts_launch_stages<7>(tm, a, st); break;
-        case 8: s = ts_launch_stages<8>(tm, a, st); break;
-        default: return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", g.R, kTsplitMaxR);
-        }
+        if (overlap && c >= 2 && (e = cudaStreamWaitEvent(st, aux->psf[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "split Jacobian: ordering the stages");
+        gbk_status s = ts_launch_stage_r(0, tm, a, st);
         if (s) return s;
+        if (overlap && ((e = cudaEventRecord(aux->line[b], st)) || (e = cudaStreamWaitEvent(sb, aux->line[b], 0))))
+            return cuda_fail(e, "split Jacobian: ordering the stages");
+        if ((s = ts_launch_stage_r(1, tm, a, sb))) return s;
+        if (overlap && (e = cudaEventRecord(aux->psf[b], sb)) != cudaSuccess)
+            return cuda_fail(e, "split Jacobian: ordering the stages");
     }
+    if (overlap && (e = cudaStreamWaitEvent(st, aux->psf[(c - 1) & 1], 0)) != cudaSuccess)
+        return cuda_fail(e, "split Jacobian: joining the stages");
     return GBK_OK;
 }
 
