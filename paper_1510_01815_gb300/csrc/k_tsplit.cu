@@ -868,8 +868,9 @@ void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std
     p->tile_base.resize(n);
     p->pl_off.resize(n);
     const long long budget = (long long)(kTsL2Budget / sizeof(float));
-    long long tab = 0, chunk_start = 0, cum = 0, pl_max = 0;
+    long long tab = 0, chunk_start = 0, cum = 0, largest = 0;
     int slots = 0;
+    std::vector<int> chunk_of(n, 0);
     p->chunk_a.push_back(0);
     p->chunk_b.push_back(0);
     bool first = true;
@@ -881,7 +882,6 @@ void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std
         const int nxp = (g.nx + 3) & ~3;
         const long long planes = (long long)kTsPlanes * g.ey * nxp;
         if (!first && (g.R != prev_r || cum + planes - chunk_start > budget)) {  // close the chunk before galaxy m
-            pl_max = std::max(pl_max, cum - chunk_start);
             p->chunk_a.push_back((int)p->work_a.size());
             p->chunk_b.push_back((int)p->work_b.size());
             p->chunk_r.push_back(prev_r);
@@ -890,6 +890,8 @@ void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std
         first = false;
         prev_r = g.R;
         p->pl_off[m] = cum - chunk_start;
+        chunk_of[m] = (int)p->chunk_r.size();
+        largest = std::max(largest, planes);
         cum += planes;
         p->tab_off[m] = (int)tab;
         tab += (kTsTabZ + 3 * ts_ezp(g) + 3) & ~3;
@@ -901,17 +903,26 @@ void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std
         slots += tiles;
         for (int t = 0; t < tiles; ++t) p->work_b.push_back(make_int2(m, t));
     }
-    pl_max = std::max(pl_max, cum - chunk_start);
     if (!first) {
         p->chunk_a.push_back((int)p->work_a.size());
         p->chunk_b.push_back((int)p->work_b.size());
         p->chunk_r.push_back(prev_r);
     }
+    // A plane buffer holds any chunk: no chunk exceeds the budget unless one
+    // galaxy does, nor the planes of all the active galaxies.  The bound
+    // does not grow when galaxies leave the plan, so a plan over the running
+    // galaxies fits the full plan's workspace.  Odd chunks use the second
+    // buffer.
+    const long long cap = (std::max(largest, std::min(budget, cum)) + 3) & ~3LL;  // 16-byte multiple
+    p->nbuf = p->chunk_r.size() > 1 ? 2 : 1;
+    if (p->nbuf == 2)
+        for (int m = 0; m < n; ++m)
+            if ((!active || (*active)[m]) && (chunk_of[m] & 1)) p->pl_off[m] += cap;
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t r = o; o += ts_al256(bytes); return r; };
     p->o_mcs = take(sizeof(ModelConst) * n);
     p->o_tab = take(sizeof(float) * (size_t)tab);
-    p->o_pl = take(sizeof(float) * (size_t)pl_max);
+    p->o_pl = take(sizeof(float) * (size_t)cap * p->nbuf);
     p->o_part = take(sizeof(double) * (size_t)slots * kTsEnt);
     p->o_arr = take(sizeof(unsigned) * n);
     p->o_taboff = take(sizeof(int) * n);
@@ -940,9 +951,9 @@ gbk_status tsplit_ragged_upload(const TsRaggedPlan &p, char *ws, cudaStream_t st
     return GBK_OK;
 }
 
-// The stages of chunk c (its galaxies share the PSF radius R).
+// Stage `stage` (0: line, 1: PSF) of chunk c (its galaxies share the PSF radius R).
 template <int R>
-static gbk_status ts_launch_ragged(const TsRaggedPlan &p, int c, TsArgs a, char *ws, cudaStream_t st)
+static gbk_status ts_launch_ragged(const TsRaggedPlan &p, int c, int stage, TsArgs a, char *ws, cudaStream_t st)
 {
     static KernelAttrMemo memo_a, memo_b;
     const size_t sb = ts_smem_b(R);
@@ -957,12 +968,12 @@ static gbk_status ts_launch_ragged(const TsRaggedPlan &p, int c, TsArgs a, char 
     const int2 *wa = (const int2 *)(ws + p.o_wa), *wb = (const int2 *)(ws + p.o_wb);
     const int na = p.chunk_a[c + 1] - p.chunk_a[c], nb = p.chunk_b[c + 1] - p.chunk_b[c];
     cudaError_t e;
-    if (na > 0) {
+    if (stage == 0 && na > 0) {
         a.work = wa + p.chunk_a[c];
         tsplit_line_kernel<R, true><<<(unsigned)na, kTsThreads, p.smem_a, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: ragged line stage launch");
     }
-    if (nb > 0) {
+    if (stage == 1 && nb > 0) {
         a.work = wb + p.chunk_b[c];
         tsplit_psf_kernel<R, true><<<(unsigned)nb, kTsThreads, sb, st>>>(none, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split Jacobian: ragged PSF stage launch");
@@ -1007,22 +1018,45 @@ gbk_status launch_tsplit_ragged(const TsRaggedPlan &p, const TsplitRaggedCall &c
     a.pl_off = (const long long *)(ws + p.o_ploff);
     a.ra_m = (const int *)(ws + p.o_ra);
     a.tile_base = (const int *)(ws + p.o_tbase);
-    for (int c = 0; c + 1 < (int)p.chunk_a.size(); ++c) {
-        gbk_status s;
-        switch (p.chunk_r[c]) {
-        case 0: s = ts_launch_ragged<0>(p, c, a, ws, st); break;
-        case 1: s = ts_launch_ragged<1>(p, c, a, ws, st); break;
-        case 2: s = ts_launch_ragged<2>(p, c, a, ws, st); break;
-        case 3: s = ts_launch_ragged<3>(p, c, a, ws, st); break;
-        case 4: s = ts_launch_ragged<4>(p, c, a, ws, st); break;
-        case 5: s = ts_launch_ragged<5>(p, c, a, ws, st); break;
-        case 6: s = ts_launch_ragged<6>(p, c, a, ws, st); break;
-        case 7: s = ts_launch_ragged<7>(p, c, a, ws, st); break;
-        case 8: s = ts_launch_ragged<8>(p, c, a, ws, st); break;
-        default: return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", p.chunk_r[c], kTsplitMaxR);
-        }
+    // chunk c's PSF stage on the auxiliary stream beside chunk c + 1's line
+    // stage (plane buffer c % 2); chunk c + 2's line stage waits for it
+    const int nch = (int)p.chunk_a.size() - 1;
+    const bool overlap = p.nbuf == 2;
+    SplitAux *aux = nullptr;
+    if (overlap) {
+        gbk_status s = split_aux(&aux);
         if (s) return s;
     }
+    cudaStream_t sb = overlap ? aux->s : st;
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        if (overlap && c >= 2 && (e = cudaStreamWaitEvent(st, aux->psf[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "split Jacobian: ordering the stages");
+        for (int stage = 0; stage < 2; ++stage) {
+            cudaStream_t ss = stage == 0 ? st : sb;
+            gbk_status s;
+            switch (p.chunk_r[c]) {
+            case 0: s = ts_launch_ragged<0>(p, c, stage, a, ws, ss); break;
+            case 1: s = ts_launch_ragged<1>(p, c, stage, a, ws, ss); break;
+            case 2: s = ts_launch_ragged<2>(p, c, stage, a, ws, ss); break;
+            case 3: s = ts_launch_ragged<3>(p, c, stage, a, ws, ss); break;
+            case 4: s = ts_launch_ragged<4>(p, c, stage, a, ws, ss); break;
+            case 5: s = ts_launch_ragged<5>(p, c, stage, a, ws, ss); break;
+            case 6: s = ts_launch_ragged<6>(p, c, stage, a, ws, ss); break;
+            case 7: s = ts_launch_ragged<7>(p, c, stage, a, ws, ss); break;
+            case 8: s = ts_launch_ragged<8>(p, c, stage, a, ws, ss); break;
+            default: return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", p.chunk_r[c], kTsplitMaxR);
+            }
+            if (s) return s;
+            if (overlap && stage == 0 &&
+                ((e = cudaEventRecord(aux->line[b], st)) || (e = cudaStreamWaitEvent(sb, aux->line[b], 0))))
+                return cuda_fail(e, "split Jacobian: ordering the stages");
+        }
+        if (overlap && (e = cudaEventRecord(aux->psf[b], sb)) != cudaSuccess)
+            return cuda_fail(e, "split Jacobian: ordering the stages");
+    }
+    if (overlap && nch > 0 && (e = cudaStreamWaitEvent(st, aux->psf[(nch - 1) & 1], 0)) != cudaSuccess)
+        return cuda_fail(e, "split Jacobian: joining the stages");
     return GBK_OK;
 }
 

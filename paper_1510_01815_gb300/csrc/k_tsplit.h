@@ -45,10 +45,11 @@ struct TsRaggedPlan {
     bool ok = false;  // every galaxy served (cube model, u = 1, PSF radius <= kTsplitMaxR)
     int n = 0;
     std::vector<int> tab_off, ra, tile_base;
-    std::vector<long long> pl_off;      // floats, relative to the galaxy's chunk
+    std::vector<long long> pl_off;      // floats, in its chunk's plane buffer (chunk c: buffer c % nbuf)
     std::vector<int2> work_a, work_b;   // (galaxy, row block) and (galaxy, tile), chunk by chunk
     std::vector<int> chunk_a, chunk_b;  // work ranges of the chunks (n_chunks + 1 entries)
     std::vector<int> chunk_r;           // PSF radius of each chunk's galaxies
+    int nbuf = 1;                       // plane buffers (2: a chunk's PSF stage beside the next line stage)
     size_t smem_a = 0;
     size_t o_mcs = 0, o_tab = 0, o_pl = 0, o_part = 0, o_arr = 0, o_taboff = 0, o_ra = 0, o_tbase = 0, o_ploff = 0,
            o_wa = 0, o_wb = 0, total = 0;
