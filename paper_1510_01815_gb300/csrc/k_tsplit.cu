@@ -33,6 +33,7 @@
 // The PSF passes accumulate as the split evaluator's (six FP32 operations
 // per tap and triplet).  Models go in chunks whose planes stay in L2.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -71,6 +72,8 @@ struct TsArgs {
     const double *params;     // [n_models][GBK_NPAR]
     const ModelConst *mcs;    // [n_models]
     const float *tab;         // taps and LSF channel moments
+    float w1[2 * kTsplitMaxR + 1];  // PSF taps of the launch's models, normalised (host-computed)
+    f32x2 w2[2 * kTsplitMaxR + 1];  // the same as (w, w) pairs
     float *pl;                // [n_models][28][ey][nxp]
     int pl_z0;                // first plane of this buffer in the PSF stage's tensor map
     gbk_obs obs;              // every model's galaxy when obs_list is null
@@ -305,12 +308,15 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
     if (tid < (int)(sizeof(ModelConst) / 4))
         reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
     for (int i = tid; i < 3 * ezp; i += kTsThreads) tz[i] = tab[kTsTabZ + i];
-    float w[W];
-#pragma unroll
-    for (int j = 0; j < W; ++j) w[j] = tab[kTsTabTaps + j];
     __syncthreads();
 
-    // phase 1: triplets of every extended spaxel of the rows
+    // phase 1: triplets of every extended spaxel of the rows.  Layout: the
+    // value triplet's three planes, then the derivative triplets in pairs
+    // (2P + 1, 2P + 2), each component of a pair one plane of interleaved
+    // (first, second) values, then the centres:
+    //   value plane m:         sm + m NPL + o
+    //   pair P, component m:   sm + 3 NPL + (3 P + m) 2 NPL + 2 o + (0 | 1)
+    //   centres:               sm + 27 NPL + o
     const double *pm = a.params + (size_t)model * GBK_NPAR;
     {
         const int nsp = nrows * g.ex;
@@ -322,7 +328,13 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
                                             (float)(row0 + r - R), rec);
             const int o = r * PA + xe;
 #pragma unroll
-            for (int p = 0; p < 3 * kTsNT; ++p) sm[p * NPL + o] = rec[p];
+            for (int m = 0; m < 3; ++m) sm[m * NPL + o] = rec[m];
+#pragma unroll
+            for (int P = 0; P < kTsNP / 2; ++P)
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    *reinterpret_cast<float2 *>(sm + 3 * NPL + (3 * P + m) * 2 * NPL + 2 * o) =
+                        make_float2(rec[3 * (2 * P + 1) + m], rec[3 * (2 * P + 2) + m]);
             sm[3 * kTsNT * NPL + o] = ac;
             xe += dx; r += dr;
             if (xe >= g.ex) { xe -= g.ex; ++r; }
@@ -337,8 +349,10 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
     float *const P0 = (RAG ? a.pl + a.pl_off[model] : a.pl + (size_t)model * kTsPlanes * pstride) + (size_t)row0 * nxp;
     const float *const QA = sm + 3 * kTsNT * NPL;
     const int ntask = nrows * ngx;
-    for (int t = tid; t < ntask * kTsNT; t += kTsThreads) {
-        const int tr = t / ntask, tk = t - tr * ntask;
+    // units: 0 the value triplet, 1 .. 4 the derivative pairs (f32x2)
+    constexpr int kUnits = 1 + kTsNP / 2;
+    for (int t = tid; t < ntask * kUnits; t += kTsThreads) {
+        const int u = t / ntask, tk = t - u * ntask;
         const int rr = tk / ngx, gx = 4 * (tk - rr * ngx);
         const int ro = rr * PA + gx;
         float av[4 * NC4], cen[4];
@@ -350,11 +364,11 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
 #pragma unroll
         for (int o = 0; o < 4; ++o) cen[o] = av[o + R];
         float *const out = P0 + (size_t)rr * nxp + gx;
-        {
-            // inputs moved exactly to the task's reference velocity (three
-            // FMAs a tap), each output's sums moved to its centre at the end
-            const float ref = cen[1];
-            const float *Q0 = sm + (3 * tr) * NPL, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
+        // inputs moved exactly to the task's reference velocity (three FMAs
+        // a tap), each output's sums moved to its centre at the end
+        const float ref = cen[1];
+        if (u == 0) {
+            const float *Q0 = sm, *Q1 = Q0 + NPL, *Q2 = Q1 + NPL;
             float s[4][3];
 #pragma unroll
             for (int o = 0; o < 4; ++o) s[o][0] = s[o][1] = s[o][2] = 0.f;
@@ -375,23 +389,79 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
                     for (int o = 0; o < 4; ++o) {
                         const int j = e - o;
                         if (j >= 0 && j < W) {
-                            s[o][0] = fmaf(w[j], q0[k], s[o][0]);
-                            s[o][1] = fmaf(w[j], l1, s[o][1]);
-                            s[o][2] = fmaf(w[j], l2, s[o][2]);
+                            s[o][0] = fmaf(a.w1[j], q0[k], s[o][0]);
+                            s[o][1] = fmaf(a.w1[j], l1, s[o][1]);
+                            s[o][2] = fmaf(a.w1[j], l2, s[o][2]);
                         }
                     }
                 }
             }
 #pragma unroll
             for (int o = 0; o < 4; ++o) shift_sums(cen[o] - ref, s[o][0], s[o][1], s[o][2]);
-            float *p = out + (size_t)(3 * tr) * pstride;
-            *reinterpret_cast<float4 *>(p) = make_float4(s[0][0], s[1][0], s[2][0], s[3][0]);
-            *reinterpret_cast<float4 *>(p + pstride) = make_float4(s[0][1], s[1][1], s[2][1], s[3][1]);
-            *reinterpret_cast<float4 *>(p + 2 * pstride) = make_float4(s[0][2], s[1][2], s[2][2], s[3][2]);
-        }
-        if (tr == 0)
+            *reinterpret_cast<float4 *>(out) = make_float4(s[0][0], s[1][0], s[2][0], s[3][0]);
+            *reinterpret_cast<float4 *>(out + pstride) = make_float4(s[0][1], s[1][1], s[2][1], s[3][1]);
+            *reinterpret_cast<float4 *>(out + 2 * pstride) = make_float4(s[0][2], s[1][2], s[2][2], s[3][2]);
             *reinterpret_cast<float4 *>(out + (size_t)(3 * kTsNT) * pstride) =
                 make_float4(cen[0], cen[1], cen[2], cen[3]);
+        } else {
+            // derivative triplets 2P + 1 and 2P + 2 side by side in f32x2
+            // lanes: the same centres, taps and arithmetic as one triplet
+            const int P = u - 1;
+            const float *B0 = sm + 3 * NPL + (3 * P) * 2 * NPL, *B1 = B0 + 2 * NPL, *B2 = B1 + 2 * NPL;
+            const f32x2 Z2 = pk2(0.f, 0.f);
+            f32x2 s0[4], s1[4], s2[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) s0[o] = s1[o] = s2[o] = Z2;
+#pragma unroll
+            for (int c4 = 0; c4 < NC4; ++c4) {
+                const float *b0 = B0 + 2 * (ro + 4 * c4), *b1 = B1 + 2 * (ro + 4 * c4), *b2 = B2 + 2 * (ro + 4 * c4);
+                const ulonglong2 x0 = *reinterpret_cast<const ulonglong2 *>(b0);
+                const ulonglong2 y0 = *reinterpret_cast<const ulonglong2 *>(b0 + 4);
+                const ulonglong2 x1 = *reinterpret_cast<const ulonglong2 *>(b1);
+                const ulonglong2 y1 = *reinterpret_cast<const ulonglong2 *>(b1 + 4);
+                const ulonglong2 x2 = *reinterpret_cast<const ulonglong2 *>(b2);
+                const ulonglong2 y2 = *reinterpret_cast<const ulonglong2 *>(b2 + 4);
+                const f32x2 q0[4] = {x0.x, x0.y, y0.x, y0.y}, q1[4] = {x1.x, x1.y, y1.x, y1.y};
+                const f32x2 q2[4] = {x2.x, x2.y, y2.x, y2.y};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = 4 * c4 + k;
+                    if (e >= NIN) break;
+                    const float d = av[e] - ref;
+                    const f32x2 D = pk2(d, d);
+                    const f32x2 l1 = fma2(D, q0[k], q1[k]);
+                    const f32x2 l2 = fma2(D, fma2(D, q0[k], add2(q1[k], q1[k])), q2[k]);
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        const int j = e - o;
+                        if (j >= 0 && j < W) {
+                            s0[o] = fma2(a.w2[j], q0[k], s0[o]);
+                            s1[o] = fma2(a.w2[j], l1, s1[o]);
+                            s2[o] = fma2(a.w2[j], l2, s2[o]);
+                        }
+                    }
+                }
+            }
+            float r[3][2][4];  // [component][triplet of the pair][output]
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                float a0, b0, a1, b1, a2, b2;
+                upk2(s0[o], a0, b0);
+                upk2(s1[o], a1, b1);
+                upk2(s2[o], a2, b2);
+                const float dl = cen[o] - ref;
+                shift_sums(dl, a0, a1, a2);
+                shift_sums(dl, b0, b1, b2);
+                r[0][0][o] = a0; r[1][0][o] = a1; r[2][0][o] = a2;
+                r[0][1][o] = b0; r[1][1][o] = b1; r[2][1][o] = b2;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    *reinterpret_cast<float4 *>(out + (size_t)(3 * (2 * P + 1 + h) + m) * pstride) =
+                        make_float4(r[m][h][0], r[m][h][1], r[m][h][2], r[m][h][3]);
+        }
     }
 }
 
@@ -435,7 +505,6 @@ __global__ void __launch_bounds__(kTsThreads, 2)
     const int tiles_x = RAG ? (g.nx + kTsTX - 1) / kTsTX : a.tiles_x;
     const int tiles = RAG ? tiles_x * ((g.ny + kTsTY - 1) / kTsTY) : a.tiles;
     double *const part0 = a.part + (RAG ? (size_t)a.tile_base[model] : (size_t)model * a.tiles) * kTsEnt;
-    const float *const tab = RAG ? a.tab + a.tab_off[model] : a.tab;
     const int tx0 = (tile % tiles_x) * kTsTX, ty0 = (tile / tiles_x) * kTsTY;
     const int nxo = min(kTsTX, g.nx - tx0), nyo = min(kTsTY, g.ny - ty0);
     bool loaded = true;
@@ -468,9 +537,6 @@ __global__ void __launch_bounds__(kTsThreads, 2)
     if (tid < (int)(sizeof(ModelConst) / 4))
         reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
     if (tid == 32) s_ob = a.obs_list ? a.obs_list[model] : a.obs;
-    float w[W];
-#pragma unroll
-    for (int j = 0; j < W; ++j) w[j] = tab[kTsTabTaps + j];
     if constexpr (!RAG) loaded = mbar_wait(&bar, 0, kTsWaitLimit);
     if (__syncthreads_or(!loaded)) {  // the same decision in every thread
         if (tid == 0) {
@@ -514,9 +580,9 @@ __global__ void __launch_bounds__(kTsThreads, 2)
                 for (int o = 0; o < 2; ++o) {
                     const int j = e - o;
                     if (j >= 0 && j < W) {
-                        s[o][0] = fmaf(w[j], q0, s[o][0]);
-                        s[o][1] = fmaf(w[j], l1, s[o][1]);
-                        s[o][2] = fmaf(w[j], l2, s[o][2]);
+                        s[o][0] = fmaf(a.w1[j], q0, s[o][0]);
+                        s[o][1] = fmaf(a.w1[j], l1, s[o][1]);
+                        s[o][2] = fmaf(a.w1[j], l2, s[o][2]);
                     }
                 }
             }
@@ -645,6 +711,25 @@ struct TsLayout {
 };
 
 static size_t ts_al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Normalised PSF taps exp(-j^2 / (2 sigma^2)) / sum of a launch (every model
+// of a launch has the same PSF), as floats and as (w, w) pairs.
+static void ts_taps(int R, float sigma, TsArgs &a)
+{
+    double v[2 * kTsplitMaxR + 1], sum = 0.0;
+    for (int j = -R; j <= R; ++j) {
+        const double t = (R == 0) ? 0.0 : (double)j / (double)sigma;
+        v[j + R] = std::exp(-0.5 * t * t);
+        sum += v[j + R];
+    }
+    for (int j = 0; j <= 2 * R; ++j) {
+        const float f = (float)(v[j] / sum);
+        uint32_t b;
+        std::memcpy(&b, &f, 4);
+        a.w1[j] = f;
+        a.w2[j] = ((f32x2)b << 32) | (f32x2)b;
+    }
+}
 
 static size_t ts_smem_a(const Geom &g, int ra)
 {
@@ -830,6 +915,7 @@ gbk_status launch_tsplit(const TsplitCall &call, void *ws, size_t ws_bytes, cuda
         a.ra = L.ra;
         a.tiles_x = L.tiles_x;
         a.tiles = L.tiles;
+        ts_taps(g.R, g.sig_xy, a);
         if (overlap && c >= 2 && (e = cudaStreamWaitEvent(st, aux->psf[b], 0)) != cudaSuccess)
             return cuda_fail(e, "split Jacobian: ordering the stages");
         gbk_status s = ts_launch_stage_r(0, tm, a, st);
@@ -858,11 +944,14 @@ void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std
             ts_smem_b(g.R) > 200 * 1024)
             return;
     }
-    // galaxies by PSF radius (the stages are compiled per radius), index
-    // order within a radius; a chunk never mixes radii
+    // galaxies by PSF radius (the stages are compiled per radius) and PSF
+    // width (a launch's taps travel in its parameters), index order within
+    // those; a chunk never mixes them
     std::vector<int> ord(n);
     for (int m = 0; m < n; ++m) ord[m] = m;
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return geo[a].R < geo[b].R; });
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        return geo[a].R != geo[b].R ? geo[a].R < geo[b].R : geo[a].sig_xy < geo[b].sig_xy;
+    });
     p->tab_off.resize(n);
     p->ra.resize(n);
     p->tile_base.resize(n);
@@ -875,20 +964,24 @@ void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std
     p->chunk_b.push_back(0);
     bool first = true;
     int prev_r = -1;
+    float prev_sig = 0.f;
     for (int j = 0; j < n; ++j) {
         const int m = ord[j];
         if (active && !(*active)[m]) continue;  // no work, no planes, no part slots
         const Geom &g = geo[m];
         const int nxp = (g.nx + 3) & ~3;
         const long long planes = (long long)kTsPlanes * g.ey * nxp;
-        if (!first && (g.R != prev_r || cum + planes - chunk_start > budget)) {  // close the chunk before galaxy m
+        if (!first && (g.R != prev_r || g.sig_xy != prev_sig || cum + planes - chunk_start > budget)) {
+            // close the chunk before galaxy m
             p->chunk_a.push_back((int)p->work_a.size());
             p->chunk_b.push_back((int)p->work_b.size());
             p->chunk_r.push_back(prev_r);
+            p->chunk_sig.push_back(prev_sig);
             chunk_start = cum;
         }
         first = false;
         prev_r = g.R;
+        prev_sig = g.sig_xy;
         p->pl_off[m] = cum - chunk_start;
         chunk_of[m] = (int)p->chunk_r.size();
         largest = std::max(largest, planes);
@@ -907,6 +1000,7 @@ void tsplit_ragged_plan(const std::vector<Geom> &geo, TsRaggedPlan *p, const std
         p->chunk_a.push_back((int)p->work_a.size());
         p->chunk_b.push_back((int)p->work_b.size());
         p->chunk_r.push_back(prev_r);
+        p->chunk_sig.push_back(prev_sig);
     }
     // A plane buffer holds any chunk: no chunk exceeds the budget unless one
     // galaxy does, nor the planes of all the active galaxies.  The bound
@@ -1030,6 +1124,9 @@ gbk_status launch_tsplit_ragged(const TsRaggedPlan &p, const TsplitRaggedCall &c
     cudaStream_t sb = overlap ? aux->s : st;
     for (int c = 0; c < nch; ++c) {
         const int b = c & 1;
+        if (p.chunk_r[c] > kTsplitMaxR)
+            return fail(GBK_EUNSUPPORTED, "split Jacobian: PSF radius %d > %d", p.chunk_r[c], kTsplitMaxR);
+        ts_taps(p.chunk_r[c], p.chunk_sig[c], a);
         if (overlap && c >= 2 && (e = cudaStreamWaitEvent(st, aux->psf[b], 0)) != cudaSuccess)
             return cuda_fail(e, "split Jacobian: ordering the stages");
         for (int stage = 0; stage < 2; ++stage) {

@@ -49,6 +49,7 @@ struct TsRaggedPlan {
     std::vector<int2> work_a, work_b;   // (galaxy, row block) and (galaxy, tile), chunk by chunk
     std::vector<int> chunk_a, chunk_b;  // work ranges of the chunks (n_chunks + 1 entries)
     std::vector<int> chunk_r;           // PSF radius of each chunk's galaxies
+    std::vector<float> chunk_sig;       // and their PSF width (sigma, pixels)
     int nbuf = 1;                       // plane buffers (2: a chunk's PSF stage beside the next line stage)
     size_t smem_a = 0;
     size_t o_mcs = 0, o_tab = 0, o_pl = 0, o_part = 0, o_arr = 0, o_taboff = 0, o_ra = 0, o_tbase = 0, o_ploff = 0,
