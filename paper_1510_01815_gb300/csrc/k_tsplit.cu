@@ -152,8 +152,8 @@ __global__ void tsplit_setup_ragged_kernel(const double *params, const Geom *geo
 // t = k + 1: d/dp_k), about the centre a (returned).  Whole warps (inactive
 // lanes allowed).
 __device__ __forceinline__ float tangent_spaxel(const Geom &g, const ModelConst &c, const double *pm, const float *tzx,
-                                                const float *tzy, const float *tzz, int ezp, float x, float y,
-                                                float rec[3 * kTsNT])
+                                                const float *tzy, const float *tzz, int ezp, int elo, int ehi,
+                                                float var_z, float x, float y, float rec[3 * kTsNT])
 {
     const float kdeg = 0.017453292519943295f;  // radians per degree
     const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;
@@ -218,21 +218,28 @@ __device__ __forceinline__ float tangent_spaxel(const Geom &g, const ModelConst 
     e0 = max(0, e0) & ~1;
     e1 = min(ezp, (e1 + 1) & ~1);
 
-    // channel sums: SG_k = sum g d^k G0 (k <= 4), S1_k = sum g d^k H1 (k <= 3), S2_k = sum g d^k H2 (k <= 2)
+    // channel sums: SG_k = sum g d^k G0 (k <= 4), S1_k = sum g d^k H1 (k <= 3), S2_k = sum g d^k H2 (k <= 2).
+    // Interior channels [elo, ehi) have their whole LSF window in the band:
+    // G0 = 1, H1 = 0, H2 = the LSF variance there, so they need no table and
+    // only the sums of g d^k; the band-edge channels read the tables.  The
+    // segments keep whole channel pairs (the interior starts and stops at
+    // even channels inside [elo, ehi); the edge loops take the rest, whose
+    // tables are valid for every channel).
     float SG[5], S1[4], S2[3];
     {
-        const f32x2 Z2 = pk2(0.f, 0.f), AL = pk2(c.alpha, c.alpha), DV2 = pk2(2.f * g.dv, 2.f * g.dv);
+        const f32x2 Z2 = pk2(0.f, 0.f), AL2 = pk2(c.alpha * c.alpha, c.alpha * c.alpha);
+        const f32x2 DV2 = pk2(2.f * g.dv, 2.f * g.dv);
         f32x2 A0 = Z2, A1 = Z2, A2 = Z2, A3 = Z2, A4 = Z2, B0 = Z2, B1 = Z2, B2 = Z2, B3 = Z2, C0 = Z2, C1 = Z2,
               C2 = Z2;
+        f32x2 I0 = Z2, I1 = Z2, I2 = Z2, I3 = Z2, I4 = Z2;
+        const int eil = max(e0, min(e1, (elo + 1) & ~1)), eih = max(eil, min(e1, ehi & ~1));
         f32x2 D = pk2(fmaf((float)e0, g.dv, base), fmaf((float)(e0 + 1), g.dv, base));
-#pragma unroll 2
-        for (int e = e0; e < e1; e += 2) {
-            const f32x2 T = mul2(D, AL);
-            const f32x2 W = mul2(T, T);
+        auto edge_pair = [&](int e) {
+            const f32x2 D2 = mul2(D, D);
+            const f32x2 W = mul2(D2, AL2);
             float w0, w1;
             upk2(W, w0, w1);
             const f32x2 G0 = pk2(ex2_approx(-w0), ex2_approx(-w1));
-            const f32x2 D2 = mul2(D, D);
             const f32x2 G1 = mul2(G0, D), G2 = mul2(G0, D2);
             const f32x2 G3 = mul2(G1, D2), G4 = mul2(G2, D2);
             const f32x2 TX = *reinterpret_cast<const f32x2 *>(tzx + e);
@@ -243,10 +250,27 @@ __device__ __forceinline__ float tangent_spaxel(const Geom &g, const ModelConst 
             B0 = fma2(G0, TY, B0); B1 = fma2(G1, TY, B1); B2 = fma2(G2, TY, B2); B3 = fma2(G3, TY, B3);
             C0 = fma2(G0, TZ, C0); C1 = fma2(G1, TZ, C1); C2 = fma2(G2, TZ, C2);
             D = add2(D, DV2);
+        };
+        int e = e0;
+        for (; e < eil; e += 2) edge_pair(e);
+#pragma unroll 2
+        for (; e < eih; e += 2) {
+            const f32x2 D2 = mul2(D, D);
+            const f32x2 W = mul2(D2, AL2);
+            float w0, w1;
+            upk2(W, w0, w1);
+            const f32x2 G0 = pk2(ex2_approx(-w0), ex2_approx(-w1));
+            const f32x2 G1 = mul2(G0, D), G2 = mul2(G0, D2);
+            I0 = add2(I0, G0); I1 = add2(I1, G1); I2 = add2(I2, G2);
+            I3 = fma2(G1, D2, I3); I4 = fma2(G2, D2, I4);
+            D = add2(D, DV2);
         }
-        SG[0] = hsum2(A0); SG[1] = hsum2(A1); SG[2] = hsum2(A2); SG[3] = hsum2(A3); SG[4] = hsum2(A4);
+        for (; e < e1; e += 2) edge_pair(e);
+        const float i0 = hsum2(I0), i1 = hsum2(I1), i2 = hsum2(I2);
+        SG[0] = hsum2(A0) + i0; SG[1] = hsum2(A1) + i1; SG[2] = hsum2(A2) + i2;
+        SG[3] = hsum2(A3) + hsum2(I3); SG[4] = hsum2(A4) + hsum2(I4);
         S1[0] = hsum2(B0); S1[1] = hsum2(B1); S1[2] = hsum2(B2); S1[3] = hsum2(B3);
-        S2[0] = hsum2(C0); S2[1] = hsum2(C1); S2[2] = hsum2(C2);
+        S2[0] = fmaf(var_z, i0, hsum2(C0)); S2[1] = fmaf(var_z, i1, hsum2(C1)); S2[2] = fmaf(var_z, i2, hsum2(C2));
     }
     // B_km (k: power of d from the derivative; m: moment weight about a)
     float B[3][3];
@@ -310,6 +334,10 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
     for (int i = tid; i < 3 * ezp; i += kTsThreads) tz[i] = tab[kTsTabZ + i];
     __syncthreads();
 
+    // the band's interior channels and the LSF variance there
+    const int elo = edge_lo_end(g), ehi = edge_hi_begin(g);
+    const float var_z = lsf_var(g);
+
     // phase 1: triplets of every extended spaxel of the rows.  Layout: the
     // value triplet's three planes, then the derivative triplets in pairs
     // (2P + 1, 2P + 2), each component of a pair one plane of interleaved
@@ -324,7 +352,7 @@ __global__ void __launch_bounds__(kTsThreads, 3) tsplit_line_kernel(TsArgs a)
         const int dr = kTsThreads / g.ex, dx = kTsThreads - dr * g.ex;
         for (int idx = tid; idx < nsp; idx += kTsThreads) {
             float rec[3 * kTsNT];
-            const float ac = tangent_spaxel(g, mc, pm, tz, tz + ezp, tz + 2 * ezp, ezp, (float)(xe - R),
+            const float ac = tangent_spaxel(g, mc, pm, tz, tz + ezp, tz + 2 * ezp, ezp, elo, ehi, var_z, (float)(xe - R),
                                             (float)(row0 + r - R), rec);
             const int o = r * PA + xe;
 #pragma unroll
