@@ -27,6 +27,7 @@
 // Jacobian (chi2 values for LM decisions come from the fused kernel).
 #include <cooperative_groups.h>
 
+#include "fused_line.cuh"
 #include "gbk_api_internal.h"
 #include "gbk_internal.cuh"
 #include "k_tangent.h"
@@ -246,6 +247,8 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
     const float kdeg = 0.017453292519943295f;  // radians per degree
     const float vz0 = g.vc - ((float)g.Rz + 0.5f * (float)(g.nz - 1)) * g.dv;
     const float v_lo = g.vc - 0.5f * (float)(g.nz - 1) * g.dv, v_hi = g.vc + 0.5f * (float)(g.nz - 1) * g.dv;
+    const int elo = edge_lo_end(g), ehi = edge_hi_begin(g);  // the band's interior channels
+    const float var_z = lsf_var(g);                          // and the LSF variance there
     const float sig = c.sigma, isig2 = 1.f / (sig * sig), isig3 = isig2 / sig;
     const float s0p = (float)a.params[(size_t)model * GBK_NPAR + GBK_SIG0];
     const float dsig_ds0 = (g.lsf_mode == 1) ? s0p / sig : 1.f;
@@ -323,15 +326,20 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
         // argument, two ex2, the powers of d as a shallow tree and twelve
         // packed accumulations; an odd last channel pairs with the padding,
         // whose tap moments are 0.  The two lanes are added at the end.
+        // Interior channels (the LSF window inside the band: G0 = 1, H1 = 0,
+        // H2 = the LSF variance) need no table and only the sums of g d^k;
+        // the segments keep whole pairs inside [elo, ehi), the edge loops
+        // take the rest (their tables hold every channel).
         float SG[5], S1[4], S2[3];
         {
             const f32x2 Z2 = pk2(0.f, 0.f), AL = pk2(c.alpha, c.alpha), DV = pk2(g.dv, g.dv);
             const f32x2 BASE = pk2(base, base), TWO = pk2(2.f, 2.f);
             f32x2 A0 = Z2, A1 = Z2, A2 = Z2, A3 = Z2, A4 = Z2, B0 = Z2, B1 = Z2, B2 = Z2, B3 = Z2, C0 = Z2, C1 = Z2,
                   C2 = Z2;
+            f32x2 I0 = Z2, I1 = Z2, I2 = Z2, I3 = Z2, I4 = Z2;
+            const int eil = max(e0, min(e1, (elo + 1) & ~1)), eih = max(eil, min(e1, ehi & ~1));
             f32x2 FE = pk2((float)e0, (float)(e0 + 1));
-#pragma unroll 2
-            for (int e = e0; e < e1; e += 2) {
+            auto edge_pair = [&](int e) {
                 const f32x2 D = fma2(FE, DV, BASE);
                 const f32x2 T = mul2(D, AL);
                 const f32x2 W = mul2(T, T);
@@ -349,10 +357,30 @@ __global__ void __launch_bounds__(kTangentThreads, NP == GBK_I0 ? 2 : 1) tangent
                 B0 = fma2(G0, TY, B0); B1 = fma2(G1, TY, B1); B2 = fma2(G2, TY, B2); B3 = fma2(G3, TY, B3);
                 C0 = fma2(G0, TZ, C0); C1 = fma2(G1, TZ, C1); C2 = fma2(G2, TZ, C2);
                 FE = add2(FE, TWO);
+            };
+            int e = e0;
+            for (; e < eil; e += 2) edge_pair(e);
+#pragma unroll 2
+            for (; e < eih; e += 2) {
+                const f32x2 D = fma2(FE, DV, BASE);
+                const f32x2 T = mul2(D, AL);
+                const f32x2 W = mul2(T, T);
+                float w0, w1;
+                upk2(W, w0, w1);
+                const f32x2 G0 = pk2(ex2_approx(-w0), ex2_approx(-w1));
+                const f32x2 D2 = mul2(D, D);
+                const f32x2 G1 = mul2(G0, D), G2 = mul2(G0, D2);
+                I0 = add2(I0, G0); I1 = add2(I1, G1); I2 = add2(I2, G2);
+                I3 = fma2(G1, D2, I3); I4 = fma2(G2, D2, I4);
+                FE = add2(FE, TWO);
             }
-            SG[0] = hsum2(A0); SG[1] = hsum2(A1); SG[2] = hsum2(A2); SG[3] = hsum2(A3); SG[4] = hsum2(A4);
+            for (; e < e1; e += 2) edge_pair(e);
+            const float i0 = hsum2(I0), i1 = hsum2(I1), i2 = hsum2(I2);
+            SG[0] = hsum2(A0) + i0; SG[1] = hsum2(A1) + i1; SG[2] = hsum2(A2) + i2;
+            SG[3] = hsum2(A3) + hsum2(I3); SG[4] = hsum2(A4) + hsum2(I4);
             S1[0] = hsum2(B0); S1[1] = hsum2(B1); S1[2] = hsum2(B2); S1[3] = hsum2(B3);
-            S2[0] = hsum2(C0); S2[1] = hsum2(C1); S2[2] = hsum2(C2);
+            S2[0] = fmaf(var_z, i0, hsum2(C0)); S2[1] = fmaf(var_z, i1, hsum2(C1));
+            S2[2] = fmaf(var_z, i2, hsum2(C2));
         }
         // B_km (k: power of d from the derivative; m: moment weight about a)
         float B[3][3];
