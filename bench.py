@@ -1338,14 +1338,21 @@ def run_gbk(args):
     e_obs = gbk.Obs(*d_obs)
     d_chi2 = torch.empty(n, dtype=torch.float64, device=dev)
 
+    if split:
+        # the host-buffer entry point: parameters, maps and chi2 in pinned
+        # host memory, the copies inside the call (the maps' copy beside the
+        # first line stage)
+        h_obs = gbk.Obs(*pin_obs)
+        ws_host = torch.empty(gbk.gbk_chi2_host_workspace_bytes(g, n), dtype=torch.uint8, device=dev)
+
     def e2e_step(s):
+        if split:
+            gbk.gbk_chi2_host(g, pin_params[s], h_obs, pin_chi2[s], ws_host, stream)
+            return
         d_params.copy_(pin_params[s], non_blocking=True)
         for d, h in zip(d_obs, pin_obs):
             d.copy_(h, non_blocking=True)
-        if split:
-            gbk.gbk_chi2(g, d_params, e_obs, d_chi2, None, gbk.PATH_SPLIT, ws_split, stream)
-        else:
-            gbk.gbk_chi2(g, d_params, e_obs, d_chi2, None, gbk.PATH_AUTO, None, stream)
+        gbk.gbk_chi2(g, d_params, e_obs, d_chi2, None, gbk.PATH_AUTO, None, stream)
         pin_chi2[s].copy_(d_chi2, non_blocking=True)
 
     for s in range(W):

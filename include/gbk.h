@@ -191,6 +191,24 @@ GBK_API gbk_status gbk_chi2(const gbk_geom *g, int32_t n_models, const double *p
                     const gbk_obs *obs, double *chi2, float *resid, uint32_t flags,
                     void *workspace, size_t ws_bytes, void *stream);
 
+/* gbk_chi2 on the split path with every array in HOST memory (Eq. 11; the
+ * call a user with data on the host makes): the parameters are copied on
+ * `stream`, the observed maps on the split evaluator's second stream so that
+ * their copy overlaps the first line stage (which does not read them), and
+ * chi2 comes back on `stream`.  Asynchronous: host buffers must stay valid
+ * until the stream has passed the call; pinned buffers make the copies
+ * asynchronous, pageable ones are copied synchronously by the runtime.
+ *  params     host [n_models][GBK_NPAR] FP64
+ *  obs        host struct of HOST pointers to the five maps [ny][nx]
+ *  chi2       host [n_models] FP64, written when the stream reaches it
+ *  workspace  device scratch of gbk_chi2_host_workspace_bytes(g, n_models)
+ *             bytes (the device copies and the split evaluator's buffer)
+ * GBK_EUNSUPPORTED for geometries the split path does not serve (cube model,
+ * u = 1, PSF radius <= 8). */
+GBK_API size_t gbk_chi2_host_workspace_bytes(const gbk_geom *g, int32_t n_models);
+GBK_API gbk_status gbk_chi2_host(const gbk_geom *g, int32_t n_models, const double *params, const gbk_obs *obs,
+                                 double *chi2, void *workspace, size_t ws_bytes, void *stream);
+
 /* gbk_chi2 on the staged path for callers that cannot allocate device
  * memory (no counterpart in the paper).  A host application whose device
  * memory is owned and pre-planned by another framework, or a real-time

@@ -332,6 +332,85 @@ gbk_status gbk_chi2(const gbk_geom *gin, int32_t n_models, const double *params,
     return run_fused(g, n_models, params, nullptr, obs, chi2, resid, st);
 }
 
+// Workspace of gbk_chi2_host: the device copies of the parameters, the
+// chi2 values and the observed maps, then the split evaluator's region.
+struct HostCallLayout {
+    size_t params, chi2, maps, mask, split, total;
+};
+
+static HostCallLayout host_call_layout(const Geom &g, int n)
+{
+    HostCallLayout L;
+    const size_t np = (size_t)g.nx * g.ny;
+    size_t o = 0;
+    L.params = o; o += align256(sizeof(double) * GBK_NPAR * n);
+    L.chi2 = o; o += align256(sizeof(double) * n);
+    L.maps = o; o += align256(sizeof(float) * 4 * np);
+    L.mask = o; o += align256(np);
+    L.split = o; o += split_workspace_bytes(g, n);
+    L.total = o;
+    return L;
+}
+
+size_t gbk_chi2_host_workspace_bytes(const gbk_geom *gin, int32_t n_models)
+{
+    ok();
+    Geom g;
+    if (derive_geom(gin, &g) != GBK_OK) return 0;
+    if (n_models < 1) { fail(GBK_EINVAL, "n_models must be >= 1"); return 0; }
+    if (!split_supported(g)) { fail(GBK_EUNSUPPORTED, "the split evaluator does not serve this geometry"); return 0; }
+    return host_call_layout(g, n_models).total;
+}
+
+gbk_status gbk_chi2_host(const gbk_geom *gin, int32_t n_models, const double *params, const gbk_obs *obs,
+                         double *chi2, void *workspace, size_t ws_bytes, void *stream)
+{
+    Geom g;
+    gbk_status s = derive_geom(gin, &g);
+    if (s) return s;
+    if (n_models < 0) return fail(GBK_EINVAL, "n_models must be >= 0");
+    if (n_models == 0) return ok();
+    if (!params || !chi2 || !obs) return fail(GBK_EINVAL, "params, obs and chi2 must not be NULL");
+    if (!obs->v_obs || !obs->s_obs || !obs->w_v || !obs->w_s || !obs->mask)
+        return fail(GBK_EINVAL, "every observed map must be given");
+    if (!split_supported(g)) return fail(GBK_EUNSUPPORTED, "the split evaluator does not serve this geometry");
+    const HostCallLayout L = host_call_layout(g, n_models);
+    if (!workspace || ws_bytes < L.total)
+        return fail(GBK_EWORKSPACE, "gbk_chi2_host needs %zu bytes of workspace (got %zu)", L.total, ws_bytes);
+    if ((s = check_device_ptr(workspace, "workspace", 256))) return s;
+    SplitAux *aux = nullptr;
+    if ((s = split_aux(&aux))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    const size_t np = (size_t)g.nx * g.ny, mb = sizeof(float) * np;
+    double *d_params = (double *)(ws + L.params), *d_chi2 = (double *)(ws + L.chi2);
+    float *d_maps = (float *)(ws + L.maps);
+    uint8_t *d_mask = (uint8_t *)(ws + L.mask);
+    const gbk_obs d_obs = {d_maps, d_maps + np, d_maps + 2 * np, d_maps + 3 * np, d_mask};
+    // The parameters go on the caller's stream (the line stage needs them);
+    // the maps on the PSF stages' stream, after everything the caller's
+    // stream holds (an earlier call's PSF stage may still read this
+    // workspace), so that their copy overlaps the line stage.
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_params, params, sizeof(double) * GBK_NPAR * n_models, cudaMemcpyDefault, st)) ||
+        (e = cudaEventRecord(aux->start, st)) || (e = cudaStreamWaitEvent(aux->s, aux->start, 0)) ||
+        (e = cudaMemcpyAsync((void *)d_obs.v_obs, obs->v_obs, mb, cudaMemcpyDefault, aux->s)) ||
+        (e = cudaMemcpyAsync((void *)d_obs.s_obs, obs->s_obs, mb, cudaMemcpyDefault, aux->s)) ||
+        (e = cudaMemcpyAsync((void *)d_obs.w_v, obs->w_v, mb, cudaMemcpyDefault, aux->s)) ||
+        (e = cudaMemcpyAsync((void *)d_obs.w_s, obs->w_s, mb, cudaMemcpyDefault, aux->s)) ||
+        (e = cudaMemcpyAsync((void *)d_obs.mask, obs->mask, np, cudaMemcpyDefault, aux->s)) ||
+        (e = cudaEventRecord(aux->obs, aux->s)))
+        return cuda_fail(e, "gbk_chi2_host: copies to the device");
+    if ((s = launch_split(g, n_models, d_params, &d_obs, nullptr, d_chi2, nullptr, ws + L.split, L.total - L.split, st,
+                          nullptr, nullptr, aux->obs)))
+        return s;
+    // the last PSF stage is joined to st (or ran on it after the maps'
+    // event), so the maps' stream holds nothing past this point
+    if ((e = cudaMemcpyAsync(chi2, d_chi2, sizeof(double) * n_models, cudaMemcpyDefault, st)))
+        return cuda_fail(e, "gbk_chi2_host: chi2 to the host");
+    return ok();
+}
+
 gbk_status gbk_chi2_stage_times(const gbk_geom *gin, int32_t n_models, const double *params, const gbk_obs *obs,
                                 double *chi2, void *workspace, size_t ws_bytes, float *stage_ms, void *stream)
 {

@@ -521,7 +521,9 @@ gbk_status split_aux(SplitAux **out)
             (e = cudaEventCreateWithFlags(&y.line[0], cudaEventDisableTiming)) ||
             (e = cudaEventCreateWithFlags(&y.line[1], cudaEventDisableTiming)) ||
             (e = cudaEventCreateWithFlags(&y.psf[0], cudaEventDisableTiming)) ||
-            (e = cudaEventCreateWithFlags(&y.psf[1], cudaEventDisableTiming)))
+            (e = cudaEventCreateWithFlags(&y.psf[1], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&y.start, cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&y.obs, cudaEventDisableTiming)))
             return cuda_fail(e, "split evaluator: creating the PSF stages' stream");
         x = y;
     }
@@ -531,7 +533,7 @@ gbk_status split_aux(SplitAux **out)
 
 gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_obs *obs, float *maps, double *chi2,
                         float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer,
-                        const SplitBatch *batch)
+                        const SplitBatch *batch, cudaEvent_t obs_ready)
 {
     if (batch && batch->mpg < 1) return fail(GBK_EINVAL, "split evaluator: models per galaxy must be >= 1");
     if ((chi2 || resid) && !obs && !(batch && batch->obs_list))
@@ -611,6 +613,8 @@ gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_ob
         if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
         if (overlap && ((e = cudaEventRecord(aux->line[b], st)) || (e = cudaStreamWaitEvent(sb, aux->line[b], 0))))
             return cuda_fail(e, "split evaluator: ordering the stages");
+        if (obs_ready && c == 0 && (e = cudaStreamWaitEvent(sb, obs_ready, 0)) != cudaSuccess)
+            return cuda_fail(e, "split evaluator: waiting for the observed maps");
         if ((s = launch_stage_r(1, tm, a, sb))) return s;
         if (timer && (e = timer->mark(st)) != cudaSuccess) return cuda_fail(e, "split evaluator: timing event");
         if (overlap && (e = cudaEventRecord(aux->psf[b], sb)) != cudaSuccess)

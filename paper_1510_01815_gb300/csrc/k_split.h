@@ -47,6 +47,7 @@ SplitEncodeFn split_encode_fn();
 struct SplitAux {
     cudaStream_t s = nullptr;
     cudaEvent_t line[2] = {nullptr, nullptr}, psf[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr, obs = nullptr;  // a host-buffer call's start and its maps' arrival
 };
 gbk_status split_aux(SplitAux **out);
 
@@ -61,8 +62,10 @@ struct SplitBatch {
     const int32_t *skip;
     int mpg;
 };
+// obs_ready (or null): an event the first PSF stage waits for (the observed
+// maps' copy); the line stages do not read the maps.
 gbk_status launch_split(const Geom &g, int n, const double *params, const gbk_obs *obs, float *maps, double *chi2,
                         float *resid, void *ws, size_t ws_bytes, cudaStream_t st, SplitTimer *timer = nullptr,
-                        const SplitBatch *batch = nullptr);
+                        const SplitBatch *batch = nullptr, cudaEvent_t obs_ready = nullptr);
 
 }  // namespace gbk

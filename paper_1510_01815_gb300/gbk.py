@@ -87,6 +87,8 @@ def lib():
             "gbk_split_stage_times": (i32, [gp, i32, vp, op, vp, vp, sz, ctypes.POINTER(ctypes.c_float),
                                             ctypes.POINTER(ctypes.c_int32), vp]),
             "gbk_chi2_noalloc": (i32, [gp, i32, vp, op, vp, vp, vp]),
+            "gbk_chi2_host_workspace_bytes": (sz, [gp, i32]),
+            "gbk_chi2_host": (i32, [gp, i32, vp, op, vp, vp, sz, vp]),
             "gbk_measure_alu_peak": (i32, [ctypes.POINTER(ctypes.c_double)] * 3 + [vp]),
             "gbk_autotune": (i32, [gp, i32, vp, op, vp, ctypes.POINTER(CTuning), vp]),
             "gbk_get_tuning": (i32, [gp, ctypes.POINTER(CTuning)]),
@@ -151,7 +153,7 @@ def lib():
 
 def exported_symbols():
     return ["gbk_workspace_bytes", "gbk_eval_cubes", "gbk_chi2", "gbk_chi2_from_maps", "gbk_chi2_stage_times", "gbk_split_stage_times",
-            "gbk_chi2_noalloc",
+            "gbk_chi2_noalloc", "gbk_chi2_host_workspace_bytes", "gbk_chi2_host",
             "gbk_measure_alu_peak", "gbk_autotune", "gbk_get_tuning", "gbk_set_tuning",
             "gbk_fit_lm_workspace_bytes", "gbk_fit_lm", "gbk_fit_lm_fallback_workspace_bytes", "gbk_fit_lm_fallback",
             "gbk_wait_selfcheck",
@@ -283,6 +285,26 @@ def gbk_chi2_noalloc(geom, params, obs, chi2, resid=None, stream=None):
     _check(lib().gbk_chi2_noalloc(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"),
                                   ctypes.byref(obs.c()), _ptr(chi2, torch.float64, "chi2"),
                                   _ptr(resid, torch.float32, "resid"), _stream(stream)))
+
+
+def gbk_chi2_host_workspace_bytes(geom, n_models):
+    g = cgeom(geom)
+    n = lib().gbk_chi2_host_workspace_bytes(ctypes.byref(g), int(n_models))
+    err = lib().gbk_last_error().decode()
+    if n == 0 and err:
+        raise GbkError(GBK_EUNSUPPORTED if "serve" in err else GBK_EINVAL, err)
+    return int(n)
+
+
+def gbk_chi2_host(geom, params, obs, chi2, workspace, stream=None):
+    """chi2 with parameters, maps (an Obs of host tensors) and result in host
+    memory; the copies run inside the call (gbk_chi2_host)."""
+    g = cgeom(geom)
+    n = params.shape[0] if params.dim() == 2 else params.numel() // NPAR
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().gbk_chi2_host(ctypes.byref(g), int(n), _ptr(params, torch.float64, "params"), ctypes.byref(obs.c()),
+                               _ptr(chi2, torch.float64, "chi2"), _ptr(workspace, None, "workspace"), ws_bytes,
+                               _stream(stream)))
 
 
 def gbk_chi2_from_maps(maps, obs, chi2, resid=None, stream=None):

@@ -75,9 +75,15 @@ def test_workspace_sizes(gbk):
     # per 64 x 32 tile and an arrival counter
     assert gbk.gbk_workspace_bytes(SINGLE_GEOM, n, gbk.PATH_SPLIT) == \
         al(60 * n) + al(4 * (24 + 3 * 12)) + al(4 * 42 * 32 * 4 * n) + al(8 * n) + al(4 * n)
-    # the Fabry-Perot geometry: chunks of 48 MiB / (4 x 204 x 192 x 4 B) = 80 models
+    # the Fabry-Perot geometry: chunks of 48 MiB / (4 x 204 x 192 x 4 B) = 80
+    # models, two plane buffers (a chunk's PSF stage beside the next chunk's
+    # line stage)
     fp = gbk.gbk_workspace_bytes(FP_GEOM, 400, gbk.PATH_SPLIT)
-    assert fp == al(60 * 400) + al(4 * (24 + 3 * 24)) + al(4 * 204 * 192 * 4 * 80) + al(8 * 18 * 80) + al(4 * 80)
+    assert fp == al(60 * 400) + al(4 * (24 + 3 * 24)) + al(2 * 4 * 204 * 192 * 4 * 80) + al(8 * 18 * 80) + al(4 * 80)
+    # the host-buffer call adds the device copies of the parameters, chi2 and
+    # the five maps
+    assert gbk.gbk_chi2_host_workspace_bytes(FP_GEOM, 400) == \
+        al(8 * 10 * 400) + al(8 * 400) + al(4 * 4 * 192 * 192) + al(192 * 192) + fp
 
 
 @pytest.mark.parametrize("bad", [
