@@ -113,22 +113,35 @@ __global__ void lm_solve_kernel(LmArgs a)
     const double *JTJ = a.jtj + (size_t)gal * NP * NP;
     const double *JTr = a.jtr + (size_t)gal * NP;
     double lam = a.lambda[gal];
-    double L[NP][NP], d[NP];
+    // the lower triangle in registers (its loads issue together), the
+    // diagonal's reciprocals so that the factorisation and the two
+    // substitutions multiply instead of dividing
+    double A[NP][NP], L[NP][NP], rd[NP], d[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int k = 0; k <= j; ++k) A[j][k] = JTJ[j * NP + k];
     bool ok = false;
     for (int attempt = 0; attempt < 12 && !ok; ++attempt) {
         ok = true;
-        for (int j = 0; j < NP && ok; ++j)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            if (!ok) break;
+#pragma unroll
             for (int k = 0; k <= j; ++k) {
-                double v = JTJ[j * NP + k];
-                if (j == k) v += lam * (JTJ[j * NP + j] > 0.0 ? JTJ[j * NP + j] : 1.0);
+                double v = A[j][k];
+                if (j == k) v += lam * (A[j][j] > 0.0 ? A[j][j] : 1.0);
+#pragma unroll
                 for (int q = 0; q < k; ++q) v -= L[j][q] * L[k][q];
                 if (j == k) {
                     if (!(v > 0.0)) { ok = false; break; }
                     L[j][j] = sqrt(v);
+                    rd[j] = 1.0 / L[j][j];
                 } else {
-                    L[j][k] = v / L[k][k];
+                    L[j][k] = v * rd[k];
                 }
             }
+        }
         if (!ok) lam *= 10.0;
     }
     a.lambda[gal] = lam;
@@ -143,15 +156,19 @@ __global__ void lm_solve_kernel(LmArgs a)
     }
     // forward then back substitution: L L^T d = -JTr
     double y[NP];
+#pragma unroll
     for (int j = 0; j < NP; ++j) {
         double v = -JTr[j];
+#pragma unroll
         for (int q = 0; q < j; ++q) v -= L[j][q] * y[q];
-        y[j] = v / L[j][j];
+        y[j] = v * rd[j];
     }
+#pragma unroll
     for (int j = NP - 1; j >= 0; --j) {
         double v = y[j];
+#pragma unroll
         for (int q = j + 1; q < NP; ++q) v -= L[q][j] * d[q];
-        d[j] = v / L[j][j];
+        d[j] = v * rd[j];
     }
     double dn = 0.0, pn = 0.0, s[NP];
     for (int j = 0; j < NP; ++j) {
@@ -167,10 +184,12 @@ __global__ void lm_solve_kernel(LmArgs a)
     }
     // predicted chi2 decrease of the clipped step s: -(2 s.J^T r + s.J^T J s)
     double sg = 0.0, sas = 0.0;
+#pragma unroll
     for (int j = 0; j < NP; ++j) {
         sg += s[j] * JTr[j];
         double as = 0.0;
-        for (int k = 0; k < NP; ++k) as += JTJ[j * NP + k] * s[k];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) as += (k <= j ? A[j][k] : A[k][j]) * s[k];
         sas += s[j] * as;
     }
     a.pred[gal] = -(2.0 * sg + sas);
@@ -288,7 +307,7 @@ template <int NP>
 static void launch_np(const LmArgs &a, int which, cudaStream_t st)
 {
     if (which == 0) lm_normal_fd_kernel<NP><<<a.n_gal, 256, 0, st>>>(a);
-    else lm_solve_kernel<NP><<<(a.n_gal + 63) / 64, 64, 0, st>>>(a);
+    else lm_solve_kernel<NP><<<(a.n_gal + 31) / 32, 32, 0, st>>>(a);
 }
 
 static void dispatch_np(const LmArgs &a, int which, cudaStream_t st)
