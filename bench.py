@@ -782,7 +782,8 @@ def run_mock_study(gbk, torch, n, device):
         else:
             z = np.abs(q[:, list(FIT_FREE)] - truth[:, list(FIT_FREE)])
             z[:, FIT_FREE.index(synth.PA)] = d[:, synth.PA]
-            z = z / err
+            with np.errstate(divide="ignore", invalid="ignore"):
+                z = z / err  # a zero error (a degenerate J^T J) gives inf: such fits are left out
             ok = np.isfinite(z).all(axis=1)
             r["standardised_within_1sigma"] = {names[k]: float(np.mean(z[ok, j] < 1.0)) for j, k in enumerate(FIT_FREE)}
             r["standardised_within_2sigma"] = {names[k]: float(np.mean(z[ok, j] < 2.0)) for j, k in enumerate(FIT_FREE)}

@@ -537,19 +537,34 @@ __global__ void __launch_bounds__(kTsThreads, 2)
     const int nxo = min(kTsTX, g.nx - tx0), nyo = min(kTsTY, g.ny - ty0);
     bool loaded = true;
     if constexpr (RAG) {
-        // the tile's rows of all 28 planes by coalesced 16-byte loads (beyond
-        // the model's planes: zeros); the plane pitch is a multiple of four
+        // the tile's rows of all 28 planes by untiled bulk copies, one per
+        // plane row inside the model's planes (ncol floats from column tx0:
+        // the plane pitch nxp and tx0 are multiples of four, so every address
+        // and size is a multiple of 16 bytes), completion on the mbarrier;
+        // rows past the planes and columns past nxp are zeroed by stores
         const int nxp = (g.nx + 3) & ~3;
         const size_t pstride = (size_t)g.ey * nxp;
         const float *const src = a.pl + a.pl_off[model];
-        constexpr int C4 = kTsTX / 4;
-        for (int i = tid; i < kTsPlanes * NR * C4; i += kTsThreads) {
-            const int c4 = i % C4, rr = (i / C4) % NR, pl = i / (C4 * NR);
-            const int y = ty0 + rr, xx = tx0 + 4 * c4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (y < g.ey && xx < nxp) v = *reinterpret_cast<const float4 *>(src + pl * pstride + (size_t)y * nxp + xx);
-            *reinterpret_cast<float4 *>(sp + pl * NPL + rr * kTsTX + 4 * c4) = v;
+        const int ncol = min(kTsTX, nxp - tx0);  // >= 4: tx0 < nx <= nxp
+        const int nrv = min(NR, g.ey - ty0);     // >= 1: ty0 < ny <= ey
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            tma_expect(&bar, (uint32_t)(kTsPlanes * nrv * ncol * sizeof(float)));
         }
+        __syncthreads();
+        for (int i = tid; i < kTsPlanes * nrv; i += kTsThreads) {
+            const int pl = i / nrv, rr = i - pl * nrv;
+            bulk_load(sp + pl * NPL + rr * kTsTX, src + pl * pstride + (size_t)(ty0 + rr) * nxp + tx0,
+                      (uint32_t)(ncol * sizeof(float)), &bar);
+        }
+        constexpr int C4 = kTsTX / 4;
+        if (nrv < NR || ncol < kTsTX)
+            for (int i = tid; i < kTsPlanes * NR * C4; i += kTsThreads) {
+                const int c4 = i % C4, rr = (i / C4) % NR, pl = i / (C4 * NR);
+                if (rr >= nrv || 4 * c4 >= ncol)
+                    *reinterpret_cast<float4 *>(sp + pl * NPL + rr * kTsTX + 4 * c4) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
     } else {
         if (tid == 0) {
             mbar_init(&bar, 1);
@@ -565,7 +580,7 @@ __global__ void __launch_bounds__(kTsThreads, 2)
     if (tid < (int)(sizeof(ModelConst) / 4))
         reinterpret_cast<float *>(&mc)[tid] = reinterpret_cast<const float *>(a.mcs + model)[tid];
     if (tid == 32) s_ob = a.obs_list ? a.obs_list[model] : a.obs;
-    if constexpr (!RAG) loaded = mbar_wait(&bar, 0, kTsWaitLimit);
+    loaded = mbar_wait(&bar, 0, kTsWaitLimit);
     if (__syncthreads_or(!loaded)) {  // the same decision in every thread
         if (tid == 0) {
             atomicExch(&g_tsplit_status, 1);

@@ -49,6 +49,19 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap *tmap, void *dst, 
         : "memory");
 }
 
+// Copies `bytes` (a multiple of 16) from global src to shared dst, both
+// 16-byte aligned (an untiled bulk copy); completion is counted on `bar`
+// (armed beforehand by tma_expect for the sum of the copies' bytes).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "{\n .reg .u64 g;\n cvta.to.global.u64 g, %1;\n"
+        " cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [g], %2, [%3];\n}" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Bounded wait for the given phase; false if it did not complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, long limit)
 {
