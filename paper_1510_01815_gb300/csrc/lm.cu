@@ -186,12 +186,13 @@ struct EvalTarget {
     LmSplit split;
     void *sws;
     const TsRaggedPlan *rag = nullptr;  // survey: the ragged split Jacobian's plan (its region at sws)
+    const SurveyLive *live = nullptr;   // survey: the evaluator's launches over the running galaxies
 };
 
 static gbk_status eval_for(const EvalTarget &t, int n_gal, int mpg, const double *params, const gbk_obs *obs_list,
                            const int32_t *skip, double *chi2, float *resid, cudaStream_t st)
 {
-    if (t.sp) return survey_eval(*t.sp, mpg, params, obs_list, skip, nullptr, chi2, resid, st);
+    if (t.sp) return survey_eval(*t.sp, mpg, params, obs_list, skip, nullptr, chi2, resid, st, t.live);
     if (t.split.eval) {
         const SplitBatch b = {obs_list, skip, mpg};
         return launch_split(*t.g, n_gal * mpg, params, nullptr, nullptr, chi2, resid, t.sws, t.split.bytes, st,
@@ -532,6 +533,8 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
     int done_iters = 1;
     int planned = n_gal;   // galaxies of the current ragged Jacobian plan
     TsRaggedPlan live;     // its re-plan over the running galaxies
+    SurveyLive slive;      // the survey evaluator's launches over them
+    std::vector<int32_t> h_sorder;
     // one geometry: galaxies in slots 0 .. n_cur; after a compaction the
     // inputs live in the workspace and cmap gives each slot's caller index
     int n_cur = n_gal, flip = 0;
@@ -637,11 +640,12 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
                 if (e != cudaSuccess) return cuda_fail(e, "LM: end graph capture");
                 if ((e = cudaGraphInstantiate(&cg.exec, cg.graph, 0))) return cuda_fail(e, "LM: graph instantiation");
             }
-            if (t.rag && h_active * 4 <= planned && planned > 16) {
-                // Ragged split Jacobian: the finished galaxies' CTAs would only
-                // return at their skip test, so once a quarter of the planned
-                // galaxies are still running, plan the running ones alone and
-                // capture the iteration again.
+            if (t.sp && h_active * 4 <= planned && planned > 16) {
+                // Survey: the finished galaxies' CTAs (ragged split Jacobian)
+                // and work items (evaluator) would only return at their skip
+                // test, so once a quarter of the planned galaxies are still
+                // running, plan the running ones alone and capture the
+                // iteration again.
                 std::vector<int32_t> h_done(n_gal);
                 if ((e = cudaMemcpyAsync(h_done.data(), a.done, sizeof(int32_t) * n_gal, cudaMemcpyDeviceToHost,
                                          st)) ||
@@ -649,12 +653,23 @@ static gbk_status lm_batched(const EvalTarget &t, int n_gal, const gbk_obs *obs,
                     return cuda_fail(e, "LM: reading the running galaxies");
                 std::vector<char> act(n_gal);
                 for (int i = 0; i < n_gal; ++i) act[i] = h_done[i] == 0;
-                tsplit_ragged_plan(t.sp->geo, &live, &act);
-                if (!live.ok || live.total > t.split.bytes) return fail(GBK_EINVAL, "LM: re-planning the survey Jacobian");
-                if ((s = tsplit_ragged_upload(live, (char *)t.sws, st))) return s;
-                planned = h_active;
                 EvalTarget t2 = t;
-                t2.rag = &live;
+                if (t.rag) {
+                    tsplit_ragged_plan(t.sp->geo, &live, &act);
+                    if (!live.ok || live.total > t.split.bytes)
+                        return fail(GBK_EINVAL, "LM: re-planning the survey Jacobian");
+                    if ((s = tsplit_ragged_upload(live, (char *)t.sws, st))) return s;
+                    t2.rag = &live;
+                }
+                survey_live(*t.sp, act, &slive, &h_sorder);
+                int32_t *d_sorder = (int32_t *)(ws + L.clive);
+                if (!h_sorder.empty() &&
+                    (e = cudaMemcpyAsync(d_sorder, h_sorder.data(), sizeof(int32_t) * h_sorder.size(),
+                                         cudaMemcpyHostToDevice, st)))
+                    return cuda_fail(e, "LM: uploading the running galaxies' order");
+                slive.d_order = d_sorder;
+                t2.live = &slive;
+                planned = h_active;
                 cudaGraphExecDestroy(cg.exec);
                 cudaGraphDestroy(cg.graph);
                 cg.exec = nullptr;

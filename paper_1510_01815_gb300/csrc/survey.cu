@@ -351,12 +351,41 @@ gbk_status survey_tangent(const SurveyPlan &sp, const TangentArgs &proto, cudaSt
     return GBK_OK;
 }
 
-gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, const gbk_obs *obs_list,
-                       const int32_t *skip, float *maps, double *chi2, float *resid, cudaStream_t st)
+void survey_live(const SurveyPlan &sp, const std::vector<char> &active, SurveyLive *live,
+                 std::vector<int32_t> *order)
 {
+    live->classes.clear();
+    live->rep.clear();
+    order->clear();
     for (const SurveyClass &c : sp.classes) {
+        SurveyClass k = c;
+        k.beg = (int)order->size();
+        int solo = 0;
+        for (int i = c.beg; i < c.end; ++i) {
+            const int gal = sp.order[i];
+            if (!active[gal]) continue;
+            order->push_back(gal);
+            if (i >= c.end - c.n_solo) ++solo;
+        }
+        k.end = (int)order->size();
+        k.n_solo = solo;
+        if (k.end > k.beg) {
+            live->classes.push_back(k);
+            live->rep.push_back(sp.order[c.beg]);
+        }
+    }
+}
+
+gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, const gbk_obs *obs_list,
+                       const int32_t *skip, float *maps, double *chi2, float *resid, cudaStream_t st,
+                       const SurveyLive *live)
+{
+    const std::vector<SurveyClass> &classes = live ? live->classes : sp.classes;
+    const int32_t *d_order = live ? live->d_order : sp.d_order;
+    for (size_t ci = 0; ci < classes.size(); ++ci) {
+        const SurveyClass &c = classes[ci];
         FusedArgs a = {};
-        a.g = sp.geo[sp.order[c.beg]];
+        a.g = sp.geo[live ? live->rep[ci] : sp.order[c.beg]];
         a.n_models = (c.end - c.beg) * mpg;
         a.params = params;
         a.obs_list = obs_list;
@@ -371,7 +400,7 @@ gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, cons
         a.persistent = c.persistent;
         a.geoms = sp.d_geo;
         a.pix_off = sp.d_pix_off;
-        a.order = sp.d_order + c.beg;
+        a.order = d_order + c.beg;
         a.smem = c.smem;
         if (c.persistent) {
             cudaError_t e = cudaMemsetAsync(sp.d_work, 0, 2 * sizeof(int), st);

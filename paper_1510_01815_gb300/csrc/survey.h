@@ -53,10 +53,24 @@ gbk_status survey_plan(const gbk_geom *geoms, int n_gal, SurveyPlan *sp, const S
 // same survey tunings): repeated calls over one survey skip the planning.
 gbk_status survey_plan_cached(const gbk_geom *geoms, int n_gal, SurveyPlan *sp);
 gbk_status survey_upload(SurveyPlan *sp, char *ws, cudaStream_t st);
-// Models gal * mpg + s (s < mpg) of every galaxy: chi2 [n_gal * mpg] and the
-// packed maps / residuals (galaxy gal at pixel offset pix_off[gal] * mpg).
+// A plan's launches restricted to some of its galaxies (a batched fit's
+// running ones): the classes' ranges index a compacted copy of the order
+// (the device copy is the caller's).
+struct SurveyLive {
+    std::vector<SurveyClass> classes;
+    std::vector<int32_t> rep;  // per class: the galaxy whose geometry the full plan's launch carries
+    const int32_t *d_order = nullptr;
+};
+// Fills live->classes and the compacted order (host) for the galaxies with
+// active[g] != 0; the caller uploads the order and sets live->d_order.
+void survey_live(const SurveyPlan &sp, const std::vector<char> &active, SurveyLive *live,
+                 std::vector<int32_t> *order);
+// Models gal * mpg + s (s < mpg) of every galaxy (or of the galaxies of
+// `live`): chi2 [n_gal * mpg] and the packed maps / residuals (galaxy gal at
+// pixel offset pix_off[gal] * mpg).
 gbk_status survey_eval(const SurveyPlan &sp, int mpg, const double *params, const gbk_obs *obs_list,
-                       const int32_t *skip, float *maps, double *chi2, float *resid, cudaStream_t st);
+                       const int32_t *skip, float *maps, double *chi2, float *resid, cudaStream_t st,
+                       const SurveyLive *live = nullptr);
 struct TangentArgs;
 // J^T J, J^T r and chi2 of one model per galaxy (the analytic Jacobian):
 // `proto` supplies params, obs_list, skip, the free parameters and outputs.
