@@ -115,6 +115,10 @@ def parse():
                     help="split (default: line and PSF stages through an L2-resident buffer), fused (one "
                          "cluster of CTAs per model) or staged (cube materialised in HBM) evaluation")
     ap.add_argument("--quick", action="store_true", help="kernel timing only (for profiler runs)")
+    ap.add_argument("--lm-only", default=None, choices=["survey", "single"],
+                    help="run one batched analytic-Jacobian LM fit of the survey (2048 ragged galaxies) or of "
+                         "the single-geometry batch (2048 C1 galaxies), print its fits/s and exit (for "
+                         "profiler runs)")
     ap.add_argument("--tuning", default=None,
                     help="CTAS,THREADS,PERSISTENT: use this fused-kernel tuning instead of autotuning")
     return ap.parse_args()
@@ -1110,6 +1114,26 @@ def run_reference(args):
     }))
 
 
+def run_lm_only(gbk, torch, which, device):
+    """One batched LM fit with the analytic Jacobian of the survey leg's or
+    the fits leg's batch (2048 galaxies each), timed from the host; one JSON
+    line.  Meant for launch lists of the fit's kernels."""
+    opts = gbk.lm_opts(max_iter=200, jacobian=gbk.JAC_TANGENT, free=FIT_FREE)
+    if which == "survey":
+        geoms, truth, obs, p0, lo, hi = survey_batch(gbk, torch, 2048, 4, device)
+        fit = lambda: gbk.survey_fit_lm(geoms, obs, np.array(p0), np.array(lo), np.array(hi), opts, device=device)
+    else:
+        g, truth, obs, p0, lo, hi = fit_batch(gbk, torch, 2048, 4242, device)
+        fit = lambda: gbk.fit_lm(g, obs, p0, lo, hi, opts, device=device)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    q, c, it, st = fit()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    print(json.dumps({"lm_only": which, "galaxies": 2048, "fits_per_s": 2048 / dt, "max_iters": int(np.max(it)),
+                      "iters_sum": int(np.sum(it))}))
+
+
 def run_gbk(args):
     import torch
     from paper_1510_01815_gb300 import build as gbuild
@@ -1121,6 +1145,9 @@ def run_gbk(args):
         raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.lm_only:
+        run_lm_only(gbk, torch, args.lm_only, dev)
+        return
     dist = None
     if ws > 1:
         import torch.distributed as dist
